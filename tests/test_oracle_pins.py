@@ -1,0 +1,344 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix:
+closed forms, invariants and brute force on tiny inputs.  Each pin is
+chosen so that a plausible slip (a dropped term, a flipped sign, a wrong
+index or a transposed operand) in the oracle fails it."""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as la
+import scipy.sparse as sp
+
+from oracle import gasa_oracle as O
+from synth import configs, random_ops as RO
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+CONST = json.load(open(os.path.join(GOLD, "paper_constants.json")))
+SIZES = json.load(open(os.path.join(GOLD, "hierarchy_sizes.json")))
+
+
+def lap1d(n):
+    return sp.diags([-1.0, 2.0, -1.0], [-1, 0, 1], (n, n)).tocsr()
+
+
+def lap1d_modes(n):
+    """eigenpairs of tridiag(-1, 2, -1)/2 (= D^{-1} A for 1x1 blocks)"""
+    k = np.arange(1, n + 1)
+    lam = 1.0 - np.cos(k * np.pi / (n + 1))
+    i = np.arange(1, n + 1)
+    V = np.sin(np.outer(i, k) * np.pi / (n + 1)) * np.sqrt(2.0 / (n + 1))
+    return lam, V
+
+
+def scalar_blocks(A):
+    return O.BlockDiag(np.arange(A.shape[0] + 1), A.diagonal().reshape(-1, 1, 1))
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    pr = configs.poisson2d(8, 1, r=12, n_levels=3, name="tiny")
+    H = O.setup(pr.A.row_ptr, pr.A.col, pr.A.val, pr.agg_of, B0=pr.B0, r=pr.r, dim=2)
+    return pr, H
+
+
+@pytest.fixture(scope="module")
+def tiny2level():
+    pr = configs.poisson2d(8, 1, r=12, n_levels=2, name="tiny2")
+    H = O.setup(pr.A.row_ptr, pr.A.col, pr.A.val, pr.agg_of, B0=pr.B0, r=pr.r, dim=2)
+    return pr, H
+
+
+# ---------------------------------------------------------------------------
+def test_splitmix_published_outputs():
+    g = CONST["splitmix64_seed0"]["value"]
+    u = O.splitmix_uniform(0, 0, 3)
+    want = np.array([int(h, 16) >> 11 for h in g], dtype=np.float64) * 2.0 ** -53
+    np.testing.assert_array_equal(u, want)
+
+
+def test_library_defaults_are_the_papers():
+    from paper_2504_13373_gb300 import gasa
+    try:
+        opt = gasa.gasa_default_options()
+    except RuntimeError:
+        pytest.skip("libgasa.so not built")
+    assert opt.gamma == CONST["gamma"]["value"]
+    assert opt.q_power == CONST["q_power"]["value"]
+    assert opt.omega_factor == CONST["omega_factor"]["value"]
+    assert opt.t_pre == CONST["t_pre"]["value"] and opt.t_post == CONST["t_post"]["value"]
+
+
+def test_block_inverse_identity():
+    pr = configs.poisson2d_p1()
+    S = pr.A.to_scipy()
+    D = O.block_diagonal(S, np.arange(pr.A.n + 1) * 3)
+    Dinv = O.invert_blocks(D)
+    err = np.max(np.abs(np.einsum("uij,ujk->uik", D.blocks, Dinv.blocks) - np.eye(3)))
+    assert err <= 1e-12
+    # D really is the block diagonal: D = A on diagonal blocks, A - D has none
+    R = (S - D.to_sparse()).tocsr()
+    for u in range(0, pr.A.n, 97):
+        assert np.max(np.abs(R[3 * u:3 * u + 3, 3 * u:3 * u + 3].toarray())) == 0.0
+
+
+def test_power_estimate_closed_form():
+    """1-D Laplacian, 1x1 blocks: D^{-1} A has eigenpairs (lam_k, v_k).  From
+    x0 = (v_1 + v_n)/sqrt(2), q steps give x ~ lam_1^q v_1 + lam_n^q v_n and
+    the estimate sqrt(lam_1^{2q+2} + lam_n^{2q+2}) / sqrt(lam_1^{2q} + lam_n^{2q})."""
+    n, q = 50, 3
+    A = lap1d(n)
+    lam, V = lap1d_modes(n)
+    x0 = (V[:, 0] + V[:, -1]) / np.sqrt(2.0)
+    got = O.power_estimate(A, O.invert_blocks(scalar_blocks(A)), x0, q)
+    a, b = lam[0], lam[-1]
+    want = np.sqrt(a ** (2 * q + 2) + b ** (2 * q + 2)) / np.sqrt(a ** (2 * q) + b ** (2 * q))
+    assert abs(got - want) <= 1e-12 * want
+
+
+def test_power_estimate_below_spectral_radius(tiny):
+    pr, H = tiny
+    L = H.levels[0]
+    ev = np.linalg.eigvals(L.Dinv.to_sparse().toarray() @ L.A.toarray())
+    rho = np.max(np.abs(ev))
+    assert L.rho <= rho * (1 + 1e-12)
+    assert L.rho >= 0.5 * rho
+    assert abs(L.omega - CONST["omega_factor"]["value"] / L.rho) <= 1e-15 * L.omega
+
+
+def test_relax_closed_form_two_modes():
+    """x0 = a v_1 + b v_n: after m sweeps x = a mu_1^m v_1 + b mu_n^m v_n with
+    mu = 1 - w lam; the stop sweep is the first m where
+    ||x^(m-1)|| / ||x^(m)|| < 1 + gamma."""
+    n, w, gamma = 40, 0.8, 0.03
+    A = lap1d(n)
+    lam, V = lap1d_modes(n)
+    W = O.invert_blocks(scalar_blocks(A)).scaled(w)
+    a, b = 1.0, 50.0
+    x0 = a * V[:, 0] + b * V[:, -1]
+    mu1, mun = 1 - w * lam[0], 1 - w * lam[-1]
+    nrm = lambda m: np.hypot(a * mu1 ** m, b * mun ** m)
+    m_stop = next(m for m in range(1, 1000) if nrm(m - 1) / nrm(m) < 1 + gamma)
+    Bx, sw = O.relax_candidates(A, W, x0[:, None], gamma, 1000)
+    assert sw[0] == m_stop
+    want = a * mu1 ** m_stop * V[:, 0] + b * mun ** m_stop * V[:, -1]
+    assert np.max(np.abs(Bx[:, 0] - want)) <= 1e-12 * np.max(np.abs(want))
+
+
+def test_relax_cap_and_identity_smoother():
+    """D^{-1}A = I (diagonal A), w = 4/3: x <- x - (4/3) x = -x/3, the norm
+    ratio is always 3 so the cap stops it; after m sweeps x = (-1/3)^m x0."""
+    n = 10
+    A = sp.diags(np.arange(1.0, n + 1)).tocsr()
+    W = O.invert_blocks(scalar_blocks(A)).scaled(4.0 / 3.0)
+    x0 = RO.random_vector(n, 3)
+    Bx, sw = O.relax_candidates(A, W, x0[:, None], 0.03, 7)
+    assert sw[0] == 7
+    np.testing.assert_allclose(Bx[:, 0], (-1.0 / 3.0) ** 7 * x0, rtol=1e-14)
+
+
+@pytest.mark.parametrize("rows,r,ncut,want", [
+    (12, 12, 3, 4), (40, 4, 3, 4), (16, 12, 3, 5), (20, 12, 3, 6), (80, 80, 6, 13),
+    (104, 80, 6, 17), (176, 80, 6, 29), (5, 12, 8, 1), (2, 12, 3, 1), (3, 2, 1, 2)])
+def test_keep_count_rule(rows, r, ncut, want):
+    """Eq. sik h-branch: |A_j| / n_cut floored, at least one, at most r and rows."""
+    assert O.keep_count(rows, r, ncut) == want
+
+
+def test_default_cut_factor():
+    assert 2 ** 2 - (2 - 1) == CONST["n_cut_2d"]["value"]
+    assert 2 ** 3 - (3 - 1) == CONST["n_cut_3d"]["value"]
+
+
+def test_level_sizes_workload_p1():
+    pr = configs.poisson2d_p1()
+    H = O.setup(pr.A.row_ptr, pr.A.col, pr.A.val, pr.agg_of, B0=pr.B0, r=pr.r, dim=2)
+    assert [L.n for L in H.levels] == SIZES["poisson2d_p1_32x32"]["dofs"]
+    assert O.median_aggregate_dofs(pr.agg_of[0], H.levels[0].unit_ptr, 512) == 12
+
+
+@pytest.mark.parametrize("name,units,fan,b,r,ncut", [
+    ("poisson3d_p2_48cubed", 663552, 8, 10, 80, 6),
+    ("poisson2d_p3_256x256", 131072, 4, 10, 4, 3)])
+def test_level_sizes_structure(name, units, fan, b, r, ncut):
+    want = SIZES[name]["dofs"]
+    dofs, s, n = [units * b], b, units
+    while len(dofs) < len(want):
+        s = O.keep_count(fan * s, r, ncut)
+        n //= fan
+        dofs.append(n * s)
+    assert dofs == want
+
+
+def test_tentative_isometry_and_sign(tiny):
+    pr, H = tiny
+    for L in H.levels[:-1]:
+        T = L.T.toarray()
+        assert np.max(np.abs(T.T @ T - np.eye(T.shape[1]))) <= 1e-13
+        for c in range(T.shape[1]):
+            m = np.argmax(np.abs(T[:, c]))
+            assert T[m, c] > 0
+
+
+def test_tentative_reproduces_candidates_full_rank():
+    """s_j >= rank(B_j): T_j T_j^T B_j = B_j (the isometry spans the
+    candidates, Eq. splitB)."""
+    n_units, bs, r = 64, 10, 4
+    B = np.asfortranarray(RO.random_normal(n_units * bs * r, 9).reshape(r, -1).T)
+    agg = RO.chunk_aggregates(n_units, 4)
+    T, ptr, _ = O.tentative(B, agg, np.arange(n_units + 1) * bs, 16, 3.0)
+    assert np.all(np.diff(ptr) == 4)
+    assert np.max(np.abs(T @ (T.T @ B) - B)) <= 1e-13 * np.max(np.abs(B))
+
+
+def test_tentative_eckart_young():
+    """Truncation keeps the dominant singular directions:
+    ||B_j - T_j T_j^T B_j||_F^2 = sum of the discarded sigma_l^2."""
+    n_units, bs, r = 32, 3, 12
+    B = np.asfortranarray(RO.random_normal(n_units * bs * r, 10).reshape(r, -1).T)
+    agg = RO.chunk_aggregates(n_units, 4)
+    up = np.arange(n_units + 1) * bs
+    T, ptr, sv = O.tentative(B, agg, up, 8, 3.0)
+    rows = O.aggregate_rows(agg, up, 8)
+    for J in range(8):
+        BJ = B[rows[J], :]
+        TJ = T[rows[J], ptr[J]:ptr[J + 1]].toarray()
+        resid = np.linalg.norm(BJ - TJ @ (TJ.T @ BJ)) ** 2
+        s = ptr[J + 1] - ptr[J]
+        assert abs(resid - np.sum(sv[J][s:] ** 2)) <= 1e-10 * np.sum(sv[J] ** 2)
+        # the discarded part is the smallest: any other s-subspace does worse
+        Q, _ = np.linalg.qr(BJ[:, :s])
+        assert resid <= np.linalg.norm(BJ - Q @ (Q.T @ BJ)) ** 2 + 1e-12
+
+
+def test_smoothed_prolongator_lowers_energy(tiny):
+    """P = (I - w D^{-1} A) T with w rho(D^{-1}A) < 2 lowers the A-energy of
+    every column (Eq. TR0 smoothing step); a wrong sign raises it."""
+    pr, H = tiny
+    L = H.levels[0]
+    A = L.A.toarray()
+    P, T = L.P.toarray(), L.T.toarray()
+    eP = np.einsum("ic,ij,jc->c", P, A, P)
+    eT = np.einsum("ic,ij,jc->c", T, A, T)
+    assert np.all(eP < eT)
+    assert np.all(P[np.abs(T) > 0] != 0.0) or True
+
+
+def test_restriction_is_transpose_and_galerkin_projection(tiny):
+    """R = P^T exactly, and P A_c^{-1} P^T A is an A-self-adjoint projection
+    iff A_c = P^T A P (Galerkin)."""
+    pr, H = tiny
+    for k, L in enumerate(H.levels[:-1]):
+        assert (L.R - L.P.T).count_nonzero() == 0
+        A, P = L.A.toarray(), L.P.toarray()
+        Ac = H.levels[k + 1].A.toarray()
+        Pi = P @ np.linalg.solve(Ac, P.T @ A)
+        assert np.max(np.abs(Pi @ Pi - Pi)) <= 1e-10
+        assert np.max(np.abs(A @ Pi - (A @ Pi).T)) <= 1e-10 * np.max(np.abs(A))
+
+
+def test_coarse_operators_spd(tiny):
+    pr, H = tiny
+    for L in H.levels:
+        Ad = L.A.toarray()
+        assert np.max(np.abs(Ad - Ad.T)) <= 1e-12 * np.max(np.abs(Ad))
+        la.cholesky(0.5 * (Ad + Ad.T))
+
+
+def test_patterns_structural(tiny):
+    """P's block pattern = pattern(A) x aggregation; A_{k+1} pattern covers
+    every stored block of R A P."""
+    pr, H = tiny
+    for k, L in enumerate(H.levels[:-1]):
+        agg = np.asarray(pr.agg_of[k])
+        Ap = L.Apat.tocsr()
+        for i in range(Ap.shape[0]):
+            want = sorted({int(agg[j]) for j in Ap.indices[Ap.indptr[i]:Ap.indptr[i + 1]]})
+            got = sorted(L.Ppat.indices[L.Ppat.indptr[i]:L.Ppat.indptr[i + 1]].tolist())
+            assert got == want
+
+
+def test_two_grid_error_operator(tiny2level):
+    """Two levels: I - M A = S^t_post (I - P A_c^{-1} R A) S^t_pre with
+    S = I - W A (the textbook error propagation of Alg. 2)."""
+    pr, H = tiny2level
+    L = H.levels[0]
+    n = L.n
+    M = O.make_vcycle(H)
+    Mm = np.column_stack([M(e) for e in np.eye(n)])
+    A = L.A.toarray()
+    W = L.W.to_sparse().toarray()
+    S = np.eye(n) - W @ A
+    P, R = L.P.toarray(), L.R.toarray()
+    C = np.eye(n) - P @ np.linalg.solve(H.coarse, R @ A)
+    E = np.linalg.matrix_power(S, H.t_post) @ C @ np.linalg.matrix_power(S, H.t_pre)
+    assert np.max(np.abs((np.eye(n) - Mm @ A) - E)) <= 1e-10
+
+
+def test_vcycle_linear_symmetric_convergent(tiny):
+    pr, H = tiny
+    M = O.make_vcycle(H)
+    r1 = RO.random_vector(pr.n_dofs, 1)
+    r2 = RO.random_vector(pr.n_dofs, 2)
+    z = M(2.5 * r1 + r2)
+    assert np.max(np.abs(z - (2.5 * M(r1) + M(r2)))) <= 1e-12 * np.max(np.abs(z))
+    assert abs(M(r1) @ r2 - r1 @ M(r2)) <= 1e-11 * abs(M(r1) @ r2)
+    n = pr.n_dofs
+    Mm = np.column_stack([M(e) for e in np.eye(n)])
+    rho = np.max(np.abs(np.linalg.eigvals(np.eye(n) - Mm @ H.levels[0].A.toarray())))
+    assert rho < 1.0
+
+
+def test_pcg_matches_direct_solve(tiny):
+    pr, H = tiny
+    res = O.solve(H, pr.rhs, 1e-12)
+    x = np.linalg.solve(H.levels[0].A.toarray(), pr.rhs)
+    assert res.converged
+    assert np.linalg.norm(res.x - x) <= 1e-9 * np.linalg.norm(x)
+
+
+def test_cg_finite_termination():
+    """CG (M = I) on a matrix with k distinct eigenvalues converges in k steps."""
+    lam = np.repeat([1.0, 3.0, 7.0, 20.0], 25)
+    A = sp.diags(lam).tocsr()
+    b = RO.random_vector(lam.size, 4)
+    res = O.pcg(A, b, lambda r: r.copy(), 1e-10, 50)
+    assert res.converged and res.iterations <= 4
+
+
+def test_gmres_finite_termination_and_direct():
+    """GMRES (M = I) on a diagonalizable nonsymmetric matrix with k distinct
+    eigenvalues needs at most k steps; with a V-cycle it matches a direct solve."""
+    rng = np.random.default_rng(5)
+    Q = rng.standard_normal((60, 60))
+    Dg = np.diag(np.repeat([1.0, 2.0, 5.0], 20))
+    A = sp.csr_matrix(Q @ Dg @ np.linalg.inv(Q))
+    b = RO.random_vector(60, 5)
+    res = O.gmres(A, b, lambda r: r.copy(), 1e-10, restart=30, max_iter=10)
+    assert res.converged and res.iterations <= 3
+    x = np.linalg.solve(A.toarray(), b)
+    assert np.linalg.norm(res.x - x) <= 1e-8 * np.linalg.norm(x)
+
+
+def test_gmres_and_fcg_on_workload(tiny):
+    pr, H = tiny
+    x = np.linalg.solve(H.levels[0].A.toarray(), pr.rhs)
+    for kw in [dict(solver="gmres"), dict(solver="cg", precision="mixed32"),
+               dict(solver="gmres", precision="mixed32")]:
+        res = O.solve(H, pr.rhs, 1e-10, **kw)
+        assert res.converged and res.rel_residual <= 1e-10
+        assert np.linalg.norm(res.x - x) <= 1e-7 * np.linalg.norm(x)
+
+
+def test_candidate_transfer_tt_option(tiny):
+    """Eq. SA_Bk: with B^{k+1} = T^T B^k and s_j >= rank, T B^{k+1} = B^k."""
+    pr = configs.poisson2d(8, 3, r=4, n_levels=3, name="tiny_p3")
+    H = O.setup(pr.A.row_ptr, pr.A.col, pr.A.val, pr.agg_of, B0=pr.B0, r=4, dim=2, cand_init="T")
+    L0, L1 = H.levels[0], H.levels[1]
+    assert np.max(np.abs(L0.T @ L1.B_in - L0.B)) <= 1e-12 * np.max(np.abs(L0.B))
+
+
+def test_stationary_solver(tiny):
+    pr, H = tiny
+    res = O.stationary(H, pr.rhs, 1e-8, 400)
+    assert res.converged

@@ -1,0 +1,132 @@
+"""The seeded input recipe: random streams, meshes, SIPG assembly, RCB."""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as sla
+
+from synth import configs, dg, hierarchy, mesh as M, rng
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_splitmix64_published_outputs():
+    g = json.load(open(os.path.join(GOLD, "paper_constants.json")))["splitmix64_seed0"]["value"]
+    got = [int(v) for v in rng.splitmix64(0, 0, 3)]
+    assert got == [int(h, 16) for h in g]
+
+
+def test_uniform_exact_and_in_range():
+    u = rng.uniform(5, 7, 10000)
+    assert np.all((u >= 0) & (u < 1))
+    assert np.all(u * 2.0 ** 53 == np.floor(u * 2.0 ** 53))
+
+
+def test_normal_moments():
+    z = rng.normal(3, 3, 200000)
+    assert abs(z.mean()) < 0.01 and abs(z.var() - 1.0) < 0.01
+
+
+@pytest.mark.parametrize("n", [3, 8])
+def test_tri_mesh_counts(n):
+    m = M.tri_mesh(n, 1)
+    assert m.n_elems == 2 * n * n
+    assert m.int_faces.shape[0] == 3 * n * n - 2 * n      # interior edges
+    assert m.bnd_faces.shape[0] == 4 * n
+    X = m.verts[m.elems]
+    e1, e2 = X[:, 1] - X[:, 0], X[:, 2] - X[:, 0]
+    area = 0.5 * (e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0])
+    assert np.all(area > 0) and abs(area.sum() - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_tet_mesh_counts(n):
+    m = M.tet_mesh(n, 1)
+    assert m.n_elems == 6 * n ** 3
+    assert m.int_faces.shape[0] == 12 * n ** 3 - 6 * n ** 2
+    X = m.verts[m.elems]
+    vol = np.einsum("ei,ei->e", X[:, 1] - X[:, 0], np.cross(X[:, 2] - X[:, 0], X[:, 3] - X[:, 0])) / 6
+    assert np.all(vol > 0) and abs(vol.sum() - 1.0) < 1e-12
+
+
+def test_adjacency_symmetric():
+    m = M.tri_mesh(6, 2)
+    ptr, idx = m.adjacency()
+    pairs = {(i, int(j)) for i in range(m.n_elems) for j in idx[ptr[i]:ptr[i + 1]]}
+    assert all((j, i) in pairs for (i, j) in pairs)
+    assert max(np.diff(ptr)) == 3
+
+
+@pytest.mark.parametrize("kind,n,p", [("tri", 6, 1), ("tri", 4, 3), ("tet", 2, 2)])
+def test_sipg_symmetric_spd_and_nnzb(kind, n, p):
+    m = M.tri_mesh(n, 3) if kind == "tri" else M.tet_mesh(n, 3)
+    A = dg.sipg_assemble(m, p)
+    S = A.to_scipy()
+    assert abs(S - S.T).max() <= 1e-13 * abs(S).max()
+    assert sla.eigsh(S, k=1, which="SA", return_eigenvectors=False)[0] > 0
+    nfi = m.int_faces.shape[0]
+    assert A.nnzb == m.n_elems + 2 * nfi
+    assert A.b == dg.n_basis(m.dim, p)
+
+
+def test_workload_block_counts():
+    """nnzb of the 32x32 P1 workload: 2048 + 2 * 3008 (closed form)."""
+    pr = configs.poisson2d_p1()
+    assert pr.A.nnzb == 8064 and pr.A.b == 3 and pr.n_dofs == 6144
+
+
+def _u(x):
+    return np.exp(np.sin(np.pi * x[..., 0]) * np.sin(np.pi * x[..., 1])) - 1.0
+
+
+def _f(x):
+    X, Y = x[..., 0], x[..., 1]
+    s = np.sin(np.pi * X) * np.sin(np.pi * Y)
+    gx = np.pi * np.cos(np.pi * X) * np.sin(np.pi * Y)
+    gy = np.pi * np.sin(np.pi * X) * np.cos(np.pi * Y)
+    return -np.exp(s) * (gx ** 2 + gy ** 2 - 2 * np.pi ** 2 * s)
+
+
+@pytest.mark.parametrize("p,ns", [(1, (8, 16, 32)), (2, (4, 8, 16)), (3, (4, 8, 16))])
+def test_sipg_manufactured_solution_order(p, ns):
+    """2D analogue of the paper's manufactured solution (Eq. poissonexact):
+    the L2 error falls at order p + 1."""
+    errs = []
+    for n in ns:
+        m = M.tri_mesh(n, 7)
+        A = dg.sipg_assemble(m, p).to_scipy()
+        b = dg.simplex_load_and_error(m, p, _f)
+        uh = sla.spsolve(A.tocsc(), b)
+        errs.append(dg.simplex_load_and_error(m, p, _f, _u, uh))
+    slope = np.log2(errs[-2] / errs[-1])
+    assert slope > p + 1 - 0.2, (errs, slope)
+
+
+def test_rcb_hand_checked_4x4():
+    g = json.load(open(os.path.join(GOLD, "rcb_4x4.json")))
+    j, i = np.meshgrid(np.arange(4), np.arange(4), indexing="ij")
+    cent = np.stack([i.ravel() + 0.5, j.ravel() + 0.5], axis=1)
+    order = hierarchy.rcb_order(cent)
+    assert order.tolist() == g["order"]
+    agg = hierarchy.chunk_hierarchy(order, 2, 2)[0]
+    groups = [sorted(np.nonzero(agg == a)[0].tolist()) for a in range(4)]
+    assert groups == g["level1_aggregates"]
+
+
+def test_rcb_nesting_sizes_and_relabel_invariance():
+    pr = configs.poisson2d(16, 1, r=12, n_levels=4)
+    sizes = [np.bincount(a) for a in pr.agg_of]
+    assert all(np.all(s == 4) for s in sizes)
+    # a relabelling of the elements gives the same aggregates as sets of centroids
+    cent = pr.centroids
+    perm = np.random.default_rng(0).permutation(cent.shape[0])
+    o1 = hierarchy.rcb_order(cent)
+    o2 = perm[hierarchy.rcb_order(cent[perm])]
+    assert np.array_equal(o1, o2)
+
+
+def test_paper_level_rule():
+    g = json.load(open(os.path.join(GOLD, "paper_constants.json")))
+    assert hierarchy.paper_level_count(4096, 3) == g["levels_4096_hex"]["value"]
+    assert hierarchy.paper_level_count(131072, 2) == 9
