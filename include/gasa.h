@@ -1,0 +1,261 @@
+/*
+ * gasa.h -- C ABI of the GB300 geometric adaptive smoothed aggregation
+ * (alpha-SA) multigrid library for DG discretisations.
+ *
+ * Method: Pan, Lindsey & Persson, "Geometric adaptive smoothed aggregation
+ * multigrid for discontinuous Galerkin discretisations" (2025).  The
+ * paper's problem statement (Section 4.5) takes the system operator A and
+ * the element graph G; the nested element aggregates (Section 4.1) are
+ * passed in as well.  gasa_setup follows Alg. 5, gasa_solve applies the
+ * V-cycle of Alg. 2 as a preconditioner of CG or GMRES (Section 6).
+ *
+ * Naming: the paper calls the tentative (orthonormal, block-diagonal)
+ * prolongator P_{k+1}^k and the smoothed one T_{k+1}^k.  This library calls
+ * the tentative one T and the smoothed one P = (I - w D^-1 A) T, R = P^T.
+ *
+ * Conventions for every entry point:
+ *  - every function returns a gasa_status (0 = GASA_OK); nothing aborts,
+ *    prints or throws; inputs are validated before any device work;
+ *  - "device pointer" means memory of the CUDA device the call runs on;
+ *    the caller keeps ownership of everything it passes in;
+ *  - BSR matrices store one dense block per stored (block row, block
+ *    column) pair, blocks row-major and contiguous, block columns sorted
+ *    ascending within each block row;
+ *  - indices are int32, values FP64 unless a name ends in _f32;
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).
+ */
+#ifndef GASA_H
+#define GASA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GASA_OK = 0,
+  GASA_ERR_INVALID_ARG = 1,     /* malformed input, detected before device work */
+  GASA_ERR_OOM = 2,             /* device allocation failed */
+  GASA_ERR_CUDA = 3,            /* a CUDA call failed; text in gasa_last_error */
+  GASA_ERR_SINGULAR_BLOCK = 4,  /* a diagonal block or the coarse matrix is singular */
+  GASA_ERR_NOT_SPD = 5,         /* CG met p^T A p <= 0 */
+  GASA_ERR_NOT_CONVERGED = 6,   /* max_iter reached; x and info hold the last iterate */
+  GASA_ERR_BREAKDOWN = 7,       /* Krylov breakdown or rank-deficient candidate block */
+  GASA_ERR_TIMEOUT = 8,
+  GASA_ERR_BUDGET = 9,
+  GASA_PENDING = 10,
+  GASA_ERR_UNSUPPORTED = 11,    /* valid input this build does not handle */
+  GASA_ERR_STATE = 12           /* call out of order (e.g. solve before setup) */
+} gasa_status;
+
+enum { GASA_SOLVER_CG = 0, GASA_SOLVER_GMRES = 1 };
+enum { GASA_PREC_FP64 = 0, GASA_PREC_MIXED32 = 1 };
+enum { GASA_CAND_R = 0, GASA_CAND_TT = 1 };
+enum { GASA_MV_ASSIGN = 0, GASA_MV_RESIDUAL = 1, GASA_MV_ADD = 2 };
+
+#define GASA_MAX_LEVELS 24
+
+/* Level-0 operator A: n_blocks x n_blocks blocks of block x block entries
+ * (one block per element pair, Section 2 / Eq. Auf).  The diagonal block of
+ * every block row must be stored. */
+typedef struct {
+  int32_t n_blocks;          /* number of elements n_e */
+  int32_t block;             /* dofs per element n_p */
+  int32_t nnzb;              /* stored blocks */
+  const int32_t *row_ptr;    /* n_blocks + 1 */
+  const int32_t *col;        /* nnzb */
+  const double *val;         /* nnzb * block * block */
+  int32_t on_device;         /* 1: the three arrays are device pointers */
+} gasa_bsr;
+
+/* Nested aggregates (Section 4.1): levels L0..LN, N = n_levels - 1.
+ * agg_of[k-1][i] (host memory) is the level-k aggregate containing level-(k-1)
+ * unit i, for k = 1..N; level-0 units are elements.  Aggregate ids of each
+ * level are 0..n-1 and every aggregate is non-empty. */
+typedef struct {
+  int32_t n_levels;
+  const int32_t *const *agg_of;
+} gasa_hierarchy;
+
+typedef struct {
+  int32_t dim;               /* spatial dimension d (sets n_cut default) */
+  int32_t solver;            /* GASA_SOLVER_CG (SPD) or GASA_SOLVER_GMRES */
+  int32_t restart;           /* GMRES restart length (default 30) */
+  int32_t precision;         /* GASA_PREC_FP64 or GASA_PREC_MIXED32 */
+  int32_t t_pre, t_post;     /* smoothing steps (Section 6: 3 and 3) */
+  int32_t q_power;           /* Alg. 4 iterations (Section 4.4: q = 3) */
+  int32_t n_cand;            /* r; 0 = median level-1 aggregate dofs (Section 4.2) */
+  int32_t max_relax;         /* cap on Eq. bsmooth sweeps per candidate (default 100) */
+  int32_t max_iter;          /* outer Krylov iterations (default 10000) */
+  int32_t cand_init;         /* GASA_CAND_R: B^{k+1} = R B^k (Alg. 5); GASA_CAND_TT: T^T B^k (Eq. SA_Bk) */
+  int32_t keep_setup_data;   /* 1: keep T and the candidates B^k for gasa_get_level */
+  double gamma;              /* Eq. bsmooth tolerance (default 0.03) */
+  double omega_factor;       /* Eq. omega numerator (default 4/3) */
+  double n_cut;              /* Eq. sik cut factor; 0 = 2^d - (d - 1) */
+  uint64_t seed;             /* splitmix64 seed of the power-iteration vectors */
+  const double *init_candidates; /* optional host B^0, n x r column-major; NULL = N(0,1) drawn on device */
+} gasa_options;
+
+typedef struct {
+  int32_t n_levels;          /* N + 1 */
+  int32_t n_cand;            /* r actually used */
+  int64_t units[GASA_MAX_LEVELS];   /* elements or aggregates per level */
+  int32_t block[GASA_MAX_LEVELS];   /* dofs per unit s_k (uniform per level) */
+  int64_t dofs[GASA_MAX_LEVELS];
+  int64_t nnzb[GASA_MAX_LEVELS];    /* stored blocks of A_k */
+  int64_t nnz[GASA_MAX_LEVELS];     /* stored scalars of A_k */
+  double omega[GASA_MAX_LEVELS];    /* w_k (0 on the coarsest level) */
+  double rho[GASA_MAX_LEVELS];      /* Alg. 4 estimate */
+  int32_t relax_sweeps_max[GASA_MAX_LEVELS];
+  double seconds;
+  int64_t device_bytes;      /* resident hierarchy size */
+} gasa_setup_info;
+
+typedef struct {
+  int32_t iterations;        /* Krylov iterations (one V-cycle each) */
+  int32_t converged;
+  double rel_residual;       /* true ||b - A x|| / ||b|| at exit */
+  double seconds;
+} gasa_solve_info;
+
+typedef struct gasa_ctx gasa_ctx;
+
+/* ------------------------------------------------------------------ */
+/* context API                                                          */
+/* ------------------------------------------------------------------ */
+
+/* Fill `opt` with the paper's defaults (Sections 4.2-4.4, 6). */
+void gasa_default_options(gasa_options *opt);
+
+/* Create a context on CUDA device `device`; `stream` (nullable) is used for
+ * every launch of the context, else the context creates its own. */
+gasa_status gasa_create(gasa_ctx **ctx, int32_t device, void *stream);
+
+/* Alg. 5: build the hierarchy on the device.  A is copied; adj (element face
+ * graph, CSR) and centroids (n_e x dim) are validated and kept for the
+ * record; `hier` gives the aggregates (NULL is GASA_ERR_UNSUPPORTED in this
+ * build).  Equal keep counts s_k per level are required
+ * (GASA_ERR_UNSUPPORTED otherwise).  `info` is nullable. */
+gasa_status gasa_setup(gasa_ctx *ctx, const gasa_bsr *A,
+                       const int32_t *adj_ptr, const int32_t *adj_idx,
+                       const double *centroids, const gasa_hierarchy *hier,
+                       const gasa_options *opt, gasa_setup_info *info);
+
+/* Solve A x = b to ||b - A x|| <= tol ||b|| from x = 0 with the V-cycle
+ * (Alg. 2) preconditioning CG (opt.solver = CG) or left-preconditioned
+ * GMRES(restart) (Section 6); precision MIXED32 runs the V-cycle in FP32
+ * inside flexible CG / FGMRES.  b and x are n_e*n_p doubles, host memory if
+ * on_device == 0, else device pointers.  x is written on GASA_OK and on
+ * GASA_ERR_NOT_CONVERGED.  `info` is nullable. */
+gasa_status gasa_solve(gasa_ctx *ctx, const double *b, double *x, double tol,
+                       int32_t precision, int32_t on_device, gasa_solve_info *info);
+
+/* One V-cycle z = M r (Alg. 2 from a zero initial guess), device pointers,
+ * FP64 or MIXED32 (FP32 inside, FP64 in and out). */
+gasa_status gasa_vcycle(gasa_ctx *ctx, const double *r, double *z, int32_t precision);
+
+/* Level data, copied to host memory for inspection. */
+enum {
+  GASA_LV_A_ROWPTR = 0, GASA_LV_A_COL = 1, GASA_LV_A_VAL = 2,
+  GASA_LV_P_ROWPTR = 3, GASA_LV_P_COL = 4, GASA_LV_P_VAL = 5,
+  GASA_LV_R_ROWPTR = 6, GASA_LV_R_COL = 7, GASA_LV_R_VAL = 8,
+  GASA_LV_T_VAL = 9,         /* units x s_k x s_{k+1}, unit i's block of T */
+  GASA_LV_W = 10,            /* units x s_k x s_k: w_k D_k^{-1} */
+  GASA_LV_CAND = 11,         /* relaxed B^k, dofs x r column-major */
+  GASA_LV_SWEEPS = 12,       /* int32 r: Eq. bsmooth sweeps per column */
+  GASA_LV_COARSE_INV = 13,   /* coarsest level: dense A_N^{-1}, row-major */
+  GASA_LV_CAND_IN = 14       /* B^k before relaxation */
+};
+/* shape[0..7] = units, s_k, nnzb(A), P nnzb, R nnzb, s_{k+1}, r, dofs */
+gasa_status gasa_level_shape(gasa_ctx *ctx, int32_t level, int64_t shape[8]);
+gasa_status gasa_get_level(gasa_ctx *ctx, int32_t level, int32_t what,
+                           void *host_out, int64_t n_bytes);
+
+/* Per-kernel timing over CUDA events on the context stream (for the
+ * benchmark's roofline): class 0 = level-0 smoothing sweeps, 1 = level-0
+ * residual SpMV, 2 = outer A*p SpMV.  Enable, run, then read total
+ * milliseconds, launches and algorithmic bytes moved. */
+gasa_status gasa_profile_enable(gasa_ctx *ctx, int32_t on);
+gasa_status gasa_profile_read(gasa_ctx *ctx, int32_t kernel_class, double *ms,
+                              int64_t *launches, double *bytes);
+
+gasa_status gasa_destroy(gasa_ctx *ctx);
+const char *gasa_status_string(gasa_status s);
+const char *gasa_last_error(const gasa_ctx *ctx);
+
+/* ------------------------------------------------------------------ */
+/* single operations on caller-owned device memory                      */
+/* ------------------------------------------------------------------ */
+
+/* Block-sparse matrix-vector product (Alg. 1 / Alg. 2 residuals, and the
+ * transfers u += P u_c, b_c = R r of Alg. 2): A has n_brows block rows of
+ * br x bc blocks.  mode ASSIGN: y = A x; RESIDUAL: y = b - A x;
+ * ADD: y += A x.  x holds (max col + 1) * bc entries, y and b n_brows * br. */
+gasa_status gasa_bsr_mv(int32_t mode, int32_t n_brows, int32_t br, int32_t bc,
+                        const int32_t *row_ptr, const int32_t *col, const double *val,
+                        const double *x, const double *b, double *y, void *stream);
+gasa_status gasa_bsr_mv_f32(int32_t mode, int32_t n_brows, int32_t br, int32_t bc,
+                            const int32_t *row_ptr, const int32_t *col, const float *val,
+                            const float *x, const float *b, float *y, void *stream);
+
+/* One block-Jacobi step of Alg. 1 with A~^{-1} = W = w D^{-1}
+ * (Eq. smoother_choice): x_out = x + W (b - A x); first != 0 gives the
+ * step from x = 0, x_out = W b (x unused).  W holds n_units blocks of
+ * bs x bs.  x_out must not alias x. */
+gasa_status gasa_jacobi_sweep(int32_t n_units, int32_t bs, const int32_t *row_ptr,
+                              const int32_t *col, const double *val, const double *W,
+                              const double *x, const double *b, double *x_out,
+                              int32_t first, void *stream);
+gasa_status gasa_jacobi_sweep_f32(int32_t n_units, int32_t bs, const int32_t *row_ptr,
+                                  const int32_t *col, const float *val, const float *W,
+                                  const float *x, const float *b, float *x_out,
+                                  int32_t first, void *stream);
+
+/* W_out = scale * D^{-1} for the diagonal blocks D of a square BSR matrix
+ * (block Jacobi, Section 4.4); LU with partial pivoting per block.
+ * *n_singular (host) receives the number of singular blocks. */
+gasa_status gasa_block_inverse(int32_t n_units, int32_t bs, const int32_t *row_ptr,
+                               const int32_t *col, const double *val, double scale,
+                               double *W_out, int32_t *n_singular, void *stream);
+
+/* Alg. 4: rho = ||D^{-1} A x_q|| after q normalised steps from x0
+ * (device, n_units*bs; x0 need not be normalised).  Dinv from
+ * gasa_block_inverse with scale 1.  *rho is written to host memory. */
+gasa_status gasa_power_estimate(int32_t n_units, int32_t bs, const int32_t *row_ptr,
+                                const int32_t *col, const double *val, const double *Dinv,
+                                const double *x0, int32_t q, double *rho, void *stream);
+
+/* Eq. bsmooth: relax every column of B (device, n x r column-major, in
+ * place) with x <- x - W A x until ||x^(m-1)|| / ||x^(m)|| < 1 + gamma
+ * (at least one and at most max_relax sweeps).  sweeps (host, r ints)
+ * receives the sweep count per column. */
+gasa_status gasa_relax_candidates(int32_t n_units, int32_t bs, const int32_t *row_ptr,
+                                  const int32_t *col, const double *val, const double *W,
+                                  double *B, int32_t r, double gamma, int32_t max_relax,
+                                  int32_t *sweeps, void *stream);
+
+/* Eq. splitB_dg + Eq. sik: per aggregate J, the left singular vectors of the
+ * rows of B (device, n x r column-major, n = n_units * bs) owned by J's
+ * units (increasing unit id, then dof), ordered by descending singular
+ * value, the first s_next kept and signed so that each column's entry of
+ * largest magnitude (lowest row on ties) is positive.  agg_of (device,
+ * n_units) maps units to aggregates 0..n_agg-1.  T_out (device): n_units
+ * blocks of bs x s_next, unit i's rows of its aggregate's kept vectors.
+ * sigma_out (device, nullable): n_agg x r singular values, descending,
+ * zero-padded. */
+gasa_status gasa_tentative(int32_t n_units, int32_t bs, int32_t n_agg, const int32_t *agg_of,
+                           const double *B, int32_t r, int32_t s_next, double *T_out,
+                           double *sigma_out, void *stream);
+
+/* Dense inverse (Gauss-Jordan, partial pivoting) of the n x n row-major
+ * device matrix A into Ainv (device); the coarsest solve u_N = A_N^{-1} b_N
+ * of Alg. 2.  *singular (host) is set to 1 if a pivot vanishes. */
+gasa_status gasa_dense_inverse(int32_t n, const double *A, double *Ainv, int32_t *singular,
+                               void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GASA_H */

@@ -1,0 +1,1492 @@
+// C ABI of the library: context, Alg. 5 setup driver, Alg. 2 V-cycle,
+// CG / GMRES outer loops, and single-operation entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "gasa.h"
+#include "internal.h"
+
+using namespace gasa;
+
+namespace {
+
+struct DevBSR {
+  int nrows = 0, ncols = 0, br = 0, bc = 0;
+  int64_t nnzb = 0;
+  int *rp = nullptr, *col = nullptr;
+  double *val = nullptr;
+  float *val32 = nullptr;
+};
+
+struct Level {
+  int n = 0;          // units on this level
+  int s = 0;          // dofs per unit
+  int64_t ndof = 0;
+  DevBSR A;
+  double *W = nullptr;        // w D^{-1}
+  float *W32 = nullptr;
+  // transfer to the next level
+  int *agg = nullptr;
+  int n_next = 0, s_next = 0, max_children = 0;
+  int *child_ptr = nullptr, *child_idx = nullptr;
+  double *T = nullptr;
+  DevBSR P, R;
+  double *cand = nullptr, *cand_in = nullptr;
+  std::vector<int> sweeps;
+  double omega = 0.0, rho = 0.0;
+  // V-cycle vectors
+  double *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr;
+  float *xf = nullptr, *x2f = nullptr, *bf = nullptr, *rf = nullptr;
+};
+
+struct ProfClass {
+  std::vector<cudaEvent_t> ev;    // pairs
+  size_t used = 0;
+  double bytes = 0.0;
+  int64_t launches = 0;
+};
+
+}  // namespace
+
+struct gasa_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  bool ready = false;
+  gasa_options opt{};
+  int N = 0;
+  int r = 0;
+  std::vector<Level> L;
+  double *coarse_inv = nullptr;
+  int nc = 0;
+  std::vector<void *> allocs;     // hierarchy allocations
+  // Krylov workspace
+  double *kx = nullptr, *kr = nullptr, *kz = nullptr, *kp = nullptr, *kq = nullptr,
+         *kzold = nullptr, *kb = nullptr, *kt = nullptr;
+  double *part = nullptr;         // 4 x kRedBlocks partials
+  double *scal = nullptr;         // device scalars
+  double *hscal = nullptr;        // pinned host mirror
+  float *kf_in = nullptr, *kf_out = nullptr;
+  double *V = nullptr, *Z = nullptr, *H = nullptr, *gm = nullptr, *mpart = nullptr;
+  int gm_restart = 0;
+  bool gm_flex = false;
+  // profiling
+  bool prof = false;
+  ProfClass pc[3];
+  double setup_seconds = 0.0;
+  int64_t device_bytes = 0;
+};
+
+namespace {
+
+const char *kStatusText[] = {"ok",
+                             "invalid argument",
+                             "device allocation failed",
+                             "CUDA error",
+                             "singular diagonal block or coarse matrix",
+                             "matrix not SPD (CG breakdown)",
+                             "not converged",
+                             "breakdown",
+                             "timeout",
+                             "over budget",
+                             "pending",
+                             "unsupported input",
+                             "call out of order"};
+
+gasa_status fail(gasa_ctx *c, gasa_status s, const std::string &msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define CU(...)                                                                        \
+  do {                                                                                 \
+    cudaError_t e_ = (__VA_ARGS__);                                                    \
+    if (e_ != cudaSuccess) {                                                           \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? GASA_ERR_OOM : GASA_ERR_CUDA, \
+                  std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));          \
+    }                                                                                  \
+  } while (0)
+
+#define ST(...)                         \
+  do {                                  \
+    gasa_status s_ = (__VA_ARGS__);     \
+    if (s_ != GASA_OK) return s_;       \
+  } while (0)
+
+template <typename T>
+gasa_status dalloc(gasa_ctx *ctx, T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(ctx, GASA_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  ctx->allocs.push_back((void *)*p);
+  ctx->device_bytes += (int64_t)(count * sizeof(T));
+  return GASA_OK;
+}
+
+void dfree(gasa_ctx *ctx, void *p) {
+  if (!p) return;
+  auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), p);
+  if (it != ctx->allocs.end()) ctx->allocs.erase(it);
+  cudaFree(p);
+}
+
+void free_all(gasa_ctx *ctx) {
+  cudaStreamSynchronize(ctx->stream);
+  for (void *p : ctx->allocs) cudaFree(p);
+  ctx->allocs.clear();
+  if (ctx->hscal) {
+    cudaFreeHost(ctx->hscal);
+    ctx->hscal = nullptr;
+  }
+  ctx->L.clear();
+  ctx->ready = false;
+  ctx->device_bytes = 0;
+  ctx->coarse_inv = nullptr;
+  ctx->V = ctx->Z = ctx->H = ctx->gm = ctx->mpart = nullptr;
+  ctx->gm_restart = 0;
+}
+
+// ----------------------------------------------------------------------------
+// profiling helpers (CUDA events on the context stream)
+// ----------------------------------------------------------------------------
+void prof_begin(gasa_ctx *ctx, int cls, cudaEvent_t *e0) {
+  *e0 = nullptr;
+  if (!ctx->prof) return;
+  ProfClass &p = ctx->pc[cls];
+  if (p.used + 2 > p.ev.size()) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t ev;
+      cudaEventCreate(&ev);
+      p.ev.push_back(ev);
+    }
+  }
+  *e0 = p.ev[p.used];
+  cudaEventRecord(*e0, ctx->stream);
+}
+void prof_end(gasa_ctx *ctx, int cls, double bytes) {
+  if (!ctx->prof) return;
+  ProfClass &p = ctx->pc[cls];
+  cudaEventRecord(p.ev[p.used + 1], ctx->stream);
+  p.used += 2;
+  p.bytes += bytes;
+  p.launches += 1;
+}
+
+// ----------------------------------------------------------------------------
+// V-cycle (Alg. 2), one pass from a zero initial guess; T = double or float
+// ----------------------------------------------------------------------------
+template <typename T> struct Prec;
+template <> struct Prec<double> {
+  static const double *A(const DevBSR &m) { return m.val; }
+  static const double *W(const Level &l) { return l.W; }
+  static double *x(Level &l) { return l.x; }
+  static double *x2(Level &l) { return l.x2; }
+  static double *b(Level &l) { return l.b; }
+  static double *r(Level &l) { return l.r; }
+};
+template <> struct Prec<float> {
+  static const float *A(const DevBSR &m) { return m.val32; }
+  static const float *W(const Level &l) { return l.W32; }
+  static float *x(Level &l) { return l.xf; }
+  static float *x2(Level &l) { return l.x2f; }
+  static float *b(Level &l) { return l.bf; }
+  static float *r(Level &l) { return l.rf; }
+};
+
+double sweep_bytes(const Level &l, int w, bool first) {
+  const double vec = (double)l.ndof * w;
+  const double Wb = (double)l.n * l.s * l.s * w;
+  if (first) return Wb + 2.0 * vec;
+  const double Ab = (double)l.A.nnzb * l.s * l.s * w + 4.0 * l.A.nnzb + 4.0 * (l.n + 1);
+  return Ab + Wb + 3.0 * vec;
+}
+double spmv_bytes(const Level &l, int w, bool residual) {
+  const double vec = (double)l.ndof * w;
+  const double Ab = (double)l.A.nnzb * l.s * l.s * w + 4.0 * l.A.nnzb + 4.0 * (l.n + 1);
+  return Ab + (residual ? 3.0 : 2.0) * vec;
+}
+
+template <typename T>
+gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out) {
+  using P = Prec<T>;
+  cudaStream_t s = ctx->stream;
+  const int N = ctx->N;
+  const int tpre = ctx->opt.t_pre, tpost = ctx->opt.t_post;
+  const int w = (int)sizeof(T);
+  std::vector<const T *> bk(N + 1);
+  std::vector<T *> xk(N + 1);
+  bk[0] = rhs;
+  for (int k = 1; k <= N; ++k) bk[k] = P::b(ctx->L[k]);
+  for (int k = 0; k < N; ++k) {
+    Level &l = ctx->L[k];
+    T *x = P::x(l), *x2 = P::x2(l);
+    // pre-smoothing from zero
+    if (tpre == 0) {
+      CU(cudaMemsetAsync(x, 0, l.ndof * sizeof(T), s));
+    } else {
+      cudaEvent_t e0;
+      if (k == 0) prof_begin(ctx, 0, &e0);
+      CU(launch_jacobi<T>(JAC_FIRST, l.n, l.s, l.A.rp, l.A.col, P::A(l.A), P::W(l), nullptr,
+                          bk[k], x, s));
+      if (k == 0) prof_end(ctx, 0, sweep_bytes(l, w, true));
+      for (int t = 1; t < tpre; ++t) {
+        if (k == 0) prof_begin(ctx, 0, &e0);
+        CU(launch_jacobi<T>(JAC_SWEEP, l.n, l.s, l.A.rp, l.A.col, P::A(l.A), P::W(l), x, bk[k],
+                            x2, s));
+        if (k == 0) prof_end(ctx, 0, sweep_bytes(l, w, false));
+        std::swap(x, x2);
+      }
+    }
+    xk[k] = x;
+    // residual and restriction
+    {
+      cudaEvent_t e0;
+      if (k == 0) prof_begin(ctx, 1, &e0);
+      CU(launch_bsr_mv<T>(GASA_MV_RESIDUAL, l.n, l.s, l.s, l.A.rp, l.A.col, P::A(l.A), x, bk[k],
+                          P::r(l), s));
+      if (k == 0) prof_end(ctx, 1, spmv_bytes(l, w, true));
+    }
+    CU(launch_bsr_mv<T>(GASA_MV_ASSIGN, l.R.nrows, l.R.br, l.R.bc, l.R.rp, l.R.col, P::A(l.R),
+                        P::r(l), nullptr, P::b(ctx->L[k + 1]), s));
+  }
+  // coarsest solve in FP64
+  Level &lc = ctx->L[N];
+  CU(launch_dense_mv<T>(ctx->nc, ctx->coarse_inv, P::b(lc), P::x(lc), s));
+  xk[N] = P::x(lc);
+  for (int k = N - 1; k >= 0; --k) {
+    Level &l = ctx->L[k];
+    T *x = xk[k];
+    T *x2 = (x == P::x(l)) ? P::x2(l) : P::x(l);
+    CU(launch_bsr_mv<T>(GASA_MV_ADD, l.P.nrows, l.P.br, l.P.bc, l.P.rp, l.P.col, P::A(l.P),
+                        xk[k + 1], nullptr, x, s));
+    if (tpost == 0 && k == 0) {
+      CU(cudaMemcpyAsync(out, x, l.ndof * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    }
+    for (int t = 0; t < tpost; ++t) {
+      T *dst = (k == 0 && t == tpost - 1) ? out : x2;
+      cudaEvent_t e0;
+      if (k == 0) prof_begin(ctx, 0, &e0);
+      CU(launch_jacobi<T>(JAC_SWEEP, l.n, l.s, l.A.rp, l.A.col, P::A(l.A), P::W(l), x, bk[k], dst,
+                          s));
+      if (k == 0) prof_end(ctx, 0, sweep_bytes(l, w, false));
+      if (dst == x2) std::swap(x, x2);
+      else x = dst;
+    }
+    xk[k] = x;
+  }
+  return GASA_OK;
+}
+
+gasa_status apply_M(gasa_ctx *ctx, const double *rr, double *z, int precision) {
+  if (precision == GASA_PREC_FP64) return vcycle_impl<double>(ctx, rr, z);
+  const int64_t n = ctx->L[0].ndof;
+  CU(launch_convert<double, float>(n, rr, ctx->kf_in, ctx->stream));
+  ST(vcycle_impl<float>(ctx, ctx->kf_in, ctx->kf_out));
+  CU(launch_convert<float, double>(n, ctx->kf_out, z, ctx->stream));
+  return GASA_OK;
+}
+
+// scalar slots in ctx->scal
+enum { S_RR = 0, S_ALPHA = 1, S_PQ = 2, S_RZ0 = 3, S_RZ1 = 4, S_BB = 5, S_TMP = 6, S_G = 7,
+       S_BETA = 8, S_COUNT = 16 };
+
+gasa_status read_scalars(gasa_ctx *ctx, int first, int count) {
+  CU(cudaMemcpyAsync(ctx->hscal + first, ctx->scal + first, count * sizeof(double),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return GASA_OK;
+}
+
+gasa_status norm2(gasa_ctx *ctx, int64_t n, const double *x, int slot, double *out) {
+  CU(launch_dot_partials(n, x, nullptr, ctx->part, ctx->stream));
+  CU(launch_finalize(ctx->part, 1, ctx->scal + slot, ctx->stream));
+  ST(read_scalars(ctx, slot, 1));
+  *out = ctx->hscal[slot];
+  return GASA_OK;
+}
+
+gasa_status spmv_outer(gasa_ctx *ctx, int mode, const double *x, const double *b, double *y) {
+  Level &l = ctx->L[0];
+  cudaEvent_t e0;
+  prof_begin(ctx, 2, &e0);
+  CU(launch_bsr_mv<double>(mode, l.n, l.s, l.s, l.A.rp, l.A.col, l.A.val, x, b, y, ctx->stream));
+  prof_end(ctx, 2, spmv_bytes(l, 8, mode == GASA_MV_RESIDUAL));
+  return GASA_OK;
+}
+
+gasa_status pcg(gasa_ctx *ctx, const double *b, double tol, int precision, int *iters,
+                double *relres, bool *conv) {
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->L[0].ndof;
+  const bool flex = precision != GASA_PREC_FP64;
+  double *x = ctx->kx, *r = ctx->kr, *z = ctx->kz, *p = ctx->kp, *q = ctx->kq, *zold = ctx->kzold;
+  double *pq_part = ctx->part, *rr_part = ctx->part + kRedBlocks,
+         *rz_part = ctx->part + 2 * kRedBlocks, *rzo_part = ctx->part + 3 * kRedBlocks;
+  *conv = false;
+  *iters = 0;
+  double bb;
+  ST(norm2(ctx, n, b, S_BB, &bb));
+  const double bn = std::sqrt(bb);
+  CU(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  if (bn == 0.0) {
+    *relres = 0.0;
+    *conv = true;
+    return GASA_OK;
+  }
+  CU(launch_copy(n, b, r, s));
+  ST(apply_M(ctx, r, z, precision));
+  CU(launch_dot_partials(n, r, z, rz_part, s));
+  CU(launch_finalize(rz_part, 1, ctx->scal + S_RZ0, s));
+  CU(launch_copy(n, z, p, s));
+  int cur = S_RZ0, nxt = S_RZ1;
+  const int max_iter = ctx->opt.max_iter;
+  for (int it = 1; it <= max_iter; ++it) {
+    ST(spmv_outer(ctx, GASA_MV_ASSIGN, p, nullptr, q));
+    CU(launch_dot_partials(n, p, q, pq_part, s));
+    CU(launch_cg_update_xr(n, x, r, p, q, ctx->scal + cur, pq_part, rr_part, ctx->scal + S_ALPHA,
+                           s));
+    CU(launch_finalize(rr_part, 1, ctx->scal + S_RR, s));
+    ST(read_scalars(ctx, 0, 3));
+    const double pq = ctx->hscal[S_PQ];
+    if (!(pq > 0.0) && !flex) {
+      *iters = it;
+      *relres = std::sqrt(ctx->hscal[S_RR]) / bn;
+      return fail(ctx, GASA_ERR_NOT_SPD, "CG: p^T A p <= 0");
+    }
+    if (!std::isfinite(pq)) return fail(ctx, GASA_ERR_BREAKDOWN, "CG: non-finite p^T A p");
+    const double rel = std::sqrt(ctx->hscal[S_RR]) / bn;
+    *iters = it;
+    if (rel <= tol) {
+      ST(spmv_outer(ctx, GASA_MV_RESIDUAL, x, b, ctx->kt));
+      double tt;
+      ST(norm2(ctx, n, ctx->kt, S_TMP, &tt));
+      const double relt = std::sqrt(tt) / bn;
+      if (relt <= tol) {
+        *relres = relt;
+        *conv = true;
+        return GASA_OK;
+      }
+      CU(launch_copy(n, ctx->kt, r, s));
+    }
+    if (flex) std::swap(z, zold);
+    ST(apply_M(ctx, r, z, precision));
+    CU(launch_dot_partials(n, r, z, rz_part, s));
+    if (flex) CU(launch_dot_partials(n, r, zold, rzo_part, s));
+    CU(launch_cg_update_p(n, p, z, ctx->scal + cur, rz_part, rzo_part, ctx->scal + nxt, flex ? 1 : 0,
+                          s));
+    std::swap(cur, nxt);
+  }
+  ST(spmv_outer(ctx, GASA_MV_RESIDUAL, x, b, ctx->kt));
+  double tt;
+  ST(norm2(ctx, n, ctx->kt, S_TMP, &tt));
+  *relres = std::sqrt(tt) / bn;
+  return GASA_OK;
+}
+
+gasa_status ensure_gmres(gasa_ctx *ctx, int m, bool flex) {
+  if (ctx->V && ctx->gm_restart == m && (ctx->gm_flex || !flex)) return GASA_OK;
+  const int64_t n = ctx->L[0].ndof;
+  if (ctx->V) { dfree(ctx, ctx->V); ctx->V = nullptr; }
+  if (ctx->Z) { dfree(ctx, ctx->Z); ctx->Z = nullptr; }
+  if (ctx->H) { dfree(ctx, ctx->H); ctx->H = nullptr; }
+  if (ctx->gm) { dfree(ctx, ctx->gm); ctx->gm = nullptr; }
+  if (ctx->mpart) { dfree(ctx, ctx->mpart); ctx->mpart = nullptr; }
+  ST(dalloc(ctx, &ctx->V, (size_t)(m + 1) * n));
+  if (flex) ST(dalloc(ctx, &ctx->Z, (size_t)m * n));
+  ST(dalloc(ctx, &ctx->H, (size_t)(m + 1) * m));
+  ST(dalloc(ctx, &ctx->gm, (size_t)6 * (m + 2)));   // cs, sn, g, y, h, h2
+  ST(dalloc(ctx, &ctx->mpart, (size_t)(m + 1) * kRedBlocks));
+  ctx->gm_restart = m;
+  ctx->gm_flex = flex;
+  return GASA_OK;
+}
+
+gasa_status gmres(gasa_ctx *ctx, const double *b, double tol, int precision, int *iters,
+                  double *relres, bool *conv) {
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->L[0].ndof;
+  const bool flex = precision != GASA_PREC_FP64;
+  const int m = ctx->opt.restart > 0 ? ctx->opt.restart : 30;
+  ST(ensure_gmres(ctx, m, flex));
+  double *x = ctx->kx, *w = ctx->kz, *t = ctx->kt;
+  const int ldh = m + 1;
+  double *cs = ctx->gm, *sn = cs + (m + 2), *g = sn + (m + 2), *y = g + (m + 2), *h = y + (m + 2),
+         *h2 = h + (m + 2);
+  *conv = false;
+  *iters = 0;
+  double bb;
+  ST(norm2(ctx, n, b, S_BB, &bb));
+  const double bn = std::sqrt(bb);
+  CU(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  if (bn == 0.0) {
+    *relres = 0.0;
+    *conv = true;
+    return GASA_OK;
+  }
+  int total = 0;
+  double inner_tol = -1.0;
+  const int max_iter = ctx->opt.max_iter;
+  while (total < max_iter) {
+    ST(spmv_outer(ctx, GASA_MV_RESIDUAL, x, b, t));
+    double rr;
+    ST(norm2(ctx, n, t, S_TMP, &rr));
+    const double rel = std::sqrt(rr) / bn;
+    *relres = rel;
+    if (rel <= tol) {
+      *conv = true;
+      *iters = total;
+      return GASA_OK;
+    }
+    if (flex) CU(launch_copy(n, t, w, s));
+    else ST(apply_M(ctx, t, w, precision));
+    double beta2;
+    ST(norm2(ctx, n, w, S_TMP, &beta2));
+    const double beta = std::sqrt(beta2);
+    if (inner_tol < 0.0) inner_tol = tol * (flex ? bn : beta);
+    CU(launch_normalize_into(n, w, ctx->scal + S_TMP, ctx->V, ctx->scal + S_BETA, s));
+    CU(cudaMemsetAsync(ctx->H, 0, sizeof(double) * (m + 1) * m, s));
+    CU(cudaMemsetAsync(g, 0, sizeof(double) * (m + 2), s));
+    CU(cudaMemcpyAsync(g, ctx->scal + S_BETA, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    int jdone = 0;
+    for (int j = 0; j < m; ++j) {
+      double *vj = ctx->V + (size_t)j * n;
+      if (flex) {
+        double *zj = ctx->Z + (size_t)j * n;
+        ST(apply_M(ctx, vj, zj, precision));
+        ST(spmv_outer(ctx, GASA_MV_ASSIGN, zj, nullptr, w));
+      } else {
+        ST(spmv_outer(ctx, GASA_MV_ASSIGN, vj, nullptr, t));
+        ST(apply_M(ctx, t, w, precision));
+      }
+      ++total;
+      double *Hj = ctx->H + (size_t)j * ldh;
+      // classical Gram-Schmidt, twice
+      for (int pass = 0; pass < 2; ++pass) {
+        CU(launch_multi_dot(n, ctx->V, n, j + 1, w, ctx->mpart, s));
+        CU(launch_multi_dot_finalize(ctx->mpart, j + 1, pass == 0 ? h : h2, Hj, s));
+        CU(launch_gs_update(n, ctx->V, n, j + 1, pass == 0 ? h : h2, w, s));
+      }
+      CU(launch_dot_partials(n, w, nullptr, ctx->part, s));
+      CU(launch_finalize(ctx->part, 1, ctx->scal + S_TMP, s));
+      CU(launch_normalize_into(n, w, ctx->scal + S_TMP, ctx->V + (size_t)(j + 1) * n, Hj + j + 1, s));
+      CU(launch_gmres_givens(ctx->H, ldh, j, cs, sn, g, s));
+      CU(cudaMemcpyAsync(ctx->scal + S_G, g + j + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+      ST(read_scalars(ctx, S_G, 1));
+      jdone = j + 1;
+      const double gres = std::fabs(ctx->hscal[S_G]);
+      if (!std::isfinite(gres)) return fail(ctx, GASA_ERR_BREAKDOWN, "GMRES: non-finite residual");
+      if (gres <= inner_tol || total >= max_iter) break;
+    }
+    CU(launch_gmres_backsolve(ctx->H, ldh, jdone, g, y, s));
+    CU(launch_combine(n, flex ? ctx->Z : ctx->V, n, jdone, y, x, s));
+  }
+  ST(spmv_outer(ctx, GASA_MV_RESIDUAL, x, b, t));
+  double rr;
+  ST(norm2(ctx, n, t, S_TMP, &rr));
+  *relres = std::sqrt(rr) / bn;
+  *iters = total;
+  *conv = *relres <= tol;
+  return GASA_OK;
+}
+
+// ----------------------------------------------------------------------------
+// setup helpers
+// ----------------------------------------------------------------------------
+int keep_count(int rows, int r, double n_cut) {
+  int s = (int)std::floor((double)rows / n_cut);
+  s = std::max(1, s);
+  s = std::min(s, r);
+  s = std::min(s, rows);
+  return s;
+}
+
+gasa_status upload_i32(gasa_ctx *ctx, int **d, const int32_t *h, size_t n) {
+  ST(dalloc(ctx, d, n));
+  CU(cudaMemcpyAsync(*d, h, n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  return GASA_OK;
+}
+
+// symbolic + numeric C = A B on BSR patterns (fresh allocations in ctx)
+gasa_status spgemm(gasa_ctx *ctx, const DevBSR &A, const DevBSR &B, DevBSR &C) {
+  cudaStream_t s = ctx->stream;
+  const int n = A.nrows;
+  int *cand = nullptr, *mx = nullptr, *cnt = nullptr;
+  ST(dalloc(ctx, &cand, n + 1));
+  ST(dalloc(ctx, &mx, 1));
+  ST(dalloc(ctx, &cnt, n + 1));
+  CU(launch_cand_count_AB(n, A.rp, A.col, B.rp, cand, s));
+  CU(launch_max_int(n, cand, mx, s));
+  int maxc = 0;
+  CU(cudaMemcpyAsync(&maxc, mx, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if ((size_t)maxc * sizeof(int) > 200 * 1024)
+    return fail(ctx, GASA_ERR_UNSUPPORTED, "Galerkin product row too dense for shared memory");
+  C.nrows = n;
+  C.ncols = B.ncols;
+  C.br = A.br;
+  C.bc = B.bc;
+  CU(launch_pattern_AB(n, A.rp, A.col, B.rp, B.col, cnt, nullptr, nullptr, maxc, s));
+  ST(dalloc(ctx, &C.rp, n + 1));
+  CU(launch_exclusive_scan(n, cnt, C.rp, nullptr, s));
+  int nnz = 0;
+  CU(cudaMemcpyAsync(&nnz, C.rp + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  C.nnzb = nnz;
+  ST(dalloc(ctx, &C.col, (size_t)nnz));
+  ST(dalloc(ctx, &C.val, (size_t)nnz * C.br * C.bc));
+  CU(launch_pattern_AB(n, A.rp, A.col, B.rp, B.col, nullptr, C.rp, C.col, maxc, s));
+  CU(launch_numeric_AB(n, A.br, A.bc, B.bc, A.rp, A.col, A.val, B.rp, B.col, B.val, C.rp, C.col,
+                       C.val, s));
+  CU(cudaStreamSynchronize(s));
+  dfree(ctx, cand);
+  dfree(ctx, mx);
+  dfree(ctx, cnt);
+  return GASA_OK;
+}
+
+gasa_status transpose(gasa_ctx *ctx, const DevBSR &P, DevBSR &R) {
+  cudaStream_t s = ctx->stream;
+  R.nrows = P.ncols;
+  R.ncols = P.nrows;
+  R.br = P.bc;
+  R.bc = P.br;
+  R.nnzb = P.nnzb;
+  int *src = nullptr, *cnt = nullptr;
+  ST(dalloc(ctx, &R.rp, R.nrows + 1));
+  ST(dalloc(ctx, &R.col, (size_t)P.nnzb));
+  ST(dalloc(ctx, &R.val, (size_t)P.nnzb * P.br * P.bc));
+  ST(dalloc(ctx, &src, (size_t)P.nnzb));
+  ST(dalloc(ctx, &cnt, (size_t)R.nrows + 1));
+  CU(launch_transpose(P.nrows, P.ncols, P.br, P.bc, P.rp, P.col, P.val, R.rp, R.col, R.val, src,
+                      cnt, s));
+  CU(cudaStreamSynchronize(s));
+  dfree(ctx, src);
+  dfree(ctx, cnt);
+  return GASA_OK;
+}
+
+gasa_status make_f32(gasa_ctx *ctx, DevBSR &m) {
+  const int64_t n = m.nnzb * m.br * m.bc;
+  ST(dalloc(ctx, &m.val32, (size_t)n));
+  CU(launch_convert<double, float>(n, m.val, m.val32, ctx->stream));
+  return GASA_OK;
+}
+
+gasa_status validate_bsr(gasa_ctx *ctx, int n, int b, int nnzb, const int32_t *rp,
+                         const int32_t *col) {
+  if (n <= 0 || b <= 0 || b > 64 || nnzb < n)
+    return fail(ctx, GASA_ERR_INVALID_ARG, "A: bad sizes (need n_blocks > 0, 0 < block <= 64)");
+  if (rp[0] != 0 || rp[n] != nnzb) return fail(ctx, GASA_ERR_INVALID_ARG, "A: row_ptr ends");
+  for (int i = 0; i < n; ++i) {
+    if (rp[i + 1] < rp[i]) return fail(ctx, GASA_ERR_INVALID_ARG, "A: row_ptr not monotone");
+    bool diag = false;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      if (col[k] < 0 || col[k] >= n) return fail(ctx, GASA_ERR_INVALID_ARG, "A: column out of range");
+      if (k > rp[i] && col[k] <= col[k - 1])
+        return fail(ctx, GASA_ERR_INVALID_ARG, "A: columns not strictly increasing");
+      if (col[k] == i) diag = true;
+    }
+    if (!diag) return fail(ctx, GASA_ERR_INVALID_ARG, "A: missing diagonal block");
+  }
+  return GASA_OK;
+}
+
+gasa_status validate_graph(gasa_ctx *ctx, int n, const int32_t *ap, const int32_t *ai) {
+  if (!ap) return GASA_OK;
+  if (!ai && ap[n] > 0) return fail(ctx, GASA_ERR_INVALID_ARG, "adjacency: null indices");
+  if (ap[0] != 0) return fail(ctx, GASA_ERR_INVALID_ARG, "adjacency: ptr[0] != 0");
+  std::vector<std::pair<int, int>> e;
+  for (int i = 0; i < n; ++i) {
+    if (ap[i + 1] < ap[i]) return fail(ctx, GASA_ERR_INVALID_ARG, "adjacency: ptr not monotone");
+    for (int k = ap[i]; k < ap[i + 1]; ++k) {
+      const int j = ai[k];
+      if (j < 0 || j >= n || j == i) return fail(ctx, GASA_ERR_INVALID_ARG, "adjacency: bad neighbour");
+      e.emplace_back(i, j);
+    }
+  }
+  std::vector<std::pair<int, int>> t(e.size());
+  for (size_t q = 0; q < e.size(); ++q) t[q] = {e[q].second, e[q].first};
+  std::sort(e.begin(), e.end());
+  std::sort(t.begin(), t.end());
+  if (e != t) return fail(ctx, GASA_ERR_INVALID_ARG, "adjacency: not symmetric");
+  return GASA_OK;
+}
+
+gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_ptr,
+                       const int32_t *adj_idx, const double *centroids,
+                       const gasa_hierarchy *hier, const gasa_options *opt,
+                       gasa_setup_info *info) {
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = ctx->stream;
+  if (!Ain || !opt) return fail(ctx, GASA_ERR_INVALID_ARG, "null A or options");
+  if (!hier) return fail(ctx, GASA_ERR_UNSUPPORTED, "a hierarchy must be given");
+  if (hier->n_levels < 2 || hier->n_levels > GASA_MAX_LEVELS || !hier->agg_of)
+    return fail(ctx, GASA_ERR_INVALID_ARG, "hierarchy: need 2..GASA_MAX_LEVELS levels");
+  if (opt->t_pre < 0 || opt->t_post < 0 || opt->q_power < 0 || opt->max_relax < 0 ||
+      opt->gamma < 0.0 || !(opt->omega_factor > 0.0) || opt->dim < 1 || opt->dim > 3)
+    return fail(ctx, GASA_ERR_INVALID_ARG, "options out of range");
+  const int n0 = Ain->n_blocks, b0 = Ain->block, nnzb0 = Ain->nnzb;
+  if (n0 <= 0 || b0 <= 0 || nnzb0 <= 0 || !Ain->row_ptr || !Ain->col || !Ain->val)
+    return fail(ctx, GASA_ERR_INVALID_ARG, "A: null or empty");
+  // host copies of the pattern for validation
+  std::vector<int32_t> hrp(n0 + 1), hcol(nnzb0);
+  if (Ain->on_device) {
+    CU(cudaMemcpy(hrp.data(), Ain->row_ptr, sizeof(int) * (n0 + 1), cudaMemcpyDeviceToHost));
+    if (hrp[n0] != nnzb0) return fail(ctx, GASA_ERR_INVALID_ARG, "A: row_ptr[n] != nnzb");
+    CU(cudaMemcpy(hcol.data(), Ain->col, sizeof(int) * nnzb0, cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(hrp.data(), Ain->row_ptr, sizeof(int) * (n0 + 1));
+    if (hrp[n0] != nnzb0) return fail(ctx, GASA_ERR_INVALID_ARG, "A: row_ptr[n] != nnzb");
+    std::memcpy(hcol.data(), Ain->col, sizeof(int) * nnzb0);
+  }
+  ST(validate_bsr(ctx, n0, b0, nnzb0, hrp.data(), hcol.data()));
+  ST(validate_graph(ctx, n0, adj_ptr, adj_idx));
+  if (centroids) {
+    for (int64_t i = 0; i < (int64_t)n0 * opt->dim; ++i)
+      if (!std::isfinite(centroids[i])) return fail(ctx, GASA_ERR_INVALID_ARG, "centroids: non-finite");
+  }
+  // hierarchy validation and per-level sizes
+  const int N = hier->n_levels - 1;
+  std::vector<int> units(N + 1), sizes(N + 1);
+  std::vector<std::vector<int>> children_count(N);
+  units[0] = n0;
+  for (int k = 1; k <= N; ++k) {
+    const int32_t *a = hier->agg_of[k - 1];
+    if (!a) return fail(ctx, GASA_ERR_INVALID_ARG, "hierarchy: null level");
+    int mx = -1;
+    for (int i = 0; i < units[k - 1]; ++i) {
+      if (a[i] < 0) return fail(ctx, GASA_ERR_INVALID_ARG, "hierarchy: negative aggregate id");
+      mx = std::max(mx, (int)a[i]);
+    }
+    units[k] = mx + 1;
+    children_count[k - 1].assign(units[k], 0);
+    for (int i = 0; i < units[k - 1]; ++i) children_count[k - 1][a[i]]++;
+    for (int J = 0; J < units[k]; ++J)
+      if (children_count[k - 1][J] == 0)
+        return fail(ctx, GASA_ERR_INVALID_ARG, "hierarchy: empty aggregate");
+  }
+  // candidate count r (Section 4.2: median level-1 aggregate dofs, lower median)
+  int r = opt->n_cand;
+  if (r <= 0) {
+    std::vector<int> d(children_count[0]);
+    for (auto &v : d) v *= b0;
+    std::sort(d.begin(), d.end());
+    r = d[(d.size() - 1) / 2];
+  }
+  if (r > 256) return fail(ctx, GASA_ERR_UNSUPPORTED, "more than 256 candidates");
+  const double n_cut = opt->n_cut > 0.0 ? opt->n_cut : (double)((1 << opt->dim) - (opt->dim - 1));
+  sizes[0] = b0;
+  std::vector<int> maxch(N);
+  for (int k = 0; k < N; ++k) {
+    int sk = -1, mc = 0;
+    for (int J = 0; J < units[k + 1]; ++J) {
+      const int rows = children_count[k][J] * sizes[k];
+      const int sj = keep_count(rows, r, n_cut);
+      if (sk < 0) sk = sj;
+      if (sj != sk)
+        return fail(ctx, GASA_ERR_UNSUPPORTED,
+                    "aggregates of one level keep different counts (Eq. sik); equal counts required");
+      mc = std::max(mc, children_count[k][J]);
+    }
+    sizes[k + 1] = sk;
+    maxch[k] = mc;
+    int smem_optin = 0;
+    CU(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    if ((size_t)mc * sizes[k] * r * sizeof(double) > (size_t)smem_optin)
+      return fail(ctx, GASA_ERR_UNSUPPORTED, "aggregate x candidates exceed shared memory");
+  }
+  if ((int64_t)units[N] * sizes[N] > 16384)
+    return fail(ctx, GASA_ERR_UNSUPPORTED, "coarsest level larger than 16384 dofs");
+
+  free_all(ctx);
+  ctx->opt = *opt;
+  if (ctx->opt.max_iter <= 0) ctx->opt.max_iter = 10000;
+  ctx->N = N;
+  ctx->r = r;
+  ctx->L.assign(N + 1, Level());
+  const bool keep = opt->keep_setup_data != 0;
+  for (int k = 0; k <= N; ++k) {
+    ctx->L[k].n = units[k];
+    ctx->L[k].s = sizes[k];
+    ctx->L[k].ndof = (int64_t)units[k] * sizes[k];
+  }
+  // level-0 operator
+  {
+    Level &l = ctx->L[0];
+    DevBSR &A = l.A;
+    A.nrows = A.ncols = n0;
+    A.br = A.bc = b0;
+    A.nnzb = nnzb0;
+    ST(upload_i32(ctx, &A.rp, hrp.data(), n0 + 1));
+    ST(upload_i32(ctx, &A.col, hcol.data(), nnzb0));
+    ST(dalloc(ctx, &A.val, (size_t)nnzb0 * b0 * b0));
+    CU(cudaMemcpyAsync(A.val, Ain->val, sizeof(double) * (size_t)nnzb0 * b0 * b0,
+                       Ain->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  }
+  // candidates B^0
+  double *B = nullptr;
+  ST(dalloc(ctx, &B, (size_t)ctx->L[0].ndof * r));
+  if (opt->init_candidates) {
+    CU(cudaMemcpyAsync(B, opt->init_candidates, sizeof(double) * ctx->L[0].ndof * r,
+                       cudaMemcpyHostToDevice, s));
+  } else {
+    CU(launch_normal(ctx->L[0].ndof * r, opt->seed, 3, B, s));
+  }
+  int *dstat = nullptr;
+  ST(dalloc(ctx, &dstat, 4));
+  double *pv = nullptr, *pv2 = nullptr;   // power-iteration vectors (level 0 is the largest)
+  ST(dalloc(ctx, &pv, (size_t)ctx->L[0].ndof));
+  ST(dalloc(ctx, &pv2, (size_t)ctx->L[0].ndof));
+  ST(dalloc(ctx, &ctx->part, (size_t)4 * kRedBlocks * std::max(1, r)));
+  ST(dalloc(ctx, &ctx->scal, S_COUNT));
+  CU(cudaMallocHost((void **)&ctx->hscal, S_COUNT * sizeof(double)));
+  double **ptab = nullptr;
+  ST(dalloc(ctx, &ptab, (size_t)2 * r));
+  double *nrmbuf = nullptr;
+  ST(dalloc(ctx, &nrmbuf, (size_t)r));
+  double *B2 = nullptr;
+  ST(dalloc(ctx, &B2, (size_t)ctx->L[0].ndof * r));
+
+  for (int k = 0; k < N; ++k) {
+    Level &l = ctx->L[k];
+    Level &ln = ctx->L[k + 1];
+    const int64_t nd = l.ndof;
+    // ---- smoother: block inverses, Alg. 4, Eq. omega ----
+    ST(dalloc(ctx, &l.W, (size_t)l.n * l.s * l.s));
+    CU(cudaMemsetAsync(dstat, 0, sizeof(int) * 4, s));
+    CU(launch_block_inverse(l.n, l.s, l.A.rp, l.A.col, l.A.val, 1.0, l.W, dstat, s));
+    int nsing = 0;
+    CU(cudaMemcpyAsync(&nsing, dstat, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (nsing) return fail(ctx, GASA_ERR_SINGULAR_BLOCK, "singular diagonal block on level " + std::to_string(k));
+    CU(launch_uniform_pm1(nd, opt->seed, 4 + 16 * (uint64_t)k, pv, s));
+    CU(launch_dot_partials(nd, pv, nullptr, ctx->part, s));
+    CU(launch_finalize(ctx->part, 1, ctx->scal + S_TMP, s));
+    CU(launch_scale_by_inv_sqrt(nd, pv, ctx->scal + S_TMP, s));
+    for (int it = 0; it < opt->q_power; ++it) {
+      CU(launch_jacobi<double>(JAC_APPLY, l.n, l.s, l.A.rp, l.A.col, l.A.val, l.W, pv, nullptr, pv2, s));
+      CU(launch_dot_partials(nd, pv2, nullptr, ctx->part, s));
+      CU(launch_finalize(ctx->part, 1, ctx->scal + S_TMP, s));
+      CU(launch_scale_by_inv_sqrt(nd, pv2, ctx->scal + S_TMP, s));
+      std::swap(pv, pv2);
+    }
+    CU(launch_jacobi<double>(JAC_APPLY, l.n, l.s, l.A.rp, l.A.col, l.A.val, l.W, pv, nullptr, pv2, s));
+    double rr;
+    ST(norm2(ctx, nd, pv2, S_TMP, &rr));
+    l.rho = std::sqrt(rr);
+    if (!(l.rho > 0.0) || !std::isfinite(l.rho))
+      return fail(ctx, GASA_ERR_BREAKDOWN, "power iteration gave a zero or non-finite estimate");
+    l.omega = opt->omega_factor / l.rho;
+    CU(launch_scale((int64_t)l.n * l.s * l.s, l.omega, l.W, s));
+    // ---- Eq. bsmooth: relax every candidate column ----
+    if (keep) {
+      ST(dalloc(ctx, &l.cand_in, (size_t)nd * r));
+      CU(cudaMemcpyAsync(l.cand_in, B, sizeof(double) * nd * r, cudaMemcpyDeviceToDevice, s));
+    }
+    {
+      std::vector<double *> cur(r), nxt(r);
+      std::vector<double> nrm(r);
+      std::vector<int> active, sweeps(r, 0);
+      for (int c = 0; c < r; ++c) {
+        cur[c] = B + (size_t)c * nd;
+        nxt[c] = B2 + (size_t)c * nd;
+        active.push_back(c);
+      }
+      // initial norms
+      {
+        std::vector<const double *> tab(r);
+        for (int c = 0; c < r; ++c) tab[c] = cur[c];
+        CU(cudaMemcpyAsync(ptab, tab.data(), sizeof(double *) * r, cudaMemcpyHostToDevice, s));
+        CU(launch_colnorm_partials(nd, (const double *const *)ptab, r, ctx->part, s));
+        CU(launch_finalize(ctx->part, r, nrmbuf, s));
+        CU(cudaMemcpyAsync(nrm.data(), nrmbuf, sizeof(double) * r, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        for (auto &v : nrm) v = std::sqrt(v);
+      }
+      std::vector<double *> tab(2 * r);
+      std::vector<double> nn(r);
+      for (int m = 0; m < opt->max_relax && !active.empty(); ++m) {
+        const int na = (int)active.size();
+        for (int q = 0; q < na; ++q) {
+          tab[q] = cur[active[q]];
+          tab[na + q] = nxt[active[q]];
+        }
+        CU(cudaMemcpyAsync(ptab, tab.data(), sizeof(double *) * 2 * na, cudaMemcpyHostToDevice, s));
+        CU(launch_relax_multi(l.n, l.s, l.A.rp, l.A.col, l.A.val, l.W, (const double *const *)ptab,
+                              (double *const *)(ptab + na), na, s));
+        CU(launch_colnorm_partials(nd, (const double *const *)(ptab + na), na, ctx->part, s));
+        CU(launch_finalize(ctx->part, na, nrmbuf, s));
+        CU(cudaMemcpyAsync(nn.data(), nrmbuf, sizeof(double) * na, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        std::vector<int> still;
+        for (int q = 0; q < na; ++q) {
+          const int c = active[q];
+          std::swap(cur[c], nxt[c]);
+          sweeps[c] = m + 1;
+          const double nnew = std::sqrt(nn[q]);
+          if (nrm[c] / nnew < 1.0 + opt->gamma) continue;   // stagnated: keep this sweep, stop
+          nrm[c] = nnew;
+          still.push_back(c);
+        }
+        active.swap(still);
+      }
+      // gather the final columns into B
+      for (int c = 0; c < r; ++c)
+        if (cur[c] != B + (size_t)c * nd)
+          CU(cudaMemcpyAsync(B + (size_t)c * nd, cur[c], sizeof(double) * nd, cudaMemcpyDeviceToDevice, s));
+      l.sweeps = sweeps;
+    }
+    if (keep) {
+      ST(dalloc(ctx, &l.cand, (size_t)nd * r));
+      CU(cudaMemcpyAsync(l.cand, B, sizeof(double) * nd * r, cudaMemcpyDeviceToDevice, s));
+    }
+    // ---- Eq. splitB_dg + Eq. sik: tentative prolongator ----
+    l.n_next = ln.n;
+    l.s_next = ln.s;
+    l.max_children = maxch[k];
+    ST(upload_i32(ctx, &l.agg, hier->agg_of[k], l.n));
+    ST(dalloc(ctx, &l.child_ptr, ln.n + 1));
+    ST(dalloc(ctx, &l.child_idx, l.n));
+    int *scr = nullptr;
+    ST(dalloc(ctx, &scr, ln.n + 1));
+    CU(build_children(l.n, ln.n, l.agg, l.child_ptr, l.child_idx, scr, s));
+    ST(dalloc(ctx, &l.T, (size_t)l.n * l.s * l.s_next));
+    CU(cudaMemsetAsync(dstat, 0, sizeof(int) * 4, s));
+    CU(launch_tentative(l.s, ln.n, l.max_children, l.child_ptr, l.child_idx, B, nd, r, l.s_next, l.T,
+                        nullptr, dstat, s));
+    int tstat = 0;
+    CU(cudaMemcpyAsync(&tstat, dstat, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    dfree(ctx, scr);
+    if (tstat) return fail(ctx, GASA_ERR_BREAKDOWN, "candidate block rank below the kept count on level " + std::to_string(k));
+    // ---- Eq. TR0: P = T - w D^{-1} A T (pattern of A times the aggregation) ----
+    {
+      DevBSR &P = l.P;
+      P.nrows = l.n;
+      P.ncols = ln.n;
+      P.br = l.s;
+      P.bc = ln.s;
+      int maxrow = 0;
+      for (int i = 0; i < l.n && k == 0; ++i) maxrow = std::max(maxrow, hrp[i + 1] - hrp[i]);
+      if (k > 0) {
+        std::vector<int> rp(l.n + 1);
+        CU(cudaMemcpy(rp.data(), l.A.rp, sizeof(int) * (l.n + 1), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < l.n; ++i) maxrow = std::max(maxrow, rp[i + 1] - rp[i]);
+      }
+      int *cnt = nullptr;
+      ST(dalloc(ctx, &cnt, l.n + 1));
+      CU(launch_pattern_P(l.n, l.A.rp, l.A.col, l.agg, cnt, nullptr, nullptr, maxrow, s));
+      ST(dalloc(ctx, &P.rp, l.n + 1));
+      CU(launch_exclusive_scan(l.n, cnt, P.rp, nullptr, s));
+      int nnz = 0;
+      CU(cudaMemcpyAsync(&nnz, P.rp + l.n, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      P.nnzb = nnz;
+      ST(dalloc(ctx, &P.col, (size_t)nnz));
+      ST(dalloc(ctx, &P.val, (size_t)nnz * P.br * P.bc));
+      CU(launch_pattern_P(l.n, l.A.rp, l.A.col, l.agg, nullptr, P.rp, P.col, maxrow, s));
+      CU(launch_numeric_P(l.n, l.s, ln.s, l.A.rp, l.A.col, l.A.val, l.W, l.T, l.agg, P.rp, P.col,
+                          P.val, s));
+      CU(cudaStreamSynchronize(s));
+      dfree(ctx, cnt);
+    }
+    // ---- Eq. SA_restrict: R = P^T ----
+    ST(transpose(ctx, l.P, l.R));
+    // ---- Galerkin: A_{k+1} = R (A P) ----
+    {
+      DevBSR AP;
+      ST(spgemm(ctx, l.A, l.P, AP));
+      ST(spgemm(ctx, l.R, AP, ln.A));
+      dfree(ctx, AP.rp);
+      dfree(ctx, AP.col);
+      dfree(ctx, AP.val);
+    }
+    // ---- next candidates: B^{k+1} = R B^k (Alg. 5) or T^T B^k (Eq. SA_Bk) ----
+    {
+      const int64_t ndn = ln.ndof;
+      double *Bn = nullptr;
+      ST(dalloc(ctx, &Bn, (size_t)ndn * r));
+      if (opt->cand_init == GASA_CAND_TT) {
+        DevBSR Tm, Tt;
+        Tm.nrows = l.n;
+        Tm.ncols = ln.n;
+        Tm.br = l.s;
+        Tm.bc = ln.s;
+        Tm.nnzb = l.n;
+        std::vector<int> seq(l.n + 1);
+        for (int i = 0; i <= l.n; ++i) seq[i] = i;
+        ST(upload_i32(ctx, &Tm.rp, seq.data(), l.n + 1));
+        Tm.col = l.agg;
+        Tm.val = l.T;
+        ST(transpose(ctx, Tm, Tt));
+        CU(launch_bsr_mm(Tt.nrows, Tt.br, Tt.bc, Tt.rp, Tt.col, Tt.val, B, nd, Bn, ndn, r, s));
+        CU(cudaStreamSynchronize(s));
+        dfree(ctx, Tm.rp);
+        dfree(ctx, Tt.rp);
+        dfree(ctx, Tt.col);
+        dfree(ctx, Tt.val);
+      } else {
+        CU(launch_bsr_mm(l.R.nrows, l.R.br, l.R.bc, l.R.rp, l.R.col, l.R.val, B, nd, Bn, ndn, r, s));
+      }
+      CU(cudaStreamSynchronize(s));
+      dfree(ctx, B);
+      B = Bn;
+    }
+    if (!keep) {
+      dfree(ctx, l.T);
+      l.T = nullptr;
+    }
+    // ---- FP32 copies for the mixed-precision V-cycle ----
+    ST(make_f32(ctx, l.A));
+    ST(make_f32(ctx, l.P));
+    ST(make_f32(ctx, l.R));
+    ST(dalloc(ctx, &l.W32, (size_t)l.n * l.s * l.s));
+    CU(launch_convert<double, float>((int64_t)l.n * l.s * l.s, l.W, l.W32, s));
+  }
+  dfree(ctx, B);
+  dfree(ctx, B2);
+  dfree(ctx, pv);
+  dfree(ctx, pv2);
+  dfree(ctx, ptab);
+  dfree(ctx, nrmbuf);
+  // ---- coarsest level: dense inverse ----
+  {
+    Level &lc = ctx->L[N];
+    ctx->nc = (int)lc.ndof;
+    const size_t nc = (size_t)ctx->nc;
+    double *D = nullptr, *work = nullptr;
+    ST(dalloc(ctx, &D, nc * nc));
+    ST(dalloc(ctx, &work, 2 * nc * nc + nc));
+    ST(dalloc(ctx, &ctx->coarse_inv, nc * nc));
+    CU(launch_bsr_to_dense(lc.n, lc.s, lc.A.rp, lc.A.col, lc.A.val, D, s));
+    CU(cudaMemsetAsync(dstat, 0, sizeof(int) * 4, s));
+    CU(launch_dense_inverse(ctx->nc, D, ctx->coarse_inv, work, dstat, s));
+    int sing = 0;
+    CU(cudaMemcpyAsync(&sing, dstat, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    dfree(ctx, D);
+    dfree(ctx, work);
+    if (sing) return fail(ctx, GASA_ERR_SINGULAR_BLOCK, "coarsest matrix is singular");
+    ST(make_f32(ctx, lc.A));
+  }
+  // ---- V-cycle vectors and Krylov workspace ----
+  for (int k = 0; k <= N; ++k) {
+    Level &l = ctx->L[k];
+    ST(dalloc(ctx, &l.x, (size_t)l.ndof));
+    ST(dalloc(ctx, &l.x2, (size_t)l.ndof));
+    ST(dalloc(ctx, &l.b, (size_t)l.ndof));
+    ST(dalloc(ctx, &l.r, (size_t)l.ndof));
+    ST(dalloc(ctx, &l.xf, (size_t)l.ndof));
+    ST(dalloc(ctx, &l.x2f, (size_t)l.ndof));
+    ST(dalloc(ctx, &l.bf, (size_t)l.ndof));
+    ST(dalloc(ctx, &l.rf, (size_t)l.ndof));
+  }
+  const int64_t n = ctx->L[0].ndof;
+  for (double **p : {&ctx->kx, &ctx->kr, &ctx->kz, &ctx->kp, &ctx->kq, &ctx->kzold, &ctx->kb, &ctx->kt})
+    ST(dalloc(ctx, p, (size_t)n));
+  ST(dalloc(ctx, &ctx->kf_in, (size_t)n));
+  ST(dalloc(ctx, &ctx->kf_out, (size_t)n));
+  CU(cudaStreamSynchronize(s));
+  ctx->ready = true;
+  ctx->setup_seconds =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->n_levels = N + 1;
+    info->n_cand = r;
+    for (int k = 0; k <= N; ++k) {
+      Level &l = ctx->L[k];
+      info->units[k] = l.n;
+      info->block[k] = l.s;
+      info->dofs[k] = l.ndof;
+      info->nnzb[k] = l.A.nnzb;
+      info->nnz[k] = l.A.nnzb * l.s * l.s;
+      info->omega[k] = l.omega;
+      info->rho[k] = l.rho;
+      int mx = 0;
+      for (int v : l.sweeps) mx = std::max(mx, v);
+      info->relax_sweeps_max[k] = mx;
+    }
+    info->seconds = ctx->setup_seconds;
+    info->device_bytes = ctx->device_bytes;
+  }
+  return GASA_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// extern "C" entry points
+// ============================================================================
+extern "C" {
+
+void gasa_default_options(gasa_options *opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->dim = 2;
+  opt->solver = GASA_SOLVER_CG;
+  opt->restart = 30;
+  opt->precision = GASA_PREC_FP64;
+  opt->t_pre = 3;
+  opt->t_post = 3;
+  opt->q_power = 3;
+  opt->n_cand = 0;
+  opt->max_relax = 100;
+  opt->max_iter = 10000;
+  opt->cand_init = GASA_CAND_R;
+  opt->gamma = 0.03;
+  opt->omega_factor = 4.0 / 3.0;
+  opt->n_cut = 0.0;
+  opt->seed = 13373;
+  opt->init_candidates = nullptr;
+}
+
+gasa_status gasa_create(gasa_ctx **out, int32_t device, void *stream) {
+  if (!out) return GASA_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return GASA_ERR_CUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return GASA_ERR_CUDA;
+  gasa_ctx *c = new gasa_ctx();
+  c->device = device;
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return GASA_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  gasa_default_options(&c->opt);
+  *out = c;
+  return GASA_OK;
+}
+
+gasa_status gasa_setup(gasa_ctx *ctx, const gasa_bsr *A, const int32_t *adj_ptr,
+                       const int32_t *adj_idx, const double *centroids,
+                       const gasa_hierarchy *hier, const gasa_options *opt,
+                       gasa_setup_info *info) {
+  if (!ctx) return GASA_ERR_INVALID_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, GASA_ERR_CUDA, "cudaSetDevice");
+  gasa_status st = setup_impl(ctx, A, adj_ptr, adj_idx, centroids, hier, opt, info);
+  if (st != GASA_OK) {
+    cudaStreamSynchronize(ctx->stream);
+    ctx->ready = false;
+  }
+  return st;
+}
+
+gasa_status gasa_solve(gasa_ctx *ctx, const double *b, double *x, double tol, int32_t precision,
+                       int32_t on_device, gasa_solve_info *info) {
+  if (!ctx) return GASA_ERR_INVALID_ARG;
+  if (!ctx->ready) return fail(ctx, GASA_ERR_STATE, "solve before setup");
+  if (!b || !x || !(tol > 0.0)) return fail(ctx, GASA_ERR_INVALID_ARG, "null vector or tol <= 0");
+  if (precision != GASA_PREC_FP64 && precision != GASA_PREC_MIXED32)
+    return fail(ctx, GASA_ERR_INVALID_ARG, "unknown precision");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, GASA_ERR_CUDA, "cudaSetDevice");
+  auto t0 = std::chrono::steady_clock::now();
+  const int64_t n = ctx->L[0].ndof;
+  const double *bd = b;
+  if (!on_device) {
+    CU(cudaMemcpyAsync(ctx->kb, b, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    bd = ctx->kb;
+  }
+  int iters = 0;
+  double rel = 0.0;
+  bool conv = false;
+  gasa_status st = ctx->opt.solver == GASA_SOLVER_GMRES
+                       ? gmres(ctx, bd, tol, precision, &iters, &rel, &conv)
+                       : pcg(ctx, bd, tol, precision, &iters, &rel, &conv);
+  if (st == GASA_OK || st == GASA_ERR_NOT_SPD) {
+    if (on_device) {
+      CU(cudaMemcpyAsync(x, ctx->kx, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    } else {
+      CU(cudaMemcpyAsync(x, ctx->kx, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+  }
+  if (info) {
+    info->iterations = iters;
+    info->converged = conv ? 1 : 0;
+    info->rel_residual = rel;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (st != GASA_OK) return st;
+  return conv ? GASA_OK : fail(ctx, GASA_ERR_NOT_CONVERGED, "max_iter reached");
+}
+
+gasa_status gasa_vcycle(gasa_ctx *ctx, const double *r, double *z, int32_t precision) {
+  if (!ctx) return GASA_ERR_INVALID_ARG;
+  if (!ctx->ready) return fail(ctx, GASA_ERR_STATE, "vcycle before setup");
+  if (!r || !z) return fail(ctx, GASA_ERR_INVALID_ARG, "null vector");
+  if (precision != GASA_PREC_FP64 && precision != GASA_PREC_MIXED32)
+    return fail(ctx, GASA_ERR_INVALID_ARG, "unknown precision");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, GASA_ERR_CUDA, "cudaSetDevice");
+  ST(apply_M(ctx, r, z, precision));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return GASA_OK;
+}
+
+gasa_status gasa_level_shape(gasa_ctx *ctx, int32_t level, int64_t shape[8]) {
+  if (!ctx || !shape) return GASA_ERR_INVALID_ARG;
+  if (!ctx->ready) return fail(ctx, GASA_ERR_STATE, "no hierarchy");
+  if (level < 0 || level > ctx->N) return fail(ctx, GASA_ERR_INVALID_ARG, "level out of range");
+  Level &l = ctx->L[level];
+  shape[0] = l.n;
+  shape[1] = l.s;
+  shape[2] = l.A.nnzb;
+  shape[3] = level < ctx->N ? l.P.nnzb : 0;
+  shape[4] = level < ctx->N ? l.R.nnzb : 0;
+  shape[5] = level < ctx->N ? l.s_next : 0;
+  shape[6] = ctx->r;
+  shape[7] = l.ndof;
+  return GASA_OK;
+}
+
+gasa_status gasa_get_level(gasa_ctx *ctx, int32_t level, int32_t what, void *host_out,
+                           int64_t n_bytes) {
+  if (!ctx || !host_out) return GASA_ERR_INVALID_ARG;
+  if (!ctx->ready) return fail(ctx, GASA_ERR_STATE, "no hierarchy");
+  if (level < 0 || level > ctx->N) return fail(ctx, GASA_ERR_INVALID_ARG, "level out of range");
+  Level &l = ctx->L[level];
+  const bool fine = level < ctx->N;
+  const void *src = nullptr;
+  int64_t bytes = 0;
+  switch (what) {
+    case GASA_LV_A_ROWPTR: src = l.A.rp; bytes = 4 * (l.n + 1); break;
+    case GASA_LV_A_COL: src = l.A.col; bytes = 4 * l.A.nnzb; break;
+    case GASA_LV_A_VAL: src = l.A.val; bytes = 8 * l.A.nnzb * l.s * l.s; break;
+    case GASA_LV_P_ROWPTR: if (fine) { src = l.P.rp; bytes = 4 * (l.n + 1); } break;
+    case GASA_LV_P_COL: if (fine) { src = l.P.col; bytes = 4 * l.P.nnzb; } break;
+    case GASA_LV_P_VAL: if (fine) { src = l.P.val; bytes = 8 * l.P.nnzb * l.s * l.s_next; } break;
+    case GASA_LV_R_ROWPTR: if (fine) { src = l.R.rp; bytes = 4 * (int64_t)(l.n_next + 1); } break;
+    case GASA_LV_R_COL: if (fine) { src = l.R.col; bytes = 4 * l.R.nnzb; } break;
+    case GASA_LV_R_VAL: if (fine) { src = l.R.val; bytes = 8 * l.R.nnzb * l.s * l.s_next; } break;
+    case GASA_LV_T_VAL: if (fine && l.T) { src = l.T; bytes = 8 * (int64_t)l.n * l.s * l.s_next; } break;
+    case GASA_LV_W: if (fine) { src = l.W; bytes = 8 * (int64_t)l.n * l.s * l.s; } break;
+    case GASA_LV_CAND: if (fine && l.cand) { src = l.cand; bytes = 8 * l.ndof * ctx->r; } break;
+    case GASA_LV_CAND_IN: if (fine && l.cand_in) { src = l.cand_in; bytes = 8 * l.ndof * ctx->r; } break;
+    case GASA_LV_SWEEPS:
+      if (fine) {
+        if (n_bytes < 4 * (int64_t)l.sweeps.size())
+          return fail(ctx, GASA_ERR_INVALID_ARG, "output buffer too small");
+        std::memcpy(host_out, l.sweeps.data(), 4 * l.sweeps.size());
+        return GASA_OK;
+      }
+      break;
+    case GASA_LV_COARSE_INV:
+      if (!fine) { src = ctx->coarse_inv; bytes = 8 * (int64_t)ctx->nc * ctx->nc; }
+      break;
+    default: return fail(ctx, GASA_ERR_INVALID_ARG, "unknown level item");
+  }
+  if (!src) return fail(ctx, GASA_ERR_INVALID_ARG, "item not available on this level (setup data is kept only with options.keep_setup_data)");
+  if (n_bytes < bytes) return fail(ctx, GASA_ERR_INVALID_ARG, "output buffer too small");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, GASA_ERR_CUDA, "cudaSetDevice");
+  CU(cudaStreamSynchronize(ctx->stream));
+  CU(cudaMemcpy(host_out, src, bytes, cudaMemcpyDeviceToHost));
+  return GASA_OK;
+}
+
+gasa_status gasa_profile_enable(gasa_ctx *ctx, int32_t on) {
+  if (!ctx) return GASA_ERR_INVALID_ARG;
+  cudaStreamSynchronize(ctx->stream);
+  ctx->prof = on != 0;
+  for (auto &p : ctx->pc) {
+    p.used = 0;
+    p.bytes = 0.0;
+    p.launches = 0;
+  }
+  return GASA_OK;
+}
+
+gasa_status gasa_profile_read(gasa_ctx *ctx, int32_t cls, double *ms, int64_t *launches,
+                              double *bytes) {
+  if (!ctx || cls < 0 || cls > 2) return GASA_ERR_INVALID_ARG;
+  CU(cudaStreamSynchronize(ctx->stream));
+  ProfClass &p = ctx->pc[cls];
+  double tot = 0.0;
+  for (size_t i = 0; i + 1 < p.used; i += 2) {
+    float t = 0.f;
+    CU(cudaEventElapsedTime(&t, p.ev[i], p.ev[i + 1]));
+    tot += t;
+  }
+  if (ms) *ms = tot;
+  if (launches) *launches = p.launches;
+  if (bytes) *bytes = p.bytes;
+  return GASA_OK;
+}
+
+gasa_status gasa_destroy(gasa_ctx *ctx) {
+  if (!ctx) return GASA_OK;
+  cudaSetDevice(ctx->device);
+  free_all(ctx);
+  for (auto &p : ctx->pc)
+    for (auto e : p.ev) cudaEventDestroy(e);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return GASA_OK;
+}
+
+const char *gasa_status_string(gasa_status s) {
+  if ((int)s < 0 || (int)s > (int)GASA_ERR_STATE) return "unknown status";
+  return kStatusText[(int)s];
+}
+
+const char *gasa_last_error(const gasa_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+// ---------------------------------------------------------------------------
+// single operations
+// ---------------------------------------------------------------------------
+static gasa_status op_status(cudaError_t e) {
+  if (e == cudaSuccess) return GASA_OK;
+  return e == cudaErrorMemoryAllocation ? GASA_ERR_OOM : GASA_ERR_CUDA;
+}
+
+gasa_status gasa_bsr_mv(int32_t mode, int32_t n_brows, int32_t br, int32_t bc,
+                        const int32_t *row_ptr, const int32_t *col, const double *val,
+                        const double *x, const double *b, double *y, void *stream) {
+  if (n_brows < 0 || br <= 0 || bc <= 0 || mode < 0 || mode > 2) return GASA_ERR_INVALID_ARG;
+  if (n_brows == 0) return GASA_OK;
+  if (!row_ptr || !col || !val || !x || !y || (mode == GASA_MV_RESIDUAL && !b))
+    return GASA_ERR_INVALID_ARG;
+  return op_status(launch_bsr_mv<double>(mode, n_brows, br, bc, row_ptr, col, val, x, b, y,
+                                         (cudaStream_t)stream));
+}
+
+gasa_status gasa_bsr_mv_f32(int32_t mode, int32_t n_brows, int32_t br, int32_t bc,
+                            const int32_t *row_ptr, const int32_t *col, const float *val,
+                            const float *x, const float *b, float *y, void *stream) {
+  if (n_brows < 0 || br <= 0 || bc <= 0 || mode < 0 || mode > 2) return GASA_ERR_INVALID_ARG;
+  if (n_brows == 0) return GASA_OK;
+  if (!row_ptr || !col || !val || !x || !y || (mode == GASA_MV_RESIDUAL && !b))
+    return GASA_ERR_INVALID_ARG;
+  return op_status(launch_bsr_mv<float>(mode, n_brows, br, bc, row_ptr, col, val, x, b, y,
+                                        (cudaStream_t)stream));
+}
+
+gasa_status gasa_jacobi_sweep(int32_t n_units, int32_t bs, const int32_t *row_ptr,
+                              const int32_t *col, const double *val, const double *W,
+                              const double *x, const double *b, double *x_out, int32_t first,
+                              void *stream) {
+  if (n_units < 0 || bs <= 0 || bs > 1024) return GASA_ERR_INVALID_ARG;
+  if (n_units == 0) return GASA_OK;
+  if (!W || !b || !x_out || (!first && (!row_ptr || !col || !val || !x)) || x == x_out)
+    return GASA_ERR_INVALID_ARG;
+  return op_status(launch_jacobi<double>(first ? JAC_FIRST : JAC_SWEEP, n_units, bs, row_ptr, col,
+                                         val, W, x, b, x_out, (cudaStream_t)stream));
+}
+
+gasa_status gasa_jacobi_sweep_f32(int32_t n_units, int32_t bs, const int32_t *row_ptr,
+                                  const int32_t *col, const float *val, const float *W,
+                                  const float *x, const float *b, float *x_out, int32_t first,
+                                  void *stream) {
+  if (n_units < 0 || bs <= 0 || bs > 1024) return GASA_ERR_INVALID_ARG;
+  if (n_units == 0) return GASA_OK;
+  if (!W || !b || !x_out || (!first && (!row_ptr || !col || !val || !x)) || x == x_out)
+    return GASA_ERR_INVALID_ARG;
+  return op_status(launch_jacobi<float>(first ? JAC_FIRST : JAC_SWEEP, n_units, bs, row_ptr, col,
+                                        val, W, x, b, x_out, (cudaStream_t)stream));
+}
+
+gasa_status gasa_block_inverse(int32_t n_units, int32_t bs, const int32_t *row_ptr,
+                               const int32_t *col, const double *val, double scale,
+                               double *W_out, int32_t *n_singular, void *stream) {
+  if (n_units < 0 || bs <= 0 || bs > 64 || !n_singular) return GASA_ERR_INVALID_ARG;
+  *n_singular = 0;
+  if (n_units == 0) return GASA_OK;
+  if (!row_ptr || !col || !val || !W_out) return GASA_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int *d = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&d, sizeof(int), s);
+  if (e != cudaSuccess) return op_status(e);
+  e = cudaMemsetAsync(d, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = launch_block_inverse(n_units, bs, row_ptr, col, val, scale, W_out, d, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(n_singular, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(d, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return op_status(e);
+}
+
+gasa_status gasa_power_estimate(int32_t n_units, int32_t bs, const int32_t *row_ptr,
+                                const int32_t *col, const double *val, const double *Dinv,
+                                const double *x0, int32_t q, double *rho, void *stream) {
+  if (n_units <= 0 || bs <= 0 || bs > 1024 || q < 0 || !row_ptr || !col || !val || !Dinv ||
+      !x0 || !rho)
+    return GASA_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = (int64_t)n_units * bs;
+  double *buf = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&buf, sizeof(double) * (2 * n + kRedBlocks + 2), s);
+  if (e != cudaSuccess) return op_status(e);
+  double *a = buf, *bb = buf + n, *part = buf + 2 * n, *sc = part + kRedBlocks;
+  e = cudaMemcpyAsync(a, x0, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = launch_dot_partials(n, a, nullptr, part, s);
+  if (e == cudaSuccess) e = launch_finalize(part, 1, sc, s);
+  if (e == cudaSuccess) e = launch_scale_by_inv_sqrt(n, a, sc, s);
+  for (int it = 0; it < q && e == cudaSuccess; ++it) {
+    e = launch_jacobi<double>(JAC_APPLY, n_units, bs, row_ptr, col, val, Dinv, a, nullptr, bb, s);
+    if (e == cudaSuccess) e = launch_dot_partials(n, bb, nullptr, part, s);
+    if (e == cudaSuccess) e = launch_finalize(part, 1, sc, s);
+    if (e == cudaSuccess) e = launch_scale_by_inv_sqrt(n, bb, sc, s);
+    std::swap(a, bb);
+  }
+  if (e == cudaSuccess)
+    e = launch_jacobi<double>(JAC_APPLY, n_units, bs, row_ptr, col, val, Dinv, a, nullptr, bb, s);
+  if (e == cudaSuccess) e = launch_dot_partials(n, bb, nullptr, part, s);
+  if (e == cudaSuccess) e = launch_finalize(part, 1, sc, s);
+  double h = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sc, sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(buf, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) *rho = std::sqrt(h);
+  return op_status(e);
+}
+
+gasa_status gasa_relax_candidates(int32_t n_units, int32_t bs, const int32_t *row_ptr,
+                                  const int32_t *col, const double *val, const double *W,
+                                  double *B, int32_t r, double gamma, int32_t max_relax,
+                                  int32_t *sweeps, void *stream) {
+  if (n_units <= 0 || bs <= 0 || bs > 1024 || r <= 0 || r > 1024 || max_relax < 0 || !row_ptr ||
+      !col || !val || !W || !B || !sweeps || gamma < 0.0)
+    return GASA_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = (int64_t)n_units * bs;
+  double *B2 = nullptr, *part = nullptr, *nr = nullptr;
+  double **tab = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&B2, sizeof(double) * n * r, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&part, sizeof(double) * kRedBlocks * r, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&nr, sizeof(double) * r, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&tab, sizeof(double *) * 2 * r, s);
+  std::vector<double *> cur(r), nxt(r), htab(2 * r);
+  std::vector<double> nrm(r), nn(r);
+  std::vector<int> active;
+  for (int c = 0; c < r; ++c) {
+    cur[c] = B + (size_t)c * n;
+    nxt[c] = B2 + (size_t)c * n;
+    active.push_back(c);
+    sweeps[c] = 0;
+  }
+  if (e == cudaSuccess) {
+    for (int c = 0; c < r; ++c) htab[c] = cur[c];
+    e = cudaMemcpyAsync(tab, htab.data(), sizeof(double *) * r, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_colnorm_partials(n, (const double *const *)tab, r, part, s);
+    if (e == cudaSuccess) e = launch_finalize(part, r, nr, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(nrm.data(), nr, sizeof(double) * r, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (auto &v : nrm) v = std::sqrt(v);
+  }
+  for (int m = 0; m < max_relax && !active.empty() && e == cudaSuccess; ++m) {
+    const int na = (int)active.size();
+    for (int q = 0; q < na; ++q) {
+      htab[q] = cur[active[q]];
+      htab[na + q] = nxt[active[q]];
+    }
+    e = cudaMemcpyAsync(tab, htab.data(), sizeof(double *) * 2 * na, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = launch_relax_multi(n_units, bs, row_ptr, col, val, W, (const double *const *)tab,
+                             (double *const *)(tab + na), na, s);
+    if (e == cudaSuccess) e = launch_colnorm_partials(n, (const double *const *)(tab + na), na, part, s);
+    if (e == cudaSuccess) e = launch_finalize(part, na, nr, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(nn.data(), nr, sizeof(double) * na, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) break;
+    std::vector<int> still;
+    for (int q = 0; q < na; ++q) {
+      const int c = active[q];
+      std::swap(cur[c], nxt[c]);
+      sweeps[c] = m + 1;
+      const double nnew = std::sqrt(nn[q]);
+      if (nrm[c] / nnew < 1.0 + gamma) continue;
+      nrm[c] = nnew;
+      still.push_back(c);
+    }
+    active.swap(still);
+  }
+  for (int c = 0; c < r && e == cudaSuccess; ++c)
+    if (cur[c] != B + (size_t)c * n)
+      e = cudaMemcpyAsync(B + (size_t)c * n, cur[c], sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  if (B2) cudaFreeAsync(B2, s);
+  if (part) cudaFreeAsync(part, s);
+  if (nr) cudaFreeAsync(nr, s);
+  if (tab) cudaFreeAsync(tab, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  return op_status(e != cudaSuccess ? e : e2);
+}
+
+gasa_status gasa_tentative(int32_t n_units, int32_t bs, int32_t n_agg, const int32_t *agg_of,
+                           const double *B, int32_t r, int32_t s_next, double *T_out,
+                           double *sigma_out, void *stream) {
+  if (n_units <= 0 || bs <= 0 || n_agg <= 0 || n_agg > n_units || r <= 0 || r > 256 ||
+      s_next <= 0 || s_next > r || !agg_of || !B || !T_out)
+    return GASA_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int *cp = nullptr, *ci = nullptr, *scr = nullptr, *st = nullptr, *mx = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&cp, sizeof(int) * (n_agg + 1), s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&ci, sizeof(int) * n_units, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&scr, sizeof(int) * (n_agg + 1), s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&st, sizeof(int) * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(int) * 2, s);
+  if (e == cudaSuccess) e = build_children(n_units, n_agg, agg_of, cp, ci, scr, s);
+  // largest aggregate (children per aggregate = cp[J+1] - cp[J])
+  int maxc = 0;
+  if (e == cudaSuccess) {
+    std::vector<int> hcp(n_agg + 1);
+    e = cudaMemcpyAsync(hcp.data(), cp, sizeof(int) * (n_agg + 1), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int J = 0; J < n_agg && e == cudaSuccess; ++J) {
+      const int c = hcp[J + 1] - hcp[J];
+      if (c <= 0) e = cudaErrorInvalidValue;   // every aggregate must own a unit
+      maxc = std::max(maxc, c);
+    }
+  }
+  int smem = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0);
+  if (e == cudaSuccess && (size_t)maxc * bs * r * sizeof(double) > (size_t)smem) e = cudaErrorInvalidValue;
+  if (e == cudaSuccess)
+    e = launch_tentative(bs, n_agg, maxc, cp, ci, B, (int64_t)n_units * bs, r, s_next, T_out,
+                         sigma_out, st, s);
+  int hst = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hst, st, sizeof(int), cudaMemcpyDeviceToHost, s);
+  (void)mx;
+  for (int *p : {cp, ci, scr, st})
+    if (p) cudaFreeAsync(p, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e == cudaErrorInvalidValue) return GASA_ERR_INVALID_ARG;
+  if (e != cudaSuccess || e2 != cudaSuccess) return op_status(e != cudaSuccess ? e : e2);
+  return hst ? GASA_ERR_BREAKDOWN : GASA_OK;
+}
+
+gasa_status gasa_dense_inverse(int32_t n, const double *A, double *Ainv, int32_t *singular,
+                               void *stream) {
+  if (n <= 0 || n > 16384 || !A || !Ainv || !singular) return GASA_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  double *work = nullptr;
+  int *d = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&work, sizeof(double) * (2 * (size_t)n * n + n), s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&d, sizeof(int), s);
+  if (e == cudaSuccess) e = launch_dense_inverse(n, A, Ainv, work, d, s);
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (work) cudaFreeAsync(work, s);
+  if (d) cudaFreeAsync(d, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  *singular = h;
+  return op_status(e != cudaSuccess ? e : e2);
+}
+
+}  // extern "C"

@@ -1,0 +1,120 @@
+// Host-side launchers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gasa {
+
+enum JacobiMode { JAC_SWEEP = 0, JAC_FIRST = 1, JAC_APPLY = 2, JAC_RELAX = 3 };
+
+// ---- kernels_mv.cu ---------------------------------------------------------
+template <typename T>
+cudaError_t launch_bsr_mv(int mode, int n_brows, int br, int bc, const int *rp, const int *col,
+                          const T *val, const T *x, const T *b, T *y, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_jacobi(int mode, int n_units, int bs, const int *rp, const int *col,
+                          const T *val, const T *W, const T *x, const T *b, T *xo,
+                          cudaStream_t s);
+
+// multi-column relaxation x_c <- x_c - W A x_c for `nc` columns given by
+// device tables of column base pointers (each column n_units*bs long).
+cudaError_t launch_relax_multi(int n_units, int bs, const int *rp, const int *col,
+                               const double *val, const double *W, const double *const *xin,
+                               double *const *xout, int nc, cudaStream_t s);
+
+// Y(:, c) = R * X(:, c) for r columns (column-major, leading dims ldx / ldy)
+cudaError_t launch_bsr_mm(int n_brows, int br, int bc, const int *rp, const int *col,
+                          const double *val, const double *X, int64_t ldx, double *Y,
+                          int64_t ldy, int ncols, cudaStream_t s);
+
+// y = A x for a dense row-major n x n matrix
+template <typename T>
+cudaError_t launch_dense_mv(int n, const double *A, const T *x, T *y, cudaStream_t s);
+
+// ---- kernels_red.cu --------------------------------------------------------
+// partials[kRedBlocks] of sum_i x_i y_i (y == nullptr: sum x_i^2)
+cudaError_t launch_dot_partials(int64_t n, const double *x, const double *y, double *partials,
+                                cudaStream_t s);
+// multi-column squared norms: partials[c * kRedBlocks + blk]
+cudaError_t launch_colnorm_partials(int64_t n, const double *const *cols, int nc,
+                                    double *partials, cudaStream_t s);
+// out[c] = sum of partials of column c (one block per column)
+cudaError_t launch_finalize(const double *partials, int nc, double *out, cudaStream_t s);
+cudaError_t launch_scale_by_inv_sqrt(int64_t n, double *x, const double *sumsq, cudaStream_t s);
+cudaError_t launch_uniform_pm1(int64_t n, uint64_t seed, uint64_t stream, double *x,
+                               cudaStream_t s);
+cudaError_t launch_normal(int64_t n, uint64_t seed, uint64_t stream, double *x, cudaStream_t s);
+template <typename Tin, typename Tout>
+cudaError_t launch_convert(int64_t n, const Tin *in, Tout *out, cudaStream_t s);
+cudaError_t launch_fill(int64_t n, double v, double *x, cudaStream_t s);
+
+// CG pieces (device scalars; partial arrays of kRedBlocks entries)
+cudaError_t launch_cg_update_xr(int64_t n, double *x, double *r, const double *p,
+                                const double *q, const double *rz, const double *pq_partials,
+                                double *rr_partials, double *alpha_out, cudaStream_t s);
+cudaError_t launch_cg_update_p(int64_t n, double *p, const double *z, const double *rz_old,
+                               const double *rz_partials, const double *rzold_partials,
+                               double *rz_out, int flexible, cudaStream_t s);
+cudaError_t launch_axpy(int64_t n, double a, const double *x, double *y, cudaStream_t s);
+cudaError_t launch_copy(int64_t n, const double *x, double *y, cudaStream_t s);
+cudaError_t launch_sub(int64_t n, const double *a, const double *b, double *out, cudaStream_t s);
+
+// GMRES pieces
+cudaError_t launch_multi_dot(int64_t n, const double *V, int64_t ldv, int k, const double *w,
+                             double *partials, cudaStream_t s);
+cudaError_t launch_multi_dot_finalize(const double *partials, int k, double *h,
+                                      double *hacc, cudaStream_t s);
+cudaError_t launch_gs_update(int64_t n, const double *V, int64_t ldv, int k, const double *h,
+                             double *w, cudaStream_t s);
+cudaError_t launch_normalize_into(int64_t n, const double *w, const double *sumsq, double *v,
+                                  double *hout, cudaStream_t s);
+cudaError_t launch_gmres_givens(double *H, int ldh, int j, double *cs, double *sn, double *g,
+                                cudaStream_t s);
+cudaError_t launch_gmres_backsolve(const double *H, int ldh, int j, const double *g, double *y,
+                                   cudaStream_t s);
+cudaError_t launch_combine(int64_t n, const double *V, int64_t ldv, int k, const double *y,
+                           double *x, cudaStream_t s);
+
+// ---- kernels_setup.cu ------------------------------------------------------
+cudaError_t launch_block_inverse(int n_units, int bs, const int *rp, const int *col,
+                                 const double *val, double scale, double *W, int *n_singular,
+                                 cudaStream_t s);
+cudaError_t launch_scale(int64_t n, double a, double *x, cudaStream_t s);
+cudaError_t launch_tentative(int bs, int n_agg, int max_children, const int *child_ptr,
+                             const int *child_idx, const double *B, int64_t ldb, int r,
+                             int s_next, double *T, double *sigma, int *status, cudaStream_t s);
+// children lists of aggregates (counting sort of agg_of, stable by unit id)
+cudaError_t build_children(int n_units, int n_agg, const int *agg_of, int *child_ptr,
+                           int *child_idx, int *scratch, cudaStream_t s);
+
+// structural products; all produce sorted unique block-column lists
+// cand_count[i] is written for every row (candidates before de-duplication)
+cudaError_t launch_pattern_P(int n, const int *Arp, const int *Acol, const int *agg,
+                             int *count_or_null, const int *Prp_or_null, int *Pcol_or_null,
+                             int max_cand, cudaStream_t s);
+cudaError_t launch_pattern_AB(int n, const int *Arp, const int *Acol, const int *Brp,
+                              const int *Bcol, int *count_or_null, const int *Crp_or_null,
+                              int *Ccol_or_null, int max_cand, cudaStream_t s);
+cudaError_t launch_cand_count_AB(int n, const int *Arp, const int *Acol, const int *Brp,
+                                 int *cand, cudaStream_t s);
+cudaError_t launch_numeric_P(int n, int sk, int sn, const int *Arp, const int *Acol,
+                             const double *Aval, const double *W, const double *T,
+                             const int *agg, const int *Prp, const int *Pcol, double *Pval,
+                             cudaStream_t s);
+cudaError_t launch_numeric_AB(int n, int br, int bm, int bc, const int *Arp, const int *Acol,
+                              const double *Aval, const int *Brp, const int *Bcol,
+                              const double *Bval, const int *Crp, const int *Ccol,
+                              double *Cval, cudaStream_t s);
+cudaError_t launch_transpose(int n_rows, int n_cols, int br, int bc, const int *Prp,
+                             const int *Pcol, const double *Pval, int *Rrp, int *Rcol,
+                             double *Rval, int *scratch_pos, int *scratch_cnt, cudaStream_t s);
+cudaError_t launch_bsr_to_dense(int n, int bs, const int *rp, const int *col, const double *val,
+                                double *D, cudaStream_t s);
+cudaError_t launch_dense_inverse(int n, const double *A, double *Ainv, double *work,
+                                 int *singular, cudaStream_t s);
+cudaError_t launch_max_int(int n, const int *x, int *out, cudaStream_t s);
+cudaError_t launch_exclusive_scan(int n, const int *in, int *out, int *scratch, cudaStream_t s);
+
+}  // namespace gasa

@@ -1,0 +1,360 @@
+// Block-sparse products on the V-cycle hot path (Alg. 1, Alg. 2).
+//
+// Layout: BSR, one dense br x bc block per stored pair, blocks row-major and
+// contiguous in block-row order.  One thread owns one scalar row (block row
+// i, row r of the block): it streams row r of every block of block row i
+// (bc contiguous values, loaded with the widest aligned vector) and gathers
+// the matching bc entries of x, which stay L2-resident.  The threads of one
+// block row read one contiguous br*bc span per block, so a warp's requests
+// cover whole 32-byte sectors and every matrix byte crosses HBM once per
+// pass.  The block-Jacobi step additionally exchanges the block row's
+// residual through shared memory and applies the precomputed w D^{-1}.
+#include "common.cuh"
+#include "internal.h"
+
+namespace gasa {
+
+// ----------------------------------------------------------------------------
+// y = A x | y = b - A x | y += A x
+// ----------------------------------------------------------------------------
+template <typename T, int BC, int MODE>
+__global__ void __launch_bounds__(256)
+bsr_mv_kernel(int n_brows, int br, const int *__restrict__ rp, const int *__restrict__ col,
+              const T *__restrict__ val, const T *__restrict__ x, const T *__restrict__ b,
+              T *__restrict__ y) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n_brows * br) return;
+  const int i = (int)(t / br);
+  const int r = (int)(t - (long long)i * br);
+  constexpr int W = RowVec<T, BC>::value;
+  const int beg = __ldg(rp + i), end = __ldg(rp + i + 1);
+  T acc = T(0);
+  for (int k = beg; k < end; ++k) {
+    const int j = __ldg(col + k);
+    const T *a = val + ((size_t)k * br + r) * BC;
+    const T *xj = x + (size_t)j * BC;
+    T av[BC], xv[BC];
+#pragma unroll
+    for (int c = 0; c < BC; c += W) load_vec_stream<T, W>(a + c, av + c);
+#pragma unroll
+    for (int c = 0; c < BC; c += W) load_vec<T, W>(xj + c, xv + c);
+#pragma unroll
+    for (int c = 0; c < BC; ++c) acc = fma(av[c], xv[c], acc);
+  }
+  if (MODE == GASA_MV_ASSIGN) y[t] = acc;
+  else if (MODE == GASA_MV_RESIDUAL) y[t] = b[t] - acc;
+  else y[t] += acc;
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256)
+bsr_mv_generic(int n_brows, int br, int bc, const int *__restrict__ rp,
+               const int *__restrict__ col, const T *__restrict__ val, const T *__restrict__ x,
+               const T *__restrict__ b, T *__restrict__ y) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n_brows * br) return;
+  const int i = (int)(t / br);
+  const int r = (int)(t - (long long)i * br);
+  const int beg = __ldg(rp + i), end = __ldg(rp + i + 1);
+  T acc = T(0);
+  for (int k = beg; k < end; ++k) {
+    const int j = __ldg(col + k);
+    const T *a = val + ((size_t)k * br + r) * bc;
+    const T *xj = x + (size_t)j * bc;
+    for (int c = 0; c < bc; ++c) acc = fma(__ldg(a + c), __ldg(xj + c), acc);
+  }
+  if (MODE == GASA_MV_ASSIGN) y[t] = acc;
+  else if (MODE == GASA_MV_RESIDUAL) y[t] = b[t] - acc;
+  else y[t] += acc;
+}
+
+static inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+template <typename T, int MODE>
+static cudaError_t mv_dispatch(int n_brows, int br, int bc, const int *rp, const int *col,
+                               const T *val, const T *x, const T *b, T *y, cudaStream_t s) {
+  const long long rows = (long long)n_brows * br;
+  if (rows == 0) return cudaSuccess;
+  const int th = 256;
+  const int grid = div_up(rows, th);
+  const bool al = aligned16(val) && aligned16(x);
+#define GASA_MV_CASE(BC)                                                                   \
+  case BC:                                                                                 \
+    bsr_mv_kernel<T, BC, MODE><<<grid, th, 0, s>>>(n_brows, br, rp, col, val, x, b, y);    \
+    return cudaGetLastError();
+  if (al) {
+    switch (bc) {
+      GASA_MV_CASE(1) GASA_MV_CASE(2) GASA_MV_CASE(3) GASA_MV_CASE(4) GASA_MV_CASE(5)
+      GASA_MV_CASE(6) GASA_MV_CASE(7) GASA_MV_CASE(8) GASA_MV_CASE(9) GASA_MV_CASE(10)
+      GASA_MV_CASE(11) GASA_MV_CASE(12) GASA_MV_CASE(13) GASA_MV_CASE(14) GASA_MV_CASE(15)
+      GASA_MV_CASE(16)
+      default: break;
+    }
+  }
+#undef GASA_MV_CASE
+  bsr_mv_generic<T, MODE><<<grid, th, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_bsr_mv(int mode, int n_brows, int br, int bc, const int *rp, const int *col,
+                          const T *val, const T *x, const T *b, T *y, cudaStream_t s) {
+  switch (mode) {
+    case GASA_MV_ASSIGN:
+      return mv_dispatch<T, GASA_MV_ASSIGN>(n_brows, br, bc, rp, col, val, x, b, y, s);
+    case GASA_MV_RESIDUAL:
+      return mv_dispatch<T, GASA_MV_RESIDUAL>(n_brows, br, bc, rp, col, val, x, b, y, s);
+    default:
+      return mv_dispatch<T, GASA_MV_ADD>(n_brows, br, bc, rp, col, val, x, b, y, s);
+  }
+}
+template cudaError_t launch_bsr_mv<double>(int, int, int, int, const int *, const int *,
+                                           const double *, const double *, const double *,
+                                           double *, cudaStream_t);
+template cudaError_t launch_bsr_mv<float>(int, int, int, int, const int *, const int *,
+                                          const float *, const float *, const float *, float *,
+                                          cudaStream_t);
+
+// ----------------------------------------------------------------------------
+// block Jacobi step (Alg. 1 with A~^{-1} = w D^{-1}):
+//   SWEEP: xo = x + W (b - A x)   FIRST: xo = W b
+//   APPLY: xo = W (A x)           RELAX: xo = x - W A x
+// A CTA owns whole block rows; thread (li, r) computes the residual entry,
+// the block row's residual meets in shared memory, then thread (li, r)
+// applies row r of W_i.
+// ----------------------------------------------------------------------------
+template <typename T, int BS, int MODE>
+__global__ void __launch_bounds__(256)
+jacobi_kernel(int n_units, const int *__restrict__ rp, const int *__restrict__ col,
+              const T *__restrict__ val, const T *__restrict__ Wm, const T *__restrict__ x,
+              const T *__restrict__ b, T *__restrict__ xo) {
+  __shared__ T res[256];
+  constexpr int RPB = 256 / BS;
+  constexpr int W = RowVec<T, BS>::value;
+  const int li = threadIdx.x / BS;
+  const int r = threadIdx.x - li * BS;
+  const int i = blockIdx.x * RPB + li;
+  const bool active = (li < RPB) && (i < n_units);
+  const size_t row = (size_t)i * BS + r;
+  T v = T(0);
+  if (active) {
+    if (MODE == JAC_FIRST) {
+      v = b[row];
+    } else {
+      const int beg = __ldg(rp + i), end = __ldg(rp + i + 1);
+      T acc = T(0);
+      for (int k = beg; k < end; ++k) {
+        const int j = __ldg(col + k);
+        const T *a = val + ((size_t)k * BS + r) * BS;
+        const T *xj = x + (size_t)j * BS;
+        T av[BS], xv[BS];
+#pragma unroll
+        for (int c = 0; c < BS; c += W) load_vec_stream<T, W>(a + c, av + c);
+#pragma unroll
+        for (int c = 0; c < BS; c += W) load_vec<T, W>(xj + c, xv + c);
+#pragma unroll
+        for (int c = 0; c < BS; ++c) acc = fma(av[c], xv[c], acc);
+      }
+      if (MODE == JAC_SWEEP) v = b[row] - acc;
+      else if (MODE == JAC_RELAX) v = -acc;
+      else v = acc;
+    }
+  }
+  res[threadIdx.x] = v;
+  __syncthreads();
+  if (!active) return;
+  const T *w = Wm + row * BS;
+  T wv[BS];
+#pragma unroll
+  for (int c = 0; c < BS; c += W) load_vec_stream<T, W>(w + c, wv + c);
+  T out = T(0);
+#pragma unroll
+  for (int c = 0; c < BS; ++c) out = fma(wv[c], res[li * BS + c], out);
+  if (MODE == JAC_SWEEP || MODE == JAC_RELAX) out += x[row];
+  xo[row] = out;
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256)
+jacobi_generic(int n_units, int bs, const int *__restrict__ rp, const int *__restrict__ col,
+               const T *__restrict__ val, const T *__restrict__ Wm, const T *__restrict__ x,
+               const T *__restrict__ b, T *__restrict__ xo) {
+  extern __shared__ unsigned char smem_raw[];
+  T *res = reinterpret_cast<T *>(smem_raw);
+  const int rpb = blockDim.x / bs;
+  const int li = threadIdx.x / bs;
+  const int r = threadIdx.x - li * bs;
+  const int i = blockIdx.x * rpb + li;
+  const bool active = (li < rpb) && (i < n_units);
+  const size_t row = (size_t)i * bs + r;
+  T v = T(0);
+  if (active) {
+    if (MODE == JAC_FIRST) {
+      v = b[row];
+    } else {
+      const int beg = __ldg(rp + i), end = __ldg(rp + i + 1);
+      T acc = T(0);
+      for (int k = beg; k < end; ++k) {
+        const int j = __ldg(col + k);
+        const T *a = val + ((size_t)k * bs + r) * bs;
+        const T *xj = x + (size_t)j * bs;
+        for (int c = 0; c < bs; ++c) acc = fma(__ldg(a + c), __ldg(xj + c), acc);
+      }
+      if (MODE == JAC_SWEEP) v = b[row] - acc;
+      else if (MODE == JAC_RELAX) v = -acc;
+      else v = acc;
+    }
+  }
+  res[threadIdx.x] = v;
+  __syncthreads();
+  if (!active) return;
+  const T *w = Wm + row * bs;
+  T out = T(0);
+  for (int c = 0; c < bs; ++c) out = fma(__ldg(w + c), res[li * bs + c], out);
+  if (MODE == JAC_SWEEP || MODE == JAC_RELAX) out += x[row];
+  xo[row] = out;
+}
+
+template <typename T, int MODE>
+static cudaError_t jac_dispatch(int n_units, int bs, const int *rp, const int *col,
+                                const T *val, const T *W, const T *x, const T *b, T *xo,
+                                cudaStream_t s) {
+  if (n_units == 0) return cudaSuccess;
+  const bool al = aligned16(val) && aligned16(W) && (MODE == JAC_FIRST || aligned16(x));
+#define GASA_JAC_CASE(BS)                                                                   \
+  case BS: {                                                                                \
+    constexpr int rpb = 256 / BS;                                                           \
+    jacobi_kernel<T, BS, MODE><<<div_up(n_units, rpb), 256, 0, s>>>(n_units, rp, col, val,  \
+                                                                    W, x, b, xo);           \
+    return cudaGetLastError();                                                              \
+  }
+  if (al && bs <= 16) {
+    switch (bs) {
+      GASA_JAC_CASE(1) GASA_JAC_CASE(2) GASA_JAC_CASE(3) GASA_JAC_CASE(4) GASA_JAC_CASE(5)
+      GASA_JAC_CASE(6) GASA_JAC_CASE(7) GASA_JAC_CASE(8) GASA_JAC_CASE(9) GASA_JAC_CASE(10)
+      GASA_JAC_CASE(11) GASA_JAC_CASE(12) GASA_JAC_CASE(13) GASA_JAC_CASE(14)
+      GASA_JAC_CASE(15) GASA_JAC_CASE(16)
+      default: break;
+    }
+  }
+#undef GASA_JAC_CASE
+  // generic path: one or more whole block rows per CTA
+  int rpb = 256 / bs;
+  if (rpb < 1) rpb = 1;
+  const int th = rpb * bs;
+  if (th > 1024) return cudaErrorInvalidValue;
+  jacobi_generic<T, MODE><<<div_up(n_units, rpb), th, th * sizeof(T), s>>>(n_units, bs, rp, col,
+                                                                           val, W, x, b, xo);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_jacobi(int mode, int n_units, int bs, const int *rp, const int *col,
+                          const T *val, const T *W, const T *x, const T *b, T *xo,
+                          cudaStream_t s) {
+  switch (mode) {
+    case JAC_SWEEP: return jac_dispatch<T, JAC_SWEEP>(n_units, bs, rp, col, val, W, x, b, xo, s);
+    case JAC_FIRST: return jac_dispatch<T, JAC_FIRST>(n_units, bs, rp, col, val, W, x, b, xo, s);
+    case JAC_APPLY: return jac_dispatch<T, JAC_APPLY>(n_units, bs, rp, col, val, W, x, b, xo, s);
+    default: return jac_dispatch<T, JAC_RELAX>(n_units, bs, rp, col, val, W, x, b, xo, s);
+  }
+}
+template cudaError_t launch_jacobi<double>(int, int, int, const int *, const int *,
+                                           const double *, const double *, const double *,
+                                           const double *, double *, cudaStream_t);
+template cudaError_t launch_jacobi<float>(int, int, int, const int *, const int *,
+                                          const float *, const float *, const float *,
+                                          const float *, float *, cudaStream_t);
+
+// ----------------------------------------------------------------------------
+// multi-column relaxation x_c <- x_c - W A x_c (Eq. bsmooth), column per
+// blockIdx.y, columns given by device pointer tables
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+relax_multi_kernel(int n_units, int bs, const int *__restrict__ rp, const int *__restrict__ col,
+                   const double *__restrict__ val, const double *__restrict__ Wm,
+                   const double *const *__restrict__ xin, double *const *__restrict__ xout) {
+  extern __shared__ double res_m[];
+  const double *x = xin[blockIdx.y];
+  double *xo = xout[blockIdx.y];
+  const int rpb = blockDim.x / bs;
+  const int li = threadIdx.x / bs;
+  const int r = threadIdx.x - li * bs;
+  const int i = blockIdx.x * rpb + li;
+  const bool active = (li < rpb) && (i < n_units);
+  const size_t row = (size_t)i * bs + r;
+  double v = 0.0;
+  if (active) {
+    const int beg = __ldg(rp + i), end = __ldg(rp + i + 1);
+    double acc = 0.0;
+    for (int k = beg; k < end; ++k) {
+      const int j = __ldg(col + k);
+      const double *a = val + ((size_t)k * bs + r) * bs;
+      const double *xj = x + (size_t)j * bs;
+      for (int c = 0; c < bs; ++c) acc = fma(__ldg(a + c), xj[c], acc);
+    }
+    v = -acc;
+  }
+  res_m[threadIdx.x] = v;
+  __syncthreads();
+  if (!active) return;
+  const double *w = Wm + row * bs;
+  double out = 0.0;
+  for (int c = 0; c < bs; ++c) out = fma(__ldg(w + c), res_m[li * bs + c], out);
+  xo[row] = x[row] + out;
+}
+
+cudaError_t launch_relax_multi(int n_units, int bs, const int *rp, const int *col,
+                               const double *val, const double *W, const double *const *xin,
+                               double *const *xout, int nc, cudaStream_t s) {
+  if (n_units == 0 || nc == 0) return cudaSuccess;
+  int rpb = 256 / bs;
+  if (rpb < 1) rpb = 1;
+  const int th = rpb * bs;
+  if (th > 1024) return cudaErrorInvalidValue;
+  dim3 grid(div_up(n_units, rpb), nc);
+  relax_multi_kernel<<<grid, th, th * sizeof(double), s>>>(n_units, bs, rp, col, val, W, xin,
+                                                           xout);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bsr_mm(int n_brows, int br, int bc, const int *rp, const int *col,
+                          const double *val, const double *X, int64_t ldx, double *Y,
+                          int64_t ldy, int ncols, cudaStream_t s) {
+  for (int c = 0; c < ncols; ++c) {
+    cudaError_t e = launch_bsr_mv<double>(GASA_MV_ASSIGN, n_brows, br, bc, rp, col, val,
+                                          X + (size_t)c * ldx, nullptr, Y + (size_t)c * ldy, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// ----------------------------------------------------------------------------
+// dense y = A x (coarsest level, A = A_N^{-1} row-major, FP64 arithmetic)
+// ----------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+dense_mv_kernel(int n, const double *__restrict__ A, const T *__restrict__ x,
+                T *__restrict__ y) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double *a = A + (size_t)warp * n;
+  double acc = 0.0;
+  for (int j = lane; j < n; j += 32) acc = fma(a[j], (double)x[j], acc);
+  acc = warp_sum(acc);
+  if (lane == 0) y[warp] = (T)acc;
+}
+
+template <typename T>
+cudaError_t launch_dense_mv(int n, const double *A, const T *x, T *y, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  dense_mv_kernel<T><<<div_up((long long)n * 32, 256), 256, 0, s>>>(n, A, x, y);
+  return cudaGetLastError();
+}
+template cudaError_t launch_dense_mv<double>(int, const double *, const double *, double *,
+                                             cudaStream_t);
+template cudaError_t launch_dense_mv<float>(int, const double *, const float *, float *,
+                                            cudaStream_t);
+
+}  // namespace gasa

@@ -1,0 +1,387 @@
+// Vector kernels of the outer Krylov loop and of setup: deterministic
+// reductions (fixed grid, fixed order: partial sums per CTA, then one CTA
+// sums the partials), fused CG updates, GMRES Arnoldi pieces, counter-based
+// random vectors and precision conversions.
+#include "common.cuh"
+#include "internal.h"
+
+namespace gasa {
+
+// ----------------------------------------------------------------------------
+// reductions
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(kRedThreads)
+dot_partials_kernel(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                    double *__restrict__ partials) {
+  __shared__ double sh[32];
+  double v = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+      v = fma(x[i], y[i], v);
+  } else {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+      v = fma(x[i], x[i], v);
+  }
+  v = block_sum(v, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = v;
+}
+
+cudaError_t launch_dot_partials(int64_t n, const double *x, const double *y, double *partials,
+                                cudaStream_t s) {
+  dot_partials_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, y, partials);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+colnorm_partials_kernel(int64_t n, const double *const *__restrict__ cols,
+                        double *__restrict__ partials) {
+  __shared__ double sh[32];
+  const double *x = cols[blockIdx.y];
+  double v = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    v = fma(x[i], x[i], v);
+  v = block_sum(v, sh);
+  if (threadIdx.x == 0) partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = v;
+}
+
+cudaError_t launch_colnorm_partials(int64_t n, const double *const *cols, int nc,
+                                    double *partials, cudaStream_t s) {
+  if (nc == 0) return cudaSuccess;
+  colnorm_partials_kernel<<<dim3(kRedBlocks, nc), kRedThreads, 0, s>>>(n, cols, partials);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+finalize_kernel(const double *__restrict__ partials, double *__restrict__ out) {
+  __shared__ double sh[32];
+  double v = block_sum_partials(partials + (size_t)blockIdx.x * kRedBlocks, kRedBlocks, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = v;
+}
+
+cudaError_t launch_finalize(const double *partials, int nc, double *out, cudaStream_t s) {
+  if (nc == 0) return cudaSuccess;
+  finalize_kernel<<<nc, kRedThreads, 0, s>>>(partials, out);
+  return cudaGetLastError();
+}
+
+__global__ void scale_inv_sqrt_kernel(int64_t n, double *x, const double *sumsq) {
+  const double a = 1.0 / sqrt(sumsq[0]);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) x[i] *= a;
+}
+
+cudaError_t launch_scale_by_inv_sqrt(int64_t n, double *x, const double *sumsq, cudaStream_t s) {
+  scale_inv_sqrt_kernel<<<kRedBlocks, 256, 0, s>>>(n, x, sumsq);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// splitmix64 (Steele, Lea & Flood 2014): draw i of (seed, stream) is
+// mix(key + (i+1) * GOLDEN), key = seed ^ (stream * GOLDEN); uniform =
+// (z >> 11) * 2^-53.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t splitmix_draw(uint64_t key, uint64_t i) {
+  uint64_t z = key + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ double splitmix_uniform(uint64_t key, uint64_t i) {
+  return (double)(splitmix_draw(key, i) >> 11) * 0x1.0p-53;
+}
+
+__global__ void uniform_pm1_kernel(int64_t n, uint64_t key, double *x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    x[i] = 2.0 * splitmix_uniform(key, (uint64_t)i) - 1.0;
+}
+
+cudaError_t launch_uniform_pm1(int64_t n, uint64_t seed, uint64_t stream, double *x,
+                               cudaStream_t s) {
+  const uint64_t key = seed ^ (stream * 0x9E3779B97F4A7C15ull);
+  uniform_pm1_kernel<<<kRedBlocks, 256, 0, s>>>(n, key, x);
+  return cudaGetLastError();
+}
+
+// Box-Muller over pairs of uniforms: u1 = 1 - U[2m], u2 = U[2m+1]
+__global__ void normal_kernel(int64_t n, uint64_t key, double *x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int64_t m = i >> 1;
+    const double u1 = 1.0 - splitmix_uniform(key, (uint64_t)(2 * m));
+    const double u2 = splitmix_uniform(key, (uint64_t)(2 * m + 1));
+    const double rr = sqrt(-2.0 * log(u1));
+    double sv, cv;
+    sincospi(2.0 * u2, &sv, &cv);
+    x[i] = (i & 1) ? rr * sv : rr * cv;
+  }
+}
+
+cudaError_t launch_normal(int64_t n, uint64_t seed, uint64_t stream, double *x, cudaStream_t s) {
+  const uint64_t key = seed ^ (stream * 0x9E3779B97F4A7C15ull);
+  normal_kernel<<<kRedBlocks, 256, 0, s>>>(n, key, x);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// elementwise
+// ----------------------------------------------------------------------------
+template <typename Tin, typename Tout>
+__global__ void convert_kernel(int64_t n, const Tin *__restrict__ in, Tout *__restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    out[i] = (Tout)in[i];
+}
+
+template <typename Tin, typename Tout>
+cudaError_t launch_convert(int64_t n, const Tin *in, Tout *out, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int grid = div_up(n, 256);
+  if (grid > 8 * kNumSM) grid = 8 * kNumSM;
+  convert_kernel<Tin, Tout><<<grid, 256, 0, s>>>(n, in, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_convert<double, float>(int64_t, const double *, float *, cudaStream_t);
+template cudaError_t launch_convert<float, double>(int64_t, const float *, double *, cudaStream_t);
+
+__global__ void fill_kernel(int64_t n, double v, double *x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) x[i] = v;
+}
+cudaError_t launch_fill(int64_t n, double v, double *x, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  fill_kernel<<<kRedBlocks, 256, 0, s>>>(n, v, x);
+  return cudaGetLastError();
+}
+
+__global__ void axpy_kernel(int64_t n, double a, const double *__restrict__ x,
+                            double *__restrict__ y) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    y[i] = fma(a, x[i], y[i]);
+}
+cudaError_t launch_axpy(int64_t n, double a, const double *x, double *y, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  axpy_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, a, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy(int64_t n, const double *x, double *y, cudaStream_t s) {
+  return cudaMemcpyAsync(y, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+}
+
+__global__ void sub_kernel(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
+                           double *__restrict__ o) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    o[i] = a[i] - b[i];
+}
+cudaError_t launch_sub(int64_t n, const double *a, const double *b, double *out, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  sub_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, a, b, out);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// CG: x += alpha p, r -= alpha q with alpha = rz / (p.q); partial ||r||^2
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(kRedThreads)
+cg_update_xr_kernel(int64_t n, double *__restrict__ x, double *__restrict__ r,
+                    const double *__restrict__ p, const double *__restrict__ q,
+                    const double *__restrict__ rz, const double *__restrict__ pq_partials,
+                    double *__restrict__ rr_partials, double *__restrict__ alpha_out) {
+  __shared__ double sh[32];
+  const double pq = block_sum_partials(pq_partials, kRedBlocks, sh);
+  const double alpha = rz[0] / pq;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    alpha_out[0] = alpha;
+    alpha_out[1] = pq;
+  }
+  double v = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    v = fma(ri, ri, v);
+  }
+  v = block_sum(v, sh);
+  if (threadIdx.x == 0) rr_partials[blockIdx.x] = v;
+}
+
+cudaError_t launch_cg_update_xr(int64_t n, double *x, double *r, const double *p,
+                                const double *q, const double *rz, const double *pq_partials,
+                                double *rr_partials, double *alpha_out, cudaStream_t s) {
+  cg_update_xr_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, r, p, q, rz, pq_partials,
+                                                         rr_partials, alpha_out);
+  return cudaGetLastError();
+}
+
+// p = z + beta p, beta = rz_new / rz_old (flexible: (rz_new - r.z_old) / rz_old)
+__global__ void __launch_bounds__(kRedThreads)
+cg_update_p_kernel(int64_t n, double *__restrict__ p, const double *__restrict__ z,
+                   const double *__restrict__ rz_old, const double *__restrict__ rz_partials,
+                   const double *__restrict__ rzold_partials, double *__restrict__ rz_out,
+                   int flexible) {
+  __shared__ double sh[32];
+  const double rz_new = block_sum_partials(rz_partials, kRedBlocks, sh);
+  double num = rz_new;
+  if (flexible) num -= block_sum_partials(rzold_partials, kRedBlocks, sh);
+  const double beta = num / rz_old[0];
+  if (blockIdx.x == 0 && threadIdx.x == 0) rz_out[0] = rz_new;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    p[i] = fma(beta, p[i], z[i]);
+}
+
+cudaError_t launch_cg_update_p(int64_t n, double *p, const double *z, const double *rz_old,
+                               const double *rz_partials, const double *rzold_partials,
+                               double *rz_out, int flexible, cudaStream_t s) {
+  cg_update_p_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, p, z, rz_old, rz_partials,
+                                                        rzold_partials, rz_out, flexible);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// GMRES (classical Gram-Schmidt applied twice; basis V column-major)
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(kRedThreads)
+multi_dot_kernel(int64_t n, const double *__restrict__ V, int64_t ldv,
+                 const double *__restrict__ w, double *__restrict__ partials) {
+  __shared__ double sh[32];
+  const double *v = V + (size_t)blockIdx.y * ldv;
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    acc = fma(v[i], w[i], acc);
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[(size_t)blockIdx.y * kRedBlocks + blockIdx.x] = acc;
+}
+
+cudaError_t launch_multi_dot(int64_t n, const double *V, int64_t ldv, int k, const double *w,
+                             double *partials, cudaStream_t s) {
+  if (k == 0) return cudaSuccess;
+  multi_dot_kernel<<<dim3(kRedBlocks, k), kRedThreads, 0, s>>>(n, V, ldv, w, partials);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+multi_dot_finalize_kernel(const double *__restrict__ partials, double *__restrict__ h,
+                          double *__restrict__ hacc) {
+  __shared__ double sh[32];
+  const double v = block_sum_partials(partials + (size_t)blockIdx.x * kRedBlocks, kRedBlocks, sh);
+  if (threadIdx.x == 0) {
+    h[blockIdx.x] = v;
+    if (hacc) hacc[blockIdx.x] += v;
+  }
+}
+
+cudaError_t launch_multi_dot_finalize(const double *partials, int k, double *h, double *hacc,
+                                      cudaStream_t s) {
+  if (k == 0) return cudaSuccess;
+  multi_dot_finalize_kernel<<<k, kRedThreads, 0, s>>>(partials, h, hacc);
+  return cudaGetLastError();
+}
+
+__global__ void gs_update_kernel(int64_t n, const double *__restrict__ V, int64_t ldv, int k,
+                                 const double *__restrict__ h, double *__restrict__ w) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double acc = w[i];
+    for (int c = 0; c < k; ++c) acc = fma(-h[c], V[(size_t)c * ldv + i], acc);
+    w[i] = acc;
+  }
+}
+
+cudaError_t launch_gs_update(int64_t n, const double *V, int64_t ldv, int k, const double *h,
+                             double *w, cudaStream_t s) {
+  if (k == 0 || n == 0) return cudaSuccess;
+  gs_update_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, V, ldv, k, h, w);
+  return cudaGetLastError();
+}
+
+__global__ void normalize_into_kernel(int64_t n, const double *__restrict__ w,
+                                      const double *__restrict__ sumsq, double *__restrict__ v,
+                                      double *__restrict__ hout) {
+  const double nr = sqrt(sumsq[0]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) hout[0] = nr;
+  const double a = nr > 0.0 ? 1.0 / nr : 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    v[i] = w[i] * a;
+}
+
+cudaError_t launch_normalize_into(int64_t n, const double *w, const double *sumsq, double *v,
+                                  double *hout, cudaStream_t s) {
+  normalize_into_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, w, sumsq, v, hout);
+  return cudaGetLastError();
+}
+
+// H column-major with leading dimension ldh (= restart + 1); column j complete
+// in rows 0..j+1.  Applies rotations 0..j-1, forms rotation j, updates g.
+__global__ void gmres_givens_kernel(double *H, int ldh, int j, double *cs, double *sn,
+                                    double *g) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double *h = H + (size_t)j * ldh;
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+    h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+    h[i] = t;
+  }
+  const double a = h[j], b = h[j + 1];
+  double c = 1.0, s = 0.0;
+  if (b != 0.0) {
+    const double hh = hypot(a, b);
+    c = a / hh;
+    s = b / hh;
+  }
+  cs[j] = c;
+  sn[j] = s;
+  h[j] = c * a + s * b;
+  h[j + 1] = 0.0;
+  g[j + 1] = -s * g[j];
+  g[j] = c * g[j];
+}
+
+cudaError_t launch_gmres_givens(double *H, int ldh, int j, double *cs, double *sn, double *g,
+                                cudaStream_t s) {
+  gmres_givens_kernel<<<1, 32, 0, s>>>(H, ldh, j, cs, sn, g);
+  return cudaGetLastError();
+}
+
+__global__ void gmres_backsolve_kernel(const double *H, int ldh, int j, const double *g,
+                                       double *y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = j - 1; i >= 0; --i) {
+    double acc = g[i];
+    for (int c = i + 1; c < j; ++c) acc -= H[(size_t)c * ldh + i] * y[c];
+    y[i] = acc / H[(size_t)i * ldh + i];
+  }
+}
+
+cudaError_t launch_gmres_backsolve(const double *H, int ldh, int j, const double *g, double *y,
+                                   cudaStream_t s) {
+  gmres_backsolve_kernel<<<1, 32, 0, s>>>(H, ldh, j, g, y);
+  return cudaGetLastError();
+}
+
+__global__ void combine_kernel(int64_t n, const double *__restrict__ V, int64_t ldv, int k,
+                               const double *__restrict__ y, double *__restrict__ x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double acc = x[i];
+    for (int c = 0; c < k; ++c) acc = fma(y[c], V[(size_t)c * ldv + i], acc);
+    x[i] = acc;
+  }
+}
+
+cudaError_t launch_combine(int64_t n, const double *V, int64_t ldv, int k, const double *y,
+                           double *x, cudaStream_t s) {
+  if (k == 0 || n == 0) return cudaSuccess;
+  combine_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, V, ldv, k, y, x);
+  return cudaGetLastError();
+}
+
+}  // namespace gasa

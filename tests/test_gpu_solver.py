@@ -1,0 +1,154 @@
+"""End-to-end parity of the CUDA path (setup of Alg. 5, V-cycle of Alg. 2,
+CG / GMRES) with the CPU oracle on the same seeded workloads.
+
+Bars: aggregates and sparsity patterns bit-exact; hierarchy values within
+1e-8 relative (rounding differences pass through up to 100 relaxation
+sweeps and per-aggregate SVDs on every level); iteration counts within +-1;
+FP64 solutions within 1e-10 relative of the oracle's; every true residual
+<= 1e-10.
+"""
+import numpy as np
+import pytest
+
+from oracle import gasa_oracle as O
+from tests.helpers import bsr_scipy, gpu_setup, oracle_setup, problem, rel_err, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+def _gasa():
+    from paper_2504_13373_gb300 import gasa
+    gasa.load()
+    return gasa
+
+
+def sparse_rel(G, Ref):
+    """max |G - Ref| / max |Ref| over stored entries of either matrix"""
+    D = (G - Ref).tocsr()
+    d = np.max(np.abs(D.data)) if D.nnz else 0.0
+    return d / np.max(np.abs(Ref.data))
+
+
+def _level_bsr(gasa, ctx, k, which, sh, br, bc, nrows):
+    base = {"A": gasa.GASA_LV_A_ROWPTR, "P": gasa.GASA_LV_P_ROWPTR, "R": gasa.GASA_LV_R_ROWPTR}[which]
+    nnz = {"A": sh["nnzb"], "P": sh["P_nnzb"], "R": sh["R_nnzb"]}[which]
+    rp = gasa.gasa_get_level(ctx, k, base, np.zeros(nrows + 1, np.int32))
+    col = gasa.gasa_get_level(ctx, k, base + 1, np.zeros(nnz, np.int32))
+    val = gasa.gasa_get_level(ctx, k, base + 2, np.zeros(nnz * br * bc)).reshape(nnz, br, bc)
+    return rp, col, val
+
+
+@pytest.mark.parametrize("name", ["tiny", "c1", "p3_16", "tet_p2_4"])
+def test_setup_hierarchy(name):
+    gasa = _gasa()
+    H = oracle_setup(name)
+    ctx, info = gpu_setup(name)
+    try:
+        assert info.n_levels == len(H.levels)
+        for k, L in enumerate(H.levels):
+            sh = gasa.gasa_level_shape(ctx, k)
+            sizes = np.diff(L.unit_ptr)
+            assert sh["units"] == sizes.size and np.all(sizes == sh["s"])
+            assert sh["dofs"] == L.n
+            # A_k: pattern bit-exact, values
+            rp, col, val = _level_bsr(gasa, ctx, k, "A", sh, sh["s"], sh["s"], sh["units"])
+            optr, ocol = O.pattern_csr(L.Apat)
+            np.testing.assert_array_equal(rp, optr)
+            np.testing.assert_array_equal(col, ocol)
+            Ag = bsr_scipy(rp, col, val)
+            assert sparse_rel(Ag, L.A) <= 1e-8
+            if k == len(H.levels) - 1:
+                Ci = gasa.gasa_get_level(ctx, k, gasa.GASA_LV_COARSE_INV, np.zeros(L.n * L.n)).reshape(L.n, L.n)
+                assert rel_err(Ci, np.linalg.inv(H.coarse)) <= 1e-7
+                continue
+            assert abs(info.rho[k] - L.rho) <= 1e-10 * L.rho
+            assert abs(info.omega[k] - L.omega) <= 1e-10 * L.omega
+            sw = gasa.gasa_get_level(ctx, k, gasa.GASA_LV_SWEEPS, np.zeros(sh["r"], np.int32))
+            np.testing.assert_array_equal(sw, L.sweeps)
+            W = gasa.gasa_get_level(ctx, k, gasa.GASA_LV_W, np.zeros(sh["units"] * sh["s"] ** 2))
+            assert rel_err(W, L.W.blocks.ravel()) <= 1e-8
+            # P: pattern bit-exact, values; R = P^T exactly (same numbers)
+            sn = sh["s_next"]
+            prp, pcol, pval = _level_bsr(gasa, ctx, k, "P", sh, sh["s"], sn, sh["units"])
+            optr, ocol = O.pattern_csr(L.Ppat)
+            np.testing.assert_array_equal(prp, optr)
+            np.testing.assert_array_equal(pcol, ocol)
+            n_next = H.levels[k + 1].unit_ptr.size - 1
+            Pg = bsr_scipy(prp, pcol, pval, n_next)
+            assert sparse_rel(Pg, L.P) <= 1e-8
+            rrp, rcol, rval = _level_bsr(gasa, ctx, k, "R", sh, sn, sh["s"], n_next)
+            Rg = bsr_scipy(rrp, rcol, rval, sh["units"])
+            assert (Rg - Pg.T).count_nonzero() == 0
+    finally:
+        gasa.gasa_destroy(ctx)
+
+
+@pytest.mark.parametrize("name", ["tiny", "c1", "tet_p2_4"])
+def test_vcycle(name):
+    gasa = _gasa()
+    H = oracle_setup(name)
+    pr = problem(name)
+    ctx, _ = gpu_setup(name, keep=False)
+    try:
+        M = O.make_vcycle(H)
+        want = M(pr.rhs)
+        z = to_dev(np.zeros_like(pr.rhs))
+        gasa.gasa_vcycle(ctx, to_dev(pr.rhs), z)
+        assert rel_err(to_host(z), want) <= 1e-9
+        Mf = O.make_vcycle(H, "fp32")
+        wantf = Mf(pr.rhs)
+        gasa.gasa_vcycle(ctx, to_dev(pr.rhs), z, gasa.GASA_PREC_MIXED32)
+        assert rel_err(to_host(z), want) <= 1e-4
+        assert rel_err(to_host(z), wantf) <= 1e-4
+    finally:
+        gasa.gasa_destroy(ctx)
+
+
+@pytest.mark.parametrize("name", ["tiny", "c1", "p3_16", "tet_p2_4"])
+def test_cg_solve(name):
+    gasa = _gasa()
+    H = oracle_setup(name)
+    pr = problem(name)
+    ref = O.solve(H, pr.rhs, TOL, "cg", max_iter=5000)
+    ref32 = O.solve(H, pr.rhs, TOL, "cg", precision="mixed32", max_iter=5000)
+    ctx, _ = gpu_setup(name, keep=False)
+    try:
+        x = np.zeros_like(pr.rhs)
+        info = gasa.gasa_solve(ctx, pr.rhs, x, TOL)
+        assert info.converged and info.rel_residual <= TOL
+        assert abs(info.iterations - ref.iterations) <= 1, (info.iterations, ref.iterations)
+        assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= TOL
+        xm = np.zeros_like(pr.rhs)
+        info32 = gasa.gasa_solve(ctx, pr.rhs, xm, TOL, gasa.GASA_PREC_MIXED32)
+        assert info32.converged and info32.rel_residual <= TOL
+        assert abs(info32.iterations - ref32.iterations) <= 1, (info32.iterations, ref32.iterations)
+        # device-resident buffers give the same answer
+        xd = to_dev(np.zeros_like(pr.rhs))
+        info_d = gasa.gasa_solve(ctx, to_dev(pr.rhs), xd, TOL, on_device=True)
+        assert info_d.iterations == info.iterations
+        assert np.max(np.abs(to_host(xd) - x)) == 0.0
+    finally:
+        gasa.gasa_destroy(ctx)
+
+
+@pytest.mark.parametrize("name", ["tiny", "c1"])
+def test_gmres_solve(name):
+    gasa = _gasa()
+    H = oracle_setup(name)
+    pr = problem(name)
+    ref = O.solve(H, pr.rhs, TOL, "gmres", restart=30, max_iter=5000)
+    ref32 = O.solve(H, pr.rhs, TOL, "gmres", precision="mixed32", restart=30, max_iter=5000)
+    ctx, _ = gpu_setup(name, keep=False, solver=1)
+    try:
+        x = np.zeros_like(pr.rhs)
+        info = gasa.gasa_solve(ctx, pr.rhs, x, TOL)
+        assert info.converged and info.rel_residual <= TOL
+        assert abs(info.iterations - ref.iterations) <= 1, (info.iterations, ref.iterations)
+        assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= 1e-9
+        xm = np.zeros_like(pr.rhs)
+        info32 = gasa.gasa_solve(ctx, pr.rhs, xm, TOL, gasa.GASA_PREC_MIXED32)
+        assert info32.converged and info32.rel_residual <= TOL
+        assert abs(info32.iterations - ref32.iterations) <= 1, (info32.iterations, ref32.iterations)
+    finally:
+        gasa.gasa_destroy(ctx)
