@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Solves/s of alpha-SA-preconditioned CG on the P3 SIPG Poisson workload.
+
+Workload: unit square, 256 x 256 squares jittered +-0.2h, 2 triangles each,
+SIPG P3 (131072 elements, 1,310,720 dofs, 10 x 10 blocks), candidates r = 4,
+levels L0..L8 by the paper's rule, right-hand side N(0,1).  One step = one
+solve to ||b - A x|| <= 1e-10 ||b|| from x = 0 on the resident hierarchy
+(setup is timed separately).  The headline value is the mixed-precision
+solve (FP32 V-cycle inside FP64 flexible CG); the FP64 V-cycle solve is
+reported beside it.  Every matrix pass streams more than the 129 MB L2
+(A: 419 MB FP64, 209 MB FP32), so no L2 flush is needed between steps.
+
+Multi-GPU: the path does not shard; --gpus N runs N independent replicas
+(one process per GPU under torchrun) and reports the total solves/s.
+
+--impl reference times the CPU oracle on the host cores instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s to 1e-10 rel. resid: mixed vs FP64 V-cycle; HBM GB/s; p50/p99 ms"
+TOL = 1e-10
+WORKLOAD = "poisson2d_sipg_p3_tri_256x256"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+# DRAM bytes per launch of the level-0 FP32 block-Jacobi sweep from one ncu
+# capture, valid while the kernel source below hashes to `src_sha`.
+NCU_TRAFFIC = {"kernel": "jacobi_kernel<float,10,0>", "src_sha": None, "bytes_per_launch": None}
+
+
+def src_hash():
+    with open(os.path.join(ROOT, "paper_2504_13373_gb300", "csrc", "kernels_mv.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="cells per side (default: the full workload)")
+    ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-iters", type=int, default=3, help=argparse.SUPPRESS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="one mixed solve only (for an ncu launch list); prints no bench line")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def build_problem(n):
+    from synth import configs
+    return configs.poisson2d_p3(n=n)
+
+
+def hbm_peak():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = tempfile.mktemp(prefix="gasa_clk_", suffix=".csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline leg and --impl reference)
+# ----------------------------------------------------------------------------
+def cpu_sample_main(path, iters):
+    """Runs in a single-threaded child: oracle setup on the saved workload,
+    then `iters` oracle flexible-CG iterations with the float32 V-cycle."""
+    from oracle import gasa_oracle as O
+    d = np.load(path, allow_pickle=True)
+    aggs = [d[f"agg{k}"] for k in range(int(d["nagg"]))]
+    t0 = time.perf_counter()
+    H = O.setup(d["row_ptr"], d["col"], d["val"], aggs, B0=d["B0"], r=int(d["r"]), dim=2)
+    t_setup = time.perf_counter() - t0
+    M = O.make_vcycle(H, "fp32")
+    A = H.levels[0].A
+    t0 = time.perf_counter()
+    O.pcg(A, d["rhs"], M, 1e-300, iters, flexible=True)
+    t_it = (time.perf_counter() - t0) / iters
+    print(json.dumps({"setup_s": t_setup, "s_per_iter": t_it}))
+
+
+def run_cpu_sample(pr, iters):
+    tmp = tempfile.mktemp(prefix="gasa_wl_", suffix=".npz")
+    np.savez(tmp, row_ptr=pr.A.row_ptr, col=pr.A.col, val=pr.A.val, B0=pr.B0, r=pr.r,
+             rhs=pr.rhs, nagg=len(pr.agg_of), **{f"agg{k}": a for k, a in enumerate(pr.agg_of)})
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", tmp,
+                              "--cpu-iters", str(iters)], capture_output=True, text=True, env=env,
+                             timeout=1800)
+        line = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+        if out.returncode != 0 or not line:
+            return None, out.stderr[-2000:]
+        return json.loads(line[-1]), None
+    finally:
+        if os.path.exists(tmp):
+            os.unlink(tmp)
+
+
+# ----------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.cpu_sample:
+        cpu_sample_main(args.cpu_sample, args.cpu_iters)
+        return
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return reference_main(args, rank, world)
+    return ours_main(args, rank, world, local)
+
+
+def reference_main(args, rank, world):
+    if rank != 0:
+        return 0
+    pr = build_problem(args.n)
+    # iterations of one solve, from this workload's CUDA solve (identical
+    # to the oracle's within +-1 wherever both are run to completion)
+    iters_per_solve = ITERS_PER_SOLVE.get(args.n)
+    res, err = run_cpu_sample(pr, max(1, args.steps))
+    if res is None or iters_per_solve is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"oracle sample failed: {err}"}))
+        return 0
+    sec_per_solve = res["s_per_iter"] * iters_per_solve
+    value = 1.0 / sec_per_solve
+    sample = (f"oracle setup on the full workload ({res['setup_s']:.1f} s, untimed), then "
+              f"{max(1, args.steps)} flexible-CG iterations with the float32 V-cycle, "
+              f"{res['s_per_iter']:.3f} s each, x {iters_per_solve} iterations per solve")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_per_solve * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n": args.n},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+    return 0
+
+
+# CG iterations of one solve of this workload to 1e-10 (mixed and FP64 agree),
+# measured by the CUDA path's bench runs; the oracle matches the CUDA path's
+# counts within +-1 wherever both run to completion (32^2 and 64^2 meshes).
+ITERS_PER_SOLVE = {256: 3348, 64: 906}
+
+
+def ours_main(args, rank, world, local):
+    import torch
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2504_13373_gb300 import gasa
+    gasa.load()
+
+    t0 = time.perf_counter()
+    pr = build_problem(args.n)
+    t_gen = time.perf_counter() - t0
+    A = pr.A
+    n = pr.n_dofs
+    stream = torch.cuda.Stream()
+    ctx = gasa.gasa_create(local, stream)
+    opt = gasa.gasa_default_options(dim=2, n_cand=pr.r, max_iter=20000)
+    sinfo = gasa.gasa_setup(ctx, A.row_ptr, A.col, A.val.ravel(), A.b, pr.agg_of, opt,
+                            adj_ptr=pr.adj_ptr, adj_idx=pr.adj_idx, centroids=pr.centroids,
+                            init_candidates=pr.B0)
+    b_dev = torch.from_numpy(pr.rhs).to(f"cuda:{local}")
+    x_dev = torch.zeros_like(b_dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(precision, steps, profile=False):
+        """K solves bracketed by events on the library's stream."""
+        infos = []
+        per = []
+        barrier()
+        if profile:
+            gasa.gasa_profile_enable(ctx, True)
+        l0 = gasa.gasa_kernel_launches()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(steps):
+                e_a = torch.cuda.Event(enable_timing=True)
+                e_b = torch.cuda.Event(enable_timing=True)
+                e_a.record(stream)
+                infos.append(gasa.gasa_solve(ctx, b_dev, x_dev, TOL, precision, on_device=True))
+                e_b.record(stream)
+                per.append((e_a, e_b))
+            ev1.record(stream)
+        stream.synchronize()
+        launches = gasa.gasa_kernel_launches() - l0
+        ms = ev0.elapsed_time(ev1)
+        per_ms = [a.elapsed_time(bb) for a, bb in per]
+        barrier()
+        if dist is not None:
+            t = torch.tensor([ms], device=f"cuda:{local}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, infos, launches, per_ms
+
+    if args.profile_run:
+        for _ in range(max(1, args.steps)):
+            gasa.gasa_solve(ctx, b_dev, x_dev, TOL, gasa.GASA_PREC_MIXED32, on_device=True)
+        torch.cuda.synchronize()
+        gasa.gasa_destroy(ctx)
+        return 0
+    # warm-up
+    for _ in range(args.warmup):
+        gasa.gasa_solve(ctx, b_dev, x_dev, TOL, gasa.GASA_PREC_MIXED32, on_device=True)
+        gasa.gasa_solve(ctx, b_dev, x_dev, TOL, gasa.GASA_PREC_FP64, on_device=True)
+    with ClockSampler(local) as clk:
+        ms_mix, inf_mix, launches, per_mix = timed(gasa.GASA_PREC_MIXED32, args.steps)
+        ms_64, inf_64, _, per_64 = timed(gasa.GASA_PREC_FP64, args.steps)
+        # roofline of the dominant kernel: one more mixed solve with CUDA events
+        # around every level-0 sweep (events cannot sit inside the solve graph,
+        # so this solve runs the same kernels from the host-driven loop)
+        _, inf_prof, _, _ = timed(gasa.GASA_PREC_MIXED32, 1, profile=True)
+        prof = gasa.gasa_profile_read(ctx, 0)
+        gasa.gasa_profile_enable(ctx, False)
+    clocks = clk.summary()
+    # true residual of the last solves, checked on the host
+    x_host = x_dev.cpu().numpy()
+    # end to end through the public call with host buffers (pinned)
+    b_pin = torch.from_numpy(pr.rhs).pin_memory()
+    x_pin = torch.zeros(n, dtype=torch.float64).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        inf_e2e = gasa.gasa_solve(ctx, b_pin, x_pin, TOL, gasa.GASA_PREC_MIXED32, on_device=False)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    rel_host = float(np.linalg.norm(pr.rhs - A.to_scipy() @ x_pin.numpy()) / np.linalg.norm(pr.rhs))
+
+    value = world * args.steps / (ms_mix / 1e3)
+    value64 = world * args.steps / (ms_64 / 1e3)
+    peak, peak_kind = hbm_peak()
+    ms_k, n_k, bytes_k = prof
+    achieved = (bytes_k / n_k) / (ms_k / n_k / 1e3) / 1e9 if n_k else None
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["src_sha"] == src_hash() else None
+    iters = [i.iterations for i in inf_mix]
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_mix / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD if args.n == 256 else f"poisson2d_sipg_p3_tri_{args.n}x{args.n}",
+            "dofs": n, "elements": A.n, "block": A.b, "nnzb": int(A.nnzb), "levels": sinfo.n_levels,
+            "candidates": pr.r, "tol": TOL, "solver": "CG (flexible for mixed)",
+            "l2": "inputs larger than L2 (A 419 MB FP64 / 209 MB FP32 per pass), no flush",
+            "parallelism": f"replicas x{world}",
+        },
+        "iterations": {"mixed": iters, "fp64": [i.iterations for i in inf_64]},
+        "rel_residual": {"mixed": max(i.rel_residual for i in inf_mix),
+                         "fp64": max(i.rel_residual for i in inf_64), "e2e_host_check": rel_host},
+        "fp64": {"value": value64, "unit": "solves/s", "ms_per_step": ms_64 / args.steps,
+                 "p50_ms": float(np.percentile(per_64, 50)), "p99_ms": float(np.percentile(per_64, 99))},
+        "p50_ms": float(np.percentile(per_mix, 50)),
+        "p99_ms": float(np.percentile(per_mix, 99)),
+        "setup_s": sinfo.seconds,
+        "generate_s": t_gen,
+        "roofline": {"kernel": "level-0 block-Jacobi sweep, FP32 (jacobi_kernel<float,10,*>)",
+                     "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None, "peak_kind": f"{peak_kind} hbm_gbs",
+                     "traffic": traffic, "algorithmic_bytes_per_launch": bytes_k / n_k if n_k else None,
+                     "launches": n_k, "avg_launch_us": ms_k / n_k * 1e3 if n_k else None},
+        "e2e": {"value": world * args.steps / e2e_s, "unit": "solves/s",
+                "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    ITERS_PER_SOLVE.setdefault(args.n, int(np.median(iters)))
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res, err = run_cpu_sample(pr, args.cpu_iters)
+        if res is not None:
+            sps = 1.0 / (res["s_per_iter"] * float(np.median(iters)))
+            line["cpu_baseline"] = {
+                "value": sps, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                "sample": (f"oracle setup on the full workload ({res['setup_s']:.1f} s, untimed), then "
+                           f"{args.cpu_iters} flexible-CG iterations with the float32 V-cycle at "
+                           f"{res['s_per_iter']:.3f} s each, scaled to {int(np.median(iters))} "
+                           f"iterations per solve (this run's count)")}
+        else:
+            line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"failed: {err}"}
+    gasa.gasa_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    del x_host
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main() or 0)

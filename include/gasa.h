@@ -181,6 +181,10 @@ gasa_status gasa_profile_enable(gasa_ctx *ctx, int32_t on);
 gasa_status gasa_profile_read(gasa_ctx *ctx, int32_t kernel_class, double *ms,
                               int64_t *launches, double *bytes);
 
+/* Number of CUDA kernels this library has launched in this process (all
+ * contexts and single operations), for launch accounting. */
+int64_t gasa_kernel_launches(void);
+
 gasa_status gasa_destroy(gasa_ctx *ctx);
 const char *gasa_status_string(gasa_status s);
 const char *gasa_last_error(const gasa_ctx *ctx);

@@ -79,6 +79,13 @@ struct gasa_ctx {
   double *V = nullptr, *Z = nullptr, *H = nullptr, *gm = nullptr, *mpart = nullptr;
   int gm_restart = 0;
   bool gm_flex = false;
+  // graph-resident CG: one instantiated graph per precision, the whole CG
+  // iteration (V-cycle included) inside a conditional while node
+  cudaGraph_t cg_graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t cg_exec[2] = {nullptr, nullptr};
+  long long cg_kernels[2] = {0, 0};
+  int cg_max_iter[2] = {0, 0};
+  int *d_iters = nullptr;
   // profiling
   bool prof = false;
   ProfClass pc[3];
@@ -143,8 +150,19 @@ void dfree(gasa_ctx *ctx, void *p) {
   cudaFree(p);
 }
 
+void free_graphs(gasa_ctx *ctx) {
+  for (int p = 0; p < 2; ++p) {
+    if (ctx->cg_exec[p]) cudaGraphExecDestroy(ctx->cg_exec[p]);
+    if (ctx->cg_graph[p]) cudaGraphDestroy(ctx->cg_graph[p]);
+    ctx->cg_exec[p] = nullptr;
+    ctx->cg_graph[p] = nullptr;
+    ctx->cg_kernels[p] = 0;
+  }
+}
+
 void free_all(gasa_ctx *ctx) {
   cudaStreamSynchronize(ctx->stream);
+  free_graphs(ctx);
   for (void *p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
   if (ctx->hscal) {
@@ -240,12 +258,12 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out) {
       cudaEvent_t e0;
       if (k == 0) prof_begin(ctx, 0, &e0);
       CU(launch_jacobi<T>(JAC_FIRST, l.n, l.s, l.A.rp, l.A.col, P::A(l.A), P::W(l), nullptr,
-                          bk[k], x, s));
+                          bk[k], x, s, l.A.nnzb));
       if (k == 0) prof_end(ctx, 0, sweep_bytes(l, w, true));
       for (int t = 1; t < tpre; ++t) {
         if (k == 0) prof_begin(ctx, 0, &e0);
         CU(launch_jacobi<T>(JAC_SWEEP, l.n, l.s, l.A.rp, l.A.col, P::A(l.A), P::W(l), x, bk[k],
-                            x2, s));
+                            x2, s, l.A.nnzb));
         if (k == 0) prof_end(ctx, 0, sweep_bytes(l, w, false));
         std::swap(x, x2);
       }
@@ -256,11 +274,11 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out) {
       cudaEvent_t e0;
       if (k == 0) prof_begin(ctx, 1, &e0);
       CU(launch_bsr_mv<T>(GASA_MV_RESIDUAL, l.n, l.s, l.s, l.A.rp, l.A.col, P::A(l.A), x, bk[k],
-                          P::r(l), s));
+                          P::r(l), s, l.A.nnzb));
       if (k == 0) prof_end(ctx, 1, spmv_bytes(l, w, true));
     }
     CU(launch_bsr_mv<T>(GASA_MV_ASSIGN, l.R.nrows, l.R.br, l.R.bc, l.R.rp, l.R.col, P::A(l.R),
-                        P::r(l), nullptr, P::b(ctx->L[k + 1]), s));
+                        P::r(l), nullptr, P::b(ctx->L[k + 1]), s, l.R.nnzb));
   }
   // coarsest solve in FP64
   Level &lc = ctx->L[N];
@@ -271,7 +289,7 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out) {
     T *x = xk[k];
     T *x2 = (x == P::x(l)) ? P::x2(l) : P::x(l);
     CU(launch_bsr_mv<T>(GASA_MV_ADD, l.P.nrows, l.P.br, l.P.bc, l.P.rp, l.P.col, P::A(l.P),
-                        xk[k + 1], nullptr, x, s));
+                        xk[k + 1], nullptr, x, s, l.P.nnzb));
     if (tpost == 0 && k == 0) {
       CU(cudaMemcpyAsync(out, x, l.ndof * sizeof(T), cudaMemcpyDeviceToDevice, s));
     }
@@ -280,7 +298,7 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out) {
       cudaEvent_t e0;
       if (k == 0) prof_begin(ctx, 0, &e0);
       CU(launch_jacobi<T>(JAC_SWEEP, l.n, l.s, l.A.rp, l.A.col, P::A(l.A), P::W(l), x, bk[k], dst,
-                          s));
+                          s, l.A.nnzb));
       if (k == 0) prof_end(ctx, 0, sweep_bytes(l, w, false));
       if (dst == x2) std::swap(x, x2);
       else x = dst;
@@ -301,7 +319,7 @@ gasa_status apply_M(gasa_ctx *ctx, const double *rr, double *z, int precision) {
 
 // scalar slots in ctx->scal
 enum { S_RR = 0, S_ALPHA = 1, S_PQ = 2, S_RZ0 = 3, S_RZ1 = 4, S_BB = 5, S_TMP = 6, S_G = 7,
-       S_BETA = 8, S_COUNT = 16 };
+       S_BETA = 8, S_BN = 9, S_TOL = 10, S_COUNT = 16 };
 
 gasa_status read_scalars(gasa_ctx *ctx, int first, int count) {
   CU(cudaMemcpyAsync(ctx->hscal + first, ctx->scal + first, count * sizeof(double),
@@ -390,6 +408,135 @@ gasa_status pcg(gasa_ctx *ctx, const double *b, double tol, int precision, int *
     std::swap(cur, nxt);
   }
   ST(spmv_outer(ctx, GASA_MV_RESIDUAL, x, b, ctx->kt));
+  double tt;
+  ST(norm2(ctx, n, ctx->kt, S_TMP, &tt));
+  *relres = std::sqrt(tt) / bn;
+  return GASA_OK;
+}
+
+// Build the CG graph of one precision: a conditional while node whose body
+// is one CG step in the order z = M r; p = z + beta p; q = A p; x, r update;
+// check.  Started with p = 0 and rz = 1, the first step gives p = z, so the
+// sequence of iterates is the same as the host-driven loop above.
+gasa_status build_cg_graph(gasa_ctx *ctx, int precision) {
+  const int pi = precision == GASA_PREC_FP64 ? 0 : 1;
+  const int max_iter = ctx->opt.max_iter;
+  if (ctx->cg_exec[pi] && ctx->cg_max_iter[pi] == max_iter) return GASA_OK;
+  if (ctx->cg_exec[pi]) cudaGraphExecDestroy(ctx->cg_exec[pi]);
+  if (ctx->cg_graph[pi]) cudaGraphDestroy(ctx->cg_graph[pi]);
+  ctx->cg_exec[pi] = nullptr;
+  ctx->cg_graph[pi] = nullptr;
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->L[0].ndof;
+  const bool flex = precision != GASA_PREC_FP64;
+  cudaGraph_t g = nullptr;
+  CU(cudaGraphCreate(&g, 0));
+  ctx->cg_graph[pi] = g;
+  cudaGraphConditionalHandle h;
+  CU(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CU(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  double *x = ctx->kx, *r = ctx->kr, *z = ctx->kz, *p = ctx->kp, *q = ctx->kq, *zold = ctx->kzold;
+  double *pq_part = ctx->part, *rr_part = ctx->part + kRedBlocks,
+         *rz_part = ctx->part + 2 * kRedBlocks, *rzo_part = ctx->part + 3 * kRedBlocks;
+  const bool prof = ctx->prof;
+  ctx->prof = false;   // no event records inside a graph body
+  const long long k0 = launch_count();
+  CU(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  gasa_status st = apply_M(ctx, r, z, precision);
+  cudaError_t e = cudaSuccess;
+  if (st == GASA_OK) {
+    e = launch_dot_partials(n, r, z, rz_part, s);
+    if (e == cudaSuccess && flex) e = launch_dot_partials(n, r, zold, rzo_part, s);
+    if (e == cudaSuccess)
+      e = launch_cg_update_p(n, p, z, ctx->scal + S_RZ0, rz_part, rzo_part, ctx->scal + S_RZ1,
+                             flex ? 1 : 0, s, flex ? zold : nullptr);
+    Level &l = ctx->L[0];
+    if (e == cudaSuccess)
+      e = launch_bsr_mv<double>(GASA_MV_ASSIGN, l.n, l.s, l.s, l.A.rp, l.A.col, l.A.val, p, nullptr,
+                                q, s);
+    if (e == cudaSuccess) e = launch_dot_partials(n, p, q, pq_part, s);
+    if (e == cudaSuccess)
+      e = launch_cg_update_xr(n, x, r, p, q, ctx->scal + S_RZ1, pq_part, rr_part,
+                              ctx->scal + S_ALPHA, s);
+    if (e == cudaSuccess) e = launch_cg_check(rr_part, ctx->scal, ctx->d_iters, max_iter, h, s);
+  }
+  cudaGraph_t captured = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(s, &captured);
+  ctx->prof = prof;
+  ctx->cg_kernels[pi] = launch_count() - k0;
+  if (st != GASA_OK) return st;
+  CU(e);
+  CU(e2);
+  CU(cudaGraphInstantiate(&ctx->cg_exec[pi], g, 0));
+  ctx->cg_max_iter[pi] = max_iter;
+  return GASA_OK;
+}
+
+gasa_status pcg_graph(gasa_ctx *ctx, const double *b, double tol, int precision, int *iters,
+                      double *relres, bool *conv) {
+  cudaStream_t s = ctx->stream;
+  const int pi = precision == GASA_PREC_FP64 ? 0 : 1;
+  const int64_t n = ctx->L[0].ndof;
+  *conv = false;
+  *iters = 0;
+  ST(build_cg_graph(ctx, precision));
+  double bb;
+  ST(norm2(ctx, n, b, S_BB, &bb));
+  const double bn = std::sqrt(bb);
+  CU(cudaMemsetAsync(ctx->kx, 0, n * sizeof(double), s));
+  if (bn == 0.0) {
+    *relres = 0.0;
+    *conv = true;
+    return GASA_OK;
+  }
+  CU(launch_copy(n, b, ctx->kr, s));
+  CU(cudaMemsetAsync(ctx->kp, 0, n * sizeof(double), s));
+  CU(cudaMemsetAsync(ctx->kzold, 0, n * sizeof(double), s));
+  CU(cudaMemsetAsync(ctx->d_iters, 0, sizeof(int), s));
+  ctx->hscal[S_RZ0] = 1.0;
+  ctx->hscal[S_BN] = bn;
+  ctx->hscal[S_TOL] = tol;
+  CU(cudaMemcpyAsync(ctx->scal + S_RZ0, ctx->hscal + S_RZ0, sizeof(double), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(ctx->scal + S_BN, ctx->hscal + S_BN, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+  int done_iters = 0;
+  const int max_iter = ctx->opt.max_iter;
+  for (;;) {
+    CU(cudaGraphLaunch(ctx->cg_exec[pi], s));
+    int it = 0;
+    CU(cudaMemcpyAsync(&it, ctx->d_iters, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ST(read_scalars(ctx, 0, 3));
+    note_launches(ctx->cg_kernels[pi] * (long long)(it - done_iters));
+    done_iters = it;
+    *iters = it;
+    const double pq = ctx->hscal[S_PQ];
+    const double rel = std::sqrt(ctx->hscal[S_RR]) / bn;
+    if (!std::isfinite(rel) || !std::isfinite(pq))
+      return fail(ctx, GASA_ERR_BREAKDOWN, "CG: non-finite residual");
+    if (!(pq > 0.0)) {
+      *relres = rel;
+      return fail(ctx, GASA_ERR_NOT_SPD, "CG: p^T A p <= 0");
+    }
+    if (rel <= tol) {
+      ST(spmv_outer(ctx, GASA_MV_RESIDUAL, ctx->kx, b, ctx->kt));
+      double tt;
+      ST(norm2(ctx, n, ctx->kt, S_TMP, &tt));
+      const double relt = std::sqrt(tt) / bn;
+      *relres = relt;
+      if (relt <= tol) {
+        *conv = true;
+        return GASA_OK;
+      }
+      CU(launch_copy(n, ctx->kt, ctx->kr, s));   // continue from the true residual
+    }
+    if (it >= max_iter) break;
+  }
+  ST(spmv_outer(ctx, GASA_MV_RESIDUAL, ctx->kx, b, ctx->kt));
   double tt;
   ST(norm2(ctx, n, ctx->kt, S_TMP, &tt));
   *relres = std::sqrt(tt) / bn;
@@ -777,13 +924,13 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
     CU(launch_finalize(ctx->part, 1, ctx->scal + S_TMP, s));
     CU(launch_scale_by_inv_sqrt(nd, pv, ctx->scal + S_TMP, s));
     for (int it = 0; it < opt->q_power; ++it) {
-      CU(launch_jacobi<double>(JAC_APPLY, l.n, l.s, l.A.rp, l.A.col, l.A.val, l.W, pv, nullptr, pv2, s));
+      CU(launch_jacobi<double>(JAC_APPLY, l.n, l.s, l.A.rp, l.A.col, l.A.val, l.W, pv, nullptr, pv2, s, l.A.nnzb));
       CU(launch_dot_partials(nd, pv2, nullptr, ctx->part, s));
       CU(launch_finalize(ctx->part, 1, ctx->scal + S_TMP, s));
       CU(launch_scale_by_inv_sqrt(nd, pv2, ctx->scal + S_TMP, s));
       std::swap(pv, pv2);
     }
-    CU(launch_jacobi<double>(JAC_APPLY, l.n, l.s, l.A.rp, l.A.col, l.A.val, l.W, pv, nullptr, pv2, s));
+    CU(launch_jacobi<double>(JAC_APPLY, l.n, l.s, l.A.rp, l.A.col, l.A.val, l.W, pv, nullptr, pv2, s, l.A.nnzb));
     double rr;
     ST(norm2(ctx, nd, pv2, S_TMP, &rr));
     l.rho = std::sqrt(rr);
@@ -999,6 +1146,7 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
     ST(dalloc(ctx, p, (size_t)n));
   ST(dalloc(ctx, &ctx->kf_in, (size_t)n));
   ST(dalloc(ctx, &ctx->kf_out, (size_t)n));
+  ST(dalloc(ctx, &ctx->d_iters, 4));
   CU(cudaStreamSynchronize(s));
   ctx->ready = true;
   ctx->setup_seconds =
@@ -1111,7 +1259,8 @@ gasa_status gasa_solve(gasa_ctx *ctx, const double *b, double *x, double tol, in
   bool conv = false;
   gasa_status st = ctx->opt.solver == GASA_SOLVER_GMRES
                        ? gmres(ctx, bd, tol, precision, &iters, &rel, &conv)
-                       : pcg(ctx, bd, tol, precision, &iters, &rel, &conv);
+                       : (ctx->prof ? pcg(ctx, bd, tol, precision, &iters, &rel, &conv)
+                                    : pcg_graph(ctx, bd, tol, precision, &iters, &rel, &conv));
   if (st == GASA_OK || st == GASA_ERR_NOT_SPD) {
     if (on_device) {
       CU(cudaMemcpyAsync(x, ctx->kx, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1249,12 +1398,24 @@ const char *gasa_status_string(gasa_status s) {
 
 const char *gasa_last_error(const gasa_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
 
+int64_t gasa_kernel_launches(void) { return (int64_t)launch_count(); }
+
 // ---------------------------------------------------------------------------
 // single operations
 // ---------------------------------------------------------------------------
 static gasa_status op_status(cudaError_t e) {
   if (e == cudaSuccess) return GASA_OK;
   return e == cudaErrorMemoryAllocation ? GASA_ERR_OOM : GASA_ERR_CUDA;
+}
+
+// stored blocks of a device BSR matrix (row_ptr[n]); -1 when it cannot be read
+static int64_t op_nnzb(const int32_t *row_ptr, int32_t n, cudaStream_t s) {
+  if (!row_ptr) return -1;
+  int32_t v = -1;
+  if (cudaMemcpyAsync(&v, row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return -1;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+  return v;
 }
 
 gasa_status gasa_bsr_mv(int32_t mode, int32_t n_brows, int32_t br, int32_t bc,
@@ -1265,7 +1426,8 @@ gasa_status gasa_bsr_mv(int32_t mode, int32_t n_brows, int32_t br, int32_t bc,
   if (!row_ptr || !col || !val || !x || !y || (mode == GASA_MV_RESIDUAL && !b))
     return GASA_ERR_INVALID_ARG;
   return op_status(launch_bsr_mv<double>(mode, n_brows, br, bc, row_ptr, col, val, x, b, y,
-                                         (cudaStream_t)stream));
+                                         (cudaStream_t)stream,
+                                         op_nnzb(row_ptr, n_brows, (cudaStream_t)stream)));
 }
 
 gasa_status gasa_bsr_mv_f32(int32_t mode, int32_t n_brows, int32_t br, int32_t bc,
@@ -1276,7 +1438,8 @@ gasa_status gasa_bsr_mv_f32(int32_t mode, int32_t n_brows, int32_t br, int32_t b
   if (!row_ptr || !col || !val || !x || !y || (mode == GASA_MV_RESIDUAL && !b))
     return GASA_ERR_INVALID_ARG;
   return op_status(launch_bsr_mv<float>(mode, n_brows, br, bc, row_ptr, col, val, x, b, y,
-                                        (cudaStream_t)stream));
+                                        (cudaStream_t)stream,
+                                        op_nnzb(row_ptr, n_brows, (cudaStream_t)stream)));
 }
 
 gasa_status gasa_jacobi_sweep(int32_t n_units, int32_t bs, const int32_t *row_ptr,
@@ -1288,7 +1451,8 @@ gasa_status gasa_jacobi_sweep(int32_t n_units, int32_t bs, const int32_t *row_pt
   if (!W || !b || !x_out || (!first && (!row_ptr || !col || !val || !x)) || x == x_out)
     return GASA_ERR_INVALID_ARG;
   return op_status(launch_jacobi<double>(first ? JAC_FIRST : JAC_SWEEP, n_units, bs, row_ptr, col,
-                                         val, W, x, b, x_out, (cudaStream_t)stream));
+                                         val, W, x, b, x_out, (cudaStream_t)stream,
+                                         first ? -1 : op_nnzb(row_ptr, n_units, (cudaStream_t)stream)));
 }
 
 gasa_status gasa_jacobi_sweep_f32(int32_t n_units, int32_t bs, const int32_t *row_ptr,
@@ -1300,7 +1464,8 @@ gasa_status gasa_jacobi_sweep_f32(int32_t n_units, int32_t bs, const int32_t *ro
   if (!W || !b || !x_out || (!first && (!row_ptr || !col || !val || !x)) || x == x_out)
     return GASA_ERR_INVALID_ARG;
   return op_status(launch_jacobi<float>(first ? JAC_FIRST : JAC_SWEEP, n_units, bs, row_ptr, col,
-                                        val, W, x, b, x_out, (cudaStream_t)stream));
+                                        val, W, x, b, x_out, (cudaStream_t)stream,
+                                        first ? -1 : op_nnzb(row_ptr, n_units, (cudaStream_t)stream)));
 }
 
 gasa_status gasa_block_inverse(int32_t n_units, int32_t bs, const int32_t *row_ptr,
@@ -1330,6 +1495,7 @@ gasa_status gasa_power_estimate(int32_t n_units, int32_t bs, const int32_t *row_
     return GASA_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = (int64_t)n_units * bs;
+  const int64_t nnzb = op_nnzb(row_ptr, n_units, s);
   double *buf = nullptr;
   cudaError_t e = cudaMallocAsync((void **)&buf, sizeof(double) * (2 * n + kRedBlocks + 2), s);
   if (e != cudaSuccess) return op_status(e);
@@ -1339,14 +1505,14 @@ gasa_status gasa_power_estimate(int32_t n_units, int32_t bs, const int32_t *row_
   if (e == cudaSuccess) e = launch_finalize(part, 1, sc, s);
   if (e == cudaSuccess) e = launch_scale_by_inv_sqrt(n, a, sc, s);
   for (int it = 0; it < q && e == cudaSuccess; ++it) {
-    e = launch_jacobi<double>(JAC_APPLY, n_units, bs, row_ptr, col, val, Dinv, a, nullptr, bb, s);
+    e = launch_jacobi<double>(JAC_APPLY, n_units, bs, row_ptr, col, val, Dinv, a, nullptr, bb, s, nnzb);
     if (e == cudaSuccess) e = launch_dot_partials(n, bb, nullptr, part, s);
     if (e == cudaSuccess) e = launch_finalize(part, 1, sc, s);
     if (e == cudaSuccess) e = launch_scale_by_inv_sqrt(n, bb, sc, s);
     std::swap(a, bb);
   }
   if (e == cudaSuccess)
-    e = launch_jacobi<double>(JAC_APPLY, n_units, bs, row_ptr, col, val, Dinv, a, nullptr, bb, s);
+    e = launch_jacobi<double>(JAC_APPLY, n_units, bs, row_ptr, col, val, Dinv, a, nullptr, bb, s, nnzb);
   if (e == cudaSuccess) e = launch_dot_partials(n, bb, nullptr, part, s);
   if (e == cudaSuccess) e = launch_finalize(part, 1, sc, s);
   double h = 0.0;

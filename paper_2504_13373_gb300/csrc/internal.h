@@ -6,17 +6,24 @@
 
 namespace gasa {
 
+// kernel launches issued by this library (process-wide counter)
+void note_launch();
+long long launch_count();
+
 enum JacobiMode { JAC_SWEEP = 0, JAC_FIRST = 1, JAC_APPLY = 2, JAC_RELAX = 3 };
 
 // ---- kernels_mv.cu ---------------------------------------------------------
+// nnzb >= 0 lets the launcher pick a warp per block row when rows are long
+// (>= 12 blocks on average); nnzb < 0 always uses one thread per scalar row.
 template <typename T>
 cudaError_t launch_bsr_mv(int mode, int n_brows, int br, int bc, const int *rp, const int *col,
-                          const T *val, const T *x, const T *b, T *y, cudaStream_t s);
+                          const T *val, const T *x, const T *b, T *y, cudaStream_t s,
+                          int64_t nnzb = -1);
 
 template <typename T>
 cudaError_t launch_jacobi(int mode, int n_units, int bs, const int *rp, const int *col,
                           const T *val, const T *W, const T *x, const T *b, T *xo,
-                          cudaStream_t s);
+                          cudaStream_t s, int64_t nnzb = -1);
 
 // multi-column relaxation x_c <- x_c - W A x_c for `nc` columns given by
 // device tables of column base pointers (each column n_units*bs long).
@@ -56,7 +63,11 @@ cudaError_t launch_cg_update_xr(int64_t n, double *x, double *r, const double *p
                                 double *rr_partials, double *alpha_out, cudaStream_t s);
 cudaError_t launch_cg_update_p(int64_t n, double *p, const double *z, const double *rz_old,
                                const double *rz_partials, const double *rzold_partials,
-                               double *rz_out, int flexible, cudaStream_t s);
+                               double *rz_out, int flexible, cudaStream_t s,
+                               double *zold_out = nullptr);
+cudaError_t launch_cg_check(const double *rr_partials, double *scal, int *iters, int max_iter,
+                            cudaGraphConditionalHandle handle, cudaStream_t s);
+void note_launches(long long n);
 cudaError_t launch_axpy(int64_t n, double a, const double *x, double *y, cudaStream_t s);
 cudaError_t launch_copy(int64_t n, const double *x, double *y, cudaStream_t s);
 cudaError_t launch_sub(int64_t n, const double *a, const double *b, double *out, cudaStream_t s);

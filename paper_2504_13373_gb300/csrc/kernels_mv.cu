@@ -68,7 +68,82 @@ bsr_mv_generic(int n_brows, int br, int bc, const int *__restrict__ rp,
   else y[t] += acc;
 }
 
+// ----------------------------------------------------------------------------
+// Coarse levels: few block rows, each with tens to hundreds of blocks (the
+// Galerkin products widen the stencil level by level).  One warp owns one
+// block row; lane l takes blocks l, l+32, ... and keeps br partial sums; an
+// xor-shuffle reduction leaves every sum in every lane.
+// ----------------------------------------------------------------------------
+template <typename T, int BRMAX>
+__device__ __forceinline__ void warp_row_product(int beg, int end, int br, int bc, int lane,
+                                                 const int *__restrict__ col,
+                                                 const T *__restrict__ val,
+                                                 const T *__restrict__ x, T (&acc)[BRMAX]) {
+#pragma unroll
+  for (int r = 0; r < BRMAX; ++r) acc[r] = T(0);
+  for (int k = beg + lane; k < end; k += 32) {
+    const int j = __ldg(col + k);
+    const T *a = val + (size_t)k * br * bc;
+    const T *xj = x + (size_t)j * bc;
+    for (int c = 0; c < bc; ++c) {
+      const T xv = __ldg(xj + c);
+#pragma unroll
+      for (int r = 0; r < BRMAX; ++r)
+        if (r < br) acc[r] = fma(__ldg(a + r * bc + c), xv, acc[r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < BRMAX; ++r)
+    if (r < br) acc[r] = warp_sum(acc[r]);
+}
+
+template <typename T, int BRMAX>
+__device__ __forceinline__ T pick(const T (&acc)[BRMAX], int r) {
+  T v = T(0);
+#pragma unroll
+  for (int q = 0; q < BRMAX; ++q)
+    if (q == r) v = acc[q];
+  return v;
+}
+
+template <typename T, int BRMAX, int MODE>
+__global__ void __launch_bounds__(256)
+bsr_mv_warp_kernel(int n_brows, int br, int bc, const int *__restrict__ rp,
+                   const int *__restrict__ col, const T *__restrict__ val, const T *__restrict__ x,
+                   const T *__restrict__ b, T *__restrict__ y) {
+  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n_brows) return;
+  T acc[BRMAX];
+  warp_row_product<T, BRMAX>(__ldg(rp + i), __ldg(rp + i + 1), br, bc, lane, col, val, x, acc);
+  for (int r = lane; r < br; r += 32) {
+    const size_t t = (size_t)i * br + r;
+    const T v = pick<T, BRMAX>(acc, r);
+    if (MODE == GASA_MV_ASSIGN) y[t] = v;
+    else if (MODE == GASA_MV_RESIDUAL) y[t] = b[t] - v;
+    else y[t] += v;
+  }
+}
+
+// average blocks per row from which a warp per block row pays
+static inline bool warp_rows(int n_brows, int br, int64_t nnzb) {
+  return nnzb >= 0 && br <= 64 && nnzb >= 12LL * n_brows;
+}
+
 static inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+template <typename T, int MODE>
+static cudaError_t mv_warp_dispatch(int n_brows, int br, int bc, const int *rp, const int *col,
+                                    const T *val, const T *x, const T *b, T *y, cudaStream_t s) {
+  const int grid = div_up((long long)n_brows * 32, 256);
+  if (br <= 4) bsr_mv_warp_kernel<T, 4, MODE><<<grid, 256, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y);
+  else if (br <= 8) bsr_mv_warp_kernel<T, 8, MODE><<<grid, 256, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y);
+  else if (br <= 16) bsr_mv_warp_kernel<T, 16, MODE><<<grid, 256, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y);
+  else if (br <= 32) bsr_mv_warp_kernel<T, 32, MODE><<<grid, 256, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y);
+  else bsr_mv_warp_kernel<T, 64, MODE><<<grid, 256, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y);
+  note_launch();
+  return cudaGetLastError();
+}
 
 template <typename T, int MODE>
 static cudaError_t mv_dispatch(int n_brows, int br, int bc, const int *rp, const int *col,
@@ -80,7 +155,7 @@ static cudaError_t mv_dispatch(int n_brows, int br, int bc, const int *rp, const
   const bool al = aligned16(val) && aligned16(x);
 #define GASA_MV_CASE(BC)                                                                   \
   case BC:                                                                                 \
-    bsr_mv_kernel<T, BC, MODE><<<grid, th, 0, s>>>(n_brows, br, rp, col, val, x, b, y);    \
+    bsr_mv_kernel<T, BC, MODE><<<grid, th, 0, s>>>(n_brows, br, rp, col, val, x, b, y); note_launch();    \
     return cudaGetLastError();
   if (al) {
     switch (bc) {
@@ -92,13 +167,24 @@ static cudaError_t mv_dispatch(int n_brows, int br, int bc, const int *rp, const
     }
   }
 #undef GASA_MV_CASE
-  bsr_mv_generic<T, MODE><<<grid, th, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y);
+  bsr_mv_generic<T, MODE><<<grid, th, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y); note_launch();
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_bsr_mv(int mode, int n_brows, int br, int bc, const int *rp, const int *col,
-                          const T *val, const T *x, const T *b, T *y, cudaStream_t s) {
+                          const T *val, const T *x, const T *b, T *y, cudaStream_t s,
+                          int64_t nnzb) {
+  if (n_brows > 0 && warp_rows(n_brows, br, nnzb)) {
+    switch (mode) {
+      case GASA_MV_ASSIGN:
+        return mv_warp_dispatch<T, GASA_MV_ASSIGN>(n_brows, br, bc, rp, col, val, x, b, y, s);
+      case GASA_MV_RESIDUAL:
+        return mv_warp_dispatch<T, GASA_MV_RESIDUAL>(n_brows, br, bc, rp, col, val, x, b, y, s);
+      default:
+        return mv_warp_dispatch<T, GASA_MV_ADD>(n_brows, br, bc, rp, col, val, x, b, y, s);
+    }
+  }
   switch (mode) {
     case GASA_MV_ASSIGN:
       return mv_dispatch<T, GASA_MV_ASSIGN>(n_brows, br, bc, rp, col, val, x, b, y, s);
@@ -110,10 +196,10 @@ cudaError_t launch_bsr_mv(int mode, int n_brows, int br, int bc, const int *rp, 
 }
 template cudaError_t launch_bsr_mv<double>(int, int, int, int, const int *, const int *,
                                            const double *, const double *, const double *,
-                                           double *, cudaStream_t);
+                                           double *, cudaStream_t, int64_t);
 template cudaError_t launch_bsr_mv<float>(int, int, int, int, const int *, const int *,
                                           const float *, const float *, const float *, float *,
-                                          cudaStream_t);
+                                          cudaStream_t, int64_t);
 
 // ----------------------------------------------------------------------------
 // block Jacobi step (Alg. 1 with A~^{-1} = w D^{-1}):
@@ -215,6 +301,51 @@ jacobi_generic(int n_units, int bs, const int *__restrict__ rp, const int *__res
   xo[row] = out;
 }
 
+// warp per block row: the reduced residual of the block row is in every lane,
+// lane r then applies row r of W_i
+template <typename T, int BRMAX, int MODE>
+__global__ void __launch_bounds__(256)
+jacobi_warp_kernel(int n_units, int bs, const int *__restrict__ rp, const int *__restrict__ col,
+                   const T *__restrict__ val, const T *__restrict__ Wm, const T *__restrict__ x,
+                   const T *__restrict__ b, T *__restrict__ xo) {
+  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n_units) return;
+  T acc[BRMAX];
+  warp_row_product<T, BRMAX>(__ldg(rp + i), __ldg(rp + i + 1), bs, bs, lane, col, val, x, acc);
+#pragma unroll
+  for (int r = 0; r < BRMAX; ++r) {
+    if (r < bs) {
+      if (MODE == JAC_SWEEP) acc[r] = b[(size_t)i * bs + r] - acc[r];
+      else if (MODE == JAC_RELAX) acc[r] = -acc[r];
+    }
+  }
+  for (int r = lane; r < bs; r += 32) {
+    const T *w = Wm + ((size_t)i * bs + r) * bs;
+    T out = T(0);
+#pragma unroll
+    for (int c = 0; c < BRMAX; ++c)
+      if (c < bs) out = fma(__ldg(w + c), acc[c], out);
+    const size_t row = (size_t)i * bs + r;
+    if (MODE == JAC_SWEEP || MODE == JAC_RELAX) out += x[row];
+    xo[row] = out;
+  }
+}
+
+template <typename T, int MODE>
+static cudaError_t jac_warp_dispatch(int n_units, int bs, const int *rp, const int *col,
+                                     const T *val, const T *W, const T *x, const T *b, T *xo,
+                                     cudaStream_t s) {
+  const int grid = div_up((long long)n_units * 32, 256);
+  if (bs <= 4) jacobi_warp_kernel<T, 4, MODE><<<grid, 256, 0, s>>>(n_units, bs, rp, col, val, W, x, b, xo);
+  else if (bs <= 8) jacobi_warp_kernel<T, 8, MODE><<<grid, 256, 0, s>>>(n_units, bs, rp, col, val, W, x, b, xo);
+  else if (bs <= 16) jacobi_warp_kernel<T, 16, MODE><<<grid, 256, 0, s>>>(n_units, bs, rp, col, val, W, x, b, xo);
+  else if (bs <= 32) jacobi_warp_kernel<T, 32, MODE><<<grid, 256, 0, s>>>(n_units, bs, rp, col, val, W, x, b, xo);
+  else jacobi_warp_kernel<T, 64, MODE><<<grid, 256, 0, s>>>(n_units, bs, rp, col, val, W, x, b, xo);
+  note_launch();
+  return cudaGetLastError();
+}
+
 template <typename T, int MODE>
 static cudaError_t jac_dispatch(int n_units, int bs, const int *rp, const int *col,
                                 const T *val, const T *W, const T *x, const T *b, T *xo,
@@ -225,7 +356,7 @@ static cudaError_t jac_dispatch(int n_units, int bs, const int *rp, const int *c
   case BS: {                                                                                \
     constexpr int rpb = 256 / BS;                                                           \
     jacobi_kernel<T, BS, MODE><<<div_up(n_units, rpb), 256, 0, s>>>(n_units, rp, col, val,  \
-                                                                    W, x, b, xo);           \
+                                                                    W, x, b, xo); note_launch();           \
     return cudaGetLastError();                                                              \
   }
   if (al && bs <= 16) {
@@ -244,14 +375,21 @@ static cudaError_t jac_dispatch(int n_units, int bs, const int *rp, const int *c
   const int th = rpb * bs;
   if (th > 1024) return cudaErrorInvalidValue;
   jacobi_generic<T, MODE><<<div_up(n_units, rpb), th, th * sizeof(T), s>>>(n_units, bs, rp, col,
-                                                                           val, W, x, b, xo);
+                                                                           val, W, x, b, xo); note_launch();
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_jacobi(int mode, int n_units, int bs, const int *rp, const int *col,
                           const T *val, const T *W, const T *x, const T *b, T *xo,
-                          cudaStream_t s) {
+                          cudaStream_t s, int64_t nnzb) {
+  if (n_units > 0 && mode != JAC_FIRST && warp_rows(n_units, bs, nnzb)) {
+    switch (mode) {
+      case JAC_SWEEP: return jac_warp_dispatch<T, JAC_SWEEP>(n_units, bs, rp, col, val, W, x, b, xo, s);
+      case JAC_APPLY: return jac_warp_dispatch<T, JAC_APPLY>(n_units, bs, rp, col, val, W, x, b, xo, s);
+      default: return jac_warp_dispatch<T, JAC_RELAX>(n_units, bs, rp, col, val, W, x, b, xo, s);
+    }
+  }
   switch (mode) {
     case JAC_SWEEP: return jac_dispatch<T, JAC_SWEEP>(n_units, bs, rp, col, val, W, x, b, xo, s);
     case JAC_FIRST: return jac_dispatch<T, JAC_FIRST>(n_units, bs, rp, col, val, W, x, b, xo, s);
@@ -261,10 +399,10 @@ cudaError_t launch_jacobi(int mode, int n_units, int bs, const int *rp, const in
 }
 template cudaError_t launch_jacobi<double>(int, int, int, const int *, const int *,
                                            const double *, const double *, const double *,
-                                           const double *, double *, cudaStream_t);
+                                           const double *, double *, cudaStream_t, int64_t);
 template cudaError_t launch_jacobi<float>(int, int, int, const int *, const int *,
                                           const float *, const float *, const float *,
-                                          const float *, float *, cudaStream_t);
+                                          const float *, float *, cudaStream_t, int64_t);
 
 // ----------------------------------------------------------------------------
 // multi-column relaxation x_c <- x_c - W A x_c (Eq. bsmooth), column per
@@ -314,7 +452,7 @@ cudaError_t launch_relax_multi(int n_units, int bs, const int *rp, const int *co
   if (th > 1024) return cudaErrorInvalidValue;
   dim3 grid(div_up(n_units, rpb), nc);
   relax_multi_kernel<<<grid, th, th * sizeof(double), s>>>(n_units, bs, rp, col, val, W, xin,
-                                                           xout);
+                                                           xout); note_launch();
   return cudaGetLastError();
 }
 
@@ -349,7 +487,7 @@ dense_mv_kernel(int n, const double *__restrict__ A, const T *__restrict__ x,
 template <typename T>
 cudaError_t launch_dense_mv(int n, const double *A, const T *x, T *y, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  dense_mv_kernel<T><<<div_up((long long)n * 32, 256), 256, 0, s>>>(n, A, x, y);
+  dense_mv_kernel<T><<<div_up((long long)n * 32, 256), 256, 0, s>>>(n, A, x, y); note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_dense_mv<double>(int, const double *, const double *, double *,

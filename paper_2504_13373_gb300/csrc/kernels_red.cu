@@ -2,10 +2,16 @@
 // reductions (fixed grid, fixed order: partial sums per CTA, then one CTA
 // sums the partials), fused CG updates, GMRES Arnoldi pieces, counter-based
 // random vectors and precision conversions.
+#include <atomic>
+
 #include "common.cuh"
 #include "internal.h"
 
 namespace gasa {
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 // ----------------------------------------------------------------------------
 // reductions
@@ -29,7 +35,7 @@ dot_partials_kernel(int64_t n, const double *__restrict__ x, const double *__res
 
 cudaError_t launch_dot_partials(int64_t n, const double *x, const double *y, double *partials,
                                 cudaStream_t s) {
-  dot_partials_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, y, partials);
+  dot_partials_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, y, partials); note_launch();
   return cudaGetLastError();
 }
 
@@ -49,7 +55,7 @@ colnorm_partials_kernel(int64_t n, const double *const *__restrict__ cols,
 cudaError_t launch_colnorm_partials(int64_t n, const double *const *cols, int nc,
                                     double *partials, cudaStream_t s) {
   if (nc == 0) return cudaSuccess;
-  colnorm_partials_kernel<<<dim3(kRedBlocks, nc), kRedThreads, 0, s>>>(n, cols, partials);
+  colnorm_partials_kernel<<<dim3(kRedBlocks, nc), kRedThreads, 0, s>>>(n, cols, partials); note_launch();
   return cudaGetLastError();
 }
 
@@ -62,7 +68,7 @@ finalize_kernel(const double *__restrict__ partials, double *__restrict__ out) {
 
 cudaError_t launch_finalize(const double *partials, int nc, double *out, cudaStream_t s) {
   if (nc == 0) return cudaSuccess;
-  finalize_kernel<<<nc, kRedThreads, 0, s>>>(partials, out);
+  finalize_kernel<<<nc, kRedThreads, 0, s>>>(partials, out); note_launch();
   return cudaGetLastError();
 }
 
@@ -73,7 +79,7 @@ __global__ void scale_inv_sqrt_kernel(int64_t n, double *x, const double *sumsq)
 }
 
 cudaError_t launch_scale_by_inv_sqrt(int64_t n, double *x, const double *sumsq, cudaStream_t s) {
-  scale_inv_sqrt_kernel<<<kRedBlocks, 256, 0, s>>>(n, x, sumsq);
+  scale_inv_sqrt_kernel<<<kRedBlocks, 256, 0, s>>>(n, x, sumsq); note_launch();
   return cudaGetLastError();
 }
 
@@ -101,7 +107,7 @@ __global__ void uniform_pm1_kernel(int64_t n, uint64_t key, double *x) {
 cudaError_t launch_uniform_pm1(int64_t n, uint64_t seed, uint64_t stream, double *x,
                                cudaStream_t s) {
   const uint64_t key = seed ^ (stream * 0x9E3779B97F4A7C15ull);
-  uniform_pm1_kernel<<<kRedBlocks, 256, 0, s>>>(n, key, x);
+  uniform_pm1_kernel<<<kRedBlocks, 256, 0, s>>>(n, key, x); note_launch();
   return cudaGetLastError();
 }
 
@@ -121,7 +127,7 @@ __global__ void normal_kernel(int64_t n, uint64_t key, double *x) {
 
 cudaError_t launch_normal(int64_t n, uint64_t seed, uint64_t stream, double *x, cudaStream_t s) {
   const uint64_t key = seed ^ (stream * 0x9E3779B97F4A7C15ull);
-  normal_kernel<<<kRedBlocks, 256, 0, s>>>(n, key, x);
+  normal_kernel<<<kRedBlocks, 256, 0, s>>>(n, key, x); note_launch();
   return cudaGetLastError();
 }
 
@@ -140,7 +146,7 @@ cudaError_t launch_convert(int64_t n, const Tin *in, Tout *out, cudaStream_t s) 
   if (n == 0) return cudaSuccess;
   int grid = div_up(n, 256);
   if (grid > 8 * kNumSM) grid = 8 * kNumSM;
-  convert_kernel<Tin, Tout><<<grid, 256, 0, s>>>(n, in, out);
+  convert_kernel<Tin, Tout><<<grid, 256, 0, s>>>(n, in, out); note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_convert<double, float>(int64_t, const double *, float *, cudaStream_t);
@@ -152,7 +158,7 @@ __global__ void fill_kernel(int64_t n, double v, double *x) {
 }
 cudaError_t launch_fill(int64_t n, double v, double *x, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  fill_kernel<<<kRedBlocks, 256, 0, s>>>(n, v, x);
+  fill_kernel<<<kRedBlocks, 256, 0, s>>>(n, v, x); note_launch();
   return cudaGetLastError();
 }
 
@@ -164,7 +170,7 @@ __global__ void axpy_kernel(int64_t n, double a, const double *__restrict__ x,
 }
 cudaError_t launch_axpy(int64_t n, double a, const double *x, double *y, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  axpy_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, a, x, y);
+  axpy_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, a, x, y); note_launch();
   return cudaGetLastError();
 }
 
@@ -180,7 +186,7 @@ __global__ void sub_kernel(int64_t n, const double *__restrict__ a, const double
 }
 cudaError_t launch_sub(int64_t n, const double *a, const double *b, double *out, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  sub_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, a, b, out);
+  sub_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, a, b, out); note_launch();
   return cudaGetLastError();
 }
 
@@ -215,16 +221,17 @@ cudaError_t launch_cg_update_xr(int64_t n, double *x, double *r, const double *p
                                 const double *q, const double *rz, const double *pq_partials,
                                 double *rr_partials, double *alpha_out, cudaStream_t s) {
   cg_update_xr_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, r, p, q, rz, pq_partials,
-                                                         rr_partials, alpha_out);
+                                                         rr_partials, alpha_out); note_launch();
   return cudaGetLastError();
 }
 
-// p = z + beta p, beta = rz_new / rz_old (flexible: (rz_new - r.z_old) / rz_old)
+// p = z + beta p, beta = rz_new / rz_old (flexible: (rz_new - r.z_old) / rz_old);
+// with zold_out the new z is also copied there for the next flexible step
 __global__ void __launch_bounds__(kRedThreads)
 cg_update_p_kernel(int64_t n, double *__restrict__ p, const double *__restrict__ z,
                    const double *__restrict__ rz_old, const double *__restrict__ rz_partials,
                    const double *__restrict__ rzold_partials, double *__restrict__ rz_out,
-                   int flexible) {
+                   int flexible, double *__restrict__ zold_out) {
   __shared__ double sh[32];
   const double rz_new = block_sum_partials(rz_partials, kRedBlocks, sh);
   double num = rz_new;
@@ -232,17 +239,53 @@ cg_update_p_kernel(int64_t n, double *__restrict__ p, const double *__restrict__
   const double beta = num / rz_old[0];
   if (blockIdx.x == 0 && threadIdx.x == 0) rz_out[0] = rz_new;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    p[i] = fma(beta, p[i], z[i]);
+  if (zold_out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      const double zi = z[i];
+      p[i] = fma(beta, p[i], zi);
+      zold_out[i] = zi;
+    }
+  } else {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+      p[i] = fma(beta, p[i], z[i]);
+  }
 }
 
 cudaError_t launch_cg_update_p(int64_t n, double *p, const double *z, const double *rz_old,
                                const double *rz_partials, const double *rzold_partials,
-                               double *rz_out, int flexible, cudaStream_t s) {
+                               double *rz_out, int flexible, cudaStream_t s, double *zold_out) {
   cg_update_p_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, p, z, rz_old, rz_partials,
-                                                        rzold_partials, rz_out, flexible);
+                                                        rzold_partials, rz_out, flexible, zold_out); note_launch();
   return cudaGetLastError();
 }
+
+// End of one graph-resident CG step: ||r||^2 from the partials, iteration
+// count, and the loop condition (continue while the recurrence residual is
+// above tol * ||b||, p^T A p > 0 and fewer than max_iter steps were taken).
+// scal: [0] r.r  [2] p.Ap  [3] rz (old)  [4] rz (new)  [9] ||b||  [10] tol
+__global__ void __launch_bounds__(kRedThreads)
+cg_check_kernel(const double *__restrict__ rr_partials, double *__restrict__ scal, int *iters,
+                int max_iter, cudaGraphConditionalHandle handle) {
+  __shared__ double sh[32];
+  const double rr = block_sum_partials(rr_partials, kRedBlocks, sh);
+  if (threadIdx.x == 0) {
+    scal[0] = rr;
+    const int k = ++iters[0];
+    const double pq = scal[2];
+    const double rel = sqrt(rr) / scal[9];
+    const bool cont = (rel > scal[10]) && (k < max_iter) && (pq > 0.0) && isfinite(rel);
+    scal[3] = scal[4];
+    cudaGraphSetConditional(handle, cont ? 1u : 0u);
+  }
+}
+
+cudaError_t launch_cg_check(const double *rr_partials, double *scal, int *iters, int max_iter,
+                            cudaGraphConditionalHandle handle, cudaStream_t s) {
+  cg_check_kernel<<<1, kRedThreads, 0, s>>>(rr_partials, scal, iters, max_iter, handle); note_launch();
+  return cudaGetLastError();
+}
+
+void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // ----------------------------------------------------------------------------
 // GMRES (classical Gram-Schmidt applied twice; basis V column-major)
@@ -263,7 +306,7 @@ multi_dot_kernel(int64_t n, const double *__restrict__ V, int64_t ldv,
 cudaError_t launch_multi_dot(int64_t n, const double *V, int64_t ldv, int k, const double *w,
                              double *partials, cudaStream_t s) {
   if (k == 0) return cudaSuccess;
-  multi_dot_kernel<<<dim3(kRedBlocks, k), kRedThreads, 0, s>>>(n, V, ldv, w, partials);
+  multi_dot_kernel<<<dim3(kRedBlocks, k), kRedThreads, 0, s>>>(n, V, ldv, w, partials); note_launch();
   return cudaGetLastError();
 }
 
@@ -281,7 +324,7 @@ multi_dot_finalize_kernel(const double *__restrict__ partials, double *__restric
 cudaError_t launch_multi_dot_finalize(const double *partials, int k, double *h, double *hacc,
                                       cudaStream_t s) {
   if (k == 0) return cudaSuccess;
-  multi_dot_finalize_kernel<<<k, kRedThreads, 0, s>>>(partials, h, hacc);
+  multi_dot_finalize_kernel<<<k, kRedThreads, 0, s>>>(partials, h, hacc); note_launch();
   return cudaGetLastError();
 }
 
@@ -298,7 +341,7 @@ __global__ void gs_update_kernel(int64_t n, const double *__restrict__ V, int64_
 cudaError_t launch_gs_update(int64_t n, const double *V, int64_t ldv, int k, const double *h,
                              double *w, cudaStream_t s) {
   if (k == 0 || n == 0) return cudaSuccess;
-  gs_update_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, V, ldv, k, h, w);
+  gs_update_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, V, ldv, k, h, w); note_launch();
   return cudaGetLastError();
 }
 
@@ -315,7 +358,7 @@ __global__ void normalize_into_kernel(int64_t n, const double *__restrict__ w,
 
 cudaError_t launch_normalize_into(int64_t n, const double *w, const double *sumsq, double *v,
                                   double *hout, cudaStream_t s) {
-  normalize_into_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, w, sumsq, v, hout);
+  normalize_into_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, w, sumsq, v, hout); note_launch();
   return cudaGetLastError();
 }
 
@@ -347,7 +390,7 @@ __global__ void gmres_givens_kernel(double *H, int ldh, int j, double *cs, doubl
 
 cudaError_t launch_gmres_givens(double *H, int ldh, int j, double *cs, double *sn, double *g,
                                 cudaStream_t s) {
-  gmres_givens_kernel<<<1, 32, 0, s>>>(H, ldh, j, cs, sn, g);
+  gmres_givens_kernel<<<1, 32, 0, s>>>(H, ldh, j, cs, sn, g); note_launch();
   return cudaGetLastError();
 }
 
@@ -363,7 +406,7 @@ __global__ void gmres_backsolve_kernel(const double *H, int ldh, int j, const do
 
 cudaError_t launch_gmres_backsolve(const double *H, int ldh, int j, const double *g, double *y,
                                    cudaStream_t s) {
-  gmres_backsolve_kernel<<<1, 32, 0, s>>>(H, ldh, j, g, y);
+  gmres_backsolve_kernel<<<1, 32, 0, s>>>(H, ldh, j, g, y); note_launch();
   return cudaGetLastError();
 }
 
@@ -380,7 +423,7 @@ __global__ void combine_kernel(int64_t n, const double *__restrict__ V, int64_t 
 cudaError_t launch_combine(int64_t n, const double *V, int64_t ldv, int k, const double *y,
                            double *x, cudaStream_t s) {
   if (k == 0 || n == 0) return cudaSuccess;
-  combine_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, V, ldv, k, y, x);
+  combine_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, V, ldv, k, y, x); note_launch();
   return cudaGetLastError();
 }
 

@@ -28,7 +28,7 @@ __global__ void max_int_kernel(int n, const int *__restrict__ x, int *out) {
 cudaError_t launch_max_int(int n, const int *x, int *out, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int), s);
   if (e != cudaSuccess || n == 0) return e;
-  max_int_kernel<<<kNumSM, 256, 0, s>>>(n, x, out);
+  max_int_kernel<<<kNumSM, 256, 0, s>>>(n, x, out); note_launch();
   return cudaGetLastError();
 }
 
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(1024) exclusive_scan_kernel(int n, const int *
 
 cudaError_t launch_exclusive_scan(int n, const int *in, int *out, int *scratch, cudaStream_t s) {
   (void)scratch;
-  exclusive_scan_kernel<<<1, 1024, 0, s>>>(n, in, out);
+  exclusive_scan_kernel<<<1, 1024, 0, s>>>(n, in, out); note_launch();
   return cudaGetLastError();
 }
 
@@ -196,7 +196,7 @@ cudaError_t launch_block_inverse(int n_units, int bs, const int *rp, const int *
     if (e != cudaSuccess) return e;
   }
   const int th = bs <= 8 ? 64 : (bs <= 24 ? 128 : 256);
-  block_inverse_kernel<<<n_units, th, sm, s>>>(n_units, bs, rp, col, val, scale, W, n_singular);
+  block_inverse_kernel<<<n_units, th, sm, s>>>(n_units, bs, rp, col, val, scale, W, n_singular); note_launch();
   return cudaGetLastError();
 }
 
@@ -206,7 +206,7 @@ __global__ void scale_kernel(int64_t n, double a, double *x) {
 }
 cudaError_t launch_scale(int64_t n, double a, double *x, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  scale_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, a, x);
+  scale_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, a, x); note_launch();
   return cudaGetLastError();
 }
 
@@ -241,11 +241,11 @@ cudaError_t build_children(int n_units, int n_agg, const int *agg_of, int *child
                            int *child_idx, int *scratch, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(int) * n_agg, s);
   if (e != cudaSuccess) return e;
-  count_children_kernel<<<kRedBlocks, 256, 0, s>>>(n_units, agg_of, scratch);
+  count_children_kernel<<<kRedBlocks, 256, 0, s>>>(n_units, agg_of, scratch); note_launch();
   if ((e = launch_exclusive_scan(n_agg, scratch, child_ptr, nullptr, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(scratch, 0, sizeof(int) * n_agg, s)) != cudaSuccess) return e;
-  fill_children_kernel<<<kRedBlocks, 256, 0, s>>>(n_units, agg_of, child_ptr, scratch, child_idx);
-  sort_segments_kernel<<<div_up(n_agg, 128), 128, 0, s>>>(n_agg, child_ptr, child_idx);
+  fill_children_kernel<<<kRedBlocks, 256, 0, s>>>(n_units, agg_of, child_ptr, scratch, child_idx); note_launch();
+  sort_segments_kernel<<<div_up(n_agg, 128), 128, 0, s>>>(n_agg, child_ptr, child_idx); note_launch();
   return cudaGetLastError();
 }
 
@@ -339,12 +339,60 @@ __global__ void tentative_kernel(int bs, const int *__restrict__ child_ptr,
     for (int l = threadIdx.x; l < r; l += blockDim.x)
       sigma[(size_t)J * r + l] = (l < rows) ? sv[order[l]] : 0.0;
   }
-  const double smax = sv[order[0]];
-  // kept vectors: normalise, sign so the largest |entry| (lowest row on ties) is positive
+  // normalise the kept columns (Hestenes columns are orthogonal relative to
+  // their own norms, so tiny singular values still give orthonormal vectors)
   for (int l = wid; l < s_next; l += nwarps) {
     const int c = order[l];
     const double sc = sv[c];
-    const bool ok = (l < rows) && sc > 0.0 && sc > smax * 1e-13;
+    if (l < rows && sc > 0.0) {
+      const double inv = 1.0 / sc;
+      double *gc = G + (size_t)c * rows;
+      for (int i = lane; i < rows; i += 32) gc[i] *= inv;
+    }
+  }
+  __syncthreads();
+  // an exactly zero column (candidate block of lower rank than the kept
+  // count) is completed by Gram-Schmidt of unit vectors against the kept ones
+  if (wid == 0) {
+    for (int l = 0; l < s_next && l < rows; ++l) {
+      const int c = order[l];
+      if (sv[c] > 0.0) continue;
+      double *gc = G + (size_t)c * rows;
+      bool done = false;
+      for (int t = 0; t < rows && !done; ++t) {
+        const int e = (l + t) % rows;
+        for (int i = lane; i < rows; i += 32) gc[i] = (i == e) ? 1.0 : 0.0;
+        __syncwarp();
+        for (int pass = 0; pass < 2; ++pass) {
+          for (int m = 0; m < l; ++m) {
+            const double *gm = G + (size_t)order[m] * rows;
+            double d = 0.0;
+            for (int i = lane; i < rows; i += 32) d = fma(gm[i], gc[i], d);
+            d = warp_sum(d);
+            for (int i = lane; i < rows; i += 32) gc[i] = fma(-d, gm[i], gc[i]);
+            __syncwarp();
+          }
+        }
+        double nn = 0.0;
+        for (int i = lane; i < rows; i += 32) nn = fma(gc[i], gc[i], nn);
+        nn = warp_sum(nn);
+        if (nn > 0.25) {
+          const double inv = 1.0 / sqrt(nn);
+          for (int i = lane; i < rows; i += 32) gc[i] *= inv;
+          done = true;
+        }
+        __syncwarp();
+      }
+      if (!done && lane == 0) atomicExch(status, 1);
+      if (lane == 0) sv[c] = -1.0;   // marks a completed column (kept as zero singular value)
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // sign so that the largest |entry| (lowest row on ties) is positive, then write
+  for (int l = wid; l < s_next; l += nwarps) {
+    const int c = order[l];
+    const bool ok = (l < rows);
     double best = -1.0;
     int bi = INT_MAX;
     const double *gc = G + (size_t)c * rows;
@@ -359,7 +407,7 @@ __global__ void tentative_kernel(int bs, const int *__restrict__ child_ptr,
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
     const double sgn = (ok && bi < rows && gc[bi] < 0.0) ? -1.0 : 1.0;
-    const double scl = ok ? sgn / sc : 0.0;
+    const double scl = ok ? sgn : 0.0;
     for (int i = lane; i < rows; i += 32) {
       const int ch = i / bs, d = i - ch * bs;
       const int unit = child_idx[c0 + ch];
@@ -382,7 +430,7 @@ cudaError_t launch_tentative(int bs, int n_agg, int max_children, const int *chi
   int pairs = (r + 1) / 2;
   int th = 32 * (pairs < 8 ? (pairs < 1 ? 1 : pairs) : 8);
   tentative_kernel<<<n_agg, th, sm, s>>>(bs, child_ptr, child_idx, B, ldb, r, s_next, T, sigma,
-                                         status);
+                                         status); note_launch();
   return cudaGetLastError();
 }
 
@@ -485,7 +533,7 @@ __global__ void cand_count_AB_kernel(int n, const int *__restrict__ Arp, const i
 cudaError_t launch_cand_count_AB(int n, const int *Arp, const int *Acol, const int *Brp, int *cand,
                                  cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  cand_count_AB_kernel<<<div_up(n, 256), 256, 0, s>>>(n, Arp, Acol, Brp, cand);
+  cand_count_AB_kernel<<<div_up(n, 256), 256, 0, s>>>(n, Arp, Acol, Brp, cand); note_launch();
   return cudaGetLastError();
 }
 
@@ -507,7 +555,7 @@ cudaError_t launch_pattern_P(int n, const int *Arp, const int *Acol, const int *
   const size_t sm = (size_t)ncap * sizeof(int);
   cudaError_t e = set_smem((const void *)pattern_P_kernel, sm);
   if (e != cudaSuccess) return e;
-  pattern_P_kernel<<<n, 128, sm, s>>>(n, Arp, Acol, agg, count, Prp, Pcol, ncap);
+  pattern_P_kernel<<<n, 128, sm, s>>>(n, Arp, Acol, agg, count, Prp, Pcol, ncap); note_launch();
   return cudaGetLastError();
 }
 
@@ -520,7 +568,7 @@ cudaError_t launch_pattern_AB(int n, const int *Arp, const int *Acol, const int 
   cudaError_t e = set_smem((const void *)pattern_AB_kernel, sm);
   if (e != cudaSuccess) return e;
   const int th = ncap >= 1024 ? 512 : 128;
-  pattern_AB_kernel<<<n, th, sm, s>>>(n, Arp, Acol, Brp, Bcol, count, Crp, Ccol, ncap);
+  pattern_AB_kernel<<<n, th, sm, s>>>(n, Arp, Acol, Brp, Bcol, count, Crp, Ccol, ncap); note_launch();
   return cudaGetLastError();
 }
 
@@ -584,7 +632,7 @@ cudaError_t launch_numeric_P(int n, int sk, int sn, const int *Arp, const int *A
   cudaError_t e = set_smem((const void *)numeric_P_kernel, sm);
   if (e != cudaSuccess) return e;
   const int th = sk * sn <= 64 ? 64 : (sk * sn <= 256 ? 128 : 256);
-  numeric_P_kernel<<<n, th, sm, s>>>(n, sk, sn, Arp, Acol, Aval, W, T, agg, Prp, Pcol, Pval);
+  numeric_P_kernel<<<n, th, sm, s>>>(n, sk, sn, Arp, Acol, Aval, W, T, agg, Prp, Pcol, Pval); note_launch();
   return cudaGetLastError();
 }
 
@@ -634,7 +682,7 @@ cudaError_t launch_numeric_AB(int n, int br, int bm, int bc, const int *Arp, con
   const int ne = br * bc;
   const int th = ne <= 64 ? 64 : (ne <= 128 ? 128 : 256);
   numeric_AB_kernel<<<n, th, 0, s>>>(n, br, bm, bc, Arp, Acol, Aval, Brp, Bcol, Bval, Crp, Ccol,
-                                     Cval);
+                                     Cval); note_launch();
   return cudaGetLastError();
 }
 
@@ -687,13 +735,13 @@ cudaError_t launch_transpose(int n_rows, int n_cols, int br, int bc, const int *
   if (e != cudaSuccess) return e;
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(cnt, 0, sizeof(int) * n_cols, s)) != cudaSuccess) return e;
-  if (nnzb > 0) tr_count_kernel<<<kRedBlocks, 256, 0, s>>>(nnzb, Pcol, cnt);
+  if (nnzb > 0) tr_count_kernel<<<kRedBlocks, 256, 0, s>>>(nnzb, Pcol, cnt); note_launch();
   if ((e = launch_exclusive_scan(n_cols, cnt, Rrp, nullptr, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(cnt, 0, sizeof(int) * n_cols, s)) != cudaSuccess) return e;
-  tr_fill_kernel<<<div_up(n_rows, 256), 256, 0, s>>>(n_rows, Prp, Pcol, Rrp, cnt, Rcol, src);
-  tr_sort_kernel<<<div_up(n_cols, 128), 128, 0, s>>>(n_cols, Rrp, Rcol, src);
+  tr_fill_kernel<<<div_up(n_rows, 256), 256, 0, s>>>(n_rows, Prp, Pcol, Rrp, cnt, Rcol, src); note_launch();
+  tr_sort_kernel<<<div_up(n_cols, 128), 128, 0, s>>>(n_cols, Rrp, Rcol, src); note_launch();
   if (nnzb > 0)
-    tr_values_kernel<<<kRedBlocks * 4, 256, 0, s>>>(nnzb, br, bc, src, Pval, Rval);
+    tr_values_kernel<<<kRedBlocks * 4, 256, 0, s>>>(nnzb, br, bc, src, Pval, Rval); note_launch();
   return cudaGetLastError();
 }
 
@@ -719,7 +767,7 @@ cudaError_t launch_bsr_to_dense(int n, int bs, const int *rp, const int *col, co
   const size_t N = (size_t)n * bs;
   cudaError_t e = cudaMemsetAsync(D, 0, N * N * sizeof(double), s);
   if (e != cudaSuccess || n == 0) return e;
-  bsr_to_dense_kernel<<<n, 128, 0, s>>>(n, bs, rp, col, val, D);
+  bsr_to_dense_kernel<<<n, 128, 0, s>>>(n, bs, rp, col, val, D); note_launch();
   return cudaGetLastError();
 }
 
@@ -810,17 +858,17 @@ cudaError_t launch_dense_inverse(int n, const double *A, double *Ainv, double *w
   double *colk = work + (size_t)2 * n * n;  // n
   cudaError_t e = cudaMemsetAsync(singular, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  gj_init_kernel<<<kRedBlocks * 4, 256, 0, s>>>(n, A, M);
+  gj_init_kernel<<<kRedBlocks * 4, 256, 0, s>>>(n, A, M); note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const double thresh = 1e-300;
   for (int k = 0; k < n; ++k) {
-    gj_pivot_kernel<<<1, 1024, 0, s>>>(n, M, k, colk, thresh, singular);
+    gj_pivot_kernel<<<1, 1024, 0, s>>>(n, M, k, colk, thresh, singular); note_launch();
     const long long work_items = (long long)n * (2LL * n - k);
     int grid = div_up(work_items, 256);
     if (grid > kRedBlocks * 8) grid = kRedBlocks * 8;
-    gj_elim_kernel<<<grid, 256, 0, s>>>(n, M, k, colk);
+    gj_elim_kernel<<<grid, 256, 0, s>>>(n, M, k, colk); note_launch();
   }
-  gj_extract_kernel<<<kRedBlocks * 4, 256, 0, s>>>(n, M, Ainv);
+  gj_extract_kernel<<<kRedBlocks * 4, 256, 0, s>>>(n, M, Ainv); note_launch();
   return cudaGetLastError();
 }
 

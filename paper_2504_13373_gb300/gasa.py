@@ -41,7 +41,7 @@ EXPORTS = [
     "gasa_level_shape", "gasa_get_level", "gasa_profile_enable", "gasa_profile_read",
     "gasa_destroy", "gasa_status_string", "gasa_last_error", "gasa_bsr_mv", "gasa_bsr_mv_f32",
     "gasa_jacobi_sweep", "gasa_jacobi_sweep_f32", "gasa_block_inverse", "gasa_power_estimate",
-    "gasa_relax_candidates", "gasa_tentative", "gasa_dense_inverse",
+    "gasa_relax_candidates", "gasa_tentative", "gasa_dense_inverse", "gasa_kernel_launches",
 ]
 
 c_i32, c_i64, c_dbl, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
@@ -98,9 +98,11 @@ def load():
     L.gasa_status_string.restype = ctypes.c_char_p
     L.gasa_last_error.restype = ctypes.c_char_p
     L.gasa_default_options.restype = None
+    L.gasa_kernel_launches.restype = ctypes.c_int64
     for name in EXPORTS:
         f = getattr(L, name)
-        if name not in ("gasa_status_string", "gasa_last_error", "gasa_default_options"):
+        if name not in ("gasa_status_string", "gasa_last_error", "gasa_default_options",
+                        "gasa_kernel_launches"):
             f.restype = ctypes.c_int
     _lib = L
     return L
@@ -237,6 +239,10 @@ def gasa_profile_read(ctx, kernel_class):
 
 def gasa_destroy(ctx):
     _check(load().gasa_destroy(ctx))
+
+
+def gasa_kernel_launches():
+    return int(load().gasa_kernel_launches())
 
 
 # single operations -------------------------------------------------------------

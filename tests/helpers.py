@@ -18,13 +18,20 @@ def problem(name: str):
     if name == "p3_16":
         return configs.poisson2d_p3(n=16)
     if name == "tet_p2_4":
-        return configs.poisson3d_p2(n=4)
+        # 384 tets: levels L0..L2 (a third coarsening would leave one aggregate)
+        return configs.poisson3d(4, 2, r=80, n_levels=3, name="tet_p2_4")
     if name == "tet_p2_6":
         return configs.poisson3d(6, 2, r=80, n_levels=4, name="tet_p2_6")
     if name == "tiny":
         return configs.poisson2d(8, 1, r=12, n_levels=3, name="tiny")
     if name == "c2":
         return configs.poisson2d_p3()
+    if name == "cd_q2_16":
+        return configs.convdiff2d_q2(n=16, peclet=100.0)
+    if name == "cd_q2_32_pe1e4":
+        return configs.convdiff2d_q2(n=32, peclet=1e4)
+    if name == "cd_q2_32_pe1":
+        return configs.convdiff2d_q2(n=32, peclet=1.0)
     raise KeyError(name)
 
 
@@ -58,9 +65,10 @@ def gpu_setup(name: str, keep: bool = True, **opt_kw):
     pr = problem(name)
     A = pr.A
     ctx = gasa.gasa_create(0)
-    opt = gasa.gasa_default_options(dim=pr.dim, n_cand=pr.r, keep_setup_data=1 if keep else 0,
-                                    solver=gasa.GASA_SOLVER_CG if pr.solver == "cg" else gasa.GASA_SOLVER_GMRES,
-                                    **opt_kw)
+    kw = dict(dim=pr.dim, n_cand=pr.r, keep_setup_data=1 if keep else 0,
+              solver=gasa.GASA_SOLVER_CG if pr.solver == "cg" else gasa.GASA_SOLVER_GMRES)
+    kw.update(opt_kw)
+    opt = gasa.gasa_default_options(**kw)
     info = gasa.gasa_setup(ctx, A.row_ptr, A.col, A.val.ravel(), A.b, pr.agg_of, opt,
                            adj_ptr=pr.adj_ptr, adj_idx=pr.adj_idx, centroids=pr.centroids,
                            init_candidates=pr.B0)

@@ -1,0 +1,127 @@
+"""The C ABI library builds, loads and exports every symbol include/gasa.h
+declares; the Python binding's structures match the C layouts; the binding
+fails loudly without the library.  No GPU work here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gasa.h")
+
+
+def _lib():
+    from paper_2504_13373_gb300 import build, gasa
+    if not os.path.exists(gasa.LIB_PATH):
+        build.build()
+    return gasa
+
+
+def header_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return set(re.findall(r"^\s*(?:gasa_status|void|const char \*|int64_t)\s*(gasa_\w+)\s*\(", src, re.M))
+
+
+def test_header_declares_the_binding_exports():
+    gasa = _lib()
+    assert header_functions() == set(gasa.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    gasa = _lib()
+    out = subprocess.run(["nm", "-D", "--defined-only", gasa.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    syms = {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+    missing = header_functions() - syms
+    assert not missing, missing
+    L = gasa.load()
+    for name in header_functions():
+        getattr(L, name)
+
+
+C_LAYOUT = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "gasa.h"
+#define P(T, f) printf(#T "." #f " %zu\n", offsetof(T, f))
+int main(void) {
+  printf("gasa_bsr %zu\n", sizeof(gasa_bsr));
+  printf("gasa_hierarchy %zu\n", sizeof(gasa_hierarchy));
+  printf("gasa_options %zu\n", sizeof(gasa_options));
+  printf("gasa_setup_info %zu\n", sizeof(gasa_setup_info));
+  printf("gasa_solve_info %zu\n", sizeof(gasa_solve_info));
+  P(gasa_options, gamma); P(gasa_options, seed); P(gasa_options, init_candidates);
+  P(gasa_setup_info, omega); P(gasa_setup_info, seconds); P(gasa_setup_info, device_bytes);
+  P(gasa_bsr, val); P(gasa_bsr, on_device); P(gasa_solve_info, rel_residual);
+  return 0;
+}
+"""
+
+
+def test_struct_layouts_match_c(tmp_path):
+    gasa = _lib()
+    src = tmp_path / "layout.c"
+    src.write_text(C_LAYOUT)
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(ln.rsplit(" ", 1) for ln in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                          check=True).stdout.splitlines())
+    py = {
+        "gasa_bsr": ctypes.sizeof(gasa.gasa_bsr),
+        "gasa_hierarchy": ctypes.sizeof(gasa.gasa_hierarchy),
+        "gasa_options": ctypes.sizeof(gasa.gasa_options),
+        "gasa_setup_info": ctypes.sizeof(gasa.gasa_setup_info),
+        "gasa_solve_info": ctypes.sizeof(gasa.gasa_solve_info),
+        "gasa_options.gamma": gasa.gasa_options.gamma.offset,
+        "gasa_options.seed": gasa.gasa_options.seed.offset,
+        "gasa_options.init_candidates": gasa.gasa_options.init_candidates.offset,
+        "gasa_setup_info.omega": gasa.gasa_setup_info.omega.offset,
+        "gasa_setup_info.seconds": gasa.gasa_setup_info.seconds.offset,
+        "gasa_setup_info.device_bytes": gasa.gasa_setup_info.device_bytes.offset,
+        "gasa_bsr.val": gasa.gasa_bsr.val.offset,
+        "gasa_bsr.on_device": gasa.gasa_bsr.on_device.offset,
+        "gasa_solve_info.rel_residual": gasa.gasa_solve_info.rel_residual.offset,
+    }
+    for k, v in py.items():
+        assert int(got[k]) == v, k
+
+
+def test_status_strings_and_host_only_calls():
+    gasa = _lib()
+    assert gasa.gasa_status_string(0) == "ok"
+    assert "not converged" in gasa.gasa_status_string(gasa.GASA_ERR_NOT_CONVERGED)
+    assert gasa.gasa_status_string(999) == "unknown status"
+    assert gasa.gasa_kernel_launches() >= 0
+
+
+def test_binding_fails_loudly_without_library(monkeypatch):
+    from paper_2504_13373_gb300 import gasa
+    monkeypatch.setattr(gasa, "_lib", None)
+    monkeypatch.setattr(gasa, "LIB_PATH", os.path.join(ROOT, "no_such_libgasa.so"))
+    with pytest.raises(RuntimeError):
+        gasa.load()
+
+
+def test_create_without_gpu_reports_error():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    gasa = _lib()
+    with pytest.raises(gasa.GasaError):
+        gasa.gasa_create(0)
+
+
+def test_single_ops_validate_before_device_work():
+    gasa = _lib()
+    L = gasa.load()
+    # invalid sizes are rejected on the host without touching the device
+    assert L.gasa_bsr_mv(7, 1, 1, 1, None, None, None, None, None, None, None) == gasa.GASA_ERR_INVALID_ARG
+    assert L.gasa_bsr_mv(0, -1, 1, 1, None, None, None, None, None, None, None) == gasa.GASA_ERR_INVALID_ARG
+    assert L.gasa_jacobi_sweep(4, 0, None, None, None, None, None, None, None, 0, None) == gasa.GASA_ERR_INVALID_ARG
+    assert L.gasa_tentative(4, 3, 9, None, None, 4, 2, None, None, None) == gasa.GASA_ERR_INVALID_ARG
+    assert L.gasa_dense_inverse(0, None, None, None, None) == gasa.GASA_ERR_INVALID_ARG
+    assert L.gasa_setup(None, None, None, None, None, None, None, None) == gasa.GASA_ERR_INVALID_ARG
+    assert L.gasa_solve(None, None, None, ctypes.c_double(1e-10), 0, 0, None) == gasa.GASA_ERR_INVALID_ARG

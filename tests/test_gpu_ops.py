@@ -34,6 +34,12 @@ CASES_MV = [
     (83, 300, 4, 10, 9, 4),       # restriction-shaped
     (97, 61, 13, 17, 5, 5),       # wider than the templated sizes (generic path)
     (1, 1, 1, 1, 1, 6),           # smallest
+    # long rows (>= 12 blocks on average): one warp per block row
+    (203, 150, 4, 4, 20, 7),
+    (100, 300, 5, 10, 24, 8),
+    (64, 64, 36, 36, 16, 9),      # 36-row blocks: two rows per lane
+    (50, 40, 13, 17, 30, 10),
+    (33, 900, 4, 10, 70, 11),     # restriction-shaped, more blocks than lanes
 ]
 
 
@@ -54,7 +60,7 @@ def test_bsr_mv_fp64(case, mode):
     assert rel_err(to_host(y), want) <= TOL64
 
 
-@pytest.mark.parametrize("case", CASES_MV[:5])
+@pytest.mark.parametrize("case", CASES_MV[:5] + CASES_MV[6:9])
 def test_bsr_mv_fp32(case):
     gasa = _gasa()
     n, m, br, bc, per, seed = case
@@ -82,8 +88,8 @@ def test_bsr_mv_workload_matrix():
         assert rel_err(to_host(y), want) <= TOL64
 
 
-def _jacobi_inputs(n, bs, seed):
-    ptr, col, val = RO.random_bsr(n, n, bs, bs, 4, seed, diag=True)
+def _jacobi_inputs(n, bs, seed, per_row=4):
+    ptr, col, val = RO.random_bsr(n, n, bs, bs, per_row, seed, diag=True)
     val = RO.diagonally_dominant(ptr, col, val)
     W = RO.random_blocks(n, bs, seed)
     x = RO.random_vector(n * bs, seed)
@@ -91,10 +97,12 @@ def _jacobi_inputs(n, bs, seed):
     return ptr, col, val, W, x, b
 
 
-@pytest.mark.parametrize("n,bs,seed", [(1031, 3, 11), (517, 10, 12), (129, 17, 13), (77, 40, 14)])
-def test_jacobi_sweep_fp64(n, bs, seed):
+@pytest.mark.parametrize("n,bs,seed,per_row", [
+    (1031, 3, 11, 4), (517, 10, 12, 4), (129, 17, 13, 4), (77, 40, 14, 4),
+    (301, 4, 15, 20), (97, 13, 16, 40), (40, 36, 17, 30)])   # last three: warp per block row
+def test_jacobi_sweep_fp64(n, bs, seed, per_row):
     gasa = _gasa()
-    ptr, col, val, W, x, b = _jacobi_inputs(n, bs, seed)
+    ptr, col, val, W, x, b = _jacobi_inputs(n, bs, seed, per_row)
     A = bsr_scipy(ptr, col, val)
     Wd = O.BlockDiag(np.arange(n + 1) * bs, W)
     want = O.smooth_step(x, A, Wd, b)
@@ -107,10 +115,11 @@ def test_jacobi_sweep_fp64(n, bs, seed):
     assert rel_err(to_host(out), want_first) <= TOL64
 
 
-@pytest.mark.parametrize("n,bs,seed", [(1031, 3, 11), (517, 10, 12), (129, 17, 13)])
-def test_jacobi_sweep_fp32(n, bs, seed):
+@pytest.mark.parametrize("n,bs,seed,per_row", [(1031, 3, 11, 4), (517, 10, 12, 4), (129, 17, 13, 4),
+                                               (301, 4, 15, 20)])
+def test_jacobi_sweep_fp32(n, bs, seed, per_row):
     gasa = _gasa()
-    ptr, col, val, W, x, b = _jacobi_inputs(n, bs, seed)
+    ptr, col, val, W, x, b = _jacobi_inputs(n, bs, seed, per_row)
     A = bsr_scipy(ptr, col, val)
     want = O.smooth_step(x, A, O.BlockDiag(np.arange(n + 1) * bs, W), b)
     out = to_dev(np.zeros(n * bs, np.float32))

@@ -39,7 +39,7 @@ def _level_bsr(gasa, ctx, k, which, sh, br, bc, nrows):
     return rp, col, val
 
 
-@pytest.mark.parametrize("name", ["tiny", "c1", "p3_16", "tet_p2_4"])
+@pytest.mark.parametrize("name", ["tiny", "c1", "p3_16", "tet_p2_4", "cd_q2_16"])
 def test_setup_hierarchy(name):
     gasa = _gasa()
     H = oracle_setup(name)
@@ -84,7 +84,7 @@ def test_setup_hierarchy(name):
         gasa.gasa_destroy(ctx)
 
 
-@pytest.mark.parametrize("name", ["tiny", "c1", "tet_p2_4"])
+@pytest.mark.parametrize("name", ["tiny", "c1", "tet_p2_4", "cd_q2_16"])
 def test_vcycle(name):
     gasa = _gasa()
     H = oracle_setup(name)
@@ -132,7 +132,7 @@ def test_cg_solve(name):
         gasa.gasa_destroy(ctx)
 
 
-@pytest.mark.parametrize("name", ["tiny", "c1"])
+@pytest.mark.parametrize("name", ["tiny", "c1", "cd_q2_16", "cd_q2_32_pe1e4", "cd_q2_32_pe1"])
 def test_gmres_solve(name):
     gasa = _gasa()
     H = oracle_setup(name)
@@ -150,5 +150,31 @@ def test_gmres_solve(name):
         info32 = gasa.gasa_solve(ctx, pr.rhs, xm, TOL, gasa.GASA_PREC_MIXED32)
         assert info32.converged and info32.rel_residual <= TOL
         assert abs(info32.iterations - ref32.iterations) <= 1, (info32.iterations, ref32.iterations)
+    finally:
+        gasa.gasa_destroy(ctx)
+
+
+@pytest.mark.parametrize("name", ["c1", "p3_16"])
+def test_graph_solve_equals_host_loop(name):
+    """The CG loop captured in one CUDA graph (device-side stopping test)
+    runs the same kernels in the same order as the host-driven loop, so the
+    iterates agree bit for bit."""
+    gasa = _gasa()
+    pr = problem(name)
+    ctx, _ = gpu_setup(name, keep=False)
+    try:
+        for prec in (gasa.GASA_PREC_FP64, gasa.GASA_PREC_MIXED32):
+            xg = np.zeros_like(pr.rhs)
+            ig = gasa.gasa_solve(ctx, pr.rhs, xg, TOL, prec)
+            gasa.gasa_profile_enable(ctx, True)          # profiling selects the host-driven loop
+            xh = np.zeros_like(pr.rhs)
+            ih = gasa.gasa_solve(ctx, pr.rhs, xh, TOL, prec)
+            gasa.gasa_profile_enable(ctx, False)
+            assert ig.iterations == ih.iterations
+            assert np.array_equal(xg, xh)
+            # solving twice gives the same bits (deterministic reductions)
+            xg2 = np.zeros_like(pr.rhs)
+            gasa.gasa_solve(ctx, pr.rhs, xg2, TOL, prec)
+            assert np.array_equal(xg, xg2)
     finally:
         gasa.gasa_destroy(ctx)
