@@ -25,6 +25,10 @@ notes as well):
 * left singular vectors are ordered by descending singular value and each
   kept column is signed so that its entry of largest magnitude (lowest row
   on ties) is positive;
+* a kept singular value at or below 1e-10 sigma_1 counts as zero (the
+  candidate block has lower numerical rank than the kept count); its vector
+  is replaced by the Gram-Schmidt completion of unit vectors described in
+  `complete_null_columns`;
 * Alg. 2's post-smoothing right-hand side is the level right-hand side b_k;
 * Alg. 4's start vector is uniform(-1, 1) per entry from splitmix64 stream
   4 + 16 k (level k), normalised;
@@ -214,6 +218,34 @@ def keep_count(rows: int, r: int, n_cut: float) -> int:
     return int(min(max(1, int(np.floor(rows / n_cut))), r, rows))
 
 
+NULL_SIGMA = 1e-10
+
+
+def complete_null_columns(U: np.ndarray, S: np.ndarray, s: int) -> np.ndarray:
+    """Kept columns whose singular value is numerically zero
+    (sigma_l <= NULL_SIGMA * sigma_1) carry no information from the
+    candidates; they are replaced, in order, by unit vectors e_t
+    (t = l, l+1, ... cyclically) orthogonalised twice against the columns
+    already fixed, the first with norm above 1/2 being kept."""
+    rows = U.shape[0]
+    U = U[:, :s].copy()
+    smax = S[0] if S.size else 0.0
+    for l in range(s):
+        if l < S.size and S[l] > NULL_SIGMA * smax:
+            continue
+        for t in range(rows):
+            v = np.zeros(rows)
+            v[(l + t) % rows] = 1.0
+            for _ in range(2):
+                for m in range(l):
+                    v = v - (U[:, m] @ v) * U[:, m]
+            nv = np.linalg.norm(v)
+            if nv * nv > 0.25:
+                U[:, l] = v / nv
+                break
+    return U
+
+
 def sign_fix(U: np.ndarray) -> np.ndarray:
     U = U.copy()
     for c in range(U.shape[1]):
@@ -244,7 +276,7 @@ def tentative(B: np.ndarray, agg: np.ndarray, unit_ptr: np.ndarray, n_agg: int,
         BJ = B[rows[J], :]
         U, S, _ = np.linalg.svd(BJ, full_matrices=False)
         s = keep_count(len(rows[J]), r, n_cut) if keep is None else keep[J]
-        Us.append(sign_fix(U[:, :s]))
+        Us.append(sign_fix(complete_null_columns(U, S, s)))
         svals.append(S)
         cols_ptr[J + 1] = cols_ptr[J] + s
     n_rows = unit_ptr[-1]

@@ -342,3 +342,23 @@ def test_stationary_solver(tiny):
     pr, H = tiny
     res = O.stationary(H, pr.rhs, 1e-8, 400)
     assert res.converged
+
+
+def test_null_singular_vectors_completed_deterministically():
+    """A rank-1 block (every candidate column a multiple of e_0) keeping two
+    vectors: the first is e_0, the second (zero singular value) is the
+    Gram-Schmidt completion of e_1 against e_0, i.e. e_1."""
+    rows, r = 4, 3
+    B = np.zeros((rows, r))
+    B[0, :] = [2.0, -1.0, 0.5]
+    T, ptr, sv = O.tentative(B, np.zeros(1, dtype=np.int64), np.array([0, rows]), 1, 1.0, keep=[2])
+    Td = T.toarray()
+    np.testing.assert_allclose(Td[:, 0], [1, 0, 0, 0], atol=1e-15)
+    np.testing.assert_allclose(Td[:, 1], [0, 1, 0, 0], atol=1e-15)
+    # rank 2 with s = 3: the completion is orthogonal to the two real vectors
+    B = RO.random_normal(6 * 2, 3).reshape(6, 2) @ RO.random_normal(2 * 5, 4).reshape(2, 5)
+    T, _, sv = O.tentative(B, np.zeros(1, dtype=np.int64), np.array([0, 6]), 1, 1.0, keep=[3])
+    Td = T.toarray()
+    assert sv[0][2] <= 1e-10 * sv[0][0]
+    assert np.max(np.abs(Td.T @ Td - np.eye(3))) <= 1e-14
+    assert np.max(np.abs(Td[:, :2] @ (Td[:, :2].T @ B) - B)) <= 1e-12 * np.max(np.abs(B))
