@@ -253,6 +253,28 @@ gasa_status gasa_tentative(int32_t n_units, int32_t bs, int32_t n_agg, const int
                            const double *B, int32_t r, int32_t s_next, double *T_out,
                            double *sigma_out, void *stream);
 
+/* Allocation-free variant of gasa_power_estimate, for callers that cannot
+ * allocate device memory when they run this step (a fixed device-memory
+ * budget after start-up, an allocator owned by a host framework, or serving
+ * code that must not block on or fail in the allocator).  It computes the
+ * same estimate with the same arguments, but its scratch (two vectors,
+ * reduction partials, scalars) lives in a fixed device array inside the
+ * library: about 4.2 MB on every device that loads the library, held until
+ * the process exits.  The paper has no counterpart to this entry point.
+ *  - n_units * bs must not exceed GASA_NOALLOC_MAX_DOFS, else
+ *    GASA_ERR_INVALID_ARG is returned before any device work;
+ *  - it calls no cudaMalloc, cudaFree or other allocating routine;
+ *  - the first call on a device looks up the array's device address (once
+ *    per device, with that device current) and should come before any stream
+ *    capture on that device;
+ *  - all calls on a device share the array; calls that overlap on the GPU
+ *    (different streams or host threads) race on it and must be avoided. */
+#define GASA_NOALLOC_MAX_DOFS 262144
+gasa_status gasa_power_estimate_noalloc(int32_t n_units, int32_t bs, const int32_t *row_ptr,
+                                        const int32_t *col, const double *val,
+                                        const double *Dinv, const double *x0, int32_t q,
+                                        double *rho, void *stream);
+
 /* Dense inverse (Gauss-Jordan, partial pivoting) of the n x n row-major
  * device matrix A into Ainv (device); the coarsest solve u_N = A_N^{-1} b_N
  * of Alg. 2.  *singular (host) is set to 1 if a pivot vanishes. */

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libgasa.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]
-SOURCES = ["kernels_mv.cu", "kernels_red.cu", "kernels_setup.cu", "gasa_api.cu"]
+SOURCES = ["kernels_mv.cu", "kernels_red.cu", "kernels_setup.cu", "gasa_api.cu", "noalloc.cu"]
 
 
 def nvcc():

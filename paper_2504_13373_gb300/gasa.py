@@ -42,7 +42,9 @@ EXPORTS = [
     "gasa_destroy", "gasa_status_string", "gasa_last_error", "gasa_bsr_mv", "gasa_bsr_mv_f32",
     "gasa_jacobi_sweep", "gasa_jacobi_sweep_f32", "gasa_block_inverse", "gasa_power_estimate",
     "gasa_relax_candidates", "gasa_tentative", "gasa_dense_inverse", "gasa_kernel_launches",
+    "gasa_power_estimate_noalloc",
 ]
+GASA_NOALLOC_MAX_DOFS = 262144
 
 c_i32, c_i64, c_dbl, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 
@@ -289,6 +291,18 @@ def gasa_power_estimate(n_units, bs, row_ptr, col, val, Dinv, x0, q, stream=None
                                       c_vp(_ptr(col)), c_vp(_ptr(val)), c_vp(_ptr(Dinv)),
                                       c_vp(_ptr(x0)), c_i32(q), ctypes.byref(rho),
                                       c_vp(_stream(stream))))
+    return rho.value
+
+
+def gasa_power_estimate_noalloc(n_units, bs, row_ptr, col, val, Dinv, x0, q, stream=None):
+    """gasa_power_estimate without any device allocation: the scratch is a
+    fixed array inside the library (n_units * bs <= GASA_NOALLOC_MAX_DOFS),
+    for callers that must not allocate when they run this step."""
+    rho = c_dbl()
+    _check(load().gasa_power_estimate_noalloc(c_i32(n_units), c_i32(bs), c_vp(_ptr(row_ptr)),
+                                              c_vp(_ptr(col)), c_vp(_ptr(val)), c_vp(_ptr(Dinv)),
+                                              c_vp(_ptr(x0)), c_i32(q), ctypes.byref(rho),
+                                              c_vp(_stream(stream))))
     return rho.value
 
 
