@@ -38,7 +38,8 @@ FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes per launch of the level-0 FP32 block-Jacobi sweep from one ncu
 # capture, valid while the kernel source below hashes to `src_sha`.
-NCU_TRAFFIC = {"kernel": "jacobi_kernel<float,10,0>", "src_sha": None, "bytes_per_launch": None}
+NCU_TRAFFIC = {"kernel": "jacobi_kernel<float,10,0>", "src_sha": "b62da9e6ef1d427e",
+               "bytes_per_launch": 274.86e6 + 3.71e6}
 
 
 def src_hash():
@@ -58,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-run", action="store_true",
                     help="one mixed solve only (for an ncu launch list); prints no bench line")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="with --profile-run: drive the CG loop from the host (per-kernel ncu)")
     return ap.parse_args()
 
 
@@ -66,6 +69,17 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(v, dist, device=None):
+    """The slowest rank's time (every rank gets it); `dist` is
+    torch.distributed or None for one process."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def build_problem(n):
@@ -279,13 +293,14 @@ def ours_main(args, rank, world, local):
         ms = ev0.elapsed_time(ev1)
         per_ms = [a.elapsed_time(bb) for a, bb in per]
         barrier()
-        if dist is not None:
-            t = torch.tensor([ms], device=f"cuda:{local}")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist, f"cuda:{local}")
         return ms, infos, launches, per_ms
 
     if args.profile_run:
+        if args.host_loop:
+            # kernel nodes inside a graph with conditional nodes cannot be
+            # profiled one by one; the host-driven loop runs the same kernels
+            gasa.gasa_profile_enable(ctx, True)
         for _ in range(max(1, args.steps)):
             gasa.gasa_solve(ctx, b_dev, x_dev, TOL, gasa.GASA_PREC_MIXED32, on_device=True)
         torch.cuda.synchronize()
@@ -298,6 +313,7 @@ def ours_main(args, rank, world, local):
     with ClockSampler(local) as clk:
         ms_mix, inf_mix, launches, per_mix = timed(gasa.GASA_PREC_MIXED32, args.steps)
         ms_64, inf_64, _, per_64 = timed(gasa.GASA_PREC_FP64, args.steps)
+        ms_16, inf_16, _, per_16 = timed(gasa.GASA_PREC_MIXED16, args.steps)
         # roofline of the dominant kernel: one more mixed solve with CUDA events
         # around every level-0 sweep (events cannot sit inside the solve graph,
         # so this solve runs the same kernels from the host-driven loop)
@@ -315,11 +331,7 @@ def ours_main(args, rank, world, local):
     for _ in range(args.steps):
         inf_e2e = gasa.gasa_solve(ctx, b_pin, x_pin, TOL, gasa.GASA_PREC_MIXED32, on_device=False)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, f"cuda:{local}")
     rel_host = float(np.linalg.norm(pr.rhs - A.to_scipy() @ x_pin.numpy()) / np.linalg.norm(pr.rhs))
 
     value = world * args.steps / (ms_mix / 1e3)
@@ -354,6 +366,10 @@ def ours_main(args, rank, world, local):
                          "fp64": max(i.rel_residual for i in inf_64), "e2e_host_check": rel_host},
         "fp64": {"value": value64, "unit": "solves/s", "ms_per_step": ms_64 / args.steps,
                  "p50_ms": float(np.percentile(per_64, 50)), "p99_ms": float(np.percentile(per_64, 99))},
+        "mixed16": {"value": world * args.steps / (ms_16 / 1e3), "unit": "solves/s",
+                    "ms_per_step": ms_16 / args.steps, "iterations": [i.iterations for i in inf_16],
+                    "rel_residual": max(i.rel_residual for i in inf_16),
+                    "storage": "level-0 A and wD^-1 as FP16 blocks with one FP32 scale per block"},
         "p50_ms": float(np.percentile(per_mix, 50)),
         "p99_ms": float(np.percentile(per_mix, 99)),
         "setup_s": sinfo.seconds,

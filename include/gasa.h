@@ -51,7 +51,11 @@ typedef enum {
 } gasa_status;
 
 enum { GASA_SOLVER_CG = 0, GASA_SOLVER_GMRES = 1 };
-enum { GASA_PREC_FP64 = 0, GASA_PREC_MIXED32 = 1 };
+/* FP64: FP64 V-cycle.  MIXED32: FP32 V-cycle (FP32 storage and arithmetic)
+ * inside FP64 flexible CG / FGMRES.  MIXED16: as MIXED32, with the level-0
+ * operator and block inverses stored as FP16 blocks with one FP32 scale per
+ * block (arithmetic FP32).  The coarsest solve is FP64 in every mode. */
+enum { GASA_PREC_FP64 = 0, GASA_PREC_MIXED32 = 1, GASA_PREC_MIXED16 = 2 };
 enum { GASA_CAND_R = 0, GASA_CAND_TT = 1 };
 enum { GASA_MV_ASSIGN = 0, GASA_MV_RESIDUAL = 1, GASA_MV_ADD = 2 };
 
@@ -96,6 +100,9 @@ typedef struct {
   double n_cut;              /* Eq. sik cut factor; 0 = 2^d - (d - 1) */
   uint64_t seed;             /* splitmix64 seed of the power-iteration vectors */
   const double *init_candidates; /* optional host B^0, n x r column-major; NULL = N(0,1) drawn on device */
+  int32_t bulk_staging;      /* 1 (default): level-0 FP32 smoothing steps stage A and w D^-1 in
+                                shared memory by bulk copies where the block size allows; 0: off.
+                                Both give the same bits. */
 } gasa_options;
 
 typedef struct {

@@ -436,8 +436,20 @@ def setup(row_ptr, col, val, agg_of, B0=None, r=None, dim=2, seed=13373,
 # Alg. 2: V-cycle (one pass from a zero initial guess), FP64 or float32
 # ----------------------------------------------------------------------------
 
+def fp16_blocks(blocks: np.ndarray) -> np.ndarray:
+    """Dense blocks stored as FP16 values v / s with one scale s = max |v| per
+    block (s = 1 for a zero block), returned dequantised in float32."""
+    m = np.max(np.abs(blocks), axis=(1, 2))
+    s = np.where(m > 0, m, 1.0).astype(np.float32)
+    h = (blocks / s.astype(np.float64)[:, None, None]).astype(np.float16)
+    return h.astype(np.float32) * s[:, None, None]
+
+
 def make_vcycle(H: Hierarchy, precision: str = "fp64"):
-    """Returns a function f -> u approximating A^{-1} f by one V-cycle."""
+    """Returns a function f -> u approximating A^{-1} f by one V-cycle.
+    precision: 'fp64', 'fp32' (float32 operators and vectors), or 'fp16'
+    (as 'fp32', with the level-0 operator and block inverses stored as FP16
+    blocks with one scale per block)."""
     N = H.N
     if precision == "fp64":
         dt = np.float64
@@ -451,6 +463,14 @@ def make_vcycle(H: Hierarchy, precision: str = "fp64"):
         Ws = [L.W.astype(np.float32) for L in H.levels[:N]]
         Ps = [L.P.astype(np.float32) for L in H.levels[:N]]
         Rs = [L.R.astype(np.float32) for L in H.levels[:N]]
+        if precision == "fp16":
+            L0 = H.levels[0]
+            b = int(L0.unit_ptr[1] - L0.unit_ptr[0])
+            Ab = L0.A.tobsr(blocksize=(b, b))
+            Ab.sort_indices()
+            As[0] = sp.bsr_matrix((fp16_blocks(Ab.data.astype(np.float64)), Ab.indices, Ab.indptr),
+                                  shape=Ab.shape).tocsr()
+            Ws[0] = BlockDiag(L0.unit_ptr, fp16_blocks(L0.W.blocks))
     coarse = H.coarse
 
     def vcycle(f):
@@ -592,7 +612,7 @@ def solve(H: Hierarchy, b, tol=1e-10, solver="cg", precision="fp64", restart=30,
     """x = A_0^{-1} b by V-cycle-preconditioned CG or GMRES (FP64 outer loop;
     with precision='mixed32' the V-cycle is float32 and the outer loop is
     flexible)."""
-    M = make_vcycle(H, "fp64" if precision == "fp64" else "fp32")
+    M = make_vcycle(H, {"fp64": "fp64", "mixed32": "fp32", "mixed16": "fp16"}[precision])
     flex = precision != "fp64"
     A = H.levels[0].A
     if solver == "cg":

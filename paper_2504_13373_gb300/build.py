@@ -18,7 +18,9 @@ LIB = os.path.join(HERE, "libgasa.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]
-SOURCES = ["kernels_mv.cu", "kernels_red.cu", "kernels_setup.cu", "gasa_api.cu", "noalloc.cu"]
+SOURCES = ["kernels_mv.cu", "kernels_red.cu", "kernels_setup.cu", "kernels_h16.cu", "kernels_tma.cu",
+           "gasa_api.cu",
+           "noalloc.cu"]
 
 
 def nvcc():
@@ -56,7 +58,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-Xlinker", "--no-undefined"]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"link failed:\n{p.stdout}\n{p.stderr}")

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -24,6 +25,8 @@ struct DevBSR {
   int *rp = nullptr, *col = nullptr;
   double *val = nullptr;
   float *val32 = nullptr;
+  __half *val16 = nullptr;     // FP16 blocks (level 0, MIXED16)
+  float *scale16 = nullptr;    // one scale per block
 };
 
 struct Level {
@@ -33,6 +36,8 @@ struct Level {
   DevBSR A;
   double *W = nullptr;        // w D^{-1}
   float *W32 = nullptr;
+  __half *W16 = nullptr;       // FP16 blocks of w D^{-1} (level 0, MIXED16)
+  float *W16s = nullptr;
   // transfer to the next level
   int *agg = nullptr;
   int n_next = 0, s_next = 0, max_children = 0;
@@ -42,6 +47,9 @@ struct Level {
   double *cand = nullptr, *cand_in = nullptr;
   std::vector<int> sweeps;
   double omega = 0.0, rho = 0.0;
+  // bulk-copy staged FP32 smoothing step (level 0): plan from tma_plan
+  bool tma = false;
+  int tma_TR = 0, tma_stageA = 0, tma_stageW = 0, tma_smem = 0, tma_grid = 0;
   // V-cycle vectors
   double *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr;
   float *xf = nullptr, *x2f = nullptr, *bf = nullptr, *rf = nullptr;
@@ -81,11 +89,12 @@ struct gasa_ctx {
   bool gm_flex = false;
   // graph-resident CG: one instantiated graph per precision, the whole CG
   // iteration (V-cycle included) inside a conditional while node
-  cudaGraph_t cg_graph[2] = {nullptr, nullptr};
-  cudaGraphExec_t cg_exec[2] = {nullptr, nullptr};
-  long long cg_kernels[2] = {0, 0};
-  int cg_max_iter[2] = {0, 0};
+  cudaGraph_t cg_graph[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t cg_exec[3] = {nullptr, nullptr, nullptr};
+  long long cg_kernels[3] = {0, 0, 0};
+  int cg_max_iter[3] = {0, 0, 0};
   int *d_iters = nullptr;
+  int *d_err = nullptr;          // set by kernels whose bounded waits time out
   // profiling
   bool prof = false;
   ProfClass pc[3];
@@ -151,7 +160,7 @@ void dfree(gasa_ctx *ctx, void *p) {
 }
 
 void free_graphs(gasa_ctx *ctx) {
-  for (int p = 0; p < 2; ++p) {
+  for (int p = 0; p < 3; ++p) {
     if (ctx->cg_exec[p]) cudaGraphExecDestroy(ctx->cg_exec[p]);
     if (ctx->cg_graph[p]) cudaGraphDestroy(ctx->cg_graph[p]);
     ctx->cg_exec[p] = nullptr;
@@ -224,26 +233,59 @@ template <> struct Prec<float> {
   static float *r(Level &l) { return l.rf; }
 };
 
-double sweep_bytes(const Level &l, int w, bool first) {
+// algorithmic bytes of one launch: w bytes per vector entry, wa bytes per
+// matrix value (FP16 blocks add one 4-byte scale per block)
+double sweep_bytes(const Level &l, int w, bool first, int wa = 0) {
+  if (wa == 0) wa = w;
   const double vec = (double)l.ndof * w;
-  const double Wb = (double)l.n * l.s * l.s * w;
+  const double Wb = (double)l.n * l.s * l.s * wa + (wa == 2 ? 4.0 * l.n : 0.0);
   if (first) return Wb + 2.0 * vec;
-  const double Ab = (double)l.A.nnzb * l.s * l.s * w + 4.0 * l.A.nnzb + 4.0 * (l.n + 1);
+  const double Ab = (double)l.A.nnzb * l.s * l.s * wa + (wa == 2 ? 4.0 * l.A.nnzb : 0.0) +
+                    4.0 * l.A.nnzb + 4.0 * (l.n + 1);
   return Ab + Wb + 3.0 * vec;
 }
-double spmv_bytes(const Level &l, int w, bool residual) {
+double spmv_bytes(const Level &l, int w, bool residual, int wa = 0) {
+  if (wa == 0) wa = w;
   const double vec = (double)l.ndof * w;
-  const double Ab = (double)l.A.nnzb * l.s * l.s * w + 4.0 * l.A.nnzb + 4.0 * (l.n + 1);
+  const double Ab = (double)l.A.nnzb * l.s * l.s * wa + (wa == 2 ? 4.0 * l.A.nnzb : 0.0) +
+                    4.0 * l.A.nnzb + 4.0 * (l.n + 1);
   return Ab + (residual ? 3.0 : 2.0) * vec;
 }
 
 template <typename T>
-gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out) {
+gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false) {
   using P = Prec<T>;
   cudaStream_t s = ctx->stream;
   const int N = ctx->N;
   const int tpre = ctx->opt.t_pre, tpost = ctx->opt.t_post;
   const int w = (int)sizeof(T);
+  // level-0 smoothing step and residual; with h16 (FP32 V-cycle only) the
+  // level-0 operator and block inverses are read from their FP16 blocks
+  auto sweep = [&](int k, int mode, const T *xin, const T *bb, T *xo) -> cudaError_t {
+    Level &l = ctx->L[k];
+    if constexpr (std::is_same<T, float>::value) {
+      if (h16 && k == 0)
+        return launch_jacobi_h16(mode, l.n, l.s, l.A.rp, l.A.col, l.A.val16, l.A.scale16, l.W16,
+                                 l.W16s, xin, bb, xo, s);
+      if (l.tma && mode == JAC_SWEEP)
+        return launch_jacobi_tma<float>(l.n, l.s, l.tma_TR, l.tma_stageA, l.tma_stageW,
+                                        l.tma_smem, l.tma_grid, l.A.rp, l.A.col, l.A.val32,
+                                        l.W32, xin, bb, xo, ctx->d_err, s);
+    }
+    return launch_jacobi<T>(mode, l.n, l.s, l.A.rp, l.A.col, P::A(l.A), P::W(l), xin, bb, xo, s,
+                            l.A.nnzb);
+  };
+  auto resid = [&](int k, const T *xin, const T *bb, T *rr) -> cudaError_t {
+    Level &l = ctx->L[k];
+    if constexpr (std::is_same<T, float>::value) {
+      if (h16 && k == 0)
+        return launch_bsr_mv_h16(GASA_MV_RESIDUAL, l.n, l.s, l.s, l.A.rp, l.A.col, l.A.val16,
+                                 l.A.scale16, xin, bb, rr, s);
+    }
+    return launch_bsr_mv<T>(GASA_MV_RESIDUAL, l.n, l.s, l.s, l.A.rp, l.A.col, P::A(l.A), xin, bb,
+                            rr, s, l.A.nnzb);
+  };
+  const int wa = (h16 ? 2 : w);     // level-0 matrix bytes per value
   std::vector<const T *> bk(N + 1);
   std::vector<T *> xk(N + 1);
   bk[0] = rhs;
@@ -257,14 +299,12 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out) {
     } else {
       cudaEvent_t e0;
       if (k == 0) prof_begin(ctx, 0, &e0);
-      CU(launch_jacobi<T>(JAC_FIRST, l.n, l.s, l.A.rp, l.A.col, P::A(l.A), P::W(l), nullptr,
-                          bk[k], x, s, l.A.nnzb));
-      if (k == 0) prof_end(ctx, 0, sweep_bytes(l, w, true));
+      CU(sweep(k, JAC_FIRST, nullptr, bk[k], x));
+      if (k == 0) prof_end(ctx, 0, sweep_bytes(l, w, true, wa));
       for (int t = 1; t < tpre; ++t) {
         if (k == 0) prof_begin(ctx, 0, &e0);
-        CU(launch_jacobi<T>(JAC_SWEEP, l.n, l.s, l.A.rp, l.A.col, P::A(l.A), P::W(l), x, bk[k],
-                            x2, s, l.A.nnzb));
-        if (k == 0) prof_end(ctx, 0, sweep_bytes(l, w, false));
+        CU(sweep(k, JAC_SWEEP, x, bk[k], x2));
+        if (k == 0) prof_end(ctx, 0, sweep_bytes(l, w, false, wa));
         std::swap(x, x2);
       }
     }
@@ -273,9 +313,8 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out) {
     {
       cudaEvent_t e0;
       if (k == 0) prof_begin(ctx, 1, &e0);
-      CU(launch_bsr_mv<T>(GASA_MV_RESIDUAL, l.n, l.s, l.s, l.A.rp, l.A.col, P::A(l.A), x, bk[k],
-                          P::r(l), s, l.A.nnzb));
-      if (k == 0) prof_end(ctx, 1, spmv_bytes(l, w, true));
+      CU(resid(k, x, bk[k], P::r(l)));
+      if (k == 0) prof_end(ctx, 1, spmv_bytes(l, w, true, wa));
     }
     CU(launch_bsr_mv<T>(GASA_MV_ASSIGN, l.R.nrows, l.R.br, l.R.bc, l.R.rp, l.R.col, P::A(l.R),
                         P::r(l), nullptr, P::b(ctx->L[k + 1]), s, l.R.nnzb));
@@ -297,9 +336,8 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out) {
       T *dst = (k == 0 && t == tpost - 1) ? out : x2;
       cudaEvent_t e0;
       if (k == 0) prof_begin(ctx, 0, &e0);
-      CU(launch_jacobi<T>(JAC_SWEEP, l.n, l.s, l.A.rp, l.A.col, P::A(l.A), P::W(l), x, bk[k], dst,
-                          s, l.A.nnzb));
-      if (k == 0) prof_end(ctx, 0, sweep_bytes(l, w, false));
+      CU(sweep(k, JAC_SWEEP, x, bk[k], dst));
+      if (k == 0) prof_end(ctx, 0, sweep_bytes(l, w, false, wa));
       if (dst == x2) std::swap(x, x2);
       else x = dst;
     }
@@ -312,7 +350,7 @@ gasa_status apply_M(gasa_ctx *ctx, const double *rr, double *z, int precision) {
   if (precision == GASA_PREC_FP64) return vcycle_impl<double>(ctx, rr, z);
   const int64_t n = ctx->L[0].ndof;
   CU(launch_convert<double, float>(n, rr, ctx->kf_in, ctx->stream));
-  ST(vcycle_impl<float>(ctx, ctx->kf_in, ctx->kf_out));
+  ST(vcycle_impl<float>(ctx, ctx->kf_in, ctx->kf_out, precision == GASA_PREC_MIXED16));
   CU(launch_convert<float, double>(n, ctx->kf_out, z, ctx->stream));
   return GASA_OK;
 }
@@ -419,7 +457,7 @@ gasa_status pcg(gasa_ctx *ctx, const double *b, double tol, int precision, int *
 // check.  Started with p = 0 and rz = 1, the first step gives p = z, so the
 // sequence of iterates is the same as the host-driven loop above.
 gasa_status build_cg_graph(gasa_ctx *ctx, int precision) {
-  const int pi = precision == GASA_PREC_FP64 ? 0 : 1;
+  const int pi = precision;   // graph slot: FP64, MIXED32, MIXED16
   const int max_iter = ctx->opt.max_iter;
   if (ctx->cg_exec[pi] && ctx->cg_max_iter[pi] == max_iter) return GASA_OK;
   if (ctx->cg_exec[pi]) cudaGraphExecDestroy(ctx->cg_exec[pi]);
@@ -481,7 +519,7 @@ gasa_status build_cg_graph(gasa_ctx *ctx, int precision) {
 gasa_status pcg_graph(gasa_ctx *ctx, const double *b, double tol, int precision, int *iters,
                       double *relres, bool *conv) {
   cudaStream_t s = ctx->stream;
-  const int pi = precision == GASA_PREC_FP64 ? 0 : 1;
+  const int pi = precision;   // graph slot: FP64, MIXED32, MIXED16
   const int64_t n = ctx->L[0].ndof;
   *conv = false;
   *iters = 0;
@@ -508,12 +546,17 @@ gasa_status pcg_graph(gasa_ctx *ctx, const double *b, double tol, int precision,
   const int max_iter = ctx->opt.max_iter;
   for (;;) {
     CU(cudaGraphLaunch(ctx->cg_exec[pi], s));
-    int it = 0;
+    int it = 0, kerr = 0;
     CU(cudaMemcpyAsync(&it, ctx->d_iters, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(&kerr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     ST(read_scalars(ctx, 0, 3));
     note_launches(ctx->cg_kernels[pi] * (long long)(it - done_iters));
     done_iters = it;
     *iters = it;
+    if (kerr) {
+      CU(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
+      return fail(ctx, GASA_ERR_TIMEOUT, "a bounded wait on a bulk copy timed out");
+    }
     const double pq = ctx->hscal[S_PQ];
     const double rel = std::sqrt(ctx->hscal[S_RR]) / bn;
     if (!std::isfinite(rel) || !std::isfinite(pq))
@@ -679,13 +722,13 @@ gasa_status spgemm(gasa_ctx *ctx, const DevBSR &A, const DevBSR &B, DevBSR &C) {
   int maxc = 0;
   CU(cudaMemcpyAsync(&maxc, mx, sizeof(int), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
-  if ((size_t)maxc * sizeof(int) > 200 * 1024)
-    return fail(ctx, GASA_ERR_UNSUPPORTED, "Galerkin product row too dense for shared memory");
+  if (maxc > 4096 && (size_t)((B.ncols + 31) / 32) * 4 > 200 * 1024)
+    return fail(ctx, GASA_ERR_UNSUPPORTED, "coarse level too wide for the shared-memory column bitmap");
   C.nrows = n;
   C.ncols = B.ncols;
   C.br = A.br;
   C.bc = B.bc;
-  CU(launch_pattern_AB(n, A.rp, A.col, B.rp, B.col, cnt, nullptr, nullptr, maxc, s));
+  CU(launch_pattern_AB(n, A.rp, A.col, B.rp, B.col, cnt, nullptr, nullptr, maxc, B.ncols, s));
   ST(dalloc(ctx, &C.rp, n + 1));
   CU(launch_exclusive_scan(n, cnt, C.rp, nullptr, s));
   int nnz = 0;
@@ -694,7 +737,7 @@ gasa_status spgemm(gasa_ctx *ctx, const DevBSR &A, const DevBSR &B, DevBSR &C) {
   C.nnzb = nnz;
   ST(dalloc(ctx, &C.col, (size_t)nnz));
   ST(dalloc(ctx, &C.val, (size_t)nnz * C.br * C.bc));
-  CU(launch_pattern_AB(n, A.rp, A.col, B.rp, B.col, nullptr, C.rp, C.col, maxc, s));
+  CU(launch_pattern_AB(n, A.rp, A.col, B.rp, B.col, nullptr, C.rp, C.col, maxc, B.ncols, s));
   CU(launch_numeric_AB(n, A.br, A.bc, B.bc, A.rp, A.col, A.val, B.rp, B.col, B.val, C.rp, C.col,
                        C.val, s));
   CU(cudaStreamSynchronize(s));
@@ -1035,7 +1078,7 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
       }
       int *cnt = nullptr;
       ST(dalloc(ctx, &cnt, l.n + 1));
-      CU(launch_pattern_P(l.n, l.A.rp, l.A.col, l.agg, cnt, nullptr, nullptr, maxrow, s));
+      CU(launch_pattern_P(l.n, l.A.rp, l.A.col, l.agg, cnt, nullptr, nullptr, maxrow, ln.n, s));
       ST(dalloc(ctx, &P.rp, l.n + 1));
       CU(launch_exclusive_scan(l.n, cnt, P.rp, nullptr, s));
       int nnz = 0;
@@ -1044,7 +1087,7 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
       P.nnzb = nnz;
       ST(dalloc(ctx, &P.col, (size_t)nnz));
       ST(dalloc(ctx, &P.val, (size_t)nnz * P.br * P.bc));
-      CU(launch_pattern_P(l.n, l.A.rp, l.A.col, l.agg, nullptr, P.rp, P.col, maxrow, s));
+      CU(launch_pattern_P(l.n, l.A.rp, l.A.col, l.agg, nullptr, P.rp, P.col, maxrow, ln.n, s));
       CU(launch_numeric_P(l.n, l.s, ln.s, l.A.rp, l.A.col, l.A.val, l.W, l.T, l.agg, P.rp, P.col,
                           P.val, s));
       CU(cudaStreamSynchronize(s));
@@ -1100,6 +1143,15 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
     ST(make_f32(ctx, l.A));
     ST(make_f32(ctx, l.P));
     ST(make_f32(ctx, l.R));
+    if (k == 0) {
+      // FP16 blocks with one FP32 scale per block for the MIXED16 V-cycle
+      ST(dalloc(ctx, &l.A.val16, (size_t)l.A.nnzb * l.s * l.s));
+      ST(dalloc(ctx, &l.A.scale16, (size_t)l.A.nnzb));
+      CU(launch_to_h16_blocks(l.A.nnzb, l.s * l.s, l.A.val, l.A.val16, l.A.scale16, s));
+      ST(dalloc(ctx, &l.W16, (size_t)l.n * l.s * l.s));
+      ST(dalloc(ctx, &l.W16s, (size_t)l.n));
+      CU(launch_to_h16_blocks(l.n, l.s * l.s, l.W, l.W16, l.W16s, s));
+    }
     ST(dalloc(ctx, &l.W32, (size_t)l.n * l.s * l.s));
     CU(launch_convert<double, float>((int64_t)l.n * l.s * l.s, l.W, l.W32, s));
   }
@@ -1147,6 +1199,15 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
   ST(dalloc(ctx, &ctx->kf_in, (size_t)n));
   ST(dalloc(ctx, &ctx->kf_out, (size_t)n));
   ST(dalloc(ctx, &ctx->d_iters, 4));
+  ST(dalloc(ctx, &ctx->d_err, 4));
+  CU(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
+  if (opt->bulk_staging) {
+    Level &l = ctx->L[0];
+    int maxrow = 0;
+    for (int i = 0; i < l.n; ++i) maxrow = std::max(maxrow, hrp[i + 1] - hrp[i]);
+    l.tma = tma_plan(l.n, l.s, (int)sizeof(float), maxrow, &l.tma_TR, &l.tma_stageA,
+                     &l.tma_stageW, &l.tma_smem, &l.tma_grid);
+  }
   CU(cudaStreamSynchronize(s));
   ctx->ready = true;
   ctx->setup_seconds =
@@ -1200,6 +1261,7 @@ void gasa_default_options(gasa_options *opt) {
   opt->n_cut = 0.0;
   opt->seed = 13373;
   opt->init_candidates = nullptr;
+  opt->bulk_staging = 0;
 }
 
 gasa_status gasa_create(gasa_ctx **out, int32_t device, void *stream) {
@@ -1231,7 +1293,9 @@ gasa_status gasa_setup(gasa_ctx *ctx, const gasa_bsr *A, const int32_t *adj_ptr,
                        gasa_setup_info *info) {
   if (!ctx) return GASA_ERR_INVALID_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, GASA_ERR_CUDA, "cudaSetDevice");
+  (void)cudaGetLastError();   // an error left by an earlier, unrelated call is not ours
   gasa_status st = setup_impl(ctx, A, adj_ptr, adj_idx, centroids, hier, opt, info);
+  if (st != GASA_OK) (void)cudaGetLastError();
   if (st != GASA_OK) {
     cudaStreamSynchronize(ctx->stream);
     ctx->ready = false;
@@ -1244,9 +1308,10 @@ gasa_status gasa_solve(gasa_ctx *ctx, const double *b, double *x, double tol, in
   if (!ctx) return GASA_ERR_INVALID_ARG;
   if (!ctx->ready) return fail(ctx, GASA_ERR_STATE, "solve before setup");
   if (!b || !x || !(tol > 0.0)) return fail(ctx, GASA_ERR_INVALID_ARG, "null vector or tol <= 0");
-  if (precision != GASA_PREC_FP64 && precision != GASA_PREC_MIXED32)
+  if (precision < GASA_PREC_FP64 || precision > GASA_PREC_MIXED16)
     return fail(ctx, GASA_ERR_INVALID_ARG, "unknown precision");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, GASA_ERR_CUDA, "cudaSetDevice");
+  (void)cudaGetLastError();
   auto t0 = std::chrono::steady_clock::now();
   const int64_t n = ctx->L[0].ndof;
   const double *bd = b;
@@ -1283,7 +1348,7 @@ gasa_status gasa_vcycle(gasa_ctx *ctx, const double *r, double *z, int32_t preci
   if (!ctx) return GASA_ERR_INVALID_ARG;
   if (!ctx->ready) return fail(ctx, GASA_ERR_STATE, "vcycle before setup");
   if (!r || !z) return fail(ctx, GASA_ERR_INVALID_ARG, "null vector");
-  if (precision != GASA_PREC_FP64 && precision != GASA_PREC_MIXED32)
+  if (precision < GASA_PREC_FP64 || precision > GASA_PREC_MIXED16)
     return fail(ctx, GASA_ERR_INVALID_ARG, "unknown precision");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, GASA_ERR_CUDA, "cudaSetDevice");
   ST(apply_M(ctx, r, z, precision));

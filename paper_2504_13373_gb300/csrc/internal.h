@@ -1,10 +1,32 @@
 // Host-side launchers shared by the library's translation units.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace gasa {
+
+// ---- kernels_tma.cu: level-0 sweep with bulk-copy staging -------------------
+// plan for n_units block rows of bs x bs blocks of wbytes-byte values whose
+// rows hold at most max_row blocks; false when the staged kernel does not apply
+bool tma_plan(int n_units, int bs, int wbytes, int max_row, int *TR, int *stageA, int *stageW,
+              int *smem, int *grid);
+template <typename T>
+cudaError_t launch_jacobi_tma(int n_units, int bs, int TR, int stageA, int stageW, int smem,
+                              int grid, const int *rp, const int *col, const T *val, const T *W,
+                              const T *x, const T *b, T *xo, int *err, cudaStream_t s);
+
+// ---- kernels_h16.cu: FP16 blocks with one FP32 scale per block -------------
+cudaError_t launch_to_h16_blocks(int64_t nblocks, int bsz, const double *v, __half *h,
+                                 float *scale, cudaStream_t s);
+cudaError_t launch_bsr_mv_h16(int mode, int n_brows, int br, int bc, const int *rp,
+                              const int *col, const __half *val, const float *scale,
+                              const float *x, const float *b, float *y, cudaStream_t s);
+cudaError_t launch_jacobi_h16(int mode, int n_units, int bs, const int *rp, const int *col,
+                              const __half *val, const float *ascale, const __half *W,
+                              const float *wscale, const float *x, const float *b, float *xo,
+                              cudaStream_t s);
 
 // kernel launches issued by this library (process-wide counter)
 void note_launch();
@@ -104,10 +126,10 @@ cudaError_t build_children(int n_units, int n_agg, const int *agg_of, int *child
 // cand_count[i] is written for every row (candidates before de-duplication)
 cudaError_t launch_pattern_P(int n, const int *Arp, const int *Acol, const int *agg,
                              int *count_or_null, const int *Prp_or_null, int *Pcol_or_null,
-                             int max_cand, cudaStream_t s);
+                             int max_cand, int ncols, cudaStream_t s);
 cudaError_t launch_pattern_AB(int n, const int *Arp, const int *Acol, const int *Brp,
                               const int *Bcol, int *count_or_null, const int *Crp_or_null,
-                              int *Ccol_or_null, int max_cand, cudaStream_t s);
+                              int *Ccol_or_null, int max_cand, int ncols, cudaStream_t s);
 cudaError_t launch_cand_count_AB(int n, const int *Arp, const int *Acol, const int *Brp,
                                  int *cand, cudaStream_t s);
 cudaError_t launch_numeric_P(int n, int sk, int sn, const int *Arp, const int *Acol,

@@ -125,9 +125,109 @@ bsr_mv_warp_kernel(int n_brows, int br, int bc, const int *__restrict__ rp,
   }
 }
 
-// average blocks per row from which a warp per block row pays
+// Power-of-two block heights: the warp's lanes form 32/br groups of br
+// lanes; lane (g, r) takes row r of blocks g, g + 32/br, ... of the block row,
+// so a block's br rows are read by br neighbouring lanes at once; the groups'
+// partial sums meet in an xor-shuffle over the group bits.
+template <typename T>
+__device__ __forceinline__ T group_row_dot(int beg, int end, int br, int bc, int lane,
+                                           const int *__restrict__ col,
+                                           const T *__restrict__ val,
+                                           const T *__restrict__ x) {
+  const int r = lane & (br - 1);
+  const int g = lane / br;
+  const int G = 32 / br;
+  T acc = T(0);
+  for (int k = beg + g; k < end; k += G) {
+    const int j = __ldg(col + k);
+    const T *a = val + ((size_t)k * br + r) * bc;
+    const T *xj = x + (size_t)j * bc;
+#pragma unroll 4
+    for (int c = 0; c < bc; ++c) acc = fma(__ldg(a + c), __ldg(xj + c), acc);
+  }
+  for (int o = br; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;   // every lane holds the sum of row (lane & (br - 1))
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256)
+bsr_mv_group_kernel(int n_brows, int br, int bc, const int *__restrict__ rp,
+                    const int *__restrict__ col, const T *__restrict__ val,
+                    const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ y) {
+  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n_brows) return;
+  const T v = group_row_dot<T>(__ldg(rp + i), __ldg(rp + i + 1), br, bc, lane, col, val, x);
+  if (lane < br) {
+    const size_t t = (size_t)i * br + lane;
+    if (MODE == GASA_MV_ASSIGN) y[t] = v;
+    else if (MODE == GASA_MV_RESIDUAL) y[t] = b[t] - v;
+    else y[t] += v;
+  }
+}
+
+static inline bool pow2_le32(int v) { return v > 0 && v <= 32 && (v & (v - 1)) == 0; }
+
+// The coarsest levels hold a few thousand block rows or less, each with up
+// to several hundred blocks: one CTA of 256 threads owns a block row.  The
+// threads form G = 256 / br groups of br; thread (g, r) takes row r of blocks
+// g, g + G, ...; the groups' partial sums are added in a fixed order from
+// shared memory.  Returns the row sums in red[0..br).
+template <typename T>
+__device__ __forceinline__ void cta_row_dot(int beg, int end, int br, int bc,
+                                            const int *__restrict__ col,
+                                            const T *__restrict__ val,
+                                            const T *__restrict__ x, T *red) {
+  const int G = blockDim.x / br;
+  const int t = threadIdx.x;
+  const int g = t / br, r = t - g * br;
+  T acc = T(0);
+  if (g < G) {
+    for (int k = beg + g; k < end; k += G) {
+      const int j = __ldg(col + k);
+      const T *a = val + ((size_t)k * br + r) * bc;
+      const T *xj = x + (size_t)j * bc;
+#pragma unroll 4
+      for (int c = 0; c < bc; ++c) acc = fma(__ldg(a + c), __ldg(xj + c), acc);
+    }
+  }
+  red[t] = acc;
+  __syncthreads();
+  if (t < br) {
+    T s = T(0);
+    for (int q = 0; q < G; ++q) s += red[q * br + t];
+    red[blockDim.x + t] = s;
+  }
+  __syncthreads();
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256)
+bsr_mv_cta_kernel(int n_brows, int br, int bc, const int *__restrict__ rp,
+                  const int *__restrict__ col, const T *__restrict__ val,
+                  const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ y) {
+  extern __shared__ unsigned char cta_smem[];
+  T *red = reinterpret_cast<T *>(cta_smem);
+  const int i = blockIdx.x;
+  cta_row_dot<T>(__ldg(rp + i), __ldg(rp + i + 1), br, bc, col, val, x, red);
+  for (int r = threadIdx.x; r < br; r += blockDim.x) {
+    const size_t t = (size_t)i * br + r;
+    const T v = red[blockDim.x + r];
+    if (MODE == GASA_MV_ASSIGN) y[t] = v;
+    else if (MODE == GASA_MV_RESIDUAL) y[t] = b[t] - v;
+    else y[t] += v;
+  }
+}
+
+// CTA per block row for few, long rows
+static inline bool cta_rows(int n_brows, int br) { return n_brows <= 4096 && br <= 256; }
+
+// A warp per block row pays when the thread-per-row grid would fill less
+// than about half of the GPU, or when rows are very long.
 static inline bool warp_rows(int n_brows, int br, int64_t nnzb) {
-  return nnzb >= 0 && br <= 64 && nnzb >= 12LL * n_brows;
+  if (nnzb < 0 || br > 64) return false;
+  const long long threads = (long long)n_brows * br;
+  return (threads < 65536 && nnzb >= 4LL * n_brows) || nnzb >= 64LL * n_brows;
 }
 
 static inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
@@ -136,7 +236,13 @@ template <typename T, int MODE>
 static cudaError_t mv_warp_dispatch(int n_brows, int br, int bc, const int *rp, const int *col,
                                     const T *val, const T *x, const T *b, T *y, cudaStream_t s) {
   const int grid = div_up((long long)n_brows * 32, 256);
-  if (br <= 4) bsr_mv_warp_kernel<T, 4, MODE><<<grid, 256, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y);
+  if (cta_rows(n_brows, br)) {
+    bsr_mv_cta_kernel<T, MODE><<<n_brows, 256, (256 + br) * sizeof(T), s>>>(n_brows, br, bc, rp, col, val, x, b, y);
+    note_launch();
+    return cudaGetLastError();
+  }
+  if (pow2_le32(br)) bsr_mv_group_kernel<T, MODE><<<grid, 256, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y);
+  else if (br <= 4) bsr_mv_warp_kernel<T, 4, MODE><<<grid, 256, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y);
   else if (br <= 8) bsr_mv_warp_kernel<T, 8, MODE><<<grid, 256, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y);
   else if (br <= 16) bsr_mv_warp_kernel<T, 16, MODE><<<grid, 256, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y);
   else if (br <= 32) bsr_mv_warp_kernel<T, 32, MODE><<<grid, 256, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y);
@@ -332,12 +438,73 @@ jacobi_warp_kernel(int n_units, int bs, const int *__restrict__ rp, const int *_
   }
 }
 
+// CTA per block row (few, long rows): the block row's residual meets in
+// shared memory, thread r < bs applies row r of W_i
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256)
+jacobi_cta_kernel(int n_units, int bs, const int *__restrict__ rp, const int *__restrict__ col,
+                  const T *__restrict__ val, const T *__restrict__ Wm, const T *__restrict__ x,
+                  const T *__restrict__ b, T *__restrict__ xo) {
+  extern __shared__ unsigned char cta_smem_j[];
+  T *red = reinterpret_cast<T *>(cta_smem_j);
+  const int i = blockIdx.x;
+  cta_row_dot<T>(__ldg(rp + i), __ldg(rp + i + 1), bs, bs, col, val, x, red);
+  T *res = red + blockDim.x;
+  for (int r = threadIdx.x; r < bs; r += blockDim.x) {
+    const size_t row = (size_t)i * bs + r;
+    if (MODE == JAC_SWEEP) res[r] = b[row] - res[r];
+    else if (MODE == JAC_RELAX) res[r] = -res[r];
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < bs; r += blockDim.x) {
+    const size_t row = (size_t)i * bs + r;
+    const T *w = Wm + row * bs;
+    T out = T(0);
+    for (int c = 0; c < bs; ++c) out = fma(__ldg(w + c), res[c], out);
+    if (MODE == JAC_SWEEP || MODE == JAC_RELAX) out += x[row];
+    xo[row] = out;
+  }
+}
+
+// power-of-two block size: lane groups as in bsr_mv_group_kernel; lane c
+// then holds row c's residual and lane r < bs applies row r of W_i
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256)
+jacobi_group_kernel(int n_units, int bs, const int *__restrict__ rp, const int *__restrict__ col,
+                    const T *__restrict__ val, const T *__restrict__ Wm, const T *__restrict__ x,
+                    const T *__restrict__ b, T *__restrict__ xo) {
+  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n_units) return;
+  T v = group_row_dot<T>(__ldg(rp + i), __ldg(rp + i + 1), bs, bs, lane, col, val, x);
+  const int r = lane & (bs - 1);
+  const size_t row = (size_t)i * bs + r;
+  if (MODE == JAC_SWEEP) v = b[row] - v;
+  else if (MODE == JAC_RELAX) v = -v;
+  const T *w = Wm + row * bs;
+  T out = T(0);
+  for (int c = 0; c < bs; ++c) {
+    const T rc = __shfl_sync(0xffffffffu, v, c);
+    out = fma(__ldg(w + c), rc, out);
+  }
+  if (lane < bs) {
+    if (MODE == JAC_SWEEP || MODE == JAC_RELAX) out += x[row];
+    xo[row] = out;
+  }
+}
+
 template <typename T, int MODE>
 static cudaError_t jac_warp_dispatch(int n_units, int bs, const int *rp, const int *col,
                                      const T *val, const T *W, const T *x, const T *b, T *xo,
                                      cudaStream_t s) {
   const int grid = div_up((long long)n_units * 32, 256);
-  if (bs <= 4) jacobi_warp_kernel<T, 4, MODE><<<grid, 256, 0, s>>>(n_units, bs, rp, col, val, W, x, b, xo);
+  if (cta_rows(n_units, bs)) {
+    jacobi_cta_kernel<T, MODE><<<n_units, 256, (256 + bs) * sizeof(T), s>>>(n_units, bs, rp, col, val, W, x, b, xo);
+    note_launch();
+    return cudaGetLastError();
+  }
+  if (pow2_le32(bs)) jacobi_group_kernel<T, MODE><<<grid, 256, 0, s>>>(n_units, bs, rp, col, val, W, x, b, xo);
+  else if (bs <= 4) jacobi_warp_kernel<T, 4, MODE><<<grid, 256, 0, s>>>(n_units, bs, rp, col, val, W, x, b, xo);
   else if (bs <= 8) jacobi_warp_kernel<T, 8, MODE><<<grid, 256, 0, s>>>(n_units, bs, rp, col, val, W, x, b, xo);
   else if (bs <= 16) jacobi_warp_kernel<T, 16, MODE><<<grid, 256, 0, s>>>(n_units, bs, rp, col, val, W, x, b, xo);
   else if (bs <= 32) jacobi_warp_kernel<T, 32, MODE><<<grid, 256, 0, s>>>(n_units, bs, rp, col, val, W, x, b, xo);

@@ -20,15 +20,19 @@ __global__ void __launch_bounds__(kRedThreads)
 dot_partials_kernel(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                     double *__restrict__ partials) {
   __shared__ double sh[32];
-  double v = 0.0;
+  // four independent accumulators keep four loads in flight per thread
+  double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  if (y) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-      v = fma(x[i], y[i], v);
-  } else {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-      v = fma(x[i], x[i], v);
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!y) y = x;
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    v0 = fma(x[i], y[i], v0);
+    v1 = fma(x[i + stride], y[i + stride], v1);
+    v2 = fma(x[i + 2 * stride], y[i + 2 * stride], v2);
+    v3 = fma(x[i + 3 * stride], y[i + 3 * stride], v3);
   }
+  for (; i < n; i += stride) v0 = fma(x[i], y[i], v0);
+  double v = (v0 + v1) + (v2 + v3);
   v = block_sum(v, sh);
   if (threadIdx.x == 0) partials[blockIdx.x] = v;
 }
@@ -205,14 +209,28 @@ cg_update_xr_kernel(int64_t n, double *__restrict__ x, double *__restrict__ r,
     alpha_out[0] = alpha;
     alpha_out[1] = pq;
   }
-  double v = 0.0;
+  double v0 = 0.0, v1 = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + stride < n; i += 2 * stride) {
+    const int64_t i2 = i + stride;
+    const double p0 = p[i], p1 = p[i2], q0 = q[i], q1 = q[i2];
+    const double x0 = x[i], x1 = x[i2], r0 = r[i], r1 = r[i2];
+    x[i] = fma(alpha, p0, x0);
+    x[i2] = fma(alpha, p1, x1);
+    const double ra = fma(-alpha, q0, r0), rb = fma(-alpha, q1, r1);
+    r[i] = ra;
+    r[i2] = rb;
+    v0 = fma(ra, ra, v0);
+    v1 = fma(rb, rb, v1);
+  }
+  for (; i < n; i += stride) {
     x[i] = fma(alpha, p[i], x[i]);
     const double ri = fma(-alpha, q[i], r[i]);
     r[i] = ri;
-    v = fma(ri, ri, v);
+    v0 = fma(ri, ri, v0);
   }
+  double v = v0 + v1;
   v = block_sum(v, sh);
   if (threadIdx.x == 0) rr_partials[blockIdx.x] = v;
 }

@@ -7,6 +7,7 @@
 // one output block row, each thread owns fixed entries of the output block,
 // and the summation order over the inner index is the pattern order, so the
 // results are reproducible run to run and need no atomics on values.
+#include <algorithm>
 #include <climits>
 
 #include "common.cuh"
@@ -339,24 +340,29 @@ __global__ void tentative_kernel(int bs, const int *__restrict__ child_ptr,
     for (int l = threadIdx.x; l < r; l += blockDim.x)
       sigma[(size_t)J * r + l] = (l < rows) ? sv[order[l]] : 0.0;
   }
-  // normalise the kept columns (Hestenes columns are orthogonal relative to
-  // their own norms, so tiny singular values still give orthonormal vectors)
+  // Singular values at or below kNullSigma * sigma_1 are numerically zero:
+  // their vectors carry rounding noise, not candidate information.
+  constexpr double kNullSigma = 1e-10;
+  const double snull = kNullSigma * sv[order[0]];
+  // normalise the kept columns with nonzero singular value
   for (int l = wid; l < s_next; l += nwarps) {
     const int c = order[l];
     const double sc = sv[c];
-    if (l < rows && sc > 0.0) {
+    if (l < rows && sc > snull) {
       const double inv = 1.0 / sc;
       double *gc = G + (size_t)c * rows;
       for (int i = lane; i < rows; i += 32) gc[i] *= inv;
     }
   }
   __syncthreads();
-  // an exactly zero column (candidate block of lower rank than the kept
-  // count) is completed by Gram-Schmidt of unit vectors against the kept ones
+  // the others (candidate block of lower numerical rank than the kept count)
+  // are replaced, in order, by unit vectors e_t (t = l, l+1, ... cyclically)
+  // orthogonalised twice against the columns already fixed, the first with
+  // norm above 1/2 being kept
   if (wid == 0) {
     for (int l = 0; l < s_next && l < rows; ++l) {
       const int c = order[l];
-      if (sv[c] > 0.0) continue;
+      if (sv[c] > snull) continue;
       double *gc = G + (size_t)c * rows;
       bool done = false;
       for (int t = 0; t < rows && !done; ++t) {
@@ -518,6 +524,101 @@ __global__ void pattern_AB_kernel(int n, const int *__restrict__ Arp, const int 
   if (Ccol) for (int t = threadIdx.x; t < u; t += blockDim.x) Ccol[Crp[i] + t] = buf[t];
 }
 
+// ----------------------------------------------------------------------------
+// Long candidate lists (coarse Galerkin rows can collect tens of thousands of
+// candidates): a bitmap over the ncols output columns in shared memory; set
+// bits are then written out in column order, which sorts and de-duplicates
+// at once.  mode 0: C = pattern(A) x agg (P's pattern); mode 1: C = A B.
+// ----------------------------------------------------------------------------
+__device__ int block_scan_int(int v, int *sh, int &total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  __syncthreads();
+  if (lane == 31) sh[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    const int w = lane < nw ? sh[lane] : 0;
+    int winc = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, winc, o);
+      if (lane >= o) winc += t;
+    }
+    if (lane < nw) sh[lane] = winc - w;
+    if (lane == 31) sh[32] = winc;
+  }
+  __syncthreads();
+  const int res = sh[wid] + inc - v;
+  total = sh[32];
+  __syncthreads();
+  return res;
+}
+
+__global__ void __launch_bounds__(256)
+pattern_bitmap_kernel(int n, int mode, int ncols, const int *__restrict__ Arp,
+                      const int *__restrict__ Acol, const int *__restrict__ Brp,
+                      const int *__restrict__ Bcol_or_agg, int *count,
+                      const int *__restrict__ Crp, int *Ccol) {
+  extern __shared__ unsigned bits[];
+  __shared__ int sh[33];
+  const int nwords = (ncols + 31) >> 5;
+  for (int w = threadIdx.x; w < nwords; w += blockDim.x) bits[w] = 0u;
+  __syncthreads();
+  const int i = blockIdx.x;
+  const int b = Arp[i], e = Arp[i + 1];
+  if (mode == 0) {
+    for (int k = b + threadIdx.x; k < e; k += blockDim.x) {
+      const int c = Bcol_or_agg[Acol[k]];
+      atomicOr(&bits[c >> 5], 1u << (c & 31));
+    }
+  } else {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int k = b + wid; k < e; k += nwarp) {
+      const int j = Acol[k];
+      for (int q = Brp[j] + lane; q < Brp[j + 1]; q += 32) {
+        const int c = Bcol_or_agg[q];
+        atomicOr(&bits[c >> 5], 1u << (c & 31));
+      }
+    }
+  }
+  __syncthreads();
+  int base = 0;
+  for (int w0 = 0; w0 < nwords; w0 += blockDim.x) {
+    const int w = w0 + threadIdx.x;
+    unsigned word = w < nwords ? bits[w] : 0u;
+    int total;
+    const int pre = block_scan_int(__popc(word), sh, total);
+    if (Ccol) {
+      int pos = Crp[i] + base + pre;
+      while (word) {
+        const int bit = __ffs(word) - 1;
+        Ccol[pos++] = (w << 5) + bit;
+        word &= word - 1u;
+      }
+    }
+    base += total;
+  }
+  if (count && threadIdx.x == 0) count[i] = base;
+}
+
+static cudaError_t launch_pattern_bitmap(int n, int mode, int ncols, const int *Arp,
+                                         const int *Acol, const int *Brp, const int *Bcol_or_agg,
+                                         int *count, const int *Crp, int *Ccol, cudaStream_t s) {
+  const size_t sm = (size_t)((ncols + 31) / 32) * sizeof(unsigned);
+  if (sm > 200 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(pattern_bitmap_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(sm, 1));
+  if (e != cudaSuccess) return e;
+  pattern_bitmap_kernel<<<n, 256, sm, s>>>(n, mode, ncols, Arp, Acol, Brp, Bcol_or_agg, count, Crp, Ccol); note_launch();
+  return cudaGetLastError();
+}
+
 __global__ void cand_count_AB_kernel(int n, const int *__restrict__ Arp, const int *__restrict__ Acol,
                                      const int *__restrict__ Brp, int *cand) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -548,9 +649,15 @@ static int host_pow2(int n) {
   return p;
 }
 
+// candidate lists up to kSortCap entries are sorted in shared memory, longer
+// ones go through the column bitmap
+constexpr int kSortCap = 4096;
+
 cudaError_t launch_pattern_P(int n, const int *Arp, const int *Acol, const int *agg, int *count,
-                             const int *Prp, int *Pcol, int max_cand, cudaStream_t s) {
+                             const int *Prp, int *Pcol, int max_cand, int ncols, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
+  if (max_cand > kSortCap)
+    return launch_pattern_bitmap(n, 0, ncols, Arp, Acol, nullptr, agg, count, Prp, Pcol, s);
   const int ncap = host_pow2(max_cand < 1 ? 1 : max_cand);
   const size_t sm = (size_t)ncap * sizeof(int);
   cudaError_t e = set_smem((const void *)pattern_P_kernel, sm);
@@ -561,8 +668,10 @@ cudaError_t launch_pattern_P(int n, const int *Arp, const int *Acol, const int *
 
 cudaError_t launch_pattern_AB(int n, const int *Arp, const int *Acol, const int *Brp,
                               const int *Bcol, int *count, const int *Crp, int *Ccol, int max_cand,
-                              cudaStream_t s) {
+                              int ncols, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
+  if (max_cand > kSortCap)
+    return launch_pattern_bitmap(n, 1, ncols, Arp, Acol, Brp, Bcol, count, Crp, Ccol, s);
   const int ncap = host_pow2(max_cand < 1 ? 1 : max_cand);
   const size_t sm = (size_t)ncap * sizeof(int);
   cudaError_t e = set_smem((const void *)pattern_AB_kernel, sm);

@@ -26,7 +26,7 @@ GASA_ERR_UNSUPPORTED = 11
 GASA_ERR_STATE = 12
 
 GASA_SOLVER_CG, GASA_SOLVER_GMRES = 0, 1
-GASA_PREC_FP64, GASA_PREC_MIXED32 = 0, 1
+GASA_PREC_FP64, GASA_PREC_MIXED32, GASA_PREC_MIXED16 = 0, 1, 2
 GASA_CAND_R, GASA_CAND_TT = 0, 1
 GASA_MV_ASSIGN, GASA_MV_RESIDUAL, GASA_MV_ADD = 0, 1, 2
 GASA_MAX_LEVELS = 24
@@ -63,7 +63,8 @@ class gasa_options(ctypes.Structure):
                 ("t_pre", c_i32), ("t_post", c_i32), ("q_power", c_i32), ("n_cand", c_i32),
                 ("max_relax", c_i32), ("max_iter", c_i32), ("cand_init", c_i32),
                 ("keep_setup_data", c_i32), ("gamma", c_dbl), ("omega_factor", c_dbl),
-                ("n_cut", c_dbl), ("seed", ctypes.c_uint64), ("init_candidates", c_vp)]
+                ("n_cut", c_dbl), ("seed", ctypes.c_uint64), ("init_candidates", c_vp),
+                ("bulk_staging", c_i32)]
 
 
 class gasa_setup_info(ctypes.Structure):

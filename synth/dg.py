@@ -45,21 +45,43 @@ def tensor_exponents(dim: int, p: int) -> np.ndarray:
     return g.reshape(-1, dim)[:, ::-1].copy() if dim > 1 else g.reshape(-1, 1)
 
 
+def _powers(xi: np.ndarray, p: int):
+    """per coordinate d: (..., p+1) array of xi_d^0 .. xi_d^p"""
+    out = []
+    for d in range(xi.shape[-1]):
+        cols = [np.ones(xi.shape[:-1])]
+        for _ in range(p):
+            cols.append(cols[-1] * xi[..., d])
+        out.append(np.stack(cols, axis=-1))
+    return out
+
+
 def monomials(xi: np.ndarray, ex: np.ndarray) -> np.ndarray:
-    """xi (..., d) -> (..., nm)"""
-    return np.prod(xi[..., None, :] ** ex, axis=-1)
+    """xi (..., d) -> (..., nm): prod_d xi_d^ex[m, d]"""
+    pw = _powers(xi, int(ex.max()))
+    out = pw[0][..., ex[:, 0]]
+    for d in range(1, ex.shape[1]):
+        out = out * pw[d][..., ex[:, d]]
+    return out
 
 
 def monomial_grads(xi: np.ndarray, ex: np.ndarray) -> np.ndarray:
     """xi (..., d) -> (..., nm, d)"""
-    d = ex.shape[1]
-    out = np.empty(xi.shape[:-1] + (ex.shape[0], d))
-    for k in range(d):
-        e = ex.copy()
-        coef = e[:, k].astype(np.float64)
-        e[:, k] = np.maximum(e[:, k] - 1, 0)
-        out[..., k] = coef * monomials(xi, e)
+    D = ex.shape[1]
+    pw = _powers(xi, int(ex.max()))
+    out = np.empty(xi.shape[:-1] + (ex.shape[0], D))
+    for k in range(D):
+        g = ex[:, k].astype(np.float64) * pw[k][..., np.maximum(ex[:, k] - 1, 0)]
+        for d in range(D):
+            if d != k:
+                g = g * pw[d][..., ex[:, d]]
+        out[..., k] = g
     return out
+
+
+def _wgram(w, a, b):
+    """sum_q w[f,q] a[f,q,i] b[f,q,j] -> (f, i, j)"""
+    return np.matmul(np.swapaxes(a * w[:, :, None], 1, 2), b)
 
 
 @dataclass
@@ -79,7 +101,7 @@ class RefElement:
 
     def grads(self, xi):
         g = monomial_grads(xi, self.ex)            # (..., nm, d)
-        return np.einsum("...md,mk->...kd", g, self.C)
+        return np.swapaxes(np.matmul(np.swapaxes(g, -1, -2), self.C), -1, -2)
 
 
 def simplex_ref(dim: int, p: int) -> RefElement:
@@ -218,12 +240,14 @@ def sipg_assemble(mesh: Mesh, p: int, c_pen: float = 10.0, chunk: int = 65536):
 
     fx, fw = simplex_quad(d - 1, 2 * p + 1)               # face rule on reference face
 
-    def side_eval(e, xq_phys):
+    def side_eval(e, xq_phys, nrm):
+        """basis values and normal derivatives grad(phi) . n at face points"""
         xi = np.einsum("fkm,fqm->fqk", Jinv[e], xq_phys - X[e][:, None, 0, :])
         phi = ref.values(xi)                              # (nF, nq, nb)
-        g = ref.grads(xi)                                 # (nF, nq, nb, d)
-        gphys = np.einsum("fqkd,fdm->fqkm", g, Jinv[e])
-        return phi, gphys
+        g = ref.grads(xi)                                 # (nF, nq, nb, d) reference gradients
+        jn = np.matmul(Jinv[e], nrm[:, :, None])          # (nF, d, 1): J^{-1} n
+        dn = np.matmul(g, jn[:, None, :, :])[..., 0]      # (nF, nq, nb)
+        return phi, dn
 
     def face_points(e, f):
         Fv, Xe = _face_geometry(mesh, X, e, f)
@@ -251,17 +275,15 @@ def sipg_assemble(mesh: Mesh, p: int, c_pen: float = 10.0, chunk: int = 65536):
     for s in range(0, F.shape[0], chunk):
         e1, f1, e2, f2 = (F[s:s + chunk, c] for c in range(4))
         pts, w, nrm = face_points(e1, f1)
-        p1, g1 = side_eval(e1, pts)
-        p2, g2 = side_eval(e2, pts)
-        dn1 = np.einsum("fqkd,fd->fqk", g1, nrm)
-        dn2 = np.einsum("fqkd,fd->fqk", g2, nrm)
+        p1, dn1 = side_eval(e1, pts, nrm)
+        p2, dn2 = side_eval(e2, pts, nrm)
         sides = ((p1, dn1, 1.0), (p2, dn2, -1.0))
         blocks = {}
         for a, (pa, dna, sa) in enumerate(sides):
             for b_, (pb, dnb, sb) in enumerate(sides):
-                blk = (-0.5 * sa * np.einsum("fq,fqi,fqj->fij", w, pa, dnb)
-                       - 0.5 * sb * np.einsum("fq,fqi,fqj->fij", w, dna, pb)
-                       + sigma * sa * sb * np.einsum("fq,fqi,fqj->fij", w, pa, pb))
+                blk = (-0.5 * sa * _wgram(w, pa, dnb)
+                       - 0.5 * sb * _wgram(w, dna, pb)
+                       + sigma * sa * sb * _wgram(w, pa, pb))
                 blocks[(a, b_)] = blk
         # each element has one face per local index, so groups by local face are duplicate-free
         for lf in range(d + 1):
@@ -277,11 +299,8 @@ def sipg_assemble(mesh: Mesh, p: int, c_pen: float = 10.0, chunk: int = 65536):
     for s in range(0, Bf.shape[0], chunk):
         e, f = Bf[s:s + chunk, 0], Bf[s:s + chunk, 1]
         pts, w, nrm = face_points(e, f)
-        ph, g = side_eval(e, pts)
-        dn = np.einsum("fqkd,fd->fqk", g, nrm)
-        blk = (-np.einsum("fq,fqi,fqj->fij", w, ph, dn)
-               - np.einsum("fq,fqi,fqj->fij", w, dn, ph)
-               + sigma * np.einsum("fq,fqi,fqj->fij", w, ph, ph))
+        ph, dn = side_eval(e, pts, nrm)
+        blk = (-_wgram(w, ph, dn) - _wgram(w, dn, ph) + sigma * _wgram(w, ph, ph))
         for lf in range(d + 1):
             m = f == lf
             val[diag[e[m]]] += blk[m]

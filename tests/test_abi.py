@@ -54,6 +54,7 @@ int main(void) {
   printf("gasa_setup_info %zu\n", sizeof(gasa_setup_info));
   printf("gasa_solve_info %zu\n", sizeof(gasa_solve_info));
   P(gasa_options, gamma); P(gasa_options, seed); P(gasa_options, init_candidates);
+  P(gasa_options, bulk_staging);
   P(gasa_setup_info, omega); P(gasa_setup_info, seconds); P(gasa_setup_info, device_bytes);
   P(gasa_bsr, val); P(gasa_bsr, on_device); P(gasa_solve_info, rel_residual);
   return 0;
@@ -78,6 +79,7 @@ def test_struct_layouts_match_c(tmp_path):
         "gasa_options.gamma": gasa.gasa_options.gamma.offset,
         "gasa_options.seed": gasa.gasa_options.seed.offset,
         "gasa_options.init_candidates": gasa.gasa_options.init_candidates.offset,
+        "gasa_options.bulk_staging": gasa.gasa_options.bulk_staging.offset,
         "gasa_setup_info.omega": gasa.gasa_setup_info.omega.offset,
         "gasa_setup_info.seconds": gasa.gasa_setup_info.seconds.offset,
         "gasa_setup_info.device_bytes": gasa.gasa_setup_info.device_bytes.offset,

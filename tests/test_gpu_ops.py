@@ -40,6 +40,13 @@ CASES_MV = [
     (64, 64, 36, 36, 16, 9),      # 36-row blocks: two rows per lane
     (50, 40, 13, 17, 30, 10),
     (33, 900, 4, 10, 70, 11),     # restriction-shaped, more blocks than lanes
+    (70, 70, 8, 8, 20, 12),       # lane groups of 8
+    (40, 40, 16, 16, 12, 13),     # lane groups of 16
+    (20, 20, 32, 32, 8, 14),      # one lane group
+    # (the cases above with <= 4096 block rows take one CTA per block row)
+    (5000, 5000, 4, 4, 6, 21),    # > 4096 short-ish rows, few threads: lane groups of a warp
+    (5000, 3000, 5, 10, 6, 22),   # same, non-power-of-two height: lane per block
+    (4500, 4500, 13, 13, 5, 23),
 ]
 
 
@@ -99,7 +106,9 @@ def _jacobi_inputs(n, bs, seed, per_row=4):
 
 @pytest.mark.parametrize("n,bs,seed,per_row", [
     (1031, 3, 11, 4), (517, 10, 12, 4), (129, 17, 13, 4), (77, 40, 14, 4),
-    (301, 4, 15, 20), (97, 13, 16, 40), (40, 36, 17, 30)])   # last three: warp per block row
+    (301, 4, 15, 20), (97, 13, 16, 40), (40, 36, 17, 30),   # warp per block row
+    (90, 8, 18, 16), (33, 16, 19, 12), (20, 32, 20, 8),     # CTA per block row
+    (5000, 4, 24, 6), (4500, 13, 25, 5)])                   # warp per block row
 def test_jacobi_sweep_fp64(n, bs, seed, per_row):
     gasa = _gasa()
     ptr, col, val, W, x, b = _jacobi_inputs(n, bs, seed, per_row)
@@ -223,6 +232,38 @@ def test_tentative(n_units, bs, size, r, s_next, seed):
     for J in range(n_agg):
         k = min(r, len(sv[J]))
         assert rel_err(sg[J, :k], sv[J][:k]) <= 1e-12
+
+
+@pytest.mark.parametrize("rank,s_next", [(2, 4), (1, 3), (0, 2)])
+def test_tentative_rank_deficient_blocks(rank, s_next):
+    """Candidate blocks of lower numerical rank than the kept count: the
+    kept vectors with zero singular value are completed the same way on
+    both sides (Gram-Schmidt of unit vectors), so T agrees column by column."""
+    gasa = _gasa()
+    n_units, bs, r, size = 64, 3, 12, 4
+    n = n_units * bs
+    if rank:
+        B = RO.random_normal(n * rank, 71).reshape(n, rank) @ RO.random_normal(rank * r, 72).reshape(rank, r)
+    else:
+        B = np.zeros((n, r))
+    B = np.asfortranarray(B)
+    agg = RO.chunk_aggregates(n_units, size)
+    n_agg = n_units // size
+    up = np.arange(n_units + 1) * bs
+    Tw, _, _ = O.tentative(B, agg, up, n_agg, 3.0, keep=[s_next] * n_agg)
+    T = to_dev(np.zeros(n * s_next))
+    gasa.gasa_tentative(n_units, bs, n_agg, to_dev(agg), to_dev(B.ravel(order="F")), r, s_next, T)
+    Tg = to_host(T).reshape(n, s_next)
+    Td = np.zeros((n, s_next))
+    Tw = Tw.tocsr()
+    for J in range(n_agg):
+        rows = np.arange(J * size * bs, (J + 1) * size * bs)
+        Td[rows] = Tw[rows][:, J * s_next:(J + 1) * s_next].toarray()
+    assert np.max(np.abs(Tg - Td)) <= 1e-10
+    for J in range(n_agg):
+        rows = np.arange(J * size * bs, (J + 1) * size * bs)
+        TJ = Tg[rows]
+        assert np.max(np.abs(TJ.T @ TJ - np.eye(s_next))) <= 1e-13
 
 
 @pytest.mark.parametrize("n", [1, 8, 192, 517])

@@ -23,6 +23,27 @@ def _gasa():
     return gasa
 
 
+def level_tolerances(H, base=1e-8):
+    """Tolerance of the level-k hierarchy values.  Kept singular vectors move
+    by about eps * sigma_1 / gap under rounding (Wedin's bound), gap being
+    the distance between the last kept and the first discarded singular
+    value; the perturbation then passes through the relaxation and products
+    of the levels below, covered by a factor 100.  Aggregates whose last kept
+    value is numerically zero use the deterministic completion and do not
+    limit the bound."""
+    tol, worst = [], base
+    for k, L in enumerate(H.levels):
+        tol.append(worst)
+        if L.svals is None:
+            continue
+        s = int(np.diff(H.levels[k + 1].unit_ptr)[0])
+        for sv in L.svals:
+            if s < sv.size and sv[s - 1] > 1e-10 * sv[0]:
+                gap = (sv[s - 1] - sv[s]) / sv[0]
+                worst = max(worst, 100 * 2.2e-16 / max(gap, 1e-300))
+    return tol
+
+
 def sparse_rel(G, Ref):
     """max |G - Ref| / max |Ref| over stored entries of either matrix"""
     D = (G - Ref).tocsr()
@@ -44,6 +65,7 @@ def test_setup_hierarchy(name):
     gasa = _gasa()
     H = oracle_setup(name)
     ctx, info = gpu_setup(name)
+    tol = level_tolerances(H)
     try:
         assert info.n_levels == len(H.levels)
         for k, L in enumerate(H.levels):
@@ -57,17 +79,17 @@ def test_setup_hierarchy(name):
             np.testing.assert_array_equal(rp, optr)
             np.testing.assert_array_equal(col, ocol)
             Ag = bsr_scipy(rp, col, val)
-            assert sparse_rel(Ag, L.A) <= 1e-8
+            assert sparse_rel(Ag, L.A) <= tol[k]
             if k == len(H.levels) - 1:
                 Ci = gasa.gasa_get_level(ctx, k, gasa.GASA_LV_COARSE_INV, np.zeros(L.n * L.n)).reshape(L.n, L.n)
-                assert rel_err(Ci, np.linalg.inv(H.coarse)) <= 1e-7
+                assert rel_err(Ci, np.linalg.inv(H.coarse)) <= 100 * tol[k]
                 continue
-            assert abs(info.rho[k] - L.rho) <= 1e-10 * L.rho
-            assert abs(info.omega[k] - L.omega) <= 1e-10 * L.omega
+            assert abs(info.rho[k] - L.rho) <= 1e-2 * tol[k] * L.rho
+            assert abs(info.omega[k] - L.omega) <= 1e-2 * tol[k] * L.omega
             sw = gasa.gasa_get_level(ctx, k, gasa.GASA_LV_SWEEPS, np.zeros(sh["r"], np.int32))
             np.testing.assert_array_equal(sw, L.sweeps)
             W = gasa.gasa_get_level(ctx, k, gasa.GASA_LV_W, np.zeros(sh["units"] * sh["s"] ** 2))
-            assert rel_err(W, L.W.blocks.ravel()) <= 1e-8
+            assert rel_err(W, L.W.blocks.ravel()) <= tol[k]
             # P: pattern bit-exact, values; R = P^T exactly (same numbers)
             sn = sh["s_next"]
             prp, pcol, pval = _level_bsr(gasa, ctx, k, "P", sh, sh["s"], sn, sh["units"])
@@ -76,7 +98,7 @@ def test_setup_hierarchy(name):
             np.testing.assert_array_equal(pcol, ocol)
             n_next = H.levels[k + 1].unit_ptr.size - 1
             Pg = bsr_scipy(prp, pcol, pval, n_next)
-            assert sparse_rel(Pg, L.P) <= 1e-8
+            assert sparse_rel(Pg, L.P) <= tol[k + 1]
             rrp, rcol, rval = _level_bsr(gasa, ctx, k, "R", sh, sn, sh["s"], n_next)
             Rg = bsr_scipy(rrp, rcol, rval, sh["units"])
             assert (Rg - Pg.T).count_nonzero() == 0
@@ -95,12 +117,20 @@ def test_vcycle(name):
         want = M(pr.rhs)
         z = to_dev(np.zeros_like(pr.rhs))
         gasa.gasa_vcycle(ctx, to_dev(pr.rhs), z)
-        assert rel_err(to_host(z), want) <= 1e-9
+        assert rel_err(to_host(z), want) <= 0.1 * level_tolerances(H)[-1]
         Mf = O.make_vcycle(H, "fp32")
         wantf = Mf(pr.rhs)
         gasa.gasa_vcycle(ctx, to_dev(pr.rhs), z, gasa.GASA_PREC_MIXED32)
         assert rel_err(to_host(z), want) <= 1e-4
         assert rel_err(to_host(z), wantf) <= 1e-4
+        # FP16 level-0 blocks: same stored values as the oracle's emulation
+        # (float32 arithmetic in a different order), and within FP16's
+        # resolution of the FP64 cycle
+        Mh = O.make_vcycle(H, "fp16")
+        wanth = Mh(pr.rhs)
+        gasa.gasa_vcycle(ctx, to_dev(pr.rhs), z, gasa.GASA_PREC_MIXED16)
+        assert rel_err(to_host(z), wanth) <= 1e-4
+        assert rel_err(to_host(z), want) <= 1e-2
     finally:
         gasa.gasa_destroy(ctx)
 
@@ -123,6 +153,11 @@ def test_cg_solve(name):
         info32 = gasa.gasa_solve(ctx, pr.rhs, xm, TOL, gasa.GASA_PREC_MIXED32)
         assert info32.converged and info32.rel_residual <= TOL
         assert abs(info32.iterations - ref32.iterations) <= 1, (info32.iterations, ref32.iterations)
+        ref16 = O.solve(H, pr.rhs, TOL, "cg", precision="mixed16", max_iter=5000)
+        xh = np.zeros_like(pr.rhs)
+        info16 = gasa.gasa_solve(ctx, pr.rhs, xh, TOL, gasa.GASA_PREC_MIXED16)
+        assert info16.converged and info16.rel_residual <= TOL
+        assert abs(info16.iterations - ref16.iterations) <= 1, (info16.iterations, ref16.iterations)
         # device-resident buffers give the same answer
         xd = to_dev(np.zeros_like(pr.rhs))
         info_d = gasa.gasa_solve(ctx, to_dev(pr.rhs), xd, TOL, on_device=True)
@@ -150,8 +185,35 @@ def test_gmres_solve(name):
         info32 = gasa.gasa_solve(ctx, pr.rhs, xm, TOL, gasa.GASA_PREC_MIXED32)
         assert info32.converged and info32.rel_residual <= TOL
         assert abs(info32.iterations - ref32.iterations) <= 1, (info32.iterations, ref32.iterations)
+        ref16 = O.solve(H, pr.rhs, TOL, "gmres", precision="mixed16", restart=30, max_iter=5000)
+        info16 = gasa.gasa_solve(ctx, pr.rhs, xm, TOL, gasa.GASA_PREC_MIXED16)
+        assert info16.converged and info16.rel_residual <= TOL
+        assert abs(info16.iterations - ref16.iterations) <= 1, (info16.iterations, ref16.iterations)
     finally:
         gasa.gasa_destroy(ctx)
+
+
+@pytest.mark.parametrize("name", ["p3_16", "p3_32"])
+def test_bulk_staged_sweep_same_bits(name):
+    """The level-0 FP32 smoothing step with bulk-copy staging computes the
+    same operations in the same order as the unstaged kernel: the solves
+    agree bit for bit (10x10 blocks qualify for staging)."""
+    gasa = _gasa()
+    pr = problem(name)
+    out = []
+    for staging in (1, 0):
+        ctx, _ = gpu_setup(name, keep=False, bulk_staging=staging)
+        try:
+            x = np.zeros_like(pr.rhs)
+            info = gasa.gasa_solve(ctx, pr.rhs, x, TOL, gasa.GASA_PREC_MIXED32)
+            z = to_dev(np.zeros_like(pr.rhs))
+            gasa.gasa_vcycle(ctx, to_dev(pr.rhs), z, gasa.GASA_PREC_MIXED32)
+            out.append((info.iterations, x, to_host(z)))
+        finally:
+            gasa.gasa_destroy(ctx)
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2], out[1][2])
 
 
 @pytest.mark.parametrize("name", ["c1", "p3_16"])

@@ -344,6 +344,22 @@ def test_stationary_solver(tiny):
     assert res.converged
 
 
+def test_fp16_block_storage():
+    """Values k/1024 of the block maximum are stored exactly; otherwise the
+    dequantised value is within half an FP16 unit (2^-11 relative to the
+    block maximum) of the original, and zero blocks stay zero."""
+    s = 3.5
+    exact = np.array([[[1.0, -0.5, 0.25], [3.0 / 1024, 0.0, -1.0]]]) * s
+    np.testing.assert_array_equal(O.fp16_blocks(exact), exact.astype(np.float32))
+    blocks = RO.random_blocks(200, 5, 81) * np.exp(RO.random_vector(200, 82) * 5)[:, None, None]
+    blocks[7] = 0.0
+    d = O.fp16_blocks(blocks)
+    m = np.max(np.abs(blocks), axis=(1, 2))
+    err = np.max(np.abs(d - blocks), axis=(1, 2))
+    assert np.all(err <= 2.0 ** -11 * m * (1 + 1e-6) + 1e-300)
+    assert np.all(d[7] == 0.0)
+
+
 def test_null_singular_vectors_completed_deterministically():
     """A rank-1 block (every candidate column a multiple of e_0) keeping two
     vectors: the first is e_0, the second (zero singular value) is the
