@@ -181,9 +181,10 @@ gasa_status gasa_get_level(gasa_ctx *ctx, int32_t level, int32_t what,
                            void *host_out, int64_t n_bytes);
 
 /* Per-kernel timing over CUDA events on the context stream (for the
- * benchmark's roofline): class 0 = level-0 smoothing sweeps, 1 = level-0
- * residual SpMV, 2 = outer A*p SpMV.  Enable, run, then read total
- * milliseconds, launches and algorithmic bytes moved. */
+ * benchmark's roofline): class 0 = level-0 smoothing sweeps
+ * x + w D^{-1}(b - A x), 1 = level-0 residual SpMV, 2 = outer A*p SpMV,
+ * 3 = level-0 first pre-smoothing step x = w D^{-1} b.  Enable, run, then
+ * read total milliseconds, launches and algorithmic bytes moved. */
 gasa_status gasa_profile_enable(gasa_ctx *ctx, int32_t on);
 gasa_status gasa_profile_read(gasa_ctx *ctx, int32_t kernel_class, double *ms,
                               int64_t *launches, double *bytes);

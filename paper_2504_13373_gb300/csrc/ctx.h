@@ -1,0 +1,99 @@
+// Device-resident state of a set-up hierarchy, shared by the solver entry
+// points and the request server.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "gasa.h"
+
+namespace gasa {
+
+struct DevBSR {
+  int nrows = 0, ncols = 0, br = 0, bc = 0;
+  int64_t nnzb = 0;
+  int *rp = nullptr, *col = nullptr;
+  double *val = nullptr;
+  float *val32 = nullptr;
+  __half *val16 = nullptr;     // FP16 blocks (level 0, MIXED16)
+  float *scale16 = nullptr;    // one scale per block
+};
+
+struct Level {
+  int n = 0;          // units on this level
+  int s = 0;          // dofs per unit
+  int64_t ndof = 0;
+  DevBSR A;
+  double *W = nullptr;        // w D^{-1}
+  float *W32 = nullptr;
+  __half *W16 = nullptr;       // FP16 blocks of w D^{-1} (level 0, MIXED16)
+  float *W16s = nullptr;
+  // transfer to the next level
+  int *agg = nullptr;
+  int n_next = 0, s_next = 0, max_children = 0;
+  int *child_ptr = nullptr, *child_idx = nullptr;
+  double *T = nullptr;
+  DevBSR P, R;
+  double *cand = nullptr, *cand_in = nullptr;
+  std::vector<int> sweeps;
+  double omega = 0.0, rho = 0.0;
+  // bulk-copy staged FP32 smoothing step (level 0): plan from tma_plan
+  bool tma = false;
+  int tma_TR = 0, tma_stageA = 0, tma_stageW = 0, tma_smem = 0, tma_grid = 0;
+  // V-cycle vectors
+  double *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr;
+  float *xf = nullptr, *x2f = nullptr, *bf = nullptr, *rf = nullptr;
+};
+
+struct ProfClass {
+  std::vector<cudaEvent_t> ev;    // pairs
+  size_t used = 0;
+  double bytes = 0.0;
+  int64_t launches = 0;
+};
+
+}  // namespace gasa
+
+struct gasa_ctx {
+  using DevBSR = gasa::DevBSR;
+  using Level = gasa::Level;
+  using ProfClass = gasa::ProfClass;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  bool ready = false;
+  gasa_options opt{};
+  int N = 0;
+  int r = 0;
+  std::vector<Level> L;
+  double *coarse_inv = nullptr;
+  int nc = 0;
+  std::vector<void *> allocs;     // hierarchy allocations
+  // Krylov workspace
+  double *kx = nullptr, *kr = nullptr, *kz = nullptr, *kp = nullptr, *kq = nullptr,
+         *kzold = nullptr, *kb = nullptr, *kt = nullptr;
+  double *part = nullptr;         // 4 x kRedBlocks partials
+  double *scal = nullptr;         // device scalars
+  double *hscal = nullptr;        // pinned host mirror
+  float *kf_in = nullptr, *kf_out = nullptr;
+  double *V = nullptr, *Z = nullptr, *H = nullptr, *gm = nullptr, *mpart = nullptr;
+  int gm_restart = 0;
+  bool gm_flex = false;
+  // graph-resident CG: one instantiated graph per precision, the whole CG
+  // iteration (V-cycle included) inside a conditional while node
+  cudaGraph_t cg_graph[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t cg_exec[3] = {nullptr, nullptr, nullptr};
+  long long cg_kernels[3] = {0, 0, 0};
+  int cg_max_iter[3] = {0, 0, 0};
+  int *d_iters = nullptr;
+  int *d_err = nullptr;          // set by kernels whose bounded waits time out
+  // profiling
+  bool prof = false;
+  ProfClass pc[4];
+  double setup_seconds = 0.0;
+  int64_t device_bytes = 0;
+};
+

@@ -57,10 +57,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
   return ok != 0;
 }
 
-// bounded wait: about a second of try_wait rounds at most
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// bounded wait: gives up after one second of wall time (or 2^24 rounds)
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity) {
-  for (int it = 0; it < (1 << 22); ++it)
+  const unsigned long long t0 = global_ns();
+  for (int it = 0; it < (1 << 24); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255) == 255 && global_ns() - t0 > 1000000000ull) return false;
+  }
   return false;
 }
 
@@ -95,7 +104,7 @@ jacobi_tma_kernel(int n_units, int TR, int n_tiles, int stageA, int stageW,
     const unsigned ab = (unsigned)((k1 - k0) * BSZ * sizeof(T));
     const unsigned wb = (unsigned)((i1 - i0) * BSZ * sizeof(T));
     mbar_arrive_expect_tx(&bar[st], ab + wb);
-    bulk_g2s(sA(st), val + (size_t)k0 * BSZ, ab, &bar[st]);
+    if (ab) bulk_g2s(sA(st), val + (size_t)k0 * BSZ, ab, &bar[st]);
     bulk_g2s(sW(st), Wm + (size_t)i0 * BSZ, wb, &bar[st]);
   };
   if (tid == 0 && blockIdx.x < n_tiles) issue(blockIdx.x, 0);
