@@ -68,6 +68,8 @@ def parse():
                     help="with --profile-run: drive the CG loop from the host (per-kernel ncu)")
     ap.add_argument("--bulk-staging", action="store_true",
                     help="level-0 FP32 sweep with bulk-copy (TMA) staging of A and w D^-1")
+    ap.add_argument("--serve-requests", type=int, default=512,
+                    help="requests of the serving stream (0: skip the serving measurement)")
     return ap.parse_args()
 
 
@@ -242,6 +244,102 @@ def reference_main(args, rank, world):
 ITERS_PER_SOLVE = {256: 3348, 64: 906}
 
 
+def serve_bench(gasa, n_requests, device=0):
+    """Serving stream: 8 resident meshes (2D/3D SIPG Poisson and 2D LDG
+    convection-diffusion, P1-P3, 1e3-2e6 dofs), requests with N(0,1)
+    right-hand sides.  Saturated throughput with every request queued at
+    once, then open-loop Poisson arrivals at 0.5x and 1.5x that rate; latency
+    is submit-to-completion as the server records it."""
+    from synth import configs, serving
+    seed = configs.SEED
+    t0 = time.perf_counter()
+    specs = serving.mesh_specs(seed)
+    probs = [serving.build_mesh(sp, seed) for sp in specs]
+    t_gen = time.perf_counter() - t0
+    ctxs, setup_s, hier_bytes = [], [], []
+    for pr in probs:
+        ctx = gasa.gasa_create(device)
+        opt = gasa.gasa_default_options(dim=pr.dim, n_cand=pr.r, max_iter=20000,
+                                        solver=gasa.GASA_SOLVER_CG if pr.solver == "cg"
+                                        else gasa.GASA_SOLVER_GMRES)
+        info = gasa.gasa_setup(ctx, pr.A.row_ptr, pr.A.col, pr.A.val.ravel(), pr.A.b, pr.agg_of,
+                               opt, adj_ptr=pr.adj_ptr, adj_idx=pr.adj_idx,
+                               centroids=pr.centroids, init_candidates=pr.B0)
+        ctxs.append(ctx)
+        setup_s.append(info.seconds)
+        hier_bytes.append(info.device_bytes)
+    which = serving.request_mesh(seed, n_requests)
+    rhs = [serving.request_rhs(seed, i, probs[m].n_dofs) for i, m in enumerate(which)]
+    budget = 40 << 30
+    srv = gasa.gasa_server_create(device, budget, 8)
+    out = {"meshes": [dict(name=sp.name, dofs=sp.dofs, levels=pr.n_levels, r=pr.r,
+                           solver=pr.solver, setup_s=su)
+                      for sp, pr, su in zip(specs, probs, setup_s)],
+           "requests": n_requests, "budget_bytes": budget, "max_batch": 8,
+           "generate_s": t_gen}
+    try:
+        ids = [gasa.gasa_server_add_mesh(srv, c) for c in ctxs]
+
+        def run(prec, times=None):
+            """Submit every request (at `times` seconds from the start if
+            given), wait for all; (wall seconds, latencies, iterations)."""
+            tickets = []
+            start = time.perf_counter()
+            for i, m in enumerate(which):
+                if times is not None:
+                    wait = start + times[i] - time.perf_counter()
+                    if wait > 0:
+                        time.sleep(wait)
+                tickets.append(gasa.gasa_server_submit(srv, ids[m], rhs[i], TOL, prec))
+            gasa.gasa_server_drain(srv, 1800.0)
+            wall = time.perf_counter() - start
+            lat, its, worst = [], [], 0.0
+            for t in tickets:
+                st, info = gasa.gasa_server_poll(srv, t)
+                if st != gasa.GASA_OK:
+                    raise RuntimeError(f"served solve failed: {gasa.gasa_status_string(st)}")
+                lat.append(info.seconds * 1e3)
+                its.append(info.iterations)
+                worst = max(worst, info.rel_residual)
+            return wall, np.array(lat), np.array(its), worst
+
+        for name, prec in (("mixed", gasa.GASA_PREC_MIXED32), ("fp64", gasa.GASA_PREC_FP64)):
+            # warm-up: one request per mesh creates the engines and their graphs
+            for m in range(len(ctxs)):
+                gasa.gasa_server_submit(srv, ids[m], serving.request_rhs(seed, 10 ** 6 + m,
+                                                                         probs[m].n_dofs), TOL, prec)
+            gasa.gasa_server_drain(srv, 600.0)
+            st0 = gasa.gasa_server_stats_read(srv)
+            wall, lat, its, worst = run(prec)
+            sat = n_requests / wall
+            res = {"saturated": {"solves_per_s": sat, "wall_s": wall,
+                                 "p50_ms": float(np.percentile(lat, 50)),
+                                 "p99_ms": float(np.percentile(lat, 99))},
+                   "iterations_median": float(np.median(its)), "rel_residual_max": worst,
+                   "per_mesh": {specs[m].name: {"requests": int((which == m).sum()),
+                                                "iterations_median": float(np.median(its[which == m])),
+                                                "iterations_max": int(its[which == m].max()),
+                                                "latency_p50_ms": float(np.percentile(lat[which == m], 50))}
+                                for m in range(len(specs)) if (which == m).any()}}
+            for f in (0.5, 1.5):
+                times = serving.arrival_times(seed, n_requests, f * sat)
+                wall, lat, its, worst = run(prec, times)
+                res[f"open_loop_{f:g}x"] = {
+                    "rate_per_s": f * sat, "solves_per_s": n_requests / wall,
+                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+                res["rel_residual_max"] = max(res["rel_residual_max"], worst)
+            st1 = gasa.gasa_server_stats_read(srv)
+            res["graph_launches"] = st1["graph_launches"] - st0["graph_launches"]
+            res["peak_running"] = st1["peak_running"]
+            out[name] = res
+        out["peak_bytes"] = gasa.gasa_server_stats_read(srv)["peak_bytes"]
+    finally:
+        gasa.gasa_server_destroy(srv)
+        for c in ctxs:
+            gasa.gasa_destroy(c)
+    return out
+
+
 def ours_main(args, rank, world, local):
     import torch
     if not torch.cuda.is_available():
@@ -408,6 +506,8 @@ def ours_main(args, rank, world, local):
             line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
                                     "sample": f"failed: {err}"}
     gasa.gasa_destroy(ctx)
+    if args.serve_requests > 0:
+        line["serving"] = serve_bench(gasa, args.serve_requests, local)
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:

@@ -50,7 +50,9 @@ typedef enum {
   GASA_ERR_STATE = 12           /* call out of order (e.g. solve before setup) */
 } gasa_status;
 
-enum { GASA_SOLVER_CG = 0, GASA_SOLVER_GMRES = 1 };
+/* CG (SPD, Section 6), left-preconditioned GMRES (Section 6), or the V-cycle
+ * of Alg. 2 as a stationary iteration x <- x + V(b - A x) */
+enum { GASA_SOLVER_CG = 0, GASA_SOLVER_GMRES = 1, GASA_SOLVER_STATIONARY = 2 };
 /* FP64: FP64 V-cycle.  MIXED32: FP32 V-cycle (FP32 storage and arithmetic)
  * inside FP64 flexible CG / FGMRES.  MIXED16: as MIXED32, with the level-0
  * operator and block inverses stored as FP16 blocks with one FP32 scale per
@@ -85,7 +87,7 @@ typedef struct {
 
 typedef struct {
   int32_t dim;               /* spatial dimension d (sets n_cut default) */
-  int32_t solver;            /* GASA_SOLVER_CG (SPD) or GASA_SOLVER_GMRES */
+  int32_t solver;            /* GASA_SOLVER_CG (SPD), GASA_SOLVER_GMRES or GASA_SOLVER_STATIONARY */
   int32_t restart;           /* GMRES restart length (default 30) */
   int32_t precision;         /* GASA_PREC_FP64 or GASA_PREC_MIXED32 */
   int32_t t_pre, t_post;     /* smoothing steps (Section 6: 3 and 3) */
@@ -100,9 +102,14 @@ typedef struct {
   double n_cut;              /* Eq. sik cut factor; 0 = 2^d - (d - 1) */
   uint64_t seed;             /* splitmix64 seed of the power-iteration vectors */
   const double *init_candidates; /* optional host B^0, n x r column-major; NULL = N(0,1) drawn on device */
-  int32_t bulk_staging;      /* 1 (default): level-0 FP32 smoothing steps stage A and w D^-1 in
-                                shared memory by bulk copies where the block size allows; 0: off.
-                                Both give the same bits. */
+  int32_t bulk_staging;      /* 1: level-0 FP32 smoothing steps stage A and w D^-1 in shared
+                                memory by bulk copies where the block size allows; 0 (default):
+                                plain loads (faster on the measured workloads).  Both give the
+                                same bits. */
+  int32_t matrix_free_levels; /* kappa of Section 4.4: A_1 .. A_kappa (kappa < N) are not kept
+                                after setup and are applied as R_{k-1} A_{k-1} P_{k-1}
+                                (Eq. matfree2 with the transfers unrolled); their block
+                                inverses are kept.  0 (default): every A_k stored. */
 } gasa_options;
 
 typedef struct {
@@ -288,6 +295,64 @@ gasa_status gasa_power_estimate_noalloc(int32_t n_units, int32_t bs, const int32
  * of Alg. 2.  *singular (host) is set to 1 if a pivot vanishes. */
 gasa_status gasa_dense_inverse(int32_t n, const double *A, double *Ainv, int32_t *singular,
                                void *stream);
+
+/* ------------------------------------------------------------------ */
+/* request server: continuous batching of solves on resident hierarchies */
+/* ------------------------------------------------------------------ */
+/* The paper solves one system at a time; this server is not in it.  It keeps
+ * the hierarchies of several set-up contexts (meshes) resident and runs the
+ * solves submitted for them in batches: for each (mesh, precision) an engine
+ * holds K slots whose right-hand sides are stored interleaved, so every
+ * matrix block of the V-cycle (Alg. 2) and of the outer A x is read once for
+ * the whole batch.  One engine step is a CUDA graph launch: for CG a
+ * conditional loop of whole iterations, for GMRES one restart cycle.
+ * Requests join free slots between launches (CG: between iterations; GMRES:
+ * between cycles) and leave when they converge, so the batch changes while
+ * others are in flight.  Engines of different meshes run on their own
+ * streams and overlap on the device.  Every result depends only on its own
+ * column (per-column reductions of fixed shape), so a solve gives the same
+ * bits alone and in any mix.  Device memory for hierarchies and engines is
+ * admitted against the budget given at creation; a request whose engine does
+ * not fit waits until idle engines are released.
+ * Precisions: GASA_PREC_FP64 and GASA_PREC_MIXED32. */
+typedef struct gasa_server gasa_server;
+
+typedef struct {
+  int64_t submitted, completed, queued, running;
+  int64_t engines, engines_created, engines_released;
+  int64_t budget_bytes, used_bytes, peak_bytes;
+  int64_t peak_running;        /* most slots iterating at the same time */
+  int64_t graph_launches;
+} gasa_server_stats;
+
+/* max_batch: slots per engine, 1, 2, 4 or 8 (an engine takes fewer when the
+ * budget does not hold max_batch).  Starts no work until a request arrives. */
+gasa_status gasa_server_create(gasa_server **srv, int32_t device, int64_t hbm_budget_bytes,
+                               int32_t max_batch);
+/* Register a set-up context.  The server reads its hierarchy (solver, restart,
+ * max_iter and tolerances come from its options and the request); the caller
+ * keeps the context alive and unchanged until gasa_server_destroy.  The
+ * hierarchy's bytes count against the budget: GASA_ERR_BUDGET if it does not
+ * fit. */
+gasa_status gasa_server_add_mesh(gasa_server *srv, gasa_ctx *ctx, int32_t *mesh_id);
+/* Queue a solve of A x = b (b: host, copied before return) to relative
+ * residual tol from x = 0.  Returns at once with a ticket. */
+gasa_status gasa_server_submit(gasa_server *srv, int32_t mesh_id, const double *b, double tol,
+                               int32_t precision, uint64_t *ticket);
+/* GASA_PENDING while the solve is queued or running.  Once finished: copies
+ * x to x_out (host, nullable) and the solve's info (seconds = latency from
+ * submit to completion), releases the ticket and returns the solve's status
+ * (GASA_OK, GASA_ERR_NOT_CONVERGED with the last iterate, or an error). */
+gasa_status gasa_server_poll(gasa_server *srv, uint64_t ticket, double *x_out,
+                             gasa_solve_info *info);
+/* Block until no request is queued or running, or timeout_s elapses
+ * (GASA_ERR_TIMEOUT). */
+gasa_status gasa_server_drain(gasa_server *srv, double timeout_s);
+gasa_status gasa_server_stats_read(gasa_server *srv, gasa_server_stats *out);
+/* Stop the engines (requests still queued or running end with
+ * GASA_ERR_STATE) and free the server's device memory. */
+gasa_status gasa_server_destroy(gasa_server *srv);
+const char *gasa_server_last_error(const gasa_server *srv);
 
 #ifdef __cplusplus
 }

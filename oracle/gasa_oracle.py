@@ -445,11 +445,26 @@ def fp16_blocks(blocks: np.ndarray) -> np.ndarray:
     return h.astype(np.float32) * s[:, None, None]
 
 
-def make_vcycle(H: Hierarchy, precision: str = "fp64"):
+class GalerkinOperator:
+    """A_k applied without storing it (Section 4.4, Eq. matfree2 with the
+    multi-level transfers of Eq. matfree1 unrolled): A_k x = R_{k-1} (A_{k-1}
+    (P_{k-1} x)), where A_{k-1} is itself stored or of this kind."""
+
+    def __init__(self, R, A_prev, P):
+        self.R, self.A_prev, self.P = R, A_prev, P
+
+    def __matmul__(self, x):
+        return self.R @ (self.A_prev @ (self.P @ x))
+
+
+def make_vcycle(H: Hierarchy, precision: str = "fp64", matrix_free_levels: int = 0):
     """Returns a function f -> u approximating A^{-1} f by one V-cycle.
     precision: 'fp64', 'fp32' (float32 operators and vectors), or 'fp16'
     (as 'fp32', with the level-0 operator and block inverses stored as FP16
-    blocks with one scale per block)."""
+    blocks with one scale per block).  matrix_free_levels = kappa: the
+    operators A_1 .. A_kappa (kappa < N) are applied through the transfers
+    (Section 4.4) instead of being used as stored matrices; in 'fp16' the
+    level-0 operator inside those products is the float32 one."""
     N = H.N
     if precision == "fp64":
         dt = np.float64
@@ -471,6 +486,12 @@ def make_vcycle(H: Hierarchy, precision: str = "fp64"):
             As[0] = sp.bsr_matrix((fp16_blocks(Ab.data.astype(np.float64)), Ab.indices, Ab.indptr),
                                   shape=Ab.shape).tocsr()
             Ws[0] = BlockDiag(L0.unit_ptr, fp16_blocks(L0.W.blocks))
+    if matrix_free_levels > 0:
+        stored0 = As[0] if precision != "fp16" else H.levels[0].A.astype(np.float32)
+        prev = stored0
+        for k in range(1, min(matrix_free_levels, N - 1) + 1):
+            prev = GalerkinOperator(Rs[k - 1], prev, Ps[k - 1])
+            As[k] = prev
     coarse = H.coarse
 
     def vcycle(f):
@@ -608,11 +629,13 @@ def gmres(A, b, M, tol=1e-10, restart=30, max_iter=1000, flexible=False) -> Solv
     return SolveResult(x, total, rel, rel <= tol, hist)
 
 
-def solve(H: Hierarchy, b, tol=1e-10, solver="cg", precision="fp64", restart=30, max_iter=500):
+def solve(H: Hierarchy, b, tol=1e-10, solver="cg", precision="fp64", restart=30, max_iter=500,
+          matrix_free_levels=0):
     """x = A_0^{-1} b by V-cycle-preconditioned CG or GMRES (FP64 outer loop;
     with precision='mixed32' the V-cycle is float32 and the outer loop is
     flexible)."""
-    M = make_vcycle(H, {"fp64": "fp64", "mixed32": "fp32", "mixed16": "fp16"}[precision])
+    M = make_vcycle(H, {"fp64": "fp64", "mixed32": "fp32", "mixed16": "fp16"}[precision],
+                    matrix_free_levels)
     flex = precision != "fp64"
     A = H.levels[0].A
     if solver == "cg":
@@ -620,9 +643,11 @@ def solve(H: Hierarchy, b, tol=1e-10, solver="cg", precision="fp64", restart=30,
     return gmres(A, b, M, tol, restart, max_iter, flexible=flex)
 
 
-def stationary(H: Hierarchy, b, tol=1e-10, max_iter=200) -> SolveResult:
-    """Alg. 2 as a solver: x <- x + V(b - A x) until ||b - A x|| <= tol ||b||."""
-    M = make_vcycle(H)
+def stationary(H: Hierarchy, b, tol=1e-10, max_iter=200, precision="fp64") -> SolveResult:
+    """Alg. 2 as a solver: x <- x + V(b - A x) until ||b - A x|| <= tol ||b||.
+    With precision='mixed32' the V-cycle is float32 and the residual and
+    update stay float64 (iterative refinement)."""
+    M = make_vcycle(H, {"fp64": "fp64", "mixed32": "fp32", "mixed16": "fp16"}[precision])
     A = H.levels[0].A
     bn = np.linalg.norm(b)
     x = np.zeros_like(b)

@@ -45,6 +45,11 @@ struct Level {
   // V-cycle vectors
   double *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr;
   float *xf = nullptr, *x2f = nullptr, *bf = nullptr, *rf = nullptr;
+  // matrix-free level (Section 4.4): A is applied as R_{k-1} A_{k-1} P_{k-1};
+  // mt / mu are this level's scratch for the product of the level above
+  bool mf = false;
+  double *mt = nullptr, *mu = nullptr;
+  float *mtf = nullptr, *muf = nullptr;
 };
 
 struct ProfClass {
@@ -84,10 +89,11 @@ struct gasa_ctx {
   bool gm_flex = false;
   // graph-resident CG: one instantiated graph per precision, the whole CG
   // iteration (V-cycle included) inside a conditional while node
-  cudaGraph_t cg_graph[3] = {nullptr, nullptr, nullptr};
-  cudaGraphExec_t cg_exec[3] = {nullptr, nullptr, nullptr};
-  long long cg_kernels[3] = {0, 0, 0};
-  int cg_max_iter[3] = {0, 0, 0};
+  // slots 0-2: CG per precision; 3-5: stationary iteration per precision
+  cudaGraph_t cg_graph[6] = {};
+  cudaGraphExec_t cg_exec[6] = {};
+  long long cg_kernels[6] = {};
+  int cg_max_iter[6] = {};
   int *d_iters = nullptr;
   int *d_err = nullptr;          // set by kernels whose bounded waits time out
   // profiling

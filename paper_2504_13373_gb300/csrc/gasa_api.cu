@@ -76,7 +76,7 @@ void dfree(gasa_ctx *ctx, void *p) {
 }
 
 void free_graphs(gasa_ctx *ctx) {
-  for (int p = 0; p < 3; ++p) {
+  for (int p = 0; p < 6; ++p) {
     if (ctx->cg_exec[p]) cudaGraphExecDestroy(ctx->cg_exec[p]);
     if (ctx->cg_graph[p]) cudaGraphDestroy(ctx->cg_graph[p]);
     ctx->cg_exec[p] = nullptr;
@@ -139,6 +139,8 @@ template <> struct Prec<double> {
   static double *x2(Level &l) { return l.x2; }
   static double *b(Level &l) { return l.b; }
   static double *r(Level &l) { return l.r; }
+  static double *mt(Level &l) { return l.mt; }
+  static double *mu(Level &l) { return l.mu; }
 };
 template <> struct Prec<float> {
   static const float *A(const DevBSR &m) { return m.val32; }
@@ -147,7 +149,29 @@ template <> struct Prec<float> {
   static float *x2(Level &l) { return l.x2f; }
   static float *b(Level &l) { return l.bf; }
   static float *r(Level &l) { return l.rf; }
+  static float *mt(Level &l) { return l.mtf; }
+  static float *mu(Level &l) { return l.muf; }
 };
+
+// y = A_k x (mode ASSIGN) or y = b - A_k x (RESIDUAL) on a matrix-free level
+// k >= 1: A_k x = R_{k-1} (A_{k-1} (P_{k-1} x)) (Section 4.4, Eq. matfree2
+// with the transfers unrolled), recursively while A_{k-1} is matrix-free too
+template <typename T>
+cudaError_t mf_apply(gasa_ctx *ctx, int k, int mode, const T *x, const T *b, T *y) {
+  using P = Prec<T>;
+  cudaStream_t s = ctx->stream;
+  Level &lp = ctx->L[k - 1];
+  T *t = P::mt(lp), *u = P::mu(lp);
+  cudaError_t e = launch_bsr_mv<T>(GASA_MV_ASSIGN, lp.P.nrows, lp.P.br, lp.P.bc, lp.P.rp, lp.P.col,
+                                   P::A(lp.P), x, nullptr, t, s, lp.P.nnzb);
+  if (e != cudaSuccess) return e;
+  if (k - 1 > 0 && lp.mf) e = mf_apply<T>(ctx, k - 1, GASA_MV_ASSIGN, t, nullptr, u);
+  else e = launch_bsr_mv<T>(GASA_MV_ASSIGN, lp.n, lp.s, lp.s, lp.A.rp, lp.A.col, P::A(lp.A), t,
+                            nullptr, u, s, lp.A.nnzb);
+  if (e != cudaSuccess) return e;
+  return launch_bsr_mv<T>(mode, lp.R.nrows, lp.R.br, lp.R.bc, lp.R.rp, lp.R.col, P::A(lp.R), u, b,
+                          y, s, lp.R.nnzb);
+}
 
 // algorithmic bytes of one launch: w bytes per vector entry, wa bytes per
 // matrix value (FP16 blocks add one 4-byte scale per block)
@@ -188,6 +212,15 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false) {
                                         l.tma_smem, l.tma_grid, l.A.rp, l.A.col, l.A.val32,
                                         l.W32, xin, bb, xo, ctx->d_err, s);
     }
+    if (l.mf && mode == JAC_SWEEP) {
+      // x_out = x + W (b - A_k x) with A_k applied through the transfers
+      cudaError_t e = mf_apply<T>(ctx, k, GASA_MV_RESIDUAL, xin, bb, P::r(l));
+      if (e == cudaSuccess)
+        e = launch_jacobi<T>(JAC_FIRST, l.n, l.s, nullptr, nullptr, nullptr, P::W(l), nullptr,
+                             P::r(l), xo, s);
+      if (e == cudaSuccess) e = launch_add<T>(l.ndof, xin, xo, s);
+      return e;
+    }
     return launch_jacobi<T>(mode, l.n, l.s, l.A.rp, l.A.col, P::A(l.A), P::W(l), xin, bb, xo, s,
                             l.A.nnzb);
   };
@@ -198,6 +231,7 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false) {
         return launch_bsr_mv_h16(GASA_MV_RESIDUAL, l.n, l.s, l.s, l.A.rp, l.A.col, l.A.val16,
                                  l.A.scale16, xin, bb, rr, s);
     }
+    if (l.mf) return mf_apply<T>(ctx, k, GASA_MV_RESIDUAL, xin, bb, rr);
     return launch_bsr_mv<T>(GASA_MV_RESIDUAL, l.n, l.s, l.s, l.A.rp, l.A.col, P::A(l.A), xin, bb,
                             rr, s, l.A.nnzb);
   };
@@ -439,7 +473,15 @@ gasa_status pcg_graph(gasa_ctx *ctx, const double *b, double tol, int precision,
   const int64_t n = ctx->L[0].ndof;
   *conv = false;
   *iters = 0;
-  ST(build_cg_graph(ctx, precision));
+  gasa_status bst = build_cg_graph(ctx, precision);
+  if (bst != GASA_OK && pdl_enabled()) {
+    // a graph with programmatic launch edges that does not build: build it
+    // with plain stream order instead
+    (void)cudaGetLastError();
+    pdl_set(false);
+    bst = build_cg_graph(ctx, precision);
+  }
+  ST(bst);
   double bb;
   ST(norm2(ctx, n, b, S_BB, &bb));
   const double bn = std::sqrt(bb);
@@ -609,6 +651,123 @@ gasa_status gmres(gasa_ctx *ctx, const double *b, double tol, int precision, int
 }
 
 // ----------------------------------------------------------------------------
+// Alg. 2 as a stand-alone solver: x <- x + V(b - A x) until
+// ||b - A x|| <= tol ||b||.  t = b - A x of the stopping test is the next
+// step's residual.  The loop runs in a conditional while node (or from the
+// host when profiling); b is read from ctx->kb.
+// ----------------------------------------------------------------------------
+gasa_status stationary_step(gasa_ctx *ctx, int precision, int max_iter,
+                            cudaGraphConditionalHandle h, bool in_graph) {
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->L[0].ndof;
+  double *rr_part = ctx->part + kRedBlocks;
+  ST(apply_M(ctx, ctx->kt, ctx->kz, precision));
+  CU(launch_axpy(n, 1.0, ctx->kz, ctx->kx, s));
+  ST(spmv_outer(ctx, GASA_MV_RESIDUAL, ctx->kx, ctx->kb, ctx->kt));
+  CU(launch_dot_partials(n, ctx->kt, nullptr, rr_part, s));
+  if (in_graph) CU(launch_cg_check(rr_part, ctx->scal, ctx->d_iters, max_iter, h, s));
+  else CU(launch_finalize(rr_part, 1, ctx->scal + S_RR, s));
+  return GASA_OK;
+}
+
+gasa_status build_st_graph(gasa_ctx *ctx, int precision) {
+  const int pi = 3 + precision;
+  const int max_iter = ctx->opt.max_iter;
+  if (ctx->cg_exec[pi] && ctx->cg_max_iter[pi] == max_iter) return GASA_OK;
+  if (ctx->cg_exec[pi]) cudaGraphExecDestroy(ctx->cg_exec[pi]);
+  if (ctx->cg_graph[pi]) cudaGraphDestroy(ctx->cg_graph[pi]);
+  ctx->cg_exec[pi] = nullptr;
+  ctx->cg_graph[pi] = nullptr;
+  cudaStream_t s = ctx->stream;
+  cudaGraph_t g = nullptr;
+  CU(cudaGraphCreate(&g, 0));
+  ctx->cg_graph[pi] = g;
+  cudaGraphConditionalHandle h;
+  CU(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CU(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  const bool prof = ctx->prof;
+  ctx->prof = false;
+  const long long k0 = launch_count();
+  CU(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  gasa_status st = stationary_step(ctx, precision, max_iter, h, true);
+  cudaGraph_t captured = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(s, &captured);
+  ctx->prof = prof;
+  ctx->cg_kernels[pi] = launch_count() - k0;
+  if (st != GASA_OK) return st;
+  CU(e2);
+  CU(cudaGraphInstantiate(&ctx->cg_exec[pi], g, 0));
+  ctx->cg_max_iter[pi] = max_iter;
+  return GASA_OK;
+}
+
+gasa_status stationary(gasa_ctx *ctx, const double *b, double tol, int precision, int *iters,
+                       double *relres, bool *conv) {
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->L[0].ndof;
+  const int max_iter = ctx->opt.max_iter;
+  *conv = false;
+  *iters = 0;
+  if (b != ctx->kb)
+    CU(cudaMemcpyAsync(ctx->kb, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  double bb;
+  ST(norm2(ctx, n, ctx->kb, S_BB, &bb));
+  const double bn = std::sqrt(bb);
+  CU(cudaMemsetAsync(ctx->kx, 0, n * sizeof(double), s));
+  if (bn == 0.0) {
+    *relres = 0.0;
+    *conv = true;
+    return GASA_OK;
+  }
+  CU(launch_copy(n, ctx->kb, ctx->kt, s));      // t = b - A 0
+  ctx->hscal[S_PQ] = 1.0;                        // the shared test also checks p^T A p > 0
+  ctx->hscal[S_BN] = bn;
+  ctx->hscal[S_TOL] = tol;
+  CU(cudaMemcpyAsync(ctx->scal + S_PQ, ctx->hscal + S_PQ, sizeof(double), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(ctx->scal + S_BN, ctx->hscal + S_BN, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (ctx->prof) {
+    for (int it = 1; it <= max_iter; ++it) {
+      ST(stationary_step(ctx, precision, max_iter, 0, false));
+      ST(read_scalars(ctx, S_RR, 1));
+      const double rel = std::sqrt(ctx->hscal[S_RR]) / bn;
+      *iters = it;
+      *relres = rel;
+      if (!std::isfinite(rel)) return fail(ctx, GASA_ERR_BREAKDOWN, "stationary: non-finite residual");
+      if (rel <= tol) {
+        *conv = true;
+        return GASA_OK;
+      }
+    }
+    return GASA_OK;
+  }
+  gasa_status bst = build_st_graph(ctx, precision);
+  if (bst != GASA_OK && pdl_enabled()) {
+    (void)cudaGetLastError();
+    pdl_set(false);
+    bst = build_st_graph(ctx, precision);
+  }
+  ST(bst);
+  const int pi = 3 + precision;
+  CU(cudaMemsetAsync(ctx->d_iters, 0, sizeof(int), s));
+  CU(cudaGraphLaunch(ctx->cg_exec[pi], s));
+  int it = 0;
+  CU(cudaMemcpyAsync(&it, ctx->d_iters, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ST(read_scalars(ctx, S_RR, 1));
+  note_launches(ctx->cg_kernels[pi] * (long long)it);
+  *iters = it;
+  *relres = std::sqrt(ctx->hscal[S_RR]) / bn;
+  if (!std::isfinite(*relres)) return fail(ctx, GASA_ERR_BREAKDOWN, "stationary: non-finite residual");
+  *conv = *relres <= tol;
+  return GASA_OK;
+}
+
+// ----------------------------------------------------------------------------
 // setup helpers
 // ----------------------------------------------------------------------------
 int keep_count(int rows, int r, double n_cut) {
@@ -742,7 +901,9 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
   if (hier->n_levels < 2 || hier->n_levels > GASA_MAX_LEVELS || !hier->agg_of)
     return fail(ctx, GASA_ERR_INVALID_ARG, "hierarchy: need 2..GASA_MAX_LEVELS levels");
   if (opt->t_pre < 0 || opt->t_post < 0 || opt->q_power < 0 || opt->max_relax < 0 ||
-      opt->gamma < 0.0 || !(opt->omega_factor > 0.0) || opt->dim < 1 || opt->dim > 3)
+      opt->gamma < 0.0 || !(opt->omega_factor > 0.0) || opt->dim < 1 || opt->dim > 3 ||
+      opt->solver < GASA_SOLVER_CG || opt->solver > GASA_SOLVER_STATIONARY || opt->max_iter < 1 ||
+      opt->matrix_free_levels < 0)
     return fail(ctx, GASA_ERR_INVALID_ARG, "options out of range");
   const int n0 = Ain->n_blocks, b0 = Ain->block, nnzb0 = Ain->nnzb;
   if (n0 <= 0 || b0 <= 0 || nnzb0 <= 0 || !Ain->row_ptr || !Ain->col || !Ain->val)
@@ -1117,6 +1278,29 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
   ST(dalloc(ctx, &ctx->d_iters, 4));
   ST(dalloc(ctx, &ctx->d_err, 4));
   CU(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
+  // ---- matrix-free levels (Section 4.4): drop A_1 .. A_kappa ----
+  {
+    const int kappa = std::min(opt->matrix_free_levels, N - 1);
+    CU(cudaStreamSynchronize(s));
+    for (int k = 1; k <= kappa; ++k) {
+      Level &l = ctx->L[k], &lp = ctx->L[k - 1];
+      const int64_t nb = l.A.nnzb;
+      const int64_t freed = nb * l.s * l.s * (int64_t)(sizeof(double) + sizeof(float)) +
+                            nb * (int64_t)sizeof(int) + (int64_t)(l.n + 1) * sizeof(int);
+      for (void *p : {(void *)l.A.val, (void *)l.A.val32, (void *)l.A.rp, (void *)l.A.col})
+        dfree(ctx, p);
+      ctx->device_bytes -= freed;
+      l.A.val = nullptr;
+      l.A.val32 = nullptr;
+      l.A.rp = nullptr;
+      l.A.col = nullptr;
+      l.mf = true;
+      ST(dalloc(ctx, &lp.mt, (size_t)lp.ndof));
+      ST(dalloc(ctx, &lp.mu, (size_t)lp.ndof));
+      ST(dalloc(ctx, &lp.mtf, (size_t)lp.ndof));
+      ST(dalloc(ctx, &lp.muf, (size_t)lp.ndof));
+    }
+  }
   if (opt->bulk_staging) {
     Level &l = ctx->L[0];
     int maxrow = 0;
@@ -1178,6 +1362,7 @@ void gasa_default_options(gasa_options *opt) {
   opt->seed = 13373;
   opt->init_candidates = nullptr;
   opt->bulk_staging = 0;
+  opt->matrix_free_levels = 0;
 }
 
 gasa_status gasa_create(gasa_ctx **out, int32_t device, void *stream) {
@@ -1238,10 +1423,12 @@ gasa_status gasa_solve(gasa_ctx *ctx, const double *b, double *x, double tol, in
   int iters = 0;
   double rel = 0.0;
   bool conv = false;
-  gasa_status st = ctx->opt.solver == GASA_SOLVER_GMRES
-                       ? gmres(ctx, bd, tol, precision, &iters, &rel, &conv)
-                       : (ctx->prof ? pcg(ctx, bd, tol, precision, &iters, &rel, &conv)
-                                    : pcg_graph(ctx, bd, tol, precision, &iters, &rel, &conv));
+  gasa_status st =
+      ctx->opt.solver == GASA_SOLVER_GMRES ? gmres(ctx, bd, tol, precision, &iters, &rel, &conv)
+      : ctx->opt.solver == GASA_SOLVER_STATIONARY
+          ? stationary(ctx, bd, tol, precision, &iters, &rel, &conv)
+          : (ctx->prof ? pcg(ctx, bd, tol, precision, &iters, &rel, &conv)
+                       : pcg_graph(ctx, bd, tol, precision, &iters, &rel, &conv));
   if (st == GASA_OK || st == GASA_ERR_NOT_SPD) {
     if (on_device) {
       CU(cudaMemcpyAsync(x, ctx->kx, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1324,7 +1511,7 @@ gasa_status gasa_get_level(gasa_ctx *ctx, int32_t level, int32_t what, void *hos
       break;
     default: return fail(ctx, GASA_ERR_INVALID_ARG, "unknown level item");
   }
-  if (!src) return fail(ctx, GASA_ERR_INVALID_ARG, "item not available on this level (setup data is kept only with options.keep_setup_data)");
+  if (!src) return fail(ctx, GASA_ERR_INVALID_ARG, "item not available on this level (setup data is kept only with options.keep_setup_data; a matrix-free level keeps no A)");
   if (n_bytes < bytes) return fail(ctx, GASA_ERR_INVALID_ARG, "output buffer too small");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, GASA_ERR_CUDA, "cudaSetDevice");
   CU(cudaStreamSynchronize(ctx->stream));

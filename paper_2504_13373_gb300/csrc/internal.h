@@ -78,6 +78,9 @@ cudaError_t launch_normal(int64_t n, uint64_t seed, uint64_t stream, double *x, 
 template <typename Tin, typename Tout>
 cudaError_t launch_convert(int64_t n, const Tin *in, Tout *out, cudaStream_t s);
 cudaError_t launch_fill(int64_t n, double v, double *x, cudaStream_t s);
+// y[i] += x[i]
+template <typename T>
+cudaError_t launch_add(int64_t n, const T *x, T *y, cudaStream_t s);
 
 // CG pieces (device scalars; partial arrays of kRedBlocks entries)
 cudaError_t launch_cg_update_xr(int64_t n, double *x, double *r, const double *p,

@@ -15,6 +15,7 @@ namespace gasa {
 // ----------------------------------------------------------------------------
 __global__ void to_h16_blocks_kernel(int64_t nblocks, int bsz, const double *__restrict__ v,
                                      __half *__restrict__ h, float *__restrict__ scale) {
+  pdl_entry();
   const int64_t blk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (blk >= nblocks) return;
@@ -30,7 +31,7 @@ __global__ void to_h16_blocks_kernel(int64_t nblocks, int bsz, const double *__r
 cudaError_t launch_to_h16_blocks(int64_t nblocks, int bsz, const double *v, __half *h,
                                  float *scale, cudaStream_t s) {
   if (nblocks == 0) return cudaSuccess;
-  to_h16_blocks_kernel<<<div_up(nblocks * 32, 256), 256, 0, s>>>(nblocks, bsz, v, h, scale); note_launch();
+  launch_k(to_h16_blocks_kernel, div_up(nblocks * 32, 256), 256, 0, s, nblocks, bsz, v, h, scale); note_launch();
   return cudaGetLastError();
 }
 
@@ -58,6 +59,7 @@ __global__ void __launch_bounds__(256)
 bsr_mv_h16_kernel(int n_brows, int br, const int *__restrict__ rp, const int *__restrict__ col,
                   const __half *__restrict__ val, const float *__restrict__ scale,
                   const float *__restrict__ x, const float *__restrict__ b, float *__restrict__ y) {
+  pdl_entry();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)n_brows * br) return;
   const int i = (int)(t / br);
@@ -87,6 +89,7 @@ bsr_mv_h16_generic(int n_brows, int br, int bc, const int *__restrict__ rp,
                    const int *__restrict__ col, const __half *__restrict__ val,
                    const float *__restrict__ scale, const float *__restrict__ x,
                    const float *__restrict__ b, float *__restrict__ y) {
+  pdl_entry();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)n_brows * br) return;
   const int i = (int)(t / br);
@@ -114,7 +117,7 @@ static cudaError_t mv_h16_dispatch(int n_brows, int br, int bc, const int *rp, c
   const int grid = div_up(rows, 256);
 #define GASA_H16_MV(BC)                                                                          \
   case BC:                                                                                       \
-    bsr_mv_h16_kernel<BC, MODE><<<grid, 256, 0, s>>>(n_brows, br, rp, col, val, scale, x, b, y); \
+    launch_k(bsr_mv_h16_kernel<BC, MODE>, grid, 256, 0, s, n_brows, br, rp, col, val, scale, x, b, y); \
     note_launch();                                                                               \
     return cudaGetLastError();
   switch (bc) {
@@ -123,7 +126,7 @@ static cudaError_t mv_h16_dispatch(int n_brows, int br, int bc, const int *rp, c
     default: break;
   }
 #undef GASA_H16_MV
-  bsr_mv_h16_generic<MODE><<<grid, 256, 0, s>>>(n_brows, br, bc, rp, col, val, scale, x, b, y); note_launch();
+  launch_k(bsr_mv_h16_generic<MODE>, grid, 256, 0, s, n_brows, br, bc, rp, col, val, scale, x, b, y); note_launch();
   return cudaGetLastError();
 }
 
@@ -151,6 +154,7 @@ jacobi_h16_kernel(int n_units, const int *__restrict__ rp, const int *__restrict
                   const __half *__restrict__ Wm, const float *__restrict__ wscale,
                   const float *__restrict__ x, const float *__restrict__ b,
                   float *__restrict__ xo) {
+  pdl_entry();
   __shared__ float res[256];
   constexpr int RPB = 256 / BS;
   constexpr int W = RowVec<float, BS>::value;
@@ -200,6 +204,7 @@ jacobi_h16_generic(int n_units, int bs, const int *__restrict__ rp, const int *_
                    const __half *__restrict__ Wm, const float *__restrict__ wscale,
                    const float *__restrict__ x, const float *__restrict__ b,
                    float *__restrict__ xo) {
+  pdl_entry();
   extern __shared__ float resg[];
   const int rpb = blockDim.x / bs;
   const int li = threadIdx.x / bs;
@@ -244,7 +249,7 @@ static cudaError_t jac_h16_dispatch(int n_units, int bs, const int *rp, const in
 #define GASA_H16_JAC(BS)                                                                        \
   case BS: {                                                                                    \
     constexpr int rpb = 256 / BS;                                                               \
-    jacobi_h16_kernel<BS, MODE><<<div_up(n_units, rpb), 256, 0, s>>>(n_units, rp, col, val,     \
+    launch_k(jacobi_h16_kernel<BS, MODE>, div_up(n_units, rpb), 256, 0, s, n_units, rp, col, val,     \
                                                                     ascale, W, wscale, x, b,    \
                                                                     xo);                        \
     note_launch();                                                                              \
@@ -260,7 +265,7 @@ static cudaError_t jac_h16_dispatch(int n_units, int bs, const int *rp, const in
   if (rpb < 1) rpb = 1;
   const int th = rpb * bs;
   if (th > 1024) return cudaErrorInvalidValue;
-  jacobi_h16_generic<MODE><<<div_up(n_units, rpb), th, th * sizeof(float), s>>>(
+  launch_k(jacobi_h16_generic<MODE>, div_up(n_units, rpb), th, th * sizeof(float), s, 
       n_units, bs, rp, col, val, ascale, W, wscale, x, b, xo); note_launch();
   return cudaGetLastError();
 }

@@ -22,6 +22,7 @@ __global__ void __launch_bounds__(256)
 bsr_mv_kernel(int n_brows, int br, const int *__restrict__ rp, const int *__restrict__ col,
               const T *__restrict__ val, const T *__restrict__ x, const T *__restrict__ b,
               T *__restrict__ y) {
+  pdl_entry();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)n_brows * br) return;
   const int i = (int)(t / br);
@@ -51,6 +52,7 @@ __global__ void __launch_bounds__(256)
 bsr_mv_generic(int n_brows, int br, int bc, const int *__restrict__ rp,
                const int *__restrict__ col, const T *__restrict__ val, const T *__restrict__ x,
                const T *__restrict__ b, T *__restrict__ y) {
+  pdl_entry();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)n_brows * br) return;
   const int i = (int)(t / br);
@@ -111,6 +113,7 @@ __global__ void __launch_bounds__(256)
 bsr_mv_warp_kernel(int n_brows, int br, int bc, const int *__restrict__ rp,
                    const int *__restrict__ col, const T *__restrict__ val, const T *__restrict__ x,
                    const T *__restrict__ b, T *__restrict__ y) {
+  pdl_entry();
   const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= n_brows) return;
@@ -154,6 +157,7 @@ __global__ void __launch_bounds__(256)
 bsr_mv_group_kernel(int n_brows, int br, int bc, const int *__restrict__ rp,
                     const int *__restrict__ col, const T *__restrict__ val,
                     const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ y) {
+  pdl_entry();
   const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= n_brows) return;
@@ -206,6 +210,7 @@ __global__ void __launch_bounds__(256)
 bsr_mv_cta_kernel(int n_brows, int br, int bc, const int *__restrict__ rp,
                   const int *__restrict__ col, const T *__restrict__ val,
                   const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ y) {
+  pdl_entry();
   extern __shared__ unsigned char cta_smem[];
   T *red = reinterpret_cast<T *>(cta_smem);
   const int i = blockIdx.x;
@@ -237,16 +242,16 @@ static cudaError_t mv_warp_dispatch(int n_brows, int br, int bc, const int *rp, 
                                     const T *val, const T *x, const T *b, T *y, cudaStream_t s) {
   const int grid = div_up((long long)n_brows * 32, 256);
   if (cta_rows(n_brows, br)) {
-    bsr_mv_cta_kernel<T, MODE><<<n_brows, 256, (256 + br) * sizeof(T), s>>>(n_brows, br, bc, rp, col, val, x, b, y);
+    launch_k(bsr_mv_cta_kernel<T, MODE>, n_brows, 256, (256 + br) * sizeof(T), s, n_brows, br, bc, rp, col, val, x, b, y);
     note_launch();
     return cudaGetLastError();
   }
-  if (pow2_le32(br)) bsr_mv_group_kernel<T, MODE><<<grid, 256, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y);
-  else if (br <= 4) bsr_mv_warp_kernel<T, 4, MODE><<<grid, 256, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y);
-  else if (br <= 8) bsr_mv_warp_kernel<T, 8, MODE><<<grid, 256, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y);
-  else if (br <= 16) bsr_mv_warp_kernel<T, 16, MODE><<<grid, 256, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y);
-  else if (br <= 32) bsr_mv_warp_kernel<T, 32, MODE><<<grid, 256, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y);
-  else bsr_mv_warp_kernel<T, 64, MODE><<<grid, 256, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y);
+  if (pow2_le32(br)) launch_k(bsr_mv_group_kernel<T, MODE>, grid, 256, 0, s, n_brows, br, bc, rp, col, val, x, b, y);
+  else if (br <= 4) launch_k(bsr_mv_warp_kernel<T, 4, MODE>, grid, 256, 0, s, n_brows, br, bc, rp, col, val, x, b, y);
+  else if (br <= 8) launch_k(bsr_mv_warp_kernel<T, 8, MODE>, grid, 256, 0, s, n_brows, br, bc, rp, col, val, x, b, y);
+  else if (br <= 16) launch_k(bsr_mv_warp_kernel<T, 16, MODE>, grid, 256, 0, s, n_brows, br, bc, rp, col, val, x, b, y);
+  else if (br <= 32) launch_k(bsr_mv_warp_kernel<T, 32, MODE>, grid, 256, 0, s, n_brows, br, bc, rp, col, val, x, b, y);
+  else launch_k(bsr_mv_warp_kernel<T, 64, MODE>, grid, 256, 0, s, n_brows, br, bc, rp, col, val, x, b, y);
   note_launch();
   return cudaGetLastError();
 }
@@ -261,7 +266,7 @@ static cudaError_t mv_dispatch(int n_brows, int br, int bc, const int *rp, const
   const bool al = aligned16(val) && aligned16(x);
 #define GASA_MV_CASE(BC)                                                                   \
   case BC:                                                                                 \
-    bsr_mv_kernel<T, BC, MODE><<<grid, th, 0, s>>>(n_brows, br, rp, col, val, x, b, y); note_launch();    \
+    launch_k(bsr_mv_kernel<T, BC, MODE>, grid, th, 0, s, n_brows, br, rp, col, val, x, b, y); note_launch();    \
     return cudaGetLastError();
   if (al) {
     switch (bc) {
@@ -273,7 +278,7 @@ static cudaError_t mv_dispatch(int n_brows, int br, int bc, const int *rp, const
     }
   }
 #undef GASA_MV_CASE
-  bsr_mv_generic<T, MODE><<<grid, th, 0, s>>>(n_brows, br, bc, rp, col, val, x, b, y); note_launch();
+  launch_k(bsr_mv_generic<T, MODE>, grid, th, 0, s, n_brows, br, bc, rp, col, val, x, b, y); note_launch();
   return cudaGetLastError();
 }
 
@@ -320,6 +325,7 @@ __global__ void __launch_bounds__(256)
 jacobi_kernel(int n_units, const int *__restrict__ rp, const int *__restrict__ col,
               const T *__restrict__ val, const T *__restrict__ Wm, const T *__restrict__ x,
               const T *__restrict__ b, T *__restrict__ xo) {
+  pdl_entry();
   __shared__ T res[256];
   constexpr int RPB = 256 / BS;
   constexpr int W = RowVec<T, BS>::value;
@@ -371,6 +377,7 @@ __global__ void __launch_bounds__(256)
 jacobi_generic(int n_units, int bs, const int *__restrict__ rp, const int *__restrict__ col,
                const T *__restrict__ val, const T *__restrict__ Wm, const T *__restrict__ x,
                const T *__restrict__ b, T *__restrict__ xo) {
+  pdl_entry();
   extern __shared__ unsigned char smem_raw[];
   T *res = reinterpret_cast<T *>(smem_raw);
   const int rpb = blockDim.x / bs;
@@ -414,6 +421,7 @@ __global__ void __launch_bounds__(256)
 jacobi_warp_kernel(int n_units, int bs, const int *__restrict__ rp, const int *__restrict__ col,
                    const T *__restrict__ val, const T *__restrict__ Wm, const T *__restrict__ x,
                    const T *__restrict__ b, T *__restrict__ xo) {
+  pdl_entry();
   const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= n_units) return;
@@ -445,6 +453,7 @@ __global__ void __launch_bounds__(256)
 jacobi_cta_kernel(int n_units, int bs, const int *__restrict__ rp, const int *__restrict__ col,
                   const T *__restrict__ val, const T *__restrict__ Wm, const T *__restrict__ x,
                   const T *__restrict__ b, T *__restrict__ xo) {
+  pdl_entry();
   extern __shared__ unsigned char cta_smem_j[];
   T *red = reinterpret_cast<T *>(cta_smem_j);
   const int i = blockIdx.x;
@@ -473,6 +482,7 @@ __global__ void __launch_bounds__(256)
 jacobi_group_kernel(int n_units, int bs, const int *__restrict__ rp, const int *__restrict__ col,
                     const T *__restrict__ val, const T *__restrict__ Wm, const T *__restrict__ x,
                     const T *__restrict__ b, T *__restrict__ xo) {
+  pdl_entry();
   const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= n_units) return;
@@ -499,16 +509,16 @@ static cudaError_t jac_warp_dispatch(int n_units, int bs, const int *rp, const i
                                      cudaStream_t s) {
   const int grid = div_up((long long)n_units * 32, 256);
   if (cta_rows(n_units, bs)) {
-    jacobi_cta_kernel<T, MODE><<<n_units, 256, (256 + bs) * sizeof(T), s>>>(n_units, bs, rp, col, val, W, x, b, xo);
+    launch_k(jacobi_cta_kernel<T, MODE>, n_units, 256, (256 + bs) * sizeof(T), s, n_units, bs, rp, col, val, W, x, b, xo);
     note_launch();
     return cudaGetLastError();
   }
-  if (pow2_le32(bs)) jacobi_group_kernel<T, MODE><<<grid, 256, 0, s>>>(n_units, bs, rp, col, val, W, x, b, xo);
-  else if (bs <= 4) jacobi_warp_kernel<T, 4, MODE><<<grid, 256, 0, s>>>(n_units, bs, rp, col, val, W, x, b, xo);
-  else if (bs <= 8) jacobi_warp_kernel<T, 8, MODE><<<grid, 256, 0, s>>>(n_units, bs, rp, col, val, W, x, b, xo);
-  else if (bs <= 16) jacobi_warp_kernel<T, 16, MODE><<<grid, 256, 0, s>>>(n_units, bs, rp, col, val, W, x, b, xo);
-  else if (bs <= 32) jacobi_warp_kernel<T, 32, MODE><<<grid, 256, 0, s>>>(n_units, bs, rp, col, val, W, x, b, xo);
-  else jacobi_warp_kernel<T, 64, MODE><<<grid, 256, 0, s>>>(n_units, bs, rp, col, val, W, x, b, xo);
+  if (pow2_le32(bs)) launch_k(jacobi_group_kernel<T, MODE>, grid, 256, 0, s, n_units, bs, rp, col, val, W, x, b, xo);
+  else if (bs <= 4) launch_k(jacobi_warp_kernel<T, 4, MODE>, grid, 256, 0, s, n_units, bs, rp, col, val, W, x, b, xo);
+  else if (bs <= 8) launch_k(jacobi_warp_kernel<T, 8, MODE>, grid, 256, 0, s, n_units, bs, rp, col, val, W, x, b, xo);
+  else if (bs <= 16) launch_k(jacobi_warp_kernel<T, 16, MODE>, grid, 256, 0, s, n_units, bs, rp, col, val, W, x, b, xo);
+  else if (bs <= 32) launch_k(jacobi_warp_kernel<T, 32, MODE>, grid, 256, 0, s, n_units, bs, rp, col, val, W, x, b, xo);
+  else launch_k(jacobi_warp_kernel<T, 64, MODE>, grid, 256, 0, s, n_units, bs, rp, col, val, W, x, b, xo);
   note_launch();
   return cudaGetLastError();
 }
@@ -522,7 +532,7 @@ static cudaError_t jac_dispatch(int n_units, int bs, const int *rp, const int *c
 #define GASA_JAC_CASE(BS)                                                                   \
   case BS: {                                                                                \
     constexpr int rpb = 256 / BS;                                                           \
-    jacobi_kernel<T, BS, MODE><<<div_up(n_units, rpb), 256, 0, s>>>(n_units, rp, col, val,  \
+    launch_k(jacobi_kernel<T, BS, MODE>, div_up(n_units, rpb), 256, 0, s, n_units, rp, col, val,  \
                                                                     W, x, b, xo); note_launch();           \
     return cudaGetLastError();                                                              \
   }
@@ -541,7 +551,7 @@ static cudaError_t jac_dispatch(int n_units, int bs, const int *rp, const int *c
   if (rpb < 1) rpb = 1;
   const int th = rpb * bs;
   if (th > 1024) return cudaErrorInvalidValue;
-  jacobi_generic<T, MODE><<<div_up(n_units, rpb), th, th * sizeof(T), s>>>(n_units, bs, rp, col,
+  launch_k(jacobi_generic<T, MODE>, div_up(n_units, rpb), th, th * sizeof(T), s, n_units, bs, rp, col,
                                                                            val, W, x, b, xo); note_launch();
   return cudaGetLastError();
 }
@@ -579,6 +589,7 @@ __global__ void __launch_bounds__(256)
 relax_multi_kernel(int n_units, int bs, const int *__restrict__ rp, const int *__restrict__ col,
                    const double *__restrict__ val, const double *__restrict__ Wm,
                    const double *const *__restrict__ xin, double *const *__restrict__ xout) {
+  pdl_entry();
   extern __shared__ double res_m[];
   const double *x = xin[blockIdx.y];
   double *xo = xout[blockIdx.y];
@@ -618,7 +629,7 @@ cudaError_t launch_relax_multi(int n_units, int bs, const int *rp, const int *co
   const int th = rpb * bs;
   if (th > 1024) return cudaErrorInvalidValue;
   dim3 grid(div_up(n_units, rpb), nc);
-  relax_multi_kernel<<<grid, th, th * sizeof(double), s>>>(n_units, bs, rp, col, val, W, xin,
+  launch_k(relax_multi_kernel, grid, th, th * sizeof(double), s, n_units, bs, rp, col, val, W, xin,
                                                            xout); note_launch();
   return cudaGetLastError();
 }
@@ -641,6 +652,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 dense_mv_kernel(int n, const double *__restrict__ A, const T *__restrict__ x,
                 T *__restrict__ y) {
+  pdl_entry();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n) return;
@@ -654,7 +666,7 @@ dense_mv_kernel(int n, const double *__restrict__ A, const T *__restrict__ x,
 template <typename T>
 cudaError_t launch_dense_mv(int n, const double *A, const T *x, T *y, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  dense_mv_kernel<T><<<div_up((long long)n * 32, 256), 256, 0, s>>>(n, A, x, y); note_launch();
+  launch_k(dense_mv_kernel<T>, div_up((long long)n * 32, 256), 256, 0, s, n, A, x, y); note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_dense_mv<double>(int, const double *, const double *, double *,

@@ -2,7 +2,9 @@
 // reductions (fixed grid, fixed order: partial sums per CTA, then one CTA
 // sums the partials), fused CG updates, GMRES Arnoldi pieces, counter-based
 // random vectors and precision conversions.
+#include <algorithm>
 #include <atomic>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "internal.h"
@@ -13,12 +15,28 @@ static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
+// programmatic dependent launch: off unless GASA_PDL=1 in the environment
+// (measured on the P3 256x256 solve: no gain for the FP32 V-cycle, 7 % slower
+// for the FP64 one); switched off after a graph that uses it fails to build
+static std::atomic<int> g_pdl{-1};
+bool pdl_enabled() {
+  int v = g_pdl.load(std::memory_order_relaxed);
+  if (v < 0) {
+    const char *e = std::getenv("GASA_PDL");
+    v = (e && e[0] == '1') ? 1 : 0;
+    g_pdl.store(v, std::memory_order_relaxed);
+  }
+  return v != 0;
+}
+void pdl_set(bool on) { g_pdl.store(on ? 1 : 0, std::memory_order_relaxed); }
+
 // ----------------------------------------------------------------------------
 // reductions
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(kRedThreads)
 dot_partials_kernel(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                     double *__restrict__ partials) {
+  pdl_entry();
   __shared__ double sh[32];
   // four independent accumulators keep four loads in flight per thread
   double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
@@ -39,13 +57,14 @@ dot_partials_kernel(int64_t n, const double *__restrict__ x, const double *__res
 
 cudaError_t launch_dot_partials(int64_t n, const double *x, const double *y, double *partials,
                                 cudaStream_t s) {
-  dot_partials_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, y, partials); note_launch();
+  launch_k(dot_partials_kernel, kRedBlocks, kRedThreads, 0, s, n, x, y, partials); note_launch();
   return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(kRedThreads)
 colnorm_partials_kernel(int64_t n, const double *const *__restrict__ cols,
                         double *__restrict__ partials) {
+  pdl_entry();
   __shared__ double sh[32];
   const double *x = cols[blockIdx.y];
   double v = 0.0;
@@ -59,12 +78,13 @@ colnorm_partials_kernel(int64_t n, const double *const *__restrict__ cols,
 cudaError_t launch_colnorm_partials(int64_t n, const double *const *cols, int nc,
                                     double *partials, cudaStream_t s) {
   if (nc == 0) return cudaSuccess;
-  colnorm_partials_kernel<<<dim3(kRedBlocks, nc), kRedThreads, 0, s>>>(n, cols, partials); note_launch();
+  launch_k(colnorm_partials_kernel, dim3(kRedBlocks, nc), kRedThreads, 0, s, n, cols, partials); note_launch();
   return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(kRedThreads)
 finalize_kernel(const double *__restrict__ partials, double *__restrict__ out) {
+  pdl_entry();
   __shared__ double sh[32];
   double v = block_sum_partials(partials + (size_t)blockIdx.x * kRedBlocks, kRedBlocks, sh);
   if (threadIdx.x == 0) out[blockIdx.x] = v;
@@ -72,18 +92,19 @@ finalize_kernel(const double *__restrict__ partials, double *__restrict__ out) {
 
 cudaError_t launch_finalize(const double *partials, int nc, double *out, cudaStream_t s) {
   if (nc == 0) return cudaSuccess;
-  finalize_kernel<<<nc, kRedThreads, 0, s>>>(partials, out); note_launch();
+  launch_k(finalize_kernel, nc, kRedThreads, 0, s, partials, out); note_launch();
   return cudaGetLastError();
 }
 
 __global__ void scale_inv_sqrt_kernel(int64_t n, double *x, const double *sumsq) {
+  pdl_entry();
   const double a = 1.0 / sqrt(sumsq[0]);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) x[i] *= a;
 }
 
 cudaError_t launch_scale_by_inv_sqrt(int64_t n, double *x, const double *sumsq, cudaStream_t s) {
-  scale_inv_sqrt_kernel<<<kRedBlocks, 256, 0, s>>>(n, x, sumsq); note_launch();
+  launch_k(scale_inv_sqrt_kernel, kRedBlocks, 256, 0, s, n, x, sumsq); note_launch();
   return cudaGetLastError();
 }
 
@@ -103,6 +124,7 @@ __device__ __forceinline__ double splitmix_uniform(uint64_t key, uint64_t i) {
 }
 
 __global__ void uniform_pm1_kernel(int64_t n, uint64_t key, double *x) {
+  pdl_entry();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
     x[i] = 2.0 * splitmix_uniform(key, (uint64_t)i) - 1.0;
@@ -111,12 +133,13 @@ __global__ void uniform_pm1_kernel(int64_t n, uint64_t key, double *x) {
 cudaError_t launch_uniform_pm1(int64_t n, uint64_t seed, uint64_t stream, double *x,
                                cudaStream_t s) {
   const uint64_t key = seed ^ (stream * 0x9E3779B97F4A7C15ull);
-  uniform_pm1_kernel<<<kRedBlocks, 256, 0, s>>>(n, key, x); note_launch();
+  launch_k(uniform_pm1_kernel, kRedBlocks, 256, 0, s, n, key, x); note_launch();
   return cudaGetLastError();
 }
 
 // Box-Muller over pairs of uniforms: u1 = 1 - U[2m], u2 = U[2m+1]
 __global__ void normal_kernel(int64_t n, uint64_t key, double *x) {
+  pdl_entry();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const int64_t m = i >> 1;
@@ -131,7 +154,7 @@ __global__ void normal_kernel(int64_t n, uint64_t key, double *x) {
 
 cudaError_t launch_normal(int64_t n, uint64_t seed, uint64_t stream, double *x, cudaStream_t s) {
   const uint64_t key = seed ^ (stream * 0x9E3779B97F4A7C15ull);
-  normal_kernel<<<kRedBlocks, 256, 0, s>>>(n, key, x); note_launch();
+  launch_k(normal_kernel, kRedBlocks, 256, 0, s, n, key, x); note_launch();
   return cudaGetLastError();
 }
 
@@ -140,6 +163,7 @@ cudaError_t launch_normal(int64_t n, uint64_t seed, uint64_t stream, double *x, 
 // ----------------------------------------------------------------------------
 template <typename Tin, typename Tout>
 __global__ void convert_kernel(int64_t n, const Tin *__restrict__ in, Tout *__restrict__ out) {
+  pdl_entry();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
     out[i] = (Tout)in[i];
@@ -150,31 +174,50 @@ cudaError_t launch_convert(int64_t n, const Tin *in, Tout *out, cudaStream_t s) 
   if (n == 0) return cudaSuccess;
   int grid = div_up(n, 256);
   if (grid > 8 * kNumSM) grid = 8 * kNumSM;
-  convert_kernel<Tin, Tout><<<grid, 256, 0, s>>>(n, in, out); note_launch();
+  launch_k(convert_kernel<Tin, Tout>, grid, 256, 0, s, n, in, out); note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_convert<double, float>(int64_t, const double *, float *, cudaStream_t);
 template cudaError_t launch_convert<float, double>(int64_t, const float *, double *, cudaStream_t);
 
 __global__ void fill_kernel(int64_t n, double v, double *x) {
+  pdl_entry();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) x[i] = v;
 }
 cudaError_t launch_fill(int64_t n, double v, double *x, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  fill_kernel<<<kRedBlocks, 256, 0, s>>>(n, v, x); note_launch();
+  launch_k(fill_kernel, kRedBlocks, 256, 0, s, n, v, x); note_launch();
   return cudaGetLastError();
 }
 
+template <typename T>
+__global__ void add_kernel(int64_t n, const T *__restrict__ x, T *__restrict__ y) {
+  pdl_entry();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    y[i] = y[i] + x[i];
+}
+template <typename T>
+cudaError_t launch_add(int64_t n, const T *x, T *y, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  launch_k(add_kernel<T>, std::min<int64_t>(div_up(n, 256), kRedBlocks * 4), 256, 0, s, n, x, y);
+  note_launch();
+  return cudaGetLastError();
+}
+template cudaError_t launch_add<double>(int64_t, const double *, double *, cudaStream_t);
+template cudaError_t launch_add<float>(int64_t, const float *, float *, cudaStream_t);
+
 __global__ void axpy_kernel(int64_t n, double a, const double *__restrict__ x,
                             double *__restrict__ y) {
+  pdl_entry();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
     y[i] = fma(a, x[i], y[i]);
 }
 cudaError_t launch_axpy(int64_t n, double a, const double *x, double *y, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  axpy_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, a, x, y); note_launch();
+  launch_k(axpy_kernel, kRedBlocks * 2, 256, 0, s, n, a, x, y); note_launch();
   return cudaGetLastError();
 }
 
@@ -184,13 +227,14 @@ cudaError_t launch_copy(int64_t n, const double *x, double *y, cudaStream_t s) {
 
 __global__ void sub_kernel(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
                            double *__restrict__ o) {
+  pdl_entry();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
     o[i] = a[i] - b[i];
 }
 cudaError_t launch_sub(int64_t n, const double *a, const double *b, double *out, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  sub_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, a, b, out); note_launch();
+  launch_k(sub_kernel, kRedBlocks * 2, 256, 0, s, n, a, b, out); note_launch();
   return cudaGetLastError();
 }
 
@@ -202,6 +246,7 @@ cg_update_xr_kernel(int64_t n, double *__restrict__ x, double *__restrict__ r,
                     const double *__restrict__ p, const double *__restrict__ q,
                     const double *__restrict__ rz, const double *__restrict__ pq_partials,
                     double *__restrict__ rr_partials, double *__restrict__ alpha_out) {
+  pdl_entry();
   __shared__ double sh[32];
   const double pq = block_sum_partials(pq_partials, kRedBlocks, sh);
   const double alpha = rz[0] / pq;
@@ -238,7 +283,7 @@ cg_update_xr_kernel(int64_t n, double *__restrict__ x, double *__restrict__ r,
 cudaError_t launch_cg_update_xr(int64_t n, double *x, double *r, const double *p,
                                 const double *q, const double *rz, const double *pq_partials,
                                 double *rr_partials, double *alpha_out, cudaStream_t s) {
-  cg_update_xr_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, x, r, p, q, rz, pq_partials,
+  launch_k(cg_update_xr_kernel, kRedBlocks, kRedThreads, 0, s, n, x, r, p, q, rz, pq_partials,
                                                          rr_partials, alpha_out); note_launch();
   return cudaGetLastError();
 }
@@ -250,6 +295,7 @@ cg_update_p_kernel(int64_t n, double *__restrict__ p, const double *__restrict__
                    const double *__restrict__ rz_old, const double *__restrict__ rz_partials,
                    const double *__restrict__ rzold_partials, double *__restrict__ rz_out,
                    int flexible, double *__restrict__ zold_out) {
+  pdl_entry();
   __shared__ double sh[32];
   const double rz_new = block_sum_partials(rz_partials, kRedBlocks, sh);
   double num = rz_new;
@@ -272,7 +318,7 @@ cg_update_p_kernel(int64_t n, double *__restrict__ p, const double *__restrict__
 cudaError_t launch_cg_update_p(int64_t n, double *p, const double *z, const double *rz_old,
                                const double *rz_partials, const double *rzold_partials,
                                double *rz_out, int flexible, cudaStream_t s, double *zold_out) {
-  cg_update_p_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, p, z, rz_old, rz_partials,
+  launch_k(cg_update_p_kernel, kRedBlocks, kRedThreads, 0, s, n, p, z, rz_old, rz_partials,
                                                         rzold_partials, rz_out, flexible, zold_out); note_launch();
   return cudaGetLastError();
 }
@@ -284,6 +330,7 @@ cudaError_t launch_cg_update_p(int64_t n, double *p, const double *z, const doub
 __global__ void __launch_bounds__(kRedThreads)
 cg_check_kernel(const double *__restrict__ rr_partials, double *__restrict__ scal, int *iters,
                 int max_iter, cudaGraphConditionalHandle handle) {
+  pdl_entry();
   __shared__ double sh[32];
   const double rr = block_sum_partials(rr_partials, kRedBlocks, sh);
   if (threadIdx.x == 0) {
@@ -299,7 +346,7 @@ cg_check_kernel(const double *__restrict__ rr_partials, double *__restrict__ sca
 
 cudaError_t launch_cg_check(const double *rr_partials, double *scal, int *iters, int max_iter,
                             cudaGraphConditionalHandle handle, cudaStream_t s) {
-  cg_check_kernel<<<1, kRedThreads, 0, s>>>(rr_partials, scal, iters, max_iter, handle); note_launch();
+  launch_k(cg_check_kernel, 1, kRedThreads, 0, s, rr_partials, scal, iters, max_iter, handle); note_launch();
   return cudaGetLastError();
 }
 
@@ -311,6 +358,7 @@ void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_rela
 __global__ void __launch_bounds__(kRedThreads)
 multi_dot_kernel(int64_t n, const double *__restrict__ V, int64_t ldv,
                  const double *__restrict__ w, double *__restrict__ partials) {
+  pdl_entry();
   __shared__ double sh[32];
   const double *v = V + (size_t)blockIdx.y * ldv;
   double acc = 0.0;
@@ -324,13 +372,14 @@ multi_dot_kernel(int64_t n, const double *__restrict__ V, int64_t ldv,
 cudaError_t launch_multi_dot(int64_t n, const double *V, int64_t ldv, int k, const double *w,
                              double *partials, cudaStream_t s) {
   if (k == 0) return cudaSuccess;
-  multi_dot_kernel<<<dim3(kRedBlocks, k), kRedThreads, 0, s>>>(n, V, ldv, w, partials); note_launch();
+  launch_k(multi_dot_kernel, dim3(kRedBlocks, k), kRedThreads, 0, s, n, V, ldv, w, partials); note_launch();
   return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(kRedThreads)
 multi_dot_finalize_kernel(const double *__restrict__ partials, double *__restrict__ h,
                           double *__restrict__ hacc) {
+  pdl_entry();
   __shared__ double sh[32];
   const double v = block_sum_partials(partials + (size_t)blockIdx.x * kRedBlocks, kRedBlocks, sh);
   if (threadIdx.x == 0) {
@@ -342,12 +391,13 @@ multi_dot_finalize_kernel(const double *__restrict__ partials, double *__restric
 cudaError_t launch_multi_dot_finalize(const double *partials, int k, double *h, double *hacc,
                                       cudaStream_t s) {
   if (k == 0) return cudaSuccess;
-  multi_dot_finalize_kernel<<<k, kRedThreads, 0, s>>>(partials, h, hacc); note_launch();
+  launch_k(multi_dot_finalize_kernel, k, kRedThreads, 0, s, partials, h, hacc); note_launch();
   return cudaGetLastError();
 }
 
 __global__ void gs_update_kernel(int64_t n, const double *__restrict__ V, int64_t ldv, int k,
                                  const double *__restrict__ h, double *__restrict__ w) {
+  pdl_entry();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     double acc = w[i];
@@ -359,13 +409,14 @@ __global__ void gs_update_kernel(int64_t n, const double *__restrict__ V, int64_
 cudaError_t launch_gs_update(int64_t n, const double *V, int64_t ldv, int k, const double *h,
                              double *w, cudaStream_t s) {
   if (k == 0 || n == 0) return cudaSuccess;
-  gs_update_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, V, ldv, k, h, w); note_launch();
+  launch_k(gs_update_kernel, kRedBlocks * 2, 256, 0, s, n, V, ldv, k, h, w); note_launch();
   return cudaGetLastError();
 }
 
 __global__ void normalize_into_kernel(int64_t n, const double *__restrict__ w,
                                       const double *__restrict__ sumsq, double *__restrict__ v,
                                       double *__restrict__ hout) {
+  pdl_entry();
   const double nr = sqrt(sumsq[0]);
   if (blockIdx.x == 0 && threadIdx.x == 0) hout[0] = nr;
   const double a = nr > 0.0 ? 1.0 / nr : 0.0;
@@ -376,7 +427,7 @@ __global__ void normalize_into_kernel(int64_t n, const double *__restrict__ w,
 
 cudaError_t launch_normalize_into(int64_t n, const double *w, const double *sumsq, double *v,
                                   double *hout, cudaStream_t s) {
-  normalize_into_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, w, sumsq, v, hout); note_launch();
+  launch_k(normalize_into_kernel, kRedBlocks * 2, 256, 0, s, n, w, sumsq, v, hout); note_launch();
   return cudaGetLastError();
 }
 
@@ -384,6 +435,7 @@ cudaError_t launch_normalize_into(int64_t n, const double *w, const double *sums
 // in rows 0..j+1.  Applies rotations 0..j-1, forms rotation j, updates g.
 __global__ void gmres_givens_kernel(double *H, int ldh, int j, double *cs, double *sn,
                                     double *g) {
+  pdl_entry();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double *h = H + (size_t)j * ldh;
   for (int i = 0; i < j; ++i) {
@@ -408,12 +460,13 @@ __global__ void gmres_givens_kernel(double *H, int ldh, int j, double *cs, doubl
 
 cudaError_t launch_gmres_givens(double *H, int ldh, int j, double *cs, double *sn, double *g,
                                 cudaStream_t s) {
-  gmres_givens_kernel<<<1, 32, 0, s>>>(H, ldh, j, cs, sn, g); note_launch();
+  launch_k(gmres_givens_kernel, 1, 32, 0, s, H, ldh, j, cs, sn, g); note_launch();
   return cudaGetLastError();
 }
 
 __global__ void gmres_backsolve_kernel(const double *H, int ldh, int j, const double *g,
                                        double *y) {
+  pdl_entry();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int i = j - 1; i >= 0; --i) {
     double acc = g[i];
@@ -424,12 +477,13 @@ __global__ void gmres_backsolve_kernel(const double *H, int ldh, int j, const do
 
 cudaError_t launch_gmres_backsolve(const double *H, int ldh, int j, const double *g, double *y,
                                    cudaStream_t s) {
-  gmres_backsolve_kernel<<<1, 32, 0, s>>>(H, ldh, j, g, y); note_launch();
+  launch_k(gmres_backsolve_kernel, 1, 32, 0, s, H, ldh, j, g, y); note_launch();
   return cudaGetLastError();
 }
 
 __global__ void combine_kernel(int64_t n, const double *__restrict__ V, int64_t ldv, int k,
                                const double *__restrict__ y, double *__restrict__ x) {
+  pdl_entry();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     double acc = x[i];
@@ -441,7 +495,7 @@ __global__ void combine_kernel(int64_t n, const double *__restrict__ V, int64_t 
 cudaError_t launch_combine(int64_t n, const double *V, int64_t ldv, int k, const double *y,
                            double *x, cudaStream_t s) {
   if (k == 0 || n == 0) return cudaSuccess;
-  combine_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, V, ldv, k, y, x); note_launch();
+  launch_k(combine_kernel, kRedBlocks * 2, 256, 0, s, n, V, ldv, k, y, x); note_launch();
   return cudaGetLastError();
 }
 

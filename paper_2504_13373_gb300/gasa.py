@@ -22,10 +22,13 @@ GASA_ERR_SINGULAR_BLOCK = 4
 GASA_ERR_NOT_SPD = 5
 GASA_ERR_NOT_CONVERGED = 6
 GASA_ERR_BREAKDOWN = 7
+GASA_ERR_TIMEOUT = 8
+GASA_ERR_BUDGET = 9
+GASA_PENDING = 10
 GASA_ERR_UNSUPPORTED = 11
 GASA_ERR_STATE = 12
 
-GASA_SOLVER_CG, GASA_SOLVER_GMRES = 0, 1
+GASA_SOLVER_CG, GASA_SOLVER_GMRES, GASA_SOLVER_STATIONARY = 0, 1, 2
 GASA_PREC_FP64, GASA_PREC_MIXED32, GASA_PREC_MIXED16 = 0, 1, 2
 GASA_CAND_R, GASA_CAND_TT = 0, 1
 GASA_MV_ASSIGN, GASA_MV_RESIDUAL, GASA_MV_ADD = 0, 1, 2
@@ -43,6 +46,8 @@ EXPORTS = [
     "gasa_jacobi_sweep", "gasa_jacobi_sweep_f32", "gasa_block_inverse", "gasa_power_estimate",
     "gasa_relax_candidates", "gasa_tentative", "gasa_dense_inverse", "gasa_kernel_launches",
     "gasa_power_estimate_noalloc",
+    "gasa_server_create", "gasa_server_add_mesh", "gasa_server_submit", "gasa_server_poll",
+    "gasa_server_drain", "gasa_server_stats_read", "gasa_server_destroy", "gasa_server_last_error",
 ]
 GASA_NOALLOC_MAX_DOFS = 262144
 
@@ -64,7 +69,7 @@ class gasa_options(ctypes.Structure):
                 ("max_relax", c_i32), ("max_iter", c_i32), ("cand_init", c_i32),
                 ("keep_setup_data", c_i32), ("gamma", c_dbl), ("omega_factor", c_dbl),
                 ("n_cut", c_dbl), ("seed", ctypes.c_uint64), ("init_candidates", c_vp),
-                ("bulk_staging", c_i32)]
+                ("bulk_staging", c_i32), ("matrix_free_levels", c_i32)]
 
 
 class gasa_setup_info(ctypes.Structure):
@@ -79,6 +84,13 @@ class gasa_setup_info(ctypes.Structure):
 class gasa_solve_info(ctypes.Structure):
     _fields_ = [("iterations", c_i32), ("converged", c_i32), ("rel_residual", c_dbl),
                 ("seconds", c_dbl)]
+
+
+class gasa_server_stats(ctypes.Structure):
+    _fields_ = [(k, c_i64) for k in (
+        "submitted", "completed", "queued", "running", "engines", "engines_created",
+        "engines_released", "budget_bytes", "used_bytes", "peak_bytes", "peak_running",
+        "graph_launches")]
 
 
 class GasaError(RuntimeError):
@@ -100,12 +112,13 @@ def load():
     L = ctypes.CDLL(LIB_PATH)
     L.gasa_status_string.restype = ctypes.c_char_p
     L.gasa_last_error.restype = ctypes.c_char_p
+    L.gasa_server_last_error.restype = ctypes.c_char_p
     L.gasa_default_options.restype = None
     L.gasa_kernel_launches.restype = ctypes.c_int64
     for name in EXPORTS:
         f = getattr(L, name)
         if name not in ("gasa_status_string", "gasa_last_error", "gasa_default_options",
-                        "gasa_kernel_launches"):
+                        "gasa_kernel_launches", "gasa_server_last_error"):
             f.restype = ctypes.c_int
     _lib = L
     return L
@@ -246,6 +259,66 @@ def gasa_destroy(ctx):
 
 def gasa_kernel_launches():
     return int(load().gasa_kernel_launches())
+
+
+# request server -----------------------------------------------------------------
+
+def _check_srv(st, srv, allow=()):
+    if st == GASA_OK or st in allow:
+        return st
+    L = load()
+    raise GasaError(st, L.gasa_status_string(st).decode() + ": " +
+                    L.gasa_server_last_error(srv).decode())
+
+
+def gasa_server_create(device=0, budget_bytes=40 << 30, max_batch=8):
+    srv = c_vp()
+    _check(load().gasa_server_create(ctypes.byref(srv), c_i32(device), c_i64(budget_bytes),
+                                     c_i32(max_batch)))
+    return srv
+
+
+def gasa_server_add_mesh(srv, ctx):
+    mid = c_i32()
+    _check_srv(load().gasa_server_add_mesh(srv, ctx, ctypes.byref(mid)), srv)
+    return mid.value
+
+
+def gasa_server_submit(srv, mesh_id, b, tol, precision=GASA_PREC_FP64):
+    """b: host float64 array (copied before return); returns the ticket."""
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    t = ctypes.c_uint64()
+    _check_srv(load().gasa_server_submit(srv, c_i32(mesh_id), c_vp(b.ctypes.data), c_dbl(tol),
+                                         c_i32(precision), ctypes.byref(t)), srv)
+    return t.value
+
+
+def gasa_server_poll(srv, ticket, x_out=None):
+    """(status, info); status GASA_PENDING while the solve is not finished.
+    x_out: host float64 array of the mesh's dofs, written when finished."""
+    info = gasa_solve_info()
+    st = load().gasa_server_poll(srv, ctypes.c_uint64(ticket), c_vp(_ptr(x_out)), ctypes.byref(info))
+    if st == GASA_ERR_INVALID_ARG:
+        _check_srv(st, srv)
+    return st, info
+
+
+def gasa_server_drain(srv, timeout_s=600.0):
+    _check_srv(load().gasa_server_drain(srv, c_dbl(timeout_s)), srv)
+
+
+def gasa_server_stats_read(srv):
+    out = gasa_server_stats()
+    _check(load().gasa_server_stats_read(srv, ctypes.byref(out)))
+    return {k: int(getattr(out, k)) for k, _ in gasa_server_stats._fields_}
+
+
+def gasa_server_destroy(srv):
+    _check(load().gasa_server_destroy(srv))
+
+
+def gasa_server_last_error(srv):
+    return load().gasa_server_last_error(srv).decode()
 
 
 # single operations -------------------------------------------------------------

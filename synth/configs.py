@@ -117,11 +117,22 @@ def poisson3d_p2(seed: int = SEED, n: int = 48) -> Problem:
     return poisson3d(n, 2, r=80, n_levels=5, seed=seed, name=f"poisson3d_p2_{n}cubed")
 
 
-def convdiff2d_q2(seed: int = SEED, n: int = 512, peclet: float = 100.0) -> Problem:
+def convdiff2d(n: int = 512, p: int = 2, peclet: float = 100.0, r: Optional[int] = None,
+               seed: int = SEED, name: Optional[str] = None) -> Problem:
+    """n x n jittered quads, LDG diffusion + upwind convection, Q_p, GMRES,
+    levels by the paper's rule; r defaults to the level-1 aggregate dofs."""
     from .ldg import ldg_convdiff_assemble
     mesh = quad_mesh(n, seed, 0.2)
-    A = ldg_convdiff_assemble(mesh, 2, peclet)
+    A = ldg_convdiff_assemble(mesh, p, peclet)
     n_levels = paper_level_count(mesh.n_elems, 2)
-    pr = _finish(f"convdiff2d_q2_{n}x{n}_pe{peclet:g}", mesh, A, n_levels, 36, "gmres", 2, seed)
+    if r is None:
+        r = 4 * A.b
+    if name is None:
+        name = f"convdiff2d_q{p}_{n}x{n}_pe{peclet:g}"
+    pr = _finish(name, mesh, A, n_levels, r, "gmres", p, seed)
     pr.extra["peclet"] = peclet
     return pr
+
+
+def convdiff2d_q2(seed: int = SEED, n: int = 512, peclet: float = 100.0) -> Problem:
+    return convdiff2d(n, 2, peclet, r=36, seed=seed)

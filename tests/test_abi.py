@@ -53,10 +53,12 @@ int main(void) {
   printf("gasa_options %zu\n", sizeof(gasa_options));
   printf("gasa_setup_info %zu\n", sizeof(gasa_setup_info));
   printf("gasa_solve_info %zu\n", sizeof(gasa_solve_info));
+  printf("gasa_server_stats %zu\n", sizeof(gasa_server_stats));
   P(gasa_options, gamma); P(gasa_options, seed); P(gasa_options, init_candidates);
-  P(gasa_options, bulk_staging);
+  P(gasa_options, bulk_staging); P(gasa_options, matrix_free_levels);
   P(gasa_setup_info, omega); P(gasa_setup_info, seconds); P(gasa_setup_info, device_bytes);
   P(gasa_bsr, val); P(gasa_bsr, on_device); P(gasa_solve_info, rel_residual);
+  P(gasa_server_stats, peak_running); P(gasa_server_stats, graph_launches);
   return 0;
 }
 """
@@ -76,16 +78,20 @@ def test_struct_layouts_match_c(tmp_path):
         "gasa_options": ctypes.sizeof(gasa.gasa_options),
         "gasa_setup_info": ctypes.sizeof(gasa.gasa_setup_info),
         "gasa_solve_info": ctypes.sizeof(gasa.gasa_solve_info),
+        "gasa_server_stats": ctypes.sizeof(gasa.gasa_server_stats),
         "gasa_options.gamma": gasa.gasa_options.gamma.offset,
         "gasa_options.seed": gasa.gasa_options.seed.offset,
         "gasa_options.init_candidates": gasa.gasa_options.init_candidates.offset,
         "gasa_options.bulk_staging": gasa.gasa_options.bulk_staging.offset,
+        "gasa_options.matrix_free_levels": gasa.gasa_options.matrix_free_levels.offset,
         "gasa_setup_info.omega": gasa.gasa_setup_info.omega.offset,
         "gasa_setup_info.seconds": gasa.gasa_setup_info.seconds.offset,
         "gasa_setup_info.device_bytes": gasa.gasa_setup_info.device_bytes.offset,
         "gasa_bsr.val": gasa.gasa_bsr.val.offset,
         "gasa_bsr.on_device": gasa.gasa_bsr.on_device.offset,
         "gasa_solve_info.rel_residual": gasa.gasa_solve_info.rel_residual.offset,
+        "gasa_server_stats.peak_running": gasa.gasa_server_stats.peak_running.offset,
+        "gasa_server_stats.graph_launches": gasa.gasa_server_stats.graph_launches.offset,
     }
     for k, v in py.items():
         assert int(got[k]) == v, k
@@ -127,3 +133,10 @@ def test_single_ops_validate_before_device_work():
     assert L.gasa_dense_inverse(0, None, None, None, None) == gasa.GASA_ERR_INVALID_ARG
     assert L.gasa_setup(None, None, None, None, None, None, None, None) == gasa.GASA_ERR_INVALID_ARG
     assert L.gasa_solve(None, None, None, ctypes.c_double(1e-10), 0, 0, None) == gasa.GASA_ERR_INVALID_ARG
+    # server calls validate before device work
+    srv = ctypes.c_void_p()
+    assert L.gasa_server_create(ctypes.byref(srv), 0, ctypes.c_int64(1 << 30), 3) == gasa.GASA_ERR_INVALID_ARG
+    assert L.gasa_server_create(ctypes.byref(srv), 0, ctypes.c_int64(0), 8) == gasa.GASA_ERR_INVALID_ARG
+    assert L.gasa_server_add_mesh(None, None, None) == gasa.GASA_ERR_INVALID_ARG
+    assert L.gasa_server_poll(None, ctypes.c_uint64(1), None, None) == gasa.GASA_ERR_INVALID_ARG
+    assert L.gasa_server_destroy(None) == gasa.GASA_OK

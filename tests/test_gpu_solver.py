@@ -240,3 +240,87 @@ def test_graph_solve_equals_host_loop(name):
             assert np.array_equal(xg, xg2)
     finally:
         gasa.gasa_destroy(ctx)
+
+
+@pytest.mark.parametrize("name", ["tiny", "c1"])
+def test_stationary_solve(name):
+    """Alg. 2 as a solver (x <- x + V(b - A x)) in FP64 and with the FP32
+    V-cycle (iterative refinement): iteration counts within 1 of the oracle,
+    FP64 solution within 1e-10; graph and host-driven loops agree bit for bit."""
+    gasa = _gasa()
+    H = oracle_setup(name)
+    pr = problem(name)
+    ref = O.stationary(H, pr.rhs, TOL, max_iter=1000)
+    ref32 = O.stationary(H, pr.rhs, TOL, max_iter=1000, precision="mixed32")
+    assert ref.converged and ref32.converged
+    ctx, _ = gpu_setup(name, keep=False, solver=gasa.GASA_SOLVER_STATIONARY)
+    try:
+        x = np.zeros_like(pr.rhs)
+        info = gasa.gasa_solve(ctx, pr.rhs, x, TOL)
+        assert info.converged and info.rel_residual <= TOL
+        assert abs(info.iterations - ref.iterations) <= 1, (info.iterations, ref.iterations)
+        assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= TOL
+        xm = np.zeros_like(pr.rhs)
+        info32 = gasa.gasa_solve(ctx, pr.rhs, xm, TOL, gasa.GASA_PREC_MIXED32)
+        assert info32.converged and info32.rel_residual <= TOL
+        assert abs(info32.iterations - ref32.iterations) <= 1, (info32.iterations, ref32.iterations)
+        gasa.gasa_profile_enable(ctx, True)
+        xh = np.zeros_like(pr.rhs)
+        ih = gasa.gasa_solve(ctx, pr.rhs, xh, TOL)
+        gasa.gasa_profile_enable(ctx, False)
+        assert ih.iterations == info.iterations
+        assert np.array_equal(xh, x)
+    finally:
+        gasa.gasa_destroy(ctx)
+
+
+@pytest.mark.parametrize("name,kappa", [("c1", 1), ("c1", 2), ("cd_q2_16", 2), ("p3_16", 3)])
+def test_matrix_free_levels(name, kappa):
+    """Section 4.4: A_1 .. A_kappa dropped after setup and applied through the
+    transfers.  The V-cycle matches the oracle's matrix-free V-cycle, the
+    solves match the oracle's (iterations within 1, FP64 solution within
+    1e-10), the stored A_k are gone and the resident hierarchy is smaller."""
+    gasa = _gasa()
+    H = oracle_setup(name)
+    pr = problem(name)
+    ctx0, info0 = gpu_setup(name, keep=False)
+    ctx, info = gpu_setup(name, keep=False, matrix_free_levels=kappa)
+    try:
+        assert info.device_bytes < info0.device_bytes
+        want = O.make_vcycle(H, matrix_free_levels=kappa)(pr.rhs)
+        z = to_dev(np.zeros_like(pr.rhs))
+        gasa.gasa_vcycle(ctx, to_dev(pr.rhs), z)
+        assert rel_err(to_host(z), want) <= 0.1 * level_tolerances(H)[-1]
+        wantf = O.make_vcycle(H, "fp32", matrix_free_levels=kappa)(pr.rhs)
+        gasa.gasa_vcycle(ctx, to_dev(pr.rhs), z, gasa.GASA_PREC_MIXED32)
+        assert rel_err(to_host(z), wantf) <= 1e-4
+        solver = pr.solver
+        ref = O.solve(H, pr.rhs, TOL, solver, restart=30, max_iter=5000, matrix_free_levels=kappa)
+        x = np.zeros_like(pr.rhs)
+        inf = gasa.gasa_solve(ctx, pr.rhs, x, TOL)
+        assert inf.converged and inf.rel_residual <= TOL
+        assert abs(inf.iterations - ref.iterations) <= 1, (inf.iterations, ref.iterations)
+        assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= TOL
+        ref32 = O.solve(H, pr.rhs, TOL, solver, precision="mixed32", restart=30, max_iter=5000,
+                        matrix_free_levels=kappa)
+        inf32 = gasa.gasa_solve(ctx, pr.rhs, x, TOL, gasa.GASA_PREC_MIXED32)
+        assert inf32.converged and abs(inf32.iterations - ref32.iterations) <= 1
+        for k in range(1, kappa + 1):
+            with pytest.raises(gasa.GasaError):
+                gasa.gasa_get_level(ctx, k, gasa.GASA_LV_A_VAL, np.zeros(1))
+        # the request server runs matrix-free levels too
+        srv = gasa.gasa_server_create(0, 8 << 30, 4)
+        try:
+            mid = gasa.gasa_server_add_mesh(srv, ctx)
+            t = gasa.gasa_server_submit(srv, mid, pr.rhs, TOL, gasa.GASA_PREC_FP64)
+            gasa.gasa_server_drain(srv, 300.0)
+            xs = np.zeros_like(pr.rhs)
+            st, si = gasa.gasa_server_poll(srv, t, xs)
+            assert st == gasa.GASA_OK and si.rel_residual <= TOL
+            assert abs(si.iterations - ref.iterations) <= 1
+            assert np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x) <= TOL
+        finally:
+            gasa.gasa_server_destroy(srv)
+    finally:
+        gasa.gasa_destroy(ctx)
+        gasa.gasa_destroy(ctx0)

@@ -378,3 +378,26 @@ def test_null_singular_vectors_completed_deterministically():
     assert sv[0][2] <= 1e-10 * sv[0][0]
     assert np.max(np.abs(Td.T @ Td - np.eye(3))) <= 1e-14
     assert np.max(np.abs(Td[:, :2] @ (Td[:, :2].T @ B) - B)) <= 1e-12 * np.max(np.abs(B))
+
+
+def test_matrix_free_levels_apply_the_galerkin_operator():
+    """Section 4.4: A_k applied as R_{k-1} A_{k-1} P_{k-1} equals the stored
+    Galerkin operator (to rounding), at every matrix-free depth, and a V-cycle
+    with matrix-free levels is the same preconditioner."""
+    pr = configs.poisson2d(8, 1, r=12, n_levels=4, name="tiny4")
+    H = O.setup(pr.A.row_ptr, pr.A.col, pr.A.val, pr.agg_of, B0=pr.B0, r=pr.r, dim=2)
+    assert H.N == 3
+    rng = np.random.default_rng(7)
+    prev = H.levels[0].A
+    for k in range(1, H.N):
+        prev = O.GalerkinOperator(H.levels[k - 1].R, prev, H.levels[k - 1].P)
+        x = rng.standard_normal(H.levels[k].A.shape[0])
+        ref = H.levels[k].A @ x
+        assert np.linalg.norm(prev @ x - ref) <= 1e-12 * np.linalg.norm(ref)
+    f = rng.standard_normal(H.levels[0].A.shape[0])
+    u0 = O.make_vcycle(H)(f)
+    for kappa in range(1, H.N):
+        u = O.make_vcycle(H, matrix_free_levels=kappa)(f)
+        assert np.linalg.norm(u - u0) <= 1e-11 * np.linalg.norm(u0)
+    # with kappa = 0 nothing changes, bit for bit
+    assert np.array_equal(O.make_vcycle(H, matrix_free_levels=0)(f), u0)
