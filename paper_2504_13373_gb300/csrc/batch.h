@@ -29,12 +29,15 @@ enum BatchInt {
   BI_COUNT = 6
 };
 
+// nnzb: stored blocks of the matrix (picks the long-row variant)
 template <typename T>
 cudaError_t launch_bmv(int mode, int n_brows, int br, int bc, const int *rp, const int *col,
-                       const T *val, const T *X, const T *B, T *Y, int K, cudaStream_t s);
+                       const T *val, const T *X, const T *B, T *Y, int K, cudaStream_t s,
+                       int64_t nnzb);
 template <typename T>
 cudaError_t launch_bjacobi(int mode, int n, int bs, const int *rp, const int *col, const T *A,
-                           const T *W, const T *X, const T *B, T *Xo, int K, cudaStream_t s);
+                           const T *W, const T *X, const T *B, T *Xo, int K, cudaStream_t s,
+                           int64_t nnzb);
 template <typename T>
 cudaError_t launch_bdense(int nc, const double *Ainv, const T *B, T *X, int K, cudaStream_t s);
 

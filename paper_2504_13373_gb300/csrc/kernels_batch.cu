@@ -19,87 +19,181 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// K consecutive values (one entry of every column) as vector loads
+template <typename T, int K>
+__device__ __forceinline__ void load_k(const T *p, T (&v)[K]) {
+  constexpr int W = (K * (int)sizeof(T) >= 16) ? 16 / (int)sizeof(T) : K;
+  using V = typename VecOf<T, W>::type;
+#pragma unroll
+  for (int c = 0; c < K; c += W) {
+    const V t = __ldg(reinterpret_cast<const V *>(p + c));
+    const T *tt = reinterpret_cast<const T *>(&t);
+#pragma unroll
+    for (int w = 0; w < W; ++w) v[c + w] = tt[w];
+  }
+}
+
+// sum over the blocks [beg, end) of scalar row r of A X, all K columns, in
+// block order; one thread
+template <typename T, int K>
+__device__ __forceinline__ void row_dot_k(int beg, int end, int r, int br, int bc,
+                                          const int *__restrict__ col, const T *__restrict__ val,
+                                          const T *__restrict__ X, T (&acc)[K]) {
+  for (int kb = beg; kb < end; ++kb) {
+    const int j = __ldg(col + kb);
+    const T *a = val + ((size_t)kb * br + r) * bc;
+    const T *x = X + (size_t)j * bc * K;
+    for (int q = 0; q < bc; ++q) {
+      const T av = __ldg(a + q);
+      T xv[K];
+      load_k<T, K>(x + (size_t)q * K, xv);
+#pragma unroll
+      for (int c = 0; c < K; ++c) acc[c] = fma(av, xv[c], acc[c]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
-// block SpMV over K columns: Y = A X, Y += A X or Y = B - A X
+// block SpMV over K columns: Y = A X, Y += A X or Y = B - A X.  Short rows:
+// one thread per scalar row computes all K columns (each matrix value is
+// read once per batch); long rows (coarse levels): one warp per scalar row.
 // ---------------------------------------------------------------------------
+template <typename T, int K>
+__device__ __forceinline__ void store_row(int mode, size_t row, const T (&acc)[K],
+                                          const T *__restrict__ B, T *__restrict__ Y) {
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+    const size_t e = row * K + c;
+    T out;
+    if (mode == GASA_MV_RESIDUAL) out = B[e] - acc[c];
+    else if (mode == GASA_MV_ADD) out = Y[e] + acc[c];
+    else out = acc[c];
+    Y[e] = out;
+  }
+}
+
 template <typename T, int K>
 __global__ void __launch_bounds__(kThreads)
 bmv_kernel(int mode, int64_t n_rows, int br, int bc, const int *__restrict__ rp,
            const int *__restrict__ col, const T *__restrict__ val, const T *__restrict__ X,
            const T *__restrict__ B, T *__restrict__ Y) {
-  pdl_entry();
-  const int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-  if (e >= n_rows * K) return;
-  const int64_t row = e / K;
-  const int c = (int)(e - row * K);
+  const int64_t row = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (row >= n_rows) return;
   const int i = (int)(row / br);
   const int r = (int)(row - (int64_t)i * br);
-  const int beg = __ldg(rp + i), end = __ldg(rp + i + 1);
-  T acc = T(0);
-  for (int kb = beg; kb < end; ++kb) {
+  T acc[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) acc[c] = T(0);
+  row_dot_k<T, K>(__ldg(rp + i), __ldg(rp + i + 1), r, br, bc, col, val, X, acc);
+  store_row<T, K>(mode, (size_t)row, acc, B, Y);
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void row_dot_k_strided(int beg, int end, int r, int br, int bc,
+                                                  int lane, const int *__restrict__ col,
+                                                  const T *__restrict__ val,
+                                                  const T *__restrict__ X, T (&acc)[K]) {
+#pragma unroll
+  for (int c = 0; c < K; ++c) acc[c] = T(0);
+  for (int kb = beg + lane; kb < end; kb += 32) {
     const int j = __ldg(col + kb);
     const T *a = val + ((size_t)kb * br + r) * bc;
-    const T *x = X + (size_t)j * bc * K + c;
-    for (int q = 0; q < bc; ++q) acc = fma(__ldg(a + q), __ldg(x + (size_t)q * K), acc);
+    const T *x = X + (size_t)j * bc * K;
+    for (int q = 0; q < bc; ++q) {
+      const T av = __ldg(a + q);
+      T xv[K];
+      load_k<T, K>(x + (size_t)q * K, xv);
+#pragma unroll
+      for (int c = 0; c < K; ++c) acc[c] = fma(av, xv[c], acc[c]);
+    }
   }
-  T out;
-  if (mode == GASA_MV_RESIDUAL) out = B[e] - acc;
-  else if (mode == GASA_MV_ADD) out = Y[e] + acc;
-  else out = acc;
-  Y[e] = out;
+#pragma unroll
+  for (int c = 0; c < K; ++c) acc[c] = warp_sum(acc[c]);
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(kThreads)
+bmv_warp_kernel(int mode, int64_t n_rows, int br, int bc, const int *__restrict__ rp,
+                const int *__restrict__ col, const T *__restrict__ val, const T *__restrict__ X,
+                const T *__restrict__ B, T *__restrict__ Y) {
+  const int64_t row = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n_rows) return;
+  const int i = (int)(row / br);
+  const int r = (int)(row - (int64_t)i * br);
+  T acc[K];
+  row_dot_k_strided<T, K>(__ldg(rp + i), __ldg(rp + i + 1), r, br, bc, lane, col, val, X, acc);
+  if (lane == 0) store_row<T, K>(mode, (size_t)row, acc, B, Y);
 }
 
 // ---------------------------------------------------------------------------
 // block-Jacobi step over K columns (Alg. 1): Xo = X + W (B - A X), or
-// Xo = W B for the first step from zero.  A CTA owns `rows_cta` whole block
-// rows; the residual of a block row goes through shared memory.
+// Xo = W B for the first step from zero.  A CTA owns whole block rows; the
+// residuals of a block row (all K columns) go through shared memory.  Short
+// rows: one thread per scalar row; long rows: one warp per scalar row.
 // ---------------------------------------------------------------------------
-template <typename T, int K>
+template <typename T, int K, bool WARP>
 __global__ void __launch_bounds__(kThreads)
 bjacobi_kernel(int mode, int n, int bs, int rows_cta, const int *__restrict__ rp,
                const int *__restrict__ col, const T *__restrict__ A, const T *__restrict__ W,
                const T *__restrict__ X, const T *__restrict__ B, T *__restrict__ Xo) {
-  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *res = reinterpret_cast<T *>(smem_raw);
-  const int per = bs * K;
+  T *res = reinterpret_cast<T *>(smem_raw);          // [rows_cta * bs][K]
   const int i0 = blockIdx.x * rows_cta;
-  const int tot = rows_cta * per;
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int li = e / per, rem = e - li * per;
-    const int r = rem / K, c = rem - r * K;
+  const int nrow = rows_cta * bs;
+  const int lane = threadIdx.x & 31;
+  const int step = WARP ? (int)(blockDim.x >> 5) : (int)blockDim.x;
+  for (int t = WARP ? (int)(threadIdx.x >> 5) : (int)threadIdx.x; t < nrow; t += step) {
+    const int li = t / bs, r = t - li * bs;
     const int i = i0 + li;
-    T v = T(0);
+    T v[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) v[c] = T(0);
     if (i < n) {
-      const size_t g = ((size_t)i * bs + r) * K + c;
-      v = B[g];
+      const size_t g = ((size_t)i * bs + r) * K;
       if (mode == JAC_SWEEP) {
-        T acc = T(0);
-        const int beg = __ldg(rp + i), end = __ldg(rp + i + 1);
-        for (int kb = beg; kb < end; ++kb) {
-          const int j = __ldg(col + kb);
-          const T *a = A + ((size_t)kb * bs + r) * bs;
-          const T *x = X + (size_t)j * bs * K + c;
-          for (int q = 0; q < bs; ++q) acc = fma(__ldg(a + q), __ldg(x + (size_t)q * K), acc);
+        T acc[K];
+        if (WARP) {
+          row_dot_k_strided<T, K>(__ldg(rp + i), __ldg(rp + i + 1), r, bs, bs, lane, col, A, X, acc);
+        } else {
+#pragma unroll
+          for (int c = 0; c < K; ++c) acc[c] = T(0);
+          row_dot_k<T, K>(__ldg(rp + i), __ldg(rp + i + 1), r, bs, bs, col, A, X, acc);
         }
-        v = v - acc;
+#pragma unroll
+        for (int c = 0; c < K; ++c) v[c] = B[g + c] - acc[c];
+      } else {
+#pragma unroll
+        for (int c = 0; c < K; ++c) v[c] = B[g + c];
       }
     }
-    res[e] = v;
+    if (!WARP || lane == 0) {
+#pragma unroll
+      for (int c = 0; c < K; ++c) res[(size_t)t * K + c] = v[c];
+    }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int li = e / per, rem = e - li * per;
-    const int r = rem / K, c = rem - r * K;
+  for (int t = threadIdx.x; t < nrow; t += blockDim.x) {
+    const int li = t / bs, r = t - li * bs;
     const int i = i0 + li;
     if (i >= n) continue;
     const T *w = W + ((size_t)i * bs + r) * bs;
-    const T *rl = res + li * per + c;
-    T out = T(0);
-    for (int q = 0; q < bs; ++q) out = fma(__ldg(w + q), rl[q * K], out);
-    const size_t g = ((size_t)i * bs + r) * K + c;
-    if (mode == JAC_SWEEP) out += X[g];
-    Xo[g] = out;
+    const T *rl = res + (size_t)li * bs * K;
+    T out[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) out[c] = T(0);
+    for (int q = 0; q < bs; ++q) {
+      const T wv = __ldg(w + q);
+#pragma unroll
+      for (int c = 0; c < K; ++c) out[c] = fma(wv, rl[q * K + c], out[c]);
+    }
+    const size_t g = ((size_t)i * bs + r) * K;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      T o = out[c];
+      if (mode == JAC_SWEEP) o += X[g + c];
+      Xo[g + c] = o;
+    }
   }
 }
 
@@ -570,27 +664,44 @@ __global__ void bcolcopy_kernel(int64_t n, int K, int c, const T *__restrict__ s
     default: return cudaErrorInvalidValue;         \
   }
 
+// long rows (coarse levels, >= 16 blocks per block row on average) take the
+// warp variants; the choice depends on the matrix only, never on K, so a
+// column's bits do not depend on the batch width
+static bool long_rows(int n_brows, int64_t nnzb) { return nnzb >= 16 * (int64_t)n_brows; }
+
 template <typename T>
 cudaError_t launch_bmv(int mode, int n_brows, int br, int bc, const int *rp, const int *col,
-                       const T *val, const T *X, const T *B, T *Y, int K, cudaStream_t s) {
-  const int64_t tot = (int64_t)n_brows * br * K;
-  if (tot == 0) return cudaSuccess;
-  GASA_KSWITCH(K, launch_k(bmv_kernel<T, KK>, div_up(tot, kThreads), kThreads, 0, s, 
-                      mode, (int64_t)n_brows * br, br, bc, rp, col, val, X, B, Y));
+                       const T *val, const T *X, const T *B, T *Y, int K, cudaStream_t s,
+                       int64_t nnzb) {
+  const int64_t rows = (int64_t)n_brows * br;
+  if (rows == 0) return cudaSuccess;
+  if (long_rows(n_brows, nnzb)) {
+    GASA_KSWITCH(K, launch_k(bmv_warp_kernel<T, KK>, div_up(rows * 32, kThreads), kThreads, 0, s,
+                             mode, rows, br, bc, rp, col, val, X, B, Y));
+  } else {
+    GASA_KSWITCH(K, launch_k(bmv_kernel<T, KK>, div_up(rows, kThreads), kThreads, 0, s,
+                             mode, rows, br, bc, rp, col, val, X, B, Y));
+  }
   note_launch();
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_bjacobi(int mode, int n, int bs, const int *rp, const int *col, const T *A,
-                           const T *W, const T *X, const T *B, T *Xo, int K, cudaStream_t s) {
+                           const T *W, const T *X, const T *B, T *Xo, int K, cudaStream_t s,
+                           int64_t nnzb) {
   if (n == 0) return cudaSuccess;
-  const int per = bs * K;
-  const int rows_cta = std::max(1, kThreads / per);
-  const size_t smem = (size_t)rows_cta * per * sizeof(T);
+  const bool warp = mode == JAC_SWEEP && long_rows(n, nnzb);
+  const int rows_cta = warp ? 1 : std::max(1, kThreads / bs);
+  const size_t smem = (size_t)rows_cta * bs * K * sizeof(T);
   if (smem > 48 * 1024) return cudaErrorInvalidValue;
-  GASA_KSWITCH(K, launch_k(bjacobi_kernel<T, KK>, div_up(n, rows_cta), kThreads, smem, s, 
-                      mode, n, bs, rows_cta, rp, col, A, W, X, B, Xo));
+  if (warp) {
+    GASA_KSWITCH(K, launch_k(bjacobi_kernel<T, KK, true>, div_up(n, rows_cta), kThreads, smem, s,
+                             mode, n, bs, rows_cta, rp, col, A, W, X, B, Xo));
+  } else {
+    GASA_KSWITCH(K, launch_k(bjacobi_kernel<T, KK, false>, div_up(n, rows_cta), kThreads, smem, s,
+                             mode, n, bs, rows_cta, rp, col, A, W, X, B, Xo));
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -777,10 +888,10 @@ cudaError_t launch_bcolcopy(int64_t n, int K, int c, const double *src, double *
 
 #define GASA_INST_T(T)                                                                          \
   template cudaError_t launch_bmv<T>(int, int, int, int, const int *, const int *, const T *,   \
-                                     const T *, const T *, T *, int, cudaStream_t);             \
+                                     const T *, const T *, T *, int, cudaStream_t, int64_t);    \
   template cudaError_t launch_bjacobi<T>(int, int, int, const int *, const int *, const T *,    \
                                          const T *, const T *, const T *, T *, int,             \
-                                         cudaStream_t);                                         \
+                                         cudaStream_t, int64_t);                                \
   template cudaError_t launch_bdense<T>(int, const double *, const T *, T *, int, cudaStream_t); \
   template cudaError_t launch_bscatter<T>(int64_t, int, int, const T *, T *, cudaStream_t);     \
   template cudaError_t launch_bgather<T>(int64_t, int, int, const T *, T *, cudaStream_t);

@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -250,12 +251,12 @@ cudaError_t bmf_apply(Engine &e, int k, int mode, const T *x, const T *b, T *y) 
   LevelVec &v = e.lv[k - 1];
   T *t = P::mt(v), *u = P::mu(v);
   ECU(launch_bmv<T>(GASA_MV_ASSIGN, lp.P.nrows, lp.P.br, lp.P.bc, lp.P.rp, lp.P.col, P::A(lp.P),
-                    x, nullptr, t, e.K, e.s));
+                    x, nullptr, t, e.K, e.s, lp.P.nnzb));
   if (k - 1 > 0 && lp.mf) ECU(bmf_apply<T>(e, k - 1, GASA_MV_ASSIGN, t, nullptr, u));
   else ECU(launch_bmv<T>(GASA_MV_ASSIGN, lp.n, lp.s, lp.s, lp.A.rp, lp.A.col, P::A(lp.A), t,
-                         nullptr, u, e.K, e.s));
+                         nullptr, u, e.K, e.s, lp.A.nnzb));
   return launch_bmv<T>(mode, lp.R.nrows, lp.R.br, lp.R.bc, lp.R.rp, lp.R.col, P::A(lp.R), u, b, y,
-                       e.K, e.s);
+                       e.K, e.s, lp.R.nnzb);
 }
 
 // one smoothing step of Alg. 1 on K columns
@@ -267,11 +268,11 @@ cudaError_t bsweep(Engine &e, int k, int mode, const T *x, const T *b, T *xo) {
     T *r = P::r(e.lv[k]);
     ECU(bmf_apply<T>(e, k, GASA_MV_RESIDUAL, x, b, r));
     ECU(launch_bjacobi<T>(JAC_FIRST, l.n, l.s, nullptr, nullptr, nullptr, P::W(l), nullptr, r, xo,
-                          e.K, e.s));
+                          e.K, e.s, 0));
     return launch_add<T>(l.ndof * e.K, x, xo, e.s);
   }
   return launch_bjacobi<T>(mode, l.n, l.s, l.A.rp, l.A.col, P::A(l.A), P::W(l), x, b, xo, e.K,
-                           e.s);
+                           e.s, l.A.nnzb);
 }
 
 template <typename T>
@@ -280,7 +281,7 @@ cudaError_t bresid(Engine &e, int k, const T *x, const T *b, T *r) {
   Level &l = e.ctx->L[k];
   if (l.mf) return bmf_apply<T>(e, k, GASA_MV_RESIDUAL, x, b, r);
   return launch_bmv<T>(GASA_MV_RESIDUAL, l.n, l.s, l.s, l.A.rp, l.A.col, P::A(l.A), x, b, r, e.K,
-                       e.s);
+                       e.s, l.A.nnzb);
 }
 
 template <typename T>
@@ -310,7 +311,7 @@ cudaError_t vcycle_b(Engine &e, const T *rhs, T *out) {
     xk[k] = x;
     ECU(bresid<T>(e, k, x, bk[k], P::r(v)));
     ECU(launch_bmv<T>(GASA_MV_ASSIGN, l.R.nrows, l.R.br, l.R.bc, l.R.rp, l.R.col, P::A(l.R),
-                      P::r(v), nullptr, P::b(e.lv[k + 1]), K, s));
+                      P::r(v), nullptr, P::b(e.lv[k + 1]), K, s, l.R.nnzb));
   }
   ECU(launch_bdense<T>(ctx->nc, ctx->coarse_inv, P::b(e.lv[N]), P::x(e.lv[N]), K, s));
   xk[N] = P::x(e.lv[N]);
@@ -320,7 +321,7 @@ cudaError_t vcycle_b(Engine &e, const T *rhs, T *out) {
     T *x = xk[k];
     T *x2 = (x == P::x(v)) ? P::x2(v) : P::x(v);
     ECU(launch_bmv<T>(GASA_MV_ADD, l.P.nrows, l.P.br, l.P.bc, l.P.rp, l.P.col, P::A(l.P),
-                      xk[k + 1], nullptr, x, K, s));
+                      xk[k + 1], nullptr, x, K, s, l.P.nnzb));
     if (tpost == 0 && k == 0)
       ECU(cudaMemcpyAsync(out, x, (size_t)l.ndof * K * sizeof(T), cudaMemcpyDeviceToDevice, s));
     for (int t = 0; t < tpost; ++t) {
@@ -344,7 +345,8 @@ cudaError_t apply_Mb(Engine &e, const double *r, double *z) {
 
 cudaError_t outer_mv(Engine &e, int mode, const double *x, const double *b, double *y) {
   Level &l = e.ctx->L[0];
-  return launch_bmv<double>(mode, l.n, l.s, l.s, l.A.rp, l.A.col, l.A.val, x, b, y, e.K, e.s);
+  return launch_bmv<double>(mode, l.n, l.s, l.s, l.A.rp, l.A.col, l.A.val, x, b, y, e.K, e.s,
+                            l.A.nnzb);
 }
 
 // ----------------------------------------------------------------------------
@@ -502,7 +504,14 @@ int64_t engine_bytes(gasa_ctx *ctx, int mesh, int prec, int K, int max_iter_unus
 
 cudaError_t create_engine(Engine &e) {
   ECU(cudaSetDevice(e.srv->device));
-  ECU(cudaStreamCreateWithFlags(&e.s, cudaStreamNonBlocking));
+  // smaller meshes get higher stream priority (shortest work first): their
+  // kernels are scheduled ahead of a large mesh's between its launches
+  int least = 0, greatest = 0;
+  ECU(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  const double lg = std::log2((double)std::max<int64_t>(e.n, 1));
+  int prio = greatest + std::max(0, (int)((lg - 10.0) / 2.0));
+  prio = std::min(prio, least);
+  ECU(cudaStreamCreateWithPriority(&e.s, cudaStreamNonBlocking, prio));
   Alloc a{&e, true};
   layout(e, a);
   e.bytes = a.bytes;

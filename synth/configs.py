@@ -134,5 +134,44 @@ def convdiff2d(n: int = 512, p: int = 2, peclet: float = 100.0, r: Optional[int]
     return pr
 
 
+def convdiff3d(n: int = 16, p: int = 1, peclet: float = 100.0, r: Optional[int] = None,
+               seed: int = SEED, name: Optional[str] = None) -> Problem:
+    """n^3 jittered cubes x 6 Kuhn tets on the unit cube, LDG diffusion +
+    upwind convection with the paper's velocity (1, 2, 3) / sqrt(14), P_p,
+    GMRES, levels by the paper's rule; Pe = 0 is pure diffusion, Pe = inf
+    pure convection; r defaults to the level-1 aggregate dofs."""
+    from .ldg_simplex import ldg_convdiff_simplex
+    mesh = tet_mesh(n, seed, 0.15)
+    vel = np.array([1.0, 2.0, 3.0]) / np.sqrt(14.0)
+    A = ldg_convdiff_simplex(mesh, p, peclet, vel)
+    n_levels = paper_level_count(mesh.n_elems, 3)
+    if r is None:
+        r = 8 * A.b
+    if name is None:
+        name = f"convdiff3d_p{p}_{n}cubed_pe{peclet:g}"
+    pr = _finish(name, mesh, A, n_levels, r, "gmres", p, seed)
+    pr.extra["peclet"] = peclet
+    return pr
+
+
+def poisson3d_hex(M: int = 4, p: int = 1, r: Optional[int] = None, seed: int = SEED) -> Problem:
+    """The paper's first elliptic test (Section 6.1): [-1, 1]^3 cut into 2^M
+    hexahedra per side, Q_p, SIPG with penalty M (p+1)^2 / 2, Dirichlet on
+    x = -1 and Neumann elsewhere; the right-hand side is the load vector of
+    the manufactured solution exp(sin(pi x) sin(pi y) sin(pi z)) - 1 (not a
+    random vector); levels by the paper's rule; r defaults to the level-1
+    aggregate dofs."""
+    from .hex import hex_mesh, load_vector, sipg_hex
+    mesh = hex_mesh(M)
+    A = sipg_hex(mesh, p, M)
+    n_levels = paper_level_count(mesh.n_elems, 3)
+    if r is None:
+        r = 8 * A.b
+    pr = _finish(f"poisson3d_hex_q{p}_M{M}", mesh, A, n_levels, r, "cg", p, seed)
+    pr.rhs = load_vector(mesh, p)
+    pr.extra["M"] = M
+    return pr
+
+
 def convdiff2d_q2(seed: int = SEED, n: int = 512, peclet: float = 100.0) -> Problem:
     return convdiff2d(n, 2, peclet, r=36, seed=seed)

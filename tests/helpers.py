@@ -32,6 +32,12 @@ def problem(name: str):
         return configs.convdiff2d_q2(n=32, peclet=1e4)
     if name == "cd_q2_32_pe1":
         return configs.convdiff2d_q2(n=32, peclet=1.0)
+    if name.startswith("hex_M"):
+        return configs.poisson3d_hex(int(name[5:]))
+    if name.startswith("cd3_"):
+        # 3-D LDG + upwind on Kuhn tets, P1: cd3_<cells>_pe<Pe>
+        _, n, pe = name.split("_")
+        return configs.convdiff3d(int(n), 1, float(pe[2:]), name=name)
     raise KeyError(name)
 
 

@@ -60,7 +60,7 @@ def _level_bsr(gasa, ctx, k, which, sh, br, bc, nrows):
     return rp, col, val
 
 
-@pytest.mark.parametrize("name", ["tiny", "c1", "p3_16", "tet_p2_4", "cd_q2_16"])
+@pytest.mark.parametrize("name", ["tiny", "c1", "p3_16", "tet_p2_4", "cd_q2_16", "cd3_8_pe100"])
 def test_setup_hierarchy(name):
     gasa = _gasa()
     H = oracle_setup(name)
@@ -106,7 +106,7 @@ def test_setup_hierarchy(name):
         gasa.gasa_destroy(ctx)
 
 
-@pytest.mark.parametrize("name", ["tiny", "c1", "tet_p2_4", "cd_q2_16"])
+@pytest.mark.parametrize("name", ["tiny", "c1", "tet_p2_4", "cd_q2_16", "cd3_4_peinf"])
 def test_vcycle(name):
     gasa = _gasa()
     H = oracle_setup(name)
@@ -167,7 +167,8 @@ def test_cg_solve(name):
         gasa.gasa_destroy(ctx)
 
 
-@pytest.mark.parametrize("name", ["tiny", "c1", "cd_q2_16", "cd_q2_32_pe1e4", "cd_q2_32_pe1"])
+@pytest.mark.parametrize("name", ["tiny", "c1", "cd_q2_16", "cd_q2_32_pe1e4", "cd_q2_32_pe1",
+                                  "cd3_4_pe0", "cd3_4_pe1000", "cd3_4_peinf", "cd3_8_pe100"])
 def test_gmres_solve(name):
     gasa = _gasa()
     H = oracle_setup(name)
@@ -324,3 +325,29 @@ def test_matrix_free_levels(name, kappa):
     finally:
         gasa.gasa_destroy(ctx)
         gasa.gasa_destroy(ctx0)
+
+
+def test_paper_hex_poisson():
+    """The paper's first elliptic test (Section 6.1) at M = 3 (4,096 dofs, Q1
+    hexahedra, mixed Dirichlet/Neumann, manufactured right-hand side, tol
+    1e-7): CG-preconditioned and stationary solves match the oracle's
+    iteration counts within 1.  The paper reports 6 (pCG) and 7 (solver) on
+    METIS aggregates; this hierarchy gives 7 and 13 (context, not parity)."""
+    gasa = _gasa()
+    name = "hex_M3"
+    H = oracle_setup(name)
+    pr = problem(name)
+    tol = 1e-7
+    ref_cg = O.solve(H, pr.rhs, tol, "cg", max_iter=500)
+    ref_st = O.stationary(H, pr.rhs, tol, max_iter=500)
+    for solver, ref in ((gasa.GASA_SOLVER_CG, ref_cg), (gasa.GASA_SOLVER_STATIONARY, ref_st)):
+        ctx, _ = gpu_setup(name, keep=False, solver=solver)
+        try:
+            x = np.zeros_like(pr.rhs)
+            info = gasa.gasa_solve(ctx, pr.rhs, x, tol)
+            assert info.converged and info.rel_residual <= tol
+            assert abs(info.iterations - ref.iterations) <= 1, (solver, info.iterations, ref.iterations)
+            assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= 1e-6
+        finally:
+            gasa.gasa_destroy(ctx)
+    assert 3 <= ref_cg.iterations <= 13

@@ -186,3 +186,86 @@ def test_ldg_stencil_and_nonsymmetry():
     assert abs(S - S.T).max() > 1e-3 * abs(S).max()
     Ad = ldg.ldg_convdiff_assemble(m, 2, 1.0, convection=False).to_scipy()
     assert abs(Ad - Ad.T).max() <= 1e-10 * abs(Ad).max()
+
+
+def _mms_simplex(dim, p, pe, ns, vel):
+    from synth.ldg_simplex import ldg_convdiff_simplex
+    mu = np.linalg.norm(vel) / pe
+
+    def u(x):
+        return np.prod(np.sin(np.pi * x), axis=-1)
+
+    def f(x):
+        s = u(x)
+        grad = []
+        for k in range(dim):
+            gk = np.pi * np.cos(np.pi * x[..., k])
+            for j in range(dim):
+                if j != k:
+                    gk = gk * np.sin(np.pi * x[..., j])
+            grad.append(gk)
+        return mu * dim * np.pi ** 2 * s + sum(vel[k] * grad[k] for k in range(dim))
+
+    errs = []
+    for n in ns:
+        m = M.tri_mesh(n, 7, 0.2) if dim == 2 else M.tet_mesh(n, 7, 0.15)
+        A = ldg_convdiff_simplex(m, p, pe, vel)
+        uh = sla.spsolve(A.to_scipy().tocsc(), dg.simplex_load_and_error(m, p, f))
+        errs.append(dg.simplex_load_and_error(m, p, f, u, uh))
+    return np.log2(errs[-2] / errs[-1]), errs
+
+
+@pytest.mark.parametrize("dim,p,pe,ns", [(2, 1, 1.0, (8, 16, 32)), (2, 2, 100.0, (8, 16, 32)),
+                                         (3, 1, 1.0, (4, 8))])
+def test_ldg_simplex_manufactured_solution_order(dim, p, pe, ns):
+    """LDG diffusion + upwind convection on triangles and Kuhn tetrahedra:
+    the L2 error of u = prod sin(pi x_k) decreases at order p + 1."""
+    vel = (np.array([np.cos(np.pi / 6), np.sin(np.pi / 6)]) if dim == 2
+           else np.array([1.0, 2.0, 3.0]) / np.sqrt(14.0))
+    slope, errs = _mms_simplex(dim, p, pe, ns, vel)
+    assert slope > p + 1 - 0.2, (errs, slope)
+
+
+def test_ldg_simplex_limits_and_structure():
+    """Pe = 0 gives the symmetric pure-diffusion LDG operator; Pe = inf the
+    pure upwind convection operator, which is block triangular in the flow
+    order (no cycles: some ordering makes it block lower triangular), and
+    finite Pe their sum with mu = |v| / Pe."""
+    from synth.ldg_simplex import ldg_convdiff_simplex
+    m = M.tet_mesh(3, 5, 0.15)
+    v = np.array([1.0, 2.0, 3.0]) / np.sqrt(14.0)
+    D = ldg_convdiff_simplex(m, 1, 0.0, v).to_scipy()
+    assert abs(D - D.T).max() <= 1e-10 * abs(D).max()
+    C = ldg_convdiff_simplex(m, 1, np.inf, v).to_scipy()
+    mix = ldg_convdiff_simplex(m, 1, 100.0, v).to_scipy()
+    Dv = ldg_convdiff_simplex(m, 1, 1.0, v, convection=False).to_scipy()   # mu = |v| = 1
+    assert abs(mix - (C + Dv / 100.0)).max() <= 1e-12 * abs(mix).max()
+    # upwind convection couples an element only to its upwind face neighbours
+    ne, nb = m.n_elems, 4
+    Cb = C.tobsr(blocksize=(nb, nb))
+    import scipy.sparse as sp
+    import scipy.sparse.csgraph as cg
+    pat = sp.csr_matrix((np.ones(Cb.indices.size), Cb.indices, Cb.indptr), shape=(ne, ne))
+    pat.setdiag(0)
+    pat.eliminate_zeros()
+    ncomp, _ = cg.connected_components(pat, directed=True, connection="strong")
+    assert ncomp == ne          # no directed cycles between elements
+
+
+def test_hex_sipg_manufactured_solution_order():
+    """The paper's first elliptic test (Section 6.1) on 2^M hexahedra per
+    side, Q1, SIPG with penalty M (p+1)^2 / 2 / h, Dirichlet on x = -1 and
+    Neumann elsewhere: the operator is symmetric with at most 7 blocks per
+    row, and the L2 error of exp(sin sin sin) - 1 falls at order p + 1."""
+    from synth import hex as HX
+    errs = []
+    for Mlev in (3, 4):
+        m = HX.hex_mesh(Mlev)
+        A = HX.sipg_hex(m, 1, Mlev)
+        S = A.to_scipy()
+        assert abs(S - S.T).max() <= 1e-14 * abs(S).max()
+        assert np.diff(A.row_ptr).max() == 7 and A.b == 8
+        uh = sla.spsolve(S.tocsc(), HX.load_vector(m, 1))
+        errs.append(HX.l2_error(m, 1, uh))
+    slope = np.log2(errs[0] / errs[1])
+    assert slope > 1.8, (errs, slope)
