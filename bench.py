@@ -70,6 +70,10 @@ def parse():
                     help="level-0 FP32 sweep with bulk-copy (TMA) staging of A and w D^-1")
     ap.add_argument("--serve-requests", type=int, default=512,
                     help="requests of the serving stream (0: skip the serving measurement)")
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"],
+                    help="c2 (default): the P3 256^2 bench line; c1 / c3 / c4: solves/s of the "
+                         "P1 32^2, LDG Q2 512^2 conv-diff and P2 48^3 tet workloads per precision")
+    ap.add_argument("--peclet", type=float, default=100.0, help="Peclet number of c3")
     return ap.parse_args()
 
 
@@ -207,6 +211,8 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return reference_main(args, rank, world)
+    if args.workload != "c2":
+        return workload_main(args, local) if rank == 0 else 0
     return ours_main(args, rank, world, local)
 
 
@@ -338,6 +344,88 @@ def serve_bench(gasa, n_requests, device=0):
         for c in ctxs:
             gasa.gasa_destroy(c)
     return out
+
+
+def workload_main(args, local):
+    """solves/s, iterations, true residual and error against the FP64 solve
+    (and against the CPU oracle's FP64 solve for c1) of one of the other
+    workloads, per precision: FP64, FP32 V-cycle, FP16-block V-cycle."""
+    import torch
+    from synth import configs
+    from paper_2504_13373_gb300 import gasa
+    gasa.load()
+    torch.cuda.set_device(local)
+    t0 = time.perf_counter()
+    if args.workload == "c1":
+        pr, name = configs.poisson2d_p1(), "poisson2d_sipg_p1_tri_32x32"
+    elif args.workload == "c3":
+        n = 512 if args.n == 256 else args.n
+        pr = configs.convdiff2d_q2(n=n, peclet=args.peclet)
+        name = f"convdiff2d_ldg_q2_quad_{n}x{n}_pe{args.peclet:g}"
+    else:
+        n = 48 if args.n == 256 else args.n
+        pr, name = configs.poisson3d_p2(n=n), f"poisson3d_sipg_p2_tet_{n}cubed"
+    t_gen = time.perf_counter() - t0
+    A = pr.A
+    ctx = gasa.gasa_create(local)
+    opt = gasa.gasa_default_options(dim=pr.dim, n_cand=pr.r, max_iter=20000,
+                                    solver=gasa.GASA_SOLVER_CG if pr.solver == "cg"
+                                    else gasa.GASA_SOLVER_GMRES)
+    sinfo = gasa.gasa_setup(ctx, A.row_ptr, A.col, A.val.ravel(), A.b, pr.agg_of, opt,
+                            adj_ptr=pr.adj_ptr, adj_idx=pr.adj_idx, centroids=pr.centroids,
+                            init_candidates=pr.B0)
+    b = torch.from_numpy(pr.rhs).cuda()
+    x = torch.zeros_like(b)
+    if args.profile_run:
+        # one mixed solve from the host-driven loop (per-kernel ncu launch list)
+        gasa.gasa_profile_enable(ctx, True)
+        gasa.gasa_solve(ctx, b, x, TOL, gasa.GASA_PREC_MIXED32, on_device=True)
+        torch.cuda.synchronize()
+        gasa.gasa_destroy(ctx)
+        return 0
+    ref_oracle = None
+    if args.workload == "c1":
+        from oracle import gasa_oracle as O
+        H = O.setup(A.row_ptr, A.col, A.val, pr.agg_of, B0=pr.B0, r=pr.r, dim=pr.dim)
+        ref_oracle = O.solve(H, pr.rhs, TOL, pr.solver, max_iter=5000).x
+    out, x64 = {}, None
+    for pname, prec in (("fp64", gasa.GASA_PREC_FP64), ("mixed32", gasa.GASA_PREC_MIXED32),
+                        ("mixed16", gasa.GASA_PREC_MIXED16)):
+        for _ in range(args.warmup):
+            gasa.gasa_solve(ctx, b, x, TOL, prec, on_device=True)
+        torch.cuda.synchronize()
+        per, infos = [], []
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            infos.append(gasa.gasa_solve(ctx, b, x, TOL, prec, on_device=True))
+            e1.record()
+            torch.cuda.synchronize()
+            per.append(e0.elapsed_time(e1))
+        xh = x.cpu().numpy()
+        if x64 is None:
+            x64 = xh.copy()
+        rec = {"solves_per_s": 1e3 / float(np.median(per)), "median_ms": float(np.median(per)),
+               "iterations": int(infos[-1].iterations),
+               "rel_residual": float(np.linalg.norm(pr.rhs - A.to_scipy() @ xh) / np.linalg.norm(pr.rhs)),
+               "rel_err_vs_fp64_solve": float(np.linalg.norm(xh - x64) / np.linalg.norm(x64))}
+        if ref_oracle is not None:
+            rec["rel_err_vs_oracle_fp64"] = float(np.linalg.norm(xh - ref_oracle) / np.linalg.norm(ref_oracle))
+        out[pname] = rec
+    gasa.gasa_destroy(ctx)
+    print(json.dumps({
+        "metric": METRIC, "value": out["mixed32"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["mixed32"]["median_ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": name, "dofs": pr.n_dofs, "block": A.b, "nnzb": int(A.nnzb),
+                   "levels": sinfo.n_levels, "candidates": pr.r, "tol": TOL, "solver": pr.solver,
+                   "level_dofs": [int(sinfo.dofs[k]) for k in range(sinfo.n_levels)],
+                   "level_nnzb": [int(sinfo.nnzb[k]) for k in range(sinfo.n_levels)],
+                   "level_block": [int(sinfo.block[k]) for k in range(sinfo.n_levels)]},
+        "precisions": out, "setup_s": sinfo.seconds, "generate_s": t_gen}))
+    return 0
 
 
 def ours_main(args, rank, world, local):

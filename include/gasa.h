@@ -110,6 +110,11 @@ typedef struct {
                                 after setup and are applied as R_{k-1} A_{k-1} P_{k-1}
                                 (Eq. matfree2 with the transfers unrolled); their block
                                 inverses are kept.  0 (default): every A_k stored. */
+  int32_t hstar;             /* 1: one h*-multigrid step at the top (Section 4.3): level 0 and its
+                                elements are duplicated, every element keeps the singular vectors
+                                of its candidate rows above delta * sigma_1 (Eq. sik, h*-branch);
+                                the given hierarchy follows one level lower.  0 (default): off */
+  double delta;              /* h* threshold; 0 = the paper's 1e-3 */
 } gasa_options;
 
 typedef struct {
@@ -180,9 +185,14 @@ enum {
   GASA_LV_CAND = 11,         /* relaxed B^k, dofs x r column-major */
   GASA_LV_SWEEPS = 12,       /* int32 r: Eq. bsmooth sweeps per column */
   GASA_LV_COARSE_INV = 13,   /* coarsest level: dense A_N^{-1}, row-major */
-  GASA_LV_CAND_IN = 14       /* B^k before relaxation */
+  GASA_LV_CAND_IN = 14,      /* B^k before relaxation */
+  GASA_LV_SIZES = 15         /* int32 units: real dofs of each unit */
 };
-/* shape[0..7] = units, s_k, nnzb(A), P nnzb, R nnzb, s_{k+1}, r, dofs */
+/* shape[0..7] = units, s_k, nnzb(A), P nnzb, R nnzb, s_{k+1}, r, dofs.  On a
+ * level whose aggregates keep different counts (h*-step, or unequal
+ * aggregates) every unit is stored padded to s_k; GASA_LV_SIZES gives the
+ * real dofs of each unit (the padding holds zeros, with 1 on the diagonal of
+ * A_k so that the block inverses exist), and dofs counts real dofs only. */
 gasa_status gasa_level_shape(gasa_ctx *ctx, int32_t level, int64_t shape[8]);
 gasa_status gasa_get_level(gasa_ctx *ctx, int32_t level, int32_t what,
                            void *host_out, int64_t n_bytes);

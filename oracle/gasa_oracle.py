@@ -218,6 +218,12 @@ def keep_count(rows: int, r: int, n_cut: float) -> int:
     return int(min(max(1, int(np.floor(rows / n_cut))), r, rows))
 
 
+def hstar_keep(S: np.ndarray, delta: float) -> int:
+    """Eq. sik, h*-multigrid branch (an aggregate that is one element of the
+    level above): the number of singular values above delta * sigma_1."""
+    return max(1, int(np.count_nonzero(S > delta * S[0])))
+
+
 NULL_SIGMA = 1e-10
 
 
@@ -265,8 +271,9 @@ def aggregate_rows(agg: np.ndarray, unit_ptr: np.ndarray, n_agg: int):
 
 
 def tentative(B: np.ndarray, agg: np.ndarray, unit_ptr: np.ndarray, n_agg: int,
-              n_cut: float, keep: Optional[List[int]] = None):
-    """T = blockdiag(U_j[:, :s_j]) with B[A_j, :] = U_j S_j V_j^T.
+              n_cut: float, keep: Optional[List[int]] = None, delta: Optional[float] = None):
+    """T = blockdiag(U_j[:, :s_j]) with B[A_j, :] = U_j S_j V_j^T; s_j by the
+    h-branch of Eq. sik, or by its h*-branch when delta is given.
     Returns (T as csr, next-level unit_ptr, singular values per aggregate)."""
     r = B.shape[1]
     rows = aggregate_rows(agg, unit_ptr, n_agg)
@@ -275,7 +282,12 @@ def tentative(B: np.ndarray, agg: np.ndarray, unit_ptr: np.ndarray, n_agg: int,
     for J in range(n_agg):
         BJ = B[rows[J], :]
         U, S, _ = np.linalg.svd(BJ, full_matrices=False)
-        s = keep_count(len(rows[J]), r, n_cut) if keep is None else keep[J]
+        if keep is not None:
+            s = keep[J]
+        elif delta is not None:
+            s = hstar_keep(S, delta)
+        else:
+            s = keep_count(len(rows[J]), r, n_cut)
         Us.append(sign_fix(complete_null_columns(U, S, s)))
         svals.append(S)
         cols_ptr[J + 1] = cols_ptr[J] + s
@@ -382,8 +394,13 @@ def median_aggregate_dofs(agg1, unit_ptr0, n_agg1):
 
 def setup(row_ptr, col, val, agg_of, B0=None, r=None, dim=2, seed=13373,
           gamma=0.03, q=3, omega_factor=4.0 / 3.0, n_cut=None, max_relax=100,
-          t_pre=3, t_post=3, cand_init="R"):
-    """Alg. 5 with the hierarchy given (levels L0..LN, N = len(agg_of))."""
+          t_pre=3, t_post=3, cand_init="R", hstar=False, delta=1e-3):
+    """Alg. 5 with the hierarchy given (levels L0..LN, N = len(agg_of)).
+    hstar: one h*-multigrid step at the top (Section 4.3): level 0 and its
+    elements are duplicated (every element its own aggregate) and the kept
+    count follows the h*-branch of Eq. sik with threshold delta; the given
+    hierarchy follows, one level lower.  r still comes from the first
+    geometric aggregates."""
     row_ptr = np.asarray(row_ptr, np.int64)
     col = np.asarray(col, np.int64)
     nb = val.shape[1]
@@ -400,6 +417,8 @@ def setup(row_ptr, col, val, agg_of, B0=None, r=None, dim=2, seed=13373,
     if B0 is None:
         raise ValueError("the oracle takes B^0 as an input")
     B = np.array(B0, dtype=np.float64, order="F")[:, :r]
+    if hstar:
+        agg_of = [np.arange(n_units)] + list(agg_of)
     for k, agg in enumerate(agg_of):
         L = levels[k]
         agg = np.asarray(agg, np.int64)
@@ -413,7 +432,8 @@ def setup(row_ptr, col, val, agg_of, B0=None, r=None, dim=2, seed=13373,
         L.B_in = B
         L.B, L.sweeps = relax_candidates(L.A, L.W, B, gamma, max_relax)
         # Eq. splitB_dg + Eq. sik
-        L.T, next_ptr, L.svals = tentative(L.B, agg, L.unit_ptr, n_agg, n_cut)
+        L.T, next_ptr, L.svals = tentative(L.B, agg, L.unit_ptr, n_agg, n_cut,
+                                           delta=delta if (hstar and k == 0) else None)
         # Eq. TR0 and Eq. SA_restrict
         L.P = smoothed_prolongator(L.A, L.W, L.T)
         L.R = L.P.T.tocsr()

@@ -23,8 +23,15 @@ struct DevBSR {
 
 struct Level {
   int n = 0;          // units on this level
-  int s = 0;          // dofs per unit
-  int64_t ndof = 0;
+  int s = 0;          // dofs per unit (stored block size; padded levels pad to it)
+  int64_t ndof = 0;   // n * s
+  // padded level (kept counts of Eq. sik differ between aggregates): unit u
+  // holds usize[u] real dofs followed by zeros
+  bool padded = false;
+  std::vector<int> usize;
+  int *d_usize = nullptr;
+  int64_t *d_uoff = nullptr;     // exclusive prefix sums of usize
+  int64_t real_dofs = 0;
   DevBSR A;
   double *W = nullptr;        // w D^{-1}
   float *W32 = nullptr;

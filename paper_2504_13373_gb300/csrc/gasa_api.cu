@@ -903,8 +903,10 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
   if (opt->t_pre < 0 || opt->t_post < 0 || opt->q_power < 0 || opt->max_relax < 0 ||
       opt->gamma < 0.0 || !(opt->omega_factor > 0.0) || opt->dim < 1 || opt->dim > 3 ||
       opt->solver < GASA_SOLVER_CG || opt->solver > GASA_SOLVER_STATIONARY || opt->max_iter < 1 ||
-      opt->matrix_free_levels < 0)
+      opt->matrix_free_levels < 0 || opt->delta < 0.0 || (opt->hstar && !(opt->delta < 1.0)))
     return fail(ctx, GASA_ERR_INVALID_ARG, "options out of range");
+  if (opt->hstar && hier->n_levels + 1 > GASA_MAX_LEVELS)
+    return fail(ctx, GASA_ERR_INVALID_ARG, "hierarchy: too many levels with the h* step");
   const int n0 = Ain->n_blocks, b0 = Ain->block, nnzb0 = Ain->nnzb;
   if (n0 <= 0 || b0 <= 0 || nnzb0 <= 0 || !Ain->row_ptr || !Ain->col || !Ain->val)
     return fail(ctx, GASA_ERR_INVALID_ARG, "A: null or empty");
@@ -925,13 +927,19 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
     for (int64_t i = 0; i < (int64_t)n0 * opt->dim; ++i)
       if (!std::isfinite(centroids[i])) return fail(ctx, GASA_ERR_INVALID_ARG, "centroids: non-finite");
   }
-  // hierarchy validation and per-level sizes
-  const int N = hier->n_levels - 1;
-  std::vector<int> units(N + 1), sizes(N + 1);
+  // hierarchy validation; with an h*-step the top level is duplicated (every
+  // element its own aggregate, Section 4.3) and the given levels follow
+  const int hs = opt->hstar ? 1 : 0;
+  const int N = hier->n_levels - 1 + hs;
+  std::vector<int32_t> ident(hs ? n0 : 0);
+  for (int i = 0; i < (int)ident.size(); ++i) ident[i] = i;
+  std::vector<const int32_t *> aggs(N);
+  for (int k = 0; k < N; ++k) aggs[k] = (hs && k == 0) ? ident.data() : hier->agg_of[k - hs];
+  std::vector<int> units(N + 1);
   std::vector<std::vector<int>> children_count(N);
   units[0] = n0;
   for (int k = 1; k <= N; ++k) {
-    const int32_t *a = hier->agg_of[k - 1];
+    const int32_t *a = aggs[k - 1];
     if (!a) return fail(ctx, GASA_ERR_INVALID_ARG, "hierarchy: null level");
     int mx = -1;
     for (int i = 0; i < units[k - 1]; ++i) {
@@ -945,38 +953,46 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
       if (children_count[k - 1][J] == 0)
         return fail(ctx, GASA_ERR_INVALID_ARG, "hierarchy: empty aggregate");
   }
-  // candidate count r (Section 4.2: median level-1 aggregate dofs, lower median)
+  // candidate count r (Section 4.2: median level-1 aggregate dofs, lower
+  // median; with the h*-step, of the first geometric aggregates)
   int r = opt->n_cand;
   if (r <= 0) {
-    std::vector<int> d(children_count[0]);
+    std::vector<int> d(children_count[hs]);
     for (auto &v : d) v *= b0;
     std::sort(d.begin(), d.end());
     r = d[(d.size() - 1) / 2];
   }
   if (r > 256) return fail(ctx, GASA_ERR_UNSUPPORTED, "more than 256 candidates");
   const double n_cut = opt->n_cut > 0.0 ? opt->n_cut : (double)((1 << opt->dim) - (opt->dim - 1));
-  sizes[0] = b0;
+  const double delta = opt->delta > 0.0 ? opt->delta : 1e-3;
   std::vector<int> maxch(N);
   for (int k = 0; k < N; ++k) {
-    int sk = -1, mc = 0;
-    for (int J = 0; J < units[k + 1]; ++J) {
-      const int rows = children_count[k][J] * sizes[k];
-      const int sj = keep_count(rows, r, n_cut);
-      if (sk < 0) sk = sj;
-      if (sj != sk)
-        return fail(ctx, GASA_ERR_UNSUPPORTED,
-                    "aggregates of one level keep different counts (Eq. sik); equal counts required");
-      mc = std::max(mc, children_count[k][J]);
-    }
-    sizes[k + 1] = sk;
+    int mc = 0;
+    for (int J = 0; J < units[k + 1]; ++J) mc = std::max(mc, children_count[k][J]);
     maxch[k] = mc;
-    int smem_optin = 0;
-    CU(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
-    if ((size_t)mc * sizes[k] * r * sizeof(double) > (size_t)smem_optin)
-      return fail(ctx, GASA_ERR_UNSUPPORTED, "aggregate x candidates exceed shared memory");
   }
-  if ((int64_t)units[N] * sizes[N] > 16384)
-    return fail(ctx, GASA_ERR_UNSUPPORTED, "coarsest level larger than 16384 dofs");
+  int smem_optin = 0;
+  CU(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+  // block sizes whose aggregates keep h-branch counts are known now; a level
+  // fed by the h*-step learns its sizes from the singular values in the loop
+  {
+    std::vector<int> usz(n0, b0);
+    for (int k = 0; k < N && !(hs && k == 0); ++k) {
+      int smax = 0, sk = 0;
+      std::vector<int> nxt(units[k + 1], 0), rows(units[k + 1], 0);
+      for (int i = 0; i < units[k]; ++i) rows[aggs[k][i]] += usz[i];
+      for (int J = 0; J < units[k + 1]; ++J) {
+        nxt[J] = keep_count(rows[J], r, n_cut);
+        smax = std::max(smax, nxt[J]);
+      }
+      for (int i = 0; i < units[k]; ++i) sk = std::max(sk, usz[i]);
+      if ((size_t)maxch[k] * sk * r * sizeof(double) > (size_t)smem_optin)
+        return fail(ctx, GASA_ERR_UNSUPPORTED, "aggregate x candidates exceed shared memory");
+      usz.swap(nxt);
+      if (k + 1 == N && (int64_t)units[N] * smax > 16384)
+        return fail(ctx, GASA_ERR_UNSUPPORTED, "coarsest level larger than 16384 dofs");
+    }
+  }
 
   free_all(ctx);
   ctx->opt = *opt;
@@ -985,11 +1001,10 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
   ctx->r = r;
   ctx->L.assign(N + 1, Level());
   const bool keep = opt->keep_setup_data != 0;
-  for (int k = 0; k <= N; ++k) {
-    ctx->L[k].n = units[k];
-    ctx->L[k].s = sizes[k];
-    ctx->L[k].ndof = (int64_t)units[k] * sizes[k];
-  }
+  for (int k = 0; k <= N; ++k) ctx->L[k].n = units[k];
+  ctx->L[0].s = b0;
+  ctx->L[0].ndof = (int64_t)n0 * b0;
+  ctx->L[0].real_dofs = ctx->L[0].ndof;
   // level-0 operator
   {
     Level &l = ctx->L[0];
@@ -1031,6 +1046,8 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
     Level &l = ctx->L[k];
     Level &ln = ctx->L[k + 1];
     const int64_t nd = l.ndof;
+    if (nd > ctx->L[0].ndof)
+      return fail(ctx, GASA_ERR_UNSUPPORTED, "a padded level larger than level 0");
     // ---- smoother: block inverses, Alg. 4, Eq. omega ----
     ST(dalloc(ctx, &l.W, (size_t)l.n * l.s * l.s));
     CU(cudaMemsetAsync(dstat, 0, sizeof(int) * 4, s));
@@ -1039,7 +1056,11 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
     CU(cudaMemcpyAsync(&nsing, dstat, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     if (nsing) return fail(ctx, GASA_ERR_SINGULAR_BLOCK, "singular diagonal block on level " + std::to_string(k));
-    CU(launch_uniform_pm1(nd, opt->seed, 4 + 16 * (uint64_t)k, pv, s));
+    if (l.padded)
+      CU(launch_uniform_pm1_padded(l.n, l.s, l.d_usize, l.d_uoff, opt->seed, 4 + 16 * (uint64_t)k,
+                                   pv, s));
+    else
+      CU(launch_uniform_pm1(nd, opt->seed, 4 + 16 * (uint64_t)k, pv, s));
     CU(launch_dot_partials(nd, pv, nullptr, ctx->part, s));
     CU(launch_finalize(ctx->part, 1, ctx->scal + S_TMP, s));
     CU(launch_scale_by_inv_sqrt(nd, pv, ctx->scal + S_TMP, s));
@@ -1121,19 +1142,71 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
       CU(cudaMemcpyAsync(l.cand, B, sizeof(double) * nd * r, cudaMemcpyDeviceToDevice, s));
     }
     // ---- Eq. splitB_dg + Eq. sik: tentative prolongator ----
-    l.n_next = ln.n;
-    l.s_next = ln.s;
     l.max_children = maxch[k];
-    ST(upload_i32(ctx, &l.agg, hier->agg_of[k], l.n));
+    if ((size_t)l.max_children * l.s * r * sizeof(double) > (size_t)smem_optin)
+      return fail(ctx, GASA_ERR_UNSUPPORTED, "aggregate x candidates exceed shared memory");
+    ST(upload_i32(ctx, &l.agg, aggs[k], l.n));
     ST(dalloc(ctx, &l.child_ptr, ln.n + 1));
     ST(dalloc(ctx, &l.child_idx, l.n));
     int *scr = nullptr;
     ST(dalloc(ctx, &scr, ln.n + 1));
     CU(build_children(l.n, ln.n, l.agg, l.child_ptr, l.child_idx, scr, s));
+    // kept counts of the next level's units (Eq. sik): h*-branch from the
+    // singular values of each element's candidate rows, else the h-branch
+    {
+      std::vector<int> kp(ln.n, 0);
+      if (hs && k == 0) {
+        double *sig = nullptr;
+        ST(dalloc(ctx, &sig, (size_t)ln.n * r));
+        CU(launch_tentative(l.s, ln.n, l.max_children, l.child_ptr, l.child_idx, B, nd, r, 0,
+                            nullptr, sig, dstat, s, l.padded ? l.d_usize : nullptr, nullptr));
+        std::vector<double> hs_sig((size_t)ln.n * r);
+        CU(cudaMemcpyAsync(hs_sig.data(), sig, sizeof(double) * hs_sig.size(), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        dfree(ctx, sig);
+        for (int J = 0; J < ln.n; ++J) {
+          const double *sj = hs_sig.data() + (size_t)J * r;
+          int c = 0;
+          for (int q = 0; q < r; ++q) c += sj[q] > delta * sj[0] ? 1 : 0;
+          kp[J] = std::max(1, c);
+        }
+      } else {
+        std::vector<int> rows(ln.n, 0);
+        for (int i = 0; i < l.n; ++i) rows[aggs[k][i]] += l.padded ? l.usize[i] : l.s;
+        for (int J = 0; J < ln.n; ++J) kp[J] = keep_count(rows[J], r, n_cut);
+      }
+      int smax = 0;
+      int64_t real = 0;
+      for (int v : kp) {
+        smax = std::max(smax, v);
+        real += v;
+      }
+      ln.s = smax;
+      ln.ndof = (int64_t)ln.n * smax;
+      ln.real_dofs = real;
+      ln.padded = real != ln.ndof;
+      if (ln.padded) {
+        ln.usize = kp;
+        std::vector<int64_t> off(ln.n);
+        int64_t acc = 0;
+        for (int J = 0; J < ln.n; ++J) {
+          off[J] = acc;
+          acc += kp[J];
+        }
+        ST(upload_i32(ctx, &ln.d_usize, kp.data(), ln.n));
+        ST(dalloc(ctx, &ln.d_uoff, (size_t)ln.n));
+        CU(cudaMemcpyAsync(ln.d_uoff, off.data(), sizeof(int64_t) * ln.n, cudaMemcpyHostToDevice, s));
+      }
+      if (k + 1 == N && ln.ndof > 16384)
+        return fail(ctx, GASA_ERR_UNSUPPORTED, "coarsest level larger than 16384 dofs");
+    }
+    l.n_next = ln.n;
+    l.s_next = ln.s;
     ST(dalloc(ctx, &l.T, (size_t)l.n * l.s * l.s_next));
     CU(cudaMemsetAsync(dstat, 0, sizeof(int) * 4, s));
     CU(launch_tentative(l.s, ln.n, l.max_children, l.child_ptr, l.child_idx, B, nd, r, l.s_next, l.T,
-                        nullptr, dstat, s));
+                        nullptr, dstat, s, l.padded ? l.d_usize : nullptr,
+                        ln.padded ? ln.d_usize : nullptr));
     int tstat = 0;
     CU(cudaMemcpyAsync(&tstat, dstat, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
@@ -1177,6 +1250,8 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
       DevBSR AP;
       ST(spgemm(ctx, l.A, l.P, AP));
       ST(spgemm(ctx, l.R, AP, ln.A));
+      if (ln.padded)
+        CU(launch_pad_identity(ln.n, ln.s, ln.d_usize, ln.A.rp, ln.A.col, ln.A.val, s));
       dfree(ctx, AP.rp);
       dfree(ctx, AP.col);
       dfree(ctx, AP.val);
@@ -1320,7 +1395,7 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
       Level &l = ctx->L[k];
       info->units[k] = l.n;
       info->block[k] = l.s;
-      info->dofs[k] = l.ndof;
+      info->dofs[k] = l.padded ? l.real_dofs : l.ndof;
       info->nnzb[k] = l.A.nnzb;
       info->nnz[k] = l.A.nnzb * l.s * l.s;
       info->omega[k] = l.omega;
@@ -1363,6 +1438,8 @@ void gasa_default_options(gasa_options *opt) {
   opt->init_candidates = nullptr;
   opt->bulk_staging = 0;
   opt->matrix_free_levels = 0;
+  opt->hstar = 0;
+  opt->delta = 1e-3;
 }
 
 gasa_status gasa_create(gasa_ctx **out, int32_t device, void *stream) {
@@ -1471,7 +1548,7 @@ gasa_status gasa_level_shape(gasa_ctx *ctx, int32_t level, int64_t shape[8]) {
   shape[4] = level < ctx->N ? l.R.nnzb : 0;
   shape[5] = level < ctx->N ? l.s_next : 0;
   shape[6] = ctx->r;
-  shape[7] = l.ndof;
+  shape[7] = l.padded ? l.real_dofs : l.ndof;
   return GASA_OK;
 }
 
@@ -1509,6 +1586,12 @@ gasa_status gasa_get_level(gasa_ctx *ctx, int32_t level, int32_t what, void *hos
     case GASA_LV_COARSE_INV:
       if (!fine) { src = ctx->coarse_inv; bytes = 8 * (int64_t)ctx->nc * ctx->nc; }
       break;
+    case GASA_LV_SIZES: {
+      if (n_bytes < 4 * (int64_t)l.n) return fail(ctx, GASA_ERR_INVALID_ARG, "output buffer too small");
+      int32_t *o = static_cast<int32_t *>(host_out);
+      for (int i = 0; i < l.n; ++i) o[i] = l.padded ? l.usize[i] : l.s;
+      return GASA_OK;
+    }
     default: return fail(ctx, GASA_ERR_INVALID_ARG, "unknown level item");
   }
   if (!src) return fail(ctx, GASA_ERR_INVALID_ARG, "item not available on this level (setup data is kept only with options.keep_setup_data; a matrix-free level keeps no A)");

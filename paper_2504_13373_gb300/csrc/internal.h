@@ -75,6 +75,13 @@ cudaError_t launch_scale_by_inv_sqrt(int64_t n, double *x, const double *sumsq, 
 cudaError_t launch_uniform_pm1(int64_t n, uint64_t seed, uint64_t stream, double *x,
                                cudaStream_t s);
 cudaError_t launch_normal(int64_t n, uint64_t seed, uint64_t stream, double *x, cudaStream_t s);
+// uniform(-1,1) draws of the real dofs of a padded level, zero on padding
+cudaError_t launch_uniform_pm1_padded(int n_units, int s_pad, const int *usize,
+                                      const int64_t *uoff, uint64_t seed, uint64_t stream,
+                                      double *x, cudaStream_t s);
+// 1 on the diagonal of a padded level's padding dofs
+cudaError_t launch_pad_identity(int n_units, int s_pad, const int *usize, const int *rp,
+                                const int *col, double *val, cudaStream_t s);
 template <typename Tin, typename Tout>
 cudaError_t launch_convert(int64_t n, const Tin *in, Tout *out, cudaStream_t s);
 cudaError_t launch_fill(int64_t n, double v, double *x, cudaStream_t s);
@@ -118,9 +125,13 @@ cudaError_t launch_block_inverse(int n_units, int bs, const int *rp, const int *
                                  const double *val, double scale, double *W, int *n_singular,
                                  cudaStream_t s);
 cudaError_t launch_scale(int64_t n, double a, double *x, cudaStream_t s);
+// T (padded to s_next columns per aggregate); unit_size (nullable): real dofs
+// of each unit of a padded level; keep (nullable): kept columns per aggregate
+// (default s_next); T may be null with s_next = 0 to compute sigma only
 cudaError_t launch_tentative(int bs, int n_agg, int max_children, const int *child_ptr,
                              const int *child_idx, const double *B, int64_t ldb, int r,
-                             int s_next, double *T, double *sigma, int *status, cudaStream_t s);
+                             int s_next, double *T, double *sigma, int *status, cudaStream_t s,
+                             const int *unit_size = nullptr, const int *keep = nullptr);
 // children lists of aggregates (counting sort of agg_of, stable by unit id)
 cudaError_t build_children(int n_units, int n_agg, const int *agg_of, int *child_ptr,
                            int *child_idx, int *scratch, cudaStream_t s);

@@ -137,6 +137,29 @@ cudaError_t launch_uniform_pm1(int64_t n, uint64_t seed, uint64_t stream, double
   return cudaGetLastError();
 }
 
+// the same vector on a padded level (unit u: usize[u] real dofs, then zeros):
+// real dof number uoff[u] + l gets draw uoff[u] + l, padding gets 0
+__global__ void uniform_pm1_padded_kernel(int n_units, int s, const int *__restrict__ usize,
+                                          const int64_t *__restrict__ uoff, uint64_t key,
+                                          double *x) {
+  pdl_entry();
+  const int64_t n = (int64_t)n_units * s;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int u = (int)(i / s), l = (int)(i - (int64_t)u * s);
+    x[i] = l < usize[u] ? 2.0 * splitmix_uniform(key, (uint64_t)(uoff[u] + l)) - 1.0 : 0.0;
+  }
+}
+
+cudaError_t launch_uniform_pm1_padded(int n_units, int s_pad, const int *usize,
+                                      const int64_t *uoff, uint64_t seed, uint64_t stream,
+                                      double *x, cudaStream_t s) {
+  const uint64_t key = seed ^ (stream * 0x9E3779B97F4A7C15ull);
+  launch_k(uniform_pm1_padded_kernel, kRedBlocks, 256, 0, s, n_units, s_pad, usize, uoff, key, x);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // Box-Muller over pairs of uniforms: u1 = 1 - U[2m], u2 = U[2m+1]
 __global__ void normal_kernel(int64_t n, uint64_t key, double *x) {
   pdl_entry();

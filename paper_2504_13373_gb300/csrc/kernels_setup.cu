@@ -259,14 +259,27 @@ cudaError_t build_children(int n_units, int n_agg, const int *agg_of, int *child
 __global__ void tentative_kernel(int bs, const int *__restrict__ child_ptr,
                                  const int *__restrict__ child_idx, const double *__restrict__ B,
                                  int64_t ldb, int r, int s_next, double *__restrict__ T,
-                                 double *__restrict__ sigma, int *status) {
+                                 double *__restrict__ sigma, int *status,
+                                 const int *__restrict__ unit_size, const int *__restrict__ keep) {
   extern __shared__ double G[];    // rows x r, column-major (ld = rows)
   __shared__ int rotated;
   __shared__ int order[256];
   __shared__ double sv[256];
+  __shared__ int rows_real_s;
   const int J = blockIdx.x;
   const int c0 = child_ptr[J], nch = child_ptr[J + 1] - c0;
   const int rows = nch * bs;
+  // padded levels: unit u holds unit_size[u] real dofs followed by zeros, and
+  // this aggregate keeps keep[J] columns of its s_next (the rest are zero)
+  if (threadIdx.x == 0) {
+    int rr = rows;
+    if (unit_size) {
+      rr = 0;
+      for (int ch = 0; ch < nch; ++ch) rr += unit_size[child_idx[c0 + ch]];
+    }
+    rows_real_s = rr;
+  }
+  const int sJ = keep ? keep[J] : s_next;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   // gather B rows of the aggregate
@@ -277,6 +290,7 @@ __global__ void tentative_kernel(int bs, const int *__restrict__ child_ptr,
     G[e] = B[(size_t)c * ldb + (size_t)unit * bs + d];
   }
   __syncthreads();
+  const int rows_real = rows_real_s;
   const int m = (r + 1) & ~1;        // even number of players (one dummy if r is odd)
   const double tol = 2.220446049250313e-16 * (double)rows;
   for (int sweep = 0; sweep < 60; ++sweep) {
@@ -338,17 +352,17 @@ __global__ void tentative_kernel(int bs, const int *__restrict__ child_ptr,
   __syncthreads();
   if (sigma) {
     for (int l = threadIdx.x; l < r; l += blockDim.x)
-      sigma[(size_t)J * r + l] = (l < rows) ? sv[order[l]] : 0.0;
+      sigma[(size_t)J * r + l] = (l < rows_real) ? sv[order[l]] : 0.0;
   }
   // Singular values at or below kNullSigma * sigma_1 are numerically zero:
   // their vectors carry rounding noise, not candidate information.
   constexpr double kNullSigma = 1e-10;
   const double snull = kNullSigma * sv[order[0]];
   // normalise the kept columns with nonzero singular value
-  for (int l = wid; l < s_next; l += nwarps) {
+  for (int l = wid; l < sJ; l += nwarps) {
     const int c = order[l];
     const double sc = sv[c];
-    if (l < rows && sc > snull) {
+    if (l < rows_real && sc > snull) {
       const double inv = 1.0 / sc;
       double *gc = G + (size_t)c * rows;
       for (int i = lane; i < rows; i += 32) gc[i] *= inv;
@@ -360,13 +374,19 @@ __global__ void tentative_kernel(int bs, const int *__restrict__ child_ptr,
   // orthogonalised twice against the columns already fixed, the first with
   // norm above 1/2 being kept
   if (wid == 0) {
-    for (int l = 0; l < s_next && l < rows; ++l) {
+    for (int l = 0; l < sJ && l < rows_real; ++l) {
       const int c = order[l];
       if (sv[c] > snull) continue;
       double *gc = G + (size_t)c * rows;
       bool done = false;
-      for (int t = 0; t < rows && !done; ++t) {
-        const int e = (l + t) % rows;
+      for (int t = 0; t < rows_real && !done; ++t) {
+        // the (l + t)-th real row, in the aggregate's padded row numbering
+        int e = (l + t) % rows_real;
+        if (unit_size) {
+          int ch = 0;
+          while (e >= unit_size[child_idx[c0 + ch]]) e -= unit_size[child_idx[c0 + ch++]];
+          e += ch * bs;
+        }
         for (int i = lane; i < rows; i += 32) gc[i] = (i == e) ? 1.0 : 0.0;
         __syncwarp();
         for (int pass = 0; pass < 2; ++pass) {
@@ -397,8 +417,15 @@ __global__ void tentative_kernel(int bs, const int *__restrict__ child_ptr,
   __syncthreads();
   // sign so that the largest |entry| (lowest row on ties) is positive, then write
   for (int l = wid; l < s_next; l += nwarps) {
+    if (l >= sJ) {   // padding column of this aggregate
+      for (int i = lane; i < rows; i += 32) {
+        const int ch = i / bs, d = i - ch * bs;
+        T[((size_t)child_idx[c0 + ch] * bs + d) * s_next + l] = 0.0;
+      }
+      continue;
+    }
     const int c = order[l];
-    const bool ok = (l < rows);
+    const bool ok = (l < rows_real);
     double best = -1.0;
     int bi = INT_MAX;
     const double *gc = G + (size_t)c * rows;
@@ -423,11 +450,34 @@ __global__ void tentative_kernel(int bs, const int *__restrict__ child_ptr,
   }
 }
 
+// Padded level: the Galerkin product leaves the padding rows and columns of
+// A zero; put 1 on their diagonal so that the block inverses exist.  The
+// padding then stays exactly zero through every smoothing step.
+__global__ void pad_identity_kernel(int n_units, int s, const int *__restrict__ usize,
+                                    const int *__restrict__ rp, const int *__restrict__ col,
+                                    double *__restrict__ val) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_units) return;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) {
+    if (col[k] != i) continue;
+    double *d = val + (size_t)k * s * s;
+    for (int l = usize[i]; l < s; ++l) d[(size_t)l * s + l] = 1.0;
+  }
+}
+
+cudaError_t launch_pad_identity(int n_units, int s_pad, const int *usize, const int *rp,
+                                const int *col, double *val, cudaStream_t s) {
+  if (n_units == 0) return cudaSuccess;
+  pad_identity_kernel<<<div_up(n_units, 128), 128, 0, s>>>(n_units, s_pad, usize, rp, col, val);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // shared memory holds the largest aggregate's rows x r block of B
 cudaError_t launch_tentative(int bs, int n_agg, int max_children, const int *child_ptr,
                                    const int *child_idx, const double *B, int64_t ldb, int r,
                                    int s_next, double *T, double *sigma, int *status,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, const int *unit_size, const int *keep) {
   if (n_agg == 0) return cudaSuccess;
   const size_t sm = (size_t)max_children * bs * r * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(tentative_kernel,
@@ -436,7 +486,7 @@ cudaError_t launch_tentative(int bs, int n_agg, int max_children, const int *chi
   int pairs = (r + 1) / 2;
   int th = 32 * (pairs < 8 ? (pairs < 1 ? 1 : pairs) : 8);
   tentative_kernel<<<n_agg, th, sm, s>>>(bs, child_ptr, child_idx, B, ldb, r, s_next, T, sigma,
-                                         status); note_launch();
+                                         status, unit_size, keep); note_launch();
   return cudaGetLastError();
 }
 

@@ -36,7 +36,7 @@ GASA_MAX_LEVELS = 24
 
 (GASA_LV_A_ROWPTR, GASA_LV_A_COL, GASA_LV_A_VAL, GASA_LV_P_ROWPTR, GASA_LV_P_COL, GASA_LV_P_VAL,
  GASA_LV_R_ROWPTR, GASA_LV_R_COL, GASA_LV_R_VAL, GASA_LV_T_VAL, GASA_LV_W, GASA_LV_CAND,
- GASA_LV_SWEEPS, GASA_LV_COARSE_INV, GASA_LV_CAND_IN) = range(15)
+ GASA_LV_SWEEPS, GASA_LV_COARSE_INV, GASA_LV_CAND_IN, GASA_LV_SIZES) = range(16)
 
 # every symbol include/gasa.h declares
 EXPORTS = [
@@ -69,7 +69,8 @@ class gasa_options(ctypes.Structure):
                 ("max_relax", c_i32), ("max_iter", c_i32), ("cand_init", c_i32),
                 ("keep_setup_data", c_i32), ("gamma", c_dbl), ("omega_factor", c_dbl),
                 ("n_cut", c_dbl), ("seed", ctypes.c_uint64), ("init_candidates", c_vp),
-                ("bulk_staging", c_i32), ("matrix_free_levels", c_i32)]
+                ("bulk_staging", c_i32), ("matrix_free_levels", c_i32), ("hstar", c_i32),
+                ("delta", c_dbl)]
 
 
 class gasa_setup_info(ctypes.Structure):

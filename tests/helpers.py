@@ -32,6 +32,12 @@ def problem(name: str):
         return configs.convdiff2d_q2(n=32, peclet=1e4)
     if name == "cd_q2_32_pe1":
         return configs.convdiff2d_q2(n=32, peclet=1.0)
+    if name == "uneq6":
+        # 72 triangles: level-2 aggregates hold 4, 4, 4, 4 and 2 units, so their
+        # kept counts differ and level 2 is stored padded
+        return configs.poisson2d(6, 1, r=12, n_levels=3, name="uneq6")
+    if name == "p2_8":
+        return configs.poisson2d(8, 2, r=24, n_levels=3, name="p2_8")
     if name.startswith("hex_M"):
         return configs.poisson3d_hex(int(name[5:]))
     if name.startswith("cd3_"):

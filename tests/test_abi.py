@@ -56,6 +56,7 @@ int main(void) {
   printf("gasa_server_stats %zu\n", sizeof(gasa_server_stats));
   P(gasa_options, gamma); P(gasa_options, seed); P(gasa_options, init_candidates);
   P(gasa_options, bulk_staging); P(gasa_options, matrix_free_levels);
+  P(gasa_options, hstar); P(gasa_options, delta);
   P(gasa_setup_info, omega); P(gasa_setup_info, seconds); P(gasa_setup_info, device_bytes);
   P(gasa_bsr, val); P(gasa_bsr, on_device); P(gasa_solve_info, rel_residual);
   P(gasa_server_stats, peak_running); P(gasa_server_stats, graph_launches);
@@ -84,6 +85,8 @@ def test_struct_layouts_match_c(tmp_path):
         "gasa_options.init_candidates": gasa.gasa_options.init_candidates.offset,
         "gasa_options.bulk_staging": gasa.gasa_options.bulk_staging.offset,
         "gasa_options.matrix_free_levels": gasa.gasa_options.matrix_free_levels.offset,
+        "gasa_options.hstar": gasa.gasa_options.hstar.offset,
+        "gasa_options.delta": gasa.gasa_options.delta.offset,
         "gasa_setup_info.omega": gasa.gasa_setup_info.omega.offset,
         "gasa_setup_info.seconds": gasa.gasa_setup_info.seconds.offset,
         "gasa_setup_info.device_bytes": gasa.gasa_setup_info.device_bytes.offset,

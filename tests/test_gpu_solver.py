@@ -36,8 +36,8 @@ def level_tolerances(H, base=1e-8):
         tol.append(worst)
         if L.svals is None:
             continue
-        s = int(np.diff(H.levels[k + 1].unit_ptr)[0])
-        for sv in L.svals:
+        kept = np.diff(H.levels[k + 1].unit_ptr)
+        for sv, s in zip(L.svals, kept):
             if s < sv.size and sv[s - 1] > 1e-10 * sv[0]:
                 gap = (sv[s - 1] - sv[s]) / sv[0]
                 worst = max(worst, 100 * 2.2e-16 / max(gap, 1e-300))
@@ -351,3 +351,92 @@ def test_paper_hex_poisson():
         finally:
             gasa.gasa_destroy(ctx)
     assert 3 <= ref_cg.iterations <= 13
+
+
+def _real_index(sizes, s):
+    """dof numbers of the real (unpadded) dofs of a level stored with s per unit"""
+    return np.concatenate([i * s + np.arange(z) for i, z in enumerate(sizes)])
+
+
+@pytest.mark.parametrize("name,hstar", [("p2_8", True), ("c1", True), ("uneq6", False)])
+def test_padded_levels(name, hstar):
+    """Unequal kept counts on a level, stored padded.  With the Section 4.3
+    h*-step at the top every element is its own aggregate and keeps the
+    singular vectors above 1e-3 sigma_1 (block sizes differ between units for
+    p2_8); without it, aggregates of unequal size keep unequal h-branch
+    counts (uneq6).  Kept counts bit-exact; unpadded A_k, w D^-1, P match the
+    oracle; the padding holds zeros with 1 on A's diagonal; V-cycle, CG and
+    served solves match."""
+    gasa = _gasa()
+    pr = problem(name)
+    H = O.setup(pr.A.row_ptr, pr.A.col, pr.A.val, pr.agg_of, B0=pr.B0, r=pr.r, dim=pr.dim,
+                hstar=hstar)
+    ctx, info = gpu_setup(name, keep=True, hstar=1 if hstar else 0)
+    tol = level_tolerances(H)
+    try:
+        assert info.n_levels == len(H.levels) == len(pr.agg_of) + 1 + (1 if hstar else 0)
+        padded_seen = False
+        for k, L in enumerate(H.levels):
+            sh = gasa.gasa_level_shape(ctx, k)
+            sizes = gasa.gasa_get_level(ctx, k, gasa.GASA_LV_SIZES, np.zeros(sh["units"], np.int32))
+            np.testing.assert_array_equal(sizes, np.diff(L.unit_ptr))
+            assert sh["dofs"] == L.n == info.dofs[k]
+            padded_seen |= bool(np.any(sizes != sh["s"]))
+            idx = _real_index(sizes, sh["s"])
+            rp, col, val = _level_bsr(gasa, ctx, k, "A", sh, sh["s"], sh["s"], sh["units"])
+            Afull = bsr_scipy(rp, col, val)
+            assert sparse_rel(Afull[idx][:, idx], L.A) <= tol[k]
+            pad = np.setdiff1d(np.arange(sh["units"] * sh["s"]), idx)
+            if pad.size:
+                Ap = Afull[pad][:, pad].toarray()
+                assert np.array_equal(Ap, np.eye(pad.size))
+                assert abs(Afull[pad][:, idx]).max() == 0.0
+            if k == len(H.levels) - 1:
+                n_all = sh["units"] * sh["s"]
+                Ci = gasa.gasa_get_level(ctx, k, gasa.GASA_LV_COARSE_INV,
+                                         np.zeros(n_all * n_all)).reshape(n_all, n_all)
+                assert rel_err(Ci[np.ix_(idx, idx)], np.linalg.inv(H.coarse)) <= 100 * tol[k]
+                continue
+            assert abs(info.omega[k] - L.omega) <= 1e-2 * tol[k] * L.omega
+            W = gasa.gasa_get_level(ctx, k, gasa.GASA_LV_W,
+                                    np.zeros(sh["units"] * sh["s"] ** 2)).reshape(-1, sh["s"], sh["s"])
+            Wref = L.W.blocks if L.W.uniform else L.W.blocks
+            for i in range(sh["units"]):
+                z = sizes[i]
+                assert rel_err(W[i, :z, :z], Wref[i]) <= tol[k]
+            sn = sh["s_next"]
+            n_next = H.levels[k + 1].unit_ptr.size - 1
+            nsz = gasa.gasa_get_level(ctx, k + 1, gasa.GASA_LV_SIZES, np.zeros(n_next, np.int32))
+            idx_n = _real_index(nsz, sn)
+            prp, pcol, pval = _level_bsr(gasa, ctx, k, "P", sh, sh["s"], sn, sh["units"])
+            Pg = bsr_scipy(prp, pcol, pval, n_next)
+            assert sparse_rel(Pg[idx][:, idx_n], L.P) <= tol[k + 1]
+            pad_n = np.setdiff1d(np.arange(n_next * sn), idx_n)
+            if pad_n.size:
+                assert abs(Pg[:, pad_n]).max() == 0.0
+        if name in ("p2_8", "uneq6"):
+            assert padded_seen
+        want = O.make_vcycle(H)(pr.rhs)
+        z = to_dev(np.zeros_like(pr.rhs))
+        gasa.gasa_vcycle(ctx, to_dev(pr.rhs), z)
+        assert rel_err(to_host(z), want) <= 0.1 * tol[-1]
+        ref = O.solve(H, pr.rhs, TOL, "cg", max_iter=5000)
+        x = np.zeros_like(pr.rhs)
+        inf = gasa.gasa_solve(ctx, pr.rhs, x, TOL)
+        assert inf.converged and abs(inf.iterations - ref.iterations) <= 1
+        assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= TOL
+        ref32 = O.solve(H, pr.rhs, TOL, "cg", precision="mixed32", max_iter=5000)
+        inf32 = gasa.gasa_solve(ctx, pr.rhs, x, TOL, gasa.GASA_PREC_MIXED32)
+        assert inf32.converged and abs(inf32.iterations - ref32.iterations) <= 1
+        srv = gasa.gasa_server_create(0, 8 << 30, 2)
+        try:
+            t = gasa.gasa_server_submit(srv, gasa.gasa_server_add_mesh(srv, ctx), pr.rhs, TOL)
+            gasa.gasa_server_drain(srv, 300.0)
+            xs = np.zeros_like(pr.rhs)
+            st, si = gasa.gasa_server_poll(srv, t, xs)
+            assert st == gasa.GASA_OK and abs(si.iterations - ref.iterations) <= 1
+            assert np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x) <= TOL
+        finally:
+            gasa.gasa_server_destroy(srv)
+    finally:
+        gasa.gasa_destroy(ctx)

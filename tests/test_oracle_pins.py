@@ -401,3 +401,35 @@ def test_matrix_free_levels_apply_the_galerkin_operator():
         assert np.linalg.norm(u - u0) <= 1e-11 * np.linalg.norm(u0)
     # with kappa = 0 nothing changes, bit for bit
     assert np.array_equal(O.make_vcycle(H, matrix_free_levels=0)(f), u0)
+
+
+def test_hstar_keep_rule():
+    """Eq. sik, h*-branch: keep the singular values above delta sigma_1."""
+    U, _ = np.linalg.qr(np.random.default_rng(3).standard_normal((10, 4)))
+    V, _ = np.linalg.qr(np.random.default_rng(4).standard_normal((6, 4)))
+    for sv, want in (([1.0, 0.5, 1e-4, 1e-9], 2), ([1.0, 0.9, 0.8, 0.7], 4), ([2.0, 1e-5, 0, 0], 1)):
+        B = U @ np.diag(sv) @ V.T
+        S = np.linalg.svd(B, compute_uv=False)
+        assert O.hstar_keep(S, 1e-3) == want
+
+
+def test_hstar_top_level():
+    """Section 4.3: with an h*-step the first coarse level has one unit per
+    element, each keeping the singular vectors above 1e-3 sigma_1 of its own
+    candidate rows (so the level-1 block sizes vary), T is an isometry, the
+    remaining levels follow the given aggregates, and the preconditioned CG
+    still converges."""
+    pr = configs.poisson2d(8, 2, r=24, n_levels=3, name="tiny_p2")
+    H = O.setup(pr.A.row_ptr, pr.A.col, pr.A.val, pr.agg_of, B0=pr.B0, r=pr.r, dim=2, hstar=True)
+    assert len(H.levels) == len(pr.agg_of) + 2
+    L0, L1 = H.levels[0], H.levels[1]
+    assert L1.unit_ptr.size == L0.unit_ptr.size
+    sizes = np.diff(L1.unit_ptr)
+    for J, S in enumerate(L0.svals):
+        assert sizes[J] == O.hstar_keep(S, 1e-3)
+    assert sizes.max() <= pr.A.b and sizes.min() >= 1
+    TT = (L0.T.T @ L0.T).toarray()
+    assert np.abs(TT - np.eye(TT.shape[0])).max() <= 1e-12
+    assert H.levels[2].unit_ptr.size - 1 == int(pr.agg_of[0].max()) + 1
+    res = O.solve(H, pr.rhs, 1e-10, "cg", max_iter=500)
+    assert res.converged
