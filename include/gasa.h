@@ -115,6 +115,12 @@ typedef struct {
                                 of its candidate rows above delta * sigma_1 (Eq. sik, h*-branch);
                                 the given hierarchy follows one level lower.  0 (default): off */
   double delta;              /* h* threshold; 0 = the paper's 1e-3 */
+  int32_t tail_kib;          /* levels k >= 1 whose operator A_k takes at most this many KiB in
+                                the V-cycle's precision, together with every coarser level and
+                                the coarsest solve, run as one thread-block-cluster launch
+                                (kernels_tail.cu) instead of one launch per step; same
+                                arithmetic per row, so results agree with the per-step
+                                launches to rounding.  0 (default): one launch per step. */
 } gasa_options;
 
 typedef struct {
@@ -194,6 +200,13 @@ enum {
  * real dofs of each unit (the padding holds zeros, with 1 on the diagonal of
  * A_k so that the block inverses exist), and dofs counts real dofs only. */
 gasa_status gasa_level_shape(gasa_ctx *ctx, int32_t level, int64_t shape[8]);
+
+/* Fused bottom of the V-cycle (option tail_kib) of one precision: out[0] =
+ * first level k0 run inside the cluster launch (n_levels - 1 when every
+ * level runs as its own launches), out[1] = CTAs per cluster (0 when
+ * unfused), out[2] = 1 when the coarsest solve runs inside the launch.
+ * GASA_PREC_MIXED16 reports the FP32 tail it shares with MIXED32. */
+gasa_status gasa_tail_info(gasa_ctx *ctx, int32_t precision, int32_t out[3]);
 gasa_status gasa_get_level(gasa_ctx *ctx, int32_t level, int32_t what,
                            void *host_out, int64_t n_bytes);
 

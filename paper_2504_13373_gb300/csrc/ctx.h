@@ -103,6 +103,13 @@ struct gasa_ctx {
   int cg_max_iter[6] = {};
   int *d_iters = nullptr;
   int *d_err = nullptr;          // set by kernels whose bounded waits time out
+  // fused bottom of the V-cycle per precision (0: FP64, 1: FP32): levels
+  // tail_k0[p] .. N-1 and the coarsest solve run in one cluster launch
+  // (kernels_tail.cu); no plan: every step is its own launch
+  void *tail_plan[2] = {};
+  int tail_k0[2] = {0, 0};
+  int tail_coarse[2] = {0, 0};   // 1: the coarsest solve runs inside the launch
+  int tail_cluster[2] = {0, 0};  // CTAs per cluster
   // profiling
   bool prof = false;
   ProfClass pc[4];

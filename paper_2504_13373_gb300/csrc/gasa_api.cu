@@ -15,6 +15,7 @@
 #include "gasa.h"
 #include "internal.h"
 #include "ctx.h"
+#include "tail.h"
 
 using namespace gasa;
 
@@ -98,6 +99,10 @@ void free_all(gasa_ctx *ctx) {
   ctx->ready = false;
   ctx->device_bytes = 0;
   ctx->coarse_inv = nullptr;
+  for (int p = 0; p < 2; ++p) {
+    ctx->tail_plan[p] = nullptr;
+    ctx->tail_k0[p] = 0;
+  }
   ctx->V = ctx->Z = ctx->H = ctx->gm = ctx->mpart = nullptr;
   ctx->gm_restart = 0;
 }
@@ -192,11 +197,90 @@ double spmv_bytes(const Level &l, int w, bool residual, int wa = 0) {
   return Ab + (residual ? 3.0 : 2.0) * vec;
 }
 
+// Plan of the fused bottom of the V-cycle for precision T (slot pi: 0 FP64,
+// 1 FP32): the deepest run of levels k >= 1 whose A_k is stored and takes at
+// most opt.tail_kib KiB, with every level below it down to the coarsest.
+template <typename T>
+gasa_status tail_build(gasa_ctx *ctx, int pi) {
+  using P = Prec<T>;
+  const int N = ctx->N;
+  ctx->tail_k0[pi] = N;
+  ctx->tail_plan[pi] = nullptr;
+  const int64_t limit = (int64_t)ctx->opt.tail_kib * 1024;
+  if (limit <= 0 || N < 2) return GASA_OK;
+  int k0 = N;
+  for (int k = N - 1; k >= 1; --k) {
+    Level &l = ctx->L[k];
+    if (l.mf || l.tma || l.s > 64 || l.R.br > 64) break;
+    if (l.P.nrows != l.n || l.P.br != l.s || l.P.bc != l.R.br || l.R.bc != l.s ||
+        l.R.nrows != ctx->L[k + 1].n || l.R.br != ctx->L[k + 1].s)
+      break;
+    if (l.A.nnzb * l.s * l.s * (int64_t)sizeof(T) > limit) break;
+    k0 = k;
+  }
+  if (k0 == N) return GASA_OK;
+  const int cl = tail_cluster_size<T>();
+  if (cl == 0) return GASA_OK;
+  TailPlan<T> h;
+  h.k0 = k0;
+  h.nlev = N - k0;
+  h.tpre = ctx->opt.t_pre;
+  h.tpost = ctx->opt.t_post;
+  h.nc = ctx->nc;
+  // the coarsest inverse joins the launch while it is small (2 MB)
+  const bool coarse_in = (int64_t)ctx->nc * ctx->nc * 8 <= (2 << 20);
+  h.Cinv = coarse_in ? ctx->coarse_inv : nullptr;
+  h.bN = P::b(ctx->L[N]);
+  h.xN = P::x(ctx->L[N]);
+  bool al = true;
+  auto chk = [&](const void *p) {
+    if (p && ((uintptr_t)p & 15u)) al = false;
+  };
+  for (int q = 0; q < h.nlev; ++q) {
+    Level &l = ctx->L[k0 + q];
+    TailLevel<T> &t = h.lv[q];
+    t.n = l.n;
+    t.s = l.s;
+    t.n_next = l.R.nrows;
+    t.s_next = l.R.br;
+    t.rp = l.A.rp;
+    t.col = l.A.col;
+    t.A = P::A(l.A);
+    t.W = P::W(l);
+    t.Prp = l.P.rp;
+    t.Pcol = l.P.col;
+    t.P = P::A(l.P);
+    t.Rrp = l.R.rp;
+    t.Rcol = l.R.col;
+    t.R = P::A(l.R);
+    t.x = P::x(l);
+    t.x2 = P::x2(l);
+    t.b = P::b(l);
+    t.r = P::r(l);
+    for (const void *p : {(const void *)t.A, (const void *)t.P, (const void *)t.R,
+                          (const void *)t.x, (const void *)t.x2, (const void *)t.r})
+      chk(p);
+  }
+  chk(h.xN);
+  h.vec = al ? 1 : 0;
+  unsigned char *d = nullptr;
+  ST(dalloc(ctx, &d, sizeof(TailPlan<T>)));
+  CU(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  ctx->tail_plan[pi] = d;
+  ctx->tail_k0[pi] = k0;
+  ctx->tail_coarse[pi] = coarse_in ? 1 : 0;
+  ctx->tail_cluster[pi] = cl;
+  return GASA_OK;
+}
+
 template <typename T>
 gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false) {
   using P = Prec<T>;
   cudaStream_t s = ctx->stream;
   const int N = ctx->N;
+  const int pi = std::is_same<T, float>::value ? 1 : 0;
+  const int kt = ctx->tail_plan[pi] ? ctx->tail_k0[pi] : N;   // first fused level
   const int tpre = ctx->opt.t_pre, tpost = ctx->opt.t_post;
   const int w = (int)sizeof(T);
   // level-0 smoothing step and residual; with h16 (FP32 V-cycle only) the
@@ -240,7 +324,7 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false) {
   std::vector<T *> xk(N + 1);
   bk[0] = rhs;
   for (int k = 1; k <= N; ++k) bk[k] = P::b(ctx->L[k]);
-  for (int k = 0; k < N; ++k) {
+  for (int k = 0; k < kt; ++k) {
     Level &l = ctx->L[k];
     T *x = P::x(l), *x2 = P::x2(l);
     // pre-smoothing from zero
@@ -269,11 +353,27 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false) {
     CU(launch_bsr_mv<T>(GASA_MV_ASSIGN, l.R.nrows, l.R.br, l.R.bc, l.R.rp, l.R.col, P::A(l.R),
                         P::r(l), nullptr, P::b(ctx->L[k + 1]), s, l.R.nnzb));
   }
-  // coarsest solve in FP64
   Level &lc = ctx->L[N];
-  CU(launch_dense_mv<T>(ctx->nc, ctx->coarse_inv, P::b(lc), P::x(lc), s));
-  xk[N] = P::x(lc);
-  for (int k = N - 1; k >= 0; --k) {
+  if (kt < N) {
+    // levels kt .. N-1 and the coarsest solve (FP64 arithmetic) in one
+    // cluster launch, or two around a whole-GPU coarsest solve
+    const TailPlan<T> *pl = static_cast<const TailPlan<T> *>(ctx->tail_plan[pi]);
+    const int cl = ctx->tail_cluster[pi];
+    if (ctx->tail_coarse[pi]) {
+      CU(launch_vcycle_tail<T>(pl, TAIL_ALL, cl, s));
+    } else {
+      CU(launch_vcycle_tail<T>(pl, TAIL_DOWN, cl, s));
+      CU(launch_dense_mv<T>(ctx->nc, ctx->coarse_inv, P::b(lc), P::x(lc), s));
+      CU(launch_vcycle_tail<T>(pl, TAIL_UP, cl, s));
+    }
+    Level &lt = ctx->L[kt];
+    xk[kt] = tail_final_buffer(ctx->opt.t_pre, ctx->opt.t_post) ? P::x2(lt) : P::x(lt);
+  } else {
+    // coarsest solve in FP64
+    CU(launch_dense_mv<T>(ctx->nc, ctx->coarse_inv, P::b(lc), P::x(lc), s));
+    xk[N] = P::x(lc);
+  }
+  for (int k = kt - 1; k >= 0; --k) {
     Level &l = ctx->L[k];
     T *x = xk[k];
     T *x2 = (x == P::x(l)) ? P::x2(l) : P::x(l);
@@ -1383,6 +1483,8 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
     l.tma = tma_plan(l.n, l.s, (int)sizeof(float), maxrow, &l.tma_TR, &l.tma_stageA,
                      &l.tma_stageW, &l.tma_smem, &l.tma_grid);
   }
+  ST(tail_build<double>(ctx, 0));
+  ST(tail_build<float>(ctx, 1));
   CU(cudaStreamSynchronize(s));
   ctx->ready = true;
   ctx->setup_seconds =
@@ -1440,6 +1542,7 @@ void gasa_default_options(gasa_options *opt) {
   opt->matrix_free_levels = 0;
   opt->hstar = 0;
   opt->delta = 1e-3;
+  opt->tail_kib = 0;
 }
 
 gasa_status gasa_create(gasa_ctx **out, int32_t device, void *stream) {
@@ -1549,6 +1652,19 @@ gasa_status gasa_level_shape(gasa_ctx *ctx, int32_t level, int64_t shape[8]) {
   shape[5] = level < ctx->N ? l.s_next : 0;
   shape[6] = ctx->r;
   shape[7] = l.padded ? l.real_dofs : l.ndof;
+  return GASA_OK;
+}
+
+gasa_status gasa_tail_info(gasa_ctx *ctx, int32_t precision, int32_t out[3]) {
+  if (!ctx || !out) return GASA_ERR_INVALID_ARG;
+  if (!ctx->ready) return fail(ctx, GASA_ERR_STATE, "no hierarchy");
+  if (precision < GASA_PREC_FP64 || precision > GASA_PREC_MIXED16)
+    return fail(ctx, GASA_ERR_INVALID_ARG, "unknown precision");
+  const int pi = precision == GASA_PREC_FP64 ? 0 : 1;
+  const bool on = ctx->tail_plan[pi] != nullptr;
+  out[0] = on ? ctx->tail_k0[pi] : ctx->N;
+  out[1] = on ? ctx->tail_cluster[pi] : 0;
+  out[2] = on ? ctx->tail_coarse[pi] : 0;
   return GASA_OK;
 }
 

@@ -41,7 +41,7 @@ GASA_MAX_LEVELS = 24
 # every symbol include/gasa.h declares
 EXPORTS = [
     "gasa_default_options", "gasa_create", "gasa_setup", "gasa_solve", "gasa_vcycle",
-    "gasa_level_shape", "gasa_get_level", "gasa_profile_enable", "gasa_profile_read",
+    "gasa_level_shape", "gasa_tail_info", "gasa_get_level", "gasa_profile_enable", "gasa_profile_read",
     "gasa_destroy", "gasa_status_string", "gasa_last_error", "gasa_bsr_mv", "gasa_bsr_mv_f32",
     "gasa_jacobi_sweep", "gasa_jacobi_sweep_f32", "gasa_block_inverse", "gasa_power_estimate",
     "gasa_relax_candidates", "gasa_tentative", "gasa_dense_inverse", "gasa_kernel_launches",
@@ -70,7 +70,7 @@ class gasa_options(ctypes.Structure):
                 ("keep_setup_data", c_i32), ("gamma", c_dbl), ("omega_factor", c_dbl),
                 ("n_cut", c_dbl), ("seed", ctypes.c_uint64), ("init_candidates", c_vp),
                 ("bulk_staging", c_i32), ("matrix_free_levels", c_i32), ("hstar", c_i32),
-                ("delta", c_dbl)]
+                ("delta", c_dbl), ("tail_kib", c_i32)]
 
 
 class gasa_setup_info(ctypes.Structure):
@@ -235,6 +235,12 @@ def gasa_level_shape(ctx, level):
     _check(load().gasa_level_shape(ctx, c_i32(level), sh), ctx)
     keys = ["units", "s", "nnzb", "P_nnzb", "R_nnzb", "s_next", "r", "dofs"]
     return dict(zip(keys, [int(v) for v in sh]))
+
+
+def gasa_tail_info(ctx, precision):
+    out = (c_i32 * 3)()
+    _check(load().gasa_tail_info(ctx, c_i32(precision), out), ctx)
+    return {"first_level": int(out[0]), "cluster": int(out[1]), "coarse_inside": int(out[2])}
 
 
 def gasa_get_level(ctx, level, what, out: np.ndarray):

@@ -440,3 +440,49 @@ def test_padded_levels(name, hstar):
             gasa.gasa_server_destroy(srv)
     finally:
         gasa.gasa_destroy(ctx)
+
+
+@pytest.mark.parametrize("name", ["c1", "p3_32", "cd_q2_16", "tet_p2_6", "uneq6"])
+def test_fused_tail(name):
+    """Levels 1..N-1 and the coarsest solve run as one thread-block-cluster
+    launch (tail_kib large) or as one launch per step (tail_kib = 0).  Both
+    compute the V-cycle of Alg. 2 with the same sum per output row, so the
+    two agree to rounding, both follow the oracle's V-cycle, and the solves
+    they drive take the same number of iterations (+-1)."""
+    gasa = _gasa()
+    H = oracle_setup(name)
+    pr = problem(name)
+    n_levels = len(H.levels)
+    ctx_f, _ = gpu_setup(name, keep=False, tail_kib=1 << 20)
+    ctx_s, _ = gpu_setup(name, keep=False, tail_kib=0)
+    try:
+        for prec, oprec, tol in ((gasa.GASA_PREC_FP64, "fp64", 1e-12),
+                                 (gasa.GASA_PREC_MIXED32, "fp32", 1e-5)):
+            tf = gasa.gasa_tail_info(ctx_f, prec)
+            assert tf["first_level"] == 1 and tf["cluster"] in (8, 16), tf
+            assert tf["coarse_inside"] == 1
+            assert gasa.gasa_tail_info(ctx_s, prec) == {"first_level": n_levels - 1, "cluster": 0,
+                                                        "coarse_inside": 0}
+            want = O.make_vcycle(H, oprec)(pr.rhs)
+            r = to_dev(pr.rhs)
+            zf, zs = to_dev(np.zeros_like(pr.rhs)), to_dev(np.zeros_like(pr.rhs))
+            gasa.gasa_vcycle(ctx_f, r, zf, prec)
+            gasa.gasa_vcycle(ctx_s, r, zs, prec)
+            zf, zs = to_host(zf), to_host(zs)
+            assert rel_err(zf, zs) <= tol
+            assert rel_err(zf, want) <= max(tol, 0.1 * level_tolerances(H)[-1])
+            # a second call on the same buffers gives the same bits
+            z2 = to_dev(np.zeros_like(pr.rhs))
+            gasa.gasa_vcycle(ctx_f, r, z2, prec)
+            assert np.array_equal(to_host(z2), zf)
+        if pr.solver == "cg":
+            for prec in (gasa.GASA_PREC_FP64, gasa.GASA_PREC_MIXED32):
+                xf, xs = np.zeros_like(pr.rhs), np.zeros_like(pr.rhs)
+                inf_f = gasa.gasa_solve(ctx_f, pr.rhs, xf, TOL, prec)
+                inf_s = gasa.gasa_solve(ctx_s, pr.rhs, xs, TOL, prec)
+                assert inf_f.converged and inf_f.rel_residual <= TOL
+                assert abs(inf_f.iterations - inf_s.iterations) <= 1
+                assert np.linalg.norm(xf - xs) / np.linalg.norm(xs) <= 10 * TOL
+    finally:
+        gasa.gasa_destroy(ctx_f)
+        gasa.gasa_destroy(ctx_s)
