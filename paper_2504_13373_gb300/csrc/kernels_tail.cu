@@ -41,6 +41,7 @@ __device__ __forceinline__ unsigned cl_size() {
 // Every thread of every CTA of the cluster arrives; global-memory writes made
 // before the barrier are visible to all threads of the cluster after it.
 __device__ __forceinline__ void cl_sync() {
+  __syncwarp();   // the .aligned barrier wants every warp converged
   asm volatile(
       "barrier.cluster.arrive.release.aligned;\n\t"
       "barrier.cluster.wait.acquire.aligned;" ::: "memory");
