@@ -34,6 +34,15 @@ long long launch_count();
 
 enum JacobiMode { JAC_SWEEP = 0, JAC_FIRST = 1, JAC_APPLY = 2, JAC_RELAX = 3 };
 
+// ---- kernels_blk.cu: small square blocks, one lane per block ---------------
+// true when square s x s blocks (2 <= s <= 8) average at least 6 per block row
+bool blk_applies(int bs, int n_brows, int64_t nnzb);
+// op 0/1/2: y = A x, y = b - A x, y += A x; op 3: y = x + W (b - A x).
+// cudaErrorNotSupported when the shape or the alignment does not fit.
+template <typename T>
+cudaError_t launch_blk(int op, int n_brows, int bs, int64_t nnzb, const int *rp, const int *col,
+                       const T *val, const T *W, const T *x, const T *b, T *y, cudaStream_t s);
+
 // ---- kernels_mv.cu ---------------------------------------------------------
 // nnzb >= 0 lets the launcher pick a warp per block row when rows are long
 // (>= 12 blocks on average); nnzb < 0 always uses one thread per scalar row.

@@ -1,0 +1,225 @@
+// Coarse-level block-sparse products with small square blocks (s <= 8):
+// one lane per block.
+//
+// Below level 0 every unit is an aggregate with s = a handful of dofs, and
+// each Galerkin product widens the stencil (tens to over a hundred blocks
+// per block row).  A thread per scalar row would walk that row's blocks one
+// after another with s-wide loads; here a team of TL lanes owns a block row
+// and lane l takes whole blocks beg + l, beg + l + TL, ...: it reads the
+// s x s block (s*s contiguous values) with the widest aligned vector loads
+// and the matching s entries of x, two blocks at a time, and keeps s
+// partial row sums.  The team's sums meet in an xor-shuffle (and, for teams
+// wider than a warp, in shared memory in a fixed order), so every row is
+// summed in an order that depends only on the matrix.
+//
+// Operations: y = A x, y = b - A x, y += A x, and the block-Jacobi step
+// x_out = x + W (b - A x) of Alg. 1 with W = w D^{-1}.
+#include <atomic>
+#include <cstdlib>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gasa {
+
+namespace {
+
+enum { BLK_ASSIGN = 0, BLK_RESID = 1, BLK_ADD = 2, BLK_SWEEP = 3 };
+
+template <typename T, int N>
+struct BlkVec {
+  // widest load (in elements) that keeps a run of N values aligned
+  static constexpr int bytes = N * (int)sizeof(T);
+  static constexpr int value = (bytes % 16 == 0) ? 16 / (int)sizeof(T)
+                               : (bytes % 8 == 0 && sizeof(T) <= 8) ? 8 / (int)sizeof(T)
+                                                                    : 1;
+};
+
+template <typename T, int N>
+__device__ __forceinline__ void load_run(const T *p, T (&out)[N]) {
+  constexpr int W = BlkVec<T, N>::value;
+#pragma unroll
+  for (int i = 0; i < N; i += W) load_vec<T, W>(p + i, out + i);
+}
+
+template <typename T, int S, int TL, int OP>
+__global__ void __launch_bounds__(256)
+bsr_blk_kernel(int n_brows, const int *__restrict__ rp, const int *__restrict__ col,
+               const T *__restrict__ val, const T *__restrict__ Wm, const T *__restrict__ x,
+               const T *__restrict__ b, T *__restrict__ y) {
+  pdl_entry();
+  constexpr int TW = TL < 32 ? TL : 32;          // lanes of a team inside one warp
+  constexpr int WPT = TL > 32 ? TL / 32 : 1;     // warps per team
+  __shared__ T red[(256 / 32) * S];
+  const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int u = (int)(gt / TL);
+  const int l = (int)(gt % TL);
+  T acc[S];
+#pragma unroll
+  for (int r = 0; r < S; ++r) acc[r] = T(0);
+  if (u < n_brows) {
+    const int beg = __ldg(rp + u), end = __ldg(rp + u + 1);
+    int k = beg + l;
+    // two blocks in flight per lane while they fit in registers
+    for (; S * S <= 25 && k + TL < end; k += 2 * TL) {
+      T a0[S * S], a1[S * S], x0[S], x1[S];
+      const int j0 = __ldg(col + k), j1 = __ldg(col + k + TL);
+      load_run<T, S * S>(val + (size_t)k * S * S, a0);
+      load_run<T, S * S>(val + (size_t)(k + TL) * S * S, a1);
+      load_run<T, S>(x + (size_t)j0 * S, x0);
+      load_run<T, S>(x + (size_t)j1 * S, x1);
+#pragma unroll
+      for (int r = 0; r < S; ++r) {
+        T s0 = T(0), s1 = T(0);
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+          s0 = fma(a0[r * S + c], x0[c], s0);
+          s1 = fma(a1[r * S + c], x1[c], s1);
+        }
+        acc[r] += s0 + s1;
+      }
+    }
+    for (; k < end; k += TL) {
+      T a0[S * S], x0[S];
+      const int j0 = __ldg(col + k);
+      load_run<T, S * S>(val + (size_t)k * S * S, a0);
+      load_run<T, S>(x + (size_t)j0 * S, x0);
+#pragma unroll
+      for (int r = 0; r < S; ++r) {
+        T s0 = T(0);
+#pragma unroll
+        for (int c = 0; c < S; ++c) s0 = fma(a0[r * S + c], x0[c], s0);
+        acc[r] += s0;
+      }
+    }
+  }
+  // team sum: xor-shuffle inside the warp, then the warps of a wide team in
+  // a fixed order through shared memory
+#pragma unroll
+  for (int o = 1; o < TW; o <<= 1) {
+#pragma unroll
+    for (int r = 0; r < S; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+  }
+  if constexpr (WPT > 1) {
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+      for (int r = 0; r < S; ++r) red[wid * S + r] = acc[r];
+    }
+    __syncthreads();
+    const int w0 = wid - wid % WPT;   // first warp of this team
+#pragma unroll
+    for (int r = 0; r < S; ++r) {
+      T v = T(0);
+#pragma unroll
+      for (int q = 0; q < WPT; ++q) v += red[(w0 + q) * S + r];
+      acc[r] = v;
+    }
+  }
+  if (u >= n_brows || l >= S) return;
+  // lane l < S of the team writes row l
+  const size_t t = (size_t)u * S + l;
+  if (OP == BLK_SWEEP) {
+    T bv[S];
+    load_run<T, S>(b + (size_t)u * S, bv);
+    T wv[S];
+    load_run<T, S>(Wm + t * S, wv);
+    T out = T(0);
+#pragma unroll
+    for (int c = 0; c < S; ++c) out = fma(wv[c], bv[c] - acc[c], out);
+    y[t] = x[t] + out;
+    return;
+  }
+  T v = T(0);
+#pragma unroll
+  for (int r = 0; r < S; ++r)
+    if (r == l) v = acc[r];
+  if (OP == BLK_ASSIGN) y[t] = v;
+  else if (OP == BLK_RESID) y[t] = b[t] - v;
+  else y[t] += v;
+}
+
+// lanes per block row from the average row length
+int blk_team(int n_brows, int64_t nnzb) {
+  const double avg = (double)nnzb / (double)(n_brows > 0 ? n_brows : 1);
+  if (avg <= 12.0) return 8;
+  if (avg <= 48.0) return 32;
+  return 128;
+}
+
+template <typename T, int S, int OP>
+cudaError_t blk_launch_s(int n_brows, int64_t nnzb, const int *rp, const int *col, const T *val,
+                         const T *W, const T *x, const T *b, T *y, cudaStream_t s) {
+  const int TL = blk_team(n_brows, nnzb);
+  const int grid = div_up((long long)n_brows * TL, 256);
+  switch (TL) {
+    case 8: launch_k(bsr_blk_kernel<T, S, 8, OP>, grid, 256, 0, s, n_brows, rp, col, val, W, x, b, y); break;
+    case 32: launch_k(bsr_blk_kernel<T, S, 32, OP>, grid, 256, 0, s, n_brows, rp, col, val, W, x, b, y); break;
+    default: launch_k(bsr_blk_kernel<T, S, 128, OP>, grid, 256, 0, s, n_brows, rp, col, val, W, x, b, y); break;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T, int OP>
+cudaError_t blk_launch(int n_brows, int bs, int64_t nnzb, const int *rp, const int *col,
+                       const T *val, const T *W, const T *x, const T *b, T *y, cudaStream_t s) {
+  switch (bs) {
+    case 2: return blk_launch_s<T, 2, OP>(n_brows, nnzb, rp, col, val, W, x, b, y, s);
+    case 3: return blk_launch_s<T, 3, OP>(n_brows, nnzb, rp, col, val, W, x, b, y, s);
+    case 4: return blk_launch_s<T, 4, OP>(n_brows, nnzb, rp, col, val, W, x, b, y, s);
+    case 5: return blk_launch_s<T, 5, OP>(n_brows, nnzb, rp, col, val, W, x, b, y, s);
+    case 6: return blk_launch_s<T, 6, OP>(n_brows, nnzb, rp, col, val, W, x, b, y, s);
+    case 7: return blk_launch_s<T, 7, OP>(n_brows, nnzb, rp, col, val, W, x, b, y, s);
+    case 8: return blk_launch_s<T, 8, OP>(n_brows, nnzb, rp, col, val, W, x, b, y, s);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+bool aligned_to(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+}  // namespace
+
+namespace {
+std::atomic<int> g_blk{-1};
+}
+
+// on unless the environment sets GASA_BLK=0 (for A/B timing against the
+// thread-, warp- and CTA-per-row kernels)
+bool blk_enabled() {
+  int v = g_blk.load(std::memory_order_relaxed);
+  if (v < 0) {
+    const char *e = std::getenv("GASA_BLK");
+    v = (e && e[0] == '0') ? 0 : 1;
+    g_blk.store(v, std::memory_order_relaxed);
+  }
+  return v != 0;
+}
+
+bool blk_applies(int bs, int n_brows, int64_t nnzb) {
+  return bs >= 2 && bs <= 8 && n_brows > 0 && nnzb >= 6LL * n_brows && blk_enabled();
+}
+
+template <typename T>
+cudaError_t launch_blk(int op, int n_brows, int bs, int64_t nnzb, const int *rp, const int *col,
+                       const T *val, const T *W, const T *x, const T *b, T *y, cudaStream_t s) {
+  if (!blk_applies(bs, n_brows, nnzb)) return cudaErrorNotSupported;
+  // vector loads need the arrays aligned like their runs (cudaMalloc gives 256 bytes)
+  for (const void *p : {(const void *)val, (const void *)W, (const void *)x, (const void *)b})
+    if (p && !aligned_to(p, 16)) return cudaErrorNotSupported;
+  switch (op) {
+    case BLK_ASSIGN: return blk_launch<T, BLK_ASSIGN>(n_brows, bs, nnzb, rp, col, val, W, x, b, y, s);
+    case BLK_RESID: return blk_launch<T, BLK_RESID>(n_brows, bs, nnzb, rp, col, val, W, x, b, y, s);
+    case BLK_ADD: return blk_launch<T, BLK_ADD>(n_brows, bs, nnzb, rp, col, val, W, x, b, y, s);
+    case BLK_SWEEP: return blk_launch<T, BLK_SWEEP>(n_brows, bs, nnzb, rp, col, val, W, x, b, y, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template cudaError_t launch_blk<double>(int, int, int, int64_t, const int *, const int *,
+                                        const double *, const double *, const double *,
+                                        const double *, double *, cudaStream_t);
+template cudaError_t launch_blk<float>(int, int, int, int64_t, const int *, const int *,
+                                       const float *, const float *, const float *,
+                                       const float *, float *, cudaStream_t);
+
+}  // namespace gasa

@@ -286,6 +286,10 @@ template <typename T>
 cudaError_t launch_bsr_mv(int mode, int n_brows, int br, int bc, const int *rp, const int *col,
                           const T *val, const T *x, const T *b, T *y, cudaStream_t s,
                           int64_t nnzb) {
+  if (br == bc && mode >= GASA_MV_ASSIGN && mode <= GASA_MV_ADD && blk_applies(br, n_brows, nnzb)) {
+    const cudaError_t e = launch_blk<T>(mode, n_brows, br, nnzb, rp, col, val, nullptr, x, b, y, s);
+    if (e != cudaErrorNotSupported) return e;
+  }
   if (n_brows > 0 && warp_rows(n_brows, br, nnzb)) {
     switch (mode) {
       case GASA_MV_ASSIGN:
@@ -560,6 +564,10 @@ template <typename T>
 cudaError_t launch_jacobi(int mode, int n_units, int bs, const int *rp, const int *col,
                           const T *val, const T *W, const T *x, const T *b, T *xo,
                           cudaStream_t s, int64_t nnzb) {
+  if (mode == JAC_SWEEP && blk_applies(bs, n_units, nnzb)) {
+    const cudaError_t e = launch_blk<T>(3, n_units, bs, nnzb, rp, col, val, W, x, b, xo, s);
+    if (e != cudaErrorNotSupported) return e;
+  }
   if (n_units > 0 && mode != JAC_FIRST && warp_rows(n_units, bs, nnzb)) {
     switch (mode) {
       case JAC_SWEEP: return jac_warp_dispatch<T, JAC_SWEEP>(n_units, bs, rp, col, val, W, x, b, xo, s);

@@ -47,6 +47,13 @@ CASES_MV = [
     (5000, 5000, 4, 4, 6, 21),    # > 4096 short-ish rows, few threads: lane groups of a warp
     (5000, 3000, 5, 10, 6, 22),   # same, non-power-of-two height: lane per block
     (4500, 4500, 13, 13, 5, 23),
+    # square blocks of 2..8 with >= 6 blocks per row: a lane per block, teams
+    # of 8, 32 or 128 lanes per block row by the average row length
+    (2000, 2000, 2, 2, 10, 31),
+    (300, 300, 3, 3, 60, 32),
+    (257, 257, 5, 5, 140, 33),
+    (129, 129, 7, 7, 30, 34),
+    (1000, 997, 6, 6, 8, 35),
 ]
 
 
@@ -108,7 +115,9 @@ def _jacobi_inputs(n, bs, seed, per_row=4):
     (1031, 3, 11, 4), (517, 10, 12, 4), (129, 17, 13, 4), (77, 40, 14, 4),
     (301, 4, 15, 20), (97, 13, 16, 40), (40, 36, 17, 30),   # warp per block row
     (90, 8, 18, 16), (33, 16, 19, 12), (20, 32, 20, 8),     # CTA per block row
-    (5000, 4, 24, 6), (4500, 13, 25, 5)])                   # warp per block row
+    (5000, 4, 24, 6), (4500, 13, 25, 5),                    # warp per block row
+    (2000, 2, 36, 10), (300, 3, 37, 60), (257, 5, 38, 140),  # lane per block
+    (129, 7, 39, 30), (1000, 6, 40, 8), (3001, 4, 41, 13)])
 def test_jacobi_sweep_fp64(n, bs, seed, per_row):
     gasa = _gasa()
     ptr, col, val, W, x, b = _jacobi_inputs(n, bs, seed, per_row)
@@ -125,7 +134,8 @@ def test_jacobi_sweep_fp64(n, bs, seed, per_row):
 
 
 @pytest.mark.parametrize("n,bs,seed,per_row", [(1031, 3, 11, 4), (517, 10, 12, 4), (129, 17, 13, 4),
-                                               (301, 4, 15, 20)])
+                                               (301, 4, 15, 20), (300, 3, 37, 60), (3001, 4, 41, 13),
+                                               (129, 8, 42, 70)])
 def test_jacobi_sweep_fp32(n, bs, seed, per_row):
     gasa = _gasa()
     ptr, col, val, W, x, b = _jacobi_inputs(n, bs, seed, per_row)
