@@ -35,7 +35,8 @@ long long launch_count();
 enum JacobiMode { JAC_SWEEP = 0, JAC_FIRST = 1, JAC_APPLY = 2, JAC_RELAX = 3 };
 
 // ---- kernels_blk.cu: small square blocks, one lane per block ---------------
-// true when square s x s blocks (2 <= s <= 8) average at least 6 per block row
+// true when square s x s blocks (2 <= s <= 8) average at least 6 per block row;
+// launch_blk then takes FP32 operands (FP64 returns cudaErrorNotSupported)
 bool blk_applies(int bs, int n_brows, int64_t nnzb);
 // op 0/1/2: y = A x, y = b - A x, y += A x; op 3: y = x + W (b - A x).
 // cudaErrorNotSupported when the shape or the alignment does not fit.

@@ -1,5 +1,5 @@
-// Coarse-level block-sparse products with small square blocks (s <= 8):
-// one lane per block.
+// Coarse-level block-sparse products with small square blocks (s <= 8) in
+// FP32: one lane per block.
 //
 // Below level 0 every unit is an aggregate with s = a handful of dofs, and
 // each Galerkin product widens the stencil (tens to over a hundred blocks
@@ -203,6 +203,10 @@ bool blk_applies(int bs, int n_brows, int64_t nnzb) {
 template <typename T>
 cudaError_t launch_blk(int op, int n_brows, int bs, int64_t nnzb, const int *rp, const int *col,
                        const T *val, const T *W, const T *x, const T *b, T *y, cudaStream_t s) {
+  // FP32 only: the team sums add s * log2(team) additions per lane, which
+  // the FP32 pipe absorbs; on GB300's narrow FP64 pipe they would cost more
+  // than the loads they hide (measured: FP64 V-cycle 1.69 -> 2.36 ms)
+  if (sizeof(T) != sizeof(float)) return cudaErrorNotSupported;
   if (!blk_applies(bs, n_brows, nnzb)) return cudaErrorNotSupported;
   // vector loads need the arrays aligned like their runs (cudaMalloc gives 256 bytes)
   for (const void *p : {(const void *)val, (const void *)W, (const void *)x, (const void *)b})

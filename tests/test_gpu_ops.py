@@ -74,7 +74,7 @@ def test_bsr_mv_fp64(case, mode):
     assert rel_err(to_host(y), want) <= TOL64
 
 
-@pytest.mark.parametrize("case", CASES_MV[:5] + CASES_MV[6:9])
+@pytest.mark.parametrize("case", CASES_MV[:5] + CASES_MV[6:9] + CASES_MV[11:12] + CASES_MV[-5:])
 def test_bsr_mv_fp32(case):
     gasa = _gasa()
     n, m, br, bc, per, seed = case
