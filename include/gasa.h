@@ -242,6 +242,19 @@ gasa_status gasa_bsr_mv_f32(int32_t mode, int32_t n_brows, int32_t br, int32_t b
                             const int32_t *row_ptr, const int32_t *col, const float *val,
                             const float *x, const float *b, float *y, void *stream);
 
+/* y = A x (FP64 result) of the outer Krylov product of the mixed-precision
+ * solve (the Alg. 2 preconditioner runs in FP32; the paper fixes no
+ * precision), in double-single arithmetic from exact two-term FP32 splits:
+ * a = a_hi + a_lo per stored value and x = x_hi + x_lo per entry (hi the FP32
+ * rounding, lo the FP32 rounding of the remainder).  Each product's leading
+ * part is exact and joins the sum by an error-free two-sum; the low word
+ * gathers the rest in FP32, so a row of n terms agrees with an FP64 product
+ * to within n * 2^-47 of sum |a x| (an FP32 product: 2^-24).  Layout as
+ * gasa_bsr_mv; all pointers device memory; errors as gasa_bsr_mv. */
+gasa_status gasa_bsr_mv_ds(int32_t n_brows, int32_t br, int32_t bc, const int32_t *row_ptr,
+                           const int32_t *col, const float *a_hi, const float *a_lo,
+                           const float *x_hi, const float *x_lo, double *y, void *stream);
+
 /* One block-Jacobi step of Alg. 1 with A~^{-1} = W = w D^{-1}
  * (Eq. smoother_choice): x_out = x + W (b - A x); first != 0 gives the
  * step from x = 0, x_out = W b (x unused).  W holds n_units blocks of

@@ -17,6 +17,7 @@ struct DevBSR {
   int *rp = nullptr, *col = nullptr;
   double *val = nullptr;
   float *val32 = nullptr;
+  float *lo32 = nullptr;       // level 0: FP32 rounding of val - val32 (double-single A x)
   __half *val16 = nullptr;     // FP16 blocks (level 0, MIXED16)
   float *scale16 = nullptr;    // one scale per block
 };
@@ -91,6 +92,7 @@ struct gasa_ctx {
   double *scal = nullptr;         // device scalars
   double *hscal = nullptr;        // pinned host mirror
   float *kf_in = nullptr, *kf_out = nullptr;
+  float *kp_hi = nullptr, *kp_lo = nullptr;   // two-term FP32 split of p (mixed precision)
   double *V = nullptr, *Z = nullptr, *H = nullptr, *gm = nullptr, *mpart = nullptr;
   int gm_restart = 0;
   bool gm_flex = false;

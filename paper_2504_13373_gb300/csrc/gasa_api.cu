@@ -433,6 +433,21 @@ gasa_status spmv_outer(gasa_ctx *ctx, int mode, const double *x, const double *b
   return GASA_OK;
 }
 
+// q = A p of the mixed-precision Krylov step: double-single arithmetic on
+// the FP32 splits of A (val32 + lo32) and of p (kp_hi + kp_lo, written by the
+// CG update or, with split_p, here)
+gasa_status spmv_outer_ds(gasa_ctx *ctx, const double *p, double *q, bool split_p) {
+  Level &l = ctx->L[0];
+  const int64_t n = l.ndof;
+  if (split_p) CU(launch_split(n, p, ctx->kp_hi, ctx->kp_lo, ctx->stream));
+  cudaEvent_t e0;
+  prof_begin(ctx, 2, &e0);
+  CU(launch_bsr_mv_ds(l.n, l.s, l.s, l.A.rp, l.A.col, l.A.val32, l.A.lo32, ctx->kp_hi,
+                      ctx->kp_lo, q, ctx->stream));
+  prof_end(ctx, 2, spmv_bytes(l, 8, false));   // 4 + 4 bytes per value and per x entry
+  return GASA_OK;
+}
+
 gasa_status pcg(gasa_ctx *ctx, const double *b, double tol, int precision, int *iters,
                 double *relres, bool *conv) {
   cudaStream_t s = ctx->stream;
@@ -460,7 +475,8 @@ gasa_status pcg(gasa_ctx *ctx, const double *b, double tol, int precision, int *
   int cur = S_RZ0, nxt = S_RZ1;
   const int max_iter = ctx->opt.max_iter;
   for (int it = 1; it <= max_iter; ++it) {
-    ST(spmv_outer(ctx, GASA_MV_ASSIGN, p, nullptr, q));
+    if (flex) ST(spmv_outer_ds(ctx, p, q, true));
+    else ST(spmv_outer(ctx, GASA_MV_ASSIGN, p, nullptr, q));
     CU(launch_dot_partials(n, p, q, pq_part, s));
     CU(launch_cg_update_xr(n, x, r, p, q, ctx->scal + cur, pq_part, rr_part, ctx->scal + S_ALPHA,
                            s));
@@ -543,9 +559,13 @@ gasa_status build_cg_graph(gasa_ctx *ctx, int precision) {
     if (e == cudaSuccess && flex) e = launch_dot_partials(n, r, zold, rzo_part, s);
     if (e == cudaSuccess)
       e = launch_cg_update_p(n, p, z, ctx->scal + S_RZ0, rz_part, rzo_part, ctx->scal + S_RZ1,
-                             flex ? 1 : 0, s, flex ? zold : nullptr);
+                             flex ? 1 : 0, s, flex ? zold : nullptr, flex ? ctx->kp_hi : nullptr,
+                             flex ? ctx->kp_lo : nullptr);
     Level &l = ctx->L[0];
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && flex)
+      e = launch_bsr_mv_ds(l.n, l.s, l.s, l.A.rp, l.A.col, l.A.val32, l.A.lo32, ctx->kp_hi,
+                           ctx->kp_lo, q, s);
+    else if (e == cudaSuccess)
       e = launch_bsr_mv<double>(GASA_MV_ASSIGN, l.n, l.s, l.s, l.A.rp, l.A.col, l.A.val, p, nullptr,
                                 q, s);
     if (e == cudaSuccess) e = launch_dot_partials(n, p, q, pq_part, s);
@@ -1396,6 +1416,9 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
     ST(make_f32(ctx, l.P));
     ST(make_f32(ctx, l.R));
     if (k == 0) {
+      // low FP32 words of A_0 for the double-single outer product
+      ST(dalloc(ctx, &l.A.lo32, (size_t)l.A.nnzb * l.s * l.s));
+      CU(launch_split((int64_t)l.A.nnzb * l.s * l.s, l.A.val, l.A.val32, l.A.lo32, s));
       // FP16 blocks with one FP32 scale per block for the MIXED16 V-cycle
       ST(dalloc(ctx, &l.A.val16, (size_t)l.A.nnzb * l.s * l.s));
       ST(dalloc(ctx, &l.A.scale16, (size_t)l.A.nnzb));
@@ -1450,6 +1473,8 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
     ST(dalloc(ctx, p, (size_t)n));
   ST(dalloc(ctx, &ctx->kf_in, (size_t)n));
   ST(dalloc(ctx, &ctx->kf_out, (size_t)n));
+  ST(dalloc(ctx, &ctx->kp_hi, (size_t)n));
+  ST(dalloc(ctx, &ctx->kp_lo, (size_t)n));
   ST(dalloc(ctx, &ctx->d_iters, 4));
   ST(dalloc(ctx, &ctx->d_err, 4));
   CU(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
@@ -1807,6 +1832,16 @@ gasa_status gasa_bsr_mv_f32(int32_t mode, int32_t n_brows, int32_t br, int32_t b
   return op_status(launch_bsr_mv<float>(mode, n_brows, br, bc, row_ptr, col, val, x, b, y,
                                         (cudaStream_t)stream,
                                         op_nnzb(row_ptr, n_brows, (cudaStream_t)stream)));
+}
+
+gasa_status gasa_bsr_mv_ds(int32_t n_brows, int32_t br, int32_t bc, const int32_t *row_ptr,
+                           const int32_t *col, const float *a_hi, const float *a_lo,
+                           const float *x_hi, const float *x_lo, double *y, void *stream) {
+  if (n_brows < 0 || br <= 0 || bc <= 0) return GASA_ERR_INVALID_ARG;
+  if (n_brows == 0) return GASA_OK;
+  if (!row_ptr || !col || !a_hi || !a_lo || !x_hi || !x_lo || !y) return GASA_ERR_INVALID_ARG;
+  return op_status(launch_bsr_mv_ds(n_brows, br, bc, row_ptr, col, a_hi, a_lo, x_hi, x_lo, y,
+                                    (cudaStream_t)stream));
 }
 
 gasa_status gasa_jacobi_sweep(int32_t n_units, int32_t bs, const int32_t *row_ptr,

@@ -68,6 +68,12 @@ cudaError_t launch_bsr_mm(int n_brows, int br, int bc, const int *rp, const int 
                           const double *val, const double *X, int64_t ldx, double *Y,
                           int64_t ldy, int ncols, cudaStream_t s);
 
+// y = A x (FP64 out) in double-single arithmetic from exact two-term FP32
+// splits of A (hi, lo) and x (hi, lo)
+cudaError_t launch_bsr_mv_ds(int n_brows, int br, int bc, const int *rp, const int *col,
+                             const float *ahi, const float *alo, const float *xhi,
+                             const float *xlo, double *y, cudaStream_t s);
+
 // y = A x for a dense row-major n x n matrix
 template <typename T>
 cudaError_t launch_dense_mv(int n, const double *A, const T *x, T *y, cudaStream_t s);
@@ -106,7 +112,10 @@ cudaError_t launch_cg_update_xr(int64_t n, double *x, double *r, const double *p
 cudaError_t launch_cg_update_p(int64_t n, double *p, const double *z, const double *rz_old,
                                const double *rz_partials, const double *rzold_partials,
                                double *rz_out, int flexible, cudaStream_t s,
-                               double *zold_out = nullptr);
+                               double *zold_out = nullptr, float *p_hi = nullptr,
+                               float *p_lo = nullptr);
+// exact two-term FP32 split v = hi + lo of an FP64 vector
+cudaError_t launch_split(int64_t n, const double *v, float *hi, float *lo, cudaStream_t s);
 cudaError_t launch_cg_check(const double *rr_partials, double *scal, int *iters, int max_iter,
                             cudaGraphConditionalHandle handle, cudaStream_t s);
 void note_launches(long long n);

@@ -139,24 +139,32 @@ bsr_blk_kernel(int n_brows, const int *__restrict__ rp, const int *__restrict__ 
   else y[t] += v;
 }
 
-// lanes per block row from the average row length
-int blk_team(int n_brows, int64_t nnzb) {
+// Lanes per block row: about 2.5 blocks per lane (two in flight, a short
+// tail), a power of two in [4, 64] and at least s, so that lanes 0..s-1 of
+// the team can write the s rows.
+int blk_team(int bs, int n_brows, int64_t nnzb) {
   const double avg = (double)nnzb / (double)(n_brows > 0 ? n_brows : 1);
-  if (avg <= 12.0) return 8;
-  if (avg <= 48.0) return 32;
-  return 128;
+  int tl = 4;
+  while (tl < 64 && tl * 2.5 < avg) tl *= 2;
+  while (tl < bs) tl *= 2;
+  return tl;
 }
 
 template <typename T, int S, int OP>
 cudaError_t blk_launch_s(int n_brows, int64_t nnzb, const int *rp, const int *col, const T *val,
                          const T *W, const T *x, const T *b, T *y, cudaStream_t s) {
-  const int TL = blk_team(n_brows, nnzb);
+  const int TL = blk_team(S, n_brows, nnzb);
   const int grid = div_up((long long)n_brows * TL, 256);
+#define GASA_BLK_TL(V)                                                                       \
+  case V:                                                                                    \
+    launch_k(bsr_blk_kernel<T, S, (V < S ? 8 : V), OP>, grid, 256, 0, s, n_brows, rp, col, val, W, \
+             x, b, y);                                                                       \
+    break;
   switch (TL) {
-    case 8: launch_k(bsr_blk_kernel<T, S, 8, OP>, grid, 256, 0, s, n_brows, rp, col, val, W, x, b, y); break;
-    case 32: launch_k(bsr_blk_kernel<T, S, 32, OP>, grid, 256, 0, s, n_brows, rp, col, val, W, x, b, y); break;
-    default: launch_k(bsr_blk_kernel<T, S, 128, OP>, grid, 256, 0, s, n_brows, rp, col, val, W, x, b, y); break;
+    GASA_BLK_TL(4) GASA_BLK_TL(8) GASA_BLK_TL(16) GASA_BLK_TL(32)
+    default: launch_k(bsr_blk_kernel<T, S, 64, OP>, grid, 256, 0, s, n_brows, rp, col, val, W, x, b, y); break;
   }
+#undef GASA_BLK_TL
   note_launch();
   return cudaGetLastError();
 }
@@ -200,17 +208,26 @@ bool blk_applies(int bs, int n_brows, int64_t nnzb) {
   return bs >= 2 && bs <= 8 && n_brows > 0 && nnzb >= 6LL * n_brows && blk_enabled();
 }
 
-template <typename T>
-cudaError_t launch_blk(int op, int n_brows, int bs, int64_t nnzb, const int *rp, const int *col,
-                       const T *val, const T *W, const T *x, const T *b, T *y, cudaStream_t s) {
-  // FP32 only: the team sums add s * log2(team) additions per lane, which
-  // the FP32 pipe absorbs; on GB300's narrow FP64 pipe they would cost more
-  // than the loads they hide (measured: FP64 V-cycle 1.69 -> 2.36 ms)
-  if (sizeof(T) != sizeof(float)) return cudaErrorNotSupported;
+// FP32 only: the team sums add s * log2(team) additions per lane, which the
+// FP32 pipe absorbs; on GB300's narrow FP64 pipe they cost more than the
+// loads they hide (measured: FP64 V-cycle 1.69 -> 2.36 ms per iteration), so
+// FP64 keeps the thread-, warp- and CTA-per-row kernels.
+template <>
+cudaError_t launch_blk<double>(int, int, int, int64_t, const int *, const int *, const double *,
+                               const double *, const double *, const double *, double *,
+                               cudaStream_t) {
+  return cudaErrorNotSupported;
+}
+
+template <>
+cudaError_t launch_blk<float>(int op, int n_brows, int bs, int64_t nnzb, const int *rp,
+                              const int *col, const float *val, const float *W, const float *x,
+                              const float *b, float *y, cudaStream_t s) {
   if (!blk_applies(bs, n_brows, nnzb)) return cudaErrorNotSupported;
   // vector loads need the arrays aligned like their runs (cudaMalloc gives 256 bytes)
   for (const void *p : {(const void *)val, (const void *)W, (const void *)x, (const void *)b})
     if (p && !aligned_to(p, 16)) return cudaErrorNotSupported;
+  using T = float;
   switch (op) {
     case BLK_ASSIGN: return blk_launch<T, BLK_ASSIGN>(n_brows, bs, nnzb, rp, col, val, W, x, b, y, s);
     case BLK_RESID: return blk_launch<T, BLK_RESID>(n_brows, bs, nnzb, rp, col, val, W, x, b, y, s);
@@ -219,11 +236,5 @@ cudaError_t launch_blk(int op, int n_brows, int bs, int64_t nnzb, const int *rp,
     default: return cudaErrorInvalidValue;
   }
 }
-template cudaError_t launch_blk<double>(int, int, int, int64_t, const int *, const int *,
-                                        const double *, const double *, const double *,
-                                        const double *, double *, cudaStream_t);
-template cudaError_t launch_blk<float>(int, int, int, int64_t, const int *, const int *,
-                                       const float *, const float *, const float *,
-                                       const float *, float *, cudaStream_t);
 
 }  // namespace gasa

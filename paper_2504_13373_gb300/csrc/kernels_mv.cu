@@ -317,6 +317,119 @@ template cudaError_t launch_bsr_mv<float>(int, int, int, int, const int *, const
                                           cudaStream_t, int64_t);
 
 // ----------------------------------------------------------------------------
+// y = A x in double-single arithmetic (the outer Krylov product of the
+// mixed-precision solve).  A and x arrive as exact two-term FP32 splits,
+// a = a_hi + a_lo and x = x_hi + x_lo (a_hi the FP32 rounding of a, a_lo the
+// FP32 rounding of a - a_hi, so each pair holds a to 2^-48 relative).  Per
+// product: a_hi x_hi = p + e exactly (p rounded, e = fma(a_hi, x_hi, -p)),
+// the cross terms a_hi x_lo + a_lo x_hi in FP32 (a_lo x_lo, below 2^-48, is
+// dropped); p joins the running sum s by an error-free two-sum and every
+// error and cross term joins the low word t.  The row result is s + t in
+// FP64.  Every step uses FP32 units: on GB300 FP64 FMAs run at a small
+// fraction of the FP32 rate, and an FP64 SpMV needs one FMA per 8 bytes of
+// matrix, more than that rate feeds at full HBM bandwidth.  The __f*_rn
+// intrinsics keep the compiler from contracting the two-sum into FMAs.
+// ----------------------------------------------------------------------------
+template <int BC>
+__global__ void __launch_bounds__(256)
+bsr_mv_ds_kernel(int n_brows, int br, const int *__restrict__ rp, const int *__restrict__ col,
+                 const float *__restrict__ ahi, const float *__restrict__ alo,
+                 const float *__restrict__ xhi, const float *__restrict__ xlo,
+                 double *__restrict__ y) {
+  pdl_entry();
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n_brows * br) return;
+  const int i = (int)(t / br);
+  const int r = (int)(t - (long long)i * br);
+  constexpr int W = RowVec<float, BC>::value;
+  const int beg = __ldg(rp + i), end = __ldg(rp + i + 1);
+  float s = 0.0f, lo = 0.0f;
+  for (int k = beg; k < end; ++k) {
+    const int j = __ldg(col + k);
+    const size_t off = ((size_t)k * br + r) * BC;
+    float ah[BC], al[BC], xh[BC], xl[BC];
+#pragma unroll
+    for (int c = 0; c < BC; c += W) load_vec_stream<float, W>(ahi + off + c, ah + c);
+#pragma unroll
+    for (int c = 0; c < BC; c += W) load_vec_stream<float, W>(alo + off + c, al + c);
+#pragma unroll
+    for (int c = 0; c < BC; c += W) load_vec<float, W>(xhi + (size_t)j * BC + c, xh + c);
+#pragma unroll
+    for (int c = 0; c < BC; c += W) load_vec<float, W>(xlo + (size_t)j * BC + c, xl + c);
+#pragma unroll
+    for (int c = 0; c < BC; ++c) {
+      const float pr = __fmul_rn(ah[c], xh[c]);
+      const float e = __fmaf_rn(ah[c], xh[c], -pr);
+      const float cross = __fmaf_rn(ah[c], xl[c], __fmul_rn(al[c], xh[c]));
+      const float s1 = __fadd_rn(s, pr);
+      const float bp = __fsub_rn(s1, s);
+      const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s1, bp)), __fsub_rn(pr, bp));
+      s = s1;
+      lo = __fadd_rn(lo, __fadd_rn(err, __fadd_rn(e, cross)));
+    }
+  }
+  y[t] = (double)s + (double)lo;
+}
+
+__global__ void __launch_bounds__(256)
+bsr_mv_ds_generic(int n_brows, int br, int bc, const int *__restrict__ rp,
+                  const int *__restrict__ col, const float *__restrict__ ahi,
+                  const float *__restrict__ alo, const float *__restrict__ xhi,
+                  const float *__restrict__ xlo, double *__restrict__ y) {
+  pdl_entry();
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n_brows * br) return;
+  const int i = (int)(t / br);
+  const int r = (int)(t - (long long)i * br);
+  const int beg = __ldg(rp + i), end = __ldg(rp + i + 1);
+  float s = 0.0f, lo = 0.0f;
+  for (int k = beg; k < end; ++k) {
+    const int j = __ldg(col + k);
+    const size_t off = ((size_t)k * br + r) * bc;
+    for (int c = 0; c < bc; ++c) {
+      const float ah = __ldg(ahi + off + c), al = __ldg(alo + off + c);
+      const float xh = __ldg(xhi + (size_t)j * bc + c), xl = __ldg(xlo + (size_t)j * bc + c);
+      const float pr = __fmul_rn(ah, xh);
+      const float e = __fmaf_rn(ah, xh, -pr);
+      const float cross = __fmaf_rn(ah, xl, __fmul_rn(al, xh));
+      const float s1 = __fadd_rn(s, pr);
+      const float bp = __fsub_rn(s1, s);
+      const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s1, bp)), __fsub_rn(pr, bp));
+      s = s1;
+      lo = __fadd_rn(lo, __fadd_rn(err, __fadd_rn(e, cross)));
+    }
+  }
+  y[t] = (double)s + (double)lo;
+}
+
+cudaError_t launch_bsr_mv_ds(int n_brows, int br, int bc, const int *rp, const int *col,
+                             const float *ahi, const float *alo, const float *xhi,
+                             const float *xlo, double *y, cudaStream_t s) {
+  const long long rows = (long long)n_brows * br;
+  if (rows == 0) return cudaSuccess;
+  const int grid = div_up(rows, 256);
+  const bool al = aligned16(ahi) && aligned16(alo) && aligned16(xhi) && aligned16(xlo);
+#define GASA_DS_CASE(BC)                                                                    \
+  case BC:                                                                                  \
+    launch_k(bsr_mv_ds_kernel<BC>, grid, 256, 0, s, n_brows, br, rp, col, ahi, alo, xhi, xlo, y); \
+    note_launch();                                                                          \
+    return cudaGetLastError();
+  if (al) {
+    switch (bc) {
+      GASA_DS_CASE(1) GASA_DS_CASE(2) GASA_DS_CASE(3) GASA_DS_CASE(4) GASA_DS_CASE(5)
+      GASA_DS_CASE(6) GASA_DS_CASE(7) GASA_DS_CASE(8) GASA_DS_CASE(9) GASA_DS_CASE(10)
+      GASA_DS_CASE(11) GASA_DS_CASE(12) GASA_DS_CASE(13) GASA_DS_CASE(14) GASA_DS_CASE(15)
+      GASA_DS_CASE(16)
+      default: break;
+    }
+  }
+#undef GASA_DS_CASE
+  launch_k(bsr_mv_ds_generic, grid, 256, 0, s, n_brows, br, bc, rp, col, ahi, alo, xhi, xlo, y);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
 // block Jacobi step (Alg. 1 with A~^{-1} = w D^{-1}):
 //   SWEEP: xo = x + W (b - A x)   FIRST: xo = W b
 //   APPLY: xo = W (A x)           RELAX: xo = x - W A x

@@ -33,31 +33,65 @@ void pdl_set(bool on) { g_pdl.store(on ? 1 : 0, std::memory_order_relaxed); }
 // ----------------------------------------------------------------------------
 // reductions
 // ----------------------------------------------------------------------------
+// Streaming vector kernels read 16-byte pairs when both arrays are 16-byte
+// aligned (VEC), four pairs per array in flight per thread; the pair index
+// runs over a grid-stride loop and the odd last entry (if any) goes to
+// thread 0 of CTA 0, so each partial sums a fixed set of entries in a fixed
+// order.
+__device__ __forceinline__ double2 ld2(const double *p, int64_t k) {
+  return __ldg(reinterpret_cast<const double2 *>(p) + k);
+}
+
+template <bool VEC>
 __global__ void __launch_bounds__(kRedThreads)
 dot_partials_kernel(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                     double *__restrict__ partials) {
   pdl_entry();
   __shared__ double sh[32];
-  // four independent accumulators keep four loads in flight per thread
   double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (!y) y = x;
-  for (; i + 3 * stride < n; i += 4 * stride) {
-    v0 = fma(x[i], y[i], v0);
-    v1 = fma(x[i + stride], y[i + stride], v1);
-    v2 = fma(x[i + 2 * stride], y[i + 2 * stride], v2);
-    v3 = fma(x[i + 3 * stride], y[i + 3 * stride], v3);
+  if (VEC) {
+    const int64_t m = n >> 1;
+    for (; i + 3 * stride < m; i += 4 * stride) {
+      const double2 a0 = ld2(x, i), a1 = ld2(x, i + stride), a2 = ld2(x, i + 2 * stride),
+                    a3 = ld2(x, i + 3 * stride);
+      const double2 b0 = ld2(y, i), b1 = ld2(y, i + stride), b2 = ld2(y, i + 2 * stride),
+                    b3 = ld2(y, i + 3 * stride);
+      v0 = fma(a0.y, b0.y, fma(a0.x, b0.x, v0));
+      v1 = fma(a1.y, b1.y, fma(a1.x, b1.x, v1));
+      v2 = fma(a2.y, b2.y, fma(a2.x, b2.x, v2));
+      v3 = fma(a3.y, b3.y, fma(a3.x, b3.x, v3));
+    }
+    for (; i < m; i += stride) {
+      const double2 a0 = ld2(x, i), b0 = ld2(y, i);
+      v0 = fma(a0.y, b0.y, fma(a0.x, b0.x, v0));
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) v0 = fma(x[n - 1], y[n - 1], v0);
+  } else {
+    for (; i + 3 * stride < n; i += 4 * stride) {
+      v0 = fma(x[i], y[i], v0);
+      v1 = fma(x[i + stride], y[i + stride], v1);
+      v2 = fma(x[i + 2 * stride], y[i + 2 * stride], v2);
+      v3 = fma(x[i + 3 * stride], y[i + 3 * stride], v3);
+    }
+    for (; i < n; i += stride) v0 = fma(x[i], y[i], v0);
   }
-  for (; i < n; i += stride) v0 = fma(x[i], y[i], v0);
   double v = (v0 + v1) + (v2 + v3);
   v = block_sum(v, sh);
   if (threadIdx.x == 0) partials[blockIdx.x] = v;
 }
 
+static bool al16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
 cudaError_t launch_dot_partials(int64_t n, const double *x, const double *y, double *partials,
                                 cudaStream_t s) {
-  launch_k(dot_partials_kernel, kRedBlocks, kRedThreads, 0, s, n, x, y, partials); note_launch();
+  if (al16(x) && (!y || al16(y)))
+    launch_k(dot_partials_kernel<true>, kRedBlocks, kRedThreads, 0, s, n, x, y, partials);
+  else
+    launch_k(dot_partials_kernel<false>, kRedBlocks, kRedThreads, 0, s, n, x, y, partials);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -264,6 +298,7 @@ cudaError_t launch_sub(int64_t n, const double *a, const double *b, double *out,
 // ----------------------------------------------------------------------------
 // CG: x += alpha p, r -= alpha q with alpha = rz / (p.q); partial ||r||^2
 // ----------------------------------------------------------------------------
+template <bool VEC>
 __global__ void __launch_bounds__(kRedThreads)
 cg_update_xr_kernel(int64_t n, double *__restrict__ x, double *__restrict__ r,
                     const double *__restrict__ p, const double *__restrict__ q,
@@ -280,23 +315,57 @@ cg_update_xr_kernel(int64_t n, double *__restrict__ x, double *__restrict__ r,
   double v0 = 0.0, v1 = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (; i + stride < n; i += 2 * stride) {
-    const int64_t i2 = i + stride;
-    const double p0 = p[i], p1 = p[i2], q0 = q[i], q1 = q[i2];
-    const double x0 = x[i], x1 = x[i2], r0 = r[i], r1 = r[i2];
-    x[i] = fma(alpha, p0, x0);
-    x[i2] = fma(alpha, p1, x1);
-    const double ra = fma(-alpha, q0, r0), rb = fma(-alpha, q1, r1);
-    r[i] = ra;
-    r[i2] = rb;
-    v0 = fma(ra, ra, v0);
-    v1 = fma(rb, rb, v1);
-  }
-  for (; i < n; i += stride) {
-    x[i] = fma(alpha, p[i], x[i]);
-    const double ri = fma(-alpha, q[i], r[i]);
-    r[i] = ri;
-    v0 = fma(ri, ri, v0);
+  if (VEC) {
+    // pairs: two pairs of each of x, r, p, q in flight per thread
+    const int64_t m = n >> 1;
+    double2 *x2 = reinterpret_cast<double2 *>(x), *r2 = reinterpret_cast<double2 *>(r);
+    for (; i < m; i += 2 * stride) {
+      const int64_t i2 = i + stride;
+      const bool two = i2 < m;
+      const double2 p0 = ld2(p, i), q0 = ld2(q, i), x0 = x2[i], r0 = r2[i];
+      double2 p1 = p0, q1 = q0, x1 = x0, r1 = r0;
+      if (two) {
+        p1 = ld2(p, i2);
+        q1 = ld2(q, i2);
+        x1 = x2[i2];
+        r1 = r2[i2];
+      }
+      x2[i] = make_double2(fma(alpha, p0.x, x0.x), fma(alpha, p0.y, x0.y));
+      const double2 ra = make_double2(fma(-alpha, q0.x, r0.x), fma(-alpha, q0.y, r0.y));
+      r2[i] = ra;
+      v0 = fma(ra.y, ra.y, fma(ra.x, ra.x, v0));
+      if (two) {
+        x2[i2] = make_double2(fma(alpha, p1.x, x1.x), fma(alpha, p1.y, x1.y));
+        const double2 rb = make_double2(fma(-alpha, q1.x, r1.x), fma(-alpha, q1.y, r1.y));
+        r2[i2] = rb;
+        v1 = fma(rb.y, rb.y, fma(rb.x, rb.x, v1));
+      }
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+      x[n - 1] = fma(alpha, p[n - 1], x[n - 1]);
+      const double ri = fma(-alpha, q[n - 1], r[n - 1]);
+      r[n - 1] = ri;
+      v0 = fma(ri, ri, v0);
+    }
+  } else {
+    for (; i + stride < n; i += 2 * stride) {
+      const int64_t i2 = i + stride;
+      const double p0 = p[i], p1 = p[i2], q0 = q[i], q1 = q[i2];
+      const double x0 = x[i], x1 = x[i2], r0 = r[i], r1 = r[i2];
+      x[i] = fma(alpha, p0, x0);
+      x[i2] = fma(alpha, p1, x1);
+      const double ra = fma(-alpha, q0, r0), rb = fma(-alpha, q1, r1);
+      r[i] = ra;
+      r[i2] = rb;
+      v0 = fma(ra, ra, v0);
+      v1 = fma(rb, rb, v1);
+    }
+    for (; i < n; i += stride) {
+      x[i] = fma(alpha, p[i], x[i]);
+      const double ri = fma(-alpha, q[i], r[i]);
+      r[i] = ri;
+      v0 = fma(ri, ri, v0);
+    }
   }
   double v = v0 + v1;
   v = block_sum(v, sh);
@@ -306,18 +375,49 @@ cg_update_xr_kernel(int64_t n, double *__restrict__ x, double *__restrict__ r,
 cudaError_t launch_cg_update_xr(int64_t n, double *x, double *r, const double *p,
                                 const double *q, const double *rz, const double *pq_partials,
                                 double *rr_partials, double *alpha_out, cudaStream_t s) {
-  launch_k(cg_update_xr_kernel, kRedBlocks, kRedThreads, 0, s, n, x, r, p, q, rz, pq_partials,
-                                                         rr_partials, alpha_out); note_launch();
+  if (al16(x) && al16(r) && al16(p) && al16(q))
+    launch_k(cg_update_xr_kernel<true>, kRedBlocks, kRedThreads, 0, s, n, x, r, p, q, rz,
+             pq_partials, rr_partials, alpha_out);
+  else
+    launch_k(cg_update_xr_kernel<false>, kRedBlocks, kRedThreads, 0, s, n, x, r, p, q, rz,
+             pq_partials, rr_partials, alpha_out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// exact two-term FP32 split v = hi + lo (hi the FP32 rounding of v, lo the
+// FP32 rounding of v - hi)
+__device__ __forceinline__ void split_f32(double v, float *hi, float *lo, int64_t i) {
+  const float h = __double2float_rn(v);
+  hi[i] = h;
+  lo[i] = __double2float_rn(v - (double)h);
+}
+
+__global__ void split_kernel(int64_t n, const double *__restrict__ v, float *__restrict__ hi,
+                             float *__restrict__ lo) {
+  pdl_entry();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    split_f32(v[i], hi, lo, i);
+}
+
+cudaError_t launch_split(int64_t n, const double *v, float *hi, float *lo, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 8 * kNumSM);
+  launch_k(split_kernel, grid, 256, 0, s, n, v, hi, lo);
+  note_launch();
   return cudaGetLastError();
 }
 
 // p = z + beta p, beta = rz_new / rz_old (flexible: (rz_new - r.z_old) / rz_old);
 // with zold_out the new z is also copied there for the next flexible step
+template <bool VEC>
 __global__ void __launch_bounds__(kRedThreads)
 cg_update_p_kernel(int64_t n, double *__restrict__ p, const double *__restrict__ z,
                    const double *__restrict__ rz_old, const double *__restrict__ rz_partials,
                    const double *__restrict__ rzold_partials, double *__restrict__ rz_out,
-                   int flexible, double *__restrict__ zold_out) {
+                   int flexible, double *__restrict__ zold_out, float *__restrict__ p_hi,
+                   float *__restrict__ p_lo) {
   pdl_entry();
   __shared__ double sh[32];
   const double rz_new = block_sum_partials(rz_partials, kRedBlocks, sh);
@@ -326,23 +426,49 @@ cg_update_p_kernel(int64_t n, double *__restrict__ p, const double *__restrict__
   const double beta = num / rz_old[0];
   if (blockIdx.x == 0 && threadIdx.x == 0) rz_out[0] = rz_new;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  if (zold_out) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-      const double zi = z[i];
-      p[i] = fma(beta, p[i], zi);
-      zold_out[i] = zi;
+  if (VEC) {
+    const int64_t m = n >> 1;
+    double2 *p2 = reinterpret_cast<double2 *>(p);
+    double2 *zo2 = reinterpret_cast<double2 *>(zold_out);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+      const double2 zi = ld2(z, i), pi = p2[i];
+      const double2 pn = make_double2(fma(beta, pi.x, zi.x), fma(beta, pi.y, zi.y));
+      p2[i] = pn;
+      if (zold_out) zo2[i] = zi;
+      if (p_hi) {
+        split_f32(pn.x, p_hi, p_lo, 2 * i);
+        split_f32(pn.y, p_hi, p_lo, 2 * i + 1);
+      }
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+      const double zi = z[n - 1];
+      const double pn = fma(beta, p[n - 1], zi);
+      p[n - 1] = pn;
+      if (zold_out) zold_out[n - 1] = zi;
+      if (p_hi) split_f32(pn, p_hi, p_lo, n - 1);
     }
   } else {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-      p[i] = fma(beta, p[i], z[i]);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      const double zi = z[i];
+      const double pn = fma(beta, p[i], zi);
+      p[i] = pn;
+      if (zold_out) zold_out[i] = zi;
+      if (p_hi) split_f32(pn, p_hi, p_lo, i);
+    }
   }
 }
 
 cudaError_t launch_cg_update_p(int64_t n, double *p, const double *z, const double *rz_old,
                                const double *rz_partials, const double *rzold_partials,
-                               double *rz_out, int flexible, cudaStream_t s, double *zold_out) {
-  launch_k(cg_update_p_kernel, kRedBlocks, kRedThreads, 0, s, n, p, z, rz_old, rz_partials,
-                                                        rzold_partials, rz_out, flexible, zold_out); note_launch();
+                               double *rz_out, int flexible, cudaStream_t s, double *zold_out,
+                               float *p_hi, float *p_lo) {
+  if (al16(p) && al16(z) && (!zold_out || al16(zold_out)))
+    launch_k(cg_update_p_kernel<true>, kRedBlocks, kRedThreads, 0, s, n, p, z, rz_old,
+             rz_partials, rzold_partials, rz_out, flexible, zold_out, p_hi, p_lo);
+  else
+    launch_k(cg_update_p_kernel<false>, kRedBlocks, kRedThreads, 0, s, n, p, z, rz_old,
+             rz_partials, rzold_partials, rz_out, flexible, zold_out, p_hi, p_lo);
+  note_launch();
   return cudaGetLastError();
 }
 

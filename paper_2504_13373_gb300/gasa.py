@@ -42,7 +42,7 @@ GASA_MAX_LEVELS = 24
 EXPORTS = [
     "gasa_default_options", "gasa_create", "gasa_setup", "gasa_solve", "gasa_vcycle",
     "gasa_level_shape", "gasa_tail_info", "gasa_get_level", "gasa_profile_enable", "gasa_profile_read",
-    "gasa_destroy", "gasa_status_string", "gasa_last_error", "gasa_bsr_mv", "gasa_bsr_mv_f32",
+    "gasa_destroy", "gasa_status_string", "gasa_last_error", "gasa_bsr_mv", "gasa_bsr_mv_f32", "gasa_bsr_mv_ds",
     "gasa_jacobi_sweep", "gasa_jacobi_sweep_f32", "gasa_block_inverse", "gasa_power_estimate",
     "gasa_relax_candidates", "gasa_tentative", "gasa_dense_inverse", "gasa_kernel_launches",
     "gasa_power_estimate_noalloc",
@@ -341,6 +341,13 @@ def gasa_bsr_mv_f32(mode, n_brows, br, bc, row_ptr, col, val, x, b, y, stream=No
                                   c_vp(_ptr(row_ptr)), c_vp(_ptr(col)), c_vp(_ptr(val)),
                                   c_vp(_ptr(x)), c_vp(_ptr(b)), c_vp(_ptr(y)),
                                   c_vp(_stream(stream))))
+
+
+def gasa_bsr_mv_ds(n_brows, br, bc, row_ptr, col, a_hi, a_lo, x_hi, x_lo, y, stream=None):
+    _check(load().gasa_bsr_mv_ds(c_i32(n_brows), c_i32(br), c_i32(bc), c_vp(_ptr(row_ptr)),
+                                 c_vp(_ptr(col)), c_vp(_ptr(a_hi)), c_vp(_ptr(a_lo)),
+                                 c_vp(_ptr(x_hi)), c_vp(_ptr(x_lo)), c_vp(_ptr(y)),
+                                 c_vp(_stream(stream))))
 
 
 def gasa_jacobi_sweep(n_units, bs, row_ptr, col, val, W, x, b, x_out, first=False, stream=None):

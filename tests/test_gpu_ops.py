@@ -88,6 +88,39 @@ def test_bsr_mv_fp32(case):
     assert rel_err(to_host(y), want) <= TOL32
 
 
+def _split(v):
+    hi = v.astype(np.float32)
+    lo = (v - hi.astype(np.float64)).astype(np.float32)
+    return hi, lo
+
+
+@pytest.mark.parametrize("case", CASES_MV[:6] + CASES_MV[6:9])
+def test_bsr_mv_double_single(case):
+    """Double-single product from exact FP32 splits of A and x: every entry
+    within 2^-40 of sum |a x| of the FP64 product.  The splits hold a and x to
+    2^-48 and the dropped lo * lo terms are below that; the FP32 low word takes
+    one rounding of at most 2^-24 of its own size (a few 2^-24 of sum |a x|)
+    per term, so n terms stay below n * 2^-47 of sum |a x| (n <= 700 here)."""
+    gasa = _gasa()
+    n, m, br, bc, per, seed = case
+    ptr, col, val = RO.random_bsr(n, m, br, bc, per, seed)
+    x = RO.random_vector(m * bc, seed)
+    S = bsr_scipy(ptr, col, val, m)
+    want = S @ x
+    bound = 2.0 ** -40 * (abs(S) @ np.abs(x)) + 1e-300
+    ah, al = _split(val.ravel())
+    xh, xl = _split(x)
+    y = to_dev(np.zeros(n * br))
+    gasa.gasa_bsr_mv_ds(n, br, bc, to_dev(ptr), to_dev(col), to_dev(ah), to_dev(al), to_dev(xh),
+                        to_dev(xl), y)
+    got = to_host(y)
+    assert np.all(np.abs(got - want) <= bound), np.max(np.abs(got - want) / bound)
+    # the FP32 product alone misses that bound by orders of magnitude
+    y32 = to_dev(np.zeros(n * br, np.float32))
+    gasa.gasa_bsr_mv_f32(0, n, br, bc, to_dev(ptr), to_dev(col), to_dev(ah), to_dev(xh), None, y32)
+    assert np.max(np.abs(to_host(y32) - want) / bound) > 100
+
+
 def test_bsr_mv_workload_matrix():
     """The 32x32 P1 and 32x32 P3 SIPG operators, residual mode."""
     gasa = _gasa()
