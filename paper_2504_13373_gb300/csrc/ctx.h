@@ -93,6 +93,8 @@ struct gasa_ctx {
   double *hscal = nullptr;        // pinned host mirror
   float *kf_in = nullptr, *kf_out = nullptr;
   float *kp_hi = nullptr, *kp_lo = nullptr;   // two-term FP32 split of p (mixed precision)
+  double *pq_ds = nullptr;   // p . Ap partials of the double-single product (one per CTA)
+  int n_pq_ds = 0;
   double *V = nullptr, *Z = nullptr, *H = nullptr, *gm = nullptr, *mpart = nullptr;
   int gm_restart = 0;
   bool gm_flex = false;

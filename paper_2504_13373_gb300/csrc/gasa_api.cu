@@ -435,7 +435,8 @@ gasa_status spmv_outer(gasa_ctx *ctx, int mode, const double *x, const double *b
 
 // q = A p of the mixed-precision Krylov step: double-single arithmetic on
 // the FP32 splits of A (val32 + lo32) and of p (kp_hi + kp_lo, written by the
-// CG update or, with split_p, here)
+// CG update or, with split_p, here); the same launch leaves the partial sums
+// of p . q in ctx->pq_ds
 gasa_status spmv_outer_ds(gasa_ctx *ctx, const double *p, double *q, bool split_p) {
   Level &l = ctx->L[0];
   const int64_t n = l.ndof;
@@ -443,7 +444,7 @@ gasa_status spmv_outer_ds(gasa_ctx *ctx, const double *p, double *q, bool split_
   cudaEvent_t e0;
   prof_begin(ctx, 2, &e0);
   CU(launch_bsr_mv_ds(l.n, l.s, l.s, l.A.rp, l.A.col, l.A.val32, l.A.lo32, ctx->kp_hi,
-                      ctx->kp_lo, q, ctx->stream));
+                      ctx->kp_lo, q, ctx->stream, p, ctx->pq_ds));
   prof_end(ctx, 2, spmv_bytes(l, 8, false));   // 4 + 4 bytes per value and per x entry
   return GASA_OK;
 }
@@ -475,11 +476,14 @@ gasa_status pcg(gasa_ctx *ctx, const double *b, double tol, int precision, int *
   int cur = S_RZ0, nxt = S_RZ1;
   const int max_iter = ctx->opt.max_iter;
   for (int it = 1; it <= max_iter; ++it) {
-    if (flex) ST(spmv_outer_ds(ctx, p, q, true));
-    else ST(spmv_outer(ctx, GASA_MV_ASSIGN, p, nullptr, q));
-    CU(launch_dot_partials(n, p, q, pq_part, s));
-    CU(launch_cg_update_xr(n, x, r, p, q, ctx->scal + cur, pq_part, rr_part, ctx->scal + S_ALPHA,
-                           s));
+    if (flex) {
+      ST(spmv_outer_ds(ctx, p, q, true));
+    } else {
+      ST(spmv_outer(ctx, GASA_MV_ASSIGN, p, nullptr, q));
+      CU(launch_dot_partials(n, p, q, pq_part, s));
+    }
+    CU(launch_cg_update_xr(n, x, r, p, q, ctx->scal + cur, flex ? ctx->pq_ds : pq_part, rr_part,
+                           ctx->scal + S_ALPHA, s, flex ? ctx->n_pq_ds : kRedBlocks));
     CU(launch_finalize(rr_part, 1, ctx->scal + S_RR, s));
     ST(read_scalars(ctx, 0, 3));
     const double pq = ctx->hscal[S_PQ];
@@ -562,16 +566,18 @@ gasa_status build_cg_graph(gasa_ctx *ctx, int precision) {
                              flex ? 1 : 0, s, flex ? zold : nullptr, flex ? ctx->kp_hi : nullptr,
                              flex ? ctx->kp_lo : nullptr);
     Level &l = ctx->L[0];
-    if (e == cudaSuccess && flex)
+    if (e == cudaSuccess && flex) {
+      // q = A p with the p . q partials in the same launch
       e = launch_bsr_mv_ds(l.n, l.s, l.s, l.A.rp, l.A.col, l.A.val32, l.A.lo32, ctx->kp_hi,
-                           ctx->kp_lo, q, s);
-    else if (e == cudaSuccess)
+                           ctx->kp_lo, q, s, p, ctx->pq_ds);
+    } else if (e == cudaSuccess) {
       e = launch_bsr_mv<double>(GASA_MV_ASSIGN, l.n, l.s, l.s, l.A.rp, l.A.col, l.A.val, p, nullptr,
                                 q, s);
-    if (e == cudaSuccess) e = launch_dot_partials(n, p, q, pq_part, s);
+      if (e == cudaSuccess) e = launch_dot_partials(n, p, q, pq_part, s);
+    }
     if (e == cudaSuccess)
-      e = launch_cg_update_xr(n, x, r, p, q, ctx->scal + S_RZ1, pq_part, rr_part,
-                              ctx->scal + S_ALPHA, s);
+      e = launch_cg_update_xr(n, x, r, p, q, ctx->scal + S_RZ1, flex ? ctx->pq_ds : pq_part,
+                              rr_part, ctx->scal + S_ALPHA, s, flex ? ctx->n_pq_ds : kRedBlocks);
     if (e == cudaSuccess) e = launch_cg_check(rr_part, ctx->scal, ctx->d_iters, max_iter, h, s);
   }
   cudaGraph_t captured = nullptr;
@@ -1475,6 +1481,8 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
   ST(dalloc(ctx, &ctx->kf_out, (size_t)n));
   ST(dalloc(ctx, &ctx->kp_hi, (size_t)n));
   ST(dalloc(ctx, &ctx->kp_lo, (size_t)n));
+  ctx->n_pq_ds = bsr_mv_ds_grid(ctx->L[0].n, ctx->L[0].s);
+  ST(dalloc(ctx, &ctx->pq_ds, (size_t)ctx->n_pq_ds));
   ST(dalloc(ctx, &ctx->d_iters, 4));
   ST(dalloc(ctx, &ctx->d_err, 4));
   CU(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));

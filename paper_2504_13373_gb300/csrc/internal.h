@@ -69,10 +69,14 @@ cudaError_t launch_bsr_mm(int n_brows, int br, int bc, const int *rp, const int 
                           int64_t ldy, int ncols, cudaStream_t s);
 
 // y = A x (FP64 out) in double-single arithmetic from exact two-term FP32
-// splits of A (hi, lo) and x (hi, lo)
+// splits of A (hi, lo) and x (hi, lo); with xd and partials also the
+// bsr_mv_ds_grid(n_brows, br) partial sums of xd . y (16-byte aligned
+// operands only, else cudaErrorNotSupported)
 cudaError_t launch_bsr_mv_ds(int n_brows, int br, int bc, const int *rp, const int *col,
                              const float *ahi, const float *alo, const float *xhi,
-                             const float *xlo, double *y, cudaStream_t s);
+                             const float *xlo, double *y, cudaStream_t s,
+                             const double *xd = nullptr, double *partials = nullptr);
+int bsr_mv_ds_grid(int n_brows, int br);
 
 // y = A x for a dense row-major n x n matrix
 template <typename T>
@@ -108,7 +112,8 @@ cudaError_t launch_add(int64_t n, const T *x, T *y, cudaStream_t s);
 // CG pieces (device scalars; partial arrays of kRedBlocks entries)
 cudaError_t launch_cg_update_xr(int64_t n, double *x, double *r, const double *p,
                                 const double *q, const double *rz, const double *pq_partials,
-                                double *rr_partials, double *alpha_out, cudaStream_t s);
+                                double *rr_partials, double *alpha_out, cudaStream_t s,
+                                int n_pq);
 cudaError_t launch_cg_update_p(int64_t n, double *p, const double *z, const double *rz_old,
                                const double *rz_partials, const double *rzold_partials,
                                double *rz_out, int flexible, cudaStream_t s,

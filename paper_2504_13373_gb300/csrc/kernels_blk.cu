@@ -57,6 +57,19 @@ bsr_blk_kernel(int n_brows, const int *__restrict__ rp, const int *__restrict__ 
   T acc[S];
 #pragma unroll
   for (int r = 0; r < S; ++r) acc[r] = T(0);
+  // the epilogue's operands (row l of W_u, b_u, x_t) do not depend on the
+  // product: lanes l < S load them first so that their latency overlaps the
+  // block loop instead of following it
+  const bool writer = u < n_brows && l < S;
+  const size_t t = (size_t)u * S + l;
+  T bv[S], wv[S], xt = T(0), bt = T(0), yt = T(0);
+  if (OP == BLK_SWEEP && writer) {
+    load_run<T, S>(b + (size_t)u * S, bv);
+    load_run<T, S>(Wm + t * S, wv);
+    xt = x[t];
+  }
+  if (OP == BLK_RESID && writer) bt = b[t];
+  if (OP == BLK_ADD && writer) yt = y[t];
   if (u < n_brows) {
     const int beg = __ldg(rp + u), end = __ldg(rp + u + 1);
     int k = beg + l;
@@ -116,18 +129,13 @@ bsr_blk_kernel(int n_brows, const int *__restrict__ rp, const int *__restrict__ 
       acc[r] = v;
     }
   }
-  if (u >= n_brows || l >= S) return;
+  if (!writer) return;
   // lane l < S of the team writes row l
-  const size_t t = (size_t)u * S + l;
   if (OP == BLK_SWEEP) {
-    T bv[S];
-    load_run<T, S>(b + (size_t)u * S, bv);
-    T wv[S];
-    load_run<T, S>(Wm + t * S, wv);
     T out = T(0);
 #pragma unroll
     for (int c = 0; c < S; ++c) out = fma(wv[c], bv[c] - acc[c], out);
-    y[t] = x[t] + out;
+    y[t] = xt + out;
     return;
   }
   T v = T(0);
@@ -135,8 +143,8 @@ bsr_blk_kernel(int n_brows, const int *__restrict__ rp, const int *__restrict__ 
   for (int r = 0; r < S; ++r)
     if (r == l) v = acc[r];
   if (OP == BLK_ASSIGN) y[t] = v;
-  else if (OP == BLK_RESID) y[t] = b[t] - v;
-  else y[t] += v;
+  else if (OP == BLK_RESID) y[t] = bt - v;
+  else y[t] = yt + v;
 }
 
 // Lanes per block row: about 2.5 blocks per lane (two in flight, a short

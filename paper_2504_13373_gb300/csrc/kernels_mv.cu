@@ -330,19 +330,23 @@ template cudaError_t launch_bsr_mv<float>(int, int, int, int, const int *, const
 // matrix, more than that rate feeds at full HBM bandwidth.  The __f*_rn
 // intrinsics keep the compiler from contracting the two-sum into FMAs.
 // ----------------------------------------------------------------------------
-template <int BC>
+// With DOT the kernel also leaves per-CTA partial sums of x . y (x given in
+// FP64 as xd) in partials[blockIdx.x], summed in a fixed order.
+template <int BC, bool DOT>
 __global__ void __launch_bounds__(256)
 bsr_mv_ds_kernel(int n_brows, int br, const int *__restrict__ rp, const int *__restrict__ col,
                  const float *__restrict__ ahi, const float *__restrict__ alo,
                  const float *__restrict__ xhi, const float *__restrict__ xlo,
-                 double *__restrict__ y) {
+                 double *__restrict__ y, const double *__restrict__ xd,
+                 double *__restrict__ partials) {
   pdl_entry();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)n_brows * br) return;
-  const int i = (int)(t / br);
-  const int r = (int)(t - (long long)i * br);
+  const bool act = t < (long long)n_brows * br;
+  const int i = act ? (int)(t / br) : 0;
+  const int r = act ? (int)(t - (long long)i * br) : 0;
   constexpr int W = RowVec<float, BC>::value;
-  const int beg = __ldg(rp + i), end = __ldg(rp + i + 1);
+  const int beg = act ? __ldg(rp + i) : 0, end = act ? __ldg(rp + i + 1) : 0;
+  const double xt = (DOT && act) ? xd[t] : 0.0;
   float s = 0.0f, lo = 0.0f;
   for (int k = beg; k < end; ++k) {
     const int j = __ldg(col + k);
@@ -368,7 +372,13 @@ bsr_mv_ds_kernel(int n_brows, int br, const int *__restrict__ rp, const int *__r
       lo = __fadd_rn(lo, __fadd_rn(err, __fadd_rn(e, cross)));
     }
   }
-  y[t] = (double)s + (double)lo;
+  const double yt = (double)s + (double)lo;
+  if (act) y[t] = yt;
+  if (DOT) {
+    __shared__ double sh[32];
+    const double v = block_sum(xt * yt, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+  }
 }
 
 __global__ void __launch_bounds__(256)
@@ -402,18 +412,28 @@ bsr_mv_ds_generic(int n_brows, int br, int bc, const int *__restrict__ rp,
   y[t] = (double)s + (double)lo;
 }
 
+int bsr_mv_ds_grid(int n_brows, int br) { return div_up((long long)n_brows * br, 256); }
+
 cudaError_t launch_bsr_mv_ds(int n_brows, int br, int bc, const int *rp, const int *col,
                              const float *ahi, const float *alo, const float *xhi,
-                             const float *xlo, double *y, cudaStream_t s) {
+                             const float *xlo, double *y, cudaStream_t s, const double *xd,
+                             double *partials) {
   const long long rows = (long long)n_brows * br;
   if (rows == 0) return cudaSuccess;
   const int grid = div_up(rows, 256);
   const bool al = aligned16(ahi) && aligned16(alo) && aligned16(xhi) && aligned16(xlo);
+  const bool dot = xd && partials;
 #define GASA_DS_CASE(BC)                                                                    \
   case BC:                                                                                  \
-    launch_k(bsr_mv_ds_kernel<BC>, grid, 256, 0, s, n_brows, br, rp, col, ahi, alo, xhi, xlo, y); \
+    if (dot)                                                                                \
+      launch_k(bsr_mv_ds_kernel<BC, true>, grid, 256, 0, s, n_brows, br, rp, col, ahi, alo, xhi, \
+               xlo, y, xd, partials);                                                       \
+    else                                                                                    \
+      launch_k(bsr_mv_ds_kernel<BC, false>, grid, 256, 0, s, n_brows, br, rp, col, ahi, alo, xhi, \
+               xlo, y, xd, partials);                                                       \
     note_launch();                                                                          \
     return cudaGetLastError();
+  if (dot && !al) return cudaErrorNotSupported;
   if (al) {
     switch (bc) {
       GASA_DS_CASE(1) GASA_DS_CASE(2) GASA_DS_CASE(3) GASA_DS_CASE(4) GASA_DS_CASE(5)
@@ -451,10 +471,17 @@ jacobi_kernel(int n_units, const int *__restrict__ rp, const int *__restrict__ c
   const int i = blockIdx.x * RPB + li;
   const bool active = (li < RPB) && (i < n_units);
   const size_t row = (size_t)i * BS + r;
-  T v = T(0);
+  const T *w = Wm + row * BS;
+  T v = T(0), b_row = T(0), x_row = T(0);
   if (active) {
+    // operands of the epilogue first: b and x of this row into registers and
+    // this row of W into L2, so that their latency overlaps the block loop
+    if (MODE == JAC_SWEEP || MODE == JAC_FIRST) b_row = b[row];
+    if (MODE == JAC_SWEEP || MODE == JAC_RELAX) x_row = x[row];
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(w));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(w + BS - 1));
     if (MODE == JAC_FIRST) {
-      v = b[row];
+      v = b_row;
     } else {
       const int beg = __ldg(rp + i), end = __ldg(rp + i + 1);
       T acc = T(0);
@@ -470,7 +497,7 @@ jacobi_kernel(int n_units, const int *__restrict__ rp, const int *__restrict__ c
 #pragma unroll
         for (int c = 0; c < BS; ++c) acc = fma(av[c], xv[c], acc);
       }
-      if (MODE == JAC_SWEEP) v = b[row] - acc;
+      if (MODE == JAC_SWEEP) v = b_row - acc;
       else if (MODE == JAC_RELAX) v = -acc;
       else v = acc;
     }
@@ -478,14 +505,13 @@ jacobi_kernel(int n_units, const int *__restrict__ rp, const int *__restrict__ c
   res[threadIdx.x] = v;
   __syncthreads();
   if (!active) return;
-  const T *w = Wm + row * BS;
   T wv[BS];
 #pragma unroll
   for (int c = 0; c < BS; c += W) load_vec_stream<T, W>(w + c, wv + c);
   T out = T(0);
 #pragma unroll
   for (int c = 0; c < BS; ++c) out = fma(wv[c], res[li * BS + c], out);
-  if (MODE == JAC_SWEEP || MODE == JAC_RELAX) out += x[row];
+  if (MODE == JAC_SWEEP || MODE == JAC_RELAX) out += x_row;
   xo[row] = out;
 }
 

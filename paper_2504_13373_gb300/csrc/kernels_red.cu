@@ -303,10 +303,10 @@ __global__ void __launch_bounds__(kRedThreads)
 cg_update_xr_kernel(int64_t n, double *__restrict__ x, double *__restrict__ r,
                     const double *__restrict__ p, const double *__restrict__ q,
                     const double *__restrict__ rz, const double *__restrict__ pq_partials,
-                    double *__restrict__ rr_partials, double *__restrict__ alpha_out) {
+                    double *__restrict__ rr_partials, double *__restrict__ alpha_out, int n_pq) {
   pdl_entry();
   __shared__ double sh[32];
-  const double pq = block_sum_partials(pq_partials, kRedBlocks, sh);
+  const double pq = block_sum_partials(pq_partials, n_pq, sh);
   const double alpha = rz[0] / pq;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     alpha_out[0] = alpha;
@@ -374,13 +374,13 @@ cg_update_xr_kernel(int64_t n, double *__restrict__ x, double *__restrict__ r,
 
 cudaError_t launch_cg_update_xr(int64_t n, double *x, double *r, const double *p,
                                 const double *q, const double *rz, const double *pq_partials,
-                                double *rr_partials, double *alpha_out, cudaStream_t s) {
+                                double *rr_partials, double *alpha_out, cudaStream_t s, int n_pq) {
   if (al16(x) && al16(r) && al16(p) && al16(q))
     launch_k(cg_update_xr_kernel<true>, kRedBlocks, kRedThreads, 0, s, n, x, r, p, q, rz,
-             pq_partials, rr_partials, alpha_out);
+             pq_partials, rr_partials, alpha_out, n_pq);
   else
     launch_k(cg_update_xr_kernel<false>, kRedBlocks, kRedThreads, 0, s, n, x, r, p, q, rz,
-             pq_partials, rr_partials, alpha_out);
+             pq_partials, rr_partials, alpha_out, n_pq);
   note_launch();
   return cudaGetLastError();
 }
