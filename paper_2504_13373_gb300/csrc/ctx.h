@@ -114,6 +114,7 @@ struct gasa_ctx {
   int tail_k0[2] = {0, 0};
   int tail_coarse[2] = {0, 0};   // 1: the coarsest solve runs inside the launch
   int tail_cluster[2] = {0, 0};  // CTAs per cluster
+  int tail_smem[2] = {0, 0};     // dynamic shared memory per CTA
   // profiling
   bool prof = false;
   ProfClass pc[4];

@@ -199,7 +199,9 @@ double spmv_bytes(const Level &l, int w, bool residual, int wa = 0) {
 
 // Plan of the fused bottom of the V-cycle for precision T (slot pi: 0 FP64,
 // 1 FP32): the deepest run of levels k >= 1 whose A_k is stored and takes at
-// most opt.tail_kib KiB, with every level below it down to the coarsest.
+// most opt.tail_kib KiB, with every level below it down to the coarsest,
+// while the coarsest inverse is small (2 MB) and the levels' vectors fit in
+// the cluster's shared memory.
 template <typename T>
 gasa_status tail_build(gasa_ctx *ctx, int pi) {
   using P = Prec<T>;
@@ -208,6 +210,8 @@ gasa_status tail_build(gasa_ctx *ctx, int pi) {
   ctx->tail_plan[pi] = nullptr;
   const int64_t limit = (int64_t)ctx->opt.tail_kib * 1024;
   if (limit <= 0 || N < 2) return GASA_OK;
+  if ((int64_t)ctx->nc * ctx->nc * 8 > (2 << 20)) return GASA_OK;
+  Level &lc = ctx->L[N];
   int k0 = N;
   for (int k = N - 1; k >= 1; --k) {
     Level &l = ctx->L[k];
@@ -221,17 +225,32 @@ gasa_status tail_build(gasa_ctx *ctx, int pi) {
   if (k0 == N) return GASA_OK;
   const int cl = tail_cluster_size<T>();
   if (cl == 0) return GASA_OK;
+  const int nw = cl * kTailWarps;
+  // distributed vector layout, dropping top levels until it fits
+  auto vec_bytes = [&](int n, int s) {
+    const int64_t b = (int64_t)tail_slots(n, nw) * s * (int64_t)sizeof(T);
+    return (b + 15) / 16 * 16;
+  };
+  auto layout_bytes = [&](int first) {
+    int64_t b = 2 * vec_bytes(lc.n, lc.s);
+    for (int k = first; k < N; ++k) b += 4 * vec_bytes(ctx->L[k].n, ctx->L[k].s);
+    return b;
+  };
+  while (k0 < N && layout_bytes(k0) > tail_smem_limit()) ++k0;
+  if (k0 == N) return GASA_OK;
   TailPlan<T> h;
   h.k0 = k0;
   h.nlev = N - k0;
   h.tpre = ctx->opt.t_pre;
   h.tpost = ctx->opt.t_post;
   h.nc = ctx->nc;
-  // the coarsest inverse joins the launch while it is small (2 MB)
-  const bool coarse_in = (int64_t)ctx->nc * ctx->nc * 8 <= (2 << 20);
-  h.Cinv = coarse_in ? ctx->coarse_inv : nullptr;
-  h.bN = P::b(ctx->L[N]);
-  h.xN = P::x(ctx->L[N]);
+  h.nN = lc.n;
+  h.sN = lc.s;
+  h.Cinv = ctx->coarse_inv;
+  h.nw = nw;
+  h.b_in = P::b(ctx->L[k0]);
+  h.x_out = P::x(ctx->L[k0]);
+  int64_t off = 0;
   bool al = true;
   auto chk = [&](const void *p) {
     if (p && ((uintptr_t)p & 15u)) al = false;
@@ -253,15 +272,18 @@ gasa_status tail_build(gasa_ctx *ctx, int pi) {
     t.Rrp = l.R.rp;
     t.Rcol = l.R.col;
     t.R = P::A(l.R);
-    t.x = P::x(l);
-    t.x2 = P::x2(l);
-    t.b = P::b(l);
-    t.r = P::r(l);
-    for (const void *p : {(const void *)t.A, (const void *)t.P, (const void *)t.R,
-                          (const void *)t.x, (const void *)t.x2, (const void *)t.r})
-      chk(p);
+    const int64_t vb = vec_bytes(l.n, l.s);
+    t.off_x = (int)off;
+    t.off_x2 = (int)(off + vb);
+    t.off_b = (int)(off + 2 * vb);
+    t.off_r = (int)(off + 3 * vb);
+    off += 4 * vb;
+    for (const void *p : {(const void *)t.A, (const void *)t.P, (const void *)t.R}) chk(p);
   }
-  chk(h.xN);
+  h.off_bN = (int)off;
+  h.off_xN = (int)(off + vec_bytes(lc.n, lc.s));
+  off += 2 * vec_bytes(lc.n, lc.s);
+  h.smem_bytes = (int)off;
   h.vec = al ? 1 : 0;
   unsigned char *d = nullptr;
   ST(dalloc(ctx, &d, sizeof(TailPlan<T>)));
@@ -269,8 +291,9 @@ gasa_status tail_build(gasa_ctx *ctx, int pi) {
   CU(cudaStreamSynchronize(ctx->stream));
   ctx->tail_plan[pi] = d;
   ctx->tail_k0[pi] = k0;
-  ctx->tail_coarse[pi] = coarse_in ? 1 : 0;
+  ctx->tail_coarse[pi] = 1;
   ctx->tail_cluster[pi] = cl;
+  ctx->tail_smem[pi] = h.smem_bytes;
   return GASA_OK;
 }
 
@@ -356,18 +379,10 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false) {
   Level &lc = ctx->L[N];
   if (kt < N) {
     // levels kt .. N-1 and the coarsest solve (FP64 arithmetic) in one
-    // cluster launch, or two around a whole-GPU coarsest solve
+    // cluster launch; it leaves the corrected x_kt in L[kt]'s x
     const TailPlan<T> *pl = static_cast<const TailPlan<T> *>(ctx->tail_plan[pi]);
-    const int cl = ctx->tail_cluster[pi];
-    if (ctx->tail_coarse[pi]) {
-      CU(launch_vcycle_tail<T>(pl, TAIL_ALL, cl, s));
-    } else {
-      CU(launch_vcycle_tail<T>(pl, TAIL_DOWN, cl, s));
-      CU(launch_dense_mv<T>(ctx->nc, ctx->coarse_inv, P::b(lc), P::x(lc), s));
-      CU(launch_vcycle_tail<T>(pl, TAIL_UP, cl, s));
-    }
-    Level &lt = ctx->L[kt];
-    xk[kt] = tail_final_buffer(ctx->opt.t_pre, ctx->opt.t_post) ? P::x2(lt) : P::x(lt);
+    CU(launch_vcycle_tail<T>(pl, ctx->tail_cluster[pi], ctx->tail_smem[pi], s));
+    xk[kt] = P::x(ctx->L[kt]);
   } else {
     // coarsest solve in FP64
     CU(launch_dense_mv<T>(ctx->nc, ctx->coarse_inv, P::b(lc), P::x(lc), s));

@@ -9,13 +9,15 @@
 // coarsest dense solve and the way back up, with a hardware cluster barrier
 // between dependent steps.
 //
-// Warp w of the cluster owns block rows w, w + NW, ... of every operator, so
-// a warp reads the same matrix rows in every pass and, after the first pass,
-// finds them in its SM's L1.  Vectors written inside the launch are read
-// through L2 (ld.global.cg); the release/acquire cluster barrier makes each
-// step's writes visible to the next step.  Arithmetic per output row: the
-// sum over the row's blocks in a fixed order, so results do not depend on
-// timing.
+// Vectors live in the cluster's distributed shared memory: warp w of the
+// cluster owns units w, w + NW, ... of every level and keeps their entries
+// of x, x2, b and r in its CTA's shared memory.  A step reads the owned
+// unit's own entries locally, gathers neighbour units' entries from the
+// owning CTAs with ld.shared::cluster, and writes only owned entries, so the
+// release/acquire cluster barrier between steps is the only synchronisation
+// and no vector crosses L2.  Matrix values never change in a launch and are
+// read through L1.  Arithmetic per output row: the sum over the row's blocks
+// in a fixed order, so results do not depend on timing.
 #include "common.cuh"
 #include "internal.h"
 #include "tail.h"
@@ -24,9 +26,9 @@ namespace gasa {
 
 namespace {
 
-constexpr int kTailThreads = 512;
-constexpr int kTailWarps = kTailThreads / 32;
 constexpr int kTailMaxS = 64;
+
+extern __shared__ __align__(16) unsigned char tail_smem[];
 
 __device__ __forceinline__ unsigned cl_rank() {
   unsigned r;
@@ -38,7 +40,7 @@ __device__ __forceinline__ unsigned cl_size() {
   asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
   return r;
 }
-// Every thread of every CTA of the cluster arrives; global-memory writes made
+// Every thread of every CTA of the cluster arrives; shared-memory writes made
 // before the barrier are visible to all threads of the cluster after it.
 __device__ __forceinline__ void cl_sync() {
   __syncwarp();   // the .aligned barrier wants every warp converged
@@ -49,6 +51,53 @@ __device__ __forceinline__ void cl_sync() {
 
 __device__ __forceinline__ int pow2_at_least(int v) {   // 1 <= v <= 32
   return v <= 1 ? 1 : 1 << (32 - __clz(v - 1));
+}
+
+// distributed vector layout (see tail.h)
+struct Dist {
+  uint32_t sbase;   // shared-window address of tail_smem in this CTA
+  int NW;
+};
+__device__ __forceinline__ int d_slot(int j, int NW) { return (j / NW) * kTailWarps + (j % kTailWarps); }
+__device__ __forceinline__ int d_owner(int j, int NW) { return (j % NW) / kTailWarps; }
+template <typename T>
+__device__ __forceinline__ T *d_local(int off, int j, int s, int NW) {
+  return reinterpret_cast<T *>(tail_smem + off) + (size_t)d_slot(j, NW) * s;
+}
+// shared::cluster address of entry 0 of unit j (s entries of esize bytes)
+__device__ __forceinline__ uint32_t d_remote(const Dist &d, int off, int j, int s, int esize) {
+  const uint32_t la = d.sbase + (uint32_t)off + (uint32_t)(d_slot(j, d.NW) * s * esize);
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(la), "r"(d_owner(j, d.NW)));
+  return ra;
+}
+
+template <typename V>
+__device__ __forceinline__ V ld_cl(uint32_t a);
+template <>
+__device__ __forceinline__ float ld_cl<float>(uint32_t a) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+  return v;
+}
+template <>
+__device__ __forceinline__ double ld_cl<double>(uint32_t a) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+  return v;
+}
+template <>
+__device__ __forceinline__ float4 ld_cl<float4>(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a) : "memory");
+  return v;
+}
+template <>
+__device__ __forceinline__ double2 ld_cl<double2>(uint32_t a) {
+  double2 v;
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a) : "memory");
+  return v;
 }
 
 template <typename T, int VW>
@@ -75,14 +124,14 @@ __device__ __forceinline__ T vdot(T a, T x, T acc) { return fma(a, x, acc); }
 
 // Rows r0 .. r0 + gs - 1 of one block row (gs a power of two <= 32): lane
 // (g, q) takes row r0 + q of blocks beg + g, beg + g + G, ... (G = 32 / gs),
-// four blocks at a time so that four gathers of x are in flight; an
-// xor-shuffle over the group bits then leaves the sum of row r0 + (lane % gs)
-// in every lane.  Matrix values are read through L1 (they never change in a
-// launch), x through L2.
+// four blocks at a time so that four gathers are in flight; an xor-shuffle
+// over the group bits then leaves the sum of row r0 + (lane % gs) in every
+// lane.  x is the distributed vector at byte offset xoff (bc entries per
+// unit).
 template <typename T, int VW>
 __device__ __forceinline__ T tail_rows(int beg, int end, int br, int bc, int r0, int gs,
                                        const int *__restrict__ col, const T *__restrict__ val,
-                                       const T *x, int lane) {
+                                       const Dist &d, int xoff, int lane) {
   using V = typename TailVec<T, VW>::V;
   const int q = lane & (gs - 1), g = lane / gs, G = 32 / gs;
   const int r = r0 + q;
@@ -91,12 +140,12 @@ __device__ __forceinline__ T tail_rows(int beg, int end, int br, int bc, int r0,
     int k = beg + g;
     for (; k + 3 * G < end; k += 4 * G) {
       const V *a[4];
-      const V *xx[4];
+      uint32_t xa[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int kk = k + u * G;
         a[u] = reinterpret_cast<const V *>(val + ((size_t)kk * br + r) * bc);
-        xx[u] = reinterpret_cast<const V *>(x + (size_t)__ldg(col + kk) * bc);
+        xa[u] = d_remote(d, xoff, __ldg(col + kk), bc, (int)sizeof(T));
       }
       T s[4] = {T(0), T(0), T(0), T(0)};
       for (int c = 0; c < bc / VW; ++c) {
@@ -104,7 +153,7 @@ __device__ __forceinline__ T tail_rows(int beg, int end, int br, int bc, int r0,
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           av[u] = __ldg(a[u] + c);
-          xv[u] = __ldcg(xx[u] + c);
+          xv[u] = ld_cl<V>(xa[u] + c * (uint32_t)sizeof(V));
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) s[u] = vdot<T>(av[u], xv[u], s[u]);
@@ -113,9 +162,10 @@ __device__ __forceinline__ T tail_rows(int beg, int end, int br, int bc, int r0,
     }
     for (; k < end; k += G) {
       const V *a = reinterpret_cast<const V *>(val + ((size_t)k * br + r) * bc);
-      const V *xx = reinterpret_cast<const V *>(x + (size_t)__ldg(col + k) * bc);
+      const uint32_t xa = d_remote(d, xoff, __ldg(col + k), bc, (int)sizeof(T));
       T s = T(0);
-      for (int c = 0; c < bc / VW; ++c) s = vdot<T>(__ldg(a + c), __ldcg(xx + c), s);
+      for (int c = 0; c < bc / VW; ++c)
+        s = vdot<T>(__ldg(a + c), ld_cl<V>(xa + c * (uint32_t)sizeof(V)), s);
       acc += s;
     }
   }
@@ -126,35 +176,38 @@ __device__ __forceinline__ T tail_rows(int beg, int end, int br, int bc, int r0,
 template <typename T>
 __device__ __forceinline__ T tail_rows_any(int beg, int end, int br, int bc, int r0, int gs,
                                            const int *__restrict__ col,
-                                           const T *__restrict__ val, const T *x, bool vec,
-                                           int lane) {
+                                           const T *__restrict__ val, const Dist &d, int xoff,
+                                           bool vec, int lane) {
   constexpr int VW = 16 / (int)sizeof(T);
-  if (vec && bc % VW == 0) return tail_rows<T, VW>(beg, end, br, bc, r0, gs, col, val, x, lane);
-  return tail_rows<T, 1>(beg, end, br, bc, r0, gs, col, val, x, lane);
+  if (vec && bc % VW == 0) return tail_rows<T, VW>(beg, end, br, bc, r0, gs, col, val, d, xoff, lane);
+  return tail_rows<T, 1>(beg, end, br, bc, r0, gs, col, val, d, xoff, lane);
 }
 
 enum { OP_SWEEP = 0, OP_FIRST = 1, OP_RESID = 2, OP_ASSIGN = 3, OP_ADD = 4 };
 
-// y = M x (ASSIGN), y = b - M x (RESID) or y += M x (ADD) for n block rows of
-// br x bc blocks, a warp per block row
+// y = M x (ASSIGN), y = b - M x (RESID) or y += M x (ADD) for the n block
+// rows of br x bc blocks of M, a warp per owned block row; x is the
+// distributed vector at xoff (bc per unit), b and y at boff / yoff (br per
+// unit, owned entries only)
 template <typename T>
 __device__ void tail_mv(int op, int n, int br, int bc, const int *__restrict__ rp,
-                        const int *__restrict__ col, const T *__restrict__ val, const T *x,
-                        const T *b, T *y, bool vec, int gw, int NW, int lane) {
-  for (int u = gw; u < n; u += NW) {
+                        const int *__restrict__ col, const T *__restrict__ val, const Dist &d,
+                        int xoff, int boff, int yoff, bool vec, int gw, int lane) {
+  for (int u = gw; u < n; u += d.NW) {
     const int beg = __ldg(rp + u), end = __ldg(rp + u + 1);
+    T *y = d_local<T>(yoff, u, br, d.NW);
     for (int r0 = 0; r0 < br; r0 += 32) {
       const int rem = br - r0;
       const int gs = rem >= 32 ? 32 : pow2_at_least(rem);
-      const T v = tail_rows_any<T>(beg, end, br, bc, r0, gs, col, val, x, vec, lane);
+      const T v = tail_rows_any<T>(beg, end, br, bc, r0, gs, col, val, d, xoff, vec, lane);
       const int r = r0 + lane;
       if (lane < gs && r < br) {
-        const size_t t = (size_t)u * br + r;
-        if (op == OP_ASSIGN) y[t] = v;
-        else if (op == OP_RESID) y[t] = __ldcg(b + t) - v;
-        else y[t] = __ldcg(y + t) + v;
+        if (op == OP_ASSIGN) y[r] = v;
+        else if (op == OP_RESID) y[r] = d_local<T>(boff, u, br, d.NW)[r] - v;
+        else y[r] += v;
       }
     }
+    __syncwarp();
   }
 }
 
@@ -162,121 +215,150 @@ __device__ void tail_mv(int op, int n, int br, int bc, const int *__restrict__ r
 // (SWEEP) or xo = W b (FIRST, from x = 0).  The block row's residual meets
 // in the warp's shared-memory row `res`, then lane r applies row r of W_u.
 template <typename T>
-__device__ void tail_jacobi(int op, const TailLevel<T> &L, const T *x, T *xo, bool vec, int gw,
-                            int NW, int lane, T *res) {
+__device__ void tail_jacobi(int op, const TailLevel<T> &L, int xoff, int ooff, const Dist &d,
+                            bool vec, int gw, int lane, T *res) {
   const int s = L.s;
-  for (int u = gw; u < L.n; u += NW) {
+  for (int u = gw; u < L.n; u += d.NW) {
     int beg = 0, end = 0;
     if (op == OP_SWEEP) {
       beg = __ldg(L.rp + u);
       end = __ldg(L.rp + u + 1);
     }
+    const T *bu = d_local<T>(L.off_b, u, s, d.NW);
     for (int r0 = 0; r0 < s; r0 += 32) {
       const int rem = s - r0;
       const int gs = rem >= 32 ? 32 : pow2_at_least(rem);
       T v = T(0);
-      if (op == OP_SWEEP) v = tail_rows_any<T>(beg, end, s, s, r0, gs, L.col, L.A, x, vec, lane);
+      if (op == OP_SWEEP)
+        v = tail_rows_any<T>(beg, end, s, s, r0, gs, L.col, L.A, d, xoff, vec, lane);
       const int r = r0 + lane;
-      if (lane < gs && r < s) res[r] = __ldcg(L.b + (size_t)u * s + r) - v;
+      if (lane < gs && r < s) res[r] = bu[r] - v;
     }
     __syncwarp();
+    const T *xu = d_local<T>(xoff, u, s, d.NW);
+    T *ou = d_local<T>(ooff, u, s, d.NW);
     for (int r = lane; r < s; r += 32) {
-      const size_t t = (size_t)u * s + r;
-      const T *w = L.W + t * s;
+      const T *w = L.W + ((size_t)u * s + r) * s;
       T out = T(0);
       for (int c = 0; c < s; ++c) out = fma(__ldg(w + c), res[c], out);
-      if (op == OP_SWEEP) out += __ldcg(x + t);
-      xo[t] = out;
+      if (op == OP_SWEEP) out += xu[r];
+      ou[r] = out;
     }
     __syncwarp();
   }
 }
 
-// x_N = A_N^{-1} b_N in FP64 arithmetic, a warp per row (the same order as
-// dense_mv_kernel)
+// x_N = A_N^{-1} b_N in FP64 arithmetic, a warp per owned coarse unit and,
+// for each of its rows, lanes over the columns (the order of dense_mv_kernel)
 template <typename T>
-__device__ void tail_dense(int nc, const double *__restrict__ C, const T *b, T *x, int gw, int NW,
-                           int lane) {
-  for (int i = gw; i < nc; i += NW) {
-    const double *a = C + (size_t)i * nc;
-    double acc = 0.0;
-    for (int j = lane; j < nc; j += 32) acc = fma(__ldg(a + j), (double)__ldcg(b + j), acc);
-    acc = warp_sum(acc);
-    if (lane == 0) x[i] = (T)acc;
+__device__ void tail_dense(const TailPlan<T> &pl, const Dist &d, int gw, int lane) {
+  const int nc = pl.nc, sN = pl.sN;
+  for (int u = gw; u < pl.nN; u += d.NW) {
+    T *xu = d_local<T>(pl.off_xN, u, sN, d.NW);
+    for (int rr = 0; rr < sN; ++rr) {
+      const double *a = pl.Cinv + (size_t)(u * sN + rr) * nc;
+      double acc = 0.0;
+      for (int j = lane; j < nc; j += 32) {
+        const uint32_t bj = d_remote(d, pl.off_bN, j / sN, sN, (int)sizeof(T)) +
+                            (uint32_t)((j % sN) * (int)sizeof(T));
+        acc = fma(__ldg(a + j), (double)ld_cl<T>(bj), acc);
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) xu[rr] = (T)acc;
+    }
+    __syncwarp();
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kTailThreads, 1)
-vcycle_tail_kernel(const TailPlan<T> *__restrict__ pl, int part) {
+vcycle_tail_kernel(const TailPlan<T> *__restrict__ plp) {
   pdl_entry();
   __shared__ T res_all[kTailWarps][kTailMaxS];
+  const TailPlan<T> &pl = *plp;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int ncta = (int)cl_size();
-  const int NW = ncta * kTailWarps;
+  Dist d;
+  d.sbase = (uint32_t)__cvta_generic_to_shared(tail_smem);
+  d.NW = (int)cl_size() * kTailWarps;
   const int gw = (int)cl_rank() * kTailWarps + wib;
   T *res = res_all[wib];
-  const int nl = pl->nlev, tpre = pl->tpre, tpost = pl->tpost;
-  const bool vec = pl->vec != 0;
-  const int pre = tail_pre_buffer(tpre), fin = tail_final_buffer(tpre, tpost);
-  if (part != TAIL_UP) {
+  const int nl = pl.nlev, tpre = pl.tpre, tpost = pl.tpost;
+  const bool vec = pl.vec != 0;
+  const bool launch_ok = d.NW == pl.nw;   // the layout was made for this cluster size
+  // b_{k0} from global memory into the owners' shared memory
+  {
+    const TailLevel<T> &L = pl.lv[0];
+    for (int u = gw; launch_ok && u < L.n; u += d.NW) {
+      T *bu = d_local<T>(L.off_b, u, L.s, d.NW);
+      for (int r = lane; r < L.s; r += 32) bu[r] = pl.b_in[(size_t)u * L.s + r];
+    }
+    __syncwarp();
+  }
+  if (launch_ok) {
+    // down: pre-smoothing, residual, restriction
     for (int q = 0; q < nl; ++q) {
-      const TailLevel<T> &L = pl->lv[q];
-      T *cur = L.x, *oth = L.x2;
+      const TailLevel<T> &L = pl.lv[q];
+      int cur = L.off_x, oth = L.off_x2;
       if (tpre == 0) {
-        const size_t nd = (size_t)L.n * L.s;
-        for (size_t i = (size_t)cl_rank() * kTailThreads + threadIdx.x; i < nd;
-             i += (size_t)ncta * kTailThreads)
-          cur[i] = T(0);
+        for (int u = gw; u < L.n; u += d.NW) {
+          T *xu = d_local<T>(cur, u, L.s, d.NW);
+          for (int r = lane; r < L.s; r += 32) xu[r] = T(0);
+        }
       } else {
-        tail_jacobi<T>(OP_FIRST, L, nullptr, cur, vec, gw, NW, lane, res);
+        tail_jacobi<T>(OP_FIRST, L, cur, cur, d, vec, gw, lane, res);
       }
       cl_sync();
       for (int t = 1; t < tpre; ++t) {
-        tail_jacobi<T>(OP_SWEEP, L, cur, oth, vec, gw, NW, lane, res);
+        tail_jacobi<T>(OP_SWEEP, L, cur, oth, d, vec, gw, lane, res);
         cl_sync();
-        T *tmp = cur;
+        const int tmp = cur;
         cur = oth;
         oth = tmp;
       }
-      tail_mv<T>(OP_RESID, L.n, L.s, L.s, L.rp, L.col, L.A, cur, L.b, L.r, vec, gw, NW, lane);
+      tail_mv<T>(OP_RESID, L.n, L.s, L.s, L.rp, L.col, L.A, d, cur, L.off_b, L.off_r, vec, gw, lane);
       cl_sync();
-      T *bn = (q + 1 < nl) ? pl->lv[q + 1].b : pl->bN;
-      tail_mv<T>(OP_ASSIGN, L.n_next, L.s_next, L.s, L.Rrp, L.Rcol, L.R, L.r, nullptr, bn, vec,
-                 gw, NW, lane);
+      const int bnext = (q + 1 < nl) ? pl.lv[q + 1].off_b : pl.off_bN;
+      tail_mv<T>(OP_ASSIGN, L.n_next, L.s_next, L.s, L.Rrp, L.Rcol, L.R, d, L.off_r, 0, bnext, vec,
+                 gw, lane);
       cl_sync();
     }
-  }
-  if (part == TAIL_ALL) {
-    tail_dense<T>(pl->nc, pl->Cinv, pl->bN, pl->xN, gw, NW, lane);
+    // coarsest level
+    tail_dense<T>(pl, d, gw, lane);
     cl_sync();
-  }
-  if (part != TAIL_DOWN) {
+    // up: prolongation and post-smoothing
+    const int pre = tail_pre_buffer(tpre), fin = tail_final_buffer(tpre, tpost);
     for (int q = nl - 1; q >= 0; --q) {
-      const TailLevel<T> &L = pl->lv[q];
-      T *cur = pre ? L.x2 : L.x, *oth = pre ? L.x : L.x2;
-      const T *xc = pl->xN;
-      if (q + 1 < nl) xc = fin ? pl->lv[q + 1].x2 : pl->lv[q + 1].x;
-      tail_mv<T>(OP_ADD, L.n, L.s, L.s_next, L.Prp, L.Pcol, L.P, xc, nullptr, cur, vec, gw, NW,
-                 lane);
+      const TailLevel<T> &L = pl.lv[q];
+      int cur = pre ? L.off_x2 : L.off_x, oth = pre ? L.off_x : L.off_x2;
+      int xc = pl.off_xN;
+      if (q + 1 < nl) xc = fin ? pl.lv[q + 1].off_x2 : pl.lv[q + 1].off_x;
+      tail_mv<T>(OP_ADD, L.n, L.s, L.s_next, L.Prp, L.Pcol, L.P, d, xc, 0, cur, vec, gw, lane);
       cl_sync();
       for (int t = 0; t < tpost; ++t) {
-        tail_jacobi<T>(OP_SWEEP, L, cur, oth, vec, gw, NW, lane, res);
+        tail_jacobi<T>(OP_SWEEP, L, cur, oth, d, vec, gw, lane, res);
         cl_sync();
-        T *tmp = cur;
+        const int tmp = cur;
         cur = oth;
         oth = tmp;
       }
+    }
+    // the corrected x_{k0} (owned entries) back to global memory
+    const TailLevel<T> &L = pl.lv[0];
+    const int xf = fin ? L.off_x2 : L.off_x;
+    for (int u = gw; u < L.n; u += d.NW) {
+      const T *xu = d_local<T>(xf, u, L.s, d.NW);
+      for (int r = lane; r < L.s; r += 32) pl.x_out[(size_t)u * L.s + r] = xu[r];
     }
   }
 }
 
 template <typename T>
-cudaLaunchConfig_t tail_config(int cluster, cudaLaunchAttribute *attr, int nattr, cudaStream_t s) {
+cudaLaunchConfig_t tail_config(int cluster, int smem, cudaLaunchAttribute *attr, int nattr,
+                               cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cluster, 1, 1);
   cfg.blockDim = dim3(kTailThreads, 1, 1);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = cluster;
@@ -291,17 +373,23 @@ cudaLaunchConfig_t tail_config(int cluster, cudaLaunchAttribute *attr, int nattr
   return cfg;
 }
 
+// dynamic shared memory the tail kernel may use (227 KB per CTA on sm_103a,
+// minus the static per-warp rows)
+constexpr int kTailSmemMax = 200 * 1024;
+
 }  // namespace
 
 template <typename T>
 int tail_cluster_size() {
   if (cudaFuncSetAttribute(vcycle_tail_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed,
-                           1) != cudaSuccess) {
+                           1) != cudaSuccess)
     (void)cudaGetLastError();
-  }
+  if (cudaFuncSetAttribute(vcycle_tail_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kTailSmemMax) != cudaSuccess)
+    (void)cudaGetLastError();
   for (int cs : {16, 8}) {
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = tail_config<T>(cs, attr, 1, nullptr);
+    cudaLaunchConfig_t cfg = tail_config<T>(cs, kTailSmemMax, attr, 1, nullptr);
     int nclusters = 0;
     if (cudaOccupancyMaxActiveClusters(&nclusters, vcycle_tail_kernel<T>, &cfg) == cudaSuccess &&
         nclusters > 0)
@@ -313,13 +401,16 @@ int tail_cluster_size() {
 template int tail_cluster_size<double>();
 template int tail_cluster_size<float>();
 
+int tail_smem_limit() { return kTailSmemMax; }
+
 template <typename T>
-cudaError_t launch_vcycle_tail(const TailPlan<T> *plan_dev, int part, int cluster,
+cudaError_t launch_vcycle_tail(const TailPlan<T> *plan_dev, int cluster, int smem_bytes,
                                cudaStream_t s) {
-  if (cluster <= 0 || !plan_dev || part < TAIL_ALL || part > TAIL_UP) return cudaErrorInvalidValue;
+  if (cluster <= 0 || !plan_dev || smem_bytes < 0 || smem_bytes > kTailSmemMax)
+    return cudaErrorInvalidValue;
   cudaLaunchAttribute attr[2];
-  cudaLaunchConfig_t cfg = tail_config<T>(cluster, attr, 2, s);
-  cudaError_t e = cudaLaunchKernelEx(&cfg, vcycle_tail_kernel<T>, plan_dev, part);
+  cudaLaunchConfig_t cfg = tail_config<T>(cluster, smem_bytes, attr, 2, s);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, vcycle_tail_kernel<T>, plan_dev);
   note_launch();
   return e;
 }
