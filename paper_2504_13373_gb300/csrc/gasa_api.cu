@@ -200,8 +200,9 @@ double spmv_bytes(const Level &l, int w, bool residual, int wa = 0) {
 // Plan of the fused bottom of the V-cycle for precision T (slot pi: 0 FP64,
 // 1 FP32): the deepest run of levels k >= 1 whose A_k is stored and takes at
 // most opt.tail_kib KiB, with every level below it down to the coarsest,
-// while the coarsest inverse is small (2 MB) and the levels' vectors fit in
-// the cluster's shared memory.
+// while the coarsest inverse is small (2 MB) and each CTA's share of the
+// vectors and matrix rows fits in its shared memory (top levels are dropped
+// until it does).  The matrix rows are packed per CTA on the host.
 template <typename T>
 gasa_status tail_build(gasa_ctx *ctx, int pi) {
   using P = Prec<T>;
@@ -224,76 +225,146 @@ gasa_status tail_build(gasa_ctx *ctx, int pi) {
   }
   if (k0 == N) return GASA_OK;
   const int cl = tail_cluster_size<T>();
-  if (cl == 0) return GASA_OK;
-  const int nw = cl * kTailWarps;
-  // distributed vector layout, dropping top levels until it fits
-  auto vec_bytes = [&](int n, int s) {
-    const int64_t b = (int64_t)tail_slots(n, nw) * s * (int64_t)sizeof(T);
-    return (b + 15) / 16 * 16;
+  if (cl == 0 || cl > kTailMaxCluster) return GASA_OK;
+  cudaStream_t s = ctx->stream;
+  CU(cudaStreamSynchronize(s));
+  // host copies of the candidate levels' operators
+  struct HostBSR {
+    std::vector<int> rp, col;
+    std::vector<T> val;
   };
-  auto layout_bytes = [&](int first) {
-    int64_t b = 2 * vec_bytes(lc.n, lc.s);
-    for (int k = first; k < N; ++k) b += 4 * vec_bytes(ctx->L[k].n, ctx->L[k].s);
-    return b;
+  auto fetch = [&](const DevBSR &m, const T *val, HostBSR &h) -> gasa_status {
+    h.rp.resize(m.nrows + 1);
+    h.col.resize(m.nnzb);
+    h.val.resize((size_t)m.nnzb * m.br * m.bc);
+    CU(cudaMemcpy(h.rp.data(), m.rp, h.rp.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(h.col.data(), m.col, h.col.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(h.val.data(), val, h.val.size() * sizeof(T), cudaMemcpyDeviceToHost));
+    return GASA_OK;
   };
-  while (k0 < N && layout_bytes(k0) > tail_smem_limit()) ++k0;
-  if (k0 == N) return GASA_OK;
-  TailPlan<T> h;
-  h.k0 = k0;
-  h.nlev = N - k0;
-  h.tpre = ctx->opt.t_pre;
-  h.tpost = ctx->opt.t_post;
-  h.nc = ctx->nc;
-  h.nN = lc.n;
-  h.sN = lc.s;
-  h.Cinv = ctx->coarse_inv;
-  h.nw = nw;
-  h.b_in = P::b(ctx->L[k0]);
-  h.x_out = P::x(ctx->L[k0]);
-  int64_t off = 0;
-  bool al = true;
-  auto chk = [&](const void *p) {
-    if (p && ((uintptr_t)p & 15u)) al = false;
-  };
-  for (int q = 0; q < h.nlev; ++q) {
+  const int nlmax = N - k0;
+  std::vector<HostBSR> hA(nlmax), hP(nlmax), hR(nlmax);
+  std::vector<std::vector<T>> hW(nlmax);
+  for (int q = 0; q < nlmax; ++q) {
     Level &l = ctx->L[k0 + q];
-    TailLevel<T> &t = h.lv[q];
-    t.n = l.n;
-    t.s = l.s;
-    t.n_next = l.R.nrows;
-    t.s_next = l.R.br;
-    t.rp = l.A.rp;
-    t.col = l.A.col;
-    t.A = P::A(l.A);
-    t.W = P::W(l);
-    t.Prp = l.P.rp;
-    t.Pcol = l.P.col;
-    t.P = P::A(l.P);
-    t.Rrp = l.R.rp;
-    t.Rcol = l.R.col;
-    t.R = P::A(l.R);
-    const int64_t vb = vec_bytes(l.n, l.s);
-    t.off_x = (int)off;
-    t.off_x2 = (int)(off + vb);
-    t.off_b = (int)(off + 2 * vb);
-    t.off_r = (int)(off + 3 * vb);
-    off += 4 * vb;
-    for (const void *p : {(const void *)t.A, (const void *)t.P, (const void *)t.R}) chk(p);
+    ST(fetch(l.A, P::A(l.A), hA[q]));
+    ST(fetch(l.P, P::A(l.P), hP[q]));
+    ST(fetch(l.R, P::A(l.R), hR[q]));
+    hW[q].resize((size_t)l.n * l.s * l.s);
+    CU(cudaMemcpy(hW[q].data(), P::W(l), hW[q].size() * sizeof(T), cudaMemcpyDeviceToHost));
   }
-  h.off_bN = (int)off;
-  h.off_xN = (int)(off + vec_bytes(lc.n, lc.s));
-  off += 2 * vec_bytes(lc.n, lc.s);
-  h.smem_bytes = (int)off;
-  h.vec = al ? 1 : 0;
-  unsigned char *d = nullptr;
-  ST(dalloc(ctx, &d, sizeof(TailPlan<T>)));
-  CU(cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
-  CU(cudaStreamSynchronize(ctx->stream));
-  ctx->tail_plan[pi] = d;
-  ctx->tail_k0[pi] = k0;
-  ctx->tail_coarse[pi] = 1;
-  ctx->tail_cluster[pi] = cl;
-  ctx->tail_smem[pi] = h.smem_bytes;
+  std::vector<double> hC((size_t)ctx->nc * ctx->nc);
+  CU(cudaMemcpy(hC.data(), ctx->coarse_inv, hC.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  auto r16 = [](int64_t b) { return (b + 15) / 16 * 16; };
+  auto vec_bytes = [&](int n, int sz) { return r16((int64_t)((n + cl - 1) / cl) * sz * (int64_t)sizeof(T)); };
+  for (; k0 < N; ++k0) {
+    const int q0 = k0 - (N - nlmax), nl = N - k0;
+    TailPlan<T> h;
+    h.k0 = k0;
+    h.nlev = nl;
+    h.tpre = ctx->opt.t_pre;
+    h.tpost = ctx->opt.t_post;
+    h.cl = cl;
+    h.vec = 1;
+    h.nc = ctx->nc;
+    h.nN = lc.n;
+    h.sN = lc.s;
+    h.b_in = P::b(ctx->L[k0]);
+    h.x_out = P::x(ctx->L[k0]);
+    // vectors: the same offsets in every CTA
+    int64_t off = 0;
+    for (int q = 0; q < nl; ++q) {
+      Level &l = ctx->L[k0 + q];
+      TailLevel<T> &t = h.lv[q];
+      t.n = l.n;
+      t.s = l.s;
+      t.n_next = l.R.nrows;
+      t.s_next = l.R.br;
+      const int64_t vb = vec_bytes(l.n, l.s);
+      t.off_x = (int)off;
+      t.off_x2 = (int)(off + vb);
+      t.off_b = (int)(off + 2 * vb);
+      t.off_r = (int)(off + 3 * vb);
+      off += 4 * vb;
+    }
+    h.off_bN = (int)off;
+    h.off_xN = (int)(off + vec_bytes(lc.n, lc.s));
+    off += 2 * vec_bytes(lc.n, lc.s);
+    h.mat_base = (int)off;
+    // packed matrix rows per CTA
+    std::vector<unsigned char> pack;
+    int64_t maxb = 0;
+    for (int c = 0; c < cl; ++c) {
+      std::vector<unsigned char> buf;
+      auto put = [&](const void *src, size_t bytes) -> int {
+        const size_t at = (size_t)r16((int64_t)buf.size());
+        buf.resize(at + bytes);
+        if (bytes) std::memcpy(buf.data() + at, src, bytes);
+        return (int)at;
+      };
+      // rows u = c, c + cl, ... of a BSR matrix: local row pointers, cols, values
+      auto put_rows = [&](const HostBSR &m, int nrows, int bsz, int *fo) {
+        std::vector<int> lrp(1, 0), lcol;
+        std::vector<T> lval;
+        for (int u = c; u < nrows; u += cl) {
+          for (int k = m.rp[u]; k < m.rp[u + 1]; ++k) {
+            lcol.push_back(m.col[k]);
+            lval.insert(lval.end(), m.val.begin() + (size_t)k * bsz, m.val.begin() + (size_t)(k + 1) * bsz);
+          }
+          lrp.push_back((int)lcol.size());
+        }
+        fo[0] = put(lrp.data(), lrp.size() * sizeof(int));
+        fo[1] = put(lcol.data(), lcol.size() * sizeof(int));
+        fo[2] = put(lval.data(), lval.size() * sizeof(T));
+      };
+      for (int q = 0; q < nl; ++q) {
+        const int qq = q0 + q;
+        Level &l = ctx->L[k0 + q];
+        int *mo = h.moff[c][q];
+        int fo[3];
+        put_rows(hA[qq], l.n, l.s * l.s, fo);
+        mo[TM_ARP] = fo[0];
+        mo[TM_ACOL] = fo[1];
+        mo[TM_AVAL] = fo[2];
+        std::vector<T> w;
+        for (int u = c; u < l.n; u += cl)
+          w.insert(w.end(), hW[qq].begin() + (size_t)u * l.s * l.s, hW[qq].begin() + (size_t)(u + 1) * l.s * l.s);
+        mo[TM_W] = put(w.data(), w.size() * sizeof(T));
+        put_rows(hP[qq], l.n, l.s * l.R.br, fo);
+        mo[TM_PRP] = fo[0];
+        mo[TM_PCOL] = fo[1];
+        mo[TM_PVAL] = fo[2];
+        put_rows(hR[qq], l.R.nrows, l.R.br * l.s, fo);
+        mo[TM_RRP] = fo[0];
+        mo[TM_RCOL] = fo[1];
+        mo[TM_RVAL] = fo[2];
+      }
+      std::vector<double> crows;
+      for (int u = c; u < lc.n; u += cl)
+        crows.insert(crows.end(), hC.begin() + (size_t)u * lc.s * ctx->nc,
+                     hC.begin() + (size_t)(u + 1) * lc.s * ctx->nc);
+      h.coff[c] = put(crows.data(), crows.size() * sizeof(double));
+      buf.resize((size_t)r16((int64_t)buf.size()));
+      h.pack_off[c] = (int64_t)pack.size();
+      h.pack_bytes[c] = (int)buf.size();
+      pack.insert(pack.end(), buf.begin(), buf.end());
+      maxb = std::max<int64_t>(maxb, (int64_t)buf.size());
+    }
+    h.smem_bytes = (int)(off + maxb);
+    if (off + maxb > tail_smem_limit()) continue;   // too big: start one level lower
+    unsigned char *dpack = nullptr, *dplan = nullptr;
+    ST(dalloc(ctx, &dpack, pack.size()));
+    CU(cudaMemcpy(dpack, pack.data(), pack.size(), cudaMemcpyHostToDevice));
+    h.pack = dpack;
+    ST(dalloc(ctx, &dplan, sizeof(TailPlan<T>)));
+    CU(cudaMemcpy(dplan, &h, sizeof(h), cudaMemcpyHostToDevice));
+    ctx->tail_plan[pi] = dplan;
+    ctx->tail_k0[pi] = k0;
+    ctx->tail_coarse[pi] = 1;
+    ctx->tail_cluster[pi] = cl;
+    ctx->tail_smem[pi] = h.smem_bytes;
+    return GASA_OK;
+  }
   return GASA_OK;
 }
 

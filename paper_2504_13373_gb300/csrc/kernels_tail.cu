@@ -9,15 +9,18 @@
 // coarsest dense solve and the way back up, with a hardware cluster barrier
 // between dependent steps.
 //
-// Vectors live in the cluster's distributed shared memory: warp w of the
-// cluster owns units w, w + NW, ... of every level and keeps their entries
-// of x, x2, b and r in its CTA's shared memory.  A step reads the owned
+// Everything the launch touches after its start sits in shared memory (the
+// layout is in tail.h): CTA c owns units c, c + C, ... of every level, copies
+// the matrix rows it computes with from a packed global buffer at the start,
+// and keeps its units' entries of x, x2, b and r.  A step reads the owned
 // unit's own entries locally, gathers neighbour units' entries from the
 // owning CTAs with ld.shared::cluster, and writes only owned entries, so the
-// release/acquire cluster barrier between steps is the only synchronisation
-// and no vector crosses L2.  Matrix values never change in a launch and are
-// read through L1.  Arithmetic per output row: the sum over the row's blocks
-// in a fixed order, so results do not depend on timing.
+// release/acquire cluster barrier between steps is the only synchronisation.
+// (The barrier's acquire drops the SM's L1, so matrix rows left in global
+// memory would come back from L2 in every step; measured on GB300 a barrier
+// costs 0.25 us, an L2 round trip after it 0.45 us.)  Arithmetic per output
+// row: the sum over the row's blocks in a fixed order, so results do not
+// depend on timing.
 #include "common.cuh"
 #include "internal.h"
 #include "tail.h"
@@ -53,22 +56,21 @@ __device__ __forceinline__ int pow2_at_least(int v) {   // 1 <= v <= 32
   return v <= 1 ? 1 : 1 << (32 - __clz(v - 1));
 }
 
-// distributed vector layout (see tail.h)
+// distributed vector layout (see tail.h): unit j of a level lives in CTA
+// j mod C at slot j / C
 struct Dist {
   uint32_t sbase;   // shared-window address of tail_smem in this CTA
-  int NW;
+  int cl;           // CTAs in the cluster
 };
-__device__ __forceinline__ int d_slot(int j, int NW) { return (j / NW) * kTailWarps + (j % kTailWarps); }
-__device__ __forceinline__ int d_owner(int j, int NW) { return (j % NW) / kTailWarps; }
 template <typename T>
-__device__ __forceinline__ T *d_local(int off, int j, int s, int NW) {
-  return reinterpret_cast<T *>(tail_smem + off) + (size_t)d_slot(j, NW) * s;
+__device__ __forceinline__ T *d_local(int off, int slot, int s) {
+  return reinterpret_cast<T *>(tail_smem + off) + (size_t)slot * s;
 }
 // shared::cluster address of entry 0 of unit j (s entries of esize bytes)
 __device__ __forceinline__ uint32_t d_remote(const Dist &d, int off, int j, int s, int esize) {
-  const uint32_t la = d.sbase + (uint32_t)off + (uint32_t)(d_slot(j, d.NW) * s * esize);
+  const uint32_t la = d.sbase + (uint32_t)off + (uint32_t)((j / d.cl) * s * esize);
   uint32_t ra;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(la), "r"(d_owner(j, d.NW)));
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(la), "r"(j % d.cl));
   return ra;
 }
 
@@ -126,12 +128,12 @@ __device__ __forceinline__ T vdot(T a, T x, T acc) { return fma(a, x, acc); }
 // (g, q) takes row r0 + q of blocks beg + g, beg + g + G, ... (G = 32 / gs),
 // four blocks at a time so that four gathers are in flight; an xor-shuffle
 // over the group bits then leaves the sum of row r0 + (lane % gs) in every
-// lane.  x is the distributed vector at byte offset xoff (bc entries per
-// unit).
+// lane.  col and val are the CTA's packed rows in shared memory; x is the
+// distributed vector at byte offset xoff (bc entries per unit).
 template <typename T, int VW>
 __device__ __forceinline__ T tail_rows(int beg, int end, int br, int bc, int r0, int gs,
-                                       const int *__restrict__ col, const T *__restrict__ val,
-                                       const Dist &d, int xoff, int lane) {
+                                       const int *col, const T *val, const Dist &d, int xoff,
+                                       int lane) {
   using V = typename TailVec<T, VW>::V;
   const int q = lane & (gs - 1), g = lane / gs, G = 32 / gs;
   const int r = r0 + q;
@@ -145,14 +147,14 @@ __device__ __forceinline__ T tail_rows(int beg, int end, int br, int bc, int r0,
       for (int u = 0; u < 4; ++u) {
         const int kk = k + u * G;
         a[u] = reinterpret_cast<const V *>(val + ((size_t)kk * br + r) * bc);
-        xa[u] = d_remote(d, xoff, __ldg(col + kk), bc, (int)sizeof(T));
+        xa[u] = d_remote(d, xoff, col[kk], bc, (int)sizeof(T));
       }
       T s[4] = {T(0), T(0), T(0), T(0)};
       for (int c = 0; c < bc / VW; ++c) {
         V av[4], xv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          av[u] = __ldg(a[u] + c);
+          av[u] = a[u][c];
           xv[u] = ld_cl<V>(xa[u] + c * (uint32_t)sizeof(V));
         }
 #pragma unroll
@@ -162,10 +164,9 @@ __device__ __forceinline__ T tail_rows(int beg, int end, int br, int bc, int r0,
     }
     for (; k < end; k += G) {
       const V *a = reinterpret_cast<const V *>(val + ((size_t)k * br + r) * bc);
-      const uint32_t xa = d_remote(d, xoff, __ldg(col + k), bc, (int)sizeof(T));
+      const uint32_t xa = d_remote(d, xoff, col[k], bc, (int)sizeof(T));
       T s = T(0);
-      for (int c = 0; c < bc / VW; ++c)
-        s = vdot<T>(__ldg(a + c), ld_cl<V>(xa + c * (uint32_t)sizeof(V)), s);
+      for (int c = 0; c < bc / VW; ++c) s = vdot<T>(a[c], ld_cl<V>(xa + c * (uint32_t)sizeof(V)), s);
       acc += s;
     }
   }
@@ -175,8 +176,7 @@ __device__ __forceinline__ T tail_rows(int beg, int end, int br, int bc, int r0,
 
 template <typename T>
 __device__ __forceinline__ T tail_rows_any(int beg, int end, int br, int bc, int r0, int gs,
-                                           const int *__restrict__ col,
-                                           const T *__restrict__ val, const Dist &d, int xoff,
+                                           const int *col, const T *val, const Dist &d, int xoff,
                                            bool vec, int lane) {
   constexpr int VW = 16 / (int)sizeof(T);
   if (vec && bc % VW == 0) return tail_rows<T, VW>(beg, end, br, bc, r0, gs, col, val, d, xoff, lane);
@@ -185,17 +185,16 @@ __device__ __forceinline__ T tail_rows_any(int beg, int end, int br, int bc, int
 
 enum { OP_SWEEP = 0, OP_FIRST = 1, OP_RESID = 2, OP_ASSIGN = 3, OP_ADD = 4 };
 
-// y = M x (ASSIGN), y = b - M x (RESID) or y += M x (ADD) for the n block
-// rows of br x bc blocks of M, a warp per owned block row; x is the
-// distributed vector at xoff (bc per unit), b and y at boff / yoff (br per
-// unit, owned entries only)
+// y = M x (ASSIGN), y = b - M x (RESID) or y += M x (ADD) for the m block
+// rows of br x bc blocks this CTA owns (packed rp / col / val), a warp per
+// row; x is the distributed vector at xoff (bc per unit), b and y at boff /
+// yoff (br per unit, own slots)
 template <typename T>
-__device__ void tail_mv(int op, int n, int br, int bc, const int *__restrict__ rp,
-                        const int *__restrict__ col, const T *__restrict__ val, const Dist &d,
-                        int xoff, int boff, int yoff, bool vec, int gw, int lane) {
-  for (int u = gw; u < n; u += d.NW) {
-    const int beg = __ldg(rp + u), end = __ldg(rp + u + 1);
-    T *y = d_local<T>(yoff, u, br, d.NW);
+__device__ void tail_mv(int op, int m, int br, int bc, const int *rp, const int *col, const T *val,
+                        const Dist &d, int xoff, int boff, int yoff, bool vec, int wib, int lane) {
+  for (int sl = wib; sl < m; sl += kTailWarps) {
+    const int beg = rp[sl], end = rp[sl + 1];
+    T *y = d_local<T>(yoff, sl, br);
     for (int r0 = 0; r0 < br; r0 += 32) {
       const int rem = br - r0;
       const int gs = rem >= 32 ? 32 : pow2_at_least(rem);
@@ -203,7 +202,7 @@ __device__ void tail_mv(int op, int n, int br, int bc, const int *__restrict__ r
       const int r = r0 + lane;
       if (lane < gs && r < br) {
         if (op == OP_ASSIGN) y[r] = v;
-        else if (op == OP_RESID) y[r] = d_local<T>(boff, u, br, d.NW)[r] - v;
+        else if (op == OP_RESID) y[r] = d_local<T>(boff, sl, br)[r] - v;
         else y[r] += v;
       }
     }
@@ -212,35 +211,36 @@ __device__ void tail_mv(int op, int n, int br, int bc, const int *__restrict__ r
 }
 
 // Smoothing step of Alg. 1 with A~^{-1} = w D^{-1}: xo = x + W (b - A x)
-// (SWEEP) or xo = W b (FIRST, from x = 0).  The block row's residual meets
-// in the warp's shared-memory row `res`, then lane r applies row r of W_u.
+// (SWEEP) or xo = W b (FIRST, from x = 0), over the CTA's m units.  The
+// block row's residual meets in the warp's shared-memory row `res`, then
+// lane r applies row r of W_u.
 template <typename T>
-__device__ void tail_jacobi(int op, const TailLevel<T> &L, int xoff, int ooff, const Dist &d,
-                            bool vec, int gw, int lane, T *res) {
+__device__ void tail_jacobi(int op, const TailLevel<T> &L, int m, const int *rp, const int *col,
+                            const T *val, const T *W, int xoff, int ooff, const Dist &d, bool vec,
+                            int wib, int lane, T *res) {
   const int s = L.s;
-  for (int u = gw; u < L.n; u += d.NW) {
+  for (int sl = wib; sl < m; sl += kTailWarps) {
     int beg = 0, end = 0;
     if (op == OP_SWEEP) {
-      beg = __ldg(L.rp + u);
-      end = __ldg(L.rp + u + 1);
+      beg = rp[sl];
+      end = rp[sl + 1];
     }
-    const T *bu = d_local<T>(L.off_b, u, s, d.NW);
+    const T *bu = d_local<T>(L.off_b, sl, s);
     for (int r0 = 0; r0 < s; r0 += 32) {
       const int rem = s - r0;
       const int gs = rem >= 32 ? 32 : pow2_at_least(rem);
       T v = T(0);
-      if (op == OP_SWEEP)
-        v = tail_rows_any<T>(beg, end, s, s, r0, gs, L.col, L.A, d, xoff, vec, lane);
+      if (op == OP_SWEEP) v = tail_rows_any<T>(beg, end, s, s, r0, gs, col, val, d, xoff, vec, lane);
       const int r = r0 + lane;
       if (lane < gs && r < s) res[r] = bu[r] - v;
     }
     __syncwarp();
-    const T *xu = d_local<T>(xoff, u, s, d.NW);
-    T *ou = d_local<T>(ooff, u, s, d.NW);
+    const T *xu = d_local<T>(xoff, sl, s);
+    T *ou = d_local<T>(ooff, sl, s);
     for (int r = lane; r < s; r += 32) {
-      const T *w = L.W + ((size_t)u * s + r) * s;
+      const T *w = W + ((size_t)sl * s + r) * s;
       T out = T(0);
-      for (int c = 0; c < s; ++c) out = fma(__ldg(w + c), res[c], out);
+      for (int c = 0; c < s; ++c) out = fma(w[c], res[c], out);
       if (op == OP_SWEEP) out += xu[r];
       ou[r] = out;
     }
@@ -251,17 +251,19 @@ __device__ void tail_jacobi(int op, const TailLevel<T> &L, int xoff, int ooff, c
 // x_N = A_N^{-1} b_N in FP64 arithmetic, a warp per owned coarse unit and,
 // for each of its rows, lanes over the columns (the order of dense_mv_kernel)
 template <typename T>
-__device__ void tail_dense(const TailPlan<T> &pl, const Dist &d, int gw, int lane) {
+__device__ void tail_dense(const TailPlan<T> &pl, const double *Crows, const Dist &d, int c,
+                           int wib, int lane) {
   const int nc = pl.nc, sN = pl.sN;
-  for (int u = gw; u < pl.nN; u += d.NW) {
-    T *xu = d_local<T>(pl.off_xN, u, sN, d.NW);
+  const int m = tail_owned(pl.nN, c, d.cl);
+  for (int sl = wib; sl < m; sl += kTailWarps) {
+    T *xu = d_local<T>(pl.off_xN, sl, sN);
     for (int rr = 0; rr < sN; ++rr) {
-      const double *a = pl.Cinv + (size_t)(u * sN + rr) * nc;
+      const double *a = Crows + (size_t)(sl * sN + rr) * nc;
       double acc = 0.0;
       for (int j = lane; j < nc; j += 32) {
         const uint32_t bj = d_remote(d, pl.off_bN, j / sN, sN, (int)sizeof(T)) +
                             (uint32_t)((j % sN) * (int)sizeof(T));
-        acc = fma(__ldg(a + j), (double)ld_cl<T>(bj), acc);
+        acc = fma(a[j], (double)ld_cl<T>(bj), acc);
       }
       acc = warp_sum(acc);
       if (lane == 0) xu[rr] = (T)acc;
@@ -279,76 +281,92 @@ vcycle_tail_kernel(const TailPlan<T> *__restrict__ plp) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   Dist d;
   d.sbase = (uint32_t)__cvta_generic_to_shared(tail_smem);
-  d.NW = (int)cl_size() * kTailWarps;
-  const int gw = (int)cl_rank() * kTailWarps + wib;
+  d.cl = (int)cl_size();
+  const int c = (int)cl_rank();
   T *res = res_all[wib];
   const int nl = pl.nlev, tpre = pl.tpre, tpost = pl.tpost;
   const bool vec = pl.vec != 0;
-  const bool launch_ok = d.NW == pl.nw;   // the layout was made for this cluster size
-  // b_{k0} from global memory into the owners' shared memory
+  if (d.cl != pl.cl) return;   // uniform over the cluster: the layout needs this size
+  // the CTA's packed matrix rows into shared memory, b_{k0} of its units
+  unsigned char *mat = tail_smem + pl.mat_base;
   {
+    const int4 *src = reinterpret_cast<const int4 *>(pl.pack + pl.pack_off[c]);
+    int4 *dst = reinterpret_cast<int4 *>(mat);
+    const int n16 = pl.pack_bytes[c] / 16;
+    for (int i = threadIdx.x; i < n16; i += kTailThreads) dst[i] = __ldg(src + i);
     const TailLevel<T> &L = pl.lv[0];
-    for (int u = gw; launch_ok && u < L.n; u += d.NW) {
-      T *bu = d_local<T>(L.off_b, u, L.s, d.NW);
-      for (int r = lane; r < L.s; r += 32) bu[r] = pl.b_in[(size_t)u * L.s + r];
+    const int m = tail_owned(L.n, c, d.cl);
+    for (int i = threadIdx.x; i < m * L.s; i += kTailThreads) {
+      const int sl = i / L.s, r = i - sl * L.s;
+      d_local<T>(L.off_b, sl, L.s)[r] = pl.b_in[(size_t)(sl * d.cl + c) * L.s + r];
     }
-    __syncwarp();
+    __syncthreads();
   }
-  if (launch_ok) {
-    // down: pre-smoothing, residual, restriction
-    for (int q = 0; q < nl; ++q) {
-      const TailLevel<T> &L = pl.lv[q];
-      int cur = L.off_x, oth = L.off_x2;
-      if (tpre == 0) {
-        for (int u = gw; u < L.n; u += d.NW) {
-          T *xu = d_local<T>(cur, u, L.s, d.NW);
-          for (int r = lane; r < L.s; r += 32) xu[r] = T(0);
-        }
-      } else {
-        tail_jacobi<T>(OP_FIRST, L, cur, cur, d, vec, gw, lane, res);
-      }
-      cl_sync();
-      for (int t = 1; t < tpre; ++t) {
-        tail_jacobi<T>(OP_SWEEP, L, cur, oth, d, vec, gw, lane, res);
-        cl_sync();
-        const int tmp = cur;
-        cur = oth;
-        oth = tmp;
-      }
-      tail_mv<T>(OP_RESID, L.n, L.s, L.s, L.rp, L.col, L.A, d, cur, L.off_b, L.off_r, vec, gw, lane);
-      cl_sync();
-      const int bnext = (q + 1 < nl) ? pl.lv[q + 1].off_b : pl.off_bN;
-      tail_mv<T>(OP_ASSIGN, L.n_next, L.s_next, L.s, L.Rrp, L.Rcol, L.R, d, L.off_r, 0, bnext, vec,
-                 gw, lane);
-      cl_sync();
+  auto fld = [&](int q, int f) { return mat + pl.moff[c][q][f]; };
+  // down: pre-smoothing, residual, restriction
+  for (int q = 0; q < nl; ++q) {
+    const TailLevel<T> &L = pl.lv[q];
+    const int m = tail_owned(L.n, c, d.cl), mn = tail_owned(L.n_next, c, d.cl);
+    const int *Arp = reinterpret_cast<const int *>(fld(q, TM_ARP));
+    const int *Acol = reinterpret_cast<const int *>(fld(q, TM_ACOL));
+    const T *Aval = reinterpret_cast<const T *>(fld(q, TM_AVAL));
+    const T *W = reinterpret_cast<const T *>(fld(q, TM_W));
+    int cur = L.off_x, oth = L.off_x2;
+    if (tpre == 0) {
+      for (int i = threadIdx.x; i < m * L.s; i += kTailThreads) d_local<T>(cur, 0, 0)[i] = T(0);
+    } else {
+      tail_jacobi<T>(OP_FIRST, L, m, Arp, Acol, Aval, W, cur, cur, d, vec, wib, lane, res);
     }
-    // coarsest level
-    tail_dense<T>(pl, d, gw, lane);
     cl_sync();
-    // up: prolongation and post-smoothing
-    const int pre = tail_pre_buffer(tpre), fin = tail_final_buffer(tpre, tpost);
-    for (int q = nl - 1; q >= 0; --q) {
-      const TailLevel<T> &L = pl.lv[q];
-      int cur = pre ? L.off_x2 : L.off_x, oth = pre ? L.off_x : L.off_x2;
-      int xc = pl.off_xN;
-      if (q + 1 < nl) xc = fin ? pl.lv[q + 1].off_x2 : pl.lv[q + 1].off_x;
-      tail_mv<T>(OP_ADD, L.n, L.s, L.s_next, L.Prp, L.Pcol, L.P, d, xc, 0, cur, vec, gw, lane);
+    for (int t = 1; t < tpre; ++t) {
+      tail_jacobi<T>(OP_SWEEP, L, m, Arp, Acol, Aval, W, cur, oth, d, vec, wib, lane, res);
       cl_sync();
-      for (int t = 0; t < tpost; ++t) {
-        tail_jacobi<T>(OP_SWEEP, L, cur, oth, d, vec, gw, lane, res);
-        cl_sync();
-        const int tmp = cur;
-        cur = oth;
-        oth = tmp;
-      }
+      const int tmp = cur;
+      cur = oth;
+      oth = tmp;
     }
-    // the corrected x_{k0} (owned entries) back to global memory
-    const TailLevel<T> &L = pl.lv[0];
-    const int xf = fin ? L.off_x2 : L.off_x;
-    for (int u = gw; u < L.n; u += d.NW) {
-      const T *xu = d_local<T>(xf, u, L.s, d.NW);
-      for (int r = lane; r < L.s; r += 32) pl.x_out[(size_t)u * L.s + r] = xu[r];
+    tail_mv<T>(OP_RESID, m, L.s, L.s, Arp, Acol, Aval, d, cur, L.off_b, L.off_r, vec, wib, lane);
+    cl_sync();
+    const int bnext = (q + 1 < nl) ? pl.lv[q + 1].off_b : pl.off_bN;
+    tail_mv<T>(OP_ASSIGN, mn, L.s_next, L.s, reinterpret_cast<const int *>(fld(q, TM_RRP)),
+               reinterpret_cast<const int *>(fld(q, TM_RCOL)),
+               reinterpret_cast<const T *>(fld(q, TM_RVAL)), d, L.off_r, 0, bnext, vec, wib, lane);
+    cl_sync();
+  }
+  // coarsest level
+  tail_dense<T>(pl, reinterpret_cast<const double *>(mat + pl.coff[c]), d, c, wib, lane);
+  cl_sync();
+  // up: prolongation and post-smoothing
+  const int pre = tail_pre_buffer(tpre), fin = tail_final_buffer(tpre, tpost);
+  for (int q = nl - 1; q >= 0; --q) {
+    const TailLevel<T> &L = pl.lv[q];
+    const int m = tail_owned(L.n, c, d.cl);
+    const int *Arp = reinterpret_cast<const int *>(fld(q, TM_ARP));
+    const int *Acol = reinterpret_cast<const int *>(fld(q, TM_ACOL));
+    const T *Aval = reinterpret_cast<const T *>(fld(q, TM_AVAL));
+    const T *W = reinterpret_cast<const T *>(fld(q, TM_W));
+    int cur = pre ? L.off_x2 : L.off_x, oth = pre ? L.off_x : L.off_x2;
+    int xc = pl.off_xN;
+    if (q + 1 < nl) xc = fin ? pl.lv[q + 1].off_x2 : pl.lv[q + 1].off_x;
+    tail_mv<T>(OP_ADD, m, L.s, L.s_next, reinterpret_cast<const int *>(fld(q, TM_PRP)),
+               reinterpret_cast<const int *>(fld(q, TM_PCOL)),
+               reinterpret_cast<const T *>(fld(q, TM_PVAL)), d, xc, 0, cur, vec, wib, lane);
+    cl_sync();
+    for (int t = 0; t < tpost; ++t) {
+      tail_jacobi<T>(OP_SWEEP, L, m, Arp, Acol, Aval, W, cur, oth, d, vec, wib, lane, res);
+      cl_sync();
+      const int tmp = cur;
+      cur = oth;
+      oth = tmp;
     }
+  }
+  // the corrected x_{k0} (own units) back to global memory
+  const TailLevel<T> &L = pl.lv[0];
+  const int m = tail_owned(L.n, c, d.cl);
+  const int xf = fin ? L.off_x2 : L.off_x;
+  for (int i = threadIdx.x; i < m * L.s; i += kTailThreads) {
+    const int sl = i / L.s, r = i - sl * L.s;
+    pl.x_out[(size_t)(sl * d.cl + c) * L.s + r] = d_local<T>(xf, sl, L.s)[r];
   }
 }
 

@@ -7,43 +7,50 @@
 
 namespace gasa {
 
-// One smoothed level k of the fused tail.  Every level of the tail keeps
-// its operator A_k (no matrix-free level) and has one block size s.
+constexpr int kTailThreads = 512;             // threads per CTA of the tail kernel
+constexpr int kTailWarps = kTailThreads / 32;
+constexpr int kTailMaxCluster = 16;
+
+// Ownership: unit u of a level belongs to CTA u mod C of the C-CTA cluster
+// and sits at slot u / C there; the CTA's warps take its slots round robin.
+// Each CTA keeps in shared memory
+//  * the vectors of every tail level (x, x2, b, r) and of the coarsest level
+//    (b_N, x_N) for its own units, at offsets that are the same in every CTA
+//    (slots for ceil(n / C) units), so that any CTA can read any unit's
+//    entries through distributed shared memory;
+//  * the matrix rows it computes with: A_k, w D_k^{-1}, P_k rows of its level-k
+//    units, R_k rows of its level-(k+1) units, A_N^{-1} rows of its coarsest
+//    units, packed per CTA in one global buffer and copied in at the start of
+//    the launch.  Row pointers are local to the packed rows; column indices
+//    stay global unit ids.
+enum { TM_ARP = 0, TM_ACOL, TM_AVAL, TM_W, TM_PRP, TM_PCOL, TM_PVAL, TM_RRP, TM_RCOL, TM_RVAL,
+       TM_FIELDS };
+
 template <typename T>
 struct TailLevel {
   int n = 0, s = 0;                   // units, dofs per unit
   int s_next = 0, n_next = 0;         // block size and units of level k+1
-  const int *rp = nullptr, *col = nullptr;
-  const T *A = nullptr;               // A_k, s x s blocks
-  const T *W = nullptr;               // w_k D_k^{-1}, n blocks of s x s
-  const int *Prp = nullptr, *Pcol = nullptr;
-  const T *P = nullptr;               // P_k: n block rows of s x s_next blocks
-  const int *Rrp = nullptr, *Rcol = nullptr;
-  const T *R = nullptr;               // R_k = P_k^T: n_next block rows of s_next x s blocks
-  // vectors x, x2, b, r of the level live in distributed shared memory: unit
-  // u belongs to warp u mod NW of the cluster (NW = CTAs x warps per CTA) and
-  // sits in that warp's CTA at slot (u / NW) * warps + u mod warps; off_* are
-  // the byte offsets of the level's vectors in every CTA's dynamic shared
-  // memory (the same layout in every CTA)
-  int off_x = 0, off_x2 = 0, off_b = 0, off_r = 0;
+  int off_x = 0, off_x2 = 0, off_b = 0, off_r = 0;   // vector offsets (bytes, every CTA)
 };
 
-// Levels k0 .. k0 + nlev - 1 smoothed in the tail and the coarsest solve
-// x_N = A_N^{-1} b_N (n_N units of s_N dofs, nc = n_N s_N).  The launch reads
-// b_{k0} from global memory (b_in) and leaves the corrected x_{k0} there
-// (x_out); everything in between stays in the cluster's shared memory.
 template <typename T>
 struct TailPlan {
   int k0 = 0, nlev = 0;
   int tpre = 0, tpost = 0;
-  int vec = 0;                        // 1: matrix arrays 16-byte aligned
+  int cl = 0;                          // CTAs per cluster the layout was made for
+  int vec = 0;                         // 1: 16-byte vector paths allowed
   int nc = 0, nN = 0, sN = 0;
-  const double *Cinv = nullptr;       // row-major A_N^{-1}
-  int off_bN = 0, off_xN = 0;         // coarsest-level vectors, distributed like the levels'
-  int smem_bytes = 0;                 // dynamic shared memory per CTA
-  int nw = 0;                         // warps of the cluster the layout was made for
-  const T *b_in = nullptr;
-  T *x_out = nullptr;
+  int off_bN = 0, off_xN = 0;          // coarsest-level vectors (every CTA)
+  int mat_base = 0;                    // start of the packed matrix rows in shared memory
+  int smem_bytes = 0;                  // dynamic shared memory per CTA
+  const unsigned char *pack = nullptr; // packed matrix rows of all CTAs
+  int64_t pack_off[kTailMaxCluster] = {};   // byte offset of CTA c's rows in pack
+  int pack_bytes[kTailMaxCluster] = {};     // and their size (multiple of 16)
+  // byte offsets of each CTA's fields within its packed rows
+  int moff[kTailMaxCluster][GASA_MAX_LEVELS][TM_FIELDS] = {};
+  int coff[kTailMaxCluster] = {};           // A_N^{-1} rows of the CTA's coarsest units
+  const T *b_in = nullptr;             // b_{k0} (global)
+  T *x_out = nullptr;                  // x_{k0} after post-smoothing (global)
   TailLevel<T> lv[GASA_MAX_LEVELS];
 };
 
@@ -53,11 +60,8 @@ __host__ __device__ inline int tail_pre_buffer(int tpre) { return tpre >= 1 ? (t
 __host__ __device__ inline int tail_final_buffer(int tpre, int tpost) {
   return ((tpre >= 1 ? tpre - 1 : 0) + tpost) & 1;
 }
-
-constexpr int kTailThreads = 512;             // threads per CTA of the tail kernel
-constexpr int kTailWarps = kTailThreads / 32;
-// slots one CTA holds of a level of n units when the cluster has nw warps
-inline int tail_slots(int n, int nw) { return ((n + nw - 1) / nw) * kTailWarps; }
+// units of an n-unit level owned by CTA c of a C-CTA cluster
+__host__ __device__ inline int tail_owned(int n, int c, int C) { return n > c ? (n - c + C - 1) / C : 0; }
 
 // cluster size the tail kernel of precision T launches with (16 where the
 // device can co-schedule a 16-CTA cluster of 512-thread CTAs, else 8); 0 if
