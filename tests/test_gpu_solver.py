@@ -444,7 +444,7 @@ def test_padded_levels(name, hstar):
 
 @pytest.mark.parametrize("name", ["c1", "p3_32", "cd_q2_16", "tet_p2_6", "uneq6"])
 def test_fused_tail(name):
-    """Levels 1..N-1 and the coarsest solve run as one thread-block-cluster
+    """The bottom levels and the coarsest solve run as one thread-block-cluster
     launch (tail_kib large) or as one launch per step (tail_kib = 0).  Both
     compute the V-cycle of Alg. 2 with the same sum per output row, so the
     two agree to rounding, both follow the oracle's V-cycle, and the solves
@@ -458,8 +458,10 @@ def test_fused_tail(name):
     try:
         for prec, oprec, tol in ((gasa.GASA_PREC_FP64, "fp64", 1e-12),
                                  (gasa.GASA_PREC_MIXED32, "fp32", 1e-5)):
+            # every level from 1 down qualifies by size; the tail starts lower
+            # only where a CTA's share of the rows would overflow shared memory
             tf = gasa.gasa_tail_info(ctx_f, prec)
-            assert tf["first_level"] == 1 and tf["cluster"] in (8, 16), tf
+            assert 1 <= tf["first_level"] <= n_levels - 2 and tf["cluster"] in (8, 16), tf
             assert tf["coarse_inside"] == 1
             assert gasa.gasa_tail_info(ctx_s, prec) == {"first_level": n_levels - 1, "cluster": 0,
                                                         "coarse_inside": 0}
