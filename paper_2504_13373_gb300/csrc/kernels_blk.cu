@@ -150,10 +150,17 @@ bsr_blk_kernel(int n_brows, const int *__restrict__ rp, const int *__restrict__ 
 // Lanes per block row: about 2.5 blocks per lane (two in flight, a short
 // tail), a power of two in [4, 64] and at least s, so that lanes 0..s-1 of
 // the team can write the s rows.
+// (GASA_BLK_TEAM = 4..64 in the environment fixes the team for A/B timing)
 int blk_team(int bs, int n_brows, int64_t nnzb) {
+  static const int forced = [] {
+    const char *e = std::getenv("GASA_BLK_TEAM");
+    const int v = e ? std::atoi(e) : 0;
+    return (v == 4 || v == 8 || v == 16 || v == 32 || v == 64) ? v : 0;
+  }();
   const double avg = (double)nnzb / (double)(n_brows > 0 ? n_brows : 1);
   int tl = 4;
   while (tl < 64 && tl * 2.5 < avg) tl *= 2;
+  if (forced) tl = forced;
   while (tl < bs) tl *= 2;
   return tl;
 }
