@@ -95,6 +95,8 @@ struct gasa_ctx {
   float *kp_hi = nullptr, *kp_lo = nullptr;   // two-term FP32 split of p (mixed precision)
   double *pq_ds = nullptr;   // p . Ap partials of the double-single product (one per CTA)
   int n_pq_ds = 0;
+  double *rz_ds = nullptr, *rzo_ds = nullptr;   // r . z, r . zold partials of the CG step
+  int n_rz_cap = 0;                             // their capacity
   double *V = nullptr, *Z = nullptr, *H = nullptr, *gm = nullptr, *mpart = nullptr;
   int gm_restart = 0;
   bool gm_flex = false;

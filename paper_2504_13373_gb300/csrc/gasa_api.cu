@@ -368,8 +368,22 @@ gasa_status tail_build(gasa_ctx *ctx, int pi) {
   return GASA_OK;
 }
 
+// The mixed-precision CG step's V-cycle with its precision conversions and
+// the two dot products that follow it folded into the first and the last
+// level-0 smoothing steps: r (FP64) is read by the first step, which leaves
+// its FP32 rounding in b32; the last step writes z (FP64) and the partial
+// sums of r . z and r . zold (n_part per product).
+struct FusedEnds {
+  const double *r;
+  float *b32;
+  double *z;
+  const double *zold;
+  double *part_rz, *part_rzo;
+};
+
 template <typename T>
-gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false) {
+gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false,
+                        const FusedEnds *fe = nullptr) {
   using P = Prec<T>;
   cudaStream_t s = ctx->stream;
   const int N = ctx->N;
@@ -427,7 +441,12 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false) {
     } else {
       cudaEvent_t e0;
       if (k == 0) prof_begin(ctx, 3, &e0);
-      CU(sweep(k, JAC_FIRST, nullptr, bk[k], x));
+      if constexpr (std::is_same<T, float>::value) {
+        if (k == 0 && fe) CU(launch_jacobi_first_conv(l.n, l.s, fe->r, fe->b32, P::W(l), x, s));
+        else CU(sweep(k, JAC_FIRST, nullptr, bk[k], x));
+      } else {
+        CU(sweep(k, JAC_FIRST, nullptr, bk[k], x));
+      }
       if (k == 0) prof_end(ctx, 3, sweep_bytes(l, w, true, wa));
       for (int t = 1; t < tpre; ++t) {
         if (k == 0) prof_begin(ctx, 0, &e0);
@@ -472,7 +491,15 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false) {
       T *dst = (k == 0 && t == tpost - 1) ? out : x2;
       cudaEvent_t e0;
       if (k == 0) prof_begin(ctx, 0, &e0);
-      CU(sweep(k, JAC_SWEEP, x, bk[k], dst));
+      bool done = false;
+      if constexpr (std::is_same<T, float>::value) {
+        if (k == 0 && t == tpost - 1 && fe) {
+          CU(launch_jacobi_last(l.n, l.s, l.A.rp, l.A.col, P::A(l.A), P::W(l), x, bk[0], fe->z,
+                                fe->r, fe->zold, fe->part_rz, fe->part_rzo, s));
+          done = true;
+        }
+      }
+      if (!done) CU(sweep(k, JAC_SWEEP, x, bk[k], dst));
       if (k == 0) prof_end(ctx, 0, sweep_bytes(l, w, false, wa));
       if (dst == x2) std::swap(x, x2);
       else x = dst;
@@ -488,6 +515,30 @@ gasa_status apply_M(gasa_ctx *ctx, const double *rr, double *z, int precision) {
   CU(launch_convert<double, float>(n, rr, ctx->kf_in, ctx->stream));
   ST(vcycle_impl<float>(ctx, ctx->kf_in, ctx->kf_out, precision == GASA_PREC_MIXED16));
   CU(launch_convert<float, double>(n, ctx->kf_out, z, ctx->stream));
+  return GASA_OK;
+}
+
+// z = M r for the CG step together with the partial sums of r . z (and of
+// r . zold when zold is given): one fused pass at the ends of the FP32
+// V-cycle where the level-0 layout allows (MIXED32, plain level-0 sweeps,
+// blocks of at most 16), else the V-cycle and two dot-product launches.
+// *n_part receives the number of partials per product.
+gasa_status apply_M_cg(gasa_ctx *ctx, const double *rr, double *z, const double *zold,
+                       int precision, double *part_rz, double *part_rzo, int *n_part) {
+  Level &l0 = ctx->L[0];
+  const int64_t n = l0.ndof;
+  const bool fuse = precision == GASA_PREC_MIXED32 && !l0.tma && !l0.mf && l0.s <= 16 &&
+                    ctx->opt.t_pre >= 1 && ctx->opt.t_post >= 1;
+  if (fuse) {
+    FusedEnds fe{rr, ctx->kf_in, z, zold, part_rz, zold ? part_rzo : nullptr};
+    ST(vcycle_impl<float>(ctx, ctx->kf_in, ctx->kf_out, false, &fe));
+    *n_part = jacobi_grid(l0.n, l0.s);
+    return GASA_OK;
+  }
+  ST(apply_M(ctx, rr, z, precision));
+  CU(launch_dot_partials(n, rr, z, part_rz, ctx->stream));
+  if (zold) CU(launch_dot_partials(n, rr, zold, part_rzo, ctx->stream));
+  *n_part = kRedBlocks;
   return GASA_OK;
 }
 
@@ -541,8 +592,7 @@ gasa_status pcg(gasa_ctx *ctx, const double *b, double tol, int precision, int *
   const int64_t n = ctx->L[0].ndof;
   const bool flex = precision != GASA_PREC_FP64;
   double *x = ctx->kx, *r = ctx->kr, *z = ctx->kz, *p = ctx->kp, *q = ctx->kq, *zold = ctx->kzold;
-  double *pq_part = ctx->part, *rr_part = ctx->part + kRedBlocks,
-         *rz_part = ctx->part + 2 * kRedBlocks, *rzo_part = ctx->part + 3 * kRedBlocks;
+  double *pq_part = ctx->part, *rr_part = ctx->part + kRedBlocks;
   *conv = false;
   *iters = 0;
   double bb;
@@ -555,9 +605,9 @@ gasa_status pcg(gasa_ctx *ctx, const double *b, double tol, int precision, int *
     return GASA_OK;
   }
   CU(launch_copy(n, b, r, s));
-  ST(apply_M(ctx, r, z, precision));
-  CU(launch_dot_partials(n, r, z, rz_part, s));
-  CU(launch_finalize(rz_part, 1, ctx->scal + S_RZ0, s));
+  int np = 0;
+  ST(apply_M_cg(ctx, r, z, nullptr, precision, ctx->rz_ds, ctx->rzo_ds, &np));
+  CU(launch_finalize_n(ctx->rz_ds, np, ctx->scal + S_RZ0, s));
   CU(launch_copy(n, z, p, s));
   int cur = S_RZ0, nxt = S_RZ1;
   const int max_iter = ctx->opt.max_iter;
@@ -594,11 +644,9 @@ gasa_status pcg(gasa_ctx *ctx, const double *b, double tol, int precision, int *
       CU(launch_copy(n, ctx->kt, r, s));
     }
     if (flex) std::swap(z, zold);
-    ST(apply_M(ctx, r, z, precision));
-    CU(launch_dot_partials(n, r, z, rz_part, s));
-    if (flex) CU(launch_dot_partials(n, r, zold, rzo_part, s));
-    CU(launch_cg_update_p(n, p, z, ctx->scal + cur, rz_part, rzo_part, ctx->scal + nxt, flex ? 1 : 0,
-                          s));
+    ST(apply_M_cg(ctx, r, z, flex ? zold : nullptr, precision, ctx->rz_ds, ctx->rzo_ds, &np));
+    CU(launch_cg_update_p(n, p, z, ctx->scal + cur, ctx->rz_ds, ctx->rzo_ds, ctx->scal + nxt,
+                          flex ? 1 : 0, s, nullptr, nullptr, nullptr, np));
     std::swap(cur, nxt);
   }
   ST(spmv_outer(ctx, GASA_MV_RESIDUAL, x, b, ctx->kt));
@@ -636,21 +684,19 @@ gasa_status build_cg_graph(gasa_ctx *ctx, int precision) {
   CU(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   double *x = ctx->kx, *r = ctx->kr, *z = ctx->kz, *p = ctx->kp, *q = ctx->kq, *zold = ctx->kzold;
-  double *pq_part = ctx->part, *rr_part = ctx->part + kRedBlocks,
-         *rz_part = ctx->part + 2 * kRedBlocks, *rzo_part = ctx->part + 3 * kRedBlocks;
+  double *pq_part = ctx->part, *rr_part = ctx->part + kRedBlocks;
   const bool prof = ctx->prof;
   ctx->prof = false;   // no event records inside a graph body
   const long long k0 = launch_count();
   CU(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  gasa_status st = apply_M(ctx, r, z, precision);
+  int np = 0;
+  gasa_status st =
+      apply_M_cg(ctx, r, z, flex ? zold : nullptr, precision, ctx->rz_ds, ctx->rzo_ds, &np);
   cudaError_t e = cudaSuccess;
   if (st == GASA_OK) {
-    e = launch_dot_partials(n, r, z, rz_part, s);
-    if (e == cudaSuccess && flex) e = launch_dot_partials(n, r, zold, rzo_part, s);
-    if (e == cudaSuccess)
-      e = launch_cg_update_p(n, p, z, ctx->scal + S_RZ0, rz_part, rzo_part, ctx->scal + S_RZ1,
-                             flex ? 1 : 0, s, flex ? zold : nullptr, flex ? ctx->kp_hi : nullptr,
-                             flex ? ctx->kp_lo : nullptr);
+    e = launch_cg_update_p(n, p, z, ctx->scal + S_RZ0, ctx->rz_ds, ctx->rzo_ds, ctx->scal + S_RZ1,
+                           flex ? 1 : 0, s, flex ? zold : nullptr, flex ? ctx->kp_hi : nullptr,
+                           flex ? ctx->kp_lo : nullptr, np);
     Level &l = ctx->L[0];
     if (e == cudaSuccess && flex) {
       // q = A p with the p . q partials in the same launch
@@ -1569,6 +1615,9 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
   ST(dalloc(ctx, &ctx->kp_lo, (size_t)n));
   ctx->n_pq_ds = bsr_mv_ds_grid(ctx->L[0].n, ctx->L[0].s);
   ST(dalloc(ctx, &ctx->pq_ds, (size_t)ctx->n_pq_ds));
+  ctx->n_rz_cap = std::max(kRedBlocks, jacobi_grid(ctx->L[0].n, std::min(ctx->L[0].s, 256)));
+  ST(dalloc(ctx, &ctx->rz_ds, (size_t)ctx->n_rz_cap));
+  ST(dalloc(ctx, &ctx->rzo_ds, (size_t)ctx->n_rz_cap));
   ST(dalloc(ctx, &ctx->d_iters, 4));
   ST(dalloc(ctx, &ctx->d_err, 4));
   CU(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));

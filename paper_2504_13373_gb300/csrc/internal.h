@@ -57,6 +57,19 @@ cudaError_t launch_jacobi(int mode, int n_units, int bs, const int *rp, const in
                           const T *val, const T *W, const T *x, const T *b, T *xo,
                           cudaStream_t s, int64_t nnzb = -1);
 
+// The two ends of the level-0 FP32 smoothing in the mixed-precision CG step,
+// fused with their precision conversions (cudaErrorNotSupported when the
+// block size or alignment does not fit): the first step x = W b reading the
+// FP64 b (b32 receives its FP32 rounding), and the last step writing the FP64
+// z with jacobi_grid(n_units, bs) partial sums of r . z and r . zold.
+int jacobi_grid(int n_units, int bs);
+cudaError_t launch_jacobi_first_conv(int n_units, int bs, const double *bd, float *b32,
+                                     const float *W, float *xo, cudaStream_t s);
+cudaError_t launch_jacobi_last(int n_units, int bs, const int *rp, const int *col,
+                               const float *val, const float *W, const float *x, const float *b,
+                               double *z, const double *rd, const double *zold, double *part_rz,
+                               double *part_rzo, cudaStream_t s);
+
 // multi-column relaxation x_c <- x_c - W A x_c for `nc` columns given by
 // device tables of column base pointers (each column n_units*bs long).
 cudaError_t launch_relax_multi(int n_units, int bs, const int *rp, const int *col,
@@ -91,6 +104,8 @@ cudaError_t launch_colnorm_partials(int64_t n, const double *const *cols, int nc
                                     double *partials, cudaStream_t s);
 // out[c] = sum of partials of column c (one block per column)
 cudaError_t launch_finalize(const double *partials, int nc, double *out, cudaStream_t s);
+// out[0] = sum of n partials
+cudaError_t launch_finalize_n(const double *partials, int n, double *out, cudaStream_t s);
 cudaError_t launch_scale_by_inv_sqrt(int64_t n, double *x, const double *sumsq, cudaStream_t s);
 cudaError_t launch_uniform_pm1(int64_t n, uint64_t seed, uint64_t stream, double *x,
                                cudaStream_t s);
@@ -117,8 +132,7 @@ cudaError_t launch_cg_update_xr(int64_t n, double *x, double *r, const double *p
 cudaError_t launch_cg_update_p(int64_t n, double *p, const double *z, const double *rz_old,
                                const double *rz_partials, const double *rzold_partials,
                                double *rz_out, int flexible, cudaStream_t s,
-                               double *zold_out = nullptr, float *p_hi = nullptr,
-                               float *p_lo = nullptr);
+                               double *zold_out, float *p_hi, float *p_lo, int n_rz);
 // exact two-term FP32 split v = hi + lo of an FP64 vector
 cudaError_t launch_split(int64_t n, const double *v, float *hi, float *lo, cudaStream_t s);
 cudaError_t launch_cg_check(const double *rr_partials, double *scal, int *iters, int max_iter,

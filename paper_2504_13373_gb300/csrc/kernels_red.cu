@@ -124,6 +124,21 @@ finalize_kernel(const double *__restrict__ partials, double *__restrict__ out) {
   if (threadIdx.x == 0) out[blockIdx.x] = v;
 }
 
+// one sum of n partials (same order as block_sum_partials elsewhere)
+__global__ void __launch_bounds__(kRedThreads)
+finalize_n_kernel(const double *__restrict__ partials, int n, double *__restrict__ out) {
+  pdl_entry();
+  __shared__ double sh[32];
+  const double v = block_sum_partials(partials, n, sh);
+  if (threadIdx.x == 0) out[0] = v;
+}
+
+cudaError_t launch_finalize_n(const double *partials, int n, double *out, cudaStream_t s) {
+  launch_k(finalize_n_kernel, 1, kRedThreads, 0, s, partials, n, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const double *partials, int nc, double *out, cudaStream_t s) {
   if (nc == 0) return cudaSuccess;
   launch_k(finalize_kernel, nc, kRedThreads, 0, s, partials, out); note_launch();
@@ -417,12 +432,12 @@ cg_update_p_kernel(int64_t n, double *__restrict__ p, const double *__restrict__
                    const double *__restrict__ rz_old, const double *__restrict__ rz_partials,
                    const double *__restrict__ rzold_partials, double *__restrict__ rz_out,
                    int flexible, double *__restrict__ zold_out, float *__restrict__ p_hi,
-                   float *__restrict__ p_lo) {
+                   float *__restrict__ p_lo, int n_rz) {
   pdl_entry();
   __shared__ double sh[32];
-  const double rz_new = block_sum_partials(rz_partials, kRedBlocks, sh);
+  const double rz_new = block_sum_partials(rz_partials, n_rz, sh);
   double num = rz_new;
-  if (flexible) num -= block_sum_partials(rzold_partials, kRedBlocks, sh);
+  if (flexible) num -= block_sum_partials(rzold_partials, n_rz, sh);
   const double beta = num / rz_old[0];
   if (blockIdx.x == 0 && threadIdx.x == 0) rz_out[0] = rz_new;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -461,13 +476,13 @@ cg_update_p_kernel(int64_t n, double *__restrict__ p, const double *__restrict__
 cudaError_t launch_cg_update_p(int64_t n, double *p, const double *z, const double *rz_old,
                                const double *rz_partials, const double *rzold_partials,
                                double *rz_out, int flexible, cudaStream_t s, double *zold_out,
-                               float *p_hi, float *p_lo) {
+                               float *p_hi, float *p_lo, int n_rz) {
   if (al16(p) && al16(z) && (!zold_out || al16(zold_out)))
     launch_k(cg_update_p_kernel<true>, kRedBlocks, kRedThreads, 0, s, n, p, z, rz_old,
-             rz_partials, rzold_partials, rz_out, flexible, zold_out, p_hi, p_lo);
+             rz_partials, rzold_partials, rz_out, flexible, zold_out, p_hi, p_lo, n_rz);
   else
     launch_k(cg_update_p_kernel<false>, kRedBlocks, kRedThreads, 0, s, n, p, z, rz_old,
-             rz_partials, rzold_partials, rz_out, flexible, zold_out, p_hi, p_lo);
+             rz_partials, rzold_partials, rz_out, flexible, zold_out, p_hi, p_lo, n_rz);
   note_launch();
   return cudaGetLastError();
 }
