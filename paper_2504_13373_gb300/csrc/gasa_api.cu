@@ -520,14 +520,16 @@ gasa_status apply_M(gasa_ctx *ctx, const double *rr, double *z, int precision) {
 
 // z = M r for the CG step together with the partial sums of r . z (and of
 // r . zold when zold is given): one fused pass at the ends of the FP32
-// V-cycle where the level-0 layout allows (MIXED32, plain level-0 sweeps,
-// blocks of at most 16), else the V-cycle and two dot-product launches.
+// V-cycle where the level-0 layout allows (MIXED32, blocks of at most 16),
+// else the V-cycle and two dot-product launches.
 // *n_part receives the number of partials per product.
 gasa_status apply_M_cg(gasa_ctx *ctx, const double *rr, double *z, const double *zold,
                        int precision, double *part_rz, double *part_rzo, int *n_part) {
   Level &l0 = ctx->L[0];
   const int64_t n = l0.ndof;
-  const bool fuse = precision == GASA_PREC_MIXED32 && !l0.tma && !l0.mf && l0.s <= 16 &&
+  // (with bulk staging the middle steps are staged; the staged and the plain
+  // step give the same bits, so the fused ends fit either)
+  const bool fuse = precision == GASA_PREC_MIXED32 && !l0.mf && l0.s <= 16 &&
                     ctx->opt.t_pre >= 1 && ctx->opt.t_post >= 1;
   if (fuse) {
     FusedEnds fe{rr, ctx->kf_in, z, zold, part_rz, zold ? part_rzo : nullptr};
