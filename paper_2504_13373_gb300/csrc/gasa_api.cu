@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <type_traits>
@@ -529,8 +530,10 @@ gasa_status apply_M_cg(gasa_ctx *ctx, const double *rr, double *z, const double 
   const int64_t n = l0.ndof;
   // (with bulk staging the middle steps are staged; the staged and the plain
   // step give the same bits, so the fused ends fit either)
+  // (GASA_FUSE_ENDS=0 in the environment keeps them apart, for A/B timing)
+  const char *env = std::getenv("GASA_FUSE_ENDS");
   const bool fuse = precision == GASA_PREC_MIXED32 && !l0.mf && l0.s <= 16 &&
-                    ctx->opt.t_pre >= 1 && ctx->opt.t_post >= 1;
+                    ctx->opt.t_pre >= 1 && ctx->opt.t_post >= 1 && !(env && env[0] == '0');
   if (fuse) {
     FusedEnds fe{rr, ctx->kf_in, z, zold, part_rz, zold ? part_rzo : nullptr};
     ST(vcycle_impl<float>(ctx, ctx->kf_in, ctx->kf_out, false, &fe));
