@@ -369,17 +369,16 @@ gasa_status tail_build(gasa_ctx *ctx, int pi) {
   return GASA_OK;
 }
 
-// The mixed-precision CG step's V-cycle with its precision conversions and
-// the two dot products that follow it folded into the first and the last
-// level-0 smoothing steps: r (FP64) is read by the first step, which leaves
-// its FP32 rounding in b32; the last step writes z (FP64) and the partial
-// sums of r . z and r . zold (n_part per product).
+// The FP32 V-cycle's first level-0 step reads the FP64 right-hand side r
+// itself and leaves its FP32 rounding in b32 (the conversion then needs no
+// launch of its own; same bits).  Folding the conversion of z and the dot
+// products r . z, r . zold into the last step as well was measured slower
+// (0.777 vs 0.767 ms per CG iteration on the P3 256x256 workload): the two
+// block reductions and FP64 reads slow the HBM-bound sweep by more than the
+// launches they save.
 struct FusedEnds {
   const double *r;
   float *b32;
-  double *z;
-  const double *zold;
-  double *part_rz, *part_rzo;
 };
 
 template <typename T>
@@ -492,15 +491,7 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false,
       T *dst = (k == 0 && t == tpost - 1) ? out : x2;
       cudaEvent_t e0;
       if (k == 0) prof_begin(ctx, 0, &e0);
-      bool done = false;
-      if constexpr (std::is_same<T, float>::value) {
-        if (k == 0 && t == tpost - 1 && fe) {
-          CU(launch_jacobi_last(l.n, l.s, l.A.rp, l.A.col, P::A(l.A), P::W(l), x, bk[0], fe->z,
-                                fe->r, fe->zold, fe->part_rz, fe->part_rzo, s));
-          done = true;
-        }
-      }
-      if (!done) CU(sweep(k, JAC_SWEEP, x, bk[k], dst));
+      CU(sweep(k, JAC_SWEEP, x, bk[k], dst));
       if (k == 0) prof_end(ctx, 0, sweep_bytes(l, w, false, wa));
       if (dst == x2) std::swap(x, x2);
       else x = dst;
@@ -512,34 +503,24 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false,
 
 gasa_status apply_M(gasa_ctx *ctx, const double *rr, double *z, int precision) {
   if (precision == GASA_PREC_FP64) return vcycle_impl<double>(ctx, rr, z);
-  const int64_t n = ctx->L[0].ndof;
-  CU(launch_convert<double, float>(n, rr, ctx->kf_in, ctx->stream));
-  ST(vcycle_impl<float>(ctx, ctx->kf_in, ctx->kf_out, precision == GASA_PREC_MIXED16));
+  Level &l0 = ctx->L[0];
+  const int64_t n = l0.ndof;
+  if (precision == GASA_PREC_MIXED32 && !l0.mf && l0.s <= 16 && ctx->opt.t_pre >= 1) {
+    FusedEnds fe{rr, ctx->kf_in};
+    ST(vcycle_impl<float>(ctx, ctx->kf_in, ctx->kf_out, false, &fe));
+  } else {
+    CU(launch_convert<double, float>(n, rr, ctx->kf_in, ctx->stream));
+    ST(vcycle_impl<float>(ctx, ctx->kf_in, ctx->kf_out, precision == GASA_PREC_MIXED16));
+  }
   CU(launch_convert<float, double>(n, ctx->kf_out, z, ctx->stream));
   return GASA_OK;
 }
 
-// z = M r for the CG step together with the partial sums of r . z (and of
-// r . zold when zold is given): one fused pass at the ends of the FP32
-// V-cycle where the level-0 layout allows (MIXED32, blocks of at most 16),
-// else the V-cycle and two dot-product launches.
-// *n_part receives the number of partials per product.
+// z = M r for the CG step and the partial sums of r . z (and of r . zold
+// when zold is given); *n_part receives the number of partials per product
 gasa_status apply_M_cg(gasa_ctx *ctx, const double *rr, double *z, const double *zold,
                        int precision, double *part_rz, double *part_rzo, int *n_part) {
-  Level &l0 = ctx->L[0];
-  const int64_t n = l0.ndof;
-  // (with bulk staging the middle steps are staged; the staged and the plain
-  // step give the same bits, so the fused ends fit either)
-  // (GASA_FUSE_ENDS=0 in the environment keeps them apart, for A/B timing)
-  const char *env = std::getenv("GASA_FUSE_ENDS");
-  const bool fuse = precision == GASA_PREC_MIXED32 && !l0.mf && l0.s <= 16 &&
-                    ctx->opt.t_pre >= 1 && ctx->opt.t_post >= 1 && !(env && env[0] == '0');
-  if (fuse) {
-    FusedEnds fe{rr, ctx->kf_in, z, zold, part_rz, zold ? part_rzo : nullptr};
-    ST(vcycle_impl<float>(ctx, ctx->kf_in, ctx->kf_out, false, &fe));
-    *n_part = jacobi_grid(l0.n, l0.s);
-    return GASA_OK;
-  }
+  const int64_t n = ctx->L[0].ndof;
   ST(apply_M(ctx, rr, z, precision));
   CU(launch_dot_partials(n, rr, z, part_rz, ctx->stream));
   if (zold) CU(launch_dot_partials(n, rr, zold, part_rzo, ctx->stream));
@@ -575,6 +556,15 @@ gasa_status spmv_outer(gasa_ctx *ctx, int mode, const double *x, const double *b
   return GASA_OK;
 }
 
+// p . q partials inside the double-single product launch (GASA_DS_DOT=0 in
+// the environment uses a separate dot-product launch instead, for A/B timing;
+// the partial count then is kRedBlocks)
+bool ds_dot() {
+  const char *e = std::getenv("GASA_DS_DOT");
+  return !(e && e[0] == '0');
+}
+int pq_ds_count(gasa_ctx *ctx) { return ds_dot() ? ctx->n_pq_ds : kRedBlocks; }
+
 // q = A p of the mixed-precision Krylov step: double-single arithmetic on
 // the FP32 splits of A (val32 + lo32) and of p (kp_hi + kp_lo, written by the
 // CG update or, with split_p, here); the same launch leaves the partial sums
@@ -586,7 +576,8 @@ gasa_status spmv_outer_ds(gasa_ctx *ctx, const double *p, double *q, bool split_
   cudaEvent_t e0;
   prof_begin(ctx, 2, &e0);
   CU(launch_bsr_mv_ds(l.n, l.s, l.s, l.A.rp, l.A.col, l.A.val32, l.A.lo32, ctx->kp_hi,
-                      ctx->kp_lo, q, ctx->stream, p, ctx->pq_ds));
+                      ctx->kp_lo, q, ctx->stream, ds_dot() ? p : nullptr, ctx->pq_ds));
+  if (!ds_dot()) CU(launch_dot_partials(n, p, q, ctx->pq_ds, ctx->stream));
   prof_end(ctx, 2, spmv_bytes(l, 8, false));   // 4 + 4 bytes per value and per x entry
   return GASA_OK;
 }
@@ -624,7 +615,7 @@ gasa_status pcg(gasa_ctx *ctx, const double *b, double tol, int precision, int *
       CU(launch_dot_partials(n, p, q, pq_part, s));
     }
     CU(launch_cg_update_xr(n, x, r, p, q, ctx->scal + cur, flex ? ctx->pq_ds : pq_part, rr_part,
-                           ctx->scal + S_ALPHA, s, flex ? ctx->n_pq_ds : kRedBlocks));
+                           ctx->scal + S_ALPHA, s, flex ? pq_ds_count(ctx) : kRedBlocks));
     CU(launch_finalize(rr_part, 1, ctx->scal + S_RR, s));
     ST(read_scalars(ctx, 0, 3));
     const double pq = ctx->hscal[S_PQ];
@@ -706,7 +697,8 @@ gasa_status build_cg_graph(gasa_ctx *ctx, int precision) {
     if (e == cudaSuccess && flex) {
       // q = A p with the p . q partials in the same launch
       e = launch_bsr_mv_ds(l.n, l.s, l.s, l.A.rp, l.A.col, l.A.val32, l.A.lo32, ctx->kp_hi,
-                           ctx->kp_lo, q, s, p, ctx->pq_ds);
+                           ctx->kp_lo, q, s, ds_dot() ? p : nullptr, ctx->pq_ds);
+      if (e == cudaSuccess && !ds_dot()) e = launch_dot_partials(n, p, q, ctx->pq_ds, s);
     } else if (e == cudaSuccess) {
       e = launch_bsr_mv<double>(GASA_MV_ASSIGN, l.n, l.s, l.s, l.A.rp, l.A.col, l.A.val, p, nullptr,
                                 q, s);
@@ -714,7 +706,7 @@ gasa_status build_cg_graph(gasa_ctx *ctx, int precision) {
     }
     if (e == cudaSuccess)
       e = launch_cg_update_xr(n, x, r, p, q, ctx->scal + S_RZ1, flex ? ctx->pq_ds : pq_part,
-                              rr_part, ctx->scal + S_ALPHA, s, flex ? ctx->n_pq_ds : kRedBlocks);
+                              rr_part, ctx->scal + S_ALPHA, s, flex ? pq_ds_count(ctx) : kRedBlocks);
     if (e == cudaSuccess) e = launch_cg_check(rr_part, ctx->scal, ctx->d_iters, max_iter, h, s);
   }
   cudaGraph_t captured = nullptr;

@@ -57,18 +57,13 @@ cudaError_t launch_jacobi(int mode, int n_units, int bs, const int *rp, const in
                           const T *val, const T *W, const T *x, const T *b, T *xo,
                           cudaStream_t s, int64_t nnzb = -1);
 
-// The two ends of the level-0 FP32 smoothing in the mixed-precision CG step,
-// fused with their precision conversions (cudaErrorNotSupported when the
-// block size or alignment does not fit): the first step x = W b reading the
-// FP64 b (b32 receives its FP32 rounding), and the last step writing the FP64
-// z with jacobi_grid(n_units, bs) partial sums of r . z and r . zold.
+// The first level-0 FP32 smoothing step of the mixed-precision V-cycle,
+// x = W b from x = 0, reading the FP64 b; b32 receives its FP32 rounding for
+// the later steps (cudaErrorNotSupported when the block size or the
+// alignment does not fit).
 int jacobi_grid(int n_units, int bs);
 cudaError_t launch_jacobi_first_conv(int n_units, int bs, const double *bd, float *b32,
                                      const float *W, float *xo, cudaStream_t s);
-cudaError_t launch_jacobi_last(int n_units, int bs, const int *rp, const int *col,
-                               const float *val, const float *W, const float *x, const float *b,
-                               double *z, const double *rd, const double *zold, double *part_rz,
-                               double *part_rzo, cudaStream_t s);
 
 // multi-column relaxation x_c <- x_c - W A x_c for `nc` columns given by
 // device tables of column base pointers (each column n_units*bs long).

@@ -551,76 +551,6 @@ jacobi_first_conv_kernel(int n_units, const double *__restrict__ bd, float *__re
   xo[row] = out;
 }
 
-// Last post-smoothing step of the mixed-precision V-cycle, x + W (b - A x) as
-// jacobi_kernel in SWEEP mode, written as the FP64 preconditioned residual z
-// (exact widening), with per-CTA partial sums of r . z and r . zold (zold
-// nullable) for the flexible CG step that follows, summed in a fixed order.
-template <int BS>
-__global__ void __launch_bounds__(256)
-jacobi_last_kernel(int n_units, const int *__restrict__ rp, const int *__restrict__ col,
-                   const float *__restrict__ val, const float *__restrict__ Wm,
-                   const float *__restrict__ x, const float *__restrict__ b,
-                   double *__restrict__ z, const double *__restrict__ rd,
-                   const double *__restrict__ zold, double *__restrict__ part_rz,
-                   double *__restrict__ part_rzo) {
-  pdl_entry();
-  __shared__ float res[256];
-  __shared__ double sh[32];
-  constexpr int RPB = 256 / BS;
-  constexpr int W = RowVec<float, BS>::value;
-  const int li = threadIdx.x / BS;
-  const int r = threadIdx.x - li * BS;
-  const int i = blockIdx.x * RPB + li;
-  const bool active = (li < RPB) && (i < n_units);
-  const size_t row = (size_t)i * BS + r;
-  const float *w = Wm + row * BS;
-  float v = 0.0f, b_row = 0.0f, x_row = 0.0f;
-  double r_row = 0.0, zo_row = 0.0;
-  if (active) {
-    b_row = b[row];
-    x_row = x[row];
-    r_row = rd[row];
-    if (zold) zo_row = zold[row];
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(w));
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(w + BS - 1));
-    const int beg = __ldg(rp + i), end = __ldg(rp + i + 1);
-    float acc = 0.0f;
-    for (int k = beg; k < end; ++k) {
-      const int j = __ldg(col + k);
-      const float *a = val + ((size_t)k * BS + r) * BS;
-      const float *xj = x + (size_t)j * BS;
-      float av[BS], xv[BS];
-#pragma unroll
-      for (int c = 0; c < BS; c += W) load_vec_stream<float, W>(a + c, av + c);
-#pragma unroll
-      for (int c = 0; c < BS; c += W) load_vec<float, W>(xj + c, xv + c);
-#pragma unroll
-      for (int c = 0; c < BS; ++c) acc = fmaf(av[c], xv[c], acc);
-    }
-    v = b_row - acc;
-  }
-  res[threadIdx.x] = v;
-  __syncthreads();
-  double zt = 0.0;
-  if (active) {
-    float wv[BS];
-#pragma unroll
-    for (int c = 0; c < BS; c += W) load_vec_stream<float, W>(w + c, wv + c);
-    float out = 0.0f;
-#pragma unroll
-    for (int c = 0; c < BS; ++c) out = fmaf(wv[c], res[li * BS + c], out);
-    out += x_row;
-    zt = (double)out;
-    z[row] = zt;
-  }
-  const double s_rz = block_sum(r_row * zt, sh);
-  const double s_rzo = block_sum(r_row * zo_row, sh);
-  if (threadIdx.x == 0) {
-    part_rz[blockIdx.x] = s_rz;
-    if (part_rzo) part_rzo[blockIdx.x] = s_rzo;
-  }
-}
-
 int jacobi_grid(int n_units, int bs) { return div_up(n_units, 256 / bs); }
 
 cudaError_t launch_jacobi_first_conv(int n_units, int bs, const double *bd, float *b32,
@@ -639,30 +569,6 @@ cudaError_t launch_jacobi_first_conv(int n_units, int bs, const double *bd, floa
     GASA_FC_CASE(16)
   }
 #undef GASA_FC_CASE
-  note_launch();
-  return cudaGetLastError();
-}
-
-cudaError_t launch_jacobi_last(int n_units, int bs, const int *rp, const int *col,
-                               const float *val, const float *W, const float *x, const float *b,
-                               double *z, const double *rd, const double *zold, double *part_rz,
-                               double *part_rzo, cudaStream_t s) {
-  if (n_units == 0) return cudaSuccess;
-  if (!aligned16(W) || !aligned16(val) || !aligned16(x) || bs < 1 || bs > 16)
-    return cudaErrorNotSupported;
-  const int grid = jacobi_grid(n_units, bs);
-#define GASA_LC_CASE(BS)                                                                      \
-  case BS:                                                                                    \
-    launch_k(jacobi_last_kernel<BS>, grid, 256, 0, s, n_units, rp, col, val, W, x, b, z, rd,  \
-             zold, part_rz, part_rzo);                                                        \
-    break;
-  switch (bs) {
-    GASA_LC_CASE(1) GASA_LC_CASE(2) GASA_LC_CASE(3) GASA_LC_CASE(4) GASA_LC_CASE(5)
-    GASA_LC_CASE(6) GASA_LC_CASE(7) GASA_LC_CASE(8) GASA_LC_CASE(9) GASA_LC_CASE(10)
-    GASA_LC_CASE(11) GASA_LC_CASE(12) GASA_LC_CASE(13) GASA_LC_CASE(14) GASA_LC_CASE(15)
-    GASA_LC_CASE(16)
-  }
-#undef GASA_LC_CASE
   note_launch();
   return cudaGetLastError();
 }
