@@ -471,17 +471,10 @@ jacobi_kernel(int n_units, const int *__restrict__ rp, const int *__restrict__ c
   const int i = blockIdx.x * RPB + li;
   const bool active = (li < RPB) && (i < n_units);
   const size_t row = (size_t)i * BS + r;
-  const T *w = Wm + row * BS;
-  T v = T(0), b_row = T(0), x_row = T(0);
+  T v = T(0);
   if (active) {
-    // operands of the epilogue first: b and x of this row into registers and
-    // this row of W into L2, so that their latency overlaps the block loop
-    if (MODE == JAC_SWEEP || MODE == JAC_FIRST) b_row = b[row];
-    if (MODE == JAC_SWEEP || MODE == JAC_RELAX) x_row = x[row];
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(w));
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(w + BS - 1));
     if (MODE == JAC_FIRST) {
-      v = b_row;
+      v = b[row];
     } else {
       const int beg = __ldg(rp + i), end = __ldg(rp + i + 1);
       T acc = T(0);
@@ -497,7 +490,7 @@ jacobi_kernel(int n_units, const int *__restrict__ rp, const int *__restrict__ c
 #pragma unroll
         for (int c = 0; c < BS; ++c) acc = fma(av[c], xv[c], acc);
       }
-      if (MODE == JAC_SWEEP) v = b_row - acc;
+      if (MODE == JAC_SWEEP) v = b[row] - acc;
       else if (MODE == JAC_RELAX) v = -acc;
       else v = acc;
     }
@@ -505,13 +498,14 @@ jacobi_kernel(int n_units, const int *__restrict__ rp, const int *__restrict__ c
   res[threadIdx.x] = v;
   __syncthreads();
   if (!active) return;
+  const T *w = Wm + row * BS;
   T wv[BS];
 #pragma unroll
   for (int c = 0; c < BS; c += W) load_vec_stream<T, W>(w + c, wv + c);
   T out = T(0);
 #pragma unroll
   for (int c = 0; c < BS; ++c) out = fma(wv[c], res[li * BS + c], out);
-  if (MODE == JAC_SWEEP || MODE == JAC_RELAX) out += x_row;
+  if (MODE == JAC_SWEEP || MODE == JAC_RELAX) out += x[row];
   xo[row] = out;
 }
 
