@@ -413,11 +413,6 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false,
       if (e == cudaSuccess) e = launch_add<T>(l.ndof, xin, xo, s);
       return e;
     }
-    if (k == 0 && mode == JAC_SWEEP && jacobi_u2_enabled()) {
-      const cudaError_t e = launch_jacobi_u2<T>(l.n, l.s, l.A.rp, l.A.col, P::A(l.A), P::W(l), xin,
-                                                bb, xo, s);
-      if (e != cudaErrorNotSupported) return e;
-    }
     return launch_jacobi<T>(mode, l.n, l.s, l.A.rp, l.A.col, P::A(l.A), P::W(l), xin, bb, xo, s,
                             l.A.nnzb);
   };

@@ -44,12 +44,6 @@ template <typename T>
 cudaError_t launch_blk(int op, int n_brows, int bs, int64_t nnzb, const int *rp, const int *col,
                        const T *val, const T *W, const T *x, const T *b, T *y, cudaStream_t s);
 
-// ---- kernels_l0.cu: level-0 smoothing step, two blocks in flight (option) --
-bool jacobi_u2_enabled();
-template <typename T>
-cudaError_t launch_jacobi_u2(int n_units, int bs, const int *rp, const int *col, const T *val,
-                             const T *W, const T *x, const T *b, T *xo, cudaStream_t s);
-
 // ---- kernels_mv.cu ---------------------------------------------------------
 // nnzb >= 0 lets the launcher pick a warp per block row when rows are long
 // (>= 12 blocks on average); nnzb < 0 always uses one thread per scalar row.
