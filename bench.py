@@ -11,7 +11,8 @@ reported beside it.  Every matrix pass streams more than the 129 MB L2
 (A: 419 MB FP64, 209 MB FP32), so no L2 flush is needed between steps.
 
 Multi-GPU: the path does not shard; --gpus N runs N independent replicas
-(one process per GPU under torchrun) and reports the total solves/s.
+(one process per GPU under torchrun) and reports the total solves/s; the
+serving stream (a per-GPU measurement) runs at N = 1 only.
 
 --impl reference times the CPU oracle on the host cores instead.
 """
@@ -594,7 +595,8 @@ def ours_main(args, rank, world, local):
             line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
                                     "sample": f"failed: {err}"}
     gasa.gasa_destroy(ctx)
-    if args.serve_requests > 0:
+    if args.serve_requests > 0 and world == 1:
+        # the serving stream is a per-GPU measurement: it runs at N = 1 only
         line["serving"] = serve_bench(gasa, args.serve_requests, local)
     if rank == 0:
         print(json.dumps(line))
