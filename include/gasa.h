@@ -115,12 +115,15 @@ typedef struct {
                                 of its candidate rows above delta * sigma_1 (Eq. sik, h*-branch);
                                 the given hierarchy follows one level lower.  0 (default): off */
   double delta;              /* h* threshold; 0 = the paper's 1e-3 */
-  int32_t tail_kib;          /* levels k >= 1 whose operator A_k takes at most this many KiB in
-                                the V-cycle's precision, together with every coarser level and
-                                the coarsest solve, run as one thread-block-cluster launch
-                                (kernels_tail.cu) instead of one launch per step; same
-                                arithmetic per row, so results agree with the per-step
-                                launches to rounding.  0 (default): one launch per step. */
+  int32_t tail_kib;          /* bottom of the V-cycle of Alg. 2 as one thread-block-cluster
+                                launch (kernels_tail.cu) instead of one launch per step: the
+                                deepest run of levels k >= 1 whose A_k takes at most this many
+                                KiB in the V-cycle's precision, with every coarser level and the
+                                coarsest solve, while A_N^{-1} takes at most 2 MB; top levels
+                                are left out until each CTA's rows and vectors fit its shared
+                                memory.  Same arithmetic per row, so results agree with the
+                                per-step launches to rounding.  0 (default): one launch per
+                                step (measured faster inside the graph-captured CG loop). */
 } gasa_options;
 
 typedef struct {
@@ -205,7 +208,9 @@ gasa_status gasa_level_shape(gasa_ctx *ctx, int32_t level, int64_t shape[8]);
  * first level k0 run inside the cluster launch (n_levels - 1 when every
  * level runs as its own launches), out[1] = CTAs per cluster (0 when
  * unfused), out[2] = 1 when the coarsest solve runs inside the launch.
- * GASA_PREC_MIXED16 reports the FP32 tail it shares with MIXED32. */
+ * GASA_PREC_MIXED16 reports the FP32 tail it shares with MIXED32.
+ * GASA_ERR_STATE before a successful gasa_setup, GASA_ERR_INVALID_ARG for an
+ * unknown precision or a null pointer. */
 gasa_status gasa_tail_info(gasa_ctx *ctx, int32_t precision, int32_t out[3]);
 gasa_status gasa_get_level(gasa_ctx *ctx, int32_t level, int32_t what,
                            void *host_out, int64_t n_bytes);
