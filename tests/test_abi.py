@@ -134,6 +134,14 @@ def test_single_ops_validate_before_device_work():
     assert L.gasa_jacobi_sweep(4, 0, None, None, None, None, None, None, None, 0, None) == gasa.GASA_ERR_INVALID_ARG
     assert L.gasa_tentative(4, 3, 9, None, None, 4, 2, None, None, None) == gasa.GASA_ERR_INVALID_ARG
     assert L.gasa_dense_inverse(0, None, None, None, None) == gasa.GASA_ERR_INVALID_ARG
+    # double-single product: sizes and pointers checked on the host
+    assert L.gasa_bsr_mv_ds(-1, 1, 1, None, None, None, None, None, None, None, None) == gasa.GASA_ERR_INVALID_ARG
+    assert L.gasa_bsr_mv_ds(4, 0, 1, None, None, None, None, None, None, None, None) == gasa.GASA_ERR_INVALID_ARG
+    assert L.gasa_bsr_mv_ds(4, 2, 2, None, None, None, None, None, None, None, None) == gasa.GASA_ERR_INVALID_ARG
+    assert L.gasa_bsr_mv_ds(0, 2, 2, None, None, None, None, None, None, None, None) == gasa.GASA_OK
+    # tail query without a context
+    out = (ctypes.c_int32 * 3)()
+    assert L.gasa_tail_info(None, 0, out) == gasa.GASA_ERR_INVALID_ARG
     assert L.gasa_setup(None, None, None, None, None, None, None, None) == gasa.GASA_ERR_INVALID_ARG
     assert L.gasa_solve(None, None, None, ctypes.c_double(1e-10), 0, 0, None) == gasa.GASA_ERR_INVALID_ARG
     # server calls validate before device work
