@@ -1,0 +1,67 @@
+"""The double-single product used for the outer q = A p of the mixed-precision
+solve, emulated step by step in FP32 on the CPU, against exact rational
+arithmetic: a row of n terms stays within n * 2^-47 of sum |a x| of the exact
+sum (the bound the GPU test's 2^-40 is derived from), and far inside the
+2^-24 of a plain FP32 product.
+
+Emulation: FP32 products and sums are numpy float32 operations (IEEE round to
+nearest); the error of an FP32 product, e = a_hi x_hi - fl(a_hi x_hi), is
+formed exactly from the float64 product of the two FP32 factors (48
+significant bits) and is itself an FP32 number, which is what the kernel's
+fma(a_hi, x_hi, -p) yields.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+f32 = np.float32
+
+
+def split(v):
+    hi = np.asarray(v, dtype=np.float64).astype(np.float32)
+    lo = (np.asarray(v, dtype=np.float64) - hi.astype(np.float64)).astype(np.float32)
+    return hi, lo
+
+
+def ds_row(a, x):
+    """s + t of the kernel's recurrence for one row (float64 result)"""
+    ah, al = split(a)
+    xh, xl = split(x)
+    s, t = f32(0.0), f32(0.0)
+    for c in range(len(a)):
+        p = f32(ah[c] * xh[c])
+        e = f32(np.float64(ah[c]) * np.float64(xh[c]) - np.float64(p))
+        cross = f32(np.float64(ah[c]) * np.float64(xl[c]) + np.float64(f32(al[c] * xh[c])))
+        s1 = f32(s + p)
+        bp = f32(s1 - s)
+        err = f32(f32(s - f32(s1 - bp)) + f32(p - bp))
+        s = s1
+        t = f32(t + f32(err + f32(e + cross)))
+    return np.float64(s) + np.float64(t)
+
+
+@pytest.mark.parametrize("n,seed,spread", [(10, 1, 0.0), (40, 2, 0.0), (140, 3, 3.0), (700, 4, 0.0),
+                                           (700, 5, 6.0)])
+def test_double_single_row_within_bound(n, seed, spread):
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal(n) * 10.0 ** rng.uniform(-spread, spread, n)
+    x = rng.standard_normal(n)
+    exact = sum(Fraction(float(ai)) * Fraction(float(xi)) for ai, xi in zip(a, x))
+    absum = float(np.sum(np.abs(a * x)))
+    got = ds_row(a, x)
+    err = abs(Fraction(float(got)) - exact)
+    assert float(err) <= n * 2.0 ** -47 * absum
+    # a plain FP32 product of the same row is orders of magnitude worse
+    p32 = f32(0.0)
+    for ai, xi in zip(a.astype(np.float32), x.astype(np.float32)):
+        p32 = f32(p32 + f32(ai * xi))
+    assert float(abs(Fraction(float(p32)) - exact)) > 1e3 * float(err)
+
+
+def test_split_is_exact_to_2_pow_48():
+    rng = np.random.default_rng(7)
+    v = rng.standard_normal(1000) * 10.0 ** rng.uniform(-5, 5, 1000)
+    hi, lo = split(v)
+    rel = np.abs(hi.astype(np.float64) + lo.astype(np.float64) - v) / np.abs(v)
+    assert np.max(rel) <= 2.0 ** -48
