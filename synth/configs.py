@@ -154,20 +154,22 @@ def convdiff3d(n: int = 16, p: int = 1, peclet: float = 100.0, r: Optional[int] 
     return pr
 
 
-def poisson3d_hex(M: int = 4, p: int = 1, r: Optional[int] = None, seed: int = SEED) -> Problem:
+def poisson3d_hex(M: int = 4, p: int = 1, r: Optional[int] = None, seed: int = SEED,
+                  flux: str = "ip") -> Problem:
     """The paper's first elliptic test (Section 6.1): [-1, 1]^3 cut into 2^M
-    hexahedra per side, Q_p, SIPG with penalty M (p+1)^2 / 2, Dirichlet on
+    hexahedra per side, Q_p, interior penalty (flux='ip', penalty
+    (p+1)^2 / h) or minimal-dissipation LDG (flux='ldg'), Dirichlet on
     x = -1 and Neumann elsewhere; the right-hand side is the load vector of
     the manufactured solution exp(sin(pi x) sin(pi y) sin(pi z)) - 1 (not a
     random vector); levels by the paper's rule; r defaults to the level-1
     aggregate dofs."""
-    from .hex import hex_mesh, load_vector, sipg_hex
+    from .hex import hex_mesh, ldg_hex, load_vector, sipg_hex
     mesh = hex_mesh(M)
-    A = sipg_hex(mesh, p, M)
+    A = sipg_hex(mesh, p) if flux == "ip" else ldg_hex(mesh, p)
     n_levels = paper_level_count(mesh.n_elems, 3)
     if r is None:
         r = 8 * A.b
-    pr = _finish(f"poisson3d_hex_q{p}_M{M}", mesh, A, n_levels, r, "cg", p, seed)
+    pr = _finish(f"poisson3d_hex_{flux}_q{p}_M{M}", mesh, A, n_levels, r, "cg", p, seed)
     pr.rhs = load_vector(mesh, p)
     pr.extra["M"] = M
     return pr

@@ -5,9 +5,16 @@ Mesh: 2^M hexahedra per side, tensor-product Q_p on each.  Problem:
 -Laplace(u) = f with Dirichlet data on the face x = -1 and Neumann data on
 the other five faces, manufactured solution
 u = exp(sin(pi x) sin(pi y) sin(pi z)) - 1 (zero on x = -1).  SIPG with the
-paper's penalty parameter mu = M (p + 1)^2 / 2, read as the face penalty
-sigma = mu / h (h the element edge).  The Dirichlet face carries the usual
-symmetric boundary terms; Neumann faces enter the right-hand side only.
+paper's penalty parameter, printed as mu = M (p + 1)^2 / 2 (Section 6.1).
+It is read as mu = n (p + 1)^2 / 2 with n = 2^M hexahedra per side, i.e.
+the exponent of 2^M lost in the printed formula, and mu is the face
+penalty itself: since h = 2 / n, mu = (p + 1)^2 / h, the usual 1/h scaling
+of an interior-penalty coefficient.  (Reading M as the refinement level and
+dividing by h again gives M (p + 1)^2 / (2 h), which grows like log(1/h)/h;
+on that reading the oracle needs 11 pCG / 28 stationary iterations at
+M = 4 against the paper's 6 / 7, on this one 6 / 9.)  The Dirichlet face
+carries the usual symmetric boundary terms; Neumann faces enter the
+right-hand side only.
 
 Elements are numbered e = i + n (j + n k) for the cell (i, j, k); local face
 2a is the face at the low end of axis a, 2a + 1 the high end.  No
@@ -61,7 +68,13 @@ def _face_ref(p, a, side):
     return xi, ws
 
 
-def sipg_hex(mesh: Mesh, p: int, M: int, dirichlet_faces=((0, 0),)) -> BSR:
+def hex_penalty(mesh: Mesh, p: int) -> float:
+    """Face penalty mu = n (p + 1)^2 / 2 = (p + 1)^2 / h (n hexahedra per
+    side of [-1, 1], h = 2 / n)."""
+    return mesh.n * (p + 1) ** 2 / 2.0
+
+
+def sipg_hex(mesh: Mesh, p: int, dirichlet_faces=((0, 0),)) -> BSR:
     """SIPG for -Laplace on the regular hex mesh; dirichlet_faces lists
     (axis, side) pairs of the domain faces with Dirichlet data (default
     x = -1); the others are Neumann."""
@@ -70,7 +83,7 @@ def sipg_hex(mesh: Mesh, p: int, M: int, dirichlet_faces=((0, 0),)) -> BSR:
     nb = ref.nb
     ne = mesh.n_elems
     h = mesh.h
-    sigma = M * (p + 1) ** 2 / 2.0 / h
+    sigma = hex_penalty(mesh, p)
     ptr, col, key = face_pattern(ne, mesh.int_faces)
     val = np.zeros((col.size, nb, nb))
     diag = block_pos(key, ne, np.arange(ne), np.arange(ne))
@@ -119,6 +132,103 @@ def sipg_hex(mesh: Mesh, p: int, M: int, dirichlet_faces=((0, 0),)) -> BSR:
                    + sigma * np.einsum("q,qi,qj->ij", wf, ph, ph))
             val[diag[B[:, 0]]] += blk[None]
     return BSR(ne, nb, ptr, col, val)
+
+
+def ldg_hex(mesh: Mesh, p: int, dirichlet_faces=((0, 0),)) -> BSR:
+    """Minimal-dissipation LDG for -Laplace on the regular hex mesh (the
+    paper's second flux in Section 6.1).  q = grad u is lifted element by
+    element: M q^d_K = G^d u_K + sum_F int_F (u_hat - u_K) n_d phi, then
+    A u = sum_d [ (G^d)^T q^d - sum_F int_F q_hat_d n_d phi ].  Switch vector
+    beta = (1, 1, 1): on an interior face u_hat comes from the element on the
+    -beta side (the low one) and q_hat from the +beta side, with no jump
+    penalty (C11 = 0).  On a Dirichlet face u_hat = 0 and
+    q_hat = q - C11 u n with C11 the face penalty of `hex_penalty`; on a
+    Neumann face u_hat = u and q_hat . n is data (right-hand side only).
+    The lifted gradients couple an element with neighbours of neighbours,
+    so A has a wider block stencil than SIPG; it is symmetric."""
+    import scipy.sparse as sp
+    assert mesh.kind == "hex"
+    ref = tensor_ref(3, p)
+    nb = ref.nb
+    ne = mesh.n_elems
+    h = mesh.h
+    C11 = hex_penalty(mesh, p)
+    g, w = gauss01(p + 2)
+    zq, yq, xq = np.meshgrid(g, g, g, indexing="ij")
+    xi = np.stack([xq.ravel(), yq.ravel(), zq.ravel()], axis=1)
+    wq = np.einsum("a,b,c->abc", w, w, w).ravel()
+    phi = ref.values(xi)
+    Gr = ref.grads(xi)
+    Mk = h ** 3 * np.einsum("q,qi,qj->ij", wq, phi, phi)
+    Minv = np.linalg.inv(Mk)
+    Gd = [h ** 2 * np.einsum("q,qi,qj->ij", wq, phi, Gr[..., d]) for d in range(3)]
+    area = h * h
+    fm = {}
+    for a in range(3):
+        for side in (0, 1):
+            xf, wf = _face_ref(p, a, side)
+            fm[(a, side)] = (ref.values(xf), wf * area)
+
+    def fmass(a, s1, s2):
+        (p1, wf), (p2, _) = fm[(a, s1)], fm[(a, s2)]
+        return np.einsum("q,qi,qj->ij", wf, p1, p2)
+
+    Qr, Qc, Qb = [[] for _ in range(3)], [[] for _ in range(3)], [[] for _ in range(3)]
+    Pr, Pc, Pb = [[] for _ in range(3)], [[] for _ in range(3)], [[] for _ in range(3)]
+    all_e = np.arange(ne)
+    for d in range(3):
+        Qr[d].append(all_e); Qc[d].append(all_e)
+        Qb[d].append(np.broadcast_to(Minv @ Gd[d], (ne, nb, nb)))
+        Pr[d].append(all_e); Pc[d].append(all_e)
+        Pb[d].append(np.broadcast_to(Gd[d].T, (ne, nb, nb)))
+    for a in range(3):
+        F = mesh.int_faces[mesh.int_faces[:, 1] == 2 * a + 1]
+        e1, e2 = F[:, 0], F[:, 2]           # e1 low (n = +e_a points into e2), e2 high
+        m = e1.size
+        F21 = fmass(a, 0, 1)                # e2's face (its low side) x e1's face (high side)
+        F22 = fmass(a, 0, 0)
+        F12 = fmass(a, 1, 0)
+        # lifting of element 2 (outward normal -e_a): int (u1 - u2) (-1) phi
+        Qr[a] += [e2, e2]; Qc[a] += [e1, e2]
+        Qb[a] += [np.broadcast_to(-Minv @ F21, (m, nb, nb)), np.broadcast_to(Minv @ F22, (m, nb, nb))]
+        # primal: q_hat = q2 on both sides; element 1 (n = +e_a), element 2 (n = -e_a)
+        Pr[a] += [e1, e2]; Pc[a] += [e2, e2]
+        Pb[a] += [np.broadcast_to(-F12, (m, nb, nb)), np.broadcast_to(F22, (m, nb, nb))]
+    Dr, Dc, Db = [], [], []
+    for a in range(3):
+        for side in (0, 1):
+            if (a, side) not in dirichlet_faces:
+                continue
+            B = mesh.bnd_faces[mesh.bnd_faces[:, 1] == 2 * a + side, 0]
+            nsign = 1.0 if side == 1 else -1.0
+            Fb = fmass(a, side, side)
+            # lifting: u_hat = 0 -> int (0 - u) n_a phi
+            Qr[a].append(B); Qc[a].append(B)
+            Qb[a].append(np.broadcast_to(-nsign * Minv @ Fb, (B.size, nb, nb)))
+            # primal: - int (q_hat . n) v with q_hat = q - C11 u n
+            Pr[a].append(B); Pc[a].append(B)
+            Pb[a].append(np.broadcast_to(-nsign * Fb, (B.size, nb, nb)))
+            Dr.append(B); Dc.append(B)
+            Db.append(np.broadcast_to(C11 * Fb, (B.size, nb, nb)))
+
+    def block_csr(r, c, b):
+        r = np.concatenate(r)
+        c = np.concatenate(c)
+        b = np.concatenate([np.asarray(x) for x in b])
+        ii = (r[:, None, None] * nb + np.arange(nb)[None, :, None]).repeat(nb, axis=2)
+        jj = (c[:, None, None] * nb + np.arange(nb)[None, None, :]).repeat(nb, axis=1)
+        return sp.csr_matrix((b.ravel(), (ii.ravel(), jj.ravel())), shape=(ne * nb, ne * nb))
+
+    A = block_csr(Dr, Dc, Db) if Dr else sp.csr_matrix((ne * nb, ne * nb))
+    for d in range(3):
+        A = A + block_csr(Pr[d], Pc[d], Pb[d]) @ block_csr(Qr[d], Qc[d], Qb[d])
+    Ab = A.tocsr().tobsr(blocksize=(nb, nb))
+    Ab.sort_indices()
+    ptr = Ab.indptr.astype(np.int64)
+    col = Ab.indices.astype(np.int64)
+    rows_of = np.repeat(np.arange(ne), np.diff(ptr))
+    assert np.all(np.isin(np.arange(ne), rows_of[col == rows_of]))
+    return BSR(ne, nb, ptr.astype(np.int32), col.astype(np.int32), np.ascontiguousarray(Ab.data))
 
 
 def exact(x):

@@ -40,6 +40,8 @@ def problem(name: str):
         return configs.poisson2d(8, 2, r=24, n_levels=3, name="p2_8")
     if name.startswith("hex_M"):
         return configs.poisson3d_hex(int(name[5:]))
+    if name.startswith("hexldg_M"):
+        return configs.poisson3d_hex(int(name[8:]), flux="ldg")
     if name.startswith("cd3_"):
         # 3-D LDG + upwind on Kuhn tets, P1: cd3_<cells>_pe<Pe>
         _, n, pe = name.split("_")

@@ -221,7 +221,11 @@ def test_smoothed_prolongator_lowers_energy(tiny):
     eP = np.einsum("ic,ij,jc->c", P, A, P)
     eT = np.einsum("ic,ij,jc->c", T, A, T)
     assert np.all(eP < eT)
-    assert np.all(P[np.abs(T) > 0] != 0.0) or True
+    assert np.all(P[np.abs(T) > 0] != 0.0)
+    # one smoothing step spreads each column of T by one ring of A's pattern
+    # and no further
+    reach = (np.abs(A) @ np.abs(T)) > 0
+    assert np.all((P != 0.0) <= (reach | (T != 0.0)))
 
 
 def test_restriction_is_transpose_and_galerkin_projection(tiny):

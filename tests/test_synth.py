@@ -254,14 +254,16 @@ def test_ldg_simplex_limits_and_structure():
 
 def test_hex_sipg_manufactured_solution_order():
     """The paper's first elliptic test (Section 6.1) on 2^M hexahedra per
-    side, Q1, SIPG with penalty M (p+1)^2 / 2 / h, Dirichlet on x = -1 and
-    Neumann elsewhere: the operator is symmetric with at most 7 blocks per
-    row, and the L2 error of exp(sin sin sin) - 1 falls at order p + 1."""
+    side, Q1, SIPG with face penalty (p+1)^2 / h, Dirichlet on x = -1 and
+    Neumann elsewhere: the operator is symmetric positive definite with at
+    most 7 blocks per row, and the L2 error of exp(sin sin sin) - 1 falls at
+    order p + 1."""
     from synth import hex as HX
     errs = []
     for Mlev in (3, 4):
         m = HX.hex_mesh(Mlev)
-        A = HX.sipg_hex(m, 1, Mlev)
+        assert HX.hex_penalty(m, 1) == 4.0 / m.h
+        A = HX.sipg_hex(m, 1)
         S = A.to_scipy()
         assert abs(S - S.T).max() <= 1e-14 * abs(S).max()
         assert np.diff(A.row_ptr).max() == 7 and A.b == 8
@@ -269,3 +271,26 @@ def test_hex_sipg_manufactured_solution_order():
         errs.append(HX.l2_error(m, 1, uh))
     slope = np.log2(errs[0] / errs[1])
     assert slope > 1.8, (errs, slope)
+    m2 = HX.hex_mesh(2)
+    assert np.linalg.eigvalsh(HX.sipg_hex(m2, 1).to_scipy().toarray())[0] > 0
+
+
+def test_hex_ldg_manufactured_solution_order():
+    """Minimal-dissipation LDG (switch (1,1,1)) on the same problem: the
+    operator is symmetric positive definite, with the compact 7-block
+    stencil that a consistent switch gives on a Cartesian mesh, and the L2
+    error falls at order p + 1."""
+    from synth import hex as HX
+    errs = []
+    for Mlev in (3, 4):
+        m = HX.hex_mesh(Mlev)
+        A = HX.ldg_hex(m, 1)
+        S = A.to_scipy()
+        assert abs(S - S.T).max() <= 1e-13 * abs(S).max()
+        assert np.diff(A.row_ptr).max() == 7 and A.b == 8
+        uh = sla.spsolve(S.tocsc(), HX.load_vector(m, 1))
+        errs.append(HX.l2_error(m, 1, uh))
+    slope = np.log2(errs[0] / errs[1])
+    assert slope > 1.8, (errs, slope)
+    m2 = HX.hex_mesh(2)
+    assert np.linalg.eigvalsh(HX.ldg_hex(m2, 1).to_scipy().toarray())[0] > 0
