@@ -320,9 +320,16 @@ gasa_status gasa_tentative(int32_t n_units, int32_t bs, int32_t n_agg, const int
  *  - n_units * bs must not exceed GASA_NOALLOC_MAX_DOFS, else
  *    GASA_ERR_INVALID_ARG is returned before any device work;
  *  - it calls no cudaMalloc, cudaFree or other allocating routine;
- *  - the first call on a device looks up the array's device address (once
- *    per device, with that device current) and should come before any stream
- *    capture on that device;
+ *  - the array's device address is looked up once per device, with that
+ *    device current: by gasa_create for its device, else by the first call
+ *    on the device.  Under CUDA's lazy module loading that lookup, and the
+ *    first launch of each of the library's kernels on the device, load the
+ *    library's device code there, which is when the array (and the code)
+ *    take device memory.  So make a first call, or create a context, on each
+ *    device before the stretch in which nothing may allocate, and before any
+ *    stream capture on that device;
+ *  - failures are reported as gasa_power_estimate reports them (the same
+ *    arithmetic runs on the scratch it allocates);
  *  - all calls on a device share the array; calls that overlap on the GPU
  *    (different streams or host threads) race on it and must be avoided. */
 #define GASA_NOALLOC_MAX_DOFS 262144

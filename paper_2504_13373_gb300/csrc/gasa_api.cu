@@ -556,14 +556,7 @@ gasa_status spmv_outer(gasa_ctx *ctx, int mode, const double *x, const double *b
   return GASA_OK;
 }
 
-// p . q partials inside the double-single product launch (GASA_DS_DOT=0 in
-// the environment uses a separate dot-product launch instead, for A/B timing;
-// the partial count then is kRedBlocks)
-bool ds_dot() {
-  const char *e = std::getenv("GASA_DS_DOT");
-  return !(e && e[0] == '0');
-}
-int pq_ds_count(gasa_ctx *ctx) { return ds_dot() ? ctx->n_pq_ds : kRedBlocks; }
+int pq_ds_count(gasa_ctx *ctx) { return ctx->n_pq_ds; }
 
 // q = A p of the mixed-precision Krylov step: double-single arithmetic on
 // the FP32 splits of A (val32 + lo32) and of p (kp_hi + kp_lo, written by the
@@ -576,8 +569,7 @@ gasa_status spmv_outer_ds(gasa_ctx *ctx, const double *p, double *q, bool split_
   cudaEvent_t e0;
   prof_begin(ctx, 2, &e0);
   CU(launch_bsr_mv_ds(l.n, l.s, l.s, l.A.rp, l.A.col, l.A.val32, l.A.lo32, ctx->kp_hi,
-                      ctx->kp_lo, q, ctx->stream, ds_dot() ? p : nullptr, ctx->pq_ds));
-  if (!ds_dot()) CU(launch_dot_partials(n, p, q, ctx->pq_ds, ctx->stream));
+                      ctx->kp_lo, q, ctx->stream, p, ctx->pq_ds));
   prof_end(ctx, 2, spmv_bytes(l, 8, false));   // 4 + 4 bytes per value and per x entry
   return GASA_OK;
 }
@@ -697,8 +689,7 @@ gasa_status build_cg_graph(gasa_ctx *ctx, int precision) {
     if (e == cudaSuccess && flex) {
       // q = A p with the p . q partials in the same launch
       e = launch_bsr_mv_ds(l.n, l.s, l.s, l.A.rp, l.A.col, l.A.val32, l.A.lo32, ctx->kp_hi,
-                           ctx->kp_lo, q, s, ds_dot() ? p : nullptr, ctx->pq_ds);
-      if (e == cudaSuccess && !ds_dot()) e = launch_dot_partials(n, p, q, ctx->pq_ds, s);
+                           ctx->kp_lo, q, s, p, ctx->pq_ds);
     } else if (e == cudaSuccess) {
       e = launch_bsr_mv<double>(GASA_MV_ASSIGN, l.n, l.s, l.s, l.A.rp, l.A.col, l.A.val, p, nullptr,
                                 q, s);
@@ -728,15 +719,7 @@ gasa_status pcg_graph(gasa_ctx *ctx, const double *b, double tol, int precision,
   const int64_t n = ctx->L[0].ndof;
   *conv = false;
   *iters = 0;
-  gasa_status bst = build_cg_graph(ctx, precision);
-  if (bst != GASA_OK && pdl_enabled()) {
-    // a graph with programmatic launch edges that does not build: build it
-    // with plain stream order instead
-    (void)cudaGetLastError();
-    pdl_set(false);
-    bst = build_cg_graph(ctx, precision);
-  }
-  ST(bst);
+  ST(build_cg_graph(ctx, precision));
   double bb;
   ST(norm2(ctx, n, b, S_BB, &bb));
   const double bn = std::sqrt(bb);
@@ -1001,13 +984,7 @@ gasa_status stationary(gasa_ctx *ctx, const double *b, double tol, int precision
     }
     return GASA_OK;
   }
-  gasa_status bst = build_st_graph(ctx, precision);
-  if (bst != GASA_OK && pdl_enabled()) {
-    (void)cudaGetLastError();
-    pdl_set(false);
-    bst = build_st_graph(ctx, precision);
-  }
-  ST(bst);
+  ST(build_st_graph(ctx, precision));
   const int pi = 3 + precision;
   CU(cudaMemsetAsync(ctx->d_iters, 0, sizeof(int), s));
   CU(cudaGraphLaunch(ctx->cg_exec[pi], s));
@@ -1680,6 +1657,56 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
 }  // namespace
 
 // ============================================================================
+// a CUDA error as the single-operation entry points report it
+static gasa_status op_status(cudaError_t e) {
+  if (e == cudaSuccess) return GASA_OK;
+  return e == cudaErrorMemoryAllocation ? GASA_ERR_OOM : GASA_ERR_CUDA;
+}
+
+int gasa::op_status_code(cudaError_t e) { return (int)op_status(e); }
+
+// stored blocks of a device BSR matrix (row_ptr[n]); -1 when it cannot be read
+int64_t gasa::op_nnzb(const int32_t *row_ptr, int32_t n, cudaStream_t s) {
+  if (!row_ptr) return -1;
+  int32_t v = -1;
+  if (cudaMemcpyAsync(&v, row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return -1;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+  return v;
+}
+
+cudaError_t gasa::power_estimate_on(int32_t n_units, int32_t bs, const int32_t *row_ptr,
+                                    const int32_t *col, const double *val, const double *Dinv,
+                                    const double *x0, int32_t q, int64_t nnzb, double *a,
+                                    double *b, double *part, double *sc, double *rho,
+                                    cudaStream_t s) {
+  const int64_t n = (int64_t)n_units * bs;
+  // Alg. 4: x = x0 / ||x0||, then q times x <- D^-1 A x / ||D^-1 A x||,
+  // then ||D^-1 A x||
+  cudaError_t e = cudaMemcpyAsync(a, x0, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = launch_dot_partials(n, a, nullptr, part, s);
+  if (e == cudaSuccess) e = launch_finalize(part, 1, sc, s);
+  if (e == cudaSuccess) e = launch_scale_by_inv_sqrt(n, a, sc, s);
+  for (int it = 0; it < q && e == cudaSuccess; ++it) {
+    e = launch_jacobi<double>(JAC_APPLY, n_units, bs, row_ptr, col, val, Dinv, a, nullptr, b, s,
+                              nnzb);
+    if (e == cudaSuccess) e = launch_dot_partials(n, b, nullptr, part, s);
+    if (e == cudaSuccess) e = launch_finalize(part, 1, sc, s);
+    if (e == cudaSuccess) e = launch_scale_by_inv_sqrt(n, b, sc, s);
+    std::swap(a, b);
+  }
+  if (e == cudaSuccess)
+    e = launch_jacobi<double>(JAC_APPLY, n_units, bs, row_ptr, col, val, Dinv, a, nullptr, b, s,
+                              nnzb);
+  if (e == cudaSuccess) e = launch_dot_partials(n, b, nullptr, part, s);
+  if (e == cudaSuccess) e = launch_finalize(part, 1, sc + 1, s);
+  double h = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sc + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) *rho = std::sqrt(h);
+  return e;
+}
+
 // extern "C" entry points
 // ============================================================================
 extern "C" {
@@ -1729,6 +1756,10 @@ gasa_status gasa_create(gasa_ctx **out, int32_t device, void *stream) {
     c->own_stream = true;
   }
   gasa_default_options(&c->opt);
+  // look up the allocation-free entry point's scratch on this device now, so
+  // that its module is loaded here rather than inside an allocation-free call
+  double *scratch = nullptr;
+  if (noalloc_scratch_on_current_device(&scratch) != cudaSuccess) (void)cudaGetLastError();
   *out = c;
   return GASA_OK;
 }
@@ -1935,20 +1966,8 @@ int64_t gasa_kernel_launches(void) { return (int64_t)launch_count(); }
 // ---------------------------------------------------------------------------
 // single operations
 // ---------------------------------------------------------------------------
-static gasa_status op_status(cudaError_t e) {
-  if (e == cudaSuccess) return GASA_OK;
-  return e == cudaErrorMemoryAllocation ? GASA_ERR_OOM : GASA_ERR_CUDA;
-}
 
-// stored blocks of a device BSR matrix (row_ptr[n]); -1 when it cannot be read
-static int64_t op_nnzb(const int32_t *row_ptr, int32_t n, cudaStream_t s) {
-  if (!row_ptr) return -1;
-  int32_t v = -1;
-  if (cudaMemcpyAsync(&v, row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    return -1;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
-  return v;
-}
+
 
 gasa_status gasa_bsr_mv(int32_t mode, int32_t n_brows, int32_t br, int32_t bc,
                         const int32_t *row_ptr, const int32_t *col, const double *val,
@@ -2029,6 +2048,7 @@ gasa_status gasa_block_inverse(int32_t n_units, int32_t bs, const int32_t *row_p
   return op_status(e);
 }
 
+
 gasa_status gasa_power_estimate(int32_t n_units, int32_t bs, const int32_t *row_ptr,
                                 const int32_t *col, const double *val, const double *Dinv,
                                 const double *x0, int32_t q, double *rho, void *stream) {
@@ -2038,30 +2058,14 @@ gasa_status gasa_power_estimate(int32_t n_units, int32_t bs, const int32_t *row_
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = (int64_t)n_units * bs;
   const int64_t nnzb = op_nnzb(row_ptr, n_units, s);
+  if (nnzb < 0) return GASA_ERR_CUDA;
   double *buf = nullptr;
   cudaError_t e = cudaMallocAsync((void **)&buf, sizeof(double) * (2 * n + kRedBlocks + 2), s);
   if (e != cudaSuccess) return op_status(e);
-  double *a = buf, *bb = buf + n, *part = buf + 2 * n, *sc = part + kRedBlocks;
-  e = cudaMemcpyAsync(a, x0, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = launch_dot_partials(n, a, nullptr, part, s);
-  if (e == cudaSuccess) e = launch_finalize(part, 1, sc, s);
-  if (e == cudaSuccess) e = launch_scale_by_inv_sqrt(n, a, sc, s);
-  for (int it = 0; it < q && e == cudaSuccess; ++it) {
-    e = launch_jacobi<double>(JAC_APPLY, n_units, bs, row_ptr, col, val, Dinv, a, nullptr, bb, s, nnzb);
-    if (e == cudaSuccess) e = launch_dot_partials(n, bb, nullptr, part, s);
-    if (e == cudaSuccess) e = launch_finalize(part, 1, sc, s);
-    if (e == cudaSuccess) e = launch_scale_by_inv_sqrt(n, bb, sc, s);
-    std::swap(a, bb);
-  }
-  if (e == cudaSuccess)
-    e = launch_jacobi<double>(JAC_APPLY, n_units, bs, row_ptr, col, val, Dinv, a, nullptr, bb, s, nnzb);
-  if (e == cudaSuccess) e = launch_dot_partials(n, bb, nullptr, part, s);
-  if (e == cudaSuccess) e = launch_finalize(part, 1, sc, s);
-  double h = 0.0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sc, sizeof(double), cudaMemcpyDeviceToHost, s);
+  e = power_estimate_on(n_units, bs, row_ptr, col, val, Dinv, x0, q, nnzb, buf, buf + n,
+                        buf + 2 * n, buf + 2 * n + kRedBlocks, rho, s);
   cudaFreeAsync(buf, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e == cudaSuccess) *rho = std::sqrt(h);
   return op_status(e);
 }
 

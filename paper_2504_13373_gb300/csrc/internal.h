@@ -28,6 +28,27 @@ cudaError_t launch_jacobi_h16(int mode, int n_units, int bs, const int *rp, cons
                               const float *wscale, const float *x, const float *b, float *xo,
                               cudaStream_t s);
 
+// ---- Alg. 4 on caller-provided scratch (gasa_api.cu) -------------------------
+// The power-iteration estimate shared by gasa_power_estimate (scratch from the
+// stream-ordered allocator) and gasa_power_estimate_noalloc (scratch in a
+// static device array).  a and b hold n_units * bs doubles each, part
+// kRedBlocks doubles, sc two doubles; nnzb is row_ptr[n_units].  On success
+// *rho holds ||D^-1 A x|| after q normalised steps from x0.
+cudaError_t power_estimate_on(int32_t n_units, int32_t bs, const int32_t *row_ptr,
+                              const int32_t *col, const double *val, const double *Dinv,
+                              const double *x0, int32_t q, int64_t nnzb, double *a, double *b,
+                              double *part, double *sc, double *rho, cudaStream_t s);
+// stored blocks of a device BSR matrix (row_ptr[n], read with a synchronous
+// copy on s); -1 when it cannot be read
+int64_t op_nnzb(const int32_t *row_ptr, int32_t n, cudaStream_t s);
+// a CUDA error as the single-operation entry points report it
+int op_status_code(cudaError_t e);
+// ---- noalloc.cu --------------------------------------------------------------
+// looks up (and caches) the device address of the static scratch array on the
+// current device; gasa_create calls it so that the lookup, and the loading of
+// the module that holds the array, happen outside allocation-free calls
+cudaError_t noalloc_scratch_on_current_device(double **out);
+
 // kernel launches issued by this library (process-wide counter)
 void note_launch();
 long long launch_count();

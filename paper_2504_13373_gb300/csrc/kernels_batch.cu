@@ -201,7 +201,6 @@ bjacobi_kernel(int mode, int n, int bs, int rows_cta, const int *__restrict__ rp
 template <typename T, int K>
 __global__ void __launch_bounds__(kThreads)
 bdense_kernel(int nc, const double *__restrict__ Ainv, const T *__restrict__ B, T *__restrict__ X) {
-  pdl_entry();
   const int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (e >= (int64_t)nc * K) return;
   const int i = (int)(e / K), c = (int)(e - (int64_t)i * K);
@@ -238,7 +237,6 @@ template <int K>
 __global__ void __launch_bounds__(kThreads)
 bdot_kernel(int64_t n, const double *__restrict__ X, const double *__restrict__ Y,
             double *__restrict__ part) {
-  pdl_entry();
   double acc[K];
 #pragma unroll
   for (int c = 0; c < K; ++c) acc[c] = 0.0;
@@ -262,7 +260,6 @@ __device__ __forceinline__ double sum_partials(const double *p) {
 
 template <int K>
 __global__ void bfinalize_kernel(const double *__restrict__ part, double *__restrict__ out) {
-  pdl_entry();
   const int c = threadIdx.x;
   if (c < K) out[c] = sum_partials(part + (size_t)c * kRedBlocks);
 }
@@ -270,7 +267,6 @@ __global__ void bfinalize_kernel(const double *__restrict__ part, double *__rest
 // out[c] = sqrt(sum of the partials of column c)
 template <int K>
 __global__ void bnorm_kernel(const double *__restrict__ part, double *__restrict__ out) {
-  pdl_entry();
   const int c = threadIdx.x;
   if (c < K) out[c] = sqrt(sum_partials(part + (size_t)c * kRedBlocks));
 }
@@ -280,7 +276,6 @@ template <int K>
 __global__ void __launch_bounds__(kThreads)
 bnormalize_kernel(int64_t nk, const double *__restrict__ w, const double *__restrict__ nrm,
                   double *__restrict__ v) {
-  pdl_entry();
   const int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (e >= nk) return;
   const double d = nrm[e % K];
@@ -294,7 +289,6 @@ bnormalize_kernel(int64_t nk, const double *__restrict__ w, const double *__rest
 template <int K>
 __global__ void bcg_beta_kernel(const double *__restrict__ part_rz, const double *__restrict__ part_rzo,
                                 double *__restrict__ sc, const int *__restrict__ st, int flex) {
-  pdl_entry();
   const int c = threadIdx.x;
   if (c >= K) return;
   const double rz = sum_partials(part_rz + (size_t)c * kRedBlocks);
@@ -311,7 +305,6 @@ template <int K>
 __global__ void __launch_bounds__(kThreads)
 bcg_update_p_kernel(int64_t nk, double *__restrict__ p, const double *__restrict__ z,
                     double *__restrict__ zold, const double *__restrict__ sc) {
-  pdl_entry();
   const int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (e >= nk) return;
   const int c = (int)(e % K);
@@ -323,7 +316,6 @@ bcg_update_p_kernel(int64_t nk, double *__restrict__ p, const double *__restrict
 template <int K>
 __global__ void bcg_alpha_kernel(const double *__restrict__ part_pq, double *__restrict__ sc,
                                  const int *__restrict__ st) {
-  pdl_entry();
   const int c = threadIdx.x;
   if (c >= K) return;
   const double pq = sum_partials(part_pq + (size_t)c * kRedBlocks);
@@ -338,7 +330,6 @@ __global__ void __launch_bounds__(kThreads)
 bcg_update_xr_kernel(int64_t n, double *__restrict__ x, double *__restrict__ r,
                      const double *__restrict__ p, const double *__restrict__ q,
                      const double *__restrict__ sc, double *__restrict__ part_rr) {
-  pdl_entry();
   double a[K], acc[K];
 #pragma unroll
   for (int c = 0; c < K; ++c) {
@@ -365,7 +356,6 @@ template <int K>
 __global__ void bcg_check_kernel(const double *__restrict__ part_rr, double *__restrict__ sc,
                                  int *__restrict__ st, int *__restrict__ ctl, int flex,
                                  cudaGraphConditionalHandle h) {
-  pdl_entry();
   __shared__ int changed, running;
   if (threadIdx.x == 0) {
     changed = 0;
@@ -414,7 +404,6 @@ __global__ void bcg_check_kernel(const double *__restrict__ part_rr, double *__r
 __global__ void __launch_bounds__(kThreads)
 bgm_load_kernel(int64_t nk, const double *__restrict__ base, int64_t ld, const int *__restrict__ dj,
                 int off, double *__restrict__ dst) {
-  pdl_entry();
   const int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (e < nk) dst[e] = base[(size_t)(*dj + off) * ld + e];
 }
@@ -422,7 +411,6 @@ bgm_load_kernel(int64_t nk, const double *__restrict__ base, int64_t ld, const i
 __global__ void __launch_bounds__(kThreads)
 bgm_store_kernel(int64_t nk, const double *__restrict__ src, double *__restrict__ base, int64_t ld,
                  const int *__restrict__ dj, int off) {
-  pdl_entry();
   const int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (e < nk) base[(size_t)(*dj + off) * ld + e] = src[e];
 }
@@ -432,7 +420,6 @@ template <int K>
 __global__ void __launch_bounds__(kThreads)
 bmulti_dot_kernel(int64_t n, const double *__restrict__ V, int64_t ldv, const int *__restrict__ dj,
                   const double *__restrict__ w, double *__restrict__ part) {
-  pdl_entry();
   const int i = blockIdx.y;
   if (i > *dj) return;
   const double *v = V + (size_t)i * ldv;
@@ -451,7 +438,6 @@ bmulti_dot_kernel(int64_t n, const double *__restrict__ V, int64_t ldv, const in
 template <int K>
 __global__ void bmulti_finalize_kernel(const double *__restrict__ part, int m, const int *__restrict__ dj,
                                        double *__restrict__ h, double *__restrict__ H, int accumulate) {
-  pdl_entry();
   const int j = *dj;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (j + 1) * K) return;
@@ -466,7 +452,6 @@ template <int K>
 __global__ void __launch_bounds__(kThreads)
 bgs_update_kernel(int64_t nk, const double *__restrict__ V, int64_t ldv, const int *__restrict__ dj,
                   const double *__restrict__ h, double *__restrict__ w) {
-  pdl_entry();
   const int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (e >= nk) return;
   const int c = (int)(e % K);
@@ -480,7 +465,6 @@ bgs_update_kernel(int64_t nk, const double *__restrict__ V, int64_t ldv, const i
 template <int K>
 __global__ void bgm_norm_kernel(const double *__restrict__ part, int m, const int *__restrict__ dj,
                                 double *__restrict__ H) {
-  pdl_entry();
   const int c = threadIdx.x;
   if (c >= K) return;
   const int j = *dj;
@@ -492,7 +476,6 @@ template <int K>
 __global__ void __launch_bounds__(kThreads)
 bgm_normalize_kernel(int64_t nk, const double *__restrict__ w, const double *__restrict__ H, int m,
                      const int *__restrict__ dj, double *__restrict__ V) {
-  pdl_entry();
   const int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (e >= nk) return;
   const int j = *dj;
@@ -507,7 +490,6 @@ template <int K>
 __global__ void bgm_start_kernel(int m, const double *__restrict__ beta, double *__restrict__ g,
                                  double *__restrict__ sc, int *__restrict__ st, int flex,
                                  int *__restrict__ dj) {
-  pdl_entry();
   const int c = threadIdx.x;
   if (c == 0) *dj = 0;
   if (c >= K) return;
@@ -534,7 +516,6 @@ __global__ void bgm_givens_kernel(int m, double *__restrict__ H, double *__restr
                                   double *__restrict__ sn, double *__restrict__ g,
                                   double *__restrict__ sc, int *__restrict__ st, int *__restrict__ dj,
                                   cudaGraphConditionalHandle h) {
-  pdl_entry();
   __shared__ int any;
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
@@ -583,7 +564,6 @@ __global__ void bgm_givens_kernel(int m, double *__restrict__ H, double *__restr
 template <int K>
 __global__ void bgm_backsolve_kernel(int m, const double *__restrict__ H, const double *__restrict__ g,
                                      double *__restrict__ y, const int *__restrict__ st) {
-  pdl_entry();
   const int c = threadIdx.x;
   if (c >= K) return;
   const int jd = st[BI_CYCLE * K + c] ? st[BI_JDONE * K + c] : 0;
@@ -600,7 +580,6 @@ template <int K>
 __global__ void __launch_bounds__(kThreads)
 bgm_combine_kernel(int64_t nk, const double *__restrict__ Bv, int64_t ldb,
                    const double *__restrict__ y, const int *__restrict__ st, double *__restrict__ x) {
-  pdl_entry();
   const int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (e >= nk) return;
   const int c = (int)(e % K);
@@ -614,7 +593,6 @@ bgm_combine_kernel(int64_t nk, const double *__restrict__ Bv, int64_t ldb,
 template <int K>
 __global__ void bgm_check_kernel(const double *__restrict__ part_rr, double *__restrict__ sc,
                                  int *__restrict__ st) {
-  pdl_entry();
   const int c = threadIdx.x;
   if (c >= K) return;
   const double rr = sum_partials(part_rr + (size_t)c * kRedBlocks);
@@ -631,21 +609,18 @@ __global__ void bgm_check_kernel(const double *__restrict__ part_rr, double *__r
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void bscatter_kernel(int64_t n, int K, int c, const T *__restrict__ src, T *__restrict__ dst) {
-  pdl_entry();
   const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (i < n) dst[i * K + c] = src ? src[i] : T(0);
 }
 
 template <typename T>
 __global__ void bgather_kernel(int64_t n, int K, int c, const T *__restrict__ src, T *__restrict__ dst) {
-  pdl_entry();
   const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (i < n) dst[i] = src[i * K + c];
 }
 
 template <typename T>
 __global__ void bcolcopy_kernel(int64_t n, int K, int c, const T *__restrict__ src, T *__restrict__ dst) {
-  pdl_entry();
   const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (i < n) dst[i * K + c] = src[i * K + c];
 }

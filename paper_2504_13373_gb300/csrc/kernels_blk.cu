@@ -47,7 +47,6 @@ __global__ void __launch_bounds__(256)
 bsr_blk_kernel(int n_brows, const int *__restrict__ rp, const int *__restrict__ col,
                const T *__restrict__ val, const T *__restrict__ Wm, const T *__restrict__ x,
                const T *__restrict__ b, T *__restrict__ y) {
-  pdl_entry();
   constexpr int TW = TL < 32 ? TL : 32;          // lanes of a team inside one warp
   constexpr int WPT = TL > 32 ? TL / 32 : 1;     // warps per team
   __shared__ T red[(256 / 32) * S];
@@ -150,17 +149,10 @@ bsr_blk_kernel(int n_brows, const int *__restrict__ rp, const int *__restrict__ 
 // Lanes per block row: about 2.5 blocks per lane (two in flight, a short
 // tail), a power of two in [4, 64] and at least s, so that lanes 0..s-1 of
 // the team can write the s rows.
-// (GASA_BLK_TEAM = 4..64 in the environment fixes the team for A/B timing)
 int blk_team(int bs, int n_brows, int64_t nnzb) {
-  static const int forced = [] {
-    const char *e = std::getenv("GASA_BLK_TEAM");
-    const int v = e ? std::atoi(e) : 0;
-    return (v == 4 || v == 8 || v == 16 || v == 32 || v == 64) ? v : 0;
-  }();
   const double avg = (double)nnzb / (double)(n_brows > 0 ? n_brows : 1);
   int tl = 4;
   while (tl < 64 && tl * 2.5 < avg) tl *= 2;
-  if (forced) tl = forced;
   while (tl < bs) tl *= 2;
   return tl;
 }
@@ -203,24 +195,8 @@ bool aligned_to(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 }  // namespace
 
-namespace {
-std::atomic<int> g_blk{-1};
-}
-
-// on unless the environment sets GASA_BLK=0 (for A/B timing against the
-// thread-, warp- and CTA-per-row kernels)
-bool blk_enabled() {
-  int v = g_blk.load(std::memory_order_relaxed);
-  if (v < 0) {
-    const char *e = std::getenv("GASA_BLK");
-    v = (e && e[0] == '0') ? 0 : 1;
-    g_blk.store(v, std::memory_order_relaxed);
-  }
-  return v != 0;
-}
-
 bool blk_applies(int bs, int n_brows, int64_t nnzb) {
-  return bs >= 2 && bs <= 8 && n_brows > 0 && nnzb >= 6LL * n_brows && blk_enabled();
+  return bs >= 2 && bs <= 8 && n_brows > 0 && nnzb >= 6LL * n_brows;
 }
 
 // FP32 only: the team sums add s * log2(team) additions per lane, which the

@@ -15,7 +15,6 @@ namespace gasa {
 // ----------------------------------------------------------------------------
 __global__ void to_h16_blocks_kernel(int64_t nblocks, int bsz, const double *__restrict__ v,
                                      __half *__restrict__ h, float *__restrict__ scale) {
-  pdl_entry();
   const int64_t blk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (blk >= nblocks) return;
@@ -59,7 +58,6 @@ __global__ void __launch_bounds__(256)
 bsr_mv_h16_kernel(int n_brows, int br, const int *__restrict__ rp, const int *__restrict__ col,
                   const __half *__restrict__ val, const float *__restrict__ scale,
                   const float *__restrict__ x, const float *__restrict__ b, float *__restrict__ y) {
-  pdl_entry();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)n_brows * br) return;
   const int i = (int)(t / br);
@@ -89,7 +87,6 @@ bsr_mv_h16_generic(int n_brows, int br, int bc, const int *__restrict__ rp,
                    const int *__restrict__ col, const __half *__restrict__ val,
                    const float *__restrict__ scale, const float *__restrict__ x,
                    const float *__restrict__ b, float *__restrict__ y) {
-  pdl_entry();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)n_brows * br) return;
   const int i = (int)(t / br);
@@ -154,7 +151,6 @@ jacobi_h16_kernel(int n_units, const int *__restrict__ rp, const int *__restrict
                   const __half *__restrict__ Wm, const float *__restrict__ wscale,
                   const float *__restrict__ x, const float *__restrict__ b,
                   float *__restrict__ xo) {
-  pdl_entry();
   __shared__ float res[256];
   constexpr int RPB = 256 / BS;
   constexpr int W = RowVec<float, BS>::value;
@@ -204,7 +200,6 @@ jacobi_h16_generic(int n_units, int bs, const int *__restrict__ rp, const int *_
                    const __half *__restrict__ Wm, const float *__restrict__ wscale,
                    const float *__restrict__ x, const float *__restrict__ b,
                    float *__restrict__ xo) {
-  pdl_entry();
   extern __shared__ float resg[];
   const int rpb = blockDim.x / bs;
   const int li = threadIdx.x / bs;

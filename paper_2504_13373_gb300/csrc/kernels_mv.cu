@@ -22,7 +22,6 @@ __global__ void __launch_bounds__(256)
 bsr_mv_kernel(int n_brows, int br, const int *__restrict__ rp, const int *__restrict__ col,
               const T *__restrict__ val, const T *__restrict__ x, const T *__restrict__ b,
               T *__restrict__ y) {
-  pdl_entry();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)n_brows * br) return;
   const int i = (int)(t / br);
@@ -52,7 +51,6 @@ __global__ void __launch_bounds__(256)
 bsr_mv_generic(int n_brows, int br, int bc, const int *__restrict__ rp,
                const int *__restrict__ col, const T *__restrict__ val, const T *__restrict__ x,
                const T *__restrict__ b, T *__restrict__ y) {
-  pdl_entry();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)n_brows * br) return;
   const int i = (int)(t / br);
@@ -113,7 +111,6 @@ __global__ void __launch_bounds__(256)
 bsr_mv_warp_kernel(int n_brows, int br, int bc, const int *__restrict__ rp,
                    const int *__restrict__ col, const T *__restrict__ val, const T *__restrict__ x,
                    const T *__restrict__ b, T *__restrict__ y) {
-  pdl_entry();
   const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= n_brows) return;
@@ -157,7 +154,6 @@ __global__ void __launch_bounds__(256)
 bsr_mv_group_kernel(int n_brows, int br, int bc, const int *__restrict__ rp,
                     const int *__restrict__ col, const T *__restrict__ val,
                     const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ y) {
-  pdl_entry();
   const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= n_brows) return;
@@ -210,7 +206,6 @@ __global__ void __launch_bounds__(256)
 bsr_mv_cta_kernel(int n_brows, int br, int bc, const int *__restrict__ rp,
                   const int *__restrict__ col, const T *__restrict__ val,
                   const T *__restrict__ x, const T *__restrict__ b, T *__restrict__ y) {
-  pdl_entry();
   extern __shared__ unsigned char cta_smem[];
   T *red = reinterpret_cast<T *>(cta_smem);
   const int i = blockIdx.x;
@@ -339,7 +334,6 @@ bsr_mv_ds_kernel(int n_brows, int br, const int *__restrict__ rp, const int *__r
                  const float *__restrict__ xhi, const float *__restrict__ xlo,
                  double *__restrict__ y, const double *__restrict__ xd,
                  double *__restrict__ partials) {
-  pdl_entry();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const bool act = t < (long long)n_brows * br;
   const int i = act ? (int)(t / br) : 0;
@@ -386,7 +380,6 @@ bsr_mv_ds_generic(int n_brows, int br, int bc, const int *__restrict__ rp,
                   const int *__restrict__ col, const float *__restrict__ ahi,
                   const float *__restrict__ alo, const float *__restrict__ xhi,
                   const float *__restrict__ xlo, double *__restrict__ y) {
-  pdl_entry();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)n_brows * br) return;
   const int i = (int)(t / br);
@@ -462,7 +455,6 @@ __global__ void __launch_bounds__(256)
 jacobi_kernel(int n_units, const int *__restrict__ rp, const int *__restrict__ col,
               const T *__restrict__ val, const T *__restrict__ Wm, const T *__restrict__ x,
               const T *__restrict__ b, T *__restrict__ xo) {
-  pdl_entry();
   __shared__ T res[256];
   constexpr int RPB = 256 / BS;
   constexpr int W = RowVec<T, BS>::value;
@@ -518,7 +510,6 @@ template <int BS>
 __global__ void __launch_bounds__(256)
 jacobi_first_conv_kernel(int n_units, const double *__restrict__ bd, float *__restrict__ b32,
                          const float *__restrict__ Wm, float *__restrict__ xo) {
-  pdl_entry();
   __shared__ float res[256];
   constexpr int RPB = 256 / BS;
   constexpr int W = RowVec<float, BS>::value;
@@ -572,7 +563,6 @@ __global__ void __launch_bounds__(256)
 jacobi_generic(int n_units, int bs, const int *__restrict__ rp, const int *__restrict__ col,
                const T *__restrict__ val, const T *__restrict__ Wm, const T *__restrict__ x,
                const T *__restrict__ b, T *__restrict__ xo) {
-  pdl_entry();
   extern __shared__ unsigned char smem_raw[];
   T *res = reinterpret_cast<T *>(smem_raw);
   const int rpb = blockDim.x / bs;
@@ -616,7 +606,6 @@ __global__ void __launch_bounds__(256)
 jacobi_warp_kernel(int n_units, int bs, const int *__restrict__ rp, const int *__restrict__ col,
                    const T *__restrict__ val, const T *__restrict__ Wm, const T *__restrict__ x,
                    const T *__restrict__ b, T *__restrict__ xo) {
-  pdl_entry();
   const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= n_units) return;
@@ -648,7 +637,6 @@ __global__ void __launch_bounds__(256)
 jacobi_cta_kernel(int n_units, int bs, const int *__restrict__ rp, const int *__restrict__ col,
                   const T *__restrict__ val, const T *__restrict__ Wm, const T *__restrict__ x,
                   const T *__restrict__ b, T *__restrict__ xo) {
-  pdl_entry();
   extern __shared__ unsigned char cta_smem_j[];
   T *red = reinterpret_cast<T *>(cta_smem_j);
   const int i = blockIdx.x;
@@ -677,7 +665,6 @@ __global__ void __launch_bounds__(256)
 jacobi_group_kernel(int n_units, int bs, const int *__restrict__ rp, const int *__restrict__ col,
                     const T *__restrict__ val, const T *__restrict__ Wm, const T *__restrict__ x,
                     const T *__restrict__ b, T *__restrict__ xo) {
-  pdl_entry();
   const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= n_units) return;
@@ -788,7 +775,6 @@ __global__ void __launch_bounds__(256)
 relax_multi_kernel(int n_units, int bs, const int *__restrict__ rp, const int *__restrict__ col,
                    const double *__restrict__ val, const double *__restrict__ Wm,
                    const double *const *__restrict__ xin, double *const *__restrict__ xout) {
-  pdl_entry();
   extern __shared__ double res_m[];
   const double *x = xin[blockIdx.y];
   double *xo = xout[blockIdx.y];
@@ -851,7 +837,6 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 dense_mv_kernel(int n, const double *__restrict__ A, const T *__restrict__ x,
                 T *__restrict__ y) {
-  pdl_entry();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n) return;

@@ -15,20 +15,6 @@ static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
-// programmatic dependent launch: off unless GASA_PDL=1 in the environment
-// (measured on the P3 256x256 solve: no gain for the FP32 V-cycle, 7 % slower
-// for the FP64 one); switched off after a graph that uses it fails to build
-static std::atomic<int> g_pdl{-1};
-bool pdl_enabled() {
-  int v = g_pdl.load(std::memory_order_relaxed);
-  if (v < 0) {
-    const char *e = std::getenv("GASA_PDL");
-    v = (e && e[0] == '1') ? 1 : 0;
-    g_pdl.store(v, std::memory_order_relaxed);
-  }
-  return v != 0;
-}
-void pdl_set(bool on) { g_pdl.store(on ? 1 : 0, std::memory_order_relaxed); }
 
 // ----------------------------------------------------------------------------
 // reductions
@@ -46,7 +32,6 @@ template <bool VEC>
 __global__ void __launch_bounds__(kRedThreads)
 dot_partials_kernel(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                     double *__restrict__ partials) {
-  pdl_entry();
   __shared__ double sh[32];
   double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -98,7 +83,6 @@ cudaError_t launch_dot_partials(int64_t n, const double *x, const double *y, dou
 __global__ void __launch_bounds__(kRedThreads)
 colnorm_partials_kernel(int64_t n, const double *const *__restrict__ cols,
                         double *__restrict__ partials) {
-  pdl_entry();
   __shared__ double sh[32];
   const double *x = cols[blockIdx.y];
   double v = 0.0;
@@ -118,7 +102,6 @@ cudaError_t launch_colnorm_partials(int64_t n, const double *const *cols, int nc
 
 __global__ void __launch_bounds__(kRedThreads)
 finalize_kernel(const double *__restrict__ partials, double *__restrict__ out) {
-  pdl_entry();
   __shared__ double sh[32];
   double v = block_sum_partials(partials + (size_t)blockIdx.x * kRedBlocks, kRedBlocks, sh);
   if (threadIdx.x == 0) out[blockIdx.x] = v;
@@ -127,7 +110,6 @@ finalize_kernel(const double *__restrict__ partials, double *__restrict__ out) {
 // one sum of n partials (same order as block_sum_partials elsewhere)
 __global__ void __launch_bounds__(kRedThreads)
 finalize_n_kernel(const double *__restrict__ partials, int n, double *__restrict__ out) {
-  pdl_entry();
   __shared__ double sh[32];
   const double v = block_sum_partials(partials, n, sh);
   if (threadIdx.x == 0) out[0] = v;
@@ -146,7 +128,6 @@ cudaError_t launch_finalize(const double *partials, int nc, double *out, cudaStr
 }
 
 __global__ void scale_inv_sqrt_kernel(int64_t n, double *x, const double *sumsq) {
-  pdl_entry();
   const double a = 1.0 / sqrt(sumsq[0]);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) x[i] *= a;
@@ -173,7 +154,6 @@ __device__ __forceinline__ double splitmix_uniform(uint64_t key, uint64_t i) {
 }
 
 __global__ void uniform_pm1_kernel(int64_t n, uint64_t key, double *x) {
-  pdl_entry();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
     x[i] = 2.0 * splitmix_uniform(key, (uint64_t)i) - 1.0;
@@ -191,7 +171,6 @@ cudaError_t launch_uniform_pm1(int64_t n, uint64_t seed, uint64_t stream, double
 __global__ void uniform_pm1_padded_kernel(int n_units, int s, const int *__restrict__ usize,
                                           const int64_t *__restrict__ uoff, uint64_t key,
                                           double *x) {
-  pdl_entry();
   const int64_t n = (int64_t)n_units * s;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -211,7 +190,6 @@ cudaError_t launch_uniform_pm1_padded(int n_units, int s_pad, const int *usize,
 
 // Box-Muller over pairs of uniforms: u1 = 1 - U[2m], u2 = U[2m+1]
 __global__ void normal_kernel(int64_t n, uint64_t key, double *x) {
-  pdl_entry();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const int64_t m = i >> 1;
@@ -235,7 +213,6 @@ cudaError_t launch_normal(int64_t n, uint64_t seed, uint64_t stream, double *x, 
 // ----------------------------------------------------------------------------
 template <typename Tin, typename Tout>
 __global__ void convert_kernel(int64_t n, const Tin *__restrict__ in, Tout *__restrict__ out) {
-  pdl_entry();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
     out[i] = (Tout)in[i];
@@ -253,7 +230,6 @@ template cudaError_t launch_convert<double, float>(int64_t, const double *, floa
 template cudaError_t launch_convert<float, double>(int64_t, const float *, double *, cudaStream_t);
 
 __global__ void fill_kernel(int64_t n, double v, double *x) {
-  pdl_entry();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) x[i] = v;
 }
@@ -265,7 +241,6 @@ cudaError_t launch_fill(int64_t n, double v, double *x, cudaStream_t s) {
 
 template <typename T>
 __global__ void add_kernel(int64_t n, const T *__restrict__ x, T *__restrict__ y) {
-  pdl_entry();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
     y[i] = y[i] + x[i];
@@ -282,7 +257,6 @@ template cudaError_t launch_add<float>(int64_t, const float *, float *, cudaStre
 
 __global__ void axpy_kernel(int64_t n, double a, const double *__restrict__ x,
                             double *__restrict__ y) {
-  pdl_entry();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
     y[i] = fma(a, x[i], y[i]);
@@ -299,7 +273,6 @@ cudaError_t launch_copy(int64_t n, const double *x, double *y, cudaStream_t s) {
 
 __global__ void sub_kernel(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
                            double *__restrict__ o) {
-  pdl_entry();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
     o[i] = a[i] - b[i];
@@ -319,7 +292,6 @@ cg_update_xr_kernel(int64_t n, double *__restrict__ x, double *__restrict__ r,
                     const double *__restrict__ p, const double *__restrict__ q,
                     const double *__restrict__ rz, const double *__restrict__ pq_partials,
                     double *__restrict__ rr_partials, double *__restrict__ alpha_out, int n_pq) {
-  pdl_entry();
   __shared__ double sh[32];
   const double pq = block_sum_partials(pq_partials, n_pq, sh);
   const double alpha = rz[0] / pq;
@@ -410,7 +382,6 @@ __device__ __forceinline__ void split_f32(double v, float *hi, float *lo, int64_
 
 __global__ void split_kernel(int64_t n, const double *__restrict__ v, float *__restrict__ hi,
                              float *__restrict__ lo) {
-  pdl_entry();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
     split_f32(v[i], hi, lo, i);
@@ -433,7 +404,6 @@ cg_update_p_kernel(int64_t n, double *__restrict__ p, const double *__restrict__
                    const double *__restrict__ rzold_partials, double *__restrict__ rz_out,
                    int flexible, double *__restrict__ zold_out, float *__restrict__ p_hi,
                    float *__restrict__ p_lo, int n_rz) {
-  pdl_entry();
   __shared__ double sh[32];
   const double rz_new = block_sum_partials(rz_partials, n_rz, sh);
   double num = rz_new;
@@ -494,7 +464,6 @@ cudaError_t launch_cg_update_p(int64_t n, double *p, const double *z, const doub
 __global__ void __launch_bounds__(kRedThreads)
 cg_check_kernel(const double *__restrict__ rr_partials, double *__restrict__ scal, int *iters,
                 int max_iter, cudaGraphConditionalHandle handle) {
-  pdl_entry();
   __shared__ double sh[32];
   const double rr = block_sum_partials(rr_partials, kRedBlocks, sh);
   if (threadIdx.x == 0) {
@@ -522,7 +491,6 @@ void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_rela
 __global__ void __launch_bounds__(kRedThreads)
 multi_dot_kernel(int64_t n, const double *__restrict__ V, int64_t ldv,
                  const double *__restrict__ w, double *__restrict__ partials) {
-  pdl_entry();
   __shared__ double sh[32];
   const double *v = V + (size_t)blockIdx.y * ldv;
   double acc = 0.0;
@@ -543,7 +511,6 @@ cudaError_t launch_multi_dot(int64_t n, const double *V, int64_t ldv, int k, con
 __global__ void __launch_bounds__(kRedThreads)
 multi_dot_finalize_kernel(const double *__restrict__ partials, double *__restrict__ h,
                           double *__restrict__ hacc) {
-  pdl_entry();
   __shared__ double sh[32];
   const double v = block_sum_partials(partials + (size_t)blockIdx.x * kRedBlocks, kRedBlocks, sh);
   if (threadIdx.x == 0) {
@@ -561,7 +528,6 @@ cudaError_t launch_multi_dot_finalize(const double *partials, int k, double *h, 
 
 __global__ void gs_update_kernel(int64_t n, const double *__restrict__ V, int64_t ldv, int k,
                                  const double *__restrict__ h, double *__restrict__ w) {
-  pdl_entry();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     double acc = w[i];
@@ -580,7 +546,6 @@ cudaError_t launch_gs_update(int64_t n, const double *V, int64_t ldv, int k, con
 __global__ void normalize_into_kernel(int64_t n, const double *__restrict__ w,
                                       const double *__restrict__ sumsq, double *__restrict__ v,
                                       double *__restrict__ hout) {
-  pdl_entry();
   const double nr = sqrt(sumsq[0]);
   if (blockIdx.x == 0 && threadIdx.x == 0) hout[0] = nr;
   const double a = nr > 0.0 ? 1.0 / nr : 0.0;
@@ -599,7 +564,6 @@ cudaError_t launch_normalize_into(int64_t n, const double *w, const double *sums
 // in rows 0..j+1.  Applies rotations 0..j-1, forms rotation j, updates g.
 __global__ void gmres_givens_kernel(double *H, int ldh, int j, double *cs, double *sn,
                                     double *g) {
-  pdl_entry();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double *h = H + (size_t)j * ldh;
   for (int i = 0; i < j; ++i) {
@@ -630,7 +594,6 @@ cudaError_t launch_gmres_givens(double *H, int ldh, int j, double *cs, double *s
 
 __global__ void gmres_backsolve_kernel(const double *H, int ldh, int j, const double *g,
                                        double *y) {
-  pdl_entry();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int i = j - 1; i >= 0; --i) {
     double acc = g[i];
@@ -647,7 +610,6 @@ cudaError_t launch_gmres_backsolve(const double *H, int ldh, int j, const double
 
 __global__ void combine_kernel(int64_t n, const double *__restrict__ V, int64_t ldv, int k,
                                const double *__restrict__ y, double *__restrict__ x) {
-  pdl_entry();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     double acc = x[i];

@@ -275,7 +275,6 @@ __device__ void tail_dense(const TailPlan<T> &pl, const double *Crows, const Dis
 template <typename T>
 __global__ void __launch_bounds__(kTailThreads, 1)
 vcycle_tail_kernel(const TailPlan<T> *__restrict__ plp) {
-  pdl_entry();
   __shared__ T res_all[kTailWarps][kTailMaxS];
   const TailPlan<T> &pl = *plp;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -382,10 +381,6 @@ cudaLaunchConfig_t tail_config(int cluster, int smem, cudaLaunchAttribute *attr,
   attr[0].val.clusterDim.x = cluster;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
-  if (nattr > 1) {
-    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[1].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
-  }
   cfg.attrs = attr;
   cfg.numAttrs = nattr;
   return cfg;
@@ -426,8 +421,8 @@ cudaError_t launch_vcycle_tail(const TailPlan<T> *plan_dev, int cluster, int sme
                                cudaStream_t s) {
   if (cluster <= 0 || !plan_dev || smem_bytes < 0 || smem_bytes > kTailSmemMax)
     return cudaErrorInvalidValue;
-  cudaLaunchAttribute attr[2];
-  cudaLaunchConfig_t cfg = tail_config<T>(cluster, smem_bytes, attr, 2, s);
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = tail_config<T>(cluster, smem_bytes, attr, 1, s);
   cudaError_t e = cudaLaunchKernelEx(&cfg, vcycle_tail_kernel<T>, plan_dev);
   note_launch();
   return e;

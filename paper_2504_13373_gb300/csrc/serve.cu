@@ -533,16 +533,6 @@ cudaError_t create_engine(Engine &e) {
   std::memset(e.hst, 0, (size_t)BI_COUNT * e.K * sizeof(int));
   std::memset(e.hsc, 0, (size_t)BD_COUNT * e.K * sizeof(double));
   cudaError_t ge = e.gm ? build_gm(e) : build_cg(e);
-  if (ge != cudaSuccess && pdl_enabled()) {
-    // programmatic launch edges that do not build: plain stream order
-    (void)cudaGetLastError();
-    pdl_set(false);
-    for (cudaGraphExec_t *x : {&e.exec, &e.x_start, &e.x_end})
-      if (*x) cudaGraphExecDestroy(*x), *x = nullptr;
-    for (cudaGraph_t *g : {&e.graph, &e.g_start, &e.g_end})
-      if (*g) cudaGraphDestroy(*g), *g = nullptr;
-    ge = e.gm ? build_gm(e) : build_cg(e);
-  }
   ECU(ge);
   ECU(cudaStreamSynchronize(e.s));
   e.slot.assign(e.K, nullptr);
