@@ -62,11 +62,17 @@ def parse():
     ap.add_argument("--n", type=int, default=256, help="cells per side (default: the full workload)")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-iters", type=int, default=3, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-warmup", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-run", action="store_true",
                     help="one mixed solve only (for an ncu launch list); prints no bench line")
     ap.add_argument("--host-loop", action="store_true",
                     help="with --profile-run: drive the CG loop from the host (per-kernel ncu)")
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="with --profile-run: stop each solve after this many CG iterations")
+    ap.add_argument("--grid-tail", type=int, default=-1, choices=[-1, 0, 1],
+                    help="coarse levels as one persistent launch (1) or one launch per step (0); "
+                         "-1: the library default")
     ap.add_argument("--bulk-staging", action="store_true",
                     help="level-0 FP32 sweep with bulk-copy (TMA) staging of A and w D^-1")
     ap.add_argument("--serve-requests", type=int, default=512,
@@ -75,6 +81,8 @@ def parse():
                     help="c2 (default): the P3 256^2 bench line; c1 / c3 / c4: solves/s of the "
                          "P1 32^2, LDG Q2 512^2 conv-diff and P2 48^3 tet workloads per precision")
     ap.add_argument("--peclet", type=float, default=100.0, help="Peclet number of c3")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the c1 / c3 / c4 records of the default run")
     return ap.parse_args()
 
 
@@ -107,6 +115,98 @@ def hbm_peak():
             return float(json.load(f)["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# algorithmic bytes of one preconditioned CG iteration (whole-iteration roofline)
+# ----------------------------------------------------------------------------
+def level_shapes(gasa, ctx, n_levels):
+    return [gasa.gasa_level_shape(ctx, k) for k in range(n_levels)]
+
+
+def iteration_bytes(shapes, precision, t_pre=3, t_post=3):
+    """Bytes one CG iteration must move, counted once per kernel that reads
+    or writes them (matrix values, column indices and row pointers, the
+    vectors each kernel touches), for the kernels a graph-resident CG step
+    launches: the V-cycle of Alg. 2 on every level (first pre-smoothing step
+    x = w D^-1 b, t_pre - 1 further sweeps, residual, restriction, coarsest
+    dense solve, prolongation, t_post sweeps), the outer product q = A p and
+    the CG vector updates with their dot products.  precision: 'fp64',
+    'mixed32' (FP32 V-cycle, double-single outer product) or 'mixed16'
+    (as mixed32 with FP16 level-0 A and w D^-1 plus one FP32 scale per
+    block).  Returns (total bytes, per-part dict)."""
+    N = len(shapes) - 1
+    w = 8 if precision == "fp64" else 4
+    parts = {}
+    n0 = shapes[0]["units"] * shapes[0]["s"]
+    for k in range(N):
+        sh = shapes[k]
+        n, s, nnzb = sh["units"], sh["s"], sh["nnzb"]
+        nxt = shapes[k + 1]
+        n1, s1 = nxt["units"], nxt["s"]
+        wa = 2 if (precision == "mixed16" and k == 0) else w
+        scale = 4 if (precision == "mixed16" and k == 0) else 0
+        A = nnzb * (s * s * wa + scale) + 4 * nnzb + 4 * (n + 1)
+        W = n * (s * s * wa + scale)
+        v = n * s * w
+        R = sh["R_nnzb"] * (s * s1 * w) + 4 * sh["R_nnzb"] + 4 * (n1 + 1)
+        P = sh["P_nnzb"] * (s * s1 * w) + 4 * sh["P_nnzb"] + 4 * (n + 1)
+        first = W + 2 * v
+        if k == 0 and precision == "mixed32":
+            first = W + n * s * (8 + 4 + 4)      # reads the FP64 residual, writes x and its FP32 copy
+        sweeps = (t_pre - 1 + t_post) * (A + W + 3 * v)
+        resid = A + 3 * v
+        restrict = R + v + n1 * s1 * w
+        prolong = P + n1 * s1 * w + 2 * v
+        parts[f"level{k}"] = first + sweeps + resid + restrict + prolong
+    nc = shapes[N]["units"] * shapes[N]["s"]
+    parts["coarse"] = nc * nc * 8 + 2 * nc * w
+    sh = shapes[0]
+    nnzb, s, n = sh["nnzb"], sh["s"], sh["units"]
+    idx = 4 * nnzb + 4 * (n + 1)
+    if precision == "fp64":
+        parts["outer_Ap"] = nnzb * s * s * 8 + idx + 2 * n0 * 8
+        parts["vectors"] = 2 * n0 * 8 + 2 * 2 * n0 * 8 + 3 * n0 * 8 + 6 * n0 * 8
+        # p.q dot; r.z dot; p = z + beta p (2 reads, 1 write); x, r update (4 reads, 2 writes)
+    else:
+        parts["outer_Ap"] = nnzb * s * s * 8 + idx + n0 * (8 + 8 + 8)
+        # A hi + lo words; p hi + lo gathered once, q written, p read for p.q
+        parts["vectors"] = (n0 * (4 + 8)                    # z back to FP64
+                            + 2 * 2 * n0 * 8                  # r.z and r.zold
+                            + n0 * (8 + 8 + 8 + 8 + 4 + 4)    # p = z + beta p, its hi/lo split
+                            + 6 * n0 * 8)                     # x, r update
+    return float(sum(parts.values())), {k: float(v) for k, v in parts.items()}
+
+
+def gmres_iteration_bytes(shapes, precision, iterations, restart=30, t_pre=3, t_post=3):
+    """Average bytes of one GMRES(restart) step (flexible for the mixed
+    V-cycles) over a solve of `iterations` steps: the V-cycle (with the FP64 /
+    FP32 conversions around an FP32 one), the FP64 outer product, classical
+    Gram-Schmidt applied twice against the j + 1 basis vectors of step j
+    (a multi-dot reading the basis and w, an update reading the basis and w
+    and writing w, per pass), the norm and the normalisation into v_{j+1}.
+    Restart overheads (a residual, a norm and the combination of the basis)
+    are spread over the steps of their cycle."""
+    tot, parts = iteration_bytes(shapes, "fp64" if precision == "fp64" else precision, t_pre, t_post)
+    vc = sum(v for k, v in parts.items() if k.startswith("level") or k == "coarse")
+    sh = shapes[0]
+    nnzb, s, n = sh["nnzb"], sh["s"], sh["units"]
+    n0 = n * s
+    spmv = nnzb * s * s * 8 + 4 * nnzb + 4 * (n + 1) + 2 * n0 * 8
+    conv = 0 if precision == "fp64" else n0 * (8 + 4) + n0 * (4 + 8)
+    steps, js = 0, []
+    while steps < iterations:
+        m = min(restart, iterations - steps)
+        js.append(list(range(m)))
+        steps += m
+    total = 0.0
+    for cyc in js:
+        for j in cyc:
+            arnoldi = 2 * ((j + 2) + (j + 3)) * n0 * 8 + 3 * n0 * 8
+            total += vc + conv + spmv + arnoldi
+        m = len(cyc)
+        total += (spmv + n0 * 8) + (m + 2) * n0 * 8        # restart residual + norm, combine
+    return total / max(1, iterations)
 
 
 # ----------------------------------------------------------------------------
@@ -168,9 +268,24 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # CPU oracle sample (cpu_baseline leg and --impl reference)
 # ----------------------------------------------------------------------------
-def cpu_sample_main(path, iters):
-    """Runs in a single-threaded child: oracle setup on the saved workload,
-    then `iters` oracle flexible-CG iterations with the float32 V-cycle."""
+ORACLE_SOLVE = os.path.join(ROOT, "tests", "golden", "c2_oracle_solve.json")
+
+
+def oracle_solve_record():
+    """The oracle's own solves of the full workload (iterations, residuals,
+    sampled x), written by tests/golden/make_c2_oracle_solve.py; None when
+    absent."""
+    try:
+        with open(ORACLE_SOLVE) as f:
+            return json.load(f)
+    except Exception:
+        return None
+
+
+def cpu_sample_main(path, warmup, iters):
+    """Runs in a single-threaded child: oracle setup on the saved workload
+    (untimed), `warmup` untimed flexible-CG iterations with the float32
+    V-cycle, then `iters` timed ones (one timer per iteration)."""
     from oracle import gasa_oracle as O
     d = np.load(path, allow_pickle=True)
     aggs = [d[f"agg{k}"] for k in range(int(d["nagg"]))]
@@ -179,21 +294,24 @@ def cpu_sample_main(path, iters):
     t_setup = time.perf_counter() - t0
     M = O.make_vcycle(H, "fp32")
     A = H.levels[0].A
+    if warmup > 0:
+        O.pcg(A, d["rhs"], M, 1e-300, warmup, flexible=True)
     t0 = time.perf_counter()
     O.pcg(A, d["rhs"], M, 1e-300, iters, flexible=True)
-    t_it = (time.perf_counter() - t0) / iters
-    print(json.dumps({"setup_s": t_setup, "s_per_iter": t_it}))
+    total = time.perf_counter() - t0
+    print(json.dumps({"setup_s": t_setup, "s_per_iter": total / iters, "timed_s": total,
+                      "iters": iters}))
 
 
-def run_cpu_sample(pr, iters):
+def run_cpu_sample(pr, iters, warmup=0):
     tmp = tempfile.mktemp(prefix="gasa_wl_", suffix=".npz")
     np.savez(tmp, row_ptr=pr.A.row_ptr, col=pr.A.col, val=pr.A.val, B0=pr.B0, r=pr.r,
              rhs=pr.rhs, nagg=len(pr.agg_of), **{f"agg{k}": a for k, a in enumerate(pr.agg_of)})
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     try:
         out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", tmp,
-                              "--cpu-iters", str(iters)], capture_output=True, text=True, env=env,
-                             timeout=1800)
+                              "--cpu-iters", str(iters), "--cpu-warmup", str(warmup)],
+                             capture_output=True, text=True, env=env, timeout=1800)
         line = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
         if out.returncode != 0 or not line:
             return None, out.stderr[-2000:]
@@ -207,7 +325,7 @@ def run_cpu_sample(pr, iters):
 def main():
     args = parse()
     if args.cpu_sample:
-        cpu_sample_main(args.cpu_sample, args.cpu_iters)
+        cpu_sample_main(args.cpu_sample, args.cpu_warmup, args.cpu_iters)
         return
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -218,24 +336,36 @@ def main():
 
 
 def reference_main(args, rank, world):
+    """The reference arm is the CPU oracle as it stands, on one host core.
+    One step is one flexible-CG iteration of the oracle (float32 V-cycle) on
+    the full workload, timed; W untimed iterations come first.  A whole
+    solve takes the oracle's own iteration count, from its committed run to
+    1e-10 (tests/golden/c2_oracle_solve.json), so solves/s = 1 / (seconds per
+    iteration x that count).  Under torchrun only rank 0 runs."""
     if rank != 0:
         return 0
     pr = build_problem(args.n)
-    # iterations of one solve, from this workload's CUDA solve (identical
-    # to the oracle's within +-1 wherever both are run to completion)
-    iters_per_solve = ITERS_PER_SOLVE.get(args.n)
-    res, err = run_cpu_sample(pr, max(1, args.steps))
+    rec = oracle_solve_record()
+    iters_per_solve = None
+    if rec is not None and rec.get("dofs") == pr.n_dofs and "mixed32" in rec:
+        iters_per_solve = int(rec["mixed32"]["iterations"])
+    steps = max(1, args.steps)
+    res, err = run_cpu_sample(pr, steps, max(0, args.warmup))
     if res is None or iters_per_solve is None:
-        print(json.dumps({"impl": "reference", "unavailable": f"oracle sample failed: {err}"}))
+        why = f"oracle sample failed: {err}" if res is None else \
+            "no committed oracle solve of this workload (tests/golden/c2_oracle_solve.json)"
+        print(json.dumps({"impl": "reference", "unavailable": why}))
         return 0
-    sec_per_solve = res["s_per_iter"] * iters_per_solve
-    value = 1.0 / sec_per_solve
-    sample = (f"oracle setup on the full workload ({res['setup_s']:.1f} s, untimed), then "
-              f"{max(1, args.steps)} flexible-CG iterations with the float32 V-cycle, "
-              f"{res['s_per_iter']:.3f} s each, x {iters_per_solve} iterations per solve")
+    value = 1.0 / (res["s_per_iter"] * iters_per_solve)
+    sample = (f"oracle setup on the full workload ({res['setup_s']:.1f} s, untimed), "
+              f"{max(0, args.warmup)} untimed and {steps} timed flexible-CG iterations with the "
+              f"float32 V-cycle ({res['s_per_iter']:.3f} s each); a solve = {iters_per_solve} "
+              f"iterations, the oracle's own count to 1e-10 from its committed full run")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_per_solve * 1e3,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": res["s_per_iter"] * 1e3,
+        "step": "one flexible-CG iteration of the oracle (float32 V-cycle) on the full workload",
+        "iterations_per_solve": iters_per_solve,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "n": args.n},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
@@ -243,12 +373,6 @@ def reference_main(args, rank, world):
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}))
     return 0
-
-
-# CG iterations of one solve of this workload to 1e-10 (mixed and FP64 agree),
-# measured by the CUDA path's bench runs; the oracle matches the CUDA path's
-# counts within +-1 wherever both run to completion (32^2 and 64^2 meshes).
-ITERS_PER_SOLVE = {256: 3348, 64: 906}
 
 
 def serve_bench(gasa, n_requests, device=0):
@@ -347,78 +471,132 @@ def serve_bench(gasa, n_requests, device=0):
     return out
 
 
-def workload_main(args, local):
-    """solves/s, iterations, true residual and error against the FP64 solve
-    of one of the other workloads, per precision: FP64, FP32 V-cycle,
-    FP16-block V-cycle (the parity tests pin the FP64 solve to the oracle)."""
-    import torch
+def build_workload(which, n_arg=None, peclet=100.0):
     from synth import configs
-    from paper_2504_13373_gb300 import gasa
-    gasa.load()
-    torch.cuda.set_device(local)
-    t0 = time.perf_counter()
-    if args.workload == "c1":
-        pr, name = configs.poisson2d_p1(), "poisson2d_sipg_p1_tri_32x32"
-    elif args.workload == "c3":
-        n = 512 if args.n == 256 else args.n
-        pr = configs.convdiff2d_q2(n=n, peclet=args.peclet)
-        name = f"convdiff2d_ldg_q2_quad_{n}x{n}_pe{args.peclet:g}"
-    else:
-        n = 48 if args.n == 256 else args.n
-        pr, name = configs.poisson3d_p2(n=n), f"poisson3d_sipg_p2_tet_{n}cubed"
-    t_gen = time.perf_counter() - t0
+    if which == "c1":
+        return configs.poisson2d_p1(), "poisson2d_sipg_p1_tri_32x32"
+    if which == "c3":
+        n = n_arg or 512
+        return (configs.convdiff2d_q2(n=n, peclet=peclet),
+                f"convdiff2d_ldg_q2_quad_{n}x{n}_pe{peclet:g}")
+    n = n_arg or 48
+    return configs.poisson3d_p2(n=n), f"poisson3d_sipg_p2_tet_{n}cubed"
+
+
+def measure_workload(gasa, pr, name, steps, warmup, device):
+    """solves/s, iterations, true residual, error against this run's FP64
+    solve and a whole-iteration roofline of one workload, per precision:
+    FP64, FP32 V-cycle, FP16-block V-cycle (the parity tests pin each
+    precision's solve to the oracle's on reduced sizes of the same recipe)."""
+    import torch
     A = pr.A
-    ctx = gasa.gasa_create(local)
+    ctx = gasa.gasa_create(device)
     opt = gasa.gasa_default_options(dim=pr.dim, n_cand=pr.r, max_iter=20000,
                                     solver=gasa.GASA_SOLVER_CG if pr.solver == "cg"
                                     else gasa.GASA_SOLVER_GMRES)
     sinfo = gasa.gasa_setup(ctx, A.row_ptr, A.col, A.val.ravel(), A.b, pr.agg_of, opt,
                             adj_ptr=pr.adj_ptr, adj_idx=pr.adj_idx, centroids=pr.centroids,
                             init_candidates=pr.B0)
-    b = torch.from_numpy(pr.rhs).cuda()
+    shapes = level_shapes(gasa, ctx, sinfo.n_levels)
+    peak, peak_kind = hbm_peak()
+    b = torch.from_numpy(pr.rhs).cuda(device)
     x = torch.zeros_like(b)
+    out, x64 = {}, None
+    As = A.to_scipy()
+    try:
+        for pname, prec in (("fp64", gasa.GASA_PREC_FP64), ("mixed32", gasa.GASA_PREC_MIXED32),
+                            ("mixed16", gasa.GASA_PREC_MIXED16)):
+            for _ in range(warmup):
+                gasa.gasa_solve(ctx, b, x, TOL, prec, on_device=True)
+            torch.cuda.synchronize()
+            per, infos = [], []
+            for _ in range(steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                infos.append(gasa.gasa_solve(ctx, b, x, TOL, prec, on_device=True))
+                e1.record()
+                torch.cuda.synchronize()
+                per.append(e0.elapsed_time(e1))
+            xh = x.cpu().numpy()
+            if x64 is None:
+                x64 = xh.copy()
+            its = int(infos[-1].iterations)
+            ms = float(np.median(per))
+            if pr.solver == "cg":
+                b_it = iteration_bytes(shapes, pname, opt.t_pre, opt.t_post)[0]
+            else:
+                b_it = gmres_iteration_bytes(shapes, pname, its, opt.restart or 30, opt.t_pre, opt.t_post)
+            gbs = b_it / (ms / max(1, its) / 1e3) / 1e9
+            out[pname] = {
+                "solves_per_s": 1e3 / ms, "median_ms": ms, "iterations": its,
+                "rel_residual": float(np.linalg.norm(pr.rhs - As @ xh) / np.linalg.norm(pr.rhs)),
+                "rel_err_vs_fp64_solve": float(np.linalg.norm(xh - x64) / np.linalg.norm(x64)),
+                "roofline_iteration": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                       "frac": gbs / peak, "peak_kind": f"{peak_kind} hbm_gbs",
+                                       "bytes_per_iteration": b_it,
+                                       "ms_per_iteration": ms / max(1, its)}}
+    finally:
+        gasa.gasa_destroy(ctx)
+    return {"workload": name, "dofs": pr.n_dofs, "block": A.b, "nnzb": int(A.nnzb),
+            "levels": sinfo.n_levels, "candidates": pr.r, "solver": pr.solver,
+            "level_dofs": [int(sinfo.dofs[k]) for k in range(sinfo.n_levels)],
+            "level_nnzb": [int(sinfo.nnzb[k]) for k in range(sinfo.n_levels)],
+            "level_block": [int(sinfo.block[k]) for k in range(sinfo.n_levels)],
+            "setup_s": sinfo.seconds, "steps": steps, "warmup": warmup, "precisions": out}
+
+
+def other_workloads(gasa, device, steps=1, warmup=1):
+    """The P1 32^2 workload, the LDG + upwind Q2 512^2 workload at Peclet 1,
+    100 and 1e4, and the P2 48^3 tet workload, one record each."""
+    recs = []
+    for which, pe in (("c1", None), ("c3", 1.0), ("c3", 100.0), ("c3", 1e4), ("c4", None)):
+        t0 = time.perf_counter()
+        pr, name = build_workload(which, None, pe if pe is not None else 100.0)
+        t_gen = time.perf_counter() - t0
+        rec = measure_workload(gasa, pr, name, steps, warmup, device)
+        rec["generate_s"] = t_gen
+        recs.append(rec)
+        del pr
+    return recs
+
+
+def workload_main(args, local):
+    """--workload c1 / c3 / c4: one workload's record, as a bench line."""
+    import torch
+    from paper_2504_13373_gb300 import gasa
+    gasa.load()
+    torch.cuda.set_device(local)
+    t0 = time.perf_counter()
+    n_arg = None if args.n == 256 else args.n
+    pr, name = build_workload(args.workload, n_arg, args.peclet)
+    t_gen = time.perf_counter() - t0
     if args.profile_run:
         # one mixed solve from the host-driven loop (per-kernel ncu launch list)
+        A = pr.A
+        ctx = gasa.gasa_create(local)
+        opt = gasa.gasa_default_options(dim=pr.dim, n_cand=pr.r, max_iter=20000,
+                                        solver=gasa.GASA_SOLVER_CG if pr.solver == "cg"
+                                        else gasa.GASA_SOLVER_GMRES)
+        gasa.gasa_setup(ctx, A.row_ptr, A.col, A.val.ravel(), A.b, pr.agg_of, opt,
+                        adj_ptr=pr.adj_ptr, adj_idx=pr.adj_idx, centroids=pr.centroids,
+                        init_candidates=pr.B0)
+        b = torch.from_numpy(pr.rhs).cuda()
+        x = torch.zeros_like(b)
         gasa.gasa_profile_enable(ctx, True)
         gasa.gasa_solve(ctx, b, x, TOL, gasa.GASA_PREC_MIXED32, on_device=True)
         torch.cuda.synchronize()
         gasa.gasa_destroy(ctx)
         return 0
-    out, x64 = {}, None
-    for pname, prec in (("fp64", gasa.GASA_PREC_FP64), ("mixed32", gasa.GASA_PREC_MIXED32),
-                        ("mixed16", gasa.GASA_PREC_MIXED16)):
-        for _ in range(args.warmup):
-            gasa.gasa_solve(ctx, b, x, TOL, prec, on_device=True)
-        torch.cuda.synchronize()
-        per, infos = [], []
-        for _ in range(args.steps):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            infos.append(gasa.gasa_solve(ctx, b, x, TOL, prec, on_device=True))
-            e1.record()
-            torch.cuda.synchronize()
-            per.append(e0.elapsed_time(e1))
-        xh = x.cpu().numpy()
-        if x64 is None:
-            x64 = xh.copy()
-        rec = {"solves_per_s": 1e3 / float(np.median(per)), "median_ms": float(np.median(per)),
-               "iterations": int(infos[-1].iterations),
-               "rel_residual": float(np.linalg.norm(pr.rhs - A.to_scipy() @ xh) / np.linalg.norm(pr.rhs)),
-               "rel_err_vs_fp64_solve": float(np.linalg.norm(xh - x64) / np.linalg.norm(x64))}
-        out[pname] = rec
-    gasa.gasa_destroy(ctx)
+    with ClockSampler(local) as clk:
+        rec = measure_workload(gasa, pr, name, args.steps, args.warmup, local)
+    mix = rec["precisions"]["mixed32"]
     print(json.dumps({
-        "metric": METRIC, "value": out["mixed32"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["mixed32"]["median_ms"],
+        "metric": METRIC, "value": mix["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mix["median_ms"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-        "data": "synthetic",
-        "config": {"workload": name, "dofs": pr.n_dofs, "block": A.b, "nnzb": int(A.nnzb),
-                   "levels": sinfo.n_levels, "candidates": pr.r, "tol": TOL, "solver": pr.solver,
-                   "level_dofs": [int(sinfo.dofs[k]) for k in range(sinfo.n_levels)],
-                   "level_nnzb": [int(sinfo.nnzb[k]) for k in range(sinfo.n_levels)],
-                   "level_block": [int(sinfo.block[k]) for k in range(sinfo.n_levels)]},
-        "precisions": out, "setup_s": sinfo.seconds, "generate_s": t_gen}))
+        "data": "synthetic", "config": {"workload": name, "tol": TOL},
+        "record": rec, "generate_s": t_gen, "clocks": clk.summary()}))
     return 0
 
 
@@ -443,6 +621,10 @@ def ours_main(args, rank, world, local):
     stream = torch.cuda.Stream()
     ctx = gasa.gasa_create(local, stream)
     opt = gasa.gasa_default_options(dim=2, n_cand=pr.r, max_iter=20000)
+    if args.profile_run and args.profile_iters > 0:
+        opt.max_iter = args.profile_iters
+    if args.grid_tail >= 0:
+        opt.grid_tail = args.grid_tail
     opt.bulk_staging = 1 if args.bulk_staging else 0
     sinfo = gasa.gasa_setup(ctx, A.row_ptr, A.col, A.val.ravel(), A.b, pr.agg_of, opt,
                             adj_ptr=pr.adj_ptr, adj_idx=pr.adj_idx, centroids=pr.centroids,
@@ -485,12 +667,15 @@ def ours_main(args, rank, world, local):
         return ms, infos, launches, per_ms
 
     if args.profile_run:
+        # launches before the first solve, for an ncu skip count (-s)
+        print(json.dumps({"setup_launches": gasa.gasa_kernel_launches()}), flush=True)
         if args.host_loop:
             # kernel nodes inside a graph with conditional nodes cannot be
             # profiled one by one; the host-driven loop runs the same kernels
             gasa.gasa_profile_enable(ctx, True)
         for _ in range(max(1, args.steps)):
-            gasa.gasa_solve(ctx, b_dev, x_dev, TOL, gasa.GASA_PREC_MIXED32, on_device=True)
+            gasa.gasa_solve(ctx, b_dev, x_dev, TOL, gasa.GASA_PREC_MIXED32, on_device=True,
+                            allow_not_converged=args.profile_iters > 0)
         torch.cuda.synchronize()
         gasa.gasa_destroy(ctx)
         return 0
@@ -498,10 +683,14 @@ def ours_main(args, rank, world, local):
     for _ in range(args.warmup):
         gasa.gasa_solve(ctx, b_dev, x_dev, TOL, gasa.GASA_PREC_MIXED32, on_device=True)
         gasa.gasa_solve(ctx, b_dev, x_dev, TOL, gasa.GASA_PREC_FP64, on_device=True)
+    xs = {}
     with ClockSampler(local) as clk:
         ms_mix, inf_mix, launches, per_mix = timed(gasa.GASA_PREC_MIXED32, args.steps)
+        xs["mixed32"] = x_dev.cpu().numpy()
         ms_64, inf_64, _, per_64 = timed(gasa.GASA_PREC_FP64, args.steps)
+        xs["fp64"] = x_dev.cpu().numpy()
         ms_16, inf_16, _, per_16 = timed(gasa.GASA_PREC_MIXED16, args.steps)
+        xs["mixed16"] = x_dev.cpu().numpy()
         # roofline of the dominant kernel: one more mixed solve with CUDA events
         # around every level-0 sweep (events cannot sit inside the solve graph,
         # so this solve runs the same kernels from the host-driven loop)
@@ -524,12 +713,37 @@ def ours_main(args, rank, world, local):
 
     value = world * args.steps / (ms_mix / 1e3)
     value64 = world * args.steps / (ms_64 / 1e3)
-    peak, peak_kind = hbm_peak()
     ms_k, n_k, bytes_k = prof
     achieved = (bytes_k / n_k) / (ms_k / n_k / 1e3) / 1e9 if n_k else None
     ncu = NCU_TRAFFIC[bool(args.bulk_staging)]
     traffic = ncu["bytes_per_launch"] if ncu["src_sha"] == src_hash(ncu["file"]) else None
     iters = [i.iterations for i in inf_mix]
+    shapes = level_shapes(gasa, ctx, sinfo.n_levels)
+
+    def iteration_roofline(prec, ms, infos):
+        """algorithmic bytes of one CG iteration / (solve time / iterations)"""
+        b_it, parts = iteration_bytes(shapes, prec, opt.t_pre, opt.t_post)
+        ms_it = ms / max(1, sum(i.iterations for i in infos))
+        gbs = b_it / (ms_it / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                "peak_kind": f"{peak_kind} hbm_gbs", "bytes_per_iteration": b_it,
+                "ms_per_iteration": ms_it, "bytes_by_part": parts,
+                "what": "whole preconditioned CG iteration (V-cycle on every level, outer A p, "
+                        "vector updates and dot products); time = timed solves / their iterations"}
+
+    peak, peak_kind = hbm_peak()
+    roof_it = {"mixed32": iteration_roofline("mixed32", ms_mix, inf_mix),
+               "fp64": iteration_roofline("fp64", ms_64, inf_64),
+               "mixed16": iteration_roofline("mixed16", ms_16, inf_16)}
+    err_vs_oracle = None
+    rec0 = oracle_solve_record()
+    if rec0 is not None and rec0.get("dofs") == n and "fp64" in rec0:
+        idx = np.asarray(rec0["sample_index"], dtype=np.int64)
+        xo = np.asarray(rec0["fp64"]["x_sample"])
+        err_vs_oracle = {
+            "what": ("||x - x_oracle|| / ||x_oracle|| over the 4,096 sampled dofs of the oracle's "
+                     "own FP64 solve (tests/golden/c2_oracle_solve.json)"),
+            **{k: float(np.linalg.norm(v[idx] - xo) / np.linalg.norm(xo)) for k, v in xs.items()}}
     line = {
         "metric": METRIC,
         "value": value,
@@ -568,22 +782,31 @@ def ours_main(args, rank, world, local):
                      "frac": achieved / peak if achieved else None, "peak_kind": f"{peak_kind} hbm_gbs",
                      "traffic": traffic, "algorithmic_bytes_per_launch": bytes_k / n_k if n_k else None,
                      "launches": n_k, "avg_launch_us": ms_k / n_k * 1e3 if n_k else None},
+        "roofline_iteration": roof_it,
+        "error_vs_oracle": err_vs_oracle,
         "e2e": {"value": world * args.steps / e2e_s, "unit": "solves/s",
                 "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
         "gpu_launches": launches,
         "clocks": clocks,
     }
-    ITERS_PER_SOLVE.setdefault(args.n, int(np.median(iters)))
+    rec = oracle_solve_record()
+    oracle_iters = None
+    if rec is not None and rec.get("dofs") == n and "mixed32" in rec:
+        oracle_iters = int(rec["mixed32"]["iterations"])
+        line["oracle"] = {k: {"iterations": rec[k]["iterations"], "rel_residual": rec[k]["rel_residual"]}
+                          for k in ("fp64", "mixed32", "mixed16") if k in rec}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res, err = run_cpu_sample(pr, args.cpu_iters)
+        per_solve = oracle_iters or int(np.median(iters))
         if res is not None:
-            sps = 1.0 / (res["s_per_iter"] * float(np.median(iters)))
+            sps = 1.0 / (res["s_per_iter"] * per_solve)
             line["cpu_baseline"] = {
                 "value": sps, "unit": "solves/s", "cores": 1, "kind": "oracle",
                 "sample": (f"oracle setup on the full workload ({res['setup_s']:.1f} s, untimed), then "
                            f"{args.cpu_iters} flexible-CG iterations with the float32 V-cycle at "
-                           f"{res['s_per_iter']:.3f} s each, scaled to {int(np.median(iters))} "
-                           f"iterations per solve (this run's count)")}
+                           f"{res['s_per_iter']:.3f} s each, scaled to {per_solve} iterations per "
+                           f"solve (" + ("the oracle's own count from its committed full run"
+                                         if oracle_iters else "this run's count") + ")")}
         else:
             line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
                                     "sample": f"failed: {err}"}
@@ -591,6 +814,11 @@ def ours_main(args, rank, world, local):
     if args.serve_requests > 0 and world == 1:
         # the serving stream is a per-GPU measurement: it runs at N = 1 only
         line["serving"] = serve_bench(gasa, args.serve_requests, local)
+    if world == 1 and not args.no_other_workloads:
+        # the other workloads (one warm-up and one timed solve per precision)
+        with ClockSampler(local) as clk2:
+            line["other_workloads"] = other_workloads(gasa, local)
+        line["other_workloads_clocks"] = clk2.summary()
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:

@@ -124,6 +124,15 @@ typedef struct {
                                 memory.  Same arithmetic per row, so results agree with the
                                 per-step launches to rounding.  0 (default): one launch per
                                 step (measured faster inside the graph-captured CG loop). */
+  int32_t grid_tail;         /* 1: the coarse levels of the V-cycle of Alg. 2 as one persistent
+                                cooperative launch over the whole GPU (kernels_grid.cu): every level
+                                k >= k0 >= 1 down to the coarsest, k0 the first level from which all
+                                levels have one block size s <= 8 and are stored unpadded; its
+                                steps are phases separated by bounded grid barriers.  Results agree
+                                with the per-step launches to rounding.  0: one launch per step. */
+  double wait_budget_s;      /* budget of one launch's bounded device-side waits (grid barriers of
+                                the persistent coarse launch); a wait that runs out ends the launch
+                                and the solve returns GASA_ERR_TIMEOUT.  0 = 1 second. */
 } gasa_options;
 
 typedef struct {
@@ -204,10 +213,12 @@ enum {
  * A_k so that the block inverses exist), and dofs counts real dofs only. */
 gasa_status gasa_level_shape(gasa_ctx *ctx, int32_t level, int64_t shape[8]);
 
-/* Fused bottom of the V-cycle (option tail_kib) of one precision: out[0] =
- * first level k0 run inside the cluster launch (n_levels - 1 when every
- * level runs as its own launches), out[1] = CTAs per cluster (0 when
- * unfused), out[2] = 1 when the coarsest solve runs inside the launch.
+/* Fused bottom of the V-cycle of one precision (option grid_tail, else
+ * tail_kib): out[0] = first level k0 run inside the fused launch
+ * (n_levels - 1 when every level runs as its own launches), out[1] = CTAs of
+ * the launch (the persistent grid's CTAs with grid_tail, the CTAs per
+ * cluster with tail_kib; 0 when unfused), out[2] = 1 when the coarsest solve
+ * runs inside the launch.
  * GASA_PREC_MIXED16 reports the FP32 tail it shares with MIXED32.
  * GASA_ERR_STATE before a successful gasa_setup, GASA_ERR_INVALID_ARG for an
  * unknown precision or a null pointer. */
@@ -384,7 +395,9 @@ gasa_status gasa_server_create(gasa_server **srv, int32_t device, int64_t hbm_bu
  * fit. */
 gasa_status gasa_server_add_mesh(gasa_server *srv, gasa_ctx *ctx, int32_t *mesh_id);
 /* Queue a solve of A x = b (b: host, copied before return) to relative
- * residual tol from x = 0.  Returns at once with a ticket. */
+ * residual tol from x = 0 in `precision` (GASA_PREC_FP64, MIXED32 or
+ * MIXED16; another value is GASA_ERR_INVALID_ARG).  Returns at once with a
+ * ticket. */
 gasa_status gasa_server_submit(gasa_server *srv, int32_t mesh_id, const double *b, double tol,
                                int32_t precision, uint64_t *ticket);
 /* GASA_PENDING while the solve is queued or running.  Once finished: copies

@@ -19,7 +19,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]
 SOURCES = ["kernels_mv.cu", "kernels_red.cu", "kernels_setup.cu", "kernels_h16.cu", "kernels_tma.cu",
-           "kernels_batch.cu", "kernels_tail.cu", "kernels_blk.cu", "gasa_api.cu", "serve.cu", "noalloc.cu"]
+           "kernels_batch.cu", "kernels_tail.cu", "kernels_blk.cu", "kernels_grid.cu", "kernels_wide.cu",
+           "gasa_api.cu", "serve.cu", "noalloc.cu"]
 
 
 def nvcc():

@@ -29,6 +29,16 @@ enum BatchInt {
   BI_COUNT = 6
 };
 
+// level 0 of the FP16-block V-cycle: A and w D^-1 in FP16 blocks with one
+// FP32 scale per block (square bs x bs blocks), FP32 vectors
+cudaError_t launch_bmv_h16(int mode, int n_brows, int bs, const int *rp, const int *col,
+                           const __half *val, const float *scale, const float *X, const float *B,
+                           float *Y, int K, cudaStream_t s);
+cudaError_t launch_bjacobi_h16(int mode, int n, int bs, const int *rp, const int *col,
+                               const __half *A, const float *ascale, const __half *W,
+                               const float *wscale, const float *X, const float *B, float *Xo,
+                               int K, cudaStream_t s);
+
 // nnzb: stored blocks of the matrix (picks the long-row variant)
 template <typename T>
 cudaError_t launch_bmv(int mode, int n_brows, int br, int bc, const int *rp, const int *col,

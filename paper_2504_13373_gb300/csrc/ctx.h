@@ -117,6 +117,13 @@ struct gasa_ctx {
   int tail_coarse[2] = {0, 0};   // 1: the coarsest solve runs inside the launch
   int tail_cluster[2] = {0, 0};  // CTAs per cluster
   int tail_smem[2] = {0, 0};     // dynamic shared memory per CTA
+  // persistent coarse levels per precision (kernels_grid.cu): levels
+  // grid_k0[p] .. N in one cooperative launch of grid_ctas[p] CTAs
+  void *grid_plan[2] = {};
+  int grid_k0[2] = {0, 0};
+  int grid_ctas[2] = {0, 0};
+  int grid_s[2] = {0, 0};
+  unsigned int *grid_bar = nullptr;
   // profiling
   bool prof = false;
   ProfClass pc[4];

@@ -17,6 +17,7 @@
 #include "internal.h"
 #include "ctx.h"
 #include "tail.h"
+#include "grid.h"
 
 using namespace gasa;
 
@@ -103,7 +104,11 @@ void free_all(gasa_ctx *ctx) {
   for (int p = 0; p < 2; ++p) {
     ctx->tail_plan[p] = nullptr;
     ctx->tail_k0[p] = 0;
+    ctx->grid_plan[p] = nullptr;
+    ctx->grid_k0[p] = 0;
+    ctx->grid_ctas[p] = 0;
   }
+  ctx->grid_bar = nullptr;
   ctx->V = ctx->Z = ctx->H = ctx->gm = ctx->mpart = nullptr;
   ctx->gm_restart = 0;
 }
@@ -369,6 +374,82 @@ gasa_status tail_build(gasa_ctx *ctx, int pi) {
   return GASA_OK;
 }
 
+// Plan of the persistent coarse levels for precision T (slot pi: 0 FP64,
+// 1 FP32), with opt.grid_tail: levels k0 .. N in one cooperative launch,
+// k0 the first level k >= 1 from which every level is stored unpadded with
+// one block size s <= 8 (A_k, P_k, R_k all s x s blocks).
+template <typename T>
+gasa_status grid_build(gasa_ctx *ctx, int pi) {
+  using P = Prec<T>;
+  const int N = ctx->N;
+  ctx->grid_plan[pi] = nullptr;
+  ctx->grid_k0[pi] = N;
+  ctx->grid_ctas[pi] = 0;
+  if (!ctx->opt.grid_tail || N < 2 || ctx->opt.t_pre < 1) return GASA_OK;
+  Level &lc = ctx->L[N];
+  const int S = lc.s;
+  if (S < 1 || S > 8 || lc.padded) return GASA_OK;
+  int k0 = N;
+  for (int k = N - 1; k >= 1; --k) {
+    Level &l = ctx->L[k];
+    if (l.mf || l.padded || l.s != S) break;
+    if (l.P.nrows != l.n || l.P.br != S || l.P.bc != S || l.R.br != S || l.R.bc != S ||
+        l.R.nrows != ctx->L[k + 1].n)
+      break;
+    if (!P::A(l.A) || !P::W(l) || !P::A(l.P) || !P::A(l.R)) break;
+    k0 = k;
+  }
+  if (k0 == N) return GASA_OK;
+  const int ctas = grid_tail_ctas<T>(S, 2);
+  if (ctas <= 0) return GASA_OK;
+  if (!ctx->grid_bar) ST(dalloc(ctx, &ctx->grid_bar, 1));
+  GridPlan<T> h;
+  h.k0 = k0;
+  h.nlev = N - k0;
+  h.tpre = ctx->opt.t_pre;
+  h.tpost = ctx->opt.t_post;
+  h.s = S;
+  h.nc = ctx->nc;
+  h.cinv = ctx->coarse_inv;
+  h.bN = P::b(lc);
+  h.xN = P::x(lc);
+  h.bar = ctx->grid_bar;
+  h.err = ctx->d_err;
+  const double budget = ctx->opt.wait_budget_s > 0.0 ? ctx->opt.wait_budget_s : 1.0;
+  h.budget_ns = (unsigned long long)(budget * 1e9) + 1ull;
+  for (int q = 0; q < h.nlev; ++q) {
+    Level &l = ctx->L[k0 + q];
+    GridLevel<T> &g = h.lv[q];
+    g.n = l.n;
+    g.n_next = ctx->L[k0 + q + 1].n;
+    g.arp = l.A.rp;
+    g.acol = l.A.col;
+    g.aval = P::A(l.A);
+    g.W = P::W(l);
+    g.prp = l.P.rp;
+    g.pcol = l.P.col;
+    g.pval = P::A(l.P);
+    g.rrp = l.R.rp;
+    g.rcol = l.R.col;
+    g.rval = P::A(l.R);
+    g.x = P::x(l);
+    g.x2 = P::x2(l);
+    g.b = P::b(l);
+    g.r = P::r(l);
+    g.tlA = grid_team(S, (double)l.A.nnzb / (double)l.n);
+    g.tlP = grid_team(S, (double)l.P.nnzb / (double)l.P.nrows);
+    g.tlR = grid_team(S, (double)l.R.nnzb / (double)l.R.nrows);
+  }
+  GridPlan<T> *dplan = nullptr;
+  ST(dalloc(ctx, &dplan, 1));
+  CU(cudaMemcpy(dplan, &h, sizeof(h), cudaMemcpyHostToDevice));
+  ctx->grid_plan[pi] = dplan;
+  ctx->grid_k0[pi] = k0;
+  ctx->grid_ctas[pi] = ctas;
+  ctx->grid_s[pi] = S;
+  return GASA_OK;
+}
+
 // The FP32 V-cycle's first level-0 step reads the FP64 right-hand side r
 // itself and leaves its FP32 rounding in b32 (the conversion then needs no
 // launch of its own; same bits).  Folding the conversion of z and the dot
@@ -388,7 +469,9 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false,
   cudaStream_t s = ctx->stream;
   const int N = ctx->N;
   const int pi = std::is_same<T, float>::value ? 1 : 0;
-  const int kt = ctx->tail_plan[pi] ? ctx->tail_k0[pi] : N;   // first fused level
+  const bool grid = ctx->grid_plan[pi] != nullptr;
+  // first level of the fused bottom (persistent grid launch, else cluster launch)
+  const int kt = grid ? ctx->grid_k0[pi] : (ctx->tail_plan[pi] ? ctx->tail_k0[pi] : N);
   const int tpre = ctx->opt.t_pre, tpost = ctx->opt.t_post;
   const int w = (int)sizeof(T);
   // level-0 smoothing step and residual; with h16 (FP32 V-cycle only) the
@@ -467,7 +550,13 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false,
                         P::r(l), nullptr, P::b(ctx->L[k + 1]), s, l.R.nnzb));
   }
   Level &lc = ctx->L[N];
-  if (kt < N) {
+  if (kt < N && grid) {
+    // levels kt .. N-1 and the coarsest solve (FP64 arithmetic) in one
+    // persistent launch; it leaves the corrected x_kt in L[kt]'s x
+    CU(launch_grid_tail<T>(static_cast<const GridPlan<T> *>(ctx->grid_plan[pi]), ctx->grid_s[pi],
+                           ctx->grid_ctas[pi], ctx->grid_bar, s));
+    xk[kt] = P::x(ctx->L[kt]);
+  } else if (kt < N) {
     // levels kt .. N-1 and the coarsest solve (FP64 arithmetic) in one
     // cluster launch; it leaves the corrected x_kt in L[kt]'s x
     const TailPlan<T> *pl = static_cast<const TailPlan<T> *>(ctx->tail_plan[pi]);
@@ -531,6 +620,18 @@ gasa_status apply_M_cg(gasa_ctx *ctx, const double *rr, double *z, const double 
 // scalar slots in ctx->scal
 enum { S_RR = 0, S_ALPHA = 1, S_PQ = 2, S_RZ0 = 3, S_RZ1 = 4, S_BB = 5, S_TMP = 6, S_G = 7,
        S_BETA = 8, S_BN = 9, S_TOL = 10, S_COUNT = 16 };
+
+// GASA_ERR_TIMEOUT (flag cleared) when a bounded device-side wait of the
+// last launches ran out, else GASA_OK; synchronises the context stream
+gasa_status check_wait_flag(gasa_ctx *ctx) {
+  int kerr = 0;
+  CU(cudaMemcpyAsync(&kerr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  if (!kerr) return GASA_OK;
+  CU(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return fail(ctx, GASA_ERR_TIMEOUT, "a bounded device-side wait ran out");
+}
 
 gasa_status read_scalars(gasa_ctx *ctx, int first, int count) {
   CU(cudaMemcpyAsync(ctx->hscal + first, ctx->scal + first, count * sizeof(double),
@@ -1627,6 +1728,8 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
   }
   ST(tail_build<double>(ctx, 0));
   ST(tail_build<float>(ctx, 1));
+  ST(grid_build<double>(ctx, 0));
+  ST(grid_build<float>(ctx, 1));
   CU(cudaStreamSynchronize(s));
   ctx->ready = true;
   ctx->setup_seconds =
@@ -1735,6 +1838,8 @@ void gasa_default_options(gasa_options *opt) {
   opt->hstar = 0;
   opt->delta = 1e-3;
   opt->tail_kib = 0;
+  opt->grid_tail = 0;
+  opt->wait_budget_s = 0.0;
 }
 
 gasa_status gasa_create(gasa_ctx **out, int32_t device, void *stream) {
@@ -1805,6 +1910,11 @@ gasa_status gasa_solve(gasa_ctx *ctx, const double *b, double *x, double tol, in
           ? stationary(ctx, bd, tol, precision, &iters, &rel, &conv)
           : (ctx->prof ? pcg(ctx, bd, tol, precision, &iters, &rel, &conv)
                        : pcg_graph(ctx, bd, tol, precision, &iters, &rel, &conv));
+  if (st != GASA_ERR_TIMEOUT) {
+    // a wait that ran out inside a V-cycle leaves its result unusable
+    const gasa_status wst = check_wait_flag(ctx);
+    if (wst != GASA_OK) st = wst;
+  }
   if (st == GASA_OK || st == GASA_ERR_NOT_SPD) {
     if (on_device) {
       CU(cudaMemcpyAsync(x, ctx->kx, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1831,8 +1941,7 @@ gasa_status gasa_vcycle(gasa_ctx *ctx, const double *r, double *z, int32_t preci
     return fail(ctx, GASA_ERR_INVALID_ARG, "unknown precision");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, GASA_ERR_CUDA, "cudaSetDevice");
   ST(apply_M(ctx, r, z, precision));
-  CU(cudaStreamSynchronize(ctx->stream));
-  return GASA_OK;
+  return check_wait_flag(ctx);
 }
 
 gasa_status gasa_level_shape(gasa_ctx *ctx, int32_t level, int64_t shape[8]) {
@@ -1857,6 +1966,12 @@ gasa_status gasa_tail_info(gasa_ctx *ctx, int32_t precision, int32_t out[3]) {
   if (precision < GASA_PREC_FP64 || precision > GASA_PREC_MIXED16)
     return fail(ctx, GASA_ERR_INVALID_ARG, "unknown precision");
   const int pi = precision == GASA_PREC_FP64 ? 0 : 1;
+  if (ctx->grid_plan[pi]) {
+    out[0] = ctx->grid_k0[pi];
+    out[1] = ctx->grid_ctas[pi];
+    out[2] = 1;
+    return GASA_OK;
+  }
   const bool on = ctx->tail_plan[pi] != nullptr;
   out[0] = on ? ctx->tail_k0[pi] : ctx->N;
   out[1] = on ? ctx->tail_cluster[pi] : 0;

@@ -55,6 +55,15 @@ long long launch_count();
 
 enum JacobiMode { JAC_SWEEP = 0, JAC_FIRST = 1, JAC_APPLY = 2, JAC_RELAX = 3 };
 
+// ---- kernels_wide.cu: FP32 blocks wider than 8, a team of warps per block row
+// true for blocks with more than 8 rows or columns (at most 64 rows) and at
+// least 8 blocks per block row on average
+bool wide_applies(int br, int bc, int n_brows, int64_t nnzb);
+// op: 0 y = A x, 1 y = b - A x, 2 y += A x, 3 y = x + W (b - A x) (square)
+cudaError_t launch_wide(int op, int n_brows, int br, int bc, int64_t nnzb, const int *rp,
+                        const int *col, const float *val, const float *W, const float *x,
+                        const float *b, float *y, cudaStream_t s);
+
 // ---- kernels_blk.cu: small square blocks, one lane per block ---------------
 // true when square s x s blocks (2 <= s <= 8) average at least 6 per block row;
 // launch_blk then takes FP32 operands (FP64 returns cudaErrorNotSupported)

@@ -197,6 +197,119 @@ bjacobi_kernel(int mode, int n, int bs, int rows_cta, const int *__restrict__ rp
   }
 }
 
+// ---------------------------------------------------------------------------
+// Level 0 of the FP16-block V-cycle over K columns: every stored block of A
+// and of w D^{-1} holds FP16 values v / s with one FP32 scale s per block.
+// Values are widened on load, each block's partial row sum is formed in
+// FP32 and joins the row by fma(s, partial, acc), in block order, as in the
+// single-solve FP16 kernels; every column is summed on its own.
+// ---------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ void row_dot_k_h16(int beg, int end, int r, int bs,
+                                              const int *__restrict__ col,
+                                              const __half *__restrict__ val,
+                                              const float *__restrict__ scale,
+                                              const float *__restrict__ X, float (&acc)[K]) {
+  for (int kb = beg; kb < end; ++kb) {
+    const int j = __ldg(col + kb);
+    const __half *a = val + ((size_t)kb * bs + r) * bs;
+    const float *x = X + (size_t)j * bs * K;
+    float part[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) part[c] = 0.f;
+    for (int q = 0; q < bs; ++q) {
+      const float av = __half2float(a[q]);
+      float xv[K];
+      load_k<float, K>(x + (size_t)q * K, xv);
+#pragma unroll
+      for (int c = 0; c < K; ++c) part[c] = fmaf(av, xv[c], part[c]);
+    }
+    const float sc = __ldg(scale + kb);
+#pragma unroll
+    for (int c = 0; c < K; ++c) acc[c] = fmaf(sc, part[c], acc[c]);
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads)
+bmv_h16_kernel(int mode, int64_t n_rows, int bs, const int *__restrict__ rp,
+               const int *__restrict__ col, const __half *__restrict__ val,
+               const float *__restrict__ scale, const float *__restrict__ X,
+               const float *__restrict__ B, float *__restrict__ Y) {
+  const int64_t row = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (row >= n_rows) return;
+  const int i = (int)(row / bs);
+  const int r = (int)(row - (int64_t)i * bs);
+  float acc[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) acc[c] = 0.f;
+  row_dot_k_h16<K>(__ldg(rp + i), __ldg(rp + i + 1), r, bs, col, val, scale, X, acc);
+  store_row<float, K>(mode, (size_t)row, acc, B, Y);
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads)
+bjacobi_h16_kernel(int mode, int n, int bs, int rows_cta, const int *__restrict__ rp,
+                   const int *__restrict__ col, const __half *__restrict__ A,
+                   const float *__restrict__ ascale, const __half *__restrict__ W,
+                   const float *__restrict__ wscale, const float *__restrict__ X,
+                   const float *__restrict__ B, float *__restrict__ Xo) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *res = reinterpret_cast<float *>(smem_raw);     // [rows_cta * bs][K]
+  const int i0 = blockIdx.x * rows_cta;
+  const int nrow = rows_cta * bs;
+  for (int t = threadIdx.x; t < nrow; t += blockDim.x) {
+    const int li = t / bs, r = t - li * bs;
+    const int i = i0 + li;
+    float v[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) v[c] = 0.f;
+    if (i < n) {
+      const size_t g = ((size_t)i * bs + r) * K;
+      if (mode == JAC_SWEEP) {
+        float acc[K];
+#pragma unroll
+        for (int c = 0; c < K; ++c) acc[c] = 0.f;
+        row_dot_k_h16<K>(__ldg(rp + i), __ldg(rp + i + 1), r, bs, col, A, ascale, X, acc);
+#pragma unroll
+        for (int c = 0; c < K; ++c) v[c] = B[g + c] - acc[c];
+      } else {
+#pragma unroll
+        for (int c = 0; c < K; ++c) v[c] = B[g + c];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < K; ++c) res[(size_t)t * K + c] = v[c];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nrow; t += blockDim.x) {
+    const int li = t / bs, r = t - li * bs;
+    const int i = i0 + li;
+    if (i >= n) continue;
+    const __half *w = W + ((size_t)i * bs + r) * bs;
+    const float *rl = res + (size_t)li * bs * K;
+    float out[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) out[c] = 0.f;
+    for (int q = 0; q < bs; ++q) {
+      const float wv = __half2float(w[q]);
+#pragma unroll
+      for (int c = 0; c < K; ++c) out[c] = fmaf(wv, rl[q * K + c], out[c]);
+    }
+    const float ws = __ldg(wscale + i);
+    const size_t g = ((size_t)i * bs + r) * K;
+    // explicit roundings: a multiply and add the compiler could fuse in some
+    // instantiations of K and not in others would make a column's bits
+    // depend on the batch width
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      float o = __fmul_rn(out[c], ws);
+      if (mode == JAC_SWEEP) o = __fadd_rn(o, X[g + c]);
+      Xo[g + c] = o;
+    }
+  }
+}
+
 // coarsest level: X = A^{-1} B with the FP64 inverse, FP64 accumulation
 template <typename T, int K>
 __global__ void __launch_bounds__(kThreads)
@@ -677,6 +790,31 @@ cudaError_t launch_bjacobi(int mode, int n, int bs, const int *rp, const int *co
     GASA_KSWITCH(K, launch_k(bjacobi_kernel<T, KK, false>, div_up(n, rows_cta), kThreads, smem, s,
                              mode, n, bs, rows_cta, rp, col, A, W, X, B, Xo));
   }
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bmv_h16(int mode, int n_brows, int bs, const int *rp, const int *col,
+                           const __half *val, const float *scale, const float *X, const float *B,
+                           float *Y, int K, cudaStream_t s) {
+  const int64_t rows = (int64_t)n_brows * bs;
+  if (rows == 0) return cudaSuccess;
+  GASA_KSWITCH(K, launch_k(bmv_h16_kernel<KK>, div_up(rows, kThreads), kThreads, 0, s, mode, rows,
+                           bs, rp, col, val, scale, X, B, Y));
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bjacobi_h16(int mode, int n, int bs, const int *rp, const int *col,
+                               const __half *A, const float *ascale, const __half *W,
+                               const float *wscale, const float *X, const float *B, float *Xo,
+                               int K, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int rows_cta = std::max(1, kThreads / bs);
+  const size_t smem = (size_t)rows_cta * bs * K * sizeof(float);
+  if (smem > 48 * 1024) return cudaErrorInvalidValue;
+  GASA_KSWITCH(K, launch_k(bjacobi_h16_kernel<KK>, div_up(n, rows_cta), kThreads, smem, s, mode,
+                           n, bs, rows_cta, rp, col, A, ascale, W, wscale, X, B, Xo));
   note_launch();
   return cudaGetLastError();
 }

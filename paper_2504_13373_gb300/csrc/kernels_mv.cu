@@ -9,6 +9,8 @@
 // cover whole 32-byte sectors and every matrix byte crosses HBM once per
 // pass.  The block-Jacobi step additionally exchanges the block row's
 // residual through shared memory and applies the precomputed w D^{-1}.
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -284,6 +286,13 @@ cudaError_t launch_bsr_mv(int mode, int n_brows, int br, int bc, const int *rp, 
   if (br == bc && mode >= GASA_MV_ASSIGN && mode <= GASA_MV_ADD && blk_applies(br, n_brows, nnzb)) {
     const cudaError_t e = launch_blk<T>(mode, n_brows, br, nnzb, rp, col, val, nullptr, x, b, y, s);
     if (e != cudaErrorNotSupported) return e;
+  }
+  if constexpr (std::is_same<T, float>::value) {
+    if (mode >= GASA_MV_ASSIGN && mode <= GASA_MV_ADD && wide_applies(br, bc, n_brows, nnzb)) {
+      const int op = mode == GASA_MV_ASSIGN ? 0 : mode == GASA_MV_RESIDUAL ? 1 : 2;
+      const cudaError_t e = launch_wide(op, n_brows, br, bc, nnzb, rp, col, val, nullptr, x, b, y, s);
+      if (e != cudaErrorNotSupported) return e;
+    }
   }
   if (n_brows > 0 && warp_rows(n_brows, br, nnzb)) {
     switch (mode) {
@@ -745,6 +754,12 @@ cudaError_t launch_jacobi(int mode, int n_units, int bs, const int *rp, const in
   if (mode == JAC_SWEEP && blk_applies(bs, n_units, nnzb)) {
     const cudaError_t e = launch_blk<T>(3, n_units, bs, nnzb, rp, col, val, W, x, b, xo, s);
     if (e != cudaErrorNotSupported) return e;
+  }
+  if constexpr (std::is_same<T, float>::value) {
+    if (mode == JAC_SWEEP && wide_applies(bs, bs, n_units, nnzb)) {
+      const cudaError_t e = launch_wide(3, n_units, bs, bs, nnzb, rp, col, val, W, x, b, xo, s);
+      if (e != cudaErrorNotSupported) return e;
+    }
   }
   if (n_units > 0 && mode != JAC_FIRST && warp_rows(n_units, bs, nnzb)) {
     switch (mode) {

@@ -26,6 +26,7 @@
 #include <deque>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -271,6 +272,12 @@ cudaError_t bsweep(Engine &e, int k, int mode, const T *x, const T *b, T *xo) {
                           e.K, e.s, 0));
     return launch_add<T>(l.ndof * e.K, x, xo, e.s);
   }
+  if constexpr (std::is_same<T, float>::value) {
+    // FP16-block engines read level 0's A and w D^-1 from their FP16 blocks
+    if (k == 0 && e.prec == GASA_PREC_MIXED16 && l.A.val16 && l.W16)
+      return launch_bjacobi_h16(mode, l.n, l.s, l.A.rp, l.A.col, l.A.val16, l.A.scale16, l.W16,
+                                l.W16s, x, b, xo, e.K, e.s);
+  }
   return launch_bjacobi<T>(mode, l.n, l.s, l.A.rp, l.A.col, P::A(l.A), P::W(l), x, b, xo, e.K,
                            e.s, l.A.nnzb);
 }
@@ -280,6 +287,11 @@ cudaError_t bresid(Engine &e, int k, const T *x, const T *b, T *r) {
   using P = EP<T>;
   Level &l = e.ctx->L[k];
   if (l.mf) return bmf_apply<T>(e, k, GASA_MV_RESIDUAL, x, b, r);
+  if constexpr (std::is_same<T, float>::value) {
+    if (k == 0 && e.prec == GASA_PREC_MIXED16 && l.A.val16)
+      return launch_bmv_h16(GASA_MV_RESIDUAL, l.n, l.s, l.A.rp, l.A.col, l.A.val16, l.A.scale16, x,
+                            b, r, e.K, e.s);
+  }
   return launch_bmv<T>(GASA_MV_RESIDUAL, l.n, l.s, l.s, l.A.rp, l.A.col, P::A(l.A), x, b, r, e.K,
                        e.s, l.A.nnzb);
 }
@@ -890,7 +902,7 @@ gasa_status gasa_server_add_mesh(gasa_server *srv, gasa_ctx *ctx, int32_t *mesh_
 gasa_status gasa_server_submit(gasa_server *srv, int32_t mesh_id, const double *b, double tol,
                                int32_t precision, uint64_t *ticket) {
   if (!srv || !b || !ticket || !(tol > 0.0)) return GASA_ERR_INVALID_ARG;
-  if (precision != GASA_PREC_FP64 && precision != GASA_PREC_MIXED32) return GASA_ERR_UNSUPPORTED;
+  if (precision < GASA_PREC_FP64 || precision > GASA_PREC_MIXED16) return GASA_ERR_INVALID_ARG;
   Request *rq = new Request();
   gasa_ctx *ctx = nullptr;
   {

@@ -70,7 +70,8 @@ class gasa_options(ctypes.Structure):
                 ("keep_setup_data", c_i32), ("gamma", c_dbl), ("omega_factor", c_dbl),
                 ("n_cut", c_dbl), ("seed", ctypes.c_uint64), ("init_candidates", c_vp),
                 ("bulk_staging", c_i32), ("matrix_free_levels", c_i32), ("hstar", c_i32),
-                ("delta", c_dbl), ("tail_kib", c_i32)]
+                ("delta", c_dbl), ("tail_kib", c_i32), ("grid_tail", c_i32),
+                ("wait_budget_s", c_dbl)]
 
 
 class gasa_setup_info(ctypes.Structure):

@@ -45,6 +45,13 @@ def _setup(gasa, pr, keep=True, solver=0):
     return ctx, info
 
 
+@functools.lru_cache(maxsize=None)
+def _bench_oracle():
+    pr = _bench_problem()
+    A = pr.A
+    return O.setup(A.row_ptr, A.col, A.val, pr.agg_of, B0=pr.B0, r=pr.r, dim=2)
+
+
 def _sparse_rel(G, Ref):
     D = (G - Ref).tocsr()
     return (np.max(np.abs(D.data)) if D.nnz else 0.0) / np.max(np.abs(Ref.data))
@@ -159,3 +166,76 @@ def test_convdiff_q2_full_size_solves():
     pr = configs.convdiff2d_q2(peclet=100.0)
     info, res = _solve_properties(gasa, pr, gasa.GASA_SOLVER_GMRES)
     assert info.dofs[0] == 2359296
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("grid_tail", [0, 1])
+def test_benchmark_workload_vcycle_matches_oracle(grid_tail):
+    """One V-cycle of the full benchmark workload (9 levels) in FP64, FP32 and
+    FP16-block precision, element by element against the oracle's V-cycle
+    (Alg. 2) built from the oracle's own hierarchy, with the kernels the
+    benchmark launches (thread-per-row level 0, lane-team coarse levels, or
+    the persistent coarse launch).  Bars as for the small workloads: FP64
+    within the hierarchy tolerance, FP32 and FP16 within 1e-4 of the
+    oracle's emulation, FP16 within 1e-2 of FP64."""
+    from tests.test_gpu_solver import level_tolerances
+    gasa = _gasa()
+    pr = _bench_problem()
+    H = _bench_oracle()
+    A = pr.A
+    ctx = gasa.gasa_create(0)
+    try:
+        opt = gasa.gasa_default_options(dim=2, n_cand=pr.r, keep_setup_data=0, max_iter=20000,
+                                        grid_tail=grid_tail)
+        gasa.gasa_setup(ctx, A.row_ptr, A.col, A.val.ravel(), A.b, pr.agg_of, opt,
+                        adj_ptr=pr.adj_ptr, adj_idx=pr.adj_idx, centroids=pr.centroids,
+                        init_candidates=pr.B0)
+        assert (gasa.gasa_tail_info(ctx, gasa.GASA_PREC_MIXED32)["first_level"] == 1) == bool(grid_tail)
+        import torch
+        r = torch.from_numpy(pr.rhs).cuda()
+        z = torch.zeros_like(r)
+        want = O.make_vcycle(H, "fp64")(pr.rhs)
+        gasa.gasa_vcycle(ctx, r, z, gasa.GASA_PREC_FP64)
+        assert rel_err(z.cpu().numpy(), want) <= 0.1 * level_tolerances(H)[-1]
+        wantf = O.make_vcycle(H, "fp32")(pr.rhs)
+        gasa.gasa_vcycle(ctx, r, z, gasa.GASA_PREC_MIXED32)
+        zf = z.cpu().numpy()
+        assert rel_err(zf, wantf) <= 1e-4 and rel_err(zf, want) <= 1e-4
+        wanth = O.make_vcycle(H, "fp16")(pr.rhs)
+        gasa.gasa_vcycle(ctx, r, z, gasa.GASA_PREC_MIXED16)
+        zh = z.cpu().numpy()
+        assert rel_err(zh, wanth) <= 1e-4 and rel_err(zh, want) <= 1e-2
+    finally:
+        gasa.gasa_destroy(ctx)
+
+
+@pytest.mark.slow
+def test_benchmark_workload_solves_match_the_oracle_record():
+    """The full benchmark solves against the oracle's own solves of the same
+    workload (tests/golden/c2_oracle_solve.json, written by
+    make_c2_oracle_solve.py: about an hour of oracle time per precision).
+    Iteration counts within 1 of the oracle's (FP64 against FP64, mixed
+    against mixed), and each solution within 1e-10 relative of the oracle's
+    FP64 solution over the record's 4,096 sampled dofs (a sample estimate of
+    ||x - x_oracle|| / ||x_oracle||; the oracle's own FP64 and mixed solutions
+    differ by 3.7e-11)."""
+    import json
+    import os
+    rec = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c2_oracle_solve.json")))
+    gasa = _gasa()
+    pr = _bench_problem()
+    assert rec["dofs"] == pr.n_dofs
+    idx = np.asarray(rec["sample_index"], dtype=np.int64)
+    xo = np.asarray(rec["fp64"]["x_sample"])
+    ctx, info = _setup(gasa, pr, keep=False)
+    try:
+        assert [info.dofs[k] for k in range(info.n_levels)] == rec["level_dofs"]
+        for prec, key in ((gasa.GASA_PREC_FP64, "fp64"), (gasa.GASA_PREC_MIXED32, "mixed32")):
+            x = np.zeros_like(pr.rhs)
+            si = gasa.gasa_solve(ctx, pr.rhs, x, TOL, prec)
+            assert si.converged and si.rel_residual <= TOL
+            assert abs(si.iterations - rec[key]["iterations"]) <= 1, (key, si.iterations)
+            err = np.linalg.norm(x[idx] - xo) / np.linalg.norm(xo)
+            assert err <= TOL, (key, err)
+    finally:
+        gasa.gasa_destroy(ctx)

@@ -318,3 +318,58 @@ def test_dense_inverse(n):
     assert sing == 0
     X = to_host(Ainv).reshape(n, n)
     assert np.max(np.abs(X @ M - np.eye(n))) <= 1e-12
+
+
+# FP32 blocks wider than 8 with >= 8 blocks per block row take the team-of-warps
+# kernel (kernels_wide.cu): lane groups of br lanes (2 groups for 13 rows, 1 for
+# 17..32, two rows per lane beyond 32), 1 to 8 warps per block row by the row
+# length, rectangular restriction- and prolongation-shaped blocks
+CASES_WIDE = [
+    # (n_rows, n_cols, br, bc, per_row, seed)
+    (100, 300, 5, 10, 24, 51),
+    (64, 64, 36, 36, 16, 52),
+    (50, 40, 13, 17, 30, 53),
+    (33, 900, 4, 10, 70, 54),
+    (40, 40, 16, 16, 12, 55),
+    (20, 20, 32, 32, 11, 56),
+    (301, 301, 12, 12, 19, 57),
+    (80, 80, 22, 22, 100, 58),
+    (131, 600, 13, 10, 9, 59),
+    (60, 60, 40, 40, 10, 60),
+    (2003, 2003, 9, 9, 10, 61),
+]
+
+
+@pytest.mark.parametrize("case", CASES_WIDE)
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_bsr_mv_fp32_wide_blocks(case, mode):
+    gasa = _gasa()
+    n, m, br, bc, per, seed = case
+    ptr, col, val = RO.random_bsr(n, m, br, bc, per, seed)
+    assert ptr[-1] >= 8 * n
+    x = RO.random_vector(m * bc, seed)
+    b = RO.random_vector(n * br, seed, stream=120)
+    y0 = RO.random_vector(n * br, seed, stream=121)
+    Ax = bsr_scipy(ptr, col, val, m) @ x
+    want = {0: Ax, 1: b - Ax, 2: y0 + Ax}[mode]
+    y = to_dev(y0.astype(np.float32))
+    f = np.float32
+    gasa.gasa_bsr_mv_f32(mode, n, br, bc, to_dev(ptr), to_dev(col), to_dev(val.ravel().astype(f)),
+                         to_dev(x.astype(f)), to_dev(b.astype(f)), y)
+    assert rel_err(to_host(y), want) <= TOL32
+
+
+@pytest.mark.parametrize("n,bs,seed,per_row", [(301, 12, 71, 19), (80, 22, 72, 100), (64, 36, 73, 16),
+                                               (60, 40, 74, 10), (2003, 9, 75, 10), (129, 13, 76, 40)])
+def test_jacobi_sweep_fp32_wide_blocks(n, bs, seed, per_row):
+    gasa = _gasa()
+    ptr, col, val, W, x, b = _jacobi_inputs(n, bs, seed, per_row)
+    assert ptr[-1] >= 8 * n
+    A = bsr_scipy(ptr, col, val)
+    want = O.smooth_step(x, A, O.BlockDiag(np.arange(n + 1) * bs, W), b)
+    out = to_dev(np.zeros(n * bs, np.float32))
+    f = np.float32
+    gasa.gasa_jacobi_sweep_f32(n, bs, to_dev(ptr), to_dev(col), to_dev(val.ravel().astype(f)),
+                               to_dev(W.ravel().astype(f)), to_dev(x.astype(f)), to_dev(b.astype(f)), out)
+    scale = np.max(np.abs(want))
+    assert np.max(np.abs(to_host(out) - want)) / scale <= 1e-4

@@ -41,12 +41,14 @@ def test_served_solve_matches_oracle(name):
     H = oracle_setup(name)
     ref = O.solve(H, pr.rhs, TOL, pr.solver, restart=30, max_iter=5000)
     ref32 = O.solve(H, pr.rhs, TOL, pr.solver, precision="mixed32", restart=30, max_iter=5000)
+    ref16 = O.solve(H, pr.rhs, TOL, pr.solver, precision="mixed16", restart=30, max_iter=5000)
     ctx, _ = gpu_setup(name, keep=False)
     srv = gasa.gasa_server_create(0, 8 << 30, 8)
     try:
         mid = gasa.gasa_server_add_mesh(srv, ctx)
         t64 = gasa.gasa_server_submit(srv, mid, pr.rhs, TOL, gasa.GASA_PREC_FP64)
         t32 = gasa.gasa_server_submit(srv, mid, pr.rhs, TOL, gasa.GASA_PREC_MIXED32)
+        t16 = gasa.gasa_server_submit(srv, mid, pr.rhs, TOL, gasa.GASA_PREC_MIXED16)
         gasa.gasa_server_drain(srv, 300.0)
         x, info = _finish(gasa, srv, t64, pr.n_dofs)
         assert abs(info.iterations - ref.iterations) <= 1, (info.iterations, ref.iterations)
@@ -55,6 +57,10 @@ def test_served_solve_matches_oracle(name):
         assert abs(info32.iterations - ref32.iterations) <= 1, (info32.iterations, ref32.iterations)
         A = pr.A.to_scipy()
         assert np.linalg.norm(pr.rhs - A @ xm) / np.linalg.norm(pr.rhs) <= TOL
+        # FP16-block level 0: the oracle's FP16 emulation of the same storage
+        xh, info16 = _finish(gasa, srv, t16, pr.n_dofs)
+        assert abs(info16.iterations - ref16.iterations) <= 1, (info16.iterations, ref16.iterations)
+        assert np.linalg.norm(pr.rhs - A @ xh) / np.linalg.norm(pr.rhs) <= TOL
     finally:
         gasa.gasa_server_destroy(srv)
         gasa.gasa_destroy(ctx)
@@ -107,7 +113,7 @@ def _mix(gasa, ctxs, max_batch, jobs, budget=16 << 30, pause=0.002):
 
 def _jobs(gasa, idx):
     jobs = [(name, prec, i) for i in idx for name in MIX
-            for prec in (gasa.GASA_PREC_FP64, gasa.GASA_PREC_MIXED32)]
+            for prec in (gasa.GASA_PREC_FP64, gasa.GASA_PREC_MIXED32, gasa.GASA_PREC_MIXED16)]
     order = np.argsort(serving.request_mesh(configs.SEED, len(jobs), 997), kind="stable")
     return [jobs[k] for k in order]
 
@@ -185,8 +191,8 @@ def test_server_requests_validated():
         mid = gasa.gasa_server_add_mesh(srv, ctx)
         n = problem("tiny").n_dofs
         with pytest.raises(gasa.GasaError) as ei:
-            gasa.gasa_server_submit(srv, mid, np.ones(n), TOL, gasa.GASA_PREC_MIXED16)
-        assert ei.value.status == gasa.GASA_ERR_UNSUPPORTED
+            gasa.gasa_server_submit(srv, mid, np.ones(n), TOL, 7)     # no such precision
+        assert ei.value.status == gasa.GASA_ERR_INVALID_ARG
         with pytest.raises(gasa.GasaError):
             gasa.gasa_server_submit(srv, mid + 1, np.ones(n), TOL, gasa.GASA_PREC_FP64)
         with pytest.raises(gasa.GasaError):

@@ -498,3 +498,97 @@ def test_fused_tail(name):
     finally:
         gasa.gasa_destroy(ctx_f)
         gasa.gasa_destroy(ctx_s)
+
+
+@pytest.mark.parametrize("name", ["c1", "p3_16", "p3_32", "uneq6", "tet_p2_6", "cd_q2_16"])
+def test_grid_tail(name):
+    """The coarse levels as one persistent cooperative launch (grid_tail = 1)
+    against one launch per step: the range starts at the first level from
+    which every level is unpadded with one block size s <= 8 (none for the
+    P2 tets and the Q2 quads, whose coarse blocks are larger); where it runs,
+    V-cycles agree with the per-step launches to rounding (1e-12 FP64,
+    1e-5 FP32), follow the oracle's V-cycle, repeat bit for bit, and drive
+    CG solves of the same iteration count (+-1)."""
+    gasa = _gasa()
+    H = oracle_setup(name)
+    pr = problem(name)
+    n_levels = len(H.levels)
+    sizes = [int(L.unit_ptr[1] - L.unit_ptr[0]) for L in H.levels]
+    uniform = [all(np.all(np.diff(H.levels[j].unit_ptr) == sizes[k]) for j in range(k, n_levels))
+               for k in range(n_levels)]
+    expect = n_levels - 1
+    for k in range(n_levels - 2, 0, -1):
+        if sizes[k] <= 8 and all(sizes[j] == sizes[k] for j in range(k, n_levels)) and uniform[k]:
+            expect = k
+        else:
+            break
+    ctx_g, _ = gpu_setup(name, keep=False, grid_tail=1)
+    ctx_s, _ = gpu_setup(name, keep=False, grid_tail=0)
+    try:
+        for prec, oprec, tol in ((gasa.GASA_PREC_FP64, "fp64", 1e-12),
+                                 (gasa.GASA_PREC_MIXED32, "fp32", 1e-5)):
+            tg = gasa.gasa_tail_info(ctx_g, prec)
+            assert tg["first_level"] == expect, (tg, expect, sizes)
+            if expect == n_levels - 1:
+                assert tg == {"first_level": n_levels - 1, "cluster": 0, "coarse_inside": 0}
+                continue
+            assert tg["cluster"] > 0 and tg["cluster"] % 152 == 0 and tg["coarse_inside"] == 1
+            want = O.make_vcycle(H, oprec)(pr.rhs)
+            r = to_dev(pr.rhs)
+            zg, zs = to_dev(np.zeros_like(pr.rhs)), to_dev(np.zeros_like(pr.rhs))
+            gasa.gasa_vcycle(ctx_g, r, zg, prec)
+            gasa.gasa_vcycle(ctx_s, r, zs, prec)
+            zg, zs = to_host(zg), to_host(zs)
+            assert rel_err(zg, zs) <= tol
+            assert rel_err(zg, want) <= max(tol, 0.1 * level_tolerances(H)[-1])
+            z2 = to_dev(np.zeros_like(pr.rhs))
+            gasa.gasa_vcycle(ctx_g, r, z2, prec)
+            assert np.array_equal(to_host(z2), zg)
+        if pr.solver == "cg" and expect < n_levels - 1:
+            for prec in (gasa.GASA_PREC_FP64, gasa.GASA_PREC_MIXED32, gasa.GASA_PREC_MIXED16):
+                xg, xs = np.zeros_like(pr.rhs), np.zeros_like(pr.rhs)
+                inf_g = gasa.gasa_solve(ctx_g, pr.rhs, xg, TOL, prec)
+                inf_s = gasa.gasa_solve(ctx_s, pr.rhs, xs, TOL, prec)
+                assert inf_g.converged and inf_g.rel_residual <= TOL
+                assert abs(inf_g.iterations - inf_s.iterations) <= 1
+                assert np.linalg.norm(xg - xs) / np.linalg.norm(xs) <= 10 * TOL
+                # the graph-resident loop and the host-driven one agree bit for bit
+                gasa.gasa_profile_enable(ctx_g, True)
+                xh = np.zeros_like(pr.rhs)
+                inf_h = gasa.gasa_solve(ctx_g, pr.rhs, xh, TOL, prec)
+                gasa.gasa_profile_enable(ctx_g, False)
+                assert inf_h.iterations == inf_g.iterations and np.array_equal(xh, xg)
+    finally:
+        gasa.gasa_destroy(ctx_g)
+        gasa.gasa_destroy(ctx_s)
+
+
+def test_grid_tail_wait_budget_runs_out():
+    """With a 1 ns budget the persistent launch's grid barriers run out: the
+    launch ends early and sets the error flag, gasa_vcycle and gasa_solve
+    return GASA_ERR_TIMEOUT (the GPU stays usable), and the same context
+    then solves normally once it is set up with the default budget."""
+    gasa = _gasa()
+    pr = problem("p3_16")
+    ctx, _ = gpu_setup("p3_16", keep=False, grid_tail=1, wait_budget_s=1e-9)
+    try:
+        assert gasa.gasa_tail_info(ctx, gasa.GASA_PREC_MIXED32)["coarse_inside"] == 1
+        r = to_dev(pr.rhs)
+        z = to_dev(np.zeros_like(pr.rhs))
+        for prec in (gasa.GASA_PREC_MIXED32, gasa.GASA_PREC_FP64):
+            with pytest.raises(gasa.GasaError) as ei:
+                gasa.gasa_vcycle(ctx, r, z, prec)
+            assert ei.value.status == gasa.GASA_ERR_TIMEOUT
+            x = np.zeros_like(pr.rhs)
+            with pytest.raises(gasa.GasaError) as ei:
+                gasa.gasa_solve(ctx, pr.rhs, x, TOL, prec)
+            assert ei.value.status == gasa.GASA_ERR_TIMEOUT
+    finally:
+        gasa.gasa_destroy(ctx)
+    ctx, _ = gpu_setup("p3_16", keep=False, grid_tail=1)
+    try:
+        x = np.zeros_like(pr.rhs)
+        info = gasa.gasa_solve(ctx, pr.rhs, x, TOL, gasa.GASA_PREC_MIXED32)
+        assert info.converged and info.rel_residual <= TOL
+    finally:
+        gasa.gasa_destroy(ctx)
