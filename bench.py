@@ -70,6 +70,9 @@ def parse():
                     help="with --profile-run: drive the CG loop from the host (per-kernel ncu)")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="with --profile-run: stop each solve after this many CG iterations")
+    ap.add_argument("--fused-restriction", type=int, default=-1, choices=[-1, 0, 1],
+                    help="residual and restriction fused through R A (1) or as two steps (0); "
+                         "-1: the library default")
     ap.add_argument("--grid-tail", type=int, default=-1, choices=[-1, 0, 1],
                     help="coarse levels as one persistent launch (1) or one launch per step (0); "
                          "-1: the library default")
@@ -121,7 +124,33 @@ def hbm_peak():
 # algorithmic bytes of one preconditioned CG iteration (whole-iteration roofline)
 # ----------------------------------------------------------------------------
 def level_shapes(gasa, ctx, n_levels):
-    return [gasa.gasa_level_shape(ctx, k) for k in range(n_levels)]
+    """gasa_level_shape per level, plus RA_nnzb: the blocks of R_k A_k where the
+    fused restriction keeps it (0 elsewhere)."""
+    shapes = []
+    for k in range(n_levels):
+        sh = dict(gasa.gasa_level_shape(ctx, k))
+        sh["RA_nnzb"] = 0
+        if k < n_levels - 1:
+            n_next = gasa.gasa_level_shape(ctx, k + 1)["units"]
+            try:
+                rp = gasa.gasa_get_level(ctx, k, gasa.GASA_LV_RA_ROWPTR, np.zeros(n_next + 1, np.int32))
+                sh["RA_nnzb"] = int(rp[-1])
+            except gasa.GasaError:
+                pass
+        shapes.append(sh)
+    return shapes
+
+
+def _fused_first(s_next, s, n_next, nnzb, w):
+    """whether the FP32 fused restriction also takes the next level's first
+    smoothing step: the lane-team kernel (square blocks of 2..8 with >= 6
+    blocks of R and R A per row) or the wide-block kernel (> 8 rows or
+    columns, at most 40, >= 8 per row)"""
+    if w != 4:
+        return False
+    if s_next == s and 2 <= s <= 8 and nnzb >= 6 * n_next:
+        return True
+    return (s_next > 8 or s > 8) and s_next <= 40 and s <= 40 and nnzb >= 8 * n_next
 
 
 def iteration_bytes(shapes, precision, t_pre=3, t_post=3):
@@ -139,6 +168,7 @@ def iteration_bytes(shapes, precision, t_pre=3, t_post=3):
     w = 8 if precision == "fp64" else 4
     parts = {}
     n0 = shapes[0]["units"] * shapes[0]["s"]
+    first_done = [False] * (N + 1)
     for k in range(N):
         sh = shapes[k]
         n, s, nnzb = sh["units"], sh["s"], sh["nnzb"]
@@ -154,9 +184,21 @@ def iteration_bytes(shapes, precision, t_pre=3, t_post=3):
         first = W + 2 * v
         if k == 0 and precision == "mixed32":
             first = W + n * s * (8 + 4 + 4)      # reads the FP64 residual, writes x and its FP32 copy
+        if first_done[k]:
+            first = 0.0                           # taken by the restriction of the level above
         sweeps = (t_pre - 1 + t_post) * (A + W + 3 * v)
-        resid = A + 3 * v
-        restrict = R + v + n1 * s1 * w
+        ra = sh.get("RA_nnzb", 0)
+        if ra and not (precision == "mixed16" and k == 0):
+            # fused: b_{k+1} = R b - (R A) x, maybe with level k+1's first step
+            RAb = ra * (s1 * s * w) + 4 * ra + 4 * (n1 + 1)
+            resid = 0.0
+            restrict = R + RAb + 2 * v + n1 * s1 * w
+            if k + 1 < N and _fused_first(s1, s, n1, sh["R_nnzb"] + ra, w):
+                restrict += n1 * s1 * s1 * w + n1 * s1 * w
+                first_done[k + 1] = True
+        else:
+            resid = A + 3 * v
+            restrict = R + v + n1 * s1 * w
         prolong = P + n1 * s1 * w + 2 * v
         parts[f"level{k}"] = first + sweeps + resid + restrict + prolong
     nc = shapes[N]["units"] * shapes[N]["s"]
@@ -625,6 +667,8 @@ def ours_main(args, rank, world, local):
         opt.max_iter = args.profile_iters
     if args.grid_tail >= 0:
         opt.grid_tail = args.grid_tail
+    if args.fused_restriction >= 0:
+        opt.fused_restriction = args.fused_restriction
     opt.bulk_staging = 1 if args.bulk_staging else 0
     sinfo = gasa.gasa_setup(ctx, A.row_ptr, A.col, A.val.ravel(), A.b, pr.agg_of, opt,
                             adj_ptr=pr.adj_ptr, adj_idx=pr.adj_idx, centroids=pr.centroids,

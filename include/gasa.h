@@ -133,6 +133,13 @@ typedef struct {
   double wait_budget_s;      /* budget of one launch's bounded device-side waits (grid barriers of
                                 the persistent coarse launch); a wait that runs out ends the launch
                                 and the solve returns GASA_ERR_TIMEOUT.  0 = 1 second. */
+  int32_t fused_restriction; /* 1 (default): setup also forms R_k A_k on every stored level where it
+                                holds no more values than A_k, and there the V-cycle restricts as
+                                b_{k+1} = R_k b_k - (R_k A_k) u_k, the same
+                                vector as R_k (b_k - A_k u_k) of Alg. 2, in one product that on
+                                the FP32 levels also takes level k+1's first smoothing step
+                                u_{k+1} = w D_{k+1}^{-1} b_{k+1}; results agree with the two-step
+                                form to rounding.  0: residual and restriction as two steps. */
 } gasa_options;
 
 typedef struct {
@@ -204,7 +211,10 @@ enum {
   GASA_LV_SWEEPS = 12,       /* int32 r: Eq. bsmooth sweeps per column */
   GASA_LV_COARSE_INV = 13,   /* coarsest level: dense A_N^{-1}, row-major */
   GASA_LV_CAND_IN = 14,      /* B^k before relaxation */
-  GASA_LV_SIZES = 15         /* int32 units: real dofs of each unit */
+  GASA_LV_SIZES = 15,        /* int32 units: real dofs of each unit */
+  GASA_LV_RA_ROWPTR = 16,    /* R_k A_k (option fused_restriction), next-level rows x level-k units */
+  GASA_LV_RA_COL = 17,
+  GASA_LV_RA_VAL = 18
 };
 /* shape[0..7] = units, s_k, nnzb(A), P nnzb, R nnzb, s_{k+1}, r, dofs.  On a
  * level whose aggregates keep different counts (h*-step, or unequal

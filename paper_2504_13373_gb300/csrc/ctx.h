@@ -44,6 +44,7 @@ struct Level {
   int *child_ptr = nullptr, *child_idx = nullptr;
   double *T = nullptr;
   DevBSR P, R;
+  DevBSR RA;                  // R_k A_k (fused residual + restriction), rows of level k+1
   double *cand = nullptr, *cand_in = nullptr;
   std::vector<int> sweeps;
   double omega = 0.0, rho = 0.0;

@@ -450,6 +450,59 @@ gasa_status grid_build(gasa_ctx *ctx, int pi) {
   return GASA_OK;
 }
 
+// Fused residual and restriction of Alg. 2 on level k: b_{k+1} = R_k b_k -
+// (R_k A_k) x_k, the vector R_k (b_k - A_k x_k) without the fine residual.
+// FP32 levels run it as one product (lane teams for s <= 8 square blocks,
+// the wide-block kernel beyond), which with Wn also takes level k+1's first
+// smoothing step xn = Wn b_{k+1}; *first_done tells whether it did.  Elsewhere
+// (FP64, or shapes neither kernel takes) it is two products, R b into tmp
+// and then tmp - (R A) x.
+template <typename T>
+cudaError_t restrict_fused(gasa_ctx *ctx, int k, const T *bk, const T *xk, T *bnext,
+                           const T *Wn, T *xn, T *tmp, bool *first_done) {
+  using P = Prec<T>;
+  cudaStream_t s = ctx->stream;
+  Level &l = ctx->L[k];
+  const DevBSR &R = l.R, &RA = l.RA;
+  *first_done = false;
+  if constexpr (std::is_same<T, float>::value) {
+    const int64_t nz = R.nnzb + RA.nnzb;
+    if (R.br == R.bc && blk_applies(R.br, R.nrows, nz)) {
+      const cudaError_t e = launch_blk_restrict(R.nrows, R.br, nz, R.rp, R.col, R.val32, RA.rp,
+                                                RA.col, RA.val32, bk, xk, bnext, Wn, xn, s);
+      if (e != cudaErrorNotSupported) {
+        *first_done = Wn != nullptr && e == cudaSuccess;
+        return e;
+      }
+    }
+    if (wide_applies(R.br, R.bc, R.nrows, nz)) {
+      const cudaError_t e = launch_wide_restrict(R.nrows, R.br, R.bc, nz, R.rp, R.col, R.val32,
+                                                 RA.rp, RA.col, RA.val32, bk, xk, bnext, Wn, xn, s);
+      if (e != cudaErrorNotSupported) {
+        *first_done = Wn != nullptr && e == cudaSuccess;
+        return e;
+      }
+    }
+  }
+  cudaError_t e = launch_bsr_mv<T>(GASA_MV_ASSIGN, R.nrows, R.br, R.bc, R.rp, R.col, P::A(R), bk,
+                                   nullptr, tmp, s, R.nnzb);
+  if (e != cudaSuccess) return e;
+  return launch_bsr_mv<T>(GASA_MV_RESIDUAL, RA.nrows, RA.br, RA.bc, RA.rp, RA.col, P::A(RA), xk,
+                          tmp, bnext, s, RA.nnzb);
+}
+
+// bytes of the fused restriction of level l (R, R A, b, x, b_{k+1}; with the
+// next level's first step also its W and x)
+double restrict_fused_bytes(const Level &l, int w, bool first) {
+  auto mat = [&](const DevBSR &m) {
+    return (double)m.nnzb * m.br * m.bc * w + 4.0 * m.nnzb + 4.0 * (m.nrows + 1);
+  };
+  const double vfine = (double)l.ndof * w, vc = (double)l.R.nrows * l.R.br * w;
+  double b = mat(l.R) + mat(l.RA) + 2.0 * vfine + vc;
+  if (first) b += (double)l.R.nrows * l.R.br * l.R.br * w + vc;
+  return b;
+}
+
 // The FP32 V-cycle's first level-0 step reads the FP64 right-hand side r
 // itself and leaves its FP32 rounding in b32 (the conversion then needs no
 // launch of its own; same bits).  Folding the conversion of z and the dot
@@ -515,6 +568,8 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false,
   std::vector<T *> xk(N + 1);
   bk[0] = rhs;
   for (int k = 1; k <= N; ++k) bk[k] = P::b(ctx->L[k]);
+  // levels whose first smoothing step the restriction of the level above took
+  std::vector<char> first_done(N + 1, 0);
   for (int k = 0; k < kt; ++k) {
     Level &l = ctx->L[k];
     T *x = P::x(l), *x2 = P::x2(l);
@@ -526,9 +581,9 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false,
       if (k == 0) prof_begin(ctx, 3, &e0);
       if constexpr (std::is_same<T, float>::value) {
         if (k == 0 && fe) CU(launch_jacobi_first_conv(l.n, l.s, fe->r, fe->b32, P::W(l), x, s));
-        else CU(sweep(k, JAC_FIRST, nullptr, bk[k], x));
+        else if (!first_done[k]) CU(sweep(k, JAC_FIRST, nullptr, bk[k], x));
       } else {
-        CU(sweep(k, JAC_FIRST, nullptr, bk[k], x));
+        if (!first_done[k]) CU(sweep(k, JAC_FIRST, nullptr, bk[k], x));
       }
       if (k == 0) prof_end(ctx, 3, sweep_bytes(l, w, true, wa));
       for (int t = 1; t < tpre; ++t) {
@@ -539,15 +594,28 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false,
       }
     }
     xk[k] = x;
-    // residual and restriction
-    {
+    // residual and restriction: fused as R b - (R A) x where R A is stored
+    // (the FP16-block level 0 keeps its own residual)
+    if (l.RA.rp && P::A(l.RA) && !(h16 && k == 0)) {
+      Level &ln = ctx->L[k + 1];
+      const bool take_first = tpre >= 1 && k + 1 < kt && k + 1 < N;
+      bool fd = false;
       cudaEvent_t e0;
       if (k == 0) prof_begin(ctx, 1, &e0);
-      CU(resid(k, x, bk[k], P::r(l)));
-      if (k == 0) prof_end(ctx, 1, spmv_bytes(l, w, true, wa));
+      CU(restrict_fused<T>(ctx, k, bk[k], x, P::b(ln), take_first ? P::W(ln) : nullptr,
+                           take_first ? P::x(ln) : nullptr, P::r(ln), &fd));
+      if (k == 0) prof_end(ctx, 1, restrict_fused_bytes(l, w, fd));
+      first_done[k + 1] = fd ? 1 : 0;
+    } else {
+      {
+        cudaEvent_t e0;
+        if (k == 0) prof_begin(ctx, 1, &e0);
+        CU(resid(k, x, bk[k], P::r(l)));
+        if (k == 0) prof_end(ctx, 1, spmv_bytes(l, w, true, wa));
+      }
+      CU(launch_bsr_mv<T>(GASA_MV_ASSIGN, l.R.nrows, l.R.br, l.R.bc, l.R.rp, l.R.col, P::A(l.R),
+                          P::r(l), nullptr, P::b(ctx->L[k + 1]), s, l.R.nnzb));
     }
-    CU(launch_bsr_mv<T>(GASA_MV_ASSIGN, l.R.nrows, l.R.br, l.R.bc, l.R.rp, l.R.col, P::A(l.R),
-                        P::r(l), nullptr, P::b(ctx->L[k + 1]), s, l.R.nnzb));
   }
   Level &lc = ctx->L[N];
   if (kt < N && grid) {
@@ -1117,8 +1185,11 @@ gasa_status upload_i32(gasa_ctx *ctx, int **d, const int32_t *h, size_t n) {
   return GASA_OK;
 }
 
-// symbolic + numeric C = A B on BSR patterns (fresh allocations in ctx)
-gasa_status spgemm(gasa_ctx *ctx, const DevBSR &A, const DevBSR &B, DevBSR &C) {
+// symbolic + numeric C = A B on BSR patterns (fresh allocations in ctx);
+// with max_values > 0, C is left empty (rp == nullptr) when it would hold
+// more than max_values scalars
+gasa_status spgemm(gasa_ctx *ctx, const DevBSR &A, const DevBSR &B, DevBSR &C,
+                   int64_t max_values = 0) {
   cudaStream_t s = ctx->stream;
   const int n = A.nrows;
   int *cand = nullptr, *mx = nullptr, *cnt = nullptr;
@@ -1142,6 +1213,14 @@ gasa_status spgemm(gasa_ctx *ctx, const DevBSR &A, const DevBSR &B, DevBSR &C) {
   int nnz = 0;
   CU(cudaMemcpyAsync(&nnz, C.rp + n, sizeof(int), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
+  if (max_values > 0 && (int64_t)nnz * C.br * C.bc > max_values) {
+    dfree(ctx, C.rp);
+    dfree(ctx, cand);
+    dfree(ctx, mx);
+    dfree(ctx, cnt);
+    C = DevBSR{};
+    return GASA_OK;
+  }
   C.nnzb = nnz;
   ST(dalloc(ctx, &C.col, (size_t)nnz));
   ST(dalloc(ctx, &C.val, (size_t)nnz * C.br * C.bc));
@@ -1624,10 +1703,16 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
       dfree(ctx, l.T);
       l.T = nullptr;
     }
+    // ---- R_k A_k for the fused restriction b_{k+1} = R b - (R A) u, kept
+    // where it holds no more values than A_k (then the fused product also
+    // moves fewer bytes than the residual and the restriction) ----
+    if (opt->fused_restriction)
+      ST(spgemm(ctx, l.R, l.A, l.RA, l.A.nnzb * (int64_t)l.s * l.s));
     // ---- FP32 copies for the mixed-precision V-cycle ----
     ST(make_f32(ctx, l.A));
     ST(make_f32(ctx, l.P));
     ST(make_f32(ctx, l.R));
+    if (l.RA.val) ST(make_f32(ctx, l.RA));
     if (k == 0) {
       // low FP32 words of A_0 for the double-single outer product
       ST(dalloc(ctx, &l.A.lo32, (size_t)l.A.nnzb * l.s * l.s));
@@ -1713,6 +1798,15 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
       l.A.rp = nullptr;
       l.A.col = nullptr;
       l.mf = true;
+      // a matrix-free level keeps no product with A_k either
+      if (l.RA.val) {
+        const int64_t nr = l.RA.nnzb;
+        ctx->device_bytes -= nr * l.RA.br * l.RA.bc * (int64_t)(sizeof(double) + sizeof(float)) +
+                             nr * (int64_t)sizeof(int) + (int64_t)(l.RA.nrows + 1) * sizeof(int);
+        for (void *p : {(void *)l.RA.val, (void *)l.RA.val32, (void *)l.RA.rp, (void *)l.RA.col})
+          dfree(ctx, p);
+        l.RA = DevBSR{};
+      }
       ST(dalloc(ctx, &lp.mt, (size_t)lp.ndof));
       ST(dalloc(ctx, &lp.mu, (size_t)lp.ndof));
       ST(dalloc(ctx, &lp.mtf, (size_t)lp.ndof));
@@ -1840,6 +1934,7 @@ void gasa_default_options(gasa_options *opt) {
   opt->tail_kib = 0;
   opt->grid_tail = 0;
   opt->wait_budget_s = 0.0;
+  opt->fused_restriction = 1;
 }
 
 gasa_status gasa_create(gasa_ctx **out, int32_t device, void *stream) {
@@ -2012,6 +2107,11 @@ gasa_status gasa_get_level(gasa_ctx *ctx, int32_t level, int32_t what, void *hos
       break;
     case GASA_LV_COARSE_INV:
       if (!fine) { src = ctx->coarse_inv; bytes = 8 * (int64_t)ctx->nc * ctx->nc; }
+      break;
+    case GASA_LV_RA_ROWPTR: if (fine && l.RA.rp) { src = l.RA.rp; bytes = 4 * (int64_t)(l.RA.nrows + 1); } break;
+    case GASA_LV_RA_COL: if (fine && l.RA.col) { src = l.RA.col; bytes = 4 * l.RA.nnzb; } break;
+    case GASA_LV_RA_VAL:
+      if (fine && l.RA.val) { src = l.RA.val; bytes = 8 * l.RA.nnzb * l.RA.br * l.RA.bc; }
       break;
     case GASA_LV_SIZES: {
       if (n_bytes < 4 * (int64_t)l.n) return fail(ctx, GASA_ERR_INVALID_ARG, "output buffer too small");

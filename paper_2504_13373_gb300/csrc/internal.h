@@ -56,9 +56,17 @@ long long launch_count();
 enum JacobiMode { JAC_SWEEP = 0, JAC_FIRST = 1, JAC_APPLY = 2, JAC_RELAX = 3 };
 
 // ---- kernels_wide.cu: FP32 blocks wider than 8, a team of warps per block row
-// true for blocks with more than 8 rows or columns (at most 64 rows) and at
-// least 8 blocks per block row on average
+// true for blocks with more than 8 rows or columns (at most 40 of either) and
+// at least 8 blocks per block row on average
 bool wide_applies(int br, int bc, int n_brows, int64_t nnzb);
+// fused residual + restriction y = R b - (R A) x (br x bc blocks of R and R A)
+// with the next level's first step xn = Wn y (square br x br) when Wn is given;
+// nnzb: blocks of R and R A together
+cudaError_t launch_wide_restrict(int n_brows, int br, int bc, int64_t nnzb, const int *rrp,
+                                 const int *rcol, const float *rval, const int *arp,
+                                 const int *acol, const float *aval, const float *b,
+                                 const float *x, float *y, const float *Wn, float *xn,
+                                 cudaStream_t s);
 // op: 0 y = A x, 1 y = b - A x, 2 y += A x, 3 y = x + W (b - A x) (square)
 cudaError_t launch_wide(int op, int n_brows, int br, int bc, int64_t nnzb, const int *rp,
                         const int *col, const float *val, const float *W, const float *x,
@@ -68,6 +76,14 @@ cudaError_t launch_wide(int op, int n_brows, int br, int bc, int64_t nnzb, const
 // true when square s x s blocks (2 <= s <= 8) average at least 6 per block row;
 // launch_blk then takes FP32 operands (FP64 returns cudaErrorNotSupported)
 bool blk_applies(int bs, int n_brows, int64_t nnzb);
+// fused residual + restriction y = R b - (R A) x (FP32, s x s blocks, s <= 8)
+// with the next level's first step xn = Wn y when Wn is given; nnzb: blocks
+// of R and R A together
+cudaError_t launch_blk_restrict(int n_brows, int bs, int64_t nnzb, const int *rrp,
+                                const int *rcol, const float *rval, const int *arp,
+                                const int *acol, const float *aval, const float *b,
+                                const float *x, float *y, const float *Wn, float *xn,
+                                cudaStream_t s);
 // op 0/1/2: y = A x, y = b - A x, y += A x; op 3: y = x + W (b - A x).
 // cudaErrorNotSupported when the shape or the alignment does not fit.
 template <typename T>

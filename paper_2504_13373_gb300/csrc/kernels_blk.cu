@@ -146,6 +146,92 @@ bsr_blk_kernel(int n_brows, const int *__restrict__ rp, const int *__restrict__ 
   else y[t] = yt + v;
 }
 
+// Fused residual and restriction of Alg. 2 on a coarse level with s x s
+// blocks: for coarse unit u, y_u = sum_j R_uj b_j - sum_j (R A)_uj x_j, the
+// vector R (b - A x) formed without the fine residual; with Wn also the
+// next level's first smoothing step xn_u = Wn_u y_u from zero (every lane of
+// the team holds all s entries of y_u after the team sum).  One block per
+// lane at a time, team sums as in bsr_blk_kernel.
+template <typename T, int S, int TL>
+__global__ void __launch_bounds__(256)
+blk_restrict_kernel(int n_brows, const int *__restrict__ rrp, const int *__restrict__ rcol,
+                    const T *__restrict__ rval, const int *__restrict__ arp,
+                    const int *__restrict__ acol, const T *__restrict__ aval,
+                    const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ y,
+                    const T *__restrict__ Wn, T *__restrict__ xn) {
+  constexpr int TW = TL < 32 ? TL : 32;
+  constexpr int WPT = TL > 32 ? TL / 32 : 1;
+  __shared__ T red[(256 / 32) * S];
+  const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int u = (int)(gt / TL);
+  const int l = (int)(gt % TL);
+  T acc[S];
+#pragma unroll
+  for (int r = 0; r < S; ++r) acc[r] = T(0);
+  if (u < n_brows) {
+    for (int k = __ldg(rrp + u) + l; k < __ldg(rrp + u + 1); k += TL) {
+      T a0[S * S], v0[S];
+      load_run<T, S * S>(rval + (size_t)k * S * S, a0);
+      load_run<T, S>(b + (size_t)__ldg(rcol + k) * S, v0);
+#pragma unroll
+      for (int r = 0; r < S; ++r) {
+        T s0 = T(0);
+#pragma unroll
+        for (int c = 0; c < S; ++c) s0 = fma(a0[r * S + c], v0[c], s0);
+        acc[r] += s0;
+      }
+    }
+    for (int k = __ldg(arp + u) + l; k < __ldg(arp + u + 1); k += TL) {
+      T a0[S * S], v0[S];
+      load_run<T, S * S>(aval + (size_t)k * S * S, a0);
+      load_run<T, S>(x + (size_t)__ldg(acol + k) * S, v0);
+#pragma unroll
+      for (int r = 0; r < S; ++r) {
+        T s0 = T(0);
+#pragma unroll
+        for (int c = 0; c < S; ++c) s0 = fma(a0[r * S + c], v0[c], s0);
+        acc[r] -= s0;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < TW; o <<= 1) {
+#pragma unroll
+    for (int r = 0; r < S; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+  }
+  if constexpr (WPT > 1) {
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+      for (int r = 0; r < S; ++r) red[wid * S + r] = acc[r];
+    }
+    __syncthreads();
+    const int w0 = wid - wid % WPT;
+#pragma unroll
+    for (int r = 0; r < S; ++r) {
+      T v = T(0);
+#pragma unroll
+      for (int q = 0; q < WPT; ++q) v += red[(w0 + q) * S + r];
+      acc[r] = v;
+    }
+  }
+  if (u >= n_brows || l >= S) return;
+  const size_t t = (size_t)u * S + l;
+  T v = T(0);
+#pragma unroll
+  for (int r = 0; r < S; ++r)
+    if (r == l) v = acc[r];
+  y[t] = v;
+  if (Wn) {
+    T wv[S];
+    load_run<T, S>(Wn + t * S, wv);
+    T out = T(0);
+#pragma unroll
+    for (int c = 0; c < S; ++c) out = fma(wv[c], acc[c], out);
+    xn[t] = out;
+  }
+}
+
 // Lanes per block row: about 2.5 blocks per lane (two in flight, a short
 // tail), a power of two in [4, 64] and at least s, so that lanes 0..s-1 of
 // the team can write the s rows.
@@ -191,12 +277,51 @@ cudaError_t blk_launch(int n_brows, int bs, int64_t nnzb, const int *rp, const i
   }
 }
 
+template <int S>
+cudaError_t blk_restrict_s(int n_brows, int64_t nnzb, const int *rrp, const int *rcol,
+                           const float *rval, const int *arp, const int *acol, const float *aval,
+                           const float *b, const float *x, float *y, const float *Wn, float *xn,
+                           cudaStream_t s) {
+  const int TL = blk_team(S, n_brows, nnzb);
+  const int grid = div_up((long long)n_brows * TL, 256);
+#define GASA_BLK_RTL(V)                                                                     \
+  case V:                                                                                   \
+    launch_k(blk_restrict_kernel<float, S, (V < S ? 8 : V)>, grid, 256, 0, s, n_brows, rrp,  \
+             rcol, rval, arp, acol, aval, b, x, y, Wn, xn);                                 \
+    break;
+  switch (TL) {
+    GASA_BLK_RTL(4) GASA_BLK_RTL(8) GASA_BLK_RTL(16) GASA_BLK_RTL(32)
+    default:
+      launch_k(blk_restrict_kernel<float, S, 64>, grid, 256, 0, s, n_brows, rrp, rcol, rval, arp,
+               acol, aval, b, x, y, Wn, xn);
+      break;
+  }
+#undef GASA_BLK_RTL
+  note_launch();
+  return cudaGetLastError();
+}
+
 bool aligned_to(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 }  // namespace
 
 bool blk_applies(int bs, int n_brows, int64_t nnzb) {
   return bs >= 2 && bs <= 8 && n_brows > 0 && nnzb >= 6LL * n_brows;
+}
+
+cudaError_t launch_blk_restrict(int n_brows, int bs, int64_t nnzb, const int *rrp,
+                                const int *rcol, const float *rval, const int *arp,
+                                const int *acol, const float *aval, const float *b,
+                                const float *x, float *y, const float *Wn, float *xn,
+                                cudaStream_t s) {
+  switch (bs) {
+#define GASA_BLK_RS(SV) \
+  case SV: return blk_restrict_s<SV>(n_brows, nnzb, rrp, rcol, rval, arp, acol, aval, b, x, y, Wn, xn, s);
+    GASA_BLK_RS(2) GASA_BLK_RS(3) GASA_BLK_RS(4) GASA_BLK_RS(5) GASA_BLK_RS(6) GASA_BLK_RS(7)
+    GASA_BLK_RS(8)
+#undef GASA_BLK_RS
+    default: return cudaErrorNotSupported;
+  }
 }
 
 // FP32 only: the team sums add s * log2(team) additions per lane, which the

@@ -36,7 +36,8 @@ GASA_MAX_LEVELS = 24
 
 (GASA_LV_A_ROWPTR, GASA_LV_A_COL, GASA_LV_A_VAL, GASA_LV_P_ROWPTR, GASA_LV_P_COL, GASA_LV_P_VAL,
  GASA_LV_R_ROWPTR, GASA_LV_R_COL, GASA_LV_R_VAL, GASA_LV_T_VAL, GASA_LV_W, GASA_LV_CAND,
- GASA_LV_SWEEPS, GASA_LV_COARSE_INV, GASA_LV_CAND_IN, GASA_LV_SIZES) = range(16)
+ GASA_LV_SWEEPS, GASA_LV_COARSE_INV, GASA_LV_CAND_IN, GASA_LV_SIZES, GASA_LV_RA_ROWPTR,
+ GASA_LV_RA_COL, GASA_LV_RA_VAL) = range(19)
 
 # every symbol include/gasa.h declares
 EXPORTS = [
@@ -71,7 +72,7 @@ class gasa_options(ctypes.Structure):
                 ("n_cut", c_dbl), ("seed", ctypes.c_uint64), ("init_candidates", c_vp),
                 ("bulk_staging", c_i32), ("matrix_free_levels", c_i32), ("hstar", c_i32),
                 ("delta", c_dbl), ("tail_kib", c_i32), ("grid_tail", c_i32),
-                ("wait_budget_s", c_dbl)]
+                ("wait_budget_s", c_dbl), ("fused_restriction", c_i32)]
 
 
 class gasa_setup_info(ctypes.Structure):

@@ -592,3 +592,71 @@ def test_grid_tail_wait_budget_runs_out():
         assert info.converged and info.rel_residual <= TOL
     finally:
         gasa.gasa_destroy(ctx)
+
+
+@pytest.mark.parametrize("name", ["c1", "p3_16", "p3_32", "tet_p2_4", "cd_q2_16", "uneq6"])
+def test_fused_restriction(name):
+    """Residual and restriction fused as b_{k+1} = R_k b_k - (R_k A_k) u_k
+    (fused_restriction = 1, the default) against the two-step form
+    R_k (b_k - A_k u_k) of Alg. 2 (fused_restriction = 0).  R_k A_k is kept
+    exactly on the levels where it holds no more values than A_k; its block
+    pattern is the structural pattern of R_k A_k (bit-exact) and its values
+    follow the oracle's product; V-cycles agree with the two-step ones and the
+    oracle's to rounding, and solves take the same iterations (+-1)."""
+    gasa = _gasa()
+    H = oracle_setup(name)
+    pr = problem(name)
+    tol = level_tolerances(H)
+    ctx_f, _ = gpu_setup(name, keep=False, fused_restriction=1)
+    ctx_u, _ = gpu_setup(name, keep=False, fused_restriction=0)
+    try:
+        kept = 0
+        for k, L in enumerate(H.levels[:-1]):
+            RA = (L.R @ L.A).tocsr()
+            units, n_next = L.unit_ptr.size - 1, H.levels[k + 1].unit_ptr.size - 1
+            s, sn = int(np.max(np.diff(L.unit_ptr))), int(np.max(np.diff(H.levels[k + 1].unit_ptr)))
+            pat = ((L.Ppat.T @ L.Apat) != 0).astype(np.float64).tocsr()
+            optr, ocol = O.pattern_csr(pat)
+            fits = ocol.size * s * sn <= L.Apat.nnz * s * s
+            try:
+                rp = gasa.gasa_get_level(ctx_f, k, gasa.GASA_LV_RA_ROWPTR, np.zeros(n_next + 1, np.int32))
+            except gasa.GasaError:
+                assert not fits, (k, "R A missing although it fits")
+                continue
+            assert fits, (k, "R A kept although larger than A")
+            kept += 1
+            np.testing.assert_array_equal(rp, optr)
+            col = gasa.gasa_get_level(ctx_f, k, gasa.GASA_LV_RA_COL, np.zeros(rp[-1], np.int32))
+            np.testing.assert_array_equal(col, ocol)
+            if np.all(np.diff(L.unit_ptr) == s) and np.all(np.diff(H.levels[k + 1].unit_ptr) == sn):
+                val = gasa.gasa_get_level(ctx_f, k, gasa.GASA_LV_RA_VAL,
+                                          np.zeros(rp[-1] * sn * s)).reshape(-1, sn, s)
+                G = bsr_scipy(rp, col, val, units)
+                # a product's perturbation scales with |R_k| |A_k|, which the
+                # cancellation in R_k A_k (smooth rows against A_k) leaves larger
+                # than |R_k A_k| by the factor below
+                cancel = (abs(L.R) @ abs(L.A)).max() / abs(RA).max()
+                assert sparse_rel(G, RA) <= tol[k + 1] * max(1.0, cancel)
+        assert kept >= 1
+        for prec, oprec, tl in ((gasa.GASA_PREC_FP64, "fp64", 1e-11),
+                                (gasa.GASA_PREC_MIXED32, "fp32", 1e-5),
+                                (gasa.GASA_PREC_MIXED16, "fp16", 1e-5)):
+            want = O.make_vcycle(H, oprec)(pr.rhs)
+            r = to_dev(pr.rhs)
+            zf, zu = to_dev(np.zeros_like(pr.rhs)), to_dev(np.zeros_like(pr.rhs))
+            gasa.gasa_vcycle(ctx_f, r, zf, prec)
+            gasa.gasa_vcycle(ctx_u, r, zu, prec)
+            zf, zu = to_host(zf), to_host(zu)
+            assert rel_err(zf, zu) <= tl, (oprec, rel_err(zf, zu))
+            assert rel_err(zf, want) <= (max(tl, 0.1 * tol[-1]) if oprec == "fp64" else 1e-4)
+        solver = gasa.GASA_SOLVER_CG if pr.solver == "cg" else gasa.GASA_SOLVER_GMRES
+        if solver == gasa.GASA_SOLVER_CG:
+            for prec in (gasa.GASA_PREC_FP64, gasa.GASA_PREC_MIXED32):
+                xf, xu = np.zeros_like(pr.rhs), np.zeros_like(pr.rhs)
+                inf_f = gasa.gasa_solve(ctx_f, pr.rhs, xf, TOL, prec)
+                inf_u = gasa.gasa_solve(ctx_u, pr.rhs, xu, TOL, prec)
+                assert inf_f.converged and inf_f.rel_residual <= TOL
+                assert abs(inf_f.iterations - inf_u.iterations) <= 1
+    finally:
+        gasa.gasa_destroy(ctx_f)
+        gasa.gasa_destroy(ctx_u)
