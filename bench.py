@@ -41,8 +41,10 @@ FALLBACK_HBM_GBS = 6800.0
 # from one ncu capture each, valid while the kernel's source file hashes to
 # `src_sha`: the plain kernel and the bulk-copy staged one.
 NCU_TRAFFIC = {
+    # captured on the 224x224 case of the same recipe (100,352 elements, 210.40 MB read +
+    # 2.19 MB written per launch, two launches) and scaled to 131,072 elements
     False: {"kernel": "jacobi_kernel<float,10,0>", "file": "kernels_mv.cu",
-            "src_sha": "2a33e599908dcaca", "bytes_per_launch": 274.855e6 + 3.249e6},
+            "src_sha": "11a0bfee7eb2b9dd", "bytes_per_launch": (210.40e6 + 2.19e6) * 131072 / 100352},
     True: {"kernel": "jacobi_tma_kernel<float,10>", "file": "kernels_tma.cu",
            "src_sha": "24cbc7a902631ea2", "bytes_per_launch": 274.87e6 + 6.52e6},
 }
@@ -70,6 +72,9 @@ def parse():
                     help="with --profile-run: drive the CG loop from the host (per-kernel ncu)")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="with --profile-run: stop each solve after this many CG iterations")
+    ap.add_argument("--dense-tail-dofs", type=int, default=-1,
+                    help="coarse levels of at most this many dofs as one dense operator "
+                         "(0: off); -1: the library default")
     ap.add_argument("--fused-restriction", type=int, default=-1, choices=[-1, 0, 1],
                     help="residual and restriction fused through R A (1) or as two steps (0); "
                          "-1: the library default")
@@ -125,7 +130,9 @@ def hbm_peak():
 # ----------------------------------------------------------------------------
 def level_shapes(gasa, ctx, n_levels):
     """gasa_level_shape per level, plus RA_nnzb: the blocks of R_k A_k where the
-    fused restriction keeps it (0 elsewhere)."""
+    fused restriction keeps it (0 elsewhere), and dense_tail: True on the first
+    level of the dense bottom operator (levels k .. N as one dense product)."""
+    dt = gasa.gasa_dense_tail_info(ctx)
     shapes = []
     for k in range(n_levels):
         sh = dict(gasa.gasa_level_shape(ctx, k))
@@ -137,6 +144,7 @@ def level_shapes(gasa, ctx, n_levels):
                 sh["RA_nnzb"] = int(rp[-1])
             except gasa.GasaError:
                 pass
+        sh["dense_tail"] = dt["n"] > 0 and k == dt["first_level"]
         shapes.append(sh)
     return shapes
 
@@ -163,13 +171,16 @@ def iteration_bytes(shapes, precision, t_pre=3, t_post=3):
     the CG vector updates with their dot products.  precision: 'fp64',
     'mixed32' (FP32 V-cycle, double-single outer product) or 'mixed16'
     (as mixed32 with FP16 level-0 A and w D^-1 plus one FP32 scale per
-    block).  Returns (total bytes, per-part dict)."""
+    block).  Where the hierarchy has a dense bottom from level kt, levels
+    kt .. N cost one dense FP64 product (n_kt^2 * 8 bytes and the two
+    vectors).  Returns (total bytes, per-part dict)."""
     N = len(shapes) - 1
     w = 8 if precision == "fp64" else 4
     parts = {}
     n0 = shapes[0]["units"] * shapes[0]["s"]
     first_done = [False] * (N + 1)
-    for k in range(N):
+    kt = next((k for k in range(N + 1) if shapes[k].get("dense_tail")), N)
+    for k in range(kt):
         sh = shapes[k]
         n, s, nnzb = sh["units"], sh["s"], sh["nnzb"]
         nxt = shapes[k + 1]
@@ -193,7 +204,7 @@ def iteration_bytes(shapes, precision, t_pre=3, t_post=3):
             RAb = ra * (s1 * s * w) + 4 * ra + 4 * (n1 + 1)
             resid = 0.0
             restrict = R + RAb + 2 * v + n1 * s1 * w
-            if k + 1 < N and _fused_first(s1, s, n1, sh["R_nnzb"] + ra, w):
+            if k + 1 < kt and _fused_first(s1, s, n1, sh["R_nnzb"] + ra, w):
                 restrict += n1 * s1 * s1 * w + n1 * s1 * w
                 first_done[k + 1] = True
         else:
@@ -201,8 +212,8 @@ def iteration_bytes(shapes, precision, t_pre=3, t_post=3):
             restrict = R + v + n1 * s1 * w
         prolong = P + n1 * s1 * w + 2 * v
         parts[f"level{k}"] = first + sweeps + resid + restrict + prolong
-    nc = shapes[N]["units"] * shapes[N]["s"]
-    parts["coarse"] = nc * nc * 8 + 2 * nc * w
+    nc = shapes[kt]["units"] * shapes[kt]["s"]
+    parts["coarse" if kt == N else "dense_tail"] = nc * nc * 8 + 2 * nc * w
     sh = shapes[0]
     nnzb, s, n = sh["nnzb"], sh["s"], sh["units"]
     idx = 4 * nnzb + 4 * (n + 1)
@@ -213,9 +224,8 @@ def iteration_bytes(shapes, precision, t_pre=3, t_post=3):
     else:
         parts["outer_Ap"] = nnzb * s * s * 8 + idx + n0 * (8 + 8 + 8)
         # A hi + lo words; p hi + lo gathered once, q written, p read for p.q
-        parts["vectors"] = (n0 * (4 + 8)                    # z back to FP64
-                            + 2 * 2 * n0 * 8                  # r.z and r.zold
-                            + n0 * (8 + 8 + 8 + 8 + 4 + 4)    # p = z + beta p, its hi/lo split
+        parts["vectors"] = (n0 * (8 + 4 + 4)                # r.z and r.zold in one pass (z, zold FP32)
+                            + n0 * (4 + 8 + 8 + 4 + 4 + 4)    # p = z + beta p, zold = z, p's hi/lo split
                             + 6 * n0 * 8)                     # x, r update
     return float(sum(parts.values())), {k: float(v) for k, v in parts.items()}
 
@@ -230,7 +240,7 @@ def gmres_iteration_bytes(shapes, precision, iterations, restart=30, t_pre=3, t_
     Restart overheads (a residual, a norm and the combination of the basis)
     are spread over the steps of their cycle."""
     tot, parts = iteration_bytes(shapes, "fp64" if precision == "fp64" else precision, t_pre, t_post)
-    vc = sum(v for k, v in parts.items() if k.startswith("level") or k == "coarse")
+    vc = sum(v for k, v in parts.items() if k.startswith("level") or k in ("coarse", "dense_tail"))
     sh = shapes[0]
     nnzb, s, n = sh["nnzb"], sh["s"], sh["units"]
     n0 = n * s
@@ -540,6 +550,7 @@ def measure_workload(gasa, pr, name, steps, warmup, device):
                             adj_ptr=pr.adj_ptr, adj_idx=pr.adj_idx, centroids=pr.centroids,
                             init_candidates=pr.B0)
     shapes = level_shapes(gasa, ctx, sinfo.n_levels)
+    dense_tail = gasa.gasa_dense_tail_info(ctx)
     peak, peak_kind = hbm_peak()
     b = torch.from_numpy(pr.rhs).cuda(device)
     x = torch.zeros_like(b)
@@ -585,7 +596,7 @@ def measure_workload(gasa, pr, name, steps, warmup, device):
             "level_dofs": [int(sinfo.dofs[k]) for k in range(sinfo.n_levels)],
             "level_nnzb": [int(sinfo.nnzb[k]) for k in range(sinfo.n_levels)],
             "level_block": [int(sinfo.block[k]) for k in range(sinfo.n_levels)],
-            "setup_s": sinfo.seconds, "steps": steps, "warmup": warmup, "precisions": out}
+            "dense_tail": dense_tail, "setup_s": sinfo.seconds, "steps": steps, "warmup": warmup, "precisions": out}
 
 
 def other_workloads(gasa, device, steps=1, warmup=1):
@@ -669,6 +680,8 @@ def ours_main(args, rank, world, local):
         opt.grid_tail = args.grid_tail
     if args.fused_restriction >= 0:
         opt.fused_restriction = args.fused_restriction
+    if args.dense_tail_dofs >= 0:
+        opt.dense_tail_dofs = args.dense_tail_dofs
     opt.bulk_staging = 1 if args.bulk_staging else 0
     sinfo = gasa.gasa_setup(ctx, A.row_ptr, A.col, A.val.ravel(), A.b, pr.agg_of, opt,
                             adj_ptr=pr.adj_ptr, adj_idx=pr.adj_idx, centroids=pr.centroids,
@@ -805,6 +818,7 @@ def ours_main(args, rank, world, local):
             "workload": WORKLOAD if args.n == 256 else f"poisson2d_sipg_p3_tri_{args.n}x{args.n}",
             "dofs": n, "elements": A.n, "block": A.b, "nnzb": int(A.nnzb), "levels": sinfo.n_levels,
             "candidates": pr.r, "tol": TOL, "solver": "CG (flexible for mixed)",
+            "dense_tail": gasa.gasa_dense_tail_info(ctx),
             "l2": "inputs larger than L2 (A 419 MB FP64 / 209 MB FP32 per pass), no flush",
             "parallelism": f"replicas x{world}",
         },

@@ -140,6 +140,15 @@ typedef struct {
                                 the FP32 levels also takes level k+1's first smoothing step
                                 u_{k+1} = w D_{k+1}^{-1} b_{k+1}; results agree with the two-step
                                 form to rounding.  0: residual and restriction as two steps. */
+  int32_t dense_tail_dofs;   /* bottom of the V-cycle of Alg. 2 as one dense operator: from the first
+                                level k >= 1 holding at most this many (stored) dofs, with every
+                                level below it stored (not matrix-free), the steps of levels
+                                k .. N-1 and the coarsest solve, started from u_k = 0, form a fixed
+                                linear map b_k -> u_k.  Setup forms it (FP64, n_k x n_k) by running
+                                those steps on the unit vectors, and the V-cycle applies it as one
+                                dense FP64 product (FP32 vectors in the FP32 cycle).  Results agree
+                                with the per-step cycle to rounding.  Not built when tail_kib or
+                                grid_tail is set.  0: off; default 2048; at most 8192. */
 } gasa_options;
 
 typedef struct {
@@ -214,7 +223,9 @@ enum {
   GASA_LV_SIZES = 15,        /* int32 units: real dofs of each unit */
   GASA_LV_RA_ROWPTR = 16,    /* R_k A_k (option fused_restriction), next-level rows x level-k units */
   GASA_LV_RA_COL = 17,
-  GASA_LV_RA_VAL = 18
+  GASA_LV_RA_VAL = 18,
+  GASA_LV_DENSE_TAIL = 19    /* first level k of the dense bottom (option dense_tail_dofs): its
+                                n_k x n_k FP64 operator b_k -> u_k, row-major */
 };
 /* shape[0..7] = units, s_k, nnzb(A), P nnzb, R nnzb, s_{k+1}, r, dofs.  On a
  * level whose aggregates keep different counts (h*-step, or unequal
@@ -233,6 +244,13 @@ gasa_status gasa_level_shape(gasa_ctx *ctx, int32_t level, int64_t shape[8]);
  * GASA_ERR_STATE before a successful gasa_setup, GASA_ERR_INVALID_ARG for an
  * unknown precision or a null pointer. */
 gasa_status gasa_tail_info(gasa_ctx *ctx, int32_t precision, int32_t out[3]);
+
+/* Dense bottom of the V-cycle (option dense_tail_dofs), shared by every
+ * precision: out[0] = its first level k (n_levels - 1 when there is none),
+ * out[1] = n_k, the operator's order (0 when there is none).
+ * GASA_ERR_STATE before a successful gasa_setup, GASA_ERR_INVALID_ARG for a
+ * null pointer. */
+gasa_status gasa_dense_tail_info(gasa_ctx *ctx, int32_t out[2]);
 gasa_status gasa_get_level(gasa_ctx *ctx, int32_t level, int32_t what,
                            void *host_out, int64_t n_bytes);
 

@@ -100,5 +100,7 @@ template <typename T>
 cudaError_t launch_bgather(int64_t n, int K, int c, const T *src, T *dst, cudaStream_t s);
 cudaError_t launch_bcolcopy(int64_t n, int K, int c, const double *src, double *dst,
                             cudaStream_t s);
+// B (n x K interleaved) = columns c0 .. c0 + K - 1 of the n x n identity
+cudaError_t launch_bunit_columns(int n, int K, int c0, double *B, cudaStream_t s);
 
 }  // namespace gasa

@@ -93,6 +93,7 @@ struct gasa_ctx {
   double *scal = nullptr;         // device scalars
   double *hscal = nullptr;        // pinned host mirror
   float *kf_in = nullptr, *kf_out = nullptr;
+  float *kzold_f = nullptr;   // previous z of the graph-resident mixed CG step (FP32)
   float *kp_hi = nullptr, *kp_lo = nullptr;   // two-term FP32 split of p (mixed precision)
   double *pq_ds = nullptr;   // p . Ap partials of the double-single product (one per CTA)
   int n_pq_ds = 0;
@@ -125,6 +126,12 @@ struct gasa_ctx {
   int grid_ctas[2] = {0, 0};
   int grid_s[2] = {0, 0};
   unsigned int *grid_bar = nullptr;
+  // dense bottom of the V-cycle (option dense_tail_dofs): levels dtail_k ..
+  // N as the FP64 dtail_n x dtail_n operator dtail_M (row-major); none when
+  // dtail_M is null (dtail_k = N)
+  double *dtail_M = nullptr;
+  int dtail_k = 0;
+  int dtail_n = 0;
   // profiling
   bool prof = false;
   ProfClass pc[4];

@@ -18,6 +18,7 @@
 #include "ctx.h"
 #include "tail.h"
 #include "grid.h"
+#include "batch.h"
 
 using namespace gasa;
 
@@ -109,6 +110,9 @@ void free_all(gasa_ctx *ctx) {
     ctx->grid_ctas[p] = 0;
   }
   ctx->grid_bar = nullptr;
+  ctx->dtail_M = nullptr;
+  ctx->dtail_k = 0;
+  ctx->dtail_n = 0;
   ctx->V = ctx->Z = ctx->H = ctx->gm = ctx->mpart = nullptr;
   ctx->gm_restart = 0;
 }
@@ -450,6 +454,112 @@ gasa_status grid_build(gasa_ctx *ctx, int pi) {
   return GASA_OK;
 }
 
+// Dense bottom of the V-cycle (opt.dense_tail_dofs).  From level kt down,
+// Alg. 2 started from u_kt = 0 is a fixed linear map of b_kt: each smoothing
+// step, residual, restriction, prolongation and the coarsest solve is linear
+// in it.  On the coarse levels each of those steps is a launch whose cost is
+// latency rather than bytes, so setup runs exactly those steps (FP64, the
+// batched kernels of the request server) on the unit vectors, eight at a
+// time, and keeps the results as the columns of M_kt; the V-cycle then
+// applies u_kt = M_kt b_kt as one dense product.  kt is the first level
+// k >= 1 from which every level holds at most dense_tail_dofs stored dofs
+// and is stored (not matrix-free).
+gasa_status dense_tail_build(gasa_ctx *ctx) {
+  const int N = ctx->N;
+  ctx->dtail_M = nullptr;
+  ctx->dtail_k = N;
+  ctx->dtail_n = 0;
+  const gasa_options &o = ctx->opt;
+  if (o.dense_tail_dofs <= 0 || o.tail_kib > 0 || o.grid_tail || N < 2) return GASA_OK;
+  int kt = N;
+  for (int k = N - 1; k >= 1; --k) {
+    const Level &l = ctx->L[k];
+    if (l.mf || !l.A.val || l.ndof > o.dense_tail_dofs) break;
+    kt = k;
+  }
+  if (kt == N) return GASA_OK;
+  constexpr int K = 8;
+  cudaStream_t s = ctx->stream;
+  const int n = (int)ctx->L[kt].ndof;
+  const int tpre = o.t_pre, tpost = o.t_post;
+  // scratch per level kt .. N: x, x2, b, r of K interleaved columns
+  size_t tot = 0;
+  for (int k = kt; k <= N; ++k) tot += 4 * (size_t)ctx->L[k].ndof * K;
+  double *scr = nullptr;
+  ST(dalloc(ctx, &scr, tot));
+  std::vector<double *> X(N + 1), X2(N + 1), B(N + 1), Rv(N + 1);
+  {
+    double *p = scr;
+    for (int k = kt; k <= N; ++k) {
+      const size_t m = (size_t)ctx->L[k].ndof * K;
+      X[k] = p;
+      X2[k] = p + m;
+      B[k] = p + 2 * m;
+      Rv[k] = p + 3 * m;
+      p += 4 * m;
+    }
+  }
+  double *M = nullptr;
+  gasa_status st = dalloc(ctx, &M, (size_t)n * n);
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+    return e == cudaSuccess;
+  };
+  for (int c0 = 0; st == GASA_OK && e == cudaSuccess && c0 < n; c0 += K) {
+    std::vector<double *> xk(N + 1);
+    if (!ok(launch_bunit_columns(n, K, c0, B[kt], s))) break;
+    for (int k = kt; k < N && e == cudaSuccess; ++k) {
+      Level &l = ctx->L[k];
+      double *x = X[k], *x2 = X2[k];
+      if (tpre == 0) {
+        ok(cudaMemsetAsync(x, 0, (size_t)l.ndof * K * sizeof(double), s));
+      } else {
+        ok(launch_bjacobi<double>(JAC_FIRST, l.n, l.s, l.A.rp, l.A.col, l.A.val, l.W, nullptr,
+                                  B[k], x, K, s, l.A.nnzb));
+        for (int t = 1; t < tpre; ++t) {
+          ok(launch_bjacobi<double>(JAC_SWEEP, l.n, l.s, l.A.rp, l.A.col, l.A.val, l.W, x, B[k],
+                                    x2, K, s, l.A.nnzb));
+          std::swap(x, x2);
+        }
+      }
+      xk[k] = x;
+      ok(launch_bmv<double>(GASA_MV_RESIDUAL, l.n, l.s, l.s, l.A.rp, l.A.col, l.A.val, x, B[k],
+                            Rv[k], K, s, l.A.nnzb));
+      ok(launch_bmv<double>(GASA_MV_ASSIGN, l.R.nrows, l.R.br, l.R.bc, l.R.rp, l.R.col, l.R.val,
+                            Rv[k], nullptr, B[k + 1], K, s, l.R.nnzb));
+    }
+    ok(launch_bdense<double>(ctx->nc, ctx->coarse_inv, B[N], X[N], K, s));
+    xk[N] = X[N];
+    for (int k = N - 1; k >= kt && e == cudaSuccess; --k) {
+      Level &l = ctx->L[k];
+      double *x = xk[k];
+      double *x2 = (x == X[k]) ? X2[k] : X[k];
+      ok(launch_bmv<double>(GASA_MV_ADD, l.P.nrows, l.P.br, l.P.bc, l.P.rp, l.P.col, l.P.val,
+                            xk[k + 1], nullptr, x, K, s, l.P.nnzb));
+      for (int t = 0; t < tpost; ++t) {
+        ok(launch_bjacobi<double>(JAC_SWEEP, l.n, l.s, l.A.rp, l.A.col, l.A.val, l.W, x, B[k], x2,
+                                  K, s, l.A.nnzb));
+        std::swap(x, x2);
+      }
+      xk[k] = x;
+    }
+    // row i of the K interleaved columns is M[i][c0 .. c0 + K)
+    const int w = std::min(K, n - c0);
+    ok(cudaMemcpy2DAsync(M + c0, (size_t)n * sizeof(double), xk[kt], K * sizeof(double),
+                         w * sizeof(double), n, cudaMemcpyDeviceToDevice, s));
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dfree(ctx, scr);
+  ctx->device_bytes -= (int64_t)(tot * sizeof(double));
+  if (st != GASA_OK) return st;
+  CU(e);
+  ctx->dtail_M = M;
+  ctx->dtail_k = kt;
+  ctx->dtail_n = n;
+  return GASA_OK;
+}
+
 // Fused residual and restriction of Alg. 2 on level k: b_{k+1} = R_k b_k -
 // (R_k A_k) x_k, the vector R_k (b_k - A_k x_k) without the fine residual.
 // FP32 levels run it as one product (lane teams for s <= 8 square blocks,
@@ -523,8 +633,12 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false,
   const int N = ctx->N;
   const int pi = std::is_same<T, float>::value ? 1 : 0;
   const bool grid = ctx->grid_plan[pi] != nullptr;
-  // first level of the fused bottom (persistent grid launch, else cluster launch)
-  const int kt = grid ? ctx->grid_k0[pi] : (ctx->tail_plan[pi] ? ctx->tail_k0[pi] : N);
+  const bool cluster = !grid && ctx->tail_plan[pi] != nullptr;
+  const bool dense = !grid && !cluster && ctx->dtail_M != nullptr;
+  // first level of the fused bottom (persistent grid launch, cluster launch
+  // or dense operator)
+  const int kt = grid ? ctx->grid_k0[pi]
+                      : (cluster ? ctx->tail_k0[pi] : (dense ? ctx->dtail_k : N));
   const int tpre = ctx->opt.t_pre, tpost = ctx->opt.t_post;
   const int w = (int)sizeof(T);
   // level-0 smoothing step and residual; with h16 (FP32 V-cycle only) the
@@ -624,12 +738,17 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false,
     CU(launch_grid_tail<T>(static_cast<const GridPlan<T> *>(ctx->grid_plan[pi]), ctx->grid_s[pi],
                            ctx->grid_ctas[pi], ctx->grid_bar, s));
     xk[kt] = P::x(ctx->L[kt]);
-  } else if (kt < N) {
+  } else if (kt < N && cluster) {
     // levels kt .. N-1 and the coarsest solve (FP64 arithmetic) in one
     // cluster launch; it leaves the corrected x_kt in L[kt]'s x
     const TailPlan<T> *pl = static_cast<const TailPlan<T> *>(ctx->tail_plan[pi]);
     CU(launch_vcycle_tail<T>(pl, ctx->tail_cluster[pi], ctx->tail_smem[pi], s));
     xk[kt] = P::x(ctx->L[kt]);
+  } else if (kt < N) {
+    // levels kt .. N-1 and the coarsest solve as their dense FP64 operator
+    Level &ld = ctx->L[kt];
+    CU(launch_dense_mv<T>(ctx->dtail_n, ctx->dtail_M, P::b(ld), P::x(ld), s));
+    xk[kt] = P::x(ld);
   } else {
     // coarsest solve in FP64
     CU(launch_dense_mv<T>(ctx->nc, ctx->coarse_inv, P::b(lc), P::x(lc), s));
@@ -658,18 +777,23 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false,
   return GASA_OK;
 }
 
-gasa_status apply_M(gasa_ctx *ctx, const double *rr, double *z, int precision) {
-  if (precision == GASA_PREC_FP64) return vcycle_impl<double>(ctx, rr, z);
+// FP32 V-cycle of the mixed precisions on the FP64 residual rr; z in FP32
+// is left in ctx->kf_out
+gasa_status vcycle_f32_out(gasa_ctx *ctx, const double *rr, int precision) {
   Level &l0 = ctx->L[0];
   const int64_t n = l0.ndof;
   if (precision == GASA_PREC_MIXED32 && !l0.mf && l0.s <= 16 && ctx->opt.t_pre >= 1) {
     FusedEnds fe{rr, ctx->kf_in};
-    ST(vcycle_impl<float>(ctx, ctx->kf_in, ctx->kf_out, false, &fe));
-  } else {
-    CU(launch_convert<double, float>(n, rr, ctx->kf_in, ctx->stream));
-    ST(vcycle_impl<float>(ctx, ctx->kf_in, ctx->kf_out, precision == GASA_PREC_MIXED16));
+    return vcycle_impl<float>(ctx, ctx->kf_in, ctx->kf_out, false, &fe);
   }
-  CU(launch_convert<float, double>(n, ctx->kf_out, z, ctx->stream));
+  CU(launch_convert<double, float>(n, rr, ctx->kf_in, ctx->stream));
+  return vcycle_impl<float>(ctx, ctx->kf_in, ctx->kf_out, precision == GASA_PREC_MIXED16);
+}
+
+gasa_status apply_M(gasa_ctx *ctx, const double *rr, double *z, int precision) {
+  if (precision == GASA_PREC_FP64) return vcycle_impl<double>(ctx, rr, z);
+  ST(vcycle_f32_out(ctx, rr, precision));
+  CU(launch_convert<float, double>(ctx->L[0].ndof, ctx->kf_out, z, ctx->stream));
   return GASA_OK;
 }
 
@@ -762,12 +886,58 @@ gasa_status pcg(gasa_ctx *ctx, const double *b, double tol, int precision, int *
     return GASA_OK;
   }
   CU(launch_copy(n, b, r, s));
+  const int max_iter = ctx->opt.max_iter;
+  if (flex) {
+    // the kernels of the graph-resident step, in its order, one by one:
+    // z = M r (FP32), r . z and r . zold, p = z + beta p with its split,
+    // q = A p with p . q, x and r; started from p = 0, zold = 0, rz = 1
+    CU(cudaMemsetAsync(p, 0, n * sizeof(double), s));
+    CU(cudaMemsetAsync(ctx->kzold_f, 0, n * sizeof(float), s));
+    ctx->hscal[S_RZ0] = 1.0;
+    CU(cudaMemcpyAsync(ctx->scal + S_RZ0, ctx->hscal + S_RZ0, sizeof(double),
+                       cudaMemcpyHostToDevice, s));
+    int cur = S_RZ0, nxt = S_RZ1;
+    for (int it = 1; it <= max_iter; ++it) {
+      ST(vcycle_f32_out(ctx, r, precision));
+      CU(launch_cg_dots_f32(n, r, ctx->kf_out, ctx->kzold_f, ctx->rz_ds, ctx->rzo_ds, s));
+      CU(launch_cg_update_p_f32(n, p, ctx->kf_out, ctx->scal + cur, ctx->rz_ds, ctx->rzo_ds,
+                                ctx->scal + nxt, ctx->kzold_f, ctx->kp_hi, ctx->kp_lo, kRedBlocks,
+                                s));
+      ST(spmv_outer_ds(ctx, p, q, false));
+      CU(launch_cg_update_xr(n, x, r, p, q, ctx->scal + nxt, ctx->pq_ds, rr_part,
+                             ctx->scal + S_ALPHA, s, pq_ds_count(ctx)));
+      CU(launch_finalize(rr_part, 1, ctx->scal + S_RR, s));
+      ST(read_scalars(ctx, 0, 3));
+      const double pq = ctx->hscal[S_PQ];
+      if (!std::isfinite(pq)) return fail(ctx, GASA_ERR_BREAKDOWN, "CG: non-finite p^T A p");
+      const double rel = std::sqrt(ctx->hscal[S_RR]) / bn;
+      *iters = it;
+      if (!std::isfinite(rel)) return fail(ctx, GASA_ERR_BREAKDOWN, "CG: non-finite residual");
+      if (rel <= tol) {
+        ST(spmv_outer(ctx, GASA_MV_RESIDUAL, x, b, ctx->kt));
+        double tt;
+        ST(norm2(ctx, n, ctx->kt, S_TMP, &tt));
+        const double relt = std::sqrt(tt) / bn;
+        if (relt <= tol) {
+          *relres = relt;
+          *conv = true;
+          return GASA_OK;
+        }
+        CU(launch_copy(n, ctx->kt, r, s));
+      }
+      std::swap(cur, nxt);
+    }
+    ST(spmv_outer(ctx, GASA_MV_RESIDUAL, x, b, ctx->kt));
+    double tt;
+    ST(norm2(ctx, n, ctx->kt, S_TMP, &tt));
+    *relres = std::sqrt(tt) / bn;
+    return GASA_OK;
+  }
   int np = 0;
   ST(apply_M_cg(ctx, r, z, nullptr, precision, ctx->rz_ds, ctx->rzo_ds, &np));
   CU(launch_finalize_n(ctx->rz_ds, np, ctx->scal + S_RZ0, s));
   CU(launch_copy(n, z, p, s));
   int cur = S_RZ0, nxt = S_RZ1;
-  const int max_iter = ctx->opt.max_iter;
   for (int it = 1; it <= max_iter; ++it) {
     if (flex) {
       ST(spmv_outer_ds(ctx, p, q, true));
@@ -846,14 +1016,25 @@ gasa_status build_cg_graph(gasa_ctx *ctx, int precision) {
   ctx->prof = false;   // no event records inside a graph body
   const long long k0 = launch_count();
   CU(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  int np = 0;
-  gasa_status st =
-      apply_M_cg(ctx, r, z, flex ? zold : nullptr, precision, ctx->rz_ds, ctx->rzo_ds, &np);
+  int np = kRedBlocks;
+  gasa_status st = GASA_OK;
   cudaError_t e = cudaSuccess;
-  if (st == GASA_OK) {
-    e = launch_cg_update_p(n, p, z, ctx->scal + S_RZ0, ctx->rz_ds, ctx->rzo_ds, ctx->scal + S_RZ1,
-                           flex ? 1 : 0, s, flex ? zold : nullptr, flex ? ctx->kp_hi : nullptr,
-                           flex ? ctx->kp_lo : nullptr, np);
+  if (flex) {
+    // z stays in FP32: one pass for r . z and r . zold, and the p update
+    // reads it there and keeps it as the next step's zold
+    st = vcycle_f32_out(ctx, r, precision);
+    if (st == GASA_OK)
+      e = launch_cg_dots_f32(n, r, ctx->kf_out, ctx->kzold_f, ctx->rz_ds, ctx->rzo_ds, s);
+  } else {
+    st = apply_M_cg(ctx, r, z, nullptr, precision, ctx->rz_ds, ctx->rzo_ds, &np);
+  }
+  if (st == GASA_OK && e == cudaSuccess) {
+    if (flex)
+      e = launch_cg_update_p_f32(n, p, ctx->kf_out, ctx->scal + S_RZ0, ctx->rz_ds, ctx->rzo_ds,
+                                 ctx->scal + S_RZ1, ctx->kzold_f, ctx->kp_hi, ctx->kp_lo, np, s);
+    else
+      e = launch_cg_update_p(n, p, z, ctx->scal + S_RZ0, ctx->rz_ds, ctx->rzo_ds,
+                             ctx->scal + S_RZ1, 0, s, nullptr, nullptr, nullptr, np);
     Level &l = ctx->L[0];
     if (e == cudaSuccess && flex) {
       // q = A p with the p . q partials in the same launch
@@ -901,6 +1082,7 @@ gasa_status pcg_graph(gasa_ctx *ctx, const double *b, double tol, int precision,
   CU(launch_copy(n, b, ctx->kr, s));
   CU(cudaMemsetAsync(ctx->kp, 0, n * sizeof(double), s));
   CU(cudaMemsetAsync(ctx->kzold, 0, n * sizeof(double), s));
+  CU(cudaMemsetAsync(ctx->kzold_f, 0, n * sizeof(float), s));
   CU(cudaMemsetAsync(ctx->d_iters, 0, sizeof(int), s));
   ctx->hscal[S_RZ0] = 1.0;
   ctx->hscal[S_BN] = bn;
@@ -1315,7 +1497,8 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
   if (opt->t_pre < 0 || opt->t_post < 0 || opt->q_power < 0 || opt->max_relax < 0 ||
       opt->gamma < 0.0 || !(opt->omega_factor > 0.0) || opt->dim < 1 || opt->dim > 3 ||
       opt->solver < GASA_SOLVER_CG || opt->solver > GASA_SOLVER_STATIONARY || opt->max_iter < 1 ||
-      opt->matrix_free_levels < 0 || opt->delta < 0.0 || (opt->hstar && !(opt->delta < 1.0)))
+      opt->matrix_free_levels < 0 || opt->delta < 0.0 || (opt->hstar && !(opt->delta < 1.0)) ||
+      opt->dense_tail_dofs < 0 || opt->dense_tail_dofs > 8192)
     return fail(ctx, GASA_ERR_INVALID_ARG, "options out of range");
   if (opt->hstar && hier->n_levels + 1 > GASA_MAX_LEVELS)
     return fail(ctx, GASA_ERR_INVALID_ARG, "hierarchy: too many levels with the h* step");
@@ -1771,6 +1954,7 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
     ST(dalloc(ctx, p, (size_t)n));
   ST(dalloc(ctx, &ctx->kf_in, (size_t)n));
   ST(dalloc(ctx, &ctx->kf_out, (size_t)n));
+  ST(dalloc(ctx, &ctx->kzold_f, (size_t)n));
   ST(dalloc(ctx, &ctx->kp_hi, (size_t)n));
   ST(dalloc(ctx, &ctx->kp_lo, (size_t)n));
   ctx->n_pq_ds = bsr_mv_ds_grid(ctx->L[0].n, ctx->L[0].s);
@@ -1820,6 +2004,7 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
     l.tma = tma_plan(l.n, l.s, (int)sizeof(float), maxrow, &l.tma_TR, &l.tma_stageA,
                      &l.tma_stageW, &l.tma_smem, &l.tma_grid);
   }
+  ST(dense_tail_build(ctx));
   ST(tail_build<double>(ctx, 0));
   ST(tail_build<float>(ctx, 1));
   ST(grid_build<double>(ctx, 0));
@@ -1935,6 +2120,7 @@ void gasa_default_options(gasa_options *opt) {
   opt->grid_tail = 0;
   opt->wait_budget_s = 0.0;
   opt->fused_restriction = 1;
+  opt->dense_tail_dofs = 2048;
 }
 
 gasa_status gasa_create(gasa_ctx **out, int32_t device, void *stream) {
@@ -2074,6 +2260,15 @@ gasa_status gasa_tail_info(gasa_ctx *ctx, int32_t precision, int32_t out[3]) {
   return GASA_OK;
 }
 
+gasa_status gasa_dense_tail_info(gasa_ctx *ctx, int32_t out[2]) {
+  if (!ctx || !out) return GASA_ERR_INVALID_ARG;
+  if (!ctx->ready) return fail(ctx, GASA_ERR_STATE, "no hierarchy");
+  const bool on = ctx->dtail_M != nullptr;
+  out[0] = on ? ctx->dtail_k : ctx->N;
+  out[1] = on ? ctx->dtail_n : 0;
+  return GASA_OK;
+}
+
 gasa_status gasa_get_level(gasa_ctx *ctx, int32_t level, int32_t what, void *host_out,
                            int64_t n_bytes) {
   if (!ctx || !host_out) return GASA_ERR_INVALID_ARG;
@@ -2112,6 +2307,12 @@ gasa_status gasa_get_level(gasa_ctx *ctx, int32_t level, int32_t what, void *hos
     case GASA_LV_RA_COL: if (fine && l.RA.col) { src = l.RA.col; bytes = 4 * l.RA.nnzb; } break;
     case GASA_LV_RA_VAL:
       if (fine && l.RA.val) { src = l.RA.val; bytes = 8 * l.RA.nnzb * l.RA.br * l.RA.bc; }
+      break;
+    case GASA_LV_DENSE_TAIL:
+      if (ctx->dtail_M && level == ctx->dtail_k) {
+        src = ctx->dtail_M;
+        bytes = 8 * (int64_t)ctx->dtail_n * ctx->dtail_n;
+      }
       break;
     case GASA_LV_SIZES: {
       if (n_bytes < 4 * (int64_t)l.n) return fail(ctx, GASA_ERR_INVALID_ARG, "output buffer too small");

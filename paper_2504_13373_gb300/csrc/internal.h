@@ -174,6 +174,17 @@ cudaError_t launch_cg_update_p(int64_t n, double *p, const double *z, const doub
                                const double *rz_partials, const double *rzold_partials,
                                double *rz_out, int flexible, cudaStream_t s,
                                double *zold_out, float *p_hi, float *p_lo, int n_rz);
+// mixed-precision CG with z, zold in FP32 (exact in FP64): partials of r . z
+// and r . zold in one pass (the sums of launch_dot_partials on FP64 copies),
+// and the flexible p update reading z from FP32, copying it to zold_out and
+// splitting p (8-byte aligned FP32 and 16-byte aligned FP64 arrays, else
+// cudaErrorNotSupported)
+cudaError_t launch_cg_dots_f32(int64_t n, const double *r, const float *z, const float *zold,
+                               double *part_rz, double *part_rzo, cudaStream_t s);
+cudaError_t launch_cg_update_p_f32(int64_t n, double *p, const float *z, const double *rz_old,
+                                   const double *rz_partials, const double *rzold_partials,
+                                   double *rz_out, float *zold_out, float *p_hi, float *p_lo,
+                                   int n_rz, cudaStream_t s);
 // exact two-term FP32 split v = hi + lo of an FP64 vector
 cudaError_t launch_split(int64_t n, const double *v, float *hi, float *lo, cudaStream_t s);
 cudaError_t launch_cg_check(const double *rr_partials, double *scal, int *iters, int max_iter,

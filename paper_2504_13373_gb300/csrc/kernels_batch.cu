@@ -738,6 +738,58 @@ __global__ void bcolcopy_kernel(int64_t n, int K, int c, const T *__restrict__ s
   if (i < n) dst[i * K + c] = src[i * K + c];
 }
 
+// B (n x K interleaved) = columns c0 .. c0 + K - 1 of the n x n identity
+// (columns past n are zero)
+__global__ void bunit_columns_kernel(int n, int K, int c0, double *__restrict__ B) {
+  const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (t >= (int64_t)n * K) return;
+  const int64_t i = t / K, c = t - i * K;
+  B[t] = (i == c0 + c) ? 1.0 : 0.0;
+}
+
+// X = A B for a dense row-major n x n FP64 A and K interleaved columns, FP64
+// arithmetic: a warp per row, lane l takes columns j = l, l + 32, ... of the
+// row in order (four rows of B in flight), then an xor-shuffle tree; a
+// column's sum does not depend on K
+template <typename T, int K>
+__global__ void __launch_bounds__(kThreads)
+bdense_warp_kernel(int n, const double *__restrict__ A, const T *__restrict__ B, T *__restrict__ X) {
+  const int row = (int)(((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const double *a = A + (size_t)row * n;
+  double acc[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) acc[c] = 0.0;
+  int j = lane;
+  for (; j + 96 < n; j += 128) {
+    const double a0 = __ldg(a + j), a1 = __ldg(a + j + 32), a2 = __ldg(a + j + 64),
+                 a3 = __ldg(a + j + 96);
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      acc[c] = fma(a0, (double)__ldg(B + (size_t)j * K + c), acc[c]);
+      acc[c] = fma(a1, (double)__ldg(B + (size_t)(j + 32) * K + c), acc[c]);
+      acc[c] = fma(a2, (double)__ldg(B + (size_t)(j + 64) * K + c), acc[c]);
+      acc[c] = fma(a3, (double)__ldg(B + (size_t)(j + 96) * K + c), acc[c]);
+    }
+  }
+  for (; j < n; j += 32) {
+    const double a0 = __ldg(a + j);
+#pragma unroll
+    for (int c = 0; c < K; ++c) acc[c] = fma(a0, (double)__ldg(B + (size_t)j * K + c), acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+    double v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    acc[c] = v;
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < K; ++c) X[(size_t)row * K + c] = (T)acc[c];
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -822,7 +874,13 @@ cudaError_t launch_bjacobi_h16(int mode, int n, int bs, const int *rp, const int
 template <typename T>
 cudaError_t launch_bdense(int nc, const double *Ainv, const T *B, T *X, int K, cudaStream_t s) {
   const int64_t tot = (int64_t)nc * K;
-  GASA_KSWITCH(K, launch_k(bdense_kernel<T, KK>, div_up(tot, kThreads), kThreads, 0, s, nc, Ainv, B, X));
+  // orders of 128 and more (the dense bottom of the V-cycle) take a warp per row
+  if (nc >= 128) {
+    GASA_KSWITCH(K, launch_k(bdense_warp_kernel<T, KK>, div_up((int64_t)nc * 32, kThreads),
+                             kThreads, 0, s, nc, Ainv, B, X));
+  } else {
+    GASA_KSWITCH(K, launch_k(bdense_kernel<T, KK>, div_up(tot, kThreads), kThreads, 0, s, nc, Ainv, B, X));
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -988,6 +1046,13 @@ cudaError_t launch_bscatter(int64_t n, int K, int c, const T *src, T *dst, cudaS
 template <typename T>
 cudaError_t launch_bgather(int64_t n, int K, int c, const T *src, T *dst, cudaStream_t s) {
   launch_k(bgather_kernel<T>, div_up(n, kThreads), kThreads, 0, s, n, K, c, src, dst);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bunit_columns(int n, int K, int c0, double *B, cudaStream_t s) {
+  if (n <= 0 || K <= 0) return cudaSuccess;
+  launch_k(bunit_columns_kernel, div_up((int64_t)n * K, kThreads), kThreads, 0, s, n, K, c0, B);
   note_launch();
   return cudaGetLastError();
 }

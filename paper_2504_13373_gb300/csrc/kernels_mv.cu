@@ -857,7 +857,19 @@ dense_mv_kernel(int n, const double *__restrict__ A, const T *__restrict__ x,
   if (warp >= n) return;
   const double *a = A + (size_t)warp * n;
   double acc = 0.0;
-  for (int j = lane; j < n; j += 32) acc = fma(a[j], (double)x[j], acc);
+  // lane l sums columns l, l + 32, ... in order, four of them in flight
+  int j = lane;
+  for (; j + 96 < n; j += 128) {
+    const double a0 = __ldg(a + j), a1 = __ldg(a + j + 32), a2 = __ldg(a + j + 64),
+                 a3 = __ldg(a + j + 96);
+    const double x0 = (double)__ldg(x + j), x1 = (double)__ldg(x + j + 32),
+                 x2 = (double)__ldg(x + j + 64), x3 = (double)__ldg(x + j + 96);
+    acc = fma(a0, x0, acc);
+    acc = fma(a1, x1, acc);
+    acc = fma(a2, x2, acc);
+    acc = fma(a3, x3, acc);
+  }
+  for (; j < n; j += 32) acc = fma(__ldg(a + j), (double)__ldg(x + j), acc);
   acc = warp_sum(acc);
   if (lane == 0) y[warp] = (T)acc;
 }

@@ -457,6 +457,110 @@ cudaError_t launch_cg_update_p(int64_t n, double *p, const double *z, const doub
   return cudaGetLastError();
 }
 
+// The mixed-precision CG step with z and zold left in FP32 by the V-cycle
+// (their FP64 values are exact): the partial sums of r . z and r . zold in
+// one pass, over the same pairs, in the same order and tree as
+// dot_partials_kernel<true>, so they equal those of FP64 copies bit for bit
+__global__ void __launch_bounds__(kRedThreads)
+cg_dots_f32_kernel(int64_t n, const double *__restrict__ r, const float *__restrict__ z,
+                   const float *__restrict__ zo, double *__restrict__ part_rz,
+                   double *__restrict__ part_rzo) {
+  __shared__ double sh[32];
+  double a[4] = {0.0, 0.0, 0.0, 0.0}, c[4] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t m = n >> 1;
+  const float2 *z2 = reinterpret_cast<const float2 *>(z);
+  const float2 *o2 = reinterpret_cast<const float2 *>(zo);
+  for (; i + 3 * stride < m; i += 4 * stride) {
+    double2 rv[4];
+    float2 zv[4], ov[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      rv[u] = ld2(r, i + u * stride);
+      zv[u] = __ldg(z2 + i + u * stride);
+      ov[u] = __ldg(o2 + i + u * stride);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      a[u] = fma(rv[u].y, (double)zv[u].y, fma(rv[u].x, (double)zv[u].x, a[u]));
+      c[u] = fma(rv[u].y, (double)ov[u].y, fma(rv[u].x, (double)ov[u].x, c[u]));
+    }
+  }
+  for (; i < m; i += stride) {
+    const double2 rv = ld2(r, i);
+    const float2 zv = __ldg(z2 + i), ov = __ldg(o2 + i);
+    a[0] = fma(rv.y, (double)zv.y, fma(rv.x, (double)zv.x, a[0]));
+    c[0] = fma(rv.y, (double)ov.y, fma(rv.x, (double)ov.x, c[0]));
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    a[0] = fma(r[n - 1], (double)z[n - 1], a[0]);
+    c[0] = fma(r[n - 1], (double)zo[n - 1], c[0]);
+  }
+  const double va = block_sum((a[0] + a[1]) + (a[2] + a[3]), sh);
+  const double vc = block_sum((c[0] + c[1]) + (c[2] + c[3]), sh);
+  if (threadIdx.x == 0) {
+    part_rz[blockIdx.x] = va;
+    part_rzo[blockIdx.x] = vc;
+  }
+}
+
+cudaError_t launch_cg_dots_f32(int64_t n, const double *r, const float *z, const float *zold,
+                               double *part_rz, double *part_rzo, cudaStream_t s) {
+  if (!al16(r) || ((uintptr_t)z & 7u) || ((uintptr_t)zold & 7u)) return cudaErrorNotSupported;
+  launch_k(cg_dots_f32_kernel, kRedBlocks, kRedThreads, 0, s, n, r, z, zold, part_rz, part_rzo);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// flexible p = z + beta p, beta = (rz_new - r . zold) / rz_old, with z read
+// from its FP32 copy (exact in FP64) and copied to zold_out for the next step,
+// and the two-term FP32 split of the new p: the values of cg_update_p_kernel
+__global__ void __launch_bounds__(kRedThreads)
+cg_update_p_f32_kernel(int64_t n, double *__restrict__ p, const float *__restrict__ z,
+                       const double *__restrict__ rz_old, const double *__restrict__ rz_partials,
+                       const double *__restrict__ rzold_partials, double *__restrict__ rz_out,
+                       float *__restrict__ zold_out, float *__restrict__ p_hi,
+                       float *__restrict__ p_lo, int n_rz) {
+  __shared__ double sh[32];
+  const double rz_new = block_sum_partials(rz_partials, n_rz, sh);
+  const double num = rz_new - block_sum_partials(rzold_partials, n_rz, sh);
+  const double beta = num / rz_old[0];
+  if (blockIdx.x == 0 && threadIdx.x == 0) rz_out[0] = rz_new;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t m = n >> 1;
+  double2 *p2 = reinterpret_cast<double2 *>(p);
+  const float2 *z2 = reinterpret_cast<const float2 *>(z);
+  float2 *zo2 = reinterpret_cast<float2 *>(zold_out);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    const float2 zi = __ldg(z2 + i);
+    const double2 pi = p2[i];
+    const double2 pn = make_double2(fma(beta, pi.x, (double)zi.x), fma(beta, pi.y, (double)zi.y));
+    p2[i] = pn;
+    zo2[i] = zi;
+    split_f32(pn.x, p_hi, p_lo, 2 * i);
+    split_f32(pn.y, p_hi, p_lo, 2 * i + 1);
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const float zi = z[n - 1];
+    const double pn = fma(beta, p[n - 1], (double)zi);
+    p[n - 1] = pn;
+    zold_out[n - 1] = zi;
+    split_f32(pn, p_hi, p_lo, n - 1);
+  }
+}
+
+cudaError_t launch_cg_update_p_f32(int64_t n, double *p, const float *z, const double *rz_old,
+                                   const double *rz_partials, const double *rzold_partials,
+                                   double *rz_out, float *zold_out, float *p_hi, float *p_lo,
+                                   int n_rz, cudaStream_t s) {
+  if (!al16(p) || ((uintptr_t)z & 7u) || ((uintptr_t)zold_out & 7u)) return cudaErrorNotSupported;
+  launch_k(cg_update_p_f32_kernel, kRedBlocks, kRedThreads, 0, s, n, p, z, rz_old, rz_partials,
+           rzold_partials, rz_out, zold_out, p_hi, p_lo, n_rz);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // End of one graph-resident CG step: ||r||^2 from the partials, iteration
 // count, and the loop condition (continue while the recurrence residual is
 // above tol * ||b||, p^T A p > 0 and fewer than max_iter steps were taken).

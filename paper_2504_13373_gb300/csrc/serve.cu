@@ -303,11 +303,13 @@ cudaError_t vcycle_b(Engine &e, const T *rhs, T *out) {
   const int N = ctx->N, K = e.K;
   const int tpre = ctx->opt.t_pre, tpost = ctx->opt.t_post;
   cudaStream_t s = e.s;
+  // levels kt .. N as the hierarchy's dense bottom operator, when it has one
+  const int kt = ctx->dtail_M ? ctx->dtail_k : N;
   std::vector<const T *> bk(N + 1);
   std::vector<T *> xk(N + 1);
   bk[0] = rhs;
   for (int k = 1; k <= N; ++k) bk[k] = P::b(e.lv[k]);
-  for (int k = 0; k < N; ++k) {
+  for (int k = 0; k < kt; ++k) {
     Level &l = ctx->L[k];
     LevelVec &v = e.lv[k];
     T *x = P::x(v), *x2 = P::x2(v);
@@ -325,9 +327,12 @@ cudaError_t vcycle_b(Engine &e, const T *rhs, T *out) {
     ECU(launch_bmv<T>(GASA_MV_ASSIGN, l.R.nrows, l.R.br, l.R.bc, l.R.rp, l.R.col, P::A(l.R),
                       P::r(v), nullptr, P::b(e.lv[k + 1]), K, s, l.R.nnzb));
   }
-  ECU(launch_bdense<T>(ctx->nc, ctx->coarse_inv, P::b(e.lv[N]), P::x(e.lv[N]), K, s));
-  xk[N] = P::x(e.lv[N]);
-  for (int k = N - 1; k >= 0; --k) {
+  if (kt < N)
+    ECU(launch_bdense<T>(ctx->dtail_n, ctx->dtail_M, P::b(e.lv[kt]), P::x(e.lv[kt]), K, s));
+  else
+    ECU(launch_bdense<T>(ctx->nc, ctx->coarse_inv, P::b(e.lv[N]), P::x(e.lv[N]), K, s));
+  xk[kt] = P::x(e.lv[kt]);
+  for (int k = kt - 1; k >= 0; --k) {
     Level &l = ctx->L[k];
     LevelVec &v = e.lv[k];
     T *x = xk[k];

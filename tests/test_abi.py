@@ -56,7 +56,9 @@ int main(void) {
   printf("gasa_server_stats %zu\n", sizeof(gasa_server_stats));
   P(gasa_options, gamma); P(gasa_options, seed); P(gasa_options, init_candidates);
   P(gasa_options, bulk_staging); P(gasa_options, matrix_free_levels);
-  P(gasa_options, hstar); P(gasa_options, delta);
+  P(gasa_options, hstar); P(gasa_options, delta); P(gasa_options, tail_kib);
+  P(gasa_options, grid_tail); P(gasa_options, wait_budget_s); P(gasa_options, fused_restriction);
+  P(gasa_options, dense_tail_dofs);
   P(gasa_setup_info, omega); P(gasa_setup_info, seconds); P(gasa_setup_info, device_bytes);
   P(gasa_bsr, val); P(gasa_bsr, on_device); P(gasa_solve_info, rel_residual);
   P(gasa_server_stats, peak_running); P(gasa_server_stats, graph_launches);
@@ -87,6 +89,11 @@ def test_struct_layouts_match_c(tmp_path):
         "gasa_options.matrix_free_levels": gasa.gasa_options.matrix_free_levels.offset,
         "gasa_options.hstar": gasa.gasa_options.hstar.offset,
         "gasa_options.delta": gasa.gasa_options.delta.offset,
+        "gasa_options.tail_kib": gasa.gasa_options.tail_kib.offset,
+        "gasa_options.grid_tail": gasa.gasa_options.grid_tail.offset,
+        "gasa_options.wait_budget_s": gasa.gasa_options.wait_budget_s.offset,
+        "gasa_options.fused_restriction": gasa.gasa_options.fused_restriction.offset,
+        "gasa_options.dense_tail_dofs": gasa.gasa_options.dense_tail_dofs.offset,
         "gasa_setup_info.omega": gasa.gasa_setup_info.omega.offset,
         "gasa_setup_info.seconds": gasa.gasa_setup_info.seconds.offset,
         "gasa_setup_info.device_bytes": gasa.gasa_setup_info.device_bytes.offset,
@@ -98,6 +105,17 @@ def test_struct_layouts_match_c(tmp_path):
     }
     for k, v in py.items():
         assert int(got[k]) == v, k
+
+
+def test_default_options():
+    """Section 6's smoothing counts, and the V-cycle's launch layout: fused
+    residual and restriction on, the dense bottom operator from 2,048 dofs,
+    the persistent and cluster tails off."""
+    gasa = _lib()
+    o = gasa.gasa_default_options()
+    assert (o.t_pre, o.t_post, o.q_power, o.restart) == (3, 3, 3, 30)
+    assert o.fused_restriction == 1 and o.dense_tail_dofs == 2048
+    assert o.grid_tail == 0 and o.tail_kib == 0 and o.bulk_staging == 0
 
 
 def test_status_strings_and_host_only_calls():

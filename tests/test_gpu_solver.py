@@ -106,12 +106,18 @@ def test_setup_hierarchy(name):
         gasa.gasa_destroy(ctx)
 
 
+# dense_tail_dofs: the library default (the coarse levels as one dense
+# operator where they are small) and 0 (every coarse step its own launch)
+DTAIL = [2048, 0]
+
+
+@pytest.mark.parametrize("dtail", DTAIL)
 @pytest.mark.parametrize("name", ["tiny", "c1", "tet_p2_4", "cd_q2_16", "cd3_4_peinf"])
-def test_vcycle(name):
+def test_vcycle(name, dtail):
     gasa = _gasa()
     H = oracle_setup(name)
     pr = problem(name)
-    ctx, _ = gpu_setup(name, keep=False)
+    ctx, _ = gpu_setup(name, keep=False, dense_tail_dofs=dtail)
     try:
         M = O.make_vcycle(H)
         want = M(pr.rhs)
@@ -135,14 +141,15 @@ def test_vcycle(name):
         gasa.gasa_destroy(ctx)
 
 
+@pytest.mark.parametrize("dtail", DTAIL)
 @pytest.mark.parametrize("name", ["tiny", "c1", "p3_16", "tet_p2_4"])
-def test_cg_solve(name):
+def test_cg_solve(name, dtail):
     gasa = _gasa()
     H = oracle_setup(name)
     pr = problem(name)
     ref = O.solve(H, pr.rhs, TOL, "cg", max_iter=5000)
     ref32 = O.solve(H, pr.rhs, TOL, "cg", precision="mixed32", max_iter=5000)
-    ctx, _ = gpu_setup(name, keep=False)
+    ctx, _ = gpu_setup(name, keep=False, dense_tail_dofs=dtail)
     try:
         x = np.zeros_like(pr.rhs)
         info = gasa.gasa_solve(ctx, pr.rhs, x, TOL)
@@ -284,10 +291,14 @@ def test_matrix_free_levels(name, kappa):
     gasa = _gasa()
     H = oracle_setup(name)
     pr = problem(name)
-    ctx0, info0 = gpu_setup(name, keep=False)
+    # the resident hierarchy is compared without the dense bottom operator,
+    # whose size depends on the first level it can start from
+    ctx0, info0 = gpu_setup(name, keep=False, dense_tail_dofs=0)
+    ctxm, infom = gpu_setup(name, keep=False, matrix_free_levels=kappa, dense_tail_dofs=0)
+    gasa.gasa_destroy(ctxm)
     ctx, info = gpu_setup(name, keep=False, matrix_free_levels=kappa)
     try:
-        assert info.device_bytes < info0.device_bytes
+        assert infom.device_bytes < info0.device_bytes
         want = O.make_vcycle(H, matrix_free_levels=kappa)(pr.rhs)
         z = to_dev(np.zeros_like(pr.rhs))
         gasa.gasa_vcycle(ctx, to_dev(pr.rhs), z)
@@ -368,8 +379,9 @@ def _real_index(sizes, s):
     return np.concatenate([i * s + np.arange(z) for i, z in enumerate(sizes)])
 
 
+@pytest.mark.parametrize("dtail", DTAIL)
 @pytest.mark.parametrize("name,hstar", [("p2_8", True), ("c1", True), ("uneq6", False)])
-def test_padded_levels(name, hstar):
+def test_padded_levels(name, hstar, dtail):
     """Unequal kept counts on a level, stored padded.  With the Section 4.3
     h*-step at the top every element is its own aggregate and keeps the
     singular vectors above 1e-3 sigma_1 (block sizes differ between units for
@@ -381,7 +393,7 @@ def test_padded_levels(name, hstar):
     pr = problem(name)
     H = O.setup(pr.A.row_ptr, pr.A.col, pr.A.val, pr.agg_of, B0=pr.B0, r=pr.r, dim=pr.dim,
                 hstar=hstar)
-    ctx, info = gpu_setup(name, keep=True, hstar=1 if hstar else 0)
+    ctx, info = gpu_setup(name, keep=True, hstar=1 if hstar else 0, dense_tail_dofs=dtail)
     tol = level_tolerances(H)
     try:
         assert info.n_levels == len(H.levels) == len(pr.agg_of) + 1 + (1 if hstar else 0)
@@ -464,7 +476,7 @@ def test_fused_tail(name):
     pr = problem(name)
     n_levels = len(H.levels)
     ctx_f, _ = gpu_setup(name, keep=False, tail_kib=1 << 20)
-    ctx_s, _ = gpu_setup(name, keep=False, tail_kib=0)
+    ctx_s, _ = gpu_setup(name, keep=False, tail_kib=0, dense_tail_dofs=0)
     try:
         for prec, oprec, tol in ((gasa.GASA_PREC_FP64, "fp64", 1e-12),
                                  (gasa.GASA_PREC_MIXED32, "fp32", 1e-5)):
@@ -523,7 +535,7 @@ def test_grid_tail(name):
         else:
             break
     ctx_g, _ = gpu_setup(name, keep=False, grid_tail=1)
-    ctx_s, _ = gpu_setup(name, keep=False, grid_tail=0)
+    ctx_s, _ = gpu_setup(name, keep=False, grid_tail=0, dense_tail_dofs=0)
     try:
         for prec, oprec, tol in ((gasa.GASA_PREC_FP64, "fp64", 1e-12),
                                  (gasa.GASA_PREC_MIXED32, "fp32", 1e-5)):
@@ -607,8 +619,8 @@ def test_fused_restriction(name):
     H = oracle_setup(name)
     pr = problem(name)
     tol = level_tolerances(H)
-    ctx_f, _ = gpu_setup(name, keep=False, fused_restriction=1)
-    ctx_u, _ = gpu_setup(name, keep=False, fused_restriction=0)
+    ctx_f, _ = gpu_setup(name, keep=False, fused_restriction=1, dense_tail_dofs=0)
+    ctx_u, _ = gpu_setup(name, keep=False, fused_restriction=0, dense_tail_dofs=0)
     try:
         kept = 0
         for k, L in enumerate(H.levels[:-1]):
@@ -632,11 +644,14 @@ def test_fused_restriction(name):
                 val = gasa.gasa_get_level(ctx_f, k, gasa.GASA_LV_RA_VAL,
                                           np.zeros(rp[-1] * sn * s)).reshape(-1, sn, s)
                 G = bsr_scipy(rp, col, val, units)
-                # a product's perturbation scales with |R_k| |A_k|, which the
-                # cancellation in R_k A_k (smooth rows against A_k) leaves larger
-                # than |R_k A_k| by the factor below
-                cancel = (abs(L.R) @ abs(L.A)).max() / abs(RA).max()
-                assert sparse_rel(G, RA) <= tol[k + 1] * max(1.0, cancel)
+                # entries of R_k within tol[k+1] max|R_k| and of A_k within
+                # tol[k] max|A_k| perturb an entry of R_k A_k by at most
+                # tol[k+1] max|R_k| ||A_k||_1 + tol[k] max|A_k| ||R_k||_inf
+                # (the cancellation in R_k A_k, smooth rows against A_k, keeps
+                # max|R_k A_k| well below both)
+                bound = (tol[k + 1] * abs(L.R).max() * np.asarray(abs(L.A).sum(axis=0)).max()
+                         + tol[k] * abs(L.A).max() * np.asarray(abs(L.R).sum(axis=1)).max())
+                assert sparse_rel(G, RA) <= bound / abs(RA).max()
         assert kept >= 1
         for prec, oprec, tl in ((gasa.GASA_PREC_FP64, "fp64", 1e-11),
                                 (gasa.GASA_PREC_MIXED32, "fp32", 1e-5),
@@ -660,3 +675,84 @@ def test_fused_restriction(name):
     finally:
         gasa.gasa_destroy(ctx_f)
         gasa.gasa_destroy(ctx_u)
+
+
+@pytest.mark.parametrize("name", ["c1", "p3_16", "p3_32", "cd_q2_16", "tet_p2_6", "uneq6"])
+def test_dense_tail(name):
+    """The bottom of the V-cycle as one dense operator (dense_tail_dofs, on by
+    default).  From the first level k >= 1 whose levels down to N - 1 hold at
+    most dense_tail_dofs stored dofs, Alg. 2 from u_k = 0 is the linear map
+    b_k -> u_k; setup forms it by running those steps on the unit vectors.  The
+    stored operator matches the oracle's V-cycle of the sub-hierarchy k .. N
+    applied to the unit vectors; V-cycles agree with the per-step ones
+    (dense_tail_dofs = 0) to rounding and with the oracle's; solves take the
+    same iterations (+-1)."""
+    gasa = _gasa()
+    H = oracle_setup(name)
+    pr = problem(name)
+    tol = level_tolerances(H)
+    N = len(H.levels) - 1
+    thr = gasa.gasa_default_options().dense_tail_dofs
+    ctx_d, _ = gpu_setup(name, keep=False)
+    ctx_s, _ = gpu_setup(name, keep=False, dense_tail_dofs=0)
+    try:
+        assert gasa.gasa_dense_tail_info(ctx_s) == {"first_level": N, "n": 0}
+        stored = [gasa.gasa_level_shape(ctx_d, k) for k in range(N + 1)]
+        want_k = N
+        for k in range(N - 1, 0, -1):
+            if stored[k]["units"] * stored[k]["s"] > thr:
+                break
+            want_k = k
+        info = gasa.gasa_dense_tail_info(ctx_d)
+        assert want_k < N, "every workload here has a small bottom"
+        assert info["first_level"] == want_k
+        kt = want_k
+        n = stored[kt]["units"] * stored[kt]["s"]
+        assert info["n"] == n
+        with pytest.raises(gasa.GasaError):
+            gasa.gasa_get_level(ctx_s, kt, gasa.GASA_LV_DENSE_TAIL, np.zeros(n * n))
+        M = gasa.gasa_get_level(ctx_d, kt, gasa.GASA_LV_DENSE_TAIL, np.zeros(n * n)).reshape(n, n)
+        sizes = gasa.gasa_get_level(ctx_d, kt, gasa.GASA_LV_SIZES,
+                                    np.zeros(stored[kt]["units"], np.int32))
+        idx = _real_index(sizes, stored[kt]["s"])
+        sub = O.Hierarchy(levels=H.levels[kt:], coarse=H.coarse, t_pre=H.t_pre, t_post=H.t_post)
+        V = O.make_vcycle(sub)
+        nr = idx.size
+        Mref = np.column_stack([V(np.eye(nr)[:, j]) for j in range(nr)])
+        assert rel_err(M[np.ix_(idx, idx)], Mref) <= 0.1 * tol[-1]
+        pad = np.setdiff1d(np.arange(n), idx)
+        if pad.size:
+            # padding entries of b never reach real entries of u
+            assert np.max(np.abs(M[np.ix_(idx, pad)])) == 0.0
+            assert np.max(np.abs(M[np.ix_(pad, idx)])) == 0.0
+        for prec, oprec, tl in ((gasa.GASA_PREC_FP64, "fp64", 1e-11),
+                                (gasa.GASA_PREC_MIXED32, "fp32", 1e-5),
+                                (gasa.GASA_PREC_MIXED16, "fp16", 1e-5)):
+            want = O.make_vcycle(H, oprec)(pr.rhs)
+            r = to_dev(pr.rhs)
+            zd, zs = to_dev(np.zeros_like(pr.rhs)), to_dev(np.zeros_like(pr.rhs))
+            gasa.gasa_vcycle(ctx_d, r, zd, prec)
+            gasa.gasa_vcycle(ctx_s, r, zs, prec)
+            zd, zs = to_host(zd), to_host(zs)
+            assert rel_err(zd, zs) <= tl, (oprec, rel_err(zd, zs))
+            assert rel_err(zd, want) <= (max(tl, 0.1 * tol[-1]) if oprec == "fp64" else 1e-4)
+        solver = gasa.GASA_SOLVER_CG if pr.solver == "cg" else gasa.GASA_SOLVER_GMRES
+        for prec in (gasa.GASA_PREC_FP64, gasa.GASA_PREC_MIXED32):
+            xd, xs = np.zeros_like(pr.rhs), np.zeros_like(pr.rhs)
+            inf_d = gasa.gasa_solve(ctx_d, pr.rhs, xd, TOL, prec)
+            inf_s = gasa.gasa_solve(ctx_s, pr.rhs, xs, TOL, prec)
+            assert inf_d.converged and inf_d.rel_residual <= TOL
+            assert abs(inf_d.iterations - inf_s.iterations) <= 1
+            assert np.linalg.norm(xd - xs) / np.linalg.norm(xs) <= 10 * TOL
+    finally:
+        gasa.gasa_destroy(ctx_d)
+        gasa.gasa_destroy(ctx_s)
+
+
+def test_dense_tail_option_range():
+    """dense_tail_dofs outside 0 .. 8192 is rejected by setup."""
+    gasa = _gasa()
+    for bad in (-1, 8193):
+        with pytest.raises(gasa.GasaError) as ei:
+            gpu_setup("tiny", keep=False, dense_tail_dofs=bad)
+        assert ei.value.status == gasa.GASA_ERR_INVALID_ARG
