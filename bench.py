@@ -40,13 +40,21 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per launch of the level-0 FP32 smoothing sweep
 # from one ncu capture each, valid while the kernel's source file hashes to
 # `src_sha`: the plain kernel and the bulk-copy staged one.
+# kernel classes of gasa_profile_read, timed by CUDA events in the host-driven loop
+PROFILE_CLASSES = ["level0_step", "level0_residual_restriction", "outer_Ap", "level0_first_step",
+                   "level0_prolongation"]
+
 NCU_TRAFFIC = {
     # captured on the 224x224 case of the same recipe (100,352 elements, 210.40 MB read +
     # 2.19 MB written per launch, two launches) and scaled to 131,072 elements
-    False: {"kernel": "jacobi_kernel<float,10,0>", "file": "kernels_mv.cu",
-            "src_sha": "11a0bfee7eb2b9dd", "bytes_per_launch": (210.40e6 + 2.19e6) * 131072 / 100352},
-    True: {"kernel": "jacobi_tma_kernel<float,10>", "file": "kernels_tma.cu",
-           "src_sha": "24cbc7a902631ea2", "bytes_per_launch": 274.87e6 + 6.52e6},
+    "plain": {"kernel": "jacobi_kernel<float,10,0>", "file": "kernels_mv.cu",
+              "src_sha": "11a0bfee7eb2b9dd",
+              "bytes_per_launch": (210.40e6 + 2.19e6) * 131072 / 100352},
+    "tma": {"kernel": "jacobi_tma_kernel<float,10>", "file": "kernels_tma.cu",
+            "src_sha": "24cbc7a902631ea2", "bytes_per_launch": 274.87e6 + 6.52e6},
+    # folded step x + c - (wD^-1 A) x: no capture of the current source yet
+    "folded": {"kernel": "bsr_mv_kernel<float,10,3>", "file": "kernels_mv.cu",
+               "src_sha": None, "bytes_per_launch": None},
 }
 
 
@@ -72,6 +80,9 @@ def parse():
                     help="with --profile-run: drive the CG loop from the host (per-kernel ncu)")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="with --profile-run: stop each solve after this many CG iterations")
+    ap.add_argument("--folded-smoother", type=int, default=-1, choices=[-1, 0, 1],
+                    help="level-0 steps as x + c - (wD^-1 A) x (1) or x + wD^-1 (b - A x) (0); "
+                         "-1: the library default")
     ap.add_argument("--dense-tail-dofs", type=int, default=-1,
                     help="coarse levels of at most this many dofs as one dense operator "
                          "(0: off); -1: the library default")
@@ -132,7 +143,7 @@ def level_shapes(gasa, ctx, n_levels):
     """gasa_level_shape per level, plus RA_nnzb: the blocks of R_k A_k where the
     fused restriction keeps it (0 elsewhere), and dense_tail: True on the first
     level of the dense bottom operator (levels k .. N as one dense product)."""
-    dt = gasa.gasa_dense_tail_info(ctx)
+    cyc = gasa.gasa_cycle_info(ctx)
     shapes = []
     for k in range(n_levels):
         sh = dict(gasa.gasa_level_shape(ctx, k))
@@ -144,7 +155,8 @@ def level_shapes(gasa, ctx, n_levels):
                 sh["RA_nnzb"] = int(rp[-1])
             except gasa.GasaError:
                 pass
-        sh["dense_tail"] = dt["n"] > 0 and k == dt["first_level"]
+        sh["dense_tail"] = cyc["dense_n"] > 0 and k == cyc["dense_first_level"]
+        sh["folded"] = k == 0 and cyc["folded"] == 1
         shapes.append(sh)
     return shapes
 
@@ -173,7 +185,8 @@ def iteration_bytes(shapes, precision, t_pre=3, t_post=3):
     (as mixed32 with FP16 level-0 A and w D^-1 plus one FP32 scale per
     block).  Where the hierarchy has a dense bottom from level kt, levels
     kt .. N cost one dense FP64 product (n_kt^2 * 8 bytes and the two
-    vectors).  Returns (total bytes, per-part dict)."""
+    vectors); with the folded level-0 smoother its later steps read W A and c
+    in place of A, W and b.  Returns (total bytes, per-part dict)."""
     N = len(shapes) - 1
     w = 8 if precision == "fp64" else 4
     parts = {}
@@ -192,12 +205,16 @@ def iteration_bytes(shapes, precision, t_pre=3, t_post=3):
         v = n * s * w
         R = sh["R_nnzb"] * (s * s1 * w) + 4 * sh["R_nnzb"] + 4 * (n1 + 1)
         P = sh["P_nnzb"] * (s * s1 * w) + 4 * sh["P_nnzb"] + 4 * (n + 1)
+        folded = bool(sh.get("folded")) and precision == "mixed32"
         first = W + 2 * v
         if k == 0 and precision == "mixed32":
             first = W + n * s * (8 + 4 + 4)      # reads the FP64 residual, writes x and its FP32 copy
+        if folded:
+            first += v                            # also keeps c = W b
         if first_done[k]:
             first = 0.0                           # taken by the restriction of the level above
-        sweeps = (t_pre - 1 + t_post) * (A + W + 3 * v)
+        # folded steps u + c - (W A) u read W A (A's size) and c, not A, W and b
+        sweeps = (t_pre - 1 + t_post) * ((A if folded else A + W) + 3 * v)
         ra = sh.get("RA_nnzb", 0)
         if ra and not (precision == "mixed16" and k == 0):
             # fused: b_{k+1} = R b - (R A) x, maybe with level k+1's first step
@@ -507,9 +524,14 @@ def serve_bench(gasa, n_requests, device=0):
             for f in (0.5, 1.5):
                 times = serving.arrival_times(seed, n_requests, f * sat)
                 wall, lat, its, worst = run(prec, times)
+                small = np.array([specs[m].dofs < 20000 for m in which])
                 res[f"open_loop_{f:g}x"] = {
                     "rate_per_s": f * sat, "solves_per_s": n_requests / wall,
-                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                    "p50_ms_meshes_under_2e4_dofs": (float(np.percentile(lat[small], 50))
+                                                     if small.any() else None),
+                    "per_mesh_p50_ms": {specs[m].name: float(np.percentile(lat[which == m], 50))
+                                        for m in range(len(specs)) if (which == m).any()}}
                 res["rel_residual_max"] = max(res["rel_residual_max"], worst)
             st1 = gasa.gasa_server_stats_read(srv)
             res["graph_launches"] = st1["graph_launches"] - st0["graph_launches"]
@@ -550,7 +572,7 @@ def measure_workload(gasa, pr, name, steps, warmup, device):
                             adj_ptr=pr.adj_ptr, adj_idx=pr.adj_idx, centroids=pr.centroids,
                             init_candidates=pr.B0)
     shapes = level_shapes(gasa, ctx, sinfo.n_levels)
-    dense_tail = gasa.gasa_dense_tail_info(ctx)
+    dense_tail = gasa.gasa_cycle_info(ctx)
     peak, peak_kind = hbm_peak()
     b = torch.from_numpy(pr.rhs).cuda(device)
     x = torch.zeros_like(b)
@@ -596,7 +618,7 @@ def measure_workload(gasa, pr, name, steps, warmup, device):
             "level_dofs": [int(sinfo.dofs[k]) for k in range(sinfo.n_levels)],
             "level_nnzb": [int(sinfo.nnzb[k]) for k in range(sinfo.n_levels)],
             "level_block": [int(sinfo.block[k]) for k in range(sinfo.n_levels)],
-            "dense_tail": dense_tail, "setup_s": sinfo.seconds, "steps": steps, "warmup": warmup, "precisions": out}
+            "cycle": dense_tail, "setup_s": sinfo.seconds, "steps": steps, "warmup": warmup, "precisions": out}
 
 
 def other_workloads(gasa, device, steps=1, warmup=1):
@@ -682,6 +704,8 @@ def ours_main(args, rank, world, local):
         opt.fused_restriction = args.fused_restriction
     if args.dense_tail_dofs >= 0:
         opt.dense_tail_dofs = args.dense_tail_dofs
+    if args.folded_smoother >= 0:
+        opt.folded_smoother = args.folded_smoother
     opt.bulk_staging = 1 if args.bulk_staging else 0
     sinfo = gasa.gasa_setup(ctx, A.row_ptr, A.col, A.val.ravel(), A.b, pr.agg_of, opt,
                             adj_ptr=pr.adj_ptr, adj_idx=pr.adj_idx, centroids=pr.centroids,
@@ -753,6 +777,7 @@ def ours_main(args, rank, world, local):
         # so this solve runs the same kernels from the host-driven loop)
         _, inf_prof, _, _ = timed(gasa.GASA_PREC_MIXED32, 1, profile=True)
         prof = gasa.gasa_profile_read(ctx, 0)
+        prof_all = {name: gasa.gasa_profile_read(ctx, c) for c, name in enumerate(PROFILE_CLASSES)}
         gasa.gasa_profile_enable(ctx, False)
     clocks = clk.summary()
     # true residual of the last solves, checked on the host
@@ -772,10 +797,11 @@ def ours_main(args, rank, world, local):
     value64 = world * args.steps / (ms_64 / 1e3)
     ms_k, n_k, bytes_k = prof
     achieved = (bytes_k / n_k) / (ms_k / n_k / 1e3) / 1e9 if n_k else None
-    ncu = NCU_TRAFFIC[bool(args.bulk_staging)]
-    traffic = ncu["bytes_per_launch"] if ncu["src_sha"] == src_hash(ncu["file"]) else None
     iters = [i.iterations for i in inf_mix]
     shapes = level_shapes(gasa, ctx, sinfo.n_levels)
+    sweep_form = "tma" if args.bulk_staging else ("folded" if shapes[0]["folded"] else "plain")
+    ncu = NCU_TRAFFIC[sweep_form]
+    traffic = ncu["bytes_per_launch"] if ncu["src_sha"] == src_hash(ncu["file"]) else None
 
     def iteration_roofline(prec, ms, infos):
         """algorithmic bytes of one CG iteration / (solve time / iterations)"""
@@ -818,7 +844,7 @@ def ours_main(args, rank, world, local):
             "workload": WORKLOAD if args.n == 256 else f"poisson2d_sipg_p3_tri_{args.n}x{args.n}",
             "dofs": n, "elements": A.n, "block": A.b, "nnzb": int(A.nnzb), "levels": sinfo.n_levels,
             "candidates": pr.r, "tol": TOL, "solver": "CG (flexible for mixed)",
-            "dense_tail": gasa.gasa_dense_tail_info(ctx),
+            "cycle": gasa.gasa_cycle_info(ctx),
             "l2": "inputs larger than L2 (A 419 MB FP64 / 209 MB FP32 per pass), no flush",
             "parallelism": f"replicas x{world}",
         },
@@ -835,12 +861,19 @@ def ours_main(args, rank, world, local):
         "p99_ms": float(np.percentile(per_mix, 99)),
         "setup_s": sinfo.seconds,
         "generate_s": t_gen,
-        "roofline": {"kernel": f"level-0 block-Jacobi sweep x + wD^-1(b - Ax), FP32 ({ncu['kernel']})",
+        "roofline": {"kernel": (f"level-0 block-Jacobi step x + c - (wD^-1 A) x, c = wD^-1 b, FP32 ({ncu['kernel']})"
+                                if sweep_form == "folded" else
+                                f"level-0 block-Jacobi step x + wD^-1(b - Ax), FP32 ({ncu['kernel']})"),
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None, "peak_kind": f"{peak_kind} hbm_gbs",
                      "traffic": traffic, "algorithmic_bytes_per_launch": bytes_k / n_k if n_k else None,
                      "launches": n_k, "avg_launch_us": ms_k / n_k * 1e3 if n_k else None},
         "roofline_iteration": roof_it,
+        "level0_kernels": {
+            name: {"avg_us": ms / n * 1e3, "launches": n, "algorithmic_bytes_per_launch": by / n,
+                   "achieved_gbs": by / n / (ms / n / 1e3) / 1e9,
+                   "frac": by / n / (ms / n / 1e3) / 1e9 / peak}
+            for name, (ms, n, by) in prof_all.items() if n},
         "error_vs_oracle": err_vs_oracle,
         "e2e": {"value": world * args.steps / e2e_s, "unit": "solves/s",
                 "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},

@@ -149,6 +149,15 @@ typedef struct {
                                 dense FP64 product (FP32 vectors in the FP32 cycle).  Results agree
                                 with the per-step cycle to rounding.  Not built when tail_kib or
                                 grid_tail is set.  0: off; default 2048; at most 8192. */
+  int32_t folded_smoother;   /* 1 (default): level 0 also stores w D_0^{-1} A_0 in FP32 (block row i
+                                multiplied by its block inverse, in A_0's pattern, formed in FP64),
+                                and the FP32 cycle's smoothing steps of Alg. 1 after the first run as
+                                u + c - (w D_0^{-1} A_0) u with c = w D_0^{-1} b, which the first
+                                step u = c leaves: the same step, without re-reading the block
+                                inverses (block sizes up to 16; the FP64 cycle and the FP16-block
+                                level 0 keep the plain step, measured faster there).  Results agree
+                                with the plain step to rounding.  0: the plain step
+                                u + w D^{-1} (b - A u). */
 } gasa_options;
 
 typedef struct {
@@ -224,8 +233,11 @@ enum {
   GASA_LV_RA_ROWPTR = 16,    /* R_k A_k (option fused_restriction), next-level rows x level-k units */
   GASA_LV_RA_COL = 17,
   GASA_LV_RA_VAL = 18,
-  GASA_LV_DENSE_TAIL = 19    /* first level k of the dense bottom (option dense_tail_dofs): its
+  GASA_LV_DENSE_TAIL = 19,   /* first level k of the dense bottom (option dense_tail_dofs): its
                                 n_k x n_k FP64 operator b_k -> u_k, row-major */
+  GASA_LV_WA = 20            /* level 0 with folded_smoother and keep_setup_data: w D_0^{-1} A_0
+                                in A_0's block pattern (nnzb x s x s, FP64; block row i
+                                multiplied by its block inverse) */
 };
 /* shape[0..7] = units, s_k, nnzb(A), P nnzb, R nnzb, s_{k+1}, r, dofs.  On a
  * level whose aggregates keep different counts (h*-step, or unequal
@@ -245,20 +257,24 @@ gasa_status gasa_level_shape(gasa_ctx *ctx, int32_t level, int64_t shape[8]);
  * unknown precision or a null pointer. */
 gasa_status gasa_tail_info(gasa_ctx *ctx, int32_t precision, int32_t out[3]);
 
-/* Dense bottom of the V-cycle (option dense_tail_dofs), shared by every
- * precision: out[0] = its first level k (n_levels - 1 when there is none),
- * out[1] = n_k, the operator's order (0 when there is none).
+/* Layout of the V-cycle as set up: out[0] = first level k of the dense bottom
+ * operator (option dense_tail_dofs; n_levels - 1 when there is none), out[1] =
+ * n_k, its order (0 when there is none), out[2] = 1 when level 0's FP32 smoothing
+ * steps run in the folded form (option folded_smoother), else 0.
  * GASA_ERR_STATE before a successful gasa_setup, GASA_ERR_INVALID_ARG for a
  * null pointer. */
-gasa_status gasa_dense_tail_info(gasa_ctx *ctx, int32_t out[2]);
+gasa_status gasa_cycle_info(gasa_ctx *ctx, int32_t out[3]);
 gasa_status gasa_get_level(gasa_ctx *ctx, int32_t level, int32_t what,
                            void *host_out, int64_t n_bytes);
 
 /* Per-kernel timing over CUDA events on the context stream (for the
- * benchmark's roofline): class 0 = level-0 smoothing sweeps
- * x + w D^{-1}(b - A x), 1 = level-0 residual SpMV, 2 = outer A*p SpMV,
- * 3 = level-0 first pre-smoothing step x = w D^{-1} b.  Enable, run, then
- * read total milliseconds, launches and algorithmic bytes moved. */
+ * benchmark's roofline; a profiled solve runs the host-driven loop): class 0 =
+ * level-0 smoothing steps after the first (x + w D^{-1}(b - A x), or the folded
+ * x + c - (w D^{-1} A) x), 1 = level-0 residual and restriction (the fused
+ * b_1 = R b - (R A) x where R A is stored, else the residual SpMV alone),
+ * 2 = outer A*p SpMV, 3 = level-0 first pre-smoothing step x = w D^{-1} b,
+ * 4 = level-0 prolongation x += P e.  Enable, run, then read total
+ * milliseconds, launches and algorithmic bytes moved. */
 gasa_status gasa_profile_enable(gasa_ctx *ctx, int32_t on);
 gasa_status gasa_profile_read(gasa_ctx *ctx, int32_t kernel_class, double *ms,
                               int64_t *launches, double *bytes);

@@ -45,6 +45,12 @@ struct Level {
   double *T = nullptr;
   DevBSR P, R;
   DevBSR RA;                  // R_k A_k (fused residual + restriction), rows of level k+1
+  // folded smoother (option folded_smoother, level 0): W A in A's block
+  // pattern, and c = W b of the current V-cycle
+  double *WA = nullptr;
+  float *WA32 = nullptr;
+  double *c = nullptr;
+  float *cf = nullptr;
   double *cand = nullptr, *cand_in = nullptr;
   std::vector<int> sweeps;
   double omega = 0.0, rho = 0.0;
@@ -134,7 +140,7 @@ struct gasa_ctx {
   int dtail_n = 0;
   // profiling
   bool prof = false;
-  ProfClass pc[4];
+  ProfClass pc[5];
   double setup_seconds = 0.0;
   int64_t device_bytes = 0;
 };

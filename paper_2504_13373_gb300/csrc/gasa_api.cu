@@ -150,6 +150,8 @@ template <typename T> struct Prec;
 template <> struct Prec<double> {
   static const double *A(const DevBSR &m) { return m.val; }
   static const double *W(const Level &l) { return l.W; }
+  static const double *WA(const Level &l) { return l.WA; }
+  static double *c(Level &l) { return l.c; }
   static double *x(Level &l) { return l.x; }
   static double *x2(Level &l) { return l.x2; }
   static double *b(Level &l) { return l.b; }
@@ -160,6 +162,8 @@ template <> struct Prec<double> {
 template <> struct Prec<float> {
   static const float *A(const DevBSR &m) { return m.val32; }
   static const float *W(const Level &l) { return l.W32; }
+  static const float *WA(const Level &l) { return l.WA32; }
+  static float *c(Level &l) { return l.cf; }
   static float *x(Level &l) { return l.xf; }
   static float *x2(Level &l) { return l.x2f; }
   static float *b(Level &l) { return l.bf; }
@@ -190,14 +194,16 @@ cudaError_t mf_apply(gasa_ctx *ctx, int k, int mode, const T *x, const T *b, T *
 
 // algorithmic bytes of one launch: w bytes per vector entry, wa bytes per
 // matrix value (FP16 blocks add one 4-byte scale per block)
-double sweep_bytes(const Level &l, int w, bool first, int wa = 0) {
+// folded: the step reads W A instead of A and W (and c instead of b); the
+// first step also writes c
+double sweep_bytes(const Level &l, int w, bool first, int wa = 0, bool folded = false) {
   if (wa == 0) wa = w;
   const double vec = (double)l.ndof * w;
   const double Wb = (double)l.n * l.s * l.s * wa + (wa == 2 ? 4.0 * l.n : 0.0);
-  if (first) return Wb + 2.0 * vec;
+  if (first) return Wb + (folded ? 3.0 : 2.0) * vec;
   const double Ab = (double)l.A.nnzb * l.s * l.s * wa + (wa == 2 ? 4.0 * l.A.nnzb : 0.0) +
                     4.0 * l.A.nnzb + 4.0 * (l.n + 1);
-  return Ab + Wb + 3.0 * vec;
+  return Ab + (folded ? 0.0 : Wb) + 3.0 * vec;
 }
 double spmv_bytes(const Level &l, int w, bool residual, int wa = 0) {
   if (wa == 0) wa = w;
@@ -585,6 +591,15 @@ cudaError_t restrict_fused(gasa_ctx *ctx, int k, const T *bk, const T *xk, T *bn
         return e;
       }
     }
+    if (blk_restrict_rect_applies(R.br, R.bc, R.nrows, nz)) {
+      const cudaError_t e = launch_blk_restrict_rect(R.nrows, R.br, R.bc, nz, R.rp, R.col,
+                                                     R.val32, RA.rp, RA.col, RA.val32, bk, xk,
+                                                     bnext, Wn, xn, s);
+      if (e != cudaErrorNotSupported) {
+        *first_done = Wn != nullptr && e == cudaSuccess;
+        return e;
+      }
+    }
     if (wide_applies(R.br, R.bc, R.nrows, nz)) {
       const cudaError_t e = launch_wide_restrict(R.nrows, R.br, R.bc, nz, R.rp, R.col, R.val32,
                                                  RA.rp, RA.col, RA.val32, bk, xk, bnext, Wn, xn, s);
@@ -641,10 +656,23 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false,
                       : (cluster ? ctx->tail_k0[pi] : (dense ? ctx->dtail_k : N));
   const int tpre = ctx->opt.t_pre, tpost = ctx->opt.t_post;
   const int w = (int)sizeof(T);
+  // level 0 smooths in the folded form u + c - (W A) u (not with FP16 blocks
+  // or the bulk-copy staged step)
+  const bool fold0 = std::is_same<T, float>::value && P::WA(ctx->L[0]) && !h16 && !ctx->L[0].tma;
   // level-0 smoothing step and residual; with h16 (FP32 V-cycle only) the
   // level-0 operator and block inverses are read from their FP16 blocks
   auto sweep = [&](int k, int mode, const T *xin, const T *bb, T *xo) -> cudaError_t {
     Level &l = ctx->L[k];
+    if (k == 0 && fold0) {
+      if (mode == JAC_SWEEP)
+        return launch_folded_sweep<T>(l.n, l.s, l.A.rp, l.A.col, P::WA(l), xin, P::c(l), xo, s);
+      // first step u = W b, kept as c for the later steps
+      cudaError_t e = launch_jacobi<T>(JAC_FIRST, l.n, l.s, l.A.rp, l.A.col, P::A(l.A), P::W(l),
+                                       nullptr, bb, xo, s, l.A.nnzb);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(P::c(l), xo, l.ndof * sizeof(T), cudaMemcpyDeviceToDevice, s);
+      return e;
+    }
     if constexpr (std::is_same<T, float>::value) {
       if (h16 && k == 0)
         return launch_jacobi_h16(mode, l.n, l.s, l.A.rp, l.A.col, l.A.val16, l.A.scale16, l.W16,
@@ -690,20 +718,26 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false,
     // pre-smoothing from zero
     if (tpre == 0) {
       CU(cudaMemsetAsync(x, 0, l.ndof * sizeof(T), s));
+      // the folded post-smoothing steps read c = W b
+      if (k == 0 && fold0)
+        CU(launch_jacobi<T>(JAC_FIRST, l.n, l.s, l.A.rp, l.A.col, P::A(l.A), P::W(l), nullptr,
+                            bk[0], P::c(l), s, l.A.nnzb));
     } else {
       cudaEvent_t e0;
       if (k == 0) prof_begin(ctx, 3, &e0);
       if constexpr (std::is_same<T, float>::value) {
-        if (k == 0 && fe) CU(launch_jacobi_first_conv(l.n, l.s, fe->r, fe->b32, P::W(l), x, s));
+        if (k == 0 && fe)
+          CU(launch_jacobi_first_conv(l.n, l.s, fe->r, fe->b32, P::W(l), x, s,
+                                      fold0 ? P::c(l) : nullptr));
         else if (!first_done[k]) CU(sweep(k, JAC_FIRST, nullptr, bk[k], x));
       } else {
         if (!first_done[k]) CU(sweep(k, JAC_FIRST, nullptr, bk[k], x));
       }
-      if (k == 0) prof_end(ctx, 3, sweep_bytes(l, w, true, wa));
+      if (k == 0) prof_end(ctx, 3, sweep_bytes(l, w, true, wa, fold0));
       for (int t = 1; t < tpre; ++t) {
         if (k == 0) prof_begin(ctx, 0, &e0);
         CU(sweep(k, JAC_SWEEP, x, bk[k], x2));
-        if (k == 0) prof_end(ctx, 0, sweep_bytes(l, w, false, wa));
+        if (k == 0) prof_end(ctx, 0, sweep_bytes(l, w, false, wa, k == 0 && fold0));
         std::swap(x, x2);
       }
     }
@@ -758,8 +792,16 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false,
     Level &l = ctx->L[k];
     T *x = xk[k];
     T *x2 = (x == P::x(l)) ? P::x2(l) : P::x(l);
-    CU(launch_bsr_mv<T>(GASA_MV_ADD, l.P.nrows, l.P.br, l.P.bc, l.P.rp, l.P.col, P::A(l.P),
-                        xk[k + 1], nullptr, x, s, l.P.nnzb));
+    {
+      cudaEvent_t e0;
+      if (k == 0) prof_begin(ctx, 4, &e0);
+      CU(launch_bsr_mv<T>(GASA_MV_ADD, l.P.nrows, l.P.br, l.P.bc, l.P.rp, l.P.col, P::A(l.P),
+                          xk[k + 1], nullptr, x, s, l.P.nnzb));
+      if (k == 0)
+        prof_end(ctx, 4, (double)l.P.nnzb * l.P.br * l.P.bc * w + 4.0 * l.P.nnzb +
+                             4.0 * (l.P.nrows + 1) + 2.0 * l.ndof * w +
+                             (double)ctx->L[1].ndof * w);
+    }
     if (tpost == 0 && k == 0) {
       CU(cudaMemcpyAsync(out, x, l.ndof * sizeof(T), cudaMemcpyDeviceToDevice, s));
     }
@@ -768,7 +810,7 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false,
       cudaEvent_t e0;
       if (k == 0) prof_begin(ctx, 0, &e0);
       CU(sweep(k, JAC_SWEEP, x, bk[k], dst));
-      if (k == 0) prof_end(ctx, 0, sweep_bytes(l, w, false, wa));
+      if (k == 0) prof_end(ctx, 0, sweep_bytes(l, w, false, wa, fold0));
       if (dst == x2) std::swap(x, x2);
       else x = dst;
     }
@@ -1910,6 +1952,21 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
     }
     ST(dalloc(ctx, &l.W32, (size_t)l.n * l.s * l.s));
     CU(launch_convert<double, float>((int64_t)l.n * l.s * l.s, l.W, l.W32, s));
+    // ---- folded smoother on level 0: W A in A's block pattern ----
+    if (k == 0 && opt->folded_smoother && l.s <= 16) {
+      const size_t nv = (size_t)l.A.nnzb * l.s * l.s;
+      ST(dalloc(ctx, &l.WA, nv));
+      CU(launch_fold_block_rows(l.n, l.s, l.A.rp, l.W, l.A.val, l.WA, s));
+      ST(dalloc(ctx, &l.WA32, nv));
+      CU(launch_convert<double, float>((int64_t)nv, l.WA, l.WA32, s));
+      if (!keep) {
+        // the FP64 cycle keeps the plain step: the FP64 copy is inspection data
+        CU(cudaStreamSynchronize(s));
+        dfree(ctx, l.WA);
+        ctx->device_bytes -= (int64_t)(nv * sizeof(double));
+        l.WA = nullptr;
+      }
+    }
   }
   dfree(ctx, B);
   dfree(ctx, B2);
@@ -1948,6 +2005,7 @@ gasa_status setup_impl(gasa_ctx *ctx, const gasa_bsr *Ain, const int32_t *adj_pt
     ST(dalloc(ctx, &l.x2f, (size_t)l.ndof));
     ST(dalloc(ctx, &l.bf, (size_t)l.ndof));
     ST(dalloc(ctx, &l.rf, (size_t)l.ndof));
+    if (l.WA32) ST(dalloc(ctx, &l.cf, (size_t)l.ndof));
   }
   const int64_t n = ctx->L[0].ndof;
   for (double **p : {&ctx->kx, &ctx->kr, &ctx->kz, &ctx->kp, &ctx->kq, &ctx->kzold, &ctx->kb, &ctx->kt})
@@ -2121,6 +2179,7 @@ void gasa_default_options(gasa_options *opt) {
   opt->wait_budget_s = 0.0;
   opt->fused_restriction = 1;
   opt->dense_tail_dofs = 2048;
+  opt->folded_smoother = 1;
 }
 
 gasa_status gasa_create(gasa_ctx **out, int32_t device, void *stream) {
@@ -2260,12 +2319,13 @@ gasa_status gasa_tail_info(gasa_ctx *ctx, int32_t precision, int32_t out[3]) {
   return GASA_OK;
 }
 
-gasa_status gasa_dense_tail_info(gasa_ctx *ctx, int32_t out[2]) {
+gasa_status gasa_cycle_info(gasa_ctx *ctx, int32_t out[3]) {
   if (!ctx || !out) return GASA_ERR_INVALID_ARG;
   if (!ctx->ready) return fail(ctx, GASA_ERR_STATE, "no hierarchy");
   const bool on = ctx->dtail_M != nullptr;
   out[0] = on ? ctx->dtail_k : ctx->N;
   out[1] = on ? ctx->dtail_n : 0;
+  out[2] = (ctx->L[0].WA32 && !ctx->L[0].tma) ? 1 : 0;
   return GASA_OK;
 }
 
@@ -2314,6 +2374,9 @@ gasa_status gasa_get_level(gasa_ctx *ctx, int32_t level, int32_t what, void *hos
         bytes = 8 * (int64_t)ctx->dtail_n * ctx->dtail_n;
       }
       break;
+    case GASA_LV_WA:
+      if (l.WA) { src = l.WA; bytes = 8 * l.A.nnzb * l.s * l.s; }
+      break;
     case GASA_LV_SIZES: {
       if (n_bytes < 4 * (int64_t)l.n) return fail(ctx, GASA_ERR_INVALID_ARG, "output buffer too small");
       int32_t *o = static_cast<int32_t *>(host_out);
@@ -2344,7 +2407,7 @@ gasa_status gasa_profile_enable(gasa_ctx *ctx, int32_t on) {
 
 gasa_status gasa_profile_read(gasa_ctx *ctx, int32_t cls, double *ms, int64_t *launches,
                               double *bytes) {
-  if (!ctx || cls < 0 || cls > 3) return GASA_ERR_INVALID_ARG;
+  if (!ctx || cls < 0 || cls > 4) return GASA_ERR_INVALID_ARG;
   CU(cudaStreamSynchronize(ctx->stream));
   ProfClass &p = ctx->pc[cls];
   double tot = 0.0;

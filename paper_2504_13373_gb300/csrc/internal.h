@@ -84,6 +84,14 @@ cudaError_t launch_blk_restrict(int n_brows, int bs, int64_t nnzb, const int *rr
                                 const int *acol, const float *aval, const float *b,
                                 const float *x, float *y, const float *Wn, float *xn,
                                 cudaStream_t s);
+// the same with br x bc blocks from the finest level (br 4 or 8 coarse rows,
+// bc 9 or 10 fine columns); cudaErrorNotSupported for other shapes
+bool blk_restrict_rect_applies(int br, int bc, int n_brows, int64_t nnzb);
+cudaError_t launch_blk_restrict_rect(int n_brows, int br, int bc, int64_t nnzb, const int *rrp,
+                                     const int *rcol, const float *rval, const int *arp,
+                                     const int *acol, const float *aval, const float *b,
+                                     const float *x, float *y, const float *Wn, float *xn,
+                                     cudaStream_t s);
 // op 0/1/2: y = A x, y = b - A x, y += A x; op 3: y = x + W (b - A x).
 // cudaErrorNotSupported when the shape or the alignment does not fit.
 template <typename T>
@@ -109,7 +117,19 @@ cudaError_t launch_jacobi(int mode, int n_units, int bs, const int *rp, const in
 // alignment does not fit).
 int jacobi_grid(int n_units, int bs);
 cudaError_t launch_jacobi_first_conv(int n_units, int bs, const double *bd, float *b32,
-                                     const float *W, float *xo, cudaStream_t s);
+                                     const float *W, float *xo, cudaStream_t s,
+                                     float *c_out = nullptr);
+
+// Smoothing step of Alg. 1 with the block inverse folded into the operator:
+// xo = x + c - (W A) x, where WA holds W_i A_ij in A's block pattern and
+// c = W b (one thread per scalar row, no exchange between the rows of a unit)
+constexpr int kMvFolded = 3;   // internal product mode next to GASA_MV_*
+template <typename T>
+cudaError_t launch_folded_sweep(int n_units, int bs, const int *rp, const int *col, const T *WA,
+                                const T *x, const T *c, T *xo, cudaStream_t s);
+// WA = W A block row by block row: block k of block row i becomes W_i A_k (FP64)
+cudaError_t launch_fold_block_rows(int n_units, int bs, const int *rp, const double *W,
+                                   const double *A, double *WA, cudaStream_t s);
 
 // multi-column relaxation x_c <- x_c - W A x_c for `nc` columns given by
 // device tables of column base pointers (each column n_units*bs long).

@@ -146,13 +146,14 @@ bsr_blk_kernel(int n_brows, const int *__restrict__ rp, const int *__restrict__ 
   else y[t] = yt + v;
 }
 
-// Fused residual and restriction of Alg. 2 on a coarse level with s x s
-// blocks: for coarse unit u, y_u = sum_j R_uj b_j - sum_j (R A)_uj x_j, the
-// vector R (b - A x) formed without the fine residual; with Wn also the
+// Fused residual and restriction of Alg. 2 with S x SC blocks (S coarse
+// rows, SC fine columns; SC = S on the coarse levels, SC up to 16 from the
+// finest level): for coarse unit u, y_u = sum_j R_uj b_j - sum_j (R A)_uj x_j,
+// the vector R (b - A x) formed without the fine residual; with Wn also the
 // next level's first smoothing step xn_u = Wn_u y_u from zero (every lane of
-// the team holds all s entries of y_u after the team sum).  One block per
+// the team holds all S entries of y_u after the team sum).  One block per
 // lane at a time, team sums as in bsr_blk_kernel.
-template <typename T, int S, int TL>
+template <typename T, int S, int SC, int TL>
 __global__ void __launch_bounds__(256)
 blk_restrict_kernel(int n_brows, const int *__restrict__ rrp, const int *__restrict__ rcol,
                     const T *__restrict__ rval, const int *__restrict__ arp,
@@ -170,26 +171,26 @@ blk_restrict_kernel(int n_brows, const int *__restrict__ rrp, const int *__restr
   for (int r = 0; r < S; ++r) acc[r] = T(0);
   if (u < n_brows) {
     for (int k = __ldg(rrp + u) + l; k < __ldg(rrp + u + 1); k += TL) {
-      T a0[S * S], v0[S];
-      load_run<T, S * S>(rval + (size_t)k * S * S, a0);
-      load_run<T, S>(b + (size_t)__ldg(rcol + k) * S, v0);
+      T a0[S * SC], v0[SC];
+      load_run<T, S * SC>(rval + (size_t)k * S * SC, a0);
+      load_run<T, SC>(b + (size_t)__ldg(rcol + k) * SC, v0);
 #pragma unroll
       for (int r = 0; r < S; ++r) {
         T s0 = T(0);
 #pragma unroll
-        for (int c = 0; c < S; ++c) s0 = fma(a0[r * S + c], v0[c], s0);
+        for (int c = 0; c < SC; ++c) s0 = fma(a0[r * SC + c], v0[c], s0);
         acc[r] += s0;
       }
     }
     for (int k = __ldg(arp + u) + l; k < __ldg(arp + u + 1); k += TL) {
-      T a0[S * S], v0[S];
-      load_run<T, S * S>(aval + (size_t)k * S * S, a0);
-      load_run<T, S>(x + (size_t)__ldg(acol + k) * S, v0);
+      T a0[S * SC], v0[SC];
+      load_run<T, S * SC>(aval + (size_t)k * S * SC, a0);
+      load_run<T, SC>(x + (size_t)__ldg(acol + k) * SC, v0);
 #pragma unroll
       for (int r = 0; r < S; ++r) {
         T s0 = T(0);
 #pragma unroll
-        for (int c = 0; c < S; ++c) s0 = fma(a0[r * S + c], v0[c], s0);
+        for (int c = 0; c < SC; ++c) s0 = fma(a0[r * SC + c], v0[c], s0);
         acc[r] -= s0;
       }
     }
@@ -277,7 +278,7 @@ cudaError_t blk_launch(int n_brows, int bs, int64_t nnzb, const int *rp, const i
   }
 }
 
-template <int S>
+template <int S, int SC = S>
 cudaError_t blk_restrict_s(int n_brows, int64_t nnzb, const int *rrp, const int *rcol,
                            const float *rval, const int *arp, const int *acol, const float *aval,
                            const float *b, const float *x, float *y, const float *Wn, float *xn,
@@ -286,14 +287,14 @@ cudaError_t blk_restrict_s(int n_brows, int64_t nnzb, const int *rrp, const int 
   const int grid = div_up((long long)n_brows * TL, 256);
 #define GASA_BLK_RTL(V)                                                                     \
   case V:                                                                                   \
-    launch_k(blk_restrict_kernel<float, S, (V < S ? 8 : V)>, grid, 256, 0, s, n_brows, rrp,  \
-             rcol, rval, arp, acol, aval, b, x, y, Wn, xn);                                 \
+    launch_k(blk_restrict_kernel<float, S, SC, (V < S ? 8 : V)>, grid, 256, 0, s, n_brows,  \
+             rrp, rcol, rval, arp, acol, aval, b, x, y, Wn, xn);                            \
     break;
   switch (TL) {
     GASA_BLK_RTL(4) GASA_BLK_RTL(8) GASA_BLK_RTL(16) GASA_BLK_RTL(32)
     default:
-      launch_k(blk_restrict_kernel<float, S, 64>, grid, 256, 0, s, n_brows, rrp, rcol, rval, arp,
-               acol, aval, b, x, y, Wn, xn);
+      launch_k(blk_restrict_kernel<float, S, SC, 64>, grid, 256, 0, s, n_brows, rrp, rcol, rval,
+               arp, acol, aval, b, x, y, Wn, xn);
       break;
   }
 #undef GASA_BLK_RTL
@@ -307,6 +308,28 @@ bool aligned_to(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 bool blk_applies(int bs, int n_brows, int64_t nnzb) {
   return bs >= 2 && bs <= 8 && n_brows > 0 && nnzb >= 6LL * n_brows;
+}
+
+// rectangular blocks from the finest level: br coarse rows (4 or 8) by bc
+// fine columns (9 or 10), with at least six blocks of R and R A per row
+bool blk_restrict_rect_applies(int br, int bc, int n_brows, int64_t nnzb) {
+  return (br == 4 || br == 8) && (bc == 9 || bc == 10) && n_brows > 0 && nnzb >= 6LL * n_brows;
+}
+
+cudaError_t launch_blk_restrict_rect(int n_brows, int br, int bc, int64_t nnzb, const int *rrp,
+                                     const int *rcol, const float *rval, const int *arp,
+                                     const int *acol, const float *aval, const float *b,
+                                     const float *x, float *y, const float *Wn, float *xn,
+                                     cudaStream_t s) {
+  // 16-byte block runs and 8-byte x runs (bc = 10), else 4-byte loads
+  if (!blk_restrict_rect_applies(br, bc, n_brows, nnzb)) return cudaErrorNotSupported;
+  if (br == 4 && bc == 10)
+    return blk_restrict_s<4, 10>(n_brows, nnzb, rrp, rcol, rval, arp, acol, aval, b, x, y, Wn, xn, s);
+  if (br == 4 && bc == 9)
+    return blk_restrict_s<4, 9>(n_brows, nnzb, rrp, rcol, rval, arp, acol, aval, b, x, y, Wn, xn, s);
+  if (br == 8 && bc == 10)
+    return blk_restrict_s<8, 10>(n_brows, nnzb, rrp, rcol, rval, arp, acol, aval, b, x, y, Wn, xn, s);
+  return blk_restrict_s<8, 9>(n_brows, nnzb, rrp, rcol, rval, arp, acol, aval, b, x, y, Wn, xn, s);
 }
 
 cudaError_t launch_blk_restrict(int n_brows, int bs, int64_t nnzb, const int *rrp,

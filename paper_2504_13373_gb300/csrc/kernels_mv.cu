@@ -45,6 +45,7 @@ bsr_mv_kernel(int n_brows, int br, const int *__restrict__ rp, const int *__rest
   }
   if (MODE == GASA_MV_ASSIGN) y[t] = acc;
   else if (MODE == GASA_MV_RESIDUAL) y[t] = b[t] - acc;
+  else if (MODE == kMvFolded) y[t] = x[t] + (b[t] - acc);
   else y[t] += acc;
 }
 
@@ -67,6 +68,7 @@ bsr_mv_generic(int n_brows, int br, int bc, const int *__restrict__ rp,
   }
   if (MODE == GASA_MV_ASSIGN) y[t] = acc;
   else if (MODE == GASA_MV_RESIDUAL) y[t] = b[t] - acc;
+  else if (MODE == kMvFolded) y[t] = x[t] + (b[t] - acc);
   else y[t] += acc;
 }
 
@@ -320,6 +322,18 @@ template cudaError_t launch_bsr_mv<float>(int, int, int, int, const int *, const
                                           const float *, const float *, const float *, float *,
                                           cudaStream_t, int64_t);
 
+template <typename T>
+cudaError_t launch_folded_sweep(int n_units, int bs, const int *rp, const int *col, const T *WA,
+                                const T *x, const T *c, T *xo, cudaStream_t s) {
+  return mv_dispatch<T, kMvFolded>(n_units, bs, bs, rp, col, WA, x, c, xo, s);
+}
+template cudaError_t launch_folded_sweep<double>(int, int, const int *, const int *, const double *,
+                                                 const double *, const double *, double *,
+                                                 cudaStream_t);
+template cudaError_t launch_folded_sweep<float>(int, int, const int *, const int *, const float *,
+                                                const float *, const float *, float *,
+                                                cudaStream_t);
+
 // ----------------------------------------------------------------------------
 // y = A x in double-single arithmetic (the outer Krylov product of the
 // mixed-precision solve).  A and x arrive as exact two-term FP32 splits,
@@ -518,7 +532,8 @@ jacobi_kernel(int n_units, const int *__restrict__ rp, const int *__restrict__ c
 template <int BS>
 __global__ void __launch_bounds__(256)
 jacobi_first_conv_kernel(int n_units, const double *__restrict__ bd, float *__restrict__ b32,
-                         const float *__restrict__ Wm, float *__restrict__ xo) {
+                         const float *__restrict__ Wm, float *__restrict__ xo,
+                         float *__restrict__ c_out) {
   __shared__ float res[256];
   constexpr int RPB = 256 / BS;
   constexpr int W = RowVec<float, BS>::value;
@@ -543,18 +558,19 @@ jacobi_first_conv_kernel(int n_units, const double *__restrict__ bd, float *__re
 #pragma unroll
   for (int c = 0; c < BS; ++c) out = fmaf(wv[c], res[li * BS + c], out);
   xo[row] = out;
+  if (c_out) c_out[row] = out;
 }
 
 int jacobi_grid(int n_units, int bs) { return div_up(n_units, 256 / bs); }
 
 cudaError_t launch_jacobi_first_conv(int n_units, int bs, const double *bd, float *b32,
-                                     const float *W, float *xo, cudaStream_t s) {
+                                     const float *W, float *xo, cudaStream_t s, float *c_out) {
   if (n_units == 0) return cudaSuccess;
   if (!aligned16(W) || bs < 1 || bs > 16) return cudaErrorNotSupported;
   const int grid = jacobi_grid(n_units, bs);
 #define GASA_FC_CASE(BS)                                                                      \
   case BS:                                                                                    \
-    launch_k(jacobi_first_conv_kernel<BS>, grid, 256, 0, s, n_units, bd, b32, W, xo);         \
+    launch_k(jacobi_first_conv_kernel<BS>, grid, 256, 0, s, n_units, bd, b32, W, xo, c_out);  \
     break;
   switch (bs) {
     GASA_FC_CASE(1) GASA_FC_CASE(2) GASA_FC_CASE(3) GASA_FC_CASE(4) GASA_FC_CASE(5)
@@ -846,38 +862,47 @@ cudaError_t launch_bsr_mm(int n_brows, int br, int bc, const int *rp, const int 
 }
 
 // ----------------------------------------------------------------------------
-// dense y = A x (coarsest level, A = A_N^{-1} row-major, FP64 arithmetic)
+// dense y = A x (coarsest level A = A_N^{-1}, or the dense bottom operator of
+// the V-cycle; A row-major FP64, FP64 arithmetic): a CTA of 256 threads per
+// row, thread t sums columns t, t + 256, ... in order (eight in flight), then
+// a warp tree and the eight warp sums in order
 // ----------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256)
 dense_mv_kernel(int n, const double *__restrict__ A, const T *__restrict__ x,
                 T *__restrict__ y) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= n) return;
-  const double *a = A + (size_t)warp * n;
+  __shared__ double sh[8];
+  const int row = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double *a = A + (size_t)row * n;
   double acc = 0.0;
-  // lane l sums columns l, l + 32, ... in order, four of them in flight
-  int j = lane;
-  for (; j + 96 < n; j += 128) {
-    const double a0 = __ldg(a + j), a1 = __ldg(a + j + 32), a2 = __ldg(a + j + 64),
-                 a3 = __ldg(a + j + 96);
-    const double x0 = (double)__ldg(x + j), x1 = (double)__ldg(x + j + 32),
-                 x2 = (double)__ldg(x + j + 64), x3 = (double)__ldg(x + j + 96);
-    acc = fma(a0, x0, acc);
-    acc = fma(a1, x1, acc);
-    acc = fma(a2, x2, acc);
-    acc = fma(a3, x3, acc);
+  int j = threadIdx.x;
+  for (; j + 7 * 256 < n; j += 8 * 256) {
+    double av[8], xv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      av[u] = __ldg(a + j + u * 256);
+      xv[u] = (double)__ldg(x + j + u * 256);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc = fma(av[u], xv[u], acc);
   }
-  for (; j < n; j += 32) acc = fma(__ldg(a + j), (double)__ldg(x + j), acc);
+  for (; j < n; j += 256) acc = fma(__ldg(a + j), (double)__ldg(x + j), acc);
   acc = warp_sum(acc);
-  if (lane == 0) y[warp] = (T)acc;
+  if (lane == 0) sh[wid] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) v += sh[w];
+    y[row] = (T)v;
+  }
 }
 
 template <typename T>
 cudaError_t launch_dense_mv(int n, const double *A, const T *x, T *y, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  launch_k(dense_mv_kernel<T>, div_up((long long)n * 32, 256), 256, 0, s, n, A, x, y); note_launch();
+  launch_k(dense_mv_kernel<T>, n, 256, 0, s, n, A, x, y); note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_dense_mv<double>(int, const double *, const double *, double *,

@@ -205,6 +205,35 @@ __global__ void scale_kernel(int64_t n, double a, double *x) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) x[i] *= a;
 }
+// WA = W A with W block diagonal: block k of block row i becomes W_i A_k
+// (bs x bs times bs x bs, FP64); one CTA per block row, threads over the
+// row's block entries
+__global__ void __launch_bounds__(256)
+fold_block_rows_kernel(int bs, const int *__restrict__ rp, const double *__restrict__ W,
+                       const double *__restrict__ A, double *__restrict__ WA) {
+  const int i = blockIdx.x;
+  const int beg = rp[i], end = rp[i + 1];
+  const int bb = bs * bs;
+  const double *w = W + (size_t)i * bb;
+  const int64_t tot = (int64_t)(end - beg) * bb;
+  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int64_t k = beg + e / bb;
+    const int rc = (int)(e % bb), r = rc / bs, c = rc - r * bs;
+    const double *a = A + (size_t)k * bb;
+    double acc = 0.0;
+    for (int q = 0; q < bs; ++q) acc = fma(w[r * bs + q], a[q * bs + c], acc);
+    WA[(size_t)k * bb + rc] = acc;
+  }
+}
+
+cudaError_t launch_fold_block_rows(int n_units, int bs, const int *rp, const double *W,
+                                   const double *A, double *WA, cudaStream_t s) {
+  if (n_units == 0) return cudaSuccess;
+  launch_k(fold_block_rows_kernel, n_units, 256, 0, s, bs, rp, W, A, WA);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_scale(int64_t n, double a, double *x, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   scale_kernel<<<kRedBlocks * 2, 256, 0, s>>>(n, a, x); note_launch();

@@ -249,7 +249,7 @@ __device__ void tail_jacobi(int op, const TailLevel<T> &L, int m, const int *rp,
 }
 
 // x_N = A_N^{-1} b_N in FP64 arithmetic, a warp per owned coarse unit and,
-// for each of its rows, lanes over the columns (the order of dense_mv_kernel)
+// for each of its rows, lanes over the columns
 template <typename T>
 __device__ void tail_dense(const TailPlan<T> &pl, const double *Crows, const Dist &d, int c,
                            int wib, int lane) {

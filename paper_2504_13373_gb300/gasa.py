@@ -37,12 +37,12 @@ GASA_MAX_LEVELS = 24
 (GASA_LV_A_ROWPTR, GASA_LV_A_COL, GASA_LV_A_VAL, GASA_LV_P_ROWPTR, GASA_LV_P_COL, GASA_LV_P_VAL,
  GASA_LV_R_ROWPTR, GASA_LV_R_COL, GASA_LV_R_VAL, GASA_LV_T_VAL, GASA_LV_W, GASA_LV_CAND,
  GASA_LV_SWEEPS, GASA_LV_COARSE_INV, GASA_LV_CAND_IN, GASA_LV_SIZES, GASA_LV_RA_ROWPTR,
- GASA_LV_RA_COL, GASA_LV_RA_VAL, GASA_LV_DENSE_TAIL) = range(20)
+ GASA_LV_RA_COL, GASA_LV_RA_VAL, GASA_LV_DENSE_TAIL, GASA_LV_WA) = range(21)
 
 # every symbol include/gasa.h declares
 EXPORTS = [
     "gasa_default_options", "gasa_create", "gasa_setup", "gasa_solve", "gasa_vcycle",
-    "gasa_level_shape", "gasa_tail_info", "gasa_dense_tail_info", "gasa_get_level", "gasa_profile_enable", "gasa_profile_read",
+    "gasa_level_shape", "gasa_tail_info", "gasa_cycle_info", "gasa_get_level", "gasa_profile_enable", "gasa_profile_read",
     "gasa_destroy", "gasa_status_string", "gasa_last_error", "gasa_bsr_mv", "gasa_bsr_mv_f32", "gasa_bsr_mv_ds",
     "gasa_jacobi_sweep", "gasa_jacobi_sweep_f32", "gasa_block_inverse", "gasa_power_estimate",
     "gasa_relax_candidates", "gasa_tentative", "gasa_dense_inverse", "gasa_kernel_launches",
@@ -73,7 +73,7 @@ class gasa_options(ctypes.Structure):
                 ("bulk_staging", c_i32), ("matrix_free_levels", c_i32), ("hstar", c_i32),
                 ("delta", c_dbl), ("tail_kib", c_i32), ("grid_tail", c_i32),
                 ("wait_budget_s", c_dbl), ("fused_restriction", c_i32),
-                ("dense_tail_dofs", c_i32)]
+                ("dense_tail_dofs", c_i32), ("folded_smoother", c_i32)]
 
 
 class gasa_setup_info(ctypes.Structure):
@@ -246,10 +246,10 @@ def gasa_tail_info(ctx, precision):
     return {"first_level": int(out[0]), "cluster": int(out[1]), "coarse_inside": int(out[2])}
 
 
-def gasa_dense_tail_info(ctx):
-    out = (c_i32 * 2)()
-    _check(load().gasa_dense_tail_info(ctx, out), ctx)
-    return {"first_level": int(out[0]), "n": int(out[1])}
+def gasa_cycle_info(ctx):
+    out = (c_i32 * 3)()
+    _check(load().gasa_cycle_info(ctx, out), ctx)
+    return {"dense_first_level": int(out[0]), "dense_n": int(out[1]), "folded": int(out[2])}
 
 
 def gasa_get_level(ctx, level, what, out: np.ndarray):

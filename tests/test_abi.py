@@ -58,7 +58,7 @@ int main(void) {
   P(gasa_options, bulk_staging); P(gasa_options, matrix_free_levels);
   P(gasa_options, hstar); P(gasa_options, delta); P(gasa_options, tail_kib);
   P(gasa_options, grid_tail); P(gasa_options, wait_budget_s); P(gasa_options, fused_restriction);
-  P(gasa_options, dense_tail_dofs);
+  P(gasa_options, dense_tail_dofs); P(gasa_options, folded_smoother);
   P(gasa_setup_info, omega); P(gasa_setup_info, seconds); P(gasa_setup_info, device_bytes);
   P(gasa_bsr, val); P(gasa_bsr, on_device); P(gasa_solve_info, rel_residual);
   P(gasa_server_stats, peak_running); P(gasa_server_stats, graph_launches);
@@ -94,6 +94,7 @@ def test_struct_layouts_match_c(tmp_path):
         "gasa_options.wait_budget_s": gasa.gasa_options.wait_budget_s.offset,
         "gasa_options.fused_restriction": gasa.gasa_options.fused_restriction.offset,
         "gasa_options.dense_tail_dofs": gasa.gasa_options.dense_tail_dofs.offset,
+        "gasa_options.folded_smoother": gasa.gasa_options.folded_smoother.offset,
         "gasa_setup_info.omega": gasa.gasa_setup_info.omega.offset,
         "gasa_setup_info.seconds": gasa.gasa_setup_info.seconds.offset,
         "gasa_setup_info.device_bytes": gasa.gasa_setup_info.device_bytes.offset,
@@ -110,11 +111,11 @@ def test_struct_layouts_match_c(tmp_path):
 def test_default_options():
     """Section 6's smoothing counts, and the V-cycle's launch layout: fused
     residual and restriction on, the dense bottom operator from 2,048 dofs,
-    the persistent and cluster tails off."""
+    the folded level-0 smoother on, the persistent and cluster tails off."""
     gasa = _lib()
     o = gasa.gasa_default_options()
     assert (o.t_pre, o.t_post, o.q_power, o.restart) == (3, 3, 3, 30)
-    assert o.fused_restriction == 1 and o.dense_tail_dofs == 2048
+    assert o.fused_restriction == 1 and o.dense_tail_dofs == 2048 and o.folded_smoother == 1
     assert o.grid_tail == 0 and o.tail_kib == 0 and o.bulk_staging == 0
 
 

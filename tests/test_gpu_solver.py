@@ -204,13 +204,14 @@ def test_gmres_solve(name):
 @pytest.mark.parametrize("name", ["p3_16", "p3_32"])
 def test_bulk_staged_sweep_same_bits(name):
     """The level-0 FP32 smoothing step with bulk-copy staging computes the
-    same operations in the same order as the unstaged kernel: the solves
-    agree bit for bit (10x10 blocks qualify for staging)."""
+    same operations in the same order as the unstaged plain step (the folded
+    step is off on both sides): the solves agree bit for bit (10x10 blocks
+    qualify for staging)."""
     gasa = _gasa()
     pr = problem(name)
     out = []
     for staging in (1, 0):
-        ctx, _ = gpu_setup(name, keep=False, bulk_staging=staging)
+        ctx, _ = gpu_setup(name, keep=False, bulk_staging=staging, folded_smoother=0)
         try:
             x = np.zeros_like(pr.rhs)
             info = gasa.gasa_solve(ctx, pr.rhs, x, TOL, gasa.GASA_PREC_MIXED32)
@@ -696,19 +697,20 @@ def test_dense_tail(name):
     ctx_d, _ = gpu_setup(name, keep=False)
     ctx_s, _ = gpu_setup(name, keep=False, dense_tail_dofs=0)
     try:
-        assert gasa.gasa_dense_tail_info(ctx_s) == {"first_level": N, "n": 0}
+        ci = gasa.gasa_cycle_info(ctx_s)
+        assert (ci["dense_first_level"], ci["dense_n"]) == (N, 0)
         stored = [gasa.gasa_level_shape(ctx_d, k) for k in range(N + 1)]
         want_k = N
         for k in range(N - 1, 0, -1):
             if stored[k]["units"] * stored[k]["s"] > thr:
                 break
             want_k = k
-        info = gasa.gasa_dense_tail_info(ctx_d)
+        info = gasa.gasa_cycle_info(ctx_d)
         assert want_k < N, "every workload here has a small bottom"
-        assert info["first_level"] == want_k
+        assert info["dense_first_level"] == want_k
         kt = want_k
         n = stored[kt]["units"] * stored[kt]["s"]
-        assert info["n"] == n
+        assert info["dense_n"] == n
         with pytest.raises(gasa.GasaError):
             gasa.gasa_get_level(ctx_s, kt, gasa.GASA_LV_DENSE_TAIL, np.zeros(n * n))
         M = gasa.gasa_get_level(ctx_d, kt, gasa.GASA_LV_DENSE_TAIL, np.zeros(n * n)).reshape(n, n)
@@ -756,3 +758,96 @@ def test_dense_tail_option_range():
         with pytest.raises(gasa.GasaError) as ei:
             gpu_setup("tiny", keep=False, dense_tail_dofs=bad)
         assert ei.value.status == gasa.GASA_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("name", ["c1", "p3_16", "tet_p2_4", "cd_q2_16", "hex_M3"])
+def test_folded_smoother(name):
+    """Level 0 smoothing in the folded form u + c - (w D^-1 A) u with
+    c = w D^-1 b (folded_smoother, on by default) against the plain step
+    u + w D^-1 (b - A u) of Alg. 1 (folded_smoother = 0).  The stored
+    w D_0^-1 A_0 follows the oracle's product W_0 A_0 in A_0's pattern; V-cycles
+    agree with the plain ones to rounding (bit for bit with FP16 level-0
+    blocks, which keep the plain step) and with the oracle's; solves take the
+    same iterations (+-1); the host-driven loop's per-launch byte count of a
+    level-0 step is that of W A, c, u and the result."""
+    gasa = _gasa()
+    H = oracle_setup(name)
+    pr = problem(name)
+    tol = level_tolerances(H)
+    ctx_f, _ = gpu_setup(name, keep=True)
+    ctx_u, _ = gpu_setup(name, keep=True, folded_smoother=0)
+    try:
+        assert gasa.gasa_cycle_info(ctx_f)["folded"] == 1
+        assert gasa.gasa_cycle_info(ctx_u)["folded"] == 0
+        sh = gasa.gasa_level_shape(ctx_f, 0)
+        s, n, nnzb = sh["s"], sh["units"], sh["nnzb"]
+        with pytest.raises(gasa.GasaError):
+            gasa.gasa_get_level(ctx_u, 0, gasa.GASA_LV_WA, np.zeros(nnzb * s * s))
+        rp, col, _ = _level_bsr(gasa, ctx_f, 0, "A", sh, s, s, n)
+        wa = gasa.gasa_get_level(ctx_f, 0, gasa.GASA_LV_WA, np.zeros(nnzb * s * s)).reshape(-1, s, s)
+        G = bsr_scipy(rp, col, wa)
+        L0 = H.levels[0]
+        Wm = L0.W.to_sparse()
+        ref = (Wm @ L0.A).tocsr()
+        # W_0 within tol[0] max|W_0| and A_0 within tol[0] max|A_0| perturb an
+        # entry of W_0 A_0 by at most tol[0] (max|W| ||A||_1 + max|A| ||W||_inf)
+        bound = tol[0] * (abs(Wm).max() * np.asarray(abs(L0.A).sum(axis=0)).max()
+                          + abs(L0.A).max() * np.asarray(abs(Wm).sum(axis=1)).max())
+        assert sparse_rel(G, ref) <= bound / abs(ref).max()
+        # FP64 and the FP16-block level 0 keep the plain step: same bits
+        for prec, oprec, tl in ((gasa.GASA_PREC_FP64, "fp64", 0.0),
+                                (gasa.GASA_PREC_MIXED32, "fp32", 1e-5),
+                                (gasa.GASA_PREC_MIXED16, "fp16", 0.0)):
+            want = O.make_vcycle(H, oprec)(pr.rhs)
+            r = to_dev(pr.rhs)
+            zf, zu = to_dev(np.zeros_like(pr.rhs)), to_dev(np.zeros_like(pr.rhs))
+            gasa.gasa_vcycle(ctx_f, r, zf, prec)
+            gasa.gasa_vcycle(ctx_u, r, zu, prec)
+            zf, zu = to_host(zf), to_host(zu)
+            if tl == 0.0:
+                assert np.array_equal(zf, zu)
+            else:
+                assert rel_err(zf, zu) <= tl, (oprec, rel_err(zf, zu))
+            assert rel_err(zf, want) <= (0.1 * tol[-1] if oprec == "fp64" else 1e-4)
+        solver = gasa.GASA_SOLVER_CG if pr.solver == "cg" else gasa.GASA_SOLVER_GMRES
+        for prec in (gasa.GASA_PREC_FP64, gasa.GASA_PREC_MIXED32):
+            xf, xu = np.zeros_like(pr.rhs), np.zeros_like(pr.rhs)
+            inf_f = gasa.gasa_solve(ctx_f, pr.rhs, xf, TOL, prec)
+            inf_u = gasa.gasa_solve(ctx_u, pr.rhs, xu, TOL, prec)
+            assert inf_f.converged and inf_f.rel_residual <= TOL
+            assert abs(inf_f.iterations - inf_u.iterations) <= 1
+        if solver == gasa.GASA_SOLVER_CG:
+            gasa.gasa_profile_enable(ctx_f, True)
+            x = np.zeros_like(pr.rhs)
+            gasa.gasa_solve(ctx_f, pr.rhs, x, TOL, gasa.GASA_PREC_MIXED32)
+            _, launches, by = gasa.gasa_profile_read(ctx_f, 0)
+            gasa.gasa_profile_enable(ctx_f, False)
+            assert launches > 0
+            want_bytes = nnzb * s * s * 4 + 4 * nnzb + 4 * (n + 1) + 3 * n * s * 4
+            assert by / launches == want_bytes
+    finally:
+        gasa.gasa_destroy(ctx_f)
+        gasa.gasa_destroy(ctx_u)
+
+
+@pytest.mark.parametrize("tpre,tpost", [(0, 2), (1, 1), (2, 0)])
+@pytest.mark.parametrize("name", ["c1", "p3_16"])
+def test_smoothing_counts(name, tpre, tpost):
+    """Alg. 2 with other pre/post smoothing counts than Section 6's 3 and 3,
+    including none on one side: the V-cycle (folded level-0 steps, dense
+    bottom operator and fused restriction at their defaults) follows the
+    oracle's with the same counts."""
+    import dataclasses
+    gasa = _gasa()
+    H = dataclasses.replace(oracle_setup(name), t_pre=tpre, t_post=tpost)
+    pr = problem(name)
+    ctx, _ = gpu_setup(name, keep=False, t_pre=tpre, t_post=tpost)
+    try:
+        for prec, oprec in ((gasa.GASA_PREC_FP64, "fp64"), (gasa.GASA_PREC_MIXED32, "fp32")):
+            want = O.make_vcycle(H, oprec)(pr.rhs)
+            z = to_dev(np.zeros_like(pr.rhs))
+            gasa.gasa_vcycle(ctx, to_dev(pr.rhs), z, prec)
+            tl = 0.1 * level_tolerances(H)[-1] if oprec == "fp64" else 1e-4
+            assert rel_err(to_host(z), want) <= tl, (oprec, rel_err(to_host(z), want))
+    finally:
+        gasa.gasa_destroy(ctx)
