@@ -48,8 +48,10 @@ template <typename T>
 cudaError_t launch_bjacobi(int mode, int n, int bs, const int *rp, const int *col, const T *A,
                            const T *W, const T *X, const T *B, T *Xo, int K, cudaStream_t s,
                            int64_t nnzb);
+// X = Ainv B for a dense row-major nc x nc Ainv with row pitch ld (>= nc; 0 = nc)
 template <typename T>
-cudaError_t launch_bdense(int nc, const double *Ainv, const T *B, T *X, int K, cudaStream_t s);
+cudaError_t launch_bdense(int nc, const double *Ainv, const T *B, T *X, int K, cudaStream_t s,
+                          int ld = 0);
 
 cudaError_t launch_bdot(int64_t n, const double *X, const double *Y, double *part, int K,
                         cudaStream_t s);

@@ -138,6 +138,8 @@ struct gasa_ctx {
   double *dtail_M = nullptr;
   int dtail_k = 0;
   int dtail_n = 0;
+  int dtail_ld = 0;   // row pitch of dtail_M in doubles (n padded against power-of-two strides)
+  float *dtail_Mh = nullptr, *dtail_Ml = nullptr;   // its exact two-term FP32 split (FP32 cycle)
   // profiling
   bool prof = false;
   ProfClass pc[5];

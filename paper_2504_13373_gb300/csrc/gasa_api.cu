@@ -111,8 +111,10 @@ void free_all(gasa_ctx *ctx) {
   }
   ctx->grid_bar = nullptr;
   ctx->dtail_M = nullptr;
+  ctx->dtail_Mh = ctx->dtail_Ml = nullptr;
   ctx->dtail_k = 0;
   ctx->dtail_n = 0;
+  ctx->dtail_ld = 0;
   ctx->V = ctx->Z = ctx->H = ctx->gm = ctx->mpart = nullptr;
   ctx->gm_restart = 0;
 }
@@ -473,6 +475,7 @@ gasa_status grid_build(gasa_ctx *ctx, int pi) {
 gasa_status dense_tail_build(gasa_ctx *ctx) {
   const int N = ctx->N;
   ctx->dtail_M = nullptr;
+  ctx->dtail_Mh = ctx->dtail_Ml = nullptr;
   ctx->dtail_k = N;
   ctx->dtail_n = 0;
   const gasa_options &o = ctx->opt;
@@ -505,8 +508,12 @@ gasa_status dense_tail_build(gasa_ctx *ctx) {
       p += 4 * m;
     }
   }
+  // rows of M 128-byte aligned and 129 * 128 bytes apart for n = 2048 (a row
+  // pitch that is no power of two)
+  const int ld = ((n + 15) / 16) * 16 + 16;
   double *M = nullptr;
-  gasa_status st = dalloc(ctx, &M, (size_t)n * n);
+  gasa_status st = dalloc(ctx, &M, (size_t)n * ld);
+  if (st == GASA_OK) CU(cudaMemsetAsync(M, 0, (size_t)n * ld * sizeof(double), s));
   cudaError_t e = cudaSuccess;
   auto ok = [&](cudaError_t r) {
     if (e == cudaSuccess) e = r;
@@ -552,17 +559,25 @@ gasa_status dense_tail_build(gasa_ctx *ctx) {
     }
     // row i of the K interleaved columns is M[i][c0 .. c0 + K)
     const int w = std::min(K, n - c0);
-    ok(cudaMemcpy2DAsync(M + c0, (size_t)n * sizeof(double), xk[kt], K * sizeof(double),
+    ok(cudaMemcpy2DAsync(M + c0, (size_t)ld * sizeof(double), xk[kt], K * sizeof(double),
                          w * sizeof(double), n, cudaMemcpyDeviceToDevice, s));
   }
+  // the FP32 cycle applies M from its exact two-term FP32 split
+  float *Mh = nullptr, *Ml = nullptr;
+  if (st == GASA_OK) st = dalloc(ctx, &Mh, (size_t)n * ld);
+  if (st == GASA_OK) st = dalloc(ctx, &Ml, (size_t)n * ld);
+  if (st == GASA_OK && e == cudaSuccess) e = launch_split((int64_t)n * ld, M, Mh, Ml, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   dfree(ctx, scr);
   ctx->device_bytes -= (int64_t)(tot * sizeof(double));
   if (st != GASA_OK) return st;
   CU(e);
+  ctx->dtail_Mh = Mh;
+  ctx->dtail_Ml = Ml;
   ctx->dtail_M = M;
   ctx->dtail_k = kt;
   ctx->dtail_n = n;
+  ctx->dtail_ld = ld;
   return GASA_OK;
 }
 
@@ -779,9 +794,15 @@ gasa_status vcycle_impl(gasa_ctx *ctx, const T *rhs, T *out, bool h16 = false,
     CU(launch_vcycle_tail<T>(pl, ctx->tail_cluster[pi], ctx->tail_smem[pi], s));
     xk[kt] = P::x(ctx->L[kt]);
   } else if (kt < N) {
-    // levels kt .. N-1 and the coarsest solve as their dense FP64 operator
+    // levels kt .. N-1 and the coarsest solve as their dense operator: FP64
+    // arithmetic in the FP64 cycle, double-single arithmetic on FP32 units
+    // (the same to about 2^-47 of sum |m x| per row) in the FP32 cycle
     Level &ld = ctx->L[kt];
-    CU(launch_dense_mv<T>(ctx->dtail_n, ctx->dtail_M, P::b(ld), P::x(ld), s));
+    if constexpr (std::is_same<T, float>::value)
+      CU(launch_dense_mv_ds(ctx->dtail_n, ctx->dtail_ld, ctx->dtail_Mh, ctx->dtail_Ml, P::b(ld),
+                            P::x(ld), s));
+    else
+      CU(launch_dense_mv<T>(ctx->dtail_n, ctx->dtail_M, P::b(ld), P::x(ld), s, ctx->dtail_ld));
     xk[kt] = P::x(ld);
   } else {
     // coarsest solve in FP64
@@ -897,10 +918,8 @@ int pq_ds_count(gasa_ctx *ctx) { return ctx->n_pq_ds; }
 // the FP32 splits of A (val32 + lo32) and of p (kp_hi + kp_lo, written by the
 // CG update or, with split_p, here); the same launch leaves the partial sums
 // of p . q in ctx->pq_ds
-gasa_status spmv_outer_ds(gasa_ctx *ctx, const double *p, double *q, bool split_p) {
+gasa_status spmv_outer_ds(gasa_ctx *ctx, const double *p, double *q) {
   Level &l = ctx->L[0];
-  const int64_t n = l.ndof;
-  if (split_p) CU(launch_split(n, p, ctx->kp_hi, ctx->kp_lo, ctx->stream));
   cudaEvent_t e0;
   prof_begin(ctx, 2, &e0);
   CU(launch_bsr_mv_ds(l.n, l.s, l.s, l.A.rp, l.A.col, l.A.val32, l.A.lo32, ctx->kp_hi,
@@ -914,7 +933,7 @@ gasa_status pcg(gasa_ctx *ctx, const double *b, double tol, int precision, int *
   cudaStream_t s = ctx->stream;
   const int64_t n = ctx->L[0].ndof;
   const bool flex = precision != GASA_PREC_FP64;
-  double *x = ctx->kx, *r = ctx->kr, *z = ctx->kz, *p = ctx->kp, *q = ctx->kq, *zold = ctx->kzold;
+  double *x = ctx->kx, *r = ctx->kr, *z = ctx->kz, *p = ctx->kp, *q = ctx->kq;
   double *pq_part = ctx->part, *rr_part = ctx->part + kRedBlocks;
   *conv = false;
   *iters = 0;
@@ -945,7 +964,7 @@ gasa_status pcg(gasa_ctx *ctx, const double *b, double tol, int precision, int *
       CU(launch_cg_update_p_f32(n, p, ctx->kf_out, ctx->scal + cur, ctx->rz_ds, ctx->rzo_ds,
                                 ctx->scal + nxt, ctx->kzold_f, ctx->kp_hi, ctx->kp_lo, kRedBlocks,
                                 s));
-      ST(spmv_outer_ds(ctx, p, q, false));
+      ST(spmv_outer_ds(ctx, p, q));
       CU(launch_cg_update_xr(n, x, r, p, q, ctx->scal + nxt, ctx->pq_ds, rr_part,
                              ctx->scal + S_ALPHA, s, pq_ds_count(ctx)));
       CU(launch_finalize(rr_part, 1, ctx->scal + S_RR, s));
@@ -981,18 +1000,14 @@ gasa_status pcg(gasa_ctx *ctx, const double *b, double tol, int precision, int *
   CU(launch_copy(n, z, p, s));
   int cur = S_RZ0, nxt = S_RZ1;
   for (int it = 1; it <= max_iter; ++it) {
-    if (flex) {
-      ST(spmv_outer_ds(ctx, p, q, true));
-    } else {
-      ST(spmv_outer(ctx, GASA_MV_ASSIGN, p, nullptr, q));
-      CU(launch_dot_partials(n, p, q, pq_part, s));
-    }
-    CU(launch_cg_update_xr(n, x, r, p, q, ctx->scal + cur, flex ? ctx->pq_ds : pq_part, rr_part,
-                           ctx->scal + S_ALPHA, s, flex ? pq_ds_count(ctx) : kRedBlocks));
+    ST(spmv_outer(ctx, GASA_MV_ASSIGN, p, nullptr, q));
+    CU(launch_dot_partials(n, p, q, pq_part, s));
+    CU(launch_cg_update_xr(n, x, r, p, q, ctx->scal + cur, pq_part, rr_part,
+                           ctx->scal + S_ALPHA, s, kRedBlocks));
     CU(launch_finalize(rr_part, 1, ctx->scal + S_RR, s));
     ST(read_scalars(ctx, 0, 3));
     const double pq = ctx->hscal[S_PQ];
-    if (!(pq > 0.0) && !flex) {
+    if (!(pq > 0.0)) {
       *iters = it;
       *relres = std::sqrt(ctx->hscal[S_RR]) / bn;
       return fail(ctx, GASA_ERR_NOT_SPD, "CG: p^T A p <= 0");
@@ -1012,10 +1027,9 @@ gasa_status pcg(gasa_ctx *ctx, const double *b, double tol, int precision, int *
       }
       CU(launch_copy(n, ctx->kt, r, s));
     }
-    if (flex) std::swap(z, zold);
-    ST(apply_M_cg(ctx, r, z, flex ? zold : nullptr, precision, ctx->rz_ds, ctx->rzo_ds, &np));
-    CU(launch_cg_update_p(n, p, z, ctx->scal + cur, ctx->rz_ds, ctx->rzo_ds, ctx->scal + nxt,
-                          flex ? 1 : 0, s, nullptr, nullptr, nullptr, np));
+    ST(apply_M_cg(ctx, r, z, nullptr, precision, ctx->rz_ds, ctx->rzo_ds, &np));
+    CU(launch_cg_update_p(n, p, z, ctx->scal + cur, ctx->rz_ds, ctx->rzo_ds, ctx->scal + nxt, 0, s,
+                          nullptr, nullptr, nullptr, np));
     std::swap(cur, nxt);
   }
   ST(spmv_outer(ctx, GASA_MV_RESIDUAL, x, b, ctx->kt));
@@ -1052,7 +1066,7 @@ gasa_status build_cg_graph(gasa_ctx *ctx, int precision) {
   cudaGraphNode_t node;
   CU(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  double *x = ctx->kx, *r = ctx->kr, *z = ctx->kz, *p = ctx->kp, *q = ctx->kq, *zold = ctx->kzold;
+  double *x = ctx->kx, *r = ctx->kr, *z = ctx->kz, *p = ctx->kp, *q = ctx->kq;
   double *pq_part = ctx->part, *rr_part = ctx->part + kRedBlocks;
   const bool prof = ctx->prof;
   ctx->prof = false;   // no event records inside a graph body
@@ -2370,8 +2384,17 @@ gasa_status gasa_get_level(gasa_ctx *ctx, int32_t level, int32_t what, void *hos
       break;
     case GASA_LV_DENSE_TAIL:
       if (ctx->dtail_M && level == ctx->dtail_k) {
-        src = ctx->dtail_M;
-        bytes = 8 * (int64_t)ctx->dtail_n * ctx->dtail_n;
+        // rows are stored with a padded pitch: copy them out unpadded
+        const size_t n = (size_t)ctx->dtail_n;
+        if (n_bytes < (int64_t)(8 * n * n))
+          return fail(ctx, GASA_ERR_INVALID_ARG, "output buffer too small");
+        if (cudaSetDevice(ctx->device) != cudaSuccess)
+          return fail(ctx, GASA_ERR_CUDA, "cudaSetDevice");
+        CU(cudaStreamSynchronize(ctx->stream));
+        CU(cudaMemcpy2D(host_out, n * sizeof(double), ctx->dtail_M,
+                        (size_t)ctx->dtail_ld * sizeof(double), n * sizeof(double), n,
+                        cudaMemcpyDeviceToHost));
+        return GASA_OK;
       }
       break;
     case GASA_LV_WA:
@@ -2626,7 +2649,7 @@ gasa_status gasa_tentative(int32_t n_units, int32_t bs, int32_t n_agg, const int
       s_next <= 0 || s_next > r || !agg_of || !B || !T_out)
     return GASA_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  int *cp = nullptr, *ci = nullptr, *scr = nullptr, *st = nullptr, *mx = nullptr;
+  int *cp = nullptr, *ci = nullptr, *scr = nullptr, *st = nullptr;
   cudaError_t e = cudaMallocAsync((void **)&cp, sizeof(int) * (n_agg + 1), s);
   if (e == cudaSuccess) e = cudaMallocAsync((void **)&ci, sizeof(int) * n_units, s);
   if (e == cudaSuccess) e = cudaMallocAsync((void **)&scr, sizeof(int) * (n_agg + 1), s);
@@ -2653,7 +2676,6 @@ gasa_status gasa_tentative(int32_t n_units, int32_t bs, int32_t n_agg, const int
                          sigma_out, st, s);
   int hst = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hst, st, sizeof(int), cudaMemcpyDeviceToHost, s);
-  (void)mx;
   for (int *p : {cp, ci, scr, st})
     if (p) cudaFreeAsync(p, s);
   cudaError_t e2 = cudaStreamSynchronize(s);

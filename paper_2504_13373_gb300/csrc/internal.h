@@ -152,9 +152,13 @@ cudaError_t launch_bsr_mv_ds(int n_brows, int br, int bc, const int *rp, const i
                              const double *xd = nullptr, double *partials = nullptr);
 int bsr_mv_ds_grid(int n_brows, int br);
 
-// y = A x for a dense row-major n x n matrix
+// y = A x for a dense row-major n x n matrix with row pitch ld (>= n; 0 = n)
 template <typename T>
-cudaError_t launch_dense_mv(int n, const double *A, const T *x, T *y, cudaStream_t s);
+cudaError_t launch_dense_mv(int n, const double *A, const T *x, T *y, cudaStream_t s, int ld = 0);
+// the same in double-single arithmetic on FP32 units from the exact two-term
+// FP32 split (Mh, Ml) of A (row pitch ld), FP32 x and y
+cudaError_t launch_dense_mv_ds(int n, int ld, const float *Mh, const float *Ml, const float *x,
+                               float *y, cudaStream_t s);
 
 // ---- kernels_red.cu --------------------------------------------------------
 // partials[kRedBlocks] of sum_i x_i y_i (y == nullptr: sum x_i^2)

@@ -313,11 +313,12 @@ bjacobi_h16_kernel(int mode, int n, int bs, int rows_cta, const int *__restrict_
 // coarsest level: X = A^{-1} B with the FP64 inverse, FP64 accumulation
 template <typename T, int K>
 __global__ void __launch_bounds__(kThreads)
-bdense_kernel(int nc, const double *__restrict__ Ainv, const T *__restrict__ B, T *__restrict__ X) {
+bdense_kernel(int nc, int ld, const double *__restrict__ Ainv, const T *__restrict__ B,
+              T *__restrict__ X) {
   const int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (e >= (int64_t)nc * K) return;
   const int i = (int)(e / K), c = (int)(e - (int64_t)i * K);
-  const double *a = Ainv + (size_t)i * nc;
+  const double *a = Ainv + (size_t)i * ld;
   double acc = 0.0;
   for (int j = 0; j < nc; ++j) acc = fma(__ldg(a + j), (double)B[(size_t)j * K + c], acc);
   X[e] = (T)acc;
@@ -753,11 +754,12 @@ __global__ void bunit_columns_kernel(int n, int K, int c0, double *__restrict__ 
 // column's sum does not depend on K
 template <typename T, int K>
 __global__ void __launch_bounds__(kThreads)
-bdense_warp_kernel(int n, const double *__restrict__ A, const T *__restrict__ B, T *__restrict__ X) {
+bdense_warp_kernel(int n, int ld, const double *__restrict__ A, const T *__restrict__ B,
+                   T *__restrict__ X) {
   const int row = (int)(((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
-  const double *a = A + (size_t)row * n;
+  const double *a = A + (size_t)row * ld;
   double acc[K];
 #pragma unroll
   for (int c = 0; c < K; ++c) acc[c] = 0.0;
@@ -872,14 +874,17 @@ cudaError_t launch_bjacobi_h16(int mode, int n, int bs, const int *rp, const int
 }
 
 template <typename T>
-cudaError_t launch_bdense(int nc, const double *Ainv, const T *B, T *X, int K, cudaStream_t s) {
+cudaError_t launch_bdense(int nc, const double *Ainv, const T *B, T *X, int K, cudaStream_t s,
+                          int ld) {
   const int64_t tot = (int64_t)nc * K;
+  if (ld < nc) ld = nc;
   // orders of 128 and more (the dense bottom of the V-cycle) take a warp per row
   if (nc >= 128) {
     GASA_KSWITCH(K, launch_k(bdense_warp_kernel<T, KK>, div_up((int64_t)nc * 32, kThreads),
-                             kThreads, 0, s, nc, Ainv, B, X));
+                             kThreads, 0, s, nc, ld, Ainv, B, X));
   } else {
-    GASA_KSWITCH(K, launch_k(bdense_kernel<T, KK>, div_up(tot, kThreads), kThreads, 0, s, nc, Ainv, B, X));
+    GASA_KSWITCH(K, launch_k(bdense_kernel<T, KK>, div_up(tot, kThreads), kThreads, 0, s, nc, ld,
+                             Ainv, B, X));
   }
   note_launch();
   return cudaGetLastError();
@@ -1070,7 +1075,8 @@ cudaError_t launch_bcolcopy(int64_t n, int K, int c, const double *src, double *
   template cudaError_t launch_bjacobi<T>(int, int, int, const int *, const int *, const T *,    \
                                          const T *, const T *, const T *, T *, int,             \
                                          cudaStream_t, int64_t);                                \
-  template cudaError_t launch_bdense<T>(int, const double *, const T *, T *, int, cudaStream_t); \
+  template cudaError_t launch_bdense<T>(int, const double *, const T *, T *, int, cudaStream_t,  \
+                                        int);                                                   \
   template cudaError_t launch_bscatter<T>(int64_t, int, int, const T *, T *, cudaStream_t);     \
   template cudaError_t launch_bgather<T>(int64_t, int, int, const T *, T *, cudaStream_t);
 GASA_INST_T(double)

@@ -869,12 +869,12 @@ cudaError_t launch_bsr_mm(int n_brows, int br, int bc, const int *rp, const int 
 // ----------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256)
-dense_mv_kernel(int n, const double *__restrict__ A, const T *__restrict__ x,
+dense_mv_kernel(int n, int ld, const double *__restrict__ A, const T *__restrict__ x,
                 T *__restrict__ y) {
   __shared__ double sh[8];
   const int row = blockIdx.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const double *a = A + (size_t)row * n;
+  const double *a = A + (size_t)row * ld;
   double acc = 0.0;
   int j = threadIdx.x;
   for (; j + 7 * 256 < n; j += 8 * 256) {
@@ -899,15 +899,76 @@ dense_mv_kernel(int n, const double *__restrict__ A, const T *__restrict__ x,
   }
 }
 
-template <typename T>
-cudaError_t launch_dense_mv(int n, const double *A, const T *x, T *y, cudaStream_t s) {
+// y = M x for the FP32 cycle's dense bottom operator: M as exact two-term
+// FP32 splits (Mh the FP32 rounding of M, Ml that of M - Mh), FP32 x,
+// products and sums in double-single arithmetic on FP32 units (the scheme of
+// bsr_mv_ds_kernel with x exact in FP32), so each row agrees with the FP64
+// product to about 2^-47 of sum |m x|; GB300's FP64 pipe would take n^2 FMAs
+// at a small fraction of the FP32 rate.  A CTA of 256 threads per row, thread
+// t over columns t, t + 256, ... (eight in flight), its (s, lo) pair to FP64,
+// then a warp tree and the eight warp sums in order.
+__global__ void __launch_bounds__(256)
+dense_mv_ds_kernel(int n, int ld, const float *__restrict__ Mh, const float *__restrict__ Ml,
+                   const float *__restrict__ x, float *__restrict__ y) {
+  __shared__ double sh[8];
+  const int row = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const float *h = Mh + (size_t)row * ld;
+  const float *l = Ml + (size_t)row * ld;
+  float s = 0.0f, lo = 0.0f;
+  auto add = [&](float ah, float al, float xh) {
+    const float pr = __fmul_rn(ah, xh);
+    const float e = __fmaf_rn(ah, xh, -pr);
+    const float cross = __fmul_rn(al, xh);
+    const float s1 = __fadd_rn(s, pr);
+    const float bp = __fsub_rn(s1, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s1, bp)), __fsub_rn(pr, bp));
+    s = s1;
+    lo = __fadd_rn(lo, __fadd_rn(err, __fadd_rn(e, cross)));
+  };
+  int j = threadIdx.x;
+  for (; j + 7 * 256 < n; j += 8 * 256) {
+    float hv[8], lv[8], xv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      hv[u] = __ldg(h + j + u * 256);
+      lv[u] = __ldg(l + j + u * 256);
+      xv[u] = __ldg(x + j + u * 256);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) add(hv[u], lv[u], xv[u]);
+  }
+  for (; j < n; j += 256) add(__ldg(h + j), __ldg(l + j), __ldg(x + j));
+  double v = (double)s + (double)lo;
+  v = warp_sum(v);
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += sh[w];
+    y[row] = (float)t;
+  }
+}
+
+cudaError_t launch_dense_mv_ds(int n, int ld, const float *Mh, const float *Ml, const float *x,
+                               float *y, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  launch_k(dense_mv_kernel<T>, n, 256, 0, s, n, A, x, y); note_launch();
+  launch_k(dense_mv_ds_kernel, n, 256, 0, s, n, ld, Mh, Ml, x, y);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dense_mv(int n, const double *A, const T *x, T *y, cudaStream_t s, int ld) {
+  if (n == 0) return cudaSuccess;
+  if (ld < n) ld = n;
+  launch_k(dense_mv_kernel<T>, n, 256, 0, s, n, ld, A, x, y); note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_dense_mv<double>(int, const double *, const double *, double *,
-                                             cudaStream_t);
+                                             cudaStream_t, int);
 template cudaError_t launch_dense_mv<float>(int, const double *, const float *, float *,
-                                            cudaStream_t);
+                                            cudaStream_t, int);
 
 }  // namespace gasa

@@ -328,7 +328,8 @@ cudaError_t vcycle_b(Engine &e, const T *rhs, T *out) {
                       P::r(v), nullptr, P::b(e.lv[k + 1]), K, s, l.R.nnzb));
   }
   if (kt < N)
-    ECU(launch_bdense<T>(ctx->dtail_n, ctx->dtail_M, P::b(e.lv[kt]), P::x(e.lv[kt]), K, s));
+    ECU(launch_bdense<T>(ctx->dtail_n, ctx->dtail_M, P::b(e.lv[kt]), P::x(e.lv[kt]), K, s,
+                         ctx->dtail_ld));
   else
     ECU(launch_bdense<T>(ctx->nc, ctx->coarse_inv, P::b(e.lv[N]), P::x(e.lv[N]), K, s));
   xk[kt] = P::x(e.lv[kt]);
