@@ -48,13 +48,15 @@ NCU_TRAFFIC = {
     # captured on the 224x224 case of the same recipe (100,352 elements, 210.40 MB read +
     # 2.19 MB written per launch, two launches) and scaled to 131,072 elements
     "plain": {"kernel": "jacobi_kernel<float,10,0>", "file": "kernels_mv.cu",
-              "src_sha": "11a0bfee7eb2b9dd",
+              "src_sha": "c119c05cb7a498bb",
               "bytes_per_launch": (210.40e6 + 2.19e6) * 131072 / 100352},
     "tma": {"kernel": "jacobi_tma_kernel<float,10>", "file": "kernels_tma.cu",
             "src_sha": "24cbc7a902631ea2", "bytes_per_launch": 274.87e6 + 6.52e6},
-    # folded step x + c - (wD^-1 A) x: no capture of the current source yet
+    # folded step x + c - (wD^-1 A) x: captured on the 224x224 case (170.25 MB read +
+    # 1.28 MB written per launch, four launches) and scaled to 131,072 elements
     "folded": {"kernel": "bsr_mv_kernel<float,10,3>", "file": "kernels_mv.cu",
-               "src_sha": None, "bytes_per_launch": None},
+               "src_sha": "c119c05cb7a498bb",
+               "bytes_per_launch": (170.25e6 + 1.28e6) * 131072 / 100352},
 }
 
 
