@@ -102,6 +102,8 @@ def parse():
                     help="c2 (default): the P3 256^2 bench line; c1 / c3 / c4: solves/s of the "
                          "P1 32^2, LDG Q2 512^2 conv-diff and P2 48^3 tet workloads per precision")
     ap.add_argument("--peclet", type=float, default=100.0, help="Peclet number of c3")
+    ap.add_argument("--matrix-free-levels", type=int, default=0,
+                    help="with --workload: levels 1..k applied matrix-free (Section 4.4)")
     ap.add_argument("--no-other-workloads", action="store_true",
                     help="skip the c1 / c3 / c4 records of the default run")
     return ap.parse_args()
@@ -559,17 +561,19 @@ def build_workload(which, n_arg=None, peclet=100.0):
     return configs.poisson3d_p2(n=n), f"poisson3d_sipg_p2_tet_{n}cubed"
 
 
-def measure_workload(gasa, pr, name, steps, warmup, device):
+def measure_workload(gasa, pr, name, steps, warmup, device, opt_kw=None):
     """solves/s, iterations, true residual, error against this run's FP64
     solve and a whole-iteration roofline of one workload, per precision:
     FP64, FP32 V-cycle, FP16-block V-cycle (the parity tests pin each
-    precision's solve to the oracle's on reduced sizes of the same recipe)."""
+    precision's solve to the oracle's on reduced sizes of the same recipe).
+    opt_kw: further gasa_options fields (the roofline's byte model counts
+    stored operators, so it overstates matrix-free levels' bytes)."""
     import torch
     A = pr.A
     ctx = gasa.gasa_create(device)
     opt = gasa.gasa_default_options(dim=pr.dim, n_cand=pr.r, max_iter=20000,
                                     solver=gasa.GASA_SOLVER_CG if pr.solver == "cg"
-                                    else gasa.GASA_SOLVER_GMRES)
+                                    else gasa.GASA_SOLVER_GMRES, **(opt_kw or {}))
     sinfo = gasa.gasa_setup(ctx, A.row_ptr, A.col, A.val.ravel(), A.b, pr.agg_of, opt,
                             adj_ptr=pr.adj_ptr, adj_idx=pr.adj_idx, centroids=pr.centroids,
                             init_candidates=pr.B0)
@@ -620,7 +624,8 @@ def measure_workload(gasa, pr, name, steps, warmup, device):
             "level_dofs": [int(sinfo.dofs[k]) for k in range(sinfo.n_levels)],
             "level_nnzb": [int(sinfo.nnzb[k]) for k in range(sinfo.n_levels)],
             "level_block": [int(sinfo.block[k]) for k in range(sinfo.n_levels)],
-            "cycle": dense_tail, "setup_s": sinfo.seconds, "steps": steps, "warmup": warmup, "precisions": out}
+            "cycle": dense_tail, "options": dict(opt_kw or {}),
+            "device_bytes": int(sinfo.device_bytes), "setup_s": sinfo.seconds, "steps": steps, "warmup": warmup, "precisions": out}
 
 
 def other_workloads(gasa, device, steps=1, warmup=1):
@@ -655,18 +660,24 @@ def workload_main(args, local):
         opt = gasa.gasa_default_options(dim=pr.dim, n_cand=pr.r, max_iter=20000,
                                         solver=gasa.GASA_SOLVER_CG if pr.solver == "cg"
                                         else gasa.GASA_SOLVER_GMRES)
+        if args.profile_iters > 0:
+            opt.max_iter = args.profile_iters
         gasa.gasa_setup(ctx, A.row_ptr, A.col, A.val.ravel(), A.b, pr.agg_of, opt,
                         adj_ptr=pr.adj_ptr, adj_idx=pr.adj_idx, centroids=pr.centroids,
                         init_candidates=pr.B0)
         b = torch.from_numpy(pr.rhs).cuda()
         x = torch.zeros_like(b)
+        # launches before the solve, for an ncu skip count (-s)
+        print(json.dumps({"setup_launches": gasa.gasa_kernel_launches()}), flush=True)
         gasa.gasa_profile_enable(ctx, True)
-        gasa.gasa_solve(ctx, b, x, TOL, gasa.GASA_PREC_MIXED32, on_device=True)
+        gasa.gasa_solve(ctx, b, x, TOL, gasa.GASA_PREC_MIXED32, on_device=True,
+                        allow_not_converged=args.profile_iters > 0)
         torch.cuda.synchronize()
         gasa.gasa_destroy(ctx)
         return 0
     with ClockSampler(local) as clk:
-        rec = measure_workload(gasa, pr, name, args.steps, args.warmup, local)
+        kw = {"matrix_free_levels": args.matrix_free_levels} if args.matrix_free_levels > 0 else None
+        rec = measure_workload(gasa, pr, name, args.steps, args.warmup, local, kw)
     mix = rec["precisions"]["mixed32"]
     print(json.dumps({
         "metric": METRIC, "value": mix["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
