@@ -293,6 +293,31 @@ def test_vcycle_linear_symmetric_convergent(tiny):
     assert rho < 1.0
 
 
+def test_vcycle_bottom_is_a_fixed_linear_map(tiny):
+    """Alg. 2 below level k, started from u_k = 0, is a fixed linear map of b_k:
+    a two-level cycle on level 0 whose coarse solve applies the sub-hierarchy's
+    V-cycle (levels 1 .. N) as a matrix M_1, formed from its action on the unit
+    vectors, is the full V-cycle (the dense bottom operator of the library).
+    A cycle that used the level-1 operator's inverse instead, or skipped the
+    level-1 smoothing, would differ."""
+    pr, H = tiny
+    assert H.N >= 2
+    sub = O.Hierarchy(levels=H.levels[1:], coarse=H.coarse, t_pre=H.t_pre, t_post=H.t_post)
+    V1 = O.make_vcycle(sub)
+    n1 = H.levels[1].n
+    M1 = np.column_stack([V1(e) for e in np.eye(n1)])
+    two = O.Hierarchy(levels=H.levels[:2], coarse=np.linalg.inv(M1), t_pre=H.t_pre,
+                      t_post=H.t_post)
+    full, split = O.make_vcycle(H), O.make_vcycle(two)
+    f = RO.random_vector(pr.n_dofs, 5)
+    zf, zs = full(f), split(f)
+    assert np.max(np.abs(zs - zf)) <= 1e-10 * np.max(np.abs(zf))
+    # the exact level-1 solve in its place gives a different (two-grid) cycle
+    exact = O.Hierarchy(levels=H.levels[:2], coarse=H.levels[1].A.toarray(), t_pre=H.t_pre,
+                        t_post=H.t_post)
+    assert np.max(np.abs(O.make_vcycle(exact)(f) - zf)) > 1e-6 * np.max(np.abs(zf))
+
+
 def test_pcg_matches_direct_solve(tiny):
     pr, H = tiny
     res = O.solve(H, pr.rhs, 1e-12)
