@@ -65,3 +65,38 @@ def test_split_is_exact_to_2_pow_48():
     hi, lo = split(v)
     rel = np.abs(hi.astype(np.float64) + lo.astype(np.float64) - v) / np.abs(v)
     assert np.max(rel) <= 2.0 ** -48
+
+
+def ds_dense_row(m, x, threads=256):
+    """the dense bottom operator's row product in the FP32 cycle: m as its exact
+    FP32 split, x exact in FP32, thread t runs the double-single recurrence over
+    columns t, t + threads, ...; the threads' s + t pairs are added in FP64"""
+    mh, ml = split(m)
+    xf = np.asarray(x, dtype=np.float32)
+    parts = []
+    for t0 in range(threads):
+        s, t = f32(0.0), f32(0.0)
+        for c in range(t0, len(m), threads):
+            p = f32(mh[c] * xf[c])
+            e = f32(np.float64(mh[c]) * np.float64(xf[c]) - np.float64(p))
+            cross = f32(ml[c] * xf[c])
+            s1 = f32(s + p)
+            bp = f32(s1 - s)
+            err = f32(f32(s - f32(s1 - bp)) + f32(p - bp))
+            s = s1
+            t = f32(t + f32(err + f32(e + cross)))
+        parts.append(np.float64(s) + np.float64(t))
+    return float(np.sum(np.array(parts)))
+
+
+@pytest.mark.parametrize("n,seed,spread", [(512, 6, 0.0), (2048, 7, 4.0)])
+def test_double_single_dense_row_within_bound(n, seed, spread):
+    """A row of the 2,048-dof bottom operator applied to an FP32 vector agrees
+    with the exact FP64-operand product to within n * 2^-47 of sum |m x|."""
+    rng = np.random.default_rng(seed)
+    m = rng.standard_normal(n) * 10.0 ** rng.uniform(-spread, spread, n)
+    x = rng.standard_normal(n).astype(np.float32).astype(np.float64)
+    exact = sum(Fraction(float(mi)) * Fraction(float(xi)) for mi, xi in zip(m, x))
+    absum = float(np.sum(np.abs(m * x)))
+    got = ds_dense_row(m, x)
+    assert float(abs(Fraction(got) - exact)) <= n * 2.0 ** -47 * absum
