@@ -417,7 +417,8 @@ gasa_status gasa_dense_inverse(int32_t n, const double *A, double *Ainv, int32_t
  * bits alone and in any mix.  Device memory for hierarchies and engines is
  * admitted against the budget given at creation; a request whose engine does
  * not fit waits until idle engines are released.
- * Precisions: GASA_PREC_FP64 and GASA_PREC_MIXED32. */
+ * Precisions: GASA_PREC_FP64, GASA_PREC_MIXED32 and GASA_PREC_MIXED16 (level 0
+ * read from its FP16 blocks, the other levels as in MIXED32). */
 typedef struct gasa_server gasa_server;
 
 typedef struct {

@@ -18,6 +18,19 @@ import pytest
 f32 = np.float32
 
 
+def round_f32(q):
+    """q (a Fraction) rounded to the nearest FP32 number, ties to even"""
+    f = f32(float(q))
+    cands = (f, np.nextafter(f, f32(np.inf)), np.nextafter(f, f32(-np.inf)))
+    return min(cands, key=lambda c: (abs(Fraction(float(c)) - q),
+                                     int(np.array(c, dtype=np.float32).view(np.uint32)) & 1))
+
+
+def fma_f32(a, b, c):
+    """fl32(a * b + c) with one rounding, for FP32 a, b, c"""
+    return round_f32(Fraction(float(a)) * Fraction(float(b)) + Fraction(float(c)))
+
+
 def split(v):
     hi = np.asarray(v, dtype=np.float64).astype(np.float32)
     lo = (np.asarray(v, dtype=np.float64) - hi.astype(np.float64)).astype(np.float32)
@@ -32,7 +45,7 @@ def ds_row(a, x):
     for c in range(len(a)):
         p = f32(ah[c] * xh[c])
         e = f32(np.float64(ah[c]) * np.float64(xh[c]) - np.float64(p))
-        cross = f32(np.float64(ah[c]) * np.float64(xl[c]) + np.float64(f32(al[c] * xh[c])))
+        cross = fma_f32(ah[c], xl[c], f32(al[c] * xh[c]))
         s1 = f32(s + p)
         bp = f32(s1 - s)
         err = f32(f32(s - f32(s1 - bp)) + f32(p - bp))
@@ -100,3 +113,19 @@ def test_double_single_dense_row_within_bound(n, seed, spread):
     absum = float(np.sum(np.abs(m * x)))
     got = ds_dense_row(m, x)
     assert float(abs(Fraction(got) - exact)) <= n * 2.0 ** -47 * absum
+
+
+def test_fma_emulation_rounds_once():
+    """A case where rounding a*b + c first to float64 and then to FP32 differs
+    from one rounding: the exact sum lies 2^-70 below the midpoint between
+    two FP32 neighbours, so float64 lands on the midpoint and ties to even
+    (up), while the single rounding goes down."""
+    a = f32(2.0 ** -12 * (1 + 2.0 ** -23))
+    b = f32(2.0 ** -12 * (1 - 2.0 ** -23))
+    c = f32(1 + 2.0 ** -23)
+    exact = Fraction(float(a)) * Fraction(float(b)) + Fraction(float(c))
+    mid = 1 + Fraction(1, 2 ** 23) + Fraction(1, 2 ** 24)
+    assert mid - exact == Fraction(1, 2 ** 70)
+    assert Fraction(float(fma_f32(a, b, c))) == 1 + Fraction(1, 2 ** 23)
+    twice = f32(np.float64(a) * np.float64(b) + np.float64(c))
+    assert Fraction(float(twice)) == 1 + Fraction(1, 2 ** 22)
