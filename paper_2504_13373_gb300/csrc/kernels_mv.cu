@@ -72,6 +72,58 @@ bsr_mv_generic(int n_brows, int br, int bc, const int *__restrict__ rp,
   else y[t] += acc;
 }
 
+// Folded smoothing step y = x + (c - A x) for the FP32 level 0, taking the
+// blocks of a row two at a time: both column indices, both matrix rows and
+// both x segments are requested before the first FMA, so each thread keeps
+// two blocks' loads in flight, and the FMAs still run in block order (the
+// same bits as bsr_mv_kernel).  MINB caps the registers so that MINB CTAs of
+// 256 threads stay resident per SM.  On the 1.31M-dof P3 pattern (10 x 10
+// blocks, about 4 per row) MINB = 6 took a step from 47.0 to 40.7 us on
+// GB300; unrolling four blocks, or two without the register cap, was slower
+// (fewer resident warps).
+template <int BC, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+folded_pair_kernel(int n_brows, int br, const int *__restrict__ rp, const int *__restrict__ col,
+                   const float *__restrict__ val, const float *__restrict__ x,
+                   const float *__restrict__ c, float *__restrict__ y) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n_brows * br) return;
+  const int i = (int)(t / br);
+  const int r = (int)(t - (long long)i * br);
+  constexpr int W = RowVec<float, BC>::value;
+  const int beg = __ldg(rp + i), end = __ldg(rp + i + 1);
+  float acc = 0.f;
+  int k = beg;
+  for (; k + 2 <= end; k += 2) {
+    const int j0 = __ldg(col + k), j1 = __ldg(col + k + 1);
+    float a0[BC], a1[BC], x0[BC], x1[BC];
+#pragma unroll
+    for (int q = 0; q < BC; q += W) load_vec_stream<float, W>(val + ((size_t)k * br + r) * BC + q, a0 + q);
+#pragma unroll
+    for (int q = 0; q < BC; q += W)
+      load_vec_stream<float, W>(val + ((size_t)(k + 1) * br + r) * BC + q, a1 + q);
+#pragma unroll
+    for (int q = 0; q < BC; q += W) load_vec<float, W>(x + (size_t)j0 * BC + q, x0 + q);
+#pragma unroll
+    for (int q = 0; q < BC; q += W) load_vec<float, W>(x + (size_t)j1 * BC + q, x1 + q);
+#pragma unroll
+    for (int q = 0; q < BC; ++q) acc = fmaf(a0[q], x0[q], acc);
+#pragma unroll
+    for (int q = 0; q < BC; ++q) acc = fmaf(a1[q], x1[q], acc);
+  }
+  if (k < end) {
+    const int j = __ldg(col + k);
+    float av[BC], xv[BC];
+#pragma unroll
+    for (int q = 0; q < BC; q += W) load_vec_stream<float, W>(val + ((size_t)k * br + r) * BC + q, av + q);
+#pragma unroll
+    for (int q = 0; q < BC; q += W) load_vec<float, W>(x + (size_t)j * BC + q, xv + q);
+#pragma unroll
+    for (int q = 0; q < BC; ++q) acc = fmaf(av[q], xv[q], acc);
+  }
+  y[t] = x[t] + (c[t] - acc);
+}
+
 // ----------------------------------------------------------------------------
 // Coarse levels: few block rows, each with tens to hundreds of blocks (the
 // Galerkin products widen the stencil level by level).  One warp owns one
@@ -325,6 +377,14 @@ template cudaError_t launch_bsr_mv<float>(int, int, int, int, const int *, const
 template <typename T>
 cudaError_t launch_folded_sweep(int n_units, int bs, const int *rp, const int *col, const T *WA,
                                 const T *x, const T *c, T *xo, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (bs == 10 && n_units > 0 && aligned16(WA) && aligned16(x)) {
+      launch_k(folded_pair_kernel<10, 6>, div_up((long long)n_units * bs, 256), 256, 0, s,
+               n_units, bs, rp, col, WA, x, c, xo);
+      note_launch();
+      return cudaGetLastError();
+    }
+  }
   return mv_dispatch<T, kMvFolded>(n_units, bs, bs, rp, col, WA, x, c, xo, s);
 }
 template cudaError_t launch_folded_sweep<double>(int, int, const int *, const int *, const double *,
@@ -348,6 +408,25 @@ template cudaError_t launch_folded_sweep<float>(int, int, const int *, const int
 // matrix, more than that rate feeds at full HBM bandwidth.  The __f*_rn
 // intrinsics keep the compiler from contracting the two-sum into FMAs.
 // ----------------------------------------------------------------------------
+// One block row segment of the recurrence above: BC products joined to the
+// running pair (s, lo) in column order.
+template <int BC>
+__device__ __forceinline__ void ds_row_accumulate(const float *ah, const float *al,
+                                                  const float *xh, const float *xl, float &s,
+                                                  float &lo) {
+#pragma unroll
+  for (int c = 0; c < BC; ++c) {
+    const float pr = __fmul_rn(ah[c], xh[c]);
+    const float e = __fmaf_rn(ah[c], xh[c], -pr);
+    const float cross = __fmaf_rn(ah[c], xl[c], __fmul_rn(al[c], xh[c]));
+    const float s1 = __fadd_rn(s, pr);
+    const float bp = __fsub_rn(s1, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s1, bp)), __fsub_rn(pr, bp));
+    s = s1;
+    lo = __fadd_rn(lo, __fadd_rn(err, __fadd_rn(e, cross)));
+  }
+}
+
 // With DOT the kernel also leaves per-CTA partial sums of x . y (x given in
 // FP64 as xd) in partials[blockIdx.x], summed in a fixed order.
 template <int BC, bool DOT>
@@ -388,6 +467,77 @@ bsr_mv_ds_kernel(int n_brows, int br, const int *__restrict__ rp, const int *__r
       s = s1;
       lo = __fadd_rn(lo, __fadd_rn(err, __fadd_rn(e, cross)));
     }
+  }
+  const double yt = (double)s + (double)lo;
+  if (act) y[t] = yt;
+  if (DOT) {
+    __shared__ double sh[32];
+    const double v = block_sum(xt * yt, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+  }
+}
+
+// The same double-single product taking the blocks of a row two at a time:
+// both blocks' hi and lo rows and x segments are requested before the first
+// product, and the products join s and t in block order (the same bits as
+// bsr_mv_ds_kernel).  MINB = 4 caps the registers at 64.  On the 1.31M-dof
+// P3 pattern it took q = A p with p.q from 129 to 94 us on GB300.
+template <int BC, bool DOT, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+bsr_mv_ds_pair_kernel(int n_brows, int br, const int *__restrict__ rp, const int *__restrict__ col,
+                      const float *__restrict__ ahi, const float *__restrict__ alo,
+                      const float *__restrict__ xhi, const float *__restrict__ xlo,
+                      double *__restrict__ y, const double *__restrict__ xd,
+                      double *__restrict__ partials) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool act = t < (long long)n_brows * br;
+  const int i = act ? (int)(t / br) : 0;
+  const int r = act ? (int)(t - (long long)i * br) : 0;
+  constexpr int W = RowVec<float, BC>::value;
+  const int beg = act ? __ldg(rp + i) : 0, end = act ? __ldg(rp + i + 1) : 0;
+  const double xt = (DOT && act) ? xd[t] : 0.0;
+  float s = 0.0f, lo = 0.0f;
+  int k = beg;
+  for (; k + 2 <= end; k += 2) {
+    const int j0 = __ldg(col + k), j1 = __ldg(col + k + 1);
+    const size_t o0 = ((size_t)k * br + r) * BC, o1 = ((size_t)(k + 1) * br + r) * BC;
+    float ah0[BC], al0[BC], ah1[BC], al1[BC], xh0[BC], xl0[BC], xh1[BC], xl1[BC];
+#pragma unroll
+    for (int q = 0; q < BC; q += W) {
+      load_vec_stream<float, W>(ahi + o0 + q, ah0 + q);
+      load_vec_stream<float, W>(alo + o0 + q, al0 + q);
+    }
+#pragma unroll
+    for (int q = 0; q < BC; q += W) {
+      load_vec_stream<float, W>(ahi + o1 + q, ah1 + q);
+      load_vec_stream<float, W>(alo + o1 + q, al1 + q);
+    }
+#pragma unroll
+    for (int q = 0; q < BC; q += W) {
+      load_vec<float, W>(xhi + (size_t)j0 * BC + q, xh0 + q);
+      load_vec<float, W>(xlo + (size_t)j0 * BC + q, xl0 + q);
+    }
+#pragma unroll
+    for (int q = 0; q < BC; q += W) {
+      load_vec<float, W>(xhi + (size_t)j1 * BC + q, xh1 + q);
+      load_vec<float, W>(xlo + (size_t)j1 * BC + q, xl1 + q);
+    }
+    ds_row_accumulate<BC>(ah0, al0, xh0, xl0, s, lo);
+    ds_row_accumulate<BC>(ah1, al1, xh1, xl1, s, lo);
+  }
+  if (k < end) {
+    const int j = __ldg(col + k);
+    const size_t off = ((size_t)k * br + r) * BC;
+    float ah[BC], al[BC], xh[BC], xl[BC];
+#pragma unroll
+    for (int q = 0; q < BC; q += W) load_vec_stream<float, W>(ahi + off + q, ah + q);
+#pragma unroll
+    for (int q = 0; q < BC; q += W) load_vec_stream<float, W>(alo + off + q, al + q);
+#pragma unroll
+    for (int q = 0; q < BC; q += W) load_vec<float, W>(xhi + (size_t)j * BC + q, xh + q);
+#pragma unroll
+    for (int q = 0; q < BC; q += W) load_vec<float, W>(xlo + (size_t)j * BC + q, xl + q);
+    ds_row_accumulate<BC>(ah, al, xh, xl, s, lo);
   }
   const double yt = (double)s + (double)lo;
   if (act) y[t] = yt;
@@ -450,10 +600,20 @@ cudaError_t launch_bsr_mv_ds(int n_brows, int br, int bc, const int *rp, const i
     note_launch();                                                                          \
     return cudaGetLastError();
   if (dot && !al) return cudaErrorNotSupported;
+  if (al && bc == 10) {
+    if (dot)
+      launch_k(bsr_mv_ds_pair_kernel<10, true, 4>, grid, 256, 0, s, n_brows, br, rp, col, ahi,
+               alo, xhi, xlo, y, xd, partials);
+    else
+      launch_k(bsr_mv_ds_pair_kernel<10, false, 4>, grid, 256, 0, s, n_brows, br, rp, col, ahi,
+               alo, xhi, xlo, y, xd, partials);
+    note_launch();
+    return cudaGetLastError();
+  }
   if (al) {
     switch (bc) {
       GASA_DS_CASE(1) GASA_DS_CASE(2) GASA_DS_CASE(3) GASA_DS_CASE(4) GASA_DS_CASE(5)
-      GASA_DS_CASE(6) GASA_DS_CASE(7) GASA_DS_CASE(8) GASA_DS_CASE(9) GASA_DS_CASE(10)
+      GASA_DS_CASE(6) GASA_DS_CASE(7) GASA_DS_CASE(8) GASA_DS_CASE(9)
       GASA_DS_CASE(11) GASA_DS_CASE(12) GASA_DS_CASE(13) GASA_DS_CASE(14) GASA_DS_CASE(15)
       GASA_DS_CASE(16)
       default: break;
