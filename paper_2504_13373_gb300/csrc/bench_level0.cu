@@ -10,9 +10,10 @@
 // (lower right of square q = j n + i) meets 2q+1 across the diagonal, the
 // square below (2(q-n)+1) and the square to the right (2(q+1)+1); triangle
 // 2q+1 meets 2q, the square to the left (2(q-1)) and the square above
-// (2(q+n)).  With 10 x 10 blocks this is exactly the benchmark's level-0
-// pattern (n = 256: 131,072 block rows, 523,264 blocks); the values are
-// seeded uniform numbers, which do not change the memory traffic.
+// (2(q+n)); tests/test_synth.py pins this rule against the mesh.  With the
+// diagonal and 10 x 10 blocks it is exactly the benchmark's level-0 pattern
+// (n = 256: 131,072 block rows, 523,264 blocks); the values are seeded
+// uniform numbers, which do not change the memory traffic.
 // Each kernel is checked on sampled rows against an FP64 host product and
 // timed by CUDA events on its stream (median over the rounds).
 //

@@ -50,6 +50,27 @@ def test_tet_mesh_counts(n):
     assert np.all(vol > 0) and abs(vol.sum() - 1.0) < 1e-12
 
 
+@pytest.mark.parametrize("n", [1, 5])
+def test_tri_mesh_face_graph_closed_form(n):
+    """The triangle mesh's face graph in element order, written out by hand:
+    square q = j n + i holds triangle 2q (lower right) and 2q + 1 (upper left);
+    2q meets 2q + 1, the upper triangle of the square below (2(q - n) + 1) and
+    that of the square to the right (2(q + 1) + 1); 2q + 1 meets 2q, the lower
+    triangle of the square to the left (2(q - 1)) and that of the square above
+    (2(q + n)).  The stand-alone level-0 kernel timing program builds the
+    benchmark's block pattern from this rule."""
+    m = M.tri_mesh(n, 3)
+    ptr, idx = m.adjacency()
+    for q in range(n * n):
+        i, j = q % n, q // n
+        lower = {2 * q + 1} | ({2 * (q - n) + 1} if j > 0 else set()) | \
+            ({2 * (q + 1) + 1} if i + 1 < n else set())
+        upper = {2 * q} | ({2 * (q - 1)} if i > 0 else set()) | \
+            ({2 * (q + n)} if j + 1 < n else set())
+        assert set(idx[ptr[2 * q]:ptr[2 * q + 1]].tolist()) == lower
+        assert set(idx[ptr[2 * q + 1]:ptr[2 * q + 2]].tolist()) == upper
+
+
 def test_adjacency_symmetric():
     m = M.tri_mesh(6, 2)
     ptr, idx = m.adjacency()
