@@ -373,6 +373,51 @@ def test_stationary_solver(tiny):
     assert res.converged
 
 
+def test_stationary_error_contracts_by_the_iteration_operator(tiny):
+    """Alg. 2 as a stationary solver from x = 0: the error e_k = x* - x_k is
+    e_k = E^k x* with E = I - M A, M the V-cycle as a matrix.  E is
+    self-adjoint in the A inner product (symmetric cycle), so every step
+    shrinks ||e||_A by at most ||E||_A = rho(E) (a dense eigenvalue problem,
+    computed apart from the solver), and the ratio of successive A-norm errors
+    tends to rho(E).  An update that dropped x, flipped the correction's sign or
+    corrected with b instead of the residual fails the first bound."""
+    pr, H = tiny
+    A = H.levels[0].A.toarray()
+    n = A.shape[0]
+    M = O.make_vcycle(H)
+    Mm = np.column_stack([M(e) for e in np.eye(n)])
+    L = np.linalg.cholesky(A)
+    Et = L.T @ (np.eye(n) - Mm @ A) @ np.linalg.inv(L.T)      # E in the A inner product
+    assert np.max(np.abs(Et - Et.T)) <= 1e-10
+    rho = np.max(np.abs(np.linalg.eigvalsh(0.5 * (Et + Et.T))))
+    assert 0.0 < rho < 1.0
+    xs = np.linalg.solve(A, pr.rhs)
+    errs = [np.sqrt(xs @ A @ xs)]
+    for k in range(1, 26):
+        e = xs - O.stationary(H, pr.rhs, 1e-300, k).x
+        errs.append(np.sqrt(e @ A @ e))
+    for k in range(25):
+        assert errs[k + 1] <= rho * errs[k] * (1 + 1e-8) + 1e-13 * errs[0], k
+    late = (errs[25] / errs[20]) ** (1 / 5)
+    assert 0.9 * rho <= late <= rho * (1 + 1e-8), (late, rho)
+
+
+@pytest.mark.parametrize("seed,n_agg", [(1, 7), (2, 8), (3, 1), (4, 2)])
+def test_median_aggregate_dofs_is_the_lower_median(seed, n_agg):
+    """Section 4.2's r: the median dof count of the level-1 aggregates, the
+    lower one for an even count (statistics.median_low), on aggregates of
+    unequal sizes built from units of unequal dof counts."""
+    import statistics
+    rng = np.random.default_rng(seed)
+    n_units = 3 * n_agg + 2
+    dofs = rng.integers(1, 12, n_units)
+    unit_ptr = np.concatenate([[0], np.cumsum(dofs)])
+    agg = np.concatenate([np.arange(n_agg), rng.integers(0, n_agg, n_units - n_agg)])
+    rng.shuffle(agg)
+    sizes = [int(sum(dofs[u] for u in range(n_units) if agg[u] == a)) for a in range(n_agg)]
+    assert O.median_aggregate_dofs(agg, unit_ptr, n_agg) == statistics.median_low(sizes)
+
+
 def test_fp16_block_storage():
     """Values k/1024 of the block maximum are stored exactly; otherwise the
     dequantised value is within half an FP16 unit (2^-11 relative to the
