@@ -408,23 +408,26 @@ template cudaError_t launch_folded_sweep<float>(int, int, const int *, const int
 // matrix, more than that rate feeds at full HBM bandwidth.  The __f*_rn
 // intrinsics keep the compiler from contracting the two-sum into FMAs.
 // ----------------------------------------------------------------------------
-// One block row segment of the recurrence above: BC products joined to the
-// running pair (s, lo) in column order.
+// One product of the recurrence above joined to the running pair (s, lo).
+__device__ __forceinline__ void ds_product_add(float ah, float al, float xh, float xl, float &s,
+                                               float &lo) {
+  const float pr = __fmul_rn(ah, xh);
+  const float e = __fmaf_rn(ah, xh, -pr);
+  const float cross = __fmaf_rn(ah, xl, __fmul_rn(al, xh));
+  const float s1 = __fadd_rn(s, pr);
+  const float bp = __fsub_rn(s1, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s1, bp)), __fsub_rn(pr, bp));
+  s = s1;
+  lo = __fadd_rn(lo, __fadd_rn(err, __fadd_rn(e, cross)));
+}
+
+// One block row segment: BC products joined in column order.
 template <int BC>
 __device__ __forceinline__ void ds_row_accumulate(const float *ah, const float *al,
                                                   const float *xh, const float *xl, float &s,
                                                   float &lo) {
 #pragma unroll
-  for (int c = 0; c < BC; ++c) {
-    const float pr = __fmul_rn(ah[c], xh[c]);
-    const float e = __fmaf_rn(ah[c], xh[c], -pr);
-    const float cross = __fmaf_rn(ah[c], xl[c], __fmul_rn(al[c], xh[c]));
-    const float s1 = __fadd_rn(s, pr);
-    const float bp = __fsub_rn(s1, s);
-    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s1, bp)), __fsub_rn(pr, bp));
-    s = s1;
-    lo = __fadd_rn(lo, __fadd_rn(err, __fadd_rn(e, cross)));
-  }
+  for (int c = 0; c < BC; ++c) ds_product_add(ah[c], al[c], xh[c], xl[c], s, lo);
 }
 
 // With DOT the kernel also leaves per-CTA partial sums of x . y (x given in
@@ -456,17 +459,7 @@ bsr_mv_ds_kernel(int n_brows, int br, const int *__restrict__ rp, const int *__r
     for (int c = 0; c < BC; c += W) load_vec<float, W>(xhi + (size_t)j * BC + c, xh + c);
 #pragma unroll
     for (int c = 0; c < BC; c += W) load_vec<float, W>(xlo + (size_t)j * BC + c, xl + c);
-#pragma unroll
-    for (int c = 0; c < BC; ++c) {
-      const float pr = __fmul_rn(ah[c], xh[c]);
-      const float e = __fmaf_rn(ah[c], xh[c], -pr);
-      const float cross = __fmaf_rn(ah[c], xl[c], __fmul_rn(al[c], xh[c]));
-      const float s1 = __fadd_rn(s, pr);
-      const float bp = __fsub_rn(s1, s);
-      const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s1, bp)), __fsub_rn(pr, bp));
-      s = s1;
-      lo = __fadd_rn(lo, __fadd_rn(err, __fadd_rn(e, cross)));
-    }
+    ds_row_accumulate<BC>(ah, al, xh, xl, s, lo);
   }
   const double yt = (double)s + (double)lo;
   if (act) y[t] = yt;
@@ -565,14 +558,7 @@ bsr_mv_ds_generic(int n_brows, int br, int bc, const int *__restrict__ rp,
     for (int c = 0; c < bc; ++c) {
       const float ah = __ldg(ahi + off + c), al = __ldg(alo + off + c);
       const float xh = __ldg(xhi + (size_t)j * bc + c), xl = __ldg(xlo + (size_t)j * bc + c);
-      const float pr = __fmul_rn(ah, xh);
-      const float e = __fmaf_rn(ah, xh, -pr);
-      const float cross = __fmaf_rn(ah, xl, __fmul_rn(al, xh));
-      const float s1 = __fadd_rn(s, pr);
-      const float bp = __fsub_rn(s1, s);
-      const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s1, bp)), __fsub_rn(pr, bp));
-      s = s1;
-      lo = __fadd_rn(lo, __fadd_rn(err, __fadd_rn(e, cross)));
+      ds_product_add(ah, al, xh, xl, s, lo);
     }
   }
   y[t] = (double)s + (double)lo;
