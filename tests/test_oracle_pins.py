@@ -349,6 +349,50 @@ def test_gmres_finite_termination_and_direct():
     assert np.linalg.norm(res.x - x) <= 1e-8 * np.linalg.norm(x)
 
 
+def _min_residual_iterate(A, Mm, b, x0, k, right):
+    """Brute force: the iterate of k steps of minimal residual from x0 over the
+    Krylov space, built from explicit powers and orthonormalised by QR, with
+    the least-squares problem solved by lstsq.  Left preconditioning
+    minimises ||M (b - A x)|| over x0 + K_k(M A, M r0); right preconditioning
+    minimises ||b - A x|| over x0 + M K_k(A M, r0)."""
+    r0 = b - A @ x0
+    start, op = (r0, A @ Mm) if right else (Mm @ r0, Mm @ A)
+    K = [start]
+    for _ in range(k - 1):
+        K.append(op @ K[-1])
+    Q, _ = np.linalg.qr(np.column_stack(K))
+    c = np.linalg.lstsq(op @ Q, start, rcond=None)[0]
+    return x0 + (Mm @ (Q @ c) if right else Q @ c)
+
+
+@pytest.mark.parametrize("flexible", [False, True])
+def test_gmres_iterates_are_minimal_residual(flexible):
+    """Each GMRES iterate minimises the (left-preconditioned, or with
+    `flexible` the true) residual over its Krylov space, checked against a
+    brute-force least-squares solve for k = 1..6 steps, and a restart begins a
+    new minimisation from the last iterate (GMRES(3), two cycles).  A slip in
+    the Arnoldi orthogonalisation, the Givens rotations or the update of x
+    fails it."""
+    rng = np.random.default_rng(11)
+    n = 40
+    A = 3.0 * np.eye(n) + 0.4 * rng.standard_normal((n, n)) + np.triu(0.3 * rng.standard_normal((n, n)), 1)
+    Mm = np.diag(1.0 / np.diag(A)) + 0.02 * rng.standard_normal((n, n))
+    b = rng.standard_normal(n)
+    As = sp.csr_matrix(A)
+
+    def M(r):
+        return Mm @ r
+
+    for k in range(1, 7):
+        got = O.gmres(As, b, M, 1e-300, restart=30, max_iter=k, flexible=flexible).x
+        want = _min_residual_iterate(A, Mm, b, np.zeros(n), k, flexible)
+        assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want), k
+    got = O.gmres(As, b, M, 1e-300, restart=3, max_iter=6, flexible=flexible).x
+    x3 = _min_residual_iterate(A, Mm, b, np.zeros(n), 3, flexible)
+    want = _min_residual_iterate(A, Mm, b, x3, 3, flexible)
+    assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
+
+
 def test_gmres_and_fcg_on_workload(tiny):
     pr, H = tiny
     x = np.linalg.solve(H.levels[0].A.toarray(), pr.rhs)
