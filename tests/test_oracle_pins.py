@@ -326,6 +326,30 @@ def test_pcg_matches_direct_solve(tiny):
     assert np.linalg.norm(res.x - x) <= 1e-9 * np.linalg.norm(x)
 
 
+@pytest.mark.parametrize("flexible", [False, True])
+def test_pcg_iterates_minimise_the_energy_error(flexible):
+    """With SPD A and a fixed SPD preconditioner M, the k-th PCG iterate is
+    the point of K_k(M A, M b) nearest to x* in the A-norm (brute force: an
+    orthonormal basis of the explicit powers and the Galerkin system), for
+    k = 1..6, whether beta is the plain or the Polak-Ribiere one (they agree
+    for a fixed M).  A slip in alpha, the residual update or beta fails it."""
+    rng = np.random.default_rng(12)
+    n = 40
+    B = rng.standard_normal((n, n))
+    A = B @ B.T / n + 0.5 * np.eye(n)
+    C = rng.standard_normal((n, n))
+    Mm = np.diag(1.0 / np.diag(A)) + 0.01 * (C @ C.T) / n
+    b = rng.standard_normal(n)
+    for k in range(1, 7):
+        got = O.pcg(sp.csr_matrix(A), b, lambda r: Mm @ r, 1e-300, k, flexible=flexible).x
+        K = [Mm @ b]
+        for _ in range(k - 1):
+            K.append(Mm @ (A @ K[-1]))
+        Q, _ = np.linalg.qr(np.column_stack(K))
+        want = Q @ np.linalg.solve(Q.T @ A @ Q, Q.T @ b)
+        assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want), k
+
+
 def test_cg_finite_termination():
     """CG (M = I) on a matrix with k distinct eigenvalues converges in k steps."""
     lam = np.repeat([1.0, 3.0, 7.0, 20.0], 25)
