@@ -315,3 +315,37 @@ def test_hex_ldg_manufactured_solution_order():
     assert slope > 1.8, (errs, slope)
     m2 = HX.hex_mesh(2)
     assert np.linalg.eigvalsh(HX.ldg_hex(m2, 1).to_scipy().toarray())[0] > 0
+
+
+def test_serving_stream_recipe():
+    """The request stream of the serving benchmark: eight meshes, the first
+    half SIPG Poisson and the rest LDG convection-diffusion on quadrilaterals,
+    2^m cells per side, 1e3 - 2e6 dofs, orders 1 - 3, Peclet numbers from
+    {1, 100, 1e4}; the dof count formula agrees with the assembled operator on
+    the smallest meshes; mesh choices are in range and cover every mesh;
+    arrivals are increasing with mean gap 1 / rate."""
+    from synth import serving
+    specs = serving.mesh_specs(configs.SEED)
+    assert len(specs) == serving.N_MESHES
+    for j, sp_ in enumerate(specs):
+        assert sp_.kind == ("poisson" if j < serving.N_MESHES // 2 else "convdiff")
+        assert sp_.cells & (sp_.cells - 1) == 0
+        assert serving.MIN_DOFS <= sp_.dofs <= serving.MAX_DOFS
+        assert sp_.p in (1, 2, 3)
+        assert (sp_.peclet in (1.0, 100.0, 1e4)) == (sp_.kind == "convdiff")
+        if sp_.kind == "convdiff":
+            assert sp_.dim == 2
+    for sp_ in sorted(specs, key=lambda s: s.dofs)[:2]:
+        pr = serving.build_mesh(sp_)
+        assert pr.n_dofs == sp_.dofs
+        assert pr.r <= serving.R_CAP
+    which = serving.request_mesh(configs.SEED, 4000)
+    assert which.min() >= 0 and which.max() < serving.N_MESHES
+    assert set(which.tolist()) == set(range(serving.N_MESHES))
+    t = serving.arrival_times(configs.SEED, 4000, 50.0)
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert np.all(gaps > 0)
+    assert abs(gaps.mean() * 50.0 - 1.0) < 0.05
+    r0, r1 = serving.request_rhs(configs.SEED, 0, 100), serving.request_rhs(configs.SEED, 1, 100)
+    assert not np.array_equal(r0, r1)
+    assert np.array_equal(r0, serving.request_rhs(configs.SEED, 0, 100))
