@@ -289,9 +289,13 @@ def gmres_iteration_bytes(shapes, precision, iterations, restart=30, t_pre=3, t_
 # clocks during the timed region
 # ----------------------------------------------------------------------------
 class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region; the SM clock
+    reported is the median over the samples taken under load (GPU utilisation
+    of at least 50 %), throttle reasons are collected over every sample."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-              "clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_power_cap,utilization.gpu")
+    LOAD_UTIL = 50.0
 
     def __init__(self, device):
         self.device = device
@@ -320,25 +324,37 @@ class ClockSampler:
     def summary(self):
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm, mx, reasons = [], [], set()
+        with open(self.path) as f:
+            out = self.parse(f)
+        os.unlink(self.path)
+        return out
+
+    @classmethod
+    def parse(cls, lines):
+        sm, mx, loaded, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in lines:
             p = [x.strip() for x in line.split(",")]
             if len(p) < 7:
                 continue
             try:
-                sm.append(float(p[0]))
-                mx.append(float(p[1]))
+                clk, clk_max = float(p[0]), float(p[1])
             except ValueError:
                 continue
+            sm.append(clk)
+            mx.append(clk_max)
+            try:
+                if len(p) > 7 and float(p[7]) >= cls.LOAD_UTIL:
+                    loaded.append(clk)
+            except ValueError:
+                pass
             for nm, v in zip(names, p[3:7]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
-        os.unlink(self.path)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": float(np.median(loaded if loaded else sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm), "samples_under_load": len(loaded)}
 
 
 # ----------------------------------------------------------------------------

@@ -47,3 +47,30 @@ def test_dense_bottom_replaces_the_levels_below():
     p = bench.iteration_bytes(shapes, "mixed32", 3, 3)[1]
     assert "level1" not in p and "coarse" not in p
     assert p["dense_tail"] == 2 * 2 * 8 + 2 * 2 * 4
+
+
+def test_clock_summary_uses_samples_under_load():
+    """The clock record's SM clock is the median of the samples taken under
+    load; idle samples between launches do not pull it down, throttle
+    reasons seen in any sample are reported, malformed lines are skipped."""
+    import bench
+    lines = [
+        "2070, 2070, 900.1, Not Active, Not Active, Not Active, Not Active, 100",
+        "2055, 2070, 950.3, Not Active, Not Active, Not Active, Active, 98",
+        "2070, 2070, 940.0, Not Active, Not Active, Not Active, Not Active, 99",
+        "345, 2070, 120.0, Not Active, Not Active, Not Active, Not Active, 0",
+        "210, 2070, 110.0, Not Active, Not Active, Not Active, Not Active, 3",
+        "[N/A], 2070, 100.0, Not Active, Not Active, Not Active, Not Active, 0",
+        "garbage",
+    ]
+    out = bench.ClockSampler.parse(lines)
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["samples"] == 5 and out["samples_under_load"] == 3
+    assert out["reasons"] == ["sw_power_cap"]
+    hot = bench.ClockSampler.parse(["1500, 2070, 1300, Active, Not Active, Not Active, Not Active, 100"])
+    assert hot["reasons"] == ["hw_slowdown"] and hot["sm_mhz"] == 1500.0
+    # without a utilisation column every sample counts
+    old = bench.ClockSampler.parse(["2000, 2070, 900, Not Active, Not Active, Not Active, Not Active",
+                                    "1000, 2070, 900, Not Active, Not Active, Not Active, Not Active"])
+    assert old["sm_mhz"] == 1500.0 and old["samples_under_load"] == 0
+    assert bench.ClockSampler.parse([])["reasons"] == ["no samples"]
