@@ -78,7 +78,7 @@ bsr_mv_generic(int n_brows, int br, int bc, const int *__restrict__ rp,
 // two blocks' loads in flight, and the FMAs still run in block order (the
 // same bits as bsr_mv_kernel).  MINB caps the registers so that MINB CTAs of
 // 256 threads stay resident per SM.  On the 1.31M-dof P3 pattern (10 x 10
-// blocks, about 4 per row) MINB = 6 took a step from 47.0 to 40.7 us on
+// blocks, about 4 per row) MINB = 6 took a step from 49.1 to 43.2 us on
 // GB300; unrolling four blocks, or two without the register cap, was slower
 // (fewer resident warps).
 template <int BC, int MINB>
@@ -474,7 +474,7 @@ bsr_mv_ds_kernel(int n_brows, int br, const int *__restrict__ rp, const int *__r
 // both blocks' hi and lo rows and x segments are requested before the first
 // product, and the products join s and t in block order (the same bits as
 // bsr_mv_ds_kernel).  MINB = 4 caps the registers at 64.  On the 1.31M-dof
-// P3 pattern it took q = A p with p.q from 129 to 94 us on GB300.
+// P3 pattern it took q = A p with p.q from 116.8 to 83.6 us on GB300.
 template <int BC, bool DOT, int MINB>
 __global__ void __launch_bounds__(256, MINB)
 bsr_mv_ds_pair_kernel(int n_brows, int br, const int *__restrict__ rp, const int *__restrict__ col,
