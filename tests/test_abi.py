@@ -170,3 +170,22 @@ def test_single_ops_validate_before_device_work():
     assert L.gasa_server_add_mesh(None, None, None) == gasa.GASA_ERR_INVALID_ARG
     assert L.gasa_server_poll(None, ctypes.c_uint64(1), None, None) == gasa.GASA_ERR_INVALID_ARG
     assert L.gasa_server_destroy(None) == gasa.GASA_OK
+
+
+def test_level0_timing_program_builds(tmp_path):
+    """The stand-alone level-0 kernel timing program (csrc/bench_level0.cu),
+    whose build line the profile summaries quote, compiles and links against
+    the library's launchers (no GPU needed to build)."""
+    import shutil
+    gasa = _lib()
+    nvcc = os.environ.get("NVCC") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc) and not shutil.which("nvcc"):
+        pytest.skip("nvcc not found")
+    nvcc = nvcc if os.path.exists(nvcc) else "nvcc"
+    csrc = os.path.join(ROOT, "paper_2504_13373_gb300", "csrc")
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17",
+                    "-I" + os.path.join(ROOT, "include"), "-I" + csrc,
+                    os.path.join(csrc, "bench_level0.cu"), "-o", str(tmp_path / "bench_level0"),
+                    "-L" + os.path.dirname(gasa.LIB_PATH), "-lgasa"], check=True,
+                   capture_output=True)
+    assert (tmp_path / "bench_level0").exists()
